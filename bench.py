@@ -1,0 +1,358 @@
+"""Benchmark: QPS at recall@10 >= 0.90 of the IVF-PQ query path on one GB300.
+
+Workload (SIFT1M-shaped synthetic stand-in): 1,000,000 x 128 non-negative
+integer vectors 0..255, 10,000 queries, nlist 1024, M 64 x 4-bit, k 10,
+rerank 200; nprobe = the smallest of the grid 8..128 whose recall@10 (ties
+counted, FP64 ground truth) reaches 0.90.  One step = one search of the
+whole 10k-query batch (rank lists, LUTs, scan, select, rerank), inputs
+resident in HBM.  L2 is flushed (256 MB write) before every timed step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun): every rank holds a replica of the index and searches
+its own 10k-query batch (weak scaling, no collective on the data path).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CFG = dict(workload="ivfpq-sift1m-shape", n=1_000_000, d=128, nq=10_000, nlist=1024, M=64, nbits=4, k=10,
+           rerank=200, metric="l2")
+GRID = (8, 12, 16, 24, 32, 48, 64, 96, 128)
+METRIC = "QPS at recall@10\u22650.90 (1M\u00d7128, 1 GB300) vs plain path; ADC-scan HBM GB/s vs peak"
+TARGET_RECALL = 0.90
+L2_FLUSH_BYTES = 256 << 20
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("KSC_BENCH_GLOO") is None else "gloo")
+    return rank, ws
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, ws):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev_index):
+        self.dev = dev_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.p:
+            self.p.terminate()
+            try:
+                out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+                out, _ = self.p.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def exact_topk(torch, X, Q, k, chunk=512):
+    """FP64 brute-force top-k (ground truth for recall; ties by id)."""
+    Xd = X.double()
+    xn = (Xd * Xd).sum(1)
+    out_d, out_i = [], []
+    for b in range(0, Q.shape[0], chunk):
+        q = Q[b:b + chunk].double()
+        D = (q * q).sum(1, keepdim=True) - 2.0 * (q @ Xd.T) + xn[None]
+        d, i = torch.topk(D, k, dim=1, largest=False, sorted=True)
+        out_d.append(d.cpu().numpy())
+        out_i.append(i.cpu().numpy())
+    return np.concatenate(out_i), np.concatenate(out_d)
+
+
+def recall_at_10(torch, X, Q, ids, true_d, k=10):
+    """A returned id counts when its exact distance <= the true 10th distance."""
+    idt = torch.as_tensor(ids, device=X.device)
+    valid = idt >= 0
+    rows = X[idt.clamp_min(0)].double()
+    d = ((rows - Q.double()[:, None, :]) ** 2).sum(-1)
+    kth = torch.as_tensor(true_d[:, k - 1], device=X.device)[:, None]
+    hit = (d <= kth + 1e-9 * kth.abs().clamp_min(1.0)) & valid
+    return float(hit[:, :k].sum(1).clamp_max(k).double().mean().item() / k)
+
+
+def scan_work(ix_export_sizes, probes):
+    """Sum over (query, probe) of list sizes -> lookups and code bytes."""
+    sizes = ix_export_sizes[probes]
+    return int(sizes.sum())
+
+
+def run_ours(args, rank, ws):
+    import torch
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    barrier(ws)
+    from paper_2511_03298_gb300 import ksc, synth
+    ksc.lib()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    X = synth.base(2)
+    Qh = synth.queries(2)
+    Xd = torch.from_numpy(X).to(dev)
+    Qd = torch.from_numpy(Qh).to(dev)
+    t0 = time.time()
+    ix = ksc.build_index(Xd, CFG["nlist"], CFG["M"], perm=synth.build_perm(2, len(X)))
+    torch.cuda.synchronize()
+    build_s = time.time() - t0
+    k, R = CFG["k"], CFG["rerank"]
+    true_i, true_d = exact_topk(torch, Xd, Qd, k)
+    # operating point: smallest nprobe of the grid with recall >= 0.90
+    sweep = {}
+    nprobe = GRID[-1]
+    for P in GRID:
+        ids, _ = ix.search(Qd, k, P, R)
+        rec = recall_at_10(torch, Xd, Qd, ids, true_d, k)
+        sweep[P] = round(rec, 4)
+        if rec >= TARGET_RECALL:
+            nprobe = P
+            break
+    recall = sweep[nprobe]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    st = torch.cuda.current_stream()
+    ids = torch.empty((CFG["nq"], k), dtype=torch.int64, device=dev)
+    dists = torch.empty((CFG["nq"], k), dtype=torch.float32, device=dev)
+    ix.profile(True)
+    for _ in range(args.warmup):
+        ix.search(Qd, k, nprobe, R, out=(ids, dists))
+    torch.cuda.synchronize()
+    stage_ms = {s: [] for s in ksc.Index.STAGES}
+    step_ms = []
+    launches = 0
+    barrier(ws)
+    with Clocks(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            ix.search(Qd, k, nprobe, R, out=(ids, dists))
+            e1.record(st)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            prof, nl = ix.profile_read()
+            launches += nl
+            for s_, v in prof.items():
+                stage_ms[s_].append(v)
+    torch.cuda.synchronize()
+    barrier(ws)
+    ms = statistics.mean(step_ms)
+    ms_max = max_over_ranks(ms, ws)
+    value = CFG["nq"] * ws / (ms_max * 1e-3)
+    # end to end through the public API with host buffers
+    Qpin = torch.from_numpy(Qh).pin_memory()
+    ids_h = torch.empty((CFG["nq"], k), dtype=torch.int64).pin_memory()
+    d_h = torch.empty((CFG["nq"], k), dtype=torch.float32).pin_memory()
+    Qtmp = torch.empty_like(Qd)
+    e2e_ms = []
+    for it in range(args.warmup + args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        Qtmp.copy_(Qpin, non_blocking=True)
+        ix.search(Qtmp, k, nprobe, R, out=(ids, dists))
+        ids_h.copy_(ids, non_blocking=True)
+        d_h.copy_(dists, non_blocking=True)
+        e1.record(st)
+        e1.synchronize()
+        if it >= args.warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e = CFG["nq"] * ws / (max_over_ranks(statistics.mean(e2e_ms), ws) * 1e-3)
+    ix.profile(False)
+    # roofline of the dominant kernel (the LUT16 scan): lookups per launch
+    probes, _ = ix.rank_lists(Qd, nprobe, want_scores=False)
+    sizes = np.bincount(ix.export()["assign"], minlength=CFG["nlist"]) if rank == 0 else None
+    out = None
+    if rank == 0:
+        pr = probes.cpu().numpy()
+        pairs_vecs = int(sizes[pr].sum())
+        lookups = pairs_vecs * CFG["M"]
+        code_bytes = pairs_vecs * CFG["M"] // 2
+        scan_ms = statistics.mean(stage_ms["scan"])
+        peak_gl = ksc.lut16_peak()
+        achieved_gl = lookups / (scan_ms * 1e-3) / 1e9
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
+        cpu = cpu_baseline(ix, X, Qh, nprobe, R, k, true_d) if (ws == 1 and not args.no_cpu) else None
+        clocks = clk.summary()
+        out = {
+            "metric": METRIC,
+            "value": round(value, 1), "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_max, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8 LUT / int32 ADC, fp32 rank+rerank",
+            "data": "synthetic (seeded mixture, SIFT1M shape)",
+            "config": {"workload": CFG["workload"], "n": CFG["n"], "d": CFG["d"], "nq": CFG["nq"],
+                       "nlist": CFG["nlist"], "M": CFG["M"], "nbits": 4, "k": k, "rerank": R,
+                       "nprobe": nprobe, "recall@10": recall, "nprobe_sweep": sweep,
+                       "l2": "flushed (256 MB write) before every timed step", "parallelism": "replica x%d" % ws},
+            "recall@10": recall,
+            "e2e": {"value": round(e2e, 1), "unit": "queries/s",
+                    "h2d_bytes_per_step": int(Qh.nbytes), "d2h_bytes_per_step": int(ids_h.numel() * 12)},
+            "gpu_launches": launches,
+            "stage_ms": {s_: round(statistics.mean(v), 4) for s_, v in stage_ms.items()},
+            "roofline": {"bound": "alu", "kernel": "k_scan (LUT16 ADC scan)", "achieved": round(achieved_gl, 1),
+                         "peak": round(peak_gl, 1), "unit": "Glookup/s", "frac": round(achieved_gl / peak_gl, 4),
+                         "peak_source": "measured: ksc_lut16_peak (same instruction sequence, registers only)",
+                         "lookups_per_launch": lookups, "traffic": None,
+                         "code_bytes_per_launch": code_bytes,
+                         "effective_code_GBps": round(code_bytes / (scan_ms * 1e-3) / 1e9, 1),
+                         "hbm_peak_gbs": peaks.get("hbm_gbs")},
+            "clocks": clocks,
+            "build_s": round(build_s, 2),
+            "cpu_baseline": cpu,
+        }
+    return out
+
+
+def cpu_baseline(ix, X, Qh, nprobe, R, k, true_d, budget_s=12.0):
+    """The CPU oracle (as it stands) on a bounded sample of the same queries,
+    all host cores, on the same (exported) index."""
+    import oracle
+    e = ix.export()
+    oix = oracle.make_index(X, e["c_rank"], e["c_mean"], e["codebook"], e["codes"], e["assign"])
+    cores = os.cpu_count() or 1
+    n = 64
+    t0 = time.time()
+    oracle.search(oix, Qh[:n], nprobe, R, k, nthreads=cores)
+    dt = time.time() - t0
+    n2 = int(min(len(Qh), max(n, n * budget_s / max(dt, 1e-3))))
+    t0 = time.time()
+    res = oracle.search(oix, Qh[:n2], nprobe, R, k, nthreads=cores)
+    dt = time.time() - t0
+    rec = oracle.recall(Qh[:n2], X, res["ids"], true_d[:n2], 10)
+    return {"value": round(n2 / dt, 1), "unit": "queries/s", "cores": cores, "kind": "oracle",
+            "sample": "first %d of the 10k queries, same index / nprobe %d / rerank %d (OpenMP over queries)"
+                      % (n2, nprobe, R), "recall@10": round(rec, 4), "seconds": round(dt, 2)}
+
+
+def run_reference(args, rank, ws):
+    """The CPU oracle as the reference arm (FP64 except the 8-bit LUT rule),
+    timed on the host cores: its own index over the full 1M base (FP64 Lloyd,
+    OpenMP over rows), nprobe chosen on a 200-query sample with FP64 ground
+    truth, then each step searches a bounded sample of 256 queries."""
+    if rank != 0:
+        return None
+    import oracle
+    from paper_2511_03298_gb300 import synth
+    oracle.lib()
+    X = synth.base(2)
+    Qh = synth.queries(2)
+    cores = os.cpu_count() or 1
+    t0 = time.time()
+    ix = oracle.build_index(X, CFG["nlist"], CFG["M"], False, synth.build_perm(2, len(X)), iters=20)
+    build_s = time.time() - t0
+    k, R = CFG["k"], CFG["rerank"]
+    ns = 200
+    _, true_d = oracle.exact_knn(Qh[:ns], X, k, nthreads=cores)
+    nprobe, sweep = GRID[-1], {}
+    for P in GRID:
+        res = oracle.search(ix, Qh[:ns], P, R, k, nthreads=cores)
+        sweep[P] = round(oracle.recall(Qh[:ns], X, res["ids"], true_d, k), 4)
+        if sweep[P] >= TARGET_RECALL:
+            nprobe = P
+            break
+    per = 256
+    times = []
+    for it in range(args.warmup + args.steps):
+        b0 = (it * per) % (len(Qh) - per)
+        t0 = time.time()
+        oracle.search(ix, Qh[b0:b0 + per], nprobe, R, k, nthreads=cores)
+        if it >= args.warmup:
+            times.append(time.time() - t0)
+    v = per / statistics.mean(times)
+    return {"impl": "reference", "metric": METRIC,
+            "value": round(v, 1), "unit": "queries/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(statistics.mean(times) * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded mixture, SIFT1M shape)",
+            "config": {"workload": CFG["workload"], "n": CFG["n"], "d": CFG["d"], "nlist": CFG["nlist"],
+                       "M": CFG["M"], "k": k, "rerank": R, "nprobe": nprobe, "recall@10": sweep[nprobe],
+                       "nprobe_sweep": sweep, "queries_per_step": per, "oracle_build_s": round(build_s, 1)},
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "value": round(v, 1),
+                             "sample": "%d queries per step of the 10k, full 1M index built by the oracle" % per},
+            "e2e": {"value": round(v, 1), "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank, ws = dist_setup()
+    out = run_reference(args, rank, ws) if args.impl == "reference" else run_ours(args, rank, ws)
+    if rank == 0 and out is not None:
+        print(json.dumps(out))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,189 @@
+/*
+ * kscann.h -- C ABI of the GB300-native KScaNN query path.
+ *
+ * Method: "KScaNN: Scalable ANN Search on Kunpeng" (arXiv 2511.03298).
+ *   build  : Alg. 1 (IVF k-means, PQ with K = 16 on residuals, SIMD blocks,
+ *            intra-cluster graphs) with the mean-centroid residual of Sec. 4.6.1.
+ *   search : Alg. 2 / Alg. 3 -- rank IVF centroids, per-query residual LUTs
+ *            quantised to 8 bits (Sec. 2.5, Sec. 4.5), LUT16 ADC scan of the
+ *            probed lists (Eq. 1), candidate pool of size `rerank` (the paper's
+ *            `reorder`, Table 1), exact re-rank, top-k.
+ *
+ * Conventions (every entry point):
+ *  - Array arguments named *_dev are DEVICE pointers, caller-allocated, read or
+ *    written in order on `stream` (a cudaStream_t passed as void*; NULL = the
+ *    legacy default stream).  Arguments named *_host are host pointers.
+ *  - Every call is asynchronous on `stream` unless stated; results are valid
+ *    once the caller synchronises that stream.
+ *  - Return value: a ksc_status.  On failure nothing has been enqueued unless
+ *    stated, and ksc_last_error() returns a message (thread-local).
+ *  - Row-major layouts: X [n x d] fp32, Q [nq x d] fp32, ids [nq x k] int64,
+ *    dists [nq x k] fp32.  Ids are row numbers of X (n < 2^31).
+ *  - Distances returned: L2 -> squared Euclidean distance, ascending;
+ *    IP -> inner product (similarity), descending.  Ties -> lower id.
+ *    Fewer than k results: id -1 and dist +inf (L2) / -inf (IP).
+ *  - An index is read-only during search; searches on different streams may
+ *    run concurrently only with distinct workspaces (see ksc_search_opts).
+ */
+#ifndef KSCANN_H
+#define KSCANN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ksc_index ksc_index; /* opaque; owns its device memory */
+
+typedef enum {
+    KSC_OK = 0,
+    KSC_EINVAL = -1,        /* bad argument (null pointer, size out of range) */
+    KSC_ENOMEM = -2,        /* device or host allocation failed */
+    KSC_ECUDA = -3,         /* a CUDA runtime call failed */
+    KSC_EUNSUPPORTED = -4,  /* valid but unsupported (e.g. nbits != 4) */
+    KSC_ETIMEOUT = -5,      /* a bounded device wait gave up */
+    KSC_ESTATE = -6         /* object in the wrong state (e.g. no MLP trained) */
+} ksc_status;
+
+typedef enum { KSC_L2 = 0, KSC_IP = 1 } ksc_metric;
+
+/* Limits of this implementation (EINVAL beyond them). */
+#define KSC_MAX_DIM 1024       /* d */
+#define KSC_MAX_M 256          /* PQ subspaces: 256 * 255 < 2^16, u16 lane sums never saturate */
+#define KSC_MAX_RERANK 4096    /* candidate pool size R */
+#define KSC_MAX_K 1024         /* results per query, k <= R */
+#define KSC_MAX_NLIST 65536
+
+/* ------------------------------------------------------------------ */
+/* Index construction (Alg. 1)                                         */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int32_t kmeans_iters;      /* Lloyd iterations for IVF and PQ k-means; 0 -> 20 */
+    int32_t spherical;         /* 1: rank lists by -<q, c/|c|> (angular data, Sec. 4.6.1);
+                                  forced to 1 for KSC_IP */
+    const int64_t* perm_host;  /* optional: a permutation of 0..n-1 (host); the IVF
+                                  k-means sample is its first min(n, 256 nlist) rows and
+                                  also its initial centroids, the PQ sample its first
+                                  min(n, 65536).  NULL: the library draws one (seed). */
+    uint64_t seed;             /* used when perm_host is NULL */
+    int32_t build_graph;       /* 1: build the per-list 32-NN graphs of Sec. 4.4 */
+} ksc_build_opts;
+
+/* Build an IVF-PQ index from X_dev [n x d] fp32 (device).  nlist = L IVF lists,
+ * M PQ subspaces (d % M == 0), nbits must be 4 (K = 16; KSC_EUNSUPPORTED
+ * otherwise).  The index copies X (for the exact re-rank).  Blocking: returns
+ * after the build has finished on `stream`.  *out is set on success. */
+int ksc_build_index(const float* X_dev, int64_t n, int32_t d, int32_t nlist, int32_t M,
+                    int32_t nbits, ksc_metric metric, const ksc_build_opts* opts,
+                    void* stream, ksc_index** out);
+
+void ksc_index_free(ksc_index* ix);
+
+/* Interchange form of an index, all HOST arrays (used to move an index
+ * between this library and other programs).  Codes are unpacked: one byte
+ * (0..15) per (vector, subspace).  graph/entry are optional (NULL). */
+typedef struct {
+    int64_t n;
+    int32_t d, nlist, M, metric, spherical;
+    float* X;         /* [n x d] */
+    float* c_rank;    /* [nlist x d] centroids used to rank lists */
+    float* c_mean;    /* [nlist x d] mean centroids used for residuals (Sec. 4.6.1) */
+    float* codebook;  /* [M x 16 x d/M] */
+    uint8_t* codes;   /* [n x M] */
+    int32_t* assign;  /* [n] list of each vector */
+    int32_t* graph;   /* [n x 32] neighbours inside the list, -1 padded (optional) */
+    int32_t* entry;   /* [nlist] graph entry node per list, -1 if empty (optional) */
+} ksc_index_arrays;
+
+/* Create an index from host arrays (copied; the caller keeps ownership).
+ * Blocking. */
+int ksc_index_import(const ksc_index_arrays* a, void* stream, ksc_index** out);
+
+/* Query the sizes of an index: fills n, d, nlist, M, metric, spherical of *a
+ * and leaves the pointers untouched. */
+int ksc_index_info(const ksc_index* ix, ksc_index_arrays* a);
+
+/* Copy an index out into caller-allocated host arrays sized from
+ * ksc_index_info (pointers left NULL are skipped).  Blocking. */
+int ksc_index_export(const ksc_index* ix, ksc_index_arrays* a);
+
+/* ------------------------------------------------------------------ */
+/* Search (Alg. 2, Alg. 3)                                             */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int32_t lanes_per_query;   /* scan kernel: 0 auto, or 8/16/32 lanes share a query */
+    int32_t hybrid;            /* 1: hybrid intra-cluster search of Sec. 4.4 (needs graphs) */
+    int32_t n_near;            /* hybrid: probes of rank < n_near are scanned fully (2) */
+    int32_t efs;               /* hybrid: graph-search result capacity (64) */
+    int32_t tau;               /* hybrid: full scan when >= tau results beat theta (8) */
+    int32_t cand_cap;          /* candidate store per query; 0 -> max(8R, 2048) */
+} ksc_search_opts;
+
+/* k nearest neighbours of Q_dev [nq x d] with a fixed nprobe (1..nlist) and
+ * candidate pool rerank (R, clamped up to k).  ids_dev [nq x k] int64,
+ * dists_dev [nq x k] fp32.  opts may be NULL. */
+int ksc_search(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t k, int32_t nprobe,
+               int32_t rerank, int64_t* ids_dev, float* dists_dev,
+               const ksc_search_opts* opts, void* stream);
+
+/* As ksc_search with per-query nprobe_dev [nq] and rerank_dev [nq] (int32,
+ * device); nprobe_max / rerank_max bound them (values are clamped into
+ * [1, nprobe_max] and [k, rerank_max]). */
+int ksc_search_varprobe(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t k,
+                        const int32_t* nprobe_dev, int32_t nprobe_max,
+                        const int32_t* rerank_dev, int32_t rerank_max,
+                        int64_t* ids_dev, float* dists_dev,
+                        const ksc_search_opts* opts, void* stream);
+
+/* Test entry: search with caller-given probe lists probes_dev [nq x P]
+ * (list ids, in rank order).  Optional outputs (NULL to skip):
+ * cand_dev [nq x R] uint64 candidate keys ((D + 2^31) << 32 | id), sorted
+ * ascending, padded with all-ones; ncand_dev [nq] int32 number of candidates. */
+int ksc_search_with_probes(ksc_index* ix, const float* Q_dev, int64_t nq, const int32_t* probes_dev,
+                           int32_t P, int32_t k, int32_t rerank, int64_t* ids_dev, float* dists_dev,
+                           uint64_t* cand_dev, int32_t* ncand_dev,
+                           const ksc_search_opts* opts, void* stream);
+
+/* Step a1 alone (TopNClusters of Alg. 2): the P best lists per query,
+ * probes_dev [nq x P] int32, scores_dev [nq x P] fp32 (L2 distance to the
+ * ranking centroid, or -<q, c> for spherical indexes); scores may be NULL. */
+int ksc_rank_lists(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t P, int32_t* probes_dev,
+                   float* scores_dev, void* stream);
+
+/* Step a2 alone: quantised LUTs lut_dev [nq x P x M x 16] uint8, biases
+ * bias_dev [nq x P] int32 and scales scale_dev [nq] fp32 for the given probes. */
+int ksc_compute_luts(ksc_index* ix, const float* Q_dev, int64_t nq, const int32_t* probes_dev,
+                     int32_t P, uint8_t* lut_dev, int32_t* bias_dev, float* scale_dev, void* stream);
+
+/* Device status word of the last search on this index: 0 = clean, else a
+ * bitwise OR of KSC_STATUS_* (blocking read). */
+#define KSC_STATUS_CAND_OVERFLOW 1  /* a query's candidate store overflowed and was redone exactly */
+int ksc_last_status(ksc_index* ix, int32_t* status_host);
+
+/* Stage timing of searches on this index (CUDA events recorded on the
+ * search stream; off by default).  Stages, in order: 0 rank lists (a1),
+ * 1 LUT build + quantise (a2), 2 threshold pre-pass, 3 work list, 4 LUT16
+ * scan (a3), 5 candidate select (a5), 6 rerank (a6).  ksc_profile_read
+ * synchronises with the last profiled search and writes its per-stage
+ * milliseconds into ms_host[0..n) (n <= 8) and the number of kernels it
+ * launched into *launches_host (may be NULL). */
+#define KSC_NUM_STAGES 7
+int ksc_profile_enable(ksc_index* ix, int32_t on);
+int ksc_profile_read(ksc_index* ix, float* ms_host, int32_t n, int32_t* launches_host);
+
+/* Diagnostic: runs the scan's lookup/accumulate instruction sequence from
+ * registers (no memory traffic) on every SM and returns the rate reached in
+ * 10^9 lookups per second (the integer-ALU ceiling of the a3 scan).  Blocking. */
+int ksc_lut16_peak(double* glookups_host, void* stream);
+
+/* Message of the last failure on this thread ("" if none). */
+const char* ksc_last_error(void);
+
+/* Library version string. */
+const char* ksc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KSCANN_H */

@@ -18,6 +18,8 @@
  * ascending, so each has exactly one answer.
  *
  * Parity status per function is listed in the docstrings of oracle/oracle.py.
+ * OpenMP only spreads independent rows or queries over threads; it changes
+ * no arithmetic (every sum over rows stays sequential).
  */
 #include <math.h>
 #include <stdint.h>
@@ -76,6 +78,9 @@ int orc_kmeans(const float* X, int64_t ld, int32_t col0, int32_t d,
     int64_t* cnt = (int64_t*)malloc(sizeof(int64_t) * L);
     for (int it = 0; it <= iters; ++it) {
         double o = 0.0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) reduction(+ : o)
+#endif
         for (int64_t s = 0; s < ns; ++s) {
             const float* x = X + sample[s] * ld + col0;
             double best = INFINITY; int32_t bi = 0;
@@ -134,6 +139,9 @@ int orc_build_index(const float* X, int64_t n, int32_t d, int32_t L, int32_t M,
         for (int t = 0; t < d; ++t) c_rank[(int64_t)c * d + t] = (float)(C[(int64_t)c * d + t] * s);
     }
     /* list assignment by the ranking score, computed from the stored fp32 c_rank */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
     for (int64_t i = 0; i < n; ++i) {
         const float* x = X + i * d;
         double best = INFINITY; int32_t bi = 0;
@@ -174,6 +182,9 @@ int orc_build_index(const float* X, int64_t n, int32_t d, int32_t L, int32_t M,
         for (int i = 0; i < ORC_K * dsub; ++i) codebook[(int64_t)j * ORC_K * dsub + i] = (float)Cj[i];
     }
     free(Rs); free(seq); free(Cj);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
     for (int64_t i = 0; i < n; ++i) {
         for (int j = 0; j < M; ++j) {
             double best = INFINITY; int bi = 0;

@@ -1,0 +1,170 @@
+// Shared device/host helpers of the KScaNN CUDA library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/kscann.h"
+
+namespace ksc {
+
+// ------------------------------------------------------------------ errors
+void set_error(const char* fmt, ...);
+const char* get_error();
+
+#define KSC_CHECK_ARG(cond, ...)              \
+    do {                                      \
+        if (!(cond)) {                        \
+            ::ksc::set_error(__VA_ARGS__);    \
+            return KSC_EINVAL;                \
+        }                                     \
+    } while (0)
+
+#define KSC_CUDA(call)                                                                  \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            ::ksc::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),    \
+                             __FILE__, __LINE__);                                       \
+            return e_ == cudaErrorMemoryAllocation ? KSC_ENOMEM : KSC_ECUDA;            \
+        }                                                                               \
+    } while (0)
+
+#define KSC_LAUNCH_CHECK() KSC_CUDA(cudaGetLastError())
+
+#define KSC_TRY(expr)                 \
+    do {                              \
+        int rc_ = (expr);             \
+        if (rc_ != KSC_OK) return rc_; \
+    } while (0)
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// ------------------------------------------------------------------ keys
+// Candidate key: lexicographic (D, id) as one unsigned 64-bit integer.
+__host__ __device__ __forceinline__ uint64_t make_key(int32_t D, int32_t id) {
+    return ((uint64_t)((uint32_t)D ^ 0x80000000u) << 32) | (uint64_t)(uint32_t)id;
+}
+// Order-preserving map of a (non-NaN) fp32 value to uint32.
+__host__ __device__ __forceinline__ uint32_t ordered_f32(float f) {
+    uint32_t u;
+#ifdef __CUDA_ARCH__
+    u = __float_as_uint(f);
+#else
+    memcpy(&u, &f, 4);
+#endif
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__host__ __device__ __forceinline__ float unordered_f32(uint32_t u) {
+    u = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
+    float f;
+#ifdef __CUDA_ARCH__
+    f = __uint_as_float(u);
+#else
+    memcpy(&f, &u, 4);
+#endif
+    return f;
+}
+constexpr uint64_t KEY_NONE = ~0ull;
+
+// ------------------------------------------------------------------ block sort / select
+// Bitonic sort, ascending, of S (power of two) keys in shared memory.
+__device__ __forceinline__ void block_bitonic_sort(uint64_t* s, int S) {
+    for (int k = 2; k <= S; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < S; i += blockDim.x) {
+                int ixj = i ^ j;
+                if (ixj > i) {
+                    uint64_t a = s[i], b = s[ixj];
+                    bool up = (i & k) == 0;
+                    if ((a > b) == up) { s[i] = b; s[ixj] = a; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__host__ __device__ __forceinline__ int pow2_ceil(int x) {
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+// K smallest of N unique keys produced by load(i), i in [0, N), written sorted
+// to out[0..K) (K <= N).  buf: shared buffer of `cap` keys (cap a power of two,
+// cap >= K); hist: 256 shared uint32.  Radix select (8-bit digits, most
+// significant first) when N > cap, then one bitonic sort of the K survivors.
+template <class Load>
+__device__ void block_select_smallest(Load load, int N, int K, uint64_t* out, uint64_t* buf, int cap,
+                                      uint32_t* hist) {
+    __shared__ uint64_t s_prefix, s_mask;
+    __shared__ int s_krem, s_cnt;
+    if (K <= 0) return;
+    if (N <= cap) {
+        int S = pow2_ceil(N);
+        for (int i = threadIdx.x; i < S; i += blockDim.x) buf[i] = i < N ? load(i) : KEY_NONE;
+        __syncthreads();
+        block_bitonic_sort(buf, S);
+        for (int i = threadIdx.x; i < K; i += blockDim.x) out[i] = buf[i];
+        __syncthreads();
+        return;
+    }
+    if (threadIdx.x == 0) { s_prefix = 0; s_mask = 0; s_krem = K; }
+    __syncthreads();
+    for (int shift = 56; shift >= 0; shift -= 8) {
+        for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0;
+        __syncthreads();
+        uint64_t pre = s_prefix, msk = s_mask;
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            uint64_t k = load(i);
+            if ((k & msk) == pre) atomicAdd(&hist[(k >> shift) & 255], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int krem = s_krem, acc = 0, b = 0;
+            for (; b < 256; ++b) {
+                if (acc + (int)hist[b] >= krem) break;
+                acc += hist[b];
+            }
+            s_krem = krem - acc;
+            s_prefix = pre | ((uint64_t)b << shift);
+            s_mask = msk | (255ull << shift);
+        }
+        __syncthreads();
+    }
+    // s_prefix is now the K-th smallest key: gather every key <= it.
+    uint64_t kth = s_prefix;
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        uint64_t k = load(i);
+        if (k <= kth) {
+            int slot = atomicAdd(&s_cnt, 1);
+            if (slot < cap) buf[slot] = k;
+        }
+    }
+    __syncthreads();
+    int S = pow2_ceil(K);
+    for (int i = s_cnt + threadIdx.x; i < S; i += blockDim.x) buf[i] = KEY_NONE;
+    __syncthreads();
+    block_bitonic_sort(buf, S);
+    for (int i = threadIdx.x; i < K; i += blockDim.x) out[i] = buf[i];
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------ workspace
+// Grow-only device buffers owned by an index (one per role).  Growing
+// synchronises the stream before freeing the old buffer.
+struct Buffer {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+int ensure(Buffer& b, size_t bytes, cudaStream_t st);
+void release(Buffer& b);
+
+int num_sms();
+
+}  // namespace ksc

@@ -1,0 +1,56 @@
+// Device-resident IVF-PQ index (Alg. 1 output) and its search workspace.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+// Block layout of the 4-bit codes (GPU-internal): every list is cut into
+// blocks of 32 vectors (the paper's SIMD data blocks, Sec. 4.5.3).  A block
+// stores M chunks of 16 bytes, one per subspace j (subspace-major); byte i
+// of chunk j holds code_j of vector 2i in its low nibble and of vector 2i+1
+// in its high nibble.  Hence the 32-bit word w of chunk j carries the codes
+// of vectors 8w..8w+7, vector 8w+t in bits 4t..4t+3.
+constexpr int BLOCK_VECS = 32;
+constexpr int PQ_K = 16;
+
+struct ksc_index {
+    int64_t n = 0;
+    int32_t d = 0, L = 0, M = 0, dsub = 0, metric = KSC_L2, spherical = 0;
+    int64_t nblocks = 0;
+    int32_t max_list = 0;
+    // device arrays
+    float* X = nullptr;          // [n x d]
+    float* c_rank = nullptr;     // [L x d]
+    float* c_rank_sq = nullptr;  // [L] ||c_rank||^2
+    float* c_mean = nullptr;     // [L x d]
+    float* codebook = nullptr;   // [M x 16 x dsub]
+    int64_t* list_boff = nullptr;  // [L + 1] first block of each list
+    int32_t* list_n = nullptr;     // [L] list sizes
+    int32_t* blk_ids = nullptr;    // [nblocks x 32] ids, -1 padding
+    uint8_t* blk_codes = nullptr;  // [nblocks x M x 16]
+    int32_t* assign = nullptr;     // [n]
+    int32_t* graph = nullptr;      // [n x 32] optional
+    int32_t* entry = nullptr;      // [L] optional
+    int32_t* status = nullptr;     // device status word
+    // host mirrors
+    std::vector<int64_t> h_boff;   // [L + 1]
+    std::vector<int32_t> h_n;      // [L]
+    // stage timing (ksc_profile_enable)
+    bool prof = false;
+    cudaEvent_t ev[KSC_NUM_STAGES + 1] = {};
+    bool ev_used[KSC_NUM_STAGES + 1] = {};
+    int32_t launches = 0;
+    // search workspace
+    ksc::Buffer ws_scores, ws_probes, ws_lut, ws_bias, ws_scale, ws_range, ws_thr, ws_cnt,
+        ws_cand, ws_topr, ws_nprobe, ws_rerank, ws_items, ws_misc;
+};
+
+namespace ksc {
+// Fill blk_ids / blk_codes / list tables from unpacked codes [n x M] (device)
+// and the list of each vector (host copy), members in ascending id order.
+int pack_lists(ksc_index* ix, const uint8_t* codes_dev, const int32_t* assign_host, cudaStream_t st);
+int free_index_memory(ksc_index* ix);
+// Per-list 32-NN graphs and entry points for the hybrid search (Sec. 4.4).
+int build_graph(ksc_index* ix, cudaStream_t st);
+}  // namespace ksc

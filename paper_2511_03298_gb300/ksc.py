@@ -1,0 +1,279 @@
+"""Thin ctypes binding of the CUDA library (include/kscann.h).
+
+Argument marshalling only: every step of the search runs in the library's
+kernels.  Device arrays are torch CUDA tensors (plumbing for memory and
+streams); the calls run on torch's current stream.  Importing this module
+does not load the library; the first call does, and fails loudly if the
+library has not been built (`__graft_entry__.build()`).
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build_ext import LIB
+
+_lib = None
+
+KSC_L2, KSC_IP = 0, 1
+STATUS_CAND_OVERFLOW = 1
+ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EUNSUPPORTED", -5: "ETIMEOUT", -6: "ESTATE"}
+
+
+class KscError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
+        self.code = code
+
+
+class BuildOpts(C.Structure):
+    _fields_ = [("kmeans_iters", C.c_int32), ("spherical", C.c_int32), ("perm_host", C.c_void_p),
+                ("seed", C.c_uint64), ("build_graph", C.c_int32)]
+
+
+class IndexArrays(C.Structure):
+    _fields_ = [("n", C.c_int64), ("d", C.c_int32), ("nlist", C.c_int32), ("M", C.c_int32),
+                ("metric", C.c_int32), ("spherical", C.c_int32),
+                ("X", C.c_void_p), ("c_rank", C.c_void_p), ("c_mean", C.c_void_p), ("codebook", C.c_void_p),
+                ("codes", C.c_void_p), ("assign", C.c_void_p), ("graph", C.c_void_p), ("entry", C.c_void_p)]
+
+
+class SearchOpts(C.Structure):
+    _fields_ = [("lanes_per_query", C.c_int32), ("hybrid", C.c_int32), ("n_near", C.c_int32),
+                ("efs", C.c_int32), ("tau", C.c_int32), ("cand_cap", C.c_int32)]
+
+
+_vp, _i32, _i64 = C.c_void_p, C.c_int32, C.c_int64
+_SIGS = {
+    "ksc_build_index": [_vp, _i64, _i32, _i32, _i32, _i32, _i32, _vp, _vp, _vp],
+    "ksc_index_free": [_vp],
+    "ksc_index_import": [_vp, _vp, _vp],
+    "ksc_index_info": [_vp, _vp],
+    "ksc_index_export": [_vp, _vp],
+    "ksc_search": [_vp, _vp, _i64, _i32, _i32, _i32, _vp, _vp, _vp, _vp],
+    "ksc_search_varprobe": [_vp, _vp, _i64, _i32, _vp, _i32, _vp, _i32, _vp, _vp, _vp, _vp],
+    "ksc_search_with_probes": [_vp, _vp, _i64, _vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp],
+    "ksc_rank_lists": [_vp, _vp, _i64, _i32, _vp, _vp, _vp],
+    "ksc_compute_luts": [_vp, _vp, _i64, _vp, _i32, _vp, _vp, _vp, _vp],
+    "ksc_last_status": [_vp, _vp],
+    "ksc_profile_enable": [_vp, _i32],
+    "ksc_profile_read": [_vp, _vp, _i32, _vp],
+    "ksc_lut16_peak": [_vp, _vp],
+    "ksc_last_error": [],
+    "ksc_version": [],
+}
+
+
+def lib_path():
+    return LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError("CUDA library %s is missing: run __graft_entry__.build() first" % LIB)
+        L = C.CDLL(LIB)
+        for name, args in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = C.c_int
+        L.ksc_last_error.restype = C.c_char_p
+        L.ksc_version.restype = C.c_char_p
+        L.ksc_index_free.restype = None
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise KscError(rc, lib().ksc_last_error().decode())
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dptr(t, dtype=None, name="tensor"):
+    torch = _torch()
+    if t is None:
+        return None
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+        raise ValueError("%s must be a contiguous CUDA tensor" % name)
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError("%s must have dtype %s" % (name, dtype))
+    return C.c_void_p(t.data_ptr())
+
+
+def _hptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def search_opts(lanes_per_query=0, hybrid=False, n_near=2, efs=64, tau=8, cand_cap=0):
+    return SearchOpts(lanes_per_query, int(hybrid), n_near, efs, tau, cand_cap)
+
+
+class Index:
+    """An index resident on the GPU (owned by the library)."""
+
+    def __init__(self, handle):
+        self._h = C.c_void_p(handle)
+
+    def __del__(self):
+        self.free()
+
+    def free(self):
+        if getattr(self, "_h", None) and self._h.value and _lib is not None:
+            _lib.ksc_index_free(self._h)
+        self._h = C.c_void_p(None)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self):
+        a = IndexArrays()
+        _check(lib().ksc_index_info(self._h, C.byref(a)))
+        return dict(n=a.n, d=a.d, nlist=a.nlist, M=a.M, metric=a.metric, spherical=a.spherical)
+
+    def export(self, with_graph=False):
+        inf = self.info()
+        n, d, L, M = inf["n"], inf["d"], inf["nlist"], inf["M"]
+        out = dict(X=np.zeros((n, d), np.float32), c_rank=np.zeros((L, d), np.float32),
+                   c_mean=np.zeros((L, d), np.float32), codebook=np.zeros((M, 16, d // M), np.float32),
+                   codes=np.zeros((n, M), np.uint8), assign=np.zeros(n, np.int32))
+        if with_graph:
+            out["graph"] = np.zeros((n, 32), np.int32)
+            out["entry"] = np.zeros(L, np.int32)
+        a = IndexArrays(n, d, L, M, inf["metric"], inf["spherical"],
+                        *[_hptr(out.get(k)) for k in ("X", "c_rank", "c_mean", "codebook", "codes", "assign",
+                                                      "graph", "entry")])
+        _check(lib().ksc_index_export(self._h, C.byref(a)))
+        out.update(inf)
+        return out
+
+    def search(self, Q, k, nprobe, rerank, opts=None, out=None, stream=None):
+        torch = _torch()
+        nq = Q.shape[0]
+        ids, dists = out if out is not None else (
+            torch.empty((nq, k), dtype=torch.int64, device=Q.device),
+            torch.empty((nq, k), dtype=torch.float32, device=Q.device))
+        _check(lib().ksc_search(self._h, _dptr(Q, torch.float32, "Q"), nq, k, nprobe, rerank,
+                                _dptr(ids), _dptr(dists), C.byref(opts) if opts else None, _stream(stream)))
+        return ids, dists
+
+    def search_varprobe(self, Q, k, nprobe, rerank, nprobe_max=None, rerank_max=None, opts=None, stream=None):
+        torch = _torch()
+        nq = Q.shape[0]
+        ids = torch.empty((nq, k), dtype=torch.int64, device=Q.device)
+        dists = torch.empty((nq, k), dtype=torch.float32, device=Q.device)
+        pm = int(nprobe.max().item()) if nprobe_max is None else nprobe_max
+        rm = int(rerank.max().item()) if rerank_max is None else rerank_max
+        _check(lib().ksc_search_varprobe(self._h, _dptr(Q, torch.float32, "Q"), nq, k,
+                                         _dptr(nprobe, torch.int32, "nprobe"), pm,
+                                         _dptr(rerank, torch.int32, "rerank"), rm,
+                                         _dptr(ids), _dptr(dists), C.byref(opts) if opts else None,
+                                         _stream(stream)))
+        return ids, dists
+
+    def search_with_probes(self, Q, probes, k, rerank, want_cands=True, opts=None, stream=None):
+        torch = _torch()
+        nq, P = probes.shape
+        R = max(rerank, k)
+        ids = torch.empty((nq, k), dtype=torch.int64, device=Q.device)
+        dists = torch.empty((nq, k), dtype=torch.float32, device=Q.device)
+        cand = torch.empty((nq, R), dtype=torch.int64, device=Q.device) if want_cands else None
+        ncand = torch.empty((nq,), dtype=torch.int32, device=Q.device) if want_cands else None
+        _check(lib().ksc_search_with_probes(self._h, _dptr(Q, torch.float32, "Q"), nq,
+                                            _dptr(probes, torch.int32, "probes"), P, k, rerank,
+                                            _dptr(ids), _dptr(dists), _dptr(cand), _dptr(ncand),
+                                            C.byref(opts) if opts else None, _stream(stream)))
+        return ids, dists, cand, ncand
+
+    def rank_lists(self, Q, P, want_scores=True, stream=None):
+        torch = _torch()
+        nq = Q.shape[0]
+        probes = torch.empty((nq, P), dtype=torch.int32, device=Q.device)
+        scores = torch.empty((nq, P), dtype=torch.float32, device=Q.device) if want_scores else None
+        _check(lib().ksc_rank_lists(self._h, _dptr(Q, torch.float32, "Q"), nq, P, _dptr(probes),
+                                    _dptr(scores), _stream(stream)))
+        return probes, scores
+
+    def compute_luts(self, Q, probes, stream=None):
+        torch = _torch()
+        nq, P = probes.shape
+        M = self.info()["M"]
+        lut = torch.empty((nq, P, M, 16), dtype=torch.uint8, device=Q.device)
+        bias = torch.empty((nq, P), dtype=torch.int32, device=Q.device)
+        scale = torch.empty((nq,), dtype=torch.float32, device=Q.device)
+        _check(lib().ksc_compute_luts(self._h, _dptr(Q, torch.float32, "Q"), nq,
+                                      _dptr(probes, torch.int32, "probes"), P, _dptr(lut), _dptr(bias),
+                                      _dptr(scale), _stream(stream)))
+        return lut, bias, scale
+
+    STAGES = ("rank", "lut", "prepass", "worklist", "scan", "select", "rerank")
+
+    def profile(self, on=True):
+        _check(lib().ksc_profile_enable(self._h, int(on)))
+
+    def profile_read(self):
+        """Per-stage milliseconds of the last search (dict) and its kernel count."""
+        ms = (C.c_float * 8)()
+        n = C.c_int32(0)
+        _check(lib().ksc_profile_read(self._h, ms, len(self.STAGES), C.byref(n)))
+        return {k: ms[i] for i, k in enumerate(self.STAGES)}, n.value
+
+    def last_status(self):
+        s = C.c_int32(0)
+        _check(lib().ksc_last_status(self._h, C.byref(s)))
+        return s.value
+
+
+def build_index(X, nlist, M, nbits=4, metric="l2", spherical=False, perm=None, iters=20, seed=0x5EED,
+                build_graph=False, stream=None):
+    torch = _torch()
+    n, d = X.shape
+    perm_np = None if perm is None else np.ascontiguousarray(perm, dtype=np.int64)
+    opts = BuildOpts(iters, int(spherical), _hptr(perm_np), seed, int(build_graph))
+    h = C.c_void_p()
+    _check(lib().ksc_build_index(_dptr(X, torch.float32, "X"), n, d, nlist, M, nbits,
+                                 KSC_IP if metric == "ip" else KSC_L2, C.byref(opts), _stream(stream),
+                                 C.byref(h)))
+    return Index(h.value)
+
+
+def index_import(arrs, metric="l2", spherical=False, stream=None):
+    """arrs: dict of numpy arrays X, c_rank, c_mean, codebook, codes, assign
+    (and optionally graph, entry)."""
+    keep = {k: np.ascontiguousarray(arrs[k]) for k in ("X", "c_rank", "c_mean", "codebook", "codes", "assign")}
+    keep["X"] = keep["X"].astype(np.float32, copy=False)
+    for k in ("graph", "entry"):
+        if arrs.get(k) is not None:
+            keep[k] = np.ascontiguousarray(arrs[k], dtype=np.int32)
+    n, d = keep["X"].shape
+    L = keep["c_rank"].shape[0]
+    M = keep["codebook"].shape[0]
+    a = IndexArrays(n, d, L, M, KSC_IP if metric == "ip" else KSC_L2, int(spherical),
+                    *[_hptr(keep.get(k)) for k in ("X", "c_rank", "c_mean", "codebook", "codes", "assign",
+                                                   "graph", "entry")])
+    h = C.c_void_p()
+    _check(lib().ksc_index_import(C.byref(a), _stream(stream), C.byref(h)))
+    return Index(h.value)
+
+
+def lut16_peak(stream=None):
+    """Measured lookup rate (Glookup/s) of the scan's instruction sequence."""
+    v = C.c_double(0)
+    _check(lib().ksc_lut16_peak(C.byref(v), _stream(stream)))
+    return v.value
+
+
+def version():
+    return lib().ksc_version().decode()

@@ -3,7 +3,10 @@
 These stand in for the paper's datasets (Table 5), which are not available:
   small  : 10k x 128 isotropic Gaussian mixture (100 centres U[-5,5], sigma 1), L2
   sift   : 1M x 128 non-negative integer vectors 0..255 from a 1000-component
-           mixture with a skewed per-dimension scale (SIFT1M / BIGANN shape), L2
+           mixture with a skewed per-dimension scale s_t (SIFT1M / BIGANN shape),
+           L2; centres U[0, 96 s_t], noise 38 s_t, rounded and clipped (many
+           zeros, as in SIFT); the noise scale puts recall@10 = 0.90 at a
+           moderate nprobe, as on SIFT1M with 1024 lists
   glove  : 1.2M x 100 unit-norm anisotropic mixture, 2000 components with
            power-law weights (GLOVE-100 / TEXT-TO-IMAGE shape), inner product
   deep   : 10M x 96 unit-norm mixture, 10000 components with Zipf(1.1) weights
@@ -15,7 +18,7 @@ CPU oracle receive these arrays as inputs; this module computes nothing else.
 """
 import numpy as np
 
-GENERATOR_VERSION = 1
+GENERATOR_VERSION = 2
 
 CONFIGS = {
     1: dict(name="small", n=10_000, d=128, nq=100, L=64, M=64, k=10, R=100, nprobe=8, metric="l2",
@@ -69,7 +72,7 @@ def _draw(cfg, prm, n, rng, chunk=1 << 20):
         if cfg == 1:
             x = prm["mu"][comp] + eps
         elif cfg == 2:
-            x = np.clip(np.rint(prm["mu"][comp] + 12.0 * prm["s"] * eps), 0, 255)
+            x = np.clip(np.rint(prm["mu"][comp] + 38.0 * prm["s"] * eps), 0, 255)
         elif cfg == 3:
             x = _normalise(prm["mu"][comp] + prm["sig"][comp] * eps)
         else:

@@ -1,0 +1,279 @@
+"""CUDA path vs the CPU oracle, through the C ABI (needs a GB300).
+
+Integer work (quantised LUTs, biases, candidate keys) must be bit-exact;
+float distances within 1e-4 relative of FP64; result ids equal except where
+two exact distances tie to within that tolerance.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2511_03298_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    return torch
+
+
+@pytest.fixture(scope="module")
+def ksc(torch):
+    from paper_2511_03298_gb300 import ksc
+    return ksc
+
+
+def mixture(n, d, L, seed, ip=False, nq=40):
+    rng = np.random.default_rng(seed)
+    centres = rng.uniform(-4, 4, size=(max(L // 2, 2), d))
+    X = (centres[rng.integers(0, len(centres), n)] + rng.normal(size=(n, d))).astype(np.float32)
+    Q = (centres[rng.integers(0, len(centres), nq)] + rng.normal(size=(nq, d))).astype(np.float32)
+    if ip:
+        X /= np.linalg.norm(X, axis=1, keepdims=True)
+        Q /= np.linalg.norm(Q, axis=1, keepdims=True)
+    return X, Q, rng.permutation(n).astype(np.int64)
+
+
+_CACHE = {}
+
+
+def small_index(kind):
+    """Oracle-built indexes (shared with the GPU through import)."""
+    if kind not in _CACHE:
+        if kind == "l2":
+            X, Q, perm = mixture(6000, 64, 24, 11)
+            ix = oracle.build_index(X, 24, 32, False, perm, iters=6)
+        elif kind == "ip":
+            X, Q, perm = mixture(5000, 48, 20, 12, ip=True)
+            ix = oracle.build_index(X, 20, 24, True, perm, iters=6, ip=True)
+        elif kind == "m50":  # d = 100, M = 50: subspaces not a multiple of the lane group
+            X, Q, perm = mixture(4000, 100, 16, 13, ip=True)
+            ix = oracle.build_index(X, 16, 50, True, perm, iters=5, ip=True)
+        elif kind == "small":  # the 10k x 128 configuration
+            X = synth.base(1)
+            Q = synth.queries(1)
+            ix = oracle.build_index(X, 64, 64, False, synth.build_perm(1, len(X)), iters=20)
+        _CACHE[kind] = (ix, Q)
+    return _CACHE[kind]
+
+
+def gpu_index(ksc, ix):
+    return ksc.index_import(ix, metric="ip" if ix["ip"] else "l2", spherical=ix["spherical"])
+
+
+def oracle_probes(ix, Q, P):
+    return np.stack([oracle.rank(q, ix["c_rank"], ix["spherical"], P)[0] for q in Q]).astype(np.int32)
+
+
+def check_results(ix, Q, ids, dists, ref_ids, ref_d, k):
+    """Tie-aware comparison of top-k results against the oracle."""
+    ip = ix["ip"]
+    X = ix["X"].astype(np.float64)
+    for qi in range(len(Q)):
+        np.testing.assert_allclose(dists[qi], ref_d[qi], rtol=RTOL, atol=1e-4)
+        for r in range(k):
+            if ids[qi, r] == ref_ids[qi, r]:
+                continue
+            assert ids[qi, r] >= 0 and ref_ids[qi, r] >= 0, (qi, r)
+            x = X[ids[qi, r]]
+            q = Q[qi].astype(np.float64)
+            exact = -(q @ x) if ip else ((q - x) ** 2).sum()
+            expect = -ref_d[qi, r] if ip else ref_d[qi, r]
+            assert abs(exact - expect) <= RTOL * max(1.0, abs(expect)), (qi, r, exact, expect)
+
+
+@pytest.mark.parametrize("kind", ["l2", "ip", "m50"])
+def test_luts_bit_exact(torch, ksc, kind):
+    ix, Q = small_index(kind)
+    g = gpu_index(ksc, ix)
+    P = 7
+    probes = oracle_probes(ix, Q, P)
+    lut, bias, scale = g.compute_luts(torch.from_numpy(Q).cuda(), torch.from_numpy(probes).cuda())
+    lut, bias, scale = lut.cpu().numpy(), bias.cpu().numpy(), scale.cpu().numpy()
+    for qi in range(len(Q)):
+        Ql, b, a = oracle.lut_q8(Q[qi], ix, probes[qi])
+        assert np.array_equal(lut[qi], Ql), qi
+        assert np.array_equal(bias[qi], b), qi
+        assert np.float32(a) == scale[qi], qi
+
+
+@pytest.mark.parametrize("kind,lanes", [("l2", 8), ("l2", 16), ("l2", 32), ("ip", 8), ("ip", 32),
+                                        ("m50", 8), ("m50", 16), ("m50", 32), ("small", 0)])
+def test_scan_candidates_bit_exact(torch, ksc, kind, lanes):
+    ix, Q = small_index(kind)
+    g = gpu_index(ksc, ix)
+    P, R, k = (8, 100, 10) if kind == "small" else (5, 150, 10)
+    probes = oracle_probes(ix, Q, P)
+    opts = ksc.search_opts(lanes_per_query=lanes)
+    ids, dists, cand, ncand = g.search_with_probes(torch.from_numpy(Q).cuda(), torch.from_numpy(probes).cuda(),
+                                                   k, R, opts=opts)
+    cand = cand.cpu().numpy().view(np.uint64)
+    ncand = ncand.cpu().numpy()
+    ids, dists = ids.cpu().numpy(), dists.cpu().numpy()
+    ref_ids = np.zeros_like(ids)
+    ref_d = np.zeros(ids.shape, np.float64)
+    for qi in range(len(Q)):
+        Ql, b, _ = oracle.lut_q8(Q[qi], ix, probes[qi])
+        ref = oracle.scan_topr(ix, probes[qi], Ql, b, R)
+        assert ncand[qi] == len(ref)
+        assert np.array_equal(cand[qi, :len(ref)], ref), qi
+        ref_ids[qi], ref_d[qi] = oracle.rerank(Q[qi], ix, oracle.key_id(ref).astype(np.int32), k)
+    check_results(ix, Q, ids, dists, ref_ids, ref_d, k)
+    assert g.last_status() == 0
+
+
+@pytest.mark.parametrize("kind", ["l2", "ip", "small"])
+def test_rank_lists_within_fp32_tolerance(torch, ksc, kind):
+    ix, Q = small_index(kind)
+    g = gpu_index(ksc, ix)
+    P = 9
+    probes, scores = g.rank_lists(torch.from_numpy(Q).cuda(), P)
+    probes, scores = probes.cpu().numpy(), scores.cpu().numpy()
+    C = ix["c_rank"].astype(np.float64)
+    for qi, q in enumerate(Q.astype(np.float64)):
+        ref, ref_s = oracle.rank(Q[qi], ix["c_rank"], ix["spherical"], P)
+        exact = -(C @ q) if ix["spherical"] else ((C - q) ** 2).sum(1)
+        tol = 1e-5 * (np.abs(q) @ np.abs(C).max(0) + (q ** 2).sum() + (C ** 2).sum(1).max())
+        assert len(set(probes[qi])) == P
+        # every returned list is within rounding of the oracle's P-th score
+        assert np.all(exact[probes[qi]] <= ref_s[-1] + tol)
+        np.testing.assert_allclose(scores[qi], exact[probes[qi]], rtol=1e-4, atol=tol)
+        assert (probes[qi] == ref).mean() >= 0.75
+
+
+@pytest.mark.parametrize("kind", ["l2", "ip", "small"])
+def test_search_end_to_end_matches_oracle(torch, ksc, kind):
+    ix, Q = small_index(kind)
+    g = gpu_index(ksc, ix)
+    P, R, k = (8, 100, 10) if kind == "small" else (6, 120, 10)
+    ids, dists = g.search(torch.from_numpy(Q).cuda(), k, P, R)
+    ids, dists = ids.cpu().numpy(), dists.cpu().numpy()
+    out = oracle.search(ix, Q, P, R, k)
+    _, true_d = oracle.exact_knn(Q, ix["X"], k, ip=ix["ip"])
+    r_gpu = oracle.recall(Q, ix["X"], ids, true_d, k, ip=ix["ip"])
+    r_orc = oracle.recall(Q, ix["X"], out["ids"], true_d, k, ip=ix["ip"])
+    assert abs(r_gpu - r_orc) <= 0.002
+    if kind == "small":
+        assert r_gpu >= 0.9
+    check_results(ix, Q, ids, dists, out["ids"], out["dists"], k)
+
+
+def test_full_probe_full_rerank_equals_brute_force(torch, ksc):
+    ix, Q = small_index("l2")
+    g = gpu_index(ksc, ix)
+    k = 10
+    ids, dists = g.search(torch.from_numpy(Q[:8]).cuda(), k, ix["L"], 4096)
+    ref_ids, ref_d = oracle.exact_knn(Q[:8], ix["X"], k)
+    check_results(ix, Q[:8], ids.cpu().numpy(), dists.cpu().numpy(), ref_ids, ref_d, k)
+
+
+def test_candidate_store_overflow_is_redone_exactly(torch, ksc):
+    ix, Q = small_index("l2")
+    g = gpu_index(ksc, ix)
+    P, R, k = 6, 100, 10
+    probes = oracle_probes(ix, Q, P)
+    opts = ksc.search_opts(cand_cap=R)  # far too small: every query overflows
+    _, _, cand, _ = g.search_with_probes(torch.from_numpy(Q).cuda(), torch.from_numpy(probes).cuda(), k, R,
+                                         opts=opts)
+    assert g.last_status() & ksc.STATUS_CAND_OVERFLOW
+    cand = cand.cpu().numpy().view(np.uint64)
+    for qi in range(0, len(Q), 5):
+        Ql, b, _ = oracle.lut_q8(Q[qi], ix, probes[qi])
+        assert np.array_equal(cand[qi], oracle.scan_topr(ix, probes[qi], Ql, b, R))
+
+
+def test_short_results_padding_and_empty_batch(torch, ksc):
+    X, Q, perm = mixture(300, 16, 4, 21, nq=5)
+    ix = oracle.build_index(X, 4, 8, False, perm, iters=3)
+    g = gpu_index(ksc, ix)
+    # one probe of ~75 vectors, R = 500, k = 200: fewer than k candidates
+    ids, dists = g.search(torch.from_numpy(Q).cuda(), 200, 1, 500)
+    ids, dists = ids.cpu().numpy(), dists.cpu().numpy()
+    out = oracle.search(ix, Q, 1, 500, 200)
+    assert np.array_equal(ids == -1, out["ids"] == -1)
+    assert np.all(np.isinf(dists[ids == -1]))
+    e_ids, e_d = g.search(torch.zeros((0, 16), device="cuda"), 10, 2, 50)
+    assert e_ids.shape == (0, 10)
+
+
+def test_varprobe_matches_oracle(torch, ksc):
+    ix, Q = small_index("l2")
+    g = gpu_index(ksc, ix)
+    rng = np.random.default_rng(31)
+    npb = rng.integers(1, 12, size=len(Q)).astype(np.int32)
+    rr = rng.integers(10, 200, size=len(Q)).astype(np.int32)
+    k = 10
+    ids, dists = g.search_varprobe(torch.from_numpy(Q).cuda(), k, torch.from_numpy(npb).cuda(),
+                                   torch.from_numpy(rr).cuda())
+    out = oracle.search(ix, Q, npb, rr, k)
+    check_results(ix, Q, ids.cpu().numpy(), dists.cpu().numpy(), out["ids"], out["dists"], k)
+
+
+@pytest.mark.parametrize("metric", ["l2", "ip"])
+def test_gpu_build_index_against_oracle(torch, ksc, metric):
+    """GPU build (FP32): assignments are the lowest ranking score and codes
+    the nearest codewords, except where two candidates tie within FP32
+    rounding; mean centroids are the member means."""
+    ip = metric == "ip"
+    X, Q, perm = mixture(8000, 32, 16, 41, ip=ip)
+    g = ksc.build_index(torch.from_numpy(X).cuda(), 16, 16, metric=metric, spherical=ip, perm=perm, iters=8)
+    e = g.export()
+    C = e["c_rank"].astype(np.float64)
+    Xd = X.astype(np.float64)
+    s = -(Xd @ C.T) if ip else ((Xd[:, None, :] - C[None]) ** 2).sum(-1)
+    best = s[np.arange(len(X)), e["assign"]]
+    assert np.all(best <= s.min(1) + 1e-5 * (1 + np.abs(s).max(1)))
+    for c in range(16):
+        mem = X[e["assign"] == c]
+        if len(mem):
+            np.testing.assert_allclose(e["c_mean"][c], mem.astype(np.float64).mean(0), rtol=1e-4, atol=1e-5)
+    Rres = X - e["c_mean"][e["assign"]]
+    codes, gap = oracle.encode(Rres, 16, e["codebook"])
+    bad = codes != e["codes"]
+    assert np.all(gap[bad] <= 1e-5 * (1 + (Rres.reshape(len(X), 16, -1) ** 2).sum(-1)[bad]))
+    assert bad.mean() < 1e-3
+    # the exported index searches like the oracle on the same index
+    ix = oracle.make_index(X, e["c_rank"], e["c_mean"], e["codebook"], e["codes"], e["assign"], ip=ip,
+                           spherical=ip)
+    ids, dists = g.search(torch.from_numpy(Q).cuda(), 10, 4, 100)
+    out = oracle.search(ix, Q, 4, 100, 10)
+    _, true_d = oracle.exact_knn(Q, X, 10, ip=ip)
+    assert abs(oracle.recall(Q, X, ids.cpu().numpy(), true_d, 10, ip=ip)
+               - oracle.recall(Q, X, out["ids"], true_d, 10, ip=ip)) <= 0.002
+
+
+def test_full_size_sift_sampled_parity(torch, ksc):
+    """1M x 128 workload in the benchmark's launch configuration (10k queries,
+    nprobe 32, R 200): candidates of sampled queries bit-exact against the
+    oracle on the same (GPU-built, exported) index and probes."""
+    X = synth.base(2)
+    Q = synth.queries(2)
+    g = ksc.build_index(torch.from_numpy(X).cuda(), 1024, 64, perm=synth.build_perm(2, len(X)))
+    e = g.export()
+    ix = oracle.make_index(X, e["c_rank"], e["c_mean"], e["codebook"], e["codes"], e["assign"])
+    P, R, k = 32, 200, 10
+    Qd = torch.from_numpy(Q).cuda()
+    gp, _ = g.rank_lists(Qd, P, want_scores=False)
+    gp = gp.cpu().numpy()
+    ids, dists, cand, ncand = g.search_with_probes(Qd, torch.from_numpy(gp).cuda(), k, R)
+    cand = cand.cpu().numpy().view(np.uint64)
+    ids, dists = ids.cpu().numpy(), dists.cpu().numpy()
+    sample = np.random.default_rng(7).choice(len(Q), 40, replace=False)
+    ref_ids = np.zeros((len(sample), k), np.int64)
+    ref_d = np.zeros((len(sample), k))
+    for i, qi in enumerate(sample):
+        Ql, b, _ = oracle.lut_q8(Q[qi], ix, gp[qi])
+        ref = oracle.scan_topr(ix, gp[qi], Ql, b, R)
+        assert np.array_equal(cand[qi], ref), qi
+        ref_ids[i], ref_d[i] = oracle.rerank(Q[qi], ix, oracle.key_id(ref).astype(np.int32), k)
+    check_results(ix, Q[sample], ids[sample], dists[sample], ref_ids, ref_d, k)
+    # the GPU ranking agrees with the FP64 ranking up to FP32 near-ties
+    for qi in sample[:10]:
+        ref, ref_s = oracle.rank(Q[qi], ix["c_rank"], False, P)
+        assert len(np.intersect1d(ref, gp[qi])) >= P - 2
