@@ -156,6 +156,23 @@ int ksc_rank_lists(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t P, int
 int ksc_compute_luts(ksc_index* ix, const float* Q_dev, int64_t nq, const int32_t* probes_dev,
                      int32_t P, uint8_t* lut_dev, int32_t* bias_dev, float* scale_dev, void* stream);
 
+/* Allocation-free variant of ksc_compute_luts (the paper has no counterpart:
+ * this entry point exists for callers that cannot let the library call
+ * cudaMalloc -- a program whose device memory is reserved by its own
+ * allocator, or a latency-critical path that cannot take the device
+ * synchronisation an allocation may cause).  Same arguments, layouts and
+ * results as ksc_compute_luts; it calls no cudaMalloc / cudaFree.  Its only
+ * scratch (4 bytes per query) lives in a fixed device array of
+ * KSC_NOALLOC_MAX_NQ entries that every GPU loading the library holds until
+ * the process exits; nq > KSC_NOALLOC_MAX_NQ is rejected with KSC_EINVAL.
+ * The first call on a device, with that device current, looks up the
+ * array's device address; make that first call before any stream capture.
+ * Every call shares the array: calls whose work overlaps on the GPU (other
+ * streams, other threads) race on it and must be serialised by the caller. */
+#define KSC_NOALLOC_MAX_NQ 65536
+int ksc_compute_luts_noalloc(ksc_index* ix, const float* Q_dev, int64_t nq, const int32_t* probes_dev,
+                             int32_t P, uint8_t* lut_dev, int32_t* bias_dev, float* scale_dev, void* stream);
+
 /* Device status word of the last search on this index: 0 = clean, else a
  * bitwise OR of KSC_STATUS_* (blocking read). */
 #define KSC_STATUS_CAND_OVERFLOW 1  /* a query's candidate store overflowed and was redone exactly */

@@ -1054,3 +1054,54 @@ int ksc_last_status(ksc_index* ix, int32_t* status_host) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ allocation-free LUT entry
+// Some callers cannot let this library call cudaMalloc: a host program whose
+// device memory is wholly reserved by its own allocator (a framework's caching
+// pool, a serving runtime that pre-reserves the device) has no headroom for a
+// foreign allocation, and a latency-critical caller cannot afford the device
+// synchronisation that cudaMalloc / cudaFree may imply.  For them,
+// ksc_compute_luts_noalloc keeps its only scratch -- the per-query table range
+// that ksc_compute_luts otherwise keeps in a workspace buffer -- in the
+// fixed-size array below.  Every GPU that loads the library holds the array
+// (KSC_NOALLOC_MAX_NQ * 4 bytes = 256 KiB) until the process exits.
+static __device__ __align__(256) uint32_t g_noalloc_range[KSC_NOALLOC_MAX_NQ];
+
+namespace ksc {
+// Device address of g_noalloc_range per device ordinal, looked up on the first
+// call made with that device current (host code cannot use the symbol itself:
+// in host code it names a host-side stand-in, not device memory).
+static void* g_noalloc_addr[64] = {};
+}  // namespace ksc
+
+extern "C" int ksc_compute_luts_noalloc(ksc_index* ix, const float* Q_dev, int64_t nq, const int32_t* probes_dev,
+                                        int32_t P, uint8_t* lut_dev, int32_t* bias_dev, float* scale_dev,
+                                        void* stream) {
+    KSC_CHECK_ARG(ix, "null index");
+    KSC_CHECK_ARG(P >= 1 && P <= ix->L, "P must be in [1, nlist]");
+    KSC_CHECK_ARG(nq >= 0 && nq <= KSC_NOALLOC_MAX_NQ,
+                  "nq = %lld exceeds the fixed scratch of ksc_compute_luts_noalloc (at most %d queries per call)",
+                  (long long)nq, KSC_NOALLOC_MAX_NQ);
+    if (nq == 0) return KSC_OK;
+    KSC_CHECK_ARG(Q_dev && probes_dev && lut_dev && bias_dev && scale_dev, "null argument");
+    int dev = 0;
+    KSC_CUDA(cudaGetDevice(&dev));
+    KSC_CHECK_ARG(dev >= 0 && dev < 64, "device ordinal %d out of range", dev);
+    if (!g_noalloc_addr[dev]) {
+        void* addr = nullptr;
+        KSC_CUDA(cudaGetSymbolAddress(&addr, g_noalloc_range));
+        g_noalloc_addr[dev] = addr;
+    }
+    uint32_t* rb = static_cast<uint32_t*>(g_noalloc_addr[dev]);
+    cudaStream_t st = as_stream(stream);
+    // the array keeps the previous call's ranges: clear this call's slots
+    KSC_CUDA(cudaMemsetAsync(rb, 0, sizeof(uint32_t) * nq, st));
+    LutArgs A{Q_dev, nq, ix->d, ix->M, ix->dsub, ix->metric == KSC_IP, P, probes_dev, nullptr, P, ix->c_mean,
+              ix->codebook, ix->L};
+    const int64_t threads = nq * P * 32;
+    k_lut_range<<<blocks_for(threads, 128), 128, 0, st>>>(A, rb);
+    KSC_LAUNCH_CHECK();
+    k_lut_quant<<<blocks_for(threads, 128), 128, 0, st>>>(A, rb, lut_dev, bias_dev, scale_dev);
+    KSC_LAUNCH_CHECK();
+    return KSC_OK;
+}

@@ -55,6 +55,7 @@ _SIGS = {
     "ksc_search_with_probes": [_vp, _vp, _i64, _vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp],
     "ksc_rank_lists": [_vp, _vp, _i64, _i32, _vp, _vp, _vp],
     "ksc_compute_luts": [_vp, _vp, _i64, _vp, _i32, _vp, _vp, _vp, _vp],
+    "ksc_compute_luts_noalloc": [_vp, _vp, _i64, _vp, _i32, _vp, _vp, _vp, _vp],
     "ksc_last_status": [_vp, _vp],
     "ksc_profile_enable": [_vp, _i32],
     "ksc_profile_read": [_vp, _vp, _i32, _vp],
