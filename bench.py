@@ -159,18 +159,22 @@ def run_ours(args, rank, ws):
     torch.cuda.synchronize()
     build_s = time.time() - t0
     k, R = CFG["k"], CFG["rerank"]
-    true_i, true_d = exact_topk(torch, Xd, Qd, k)
-    # operating point: smallest nprobe of the grid with recall >= 0.90
     sweep = {}
-    nprobe = GRID[-1]
-    for P in GRID:
-        ids, _ = ix.search(Qd, k, P, R)
-        rec = recall_at_10(torch, Xd, Qd, ids, true_d, k)
-        sweep[P] = round(rec, 4)
-        if rec >= TARGET_RECALL:
-            nprobe = P
-            break
-    recall = sweep[nprobe]
+    if args.quick:
+        # profiling mode: fixed nprobe, no ground truth, sweep, e2e or CPU leg
+        nprobe, recall, true_d = args.nprobe or 8, None, None
+    else:
+        true_i, true_d = exact_topk(torch, Xd, Qd, k)
+        # operating point: smallest nprobe of the grid with recall >= 0.90
+        nprobe = GRID[-1]
+        for P in GRID:
+            ids, _ = ix.search(Qd, k, P, R)
+            rec = recall_at_10(torch, Xd, Qd, ids, true_d, k)
+            sweep[P] = round(rec, 4)
+            if rec >= TARGET_RECALL:
+                nprobe = P
+                break
+        recall = sweep[nprobe]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     st = torch.cuda.current_stream()
     ids = torch.empty((CFG["nq"], k), dtype=torch.int64, device=dev)
@@ -202,6 +206,14 @@ def run_ours(args, rank, ws):
     ms = statistics.mean(step_ms)
     ms_max = max_over_ranks(ms, ws)
     value = CFG["nq"] * ws / (ms_max * 1e-3)
+    stats = ix.search_stats()
+    if args.quick:
+        if rank == 0:
+            print(json.dumps({"quick": True, "nprobe": nprobe, "ms_per_step": round(ms_max, 4),
+                              "value": round(value, 1), "stage_ms": {s_: round(statistics.mean(v), 4)
+                                                                      for s_, v in stage_ms.items()},
+                              "search_stats": stats}))
+        return None
     # end to end through the public API with host buffers
     Qpin = torch.from_numpy(Qh).pin_memory()
     ids_h = torch.empty((CFG["nq"], k), dtype=torch.int64).pin_memory()
@@ -253,6 +265,7 @@ def run_ours(args, rank, ws):
             "e2e": {"value": round(e2e, 1), "unit": "queries/s",
                     "h2d_bytes_per_step": int(Qh.nbytes), "d2h_bytes_per_step": int(ids_h.numel() * 12)},
             "gpu_launches": launches,
+            "search_stats": stats,
             "stage_ms": {s_: round(statistics.mean(v), 4) for s_, v in stage_ms.items()},
             "roofline": {"bound": "alu", "kernel": "k_scan (LUT16 ADC scan)", "achieved": round(achieved_gl, 1),
                          "peak": round(peak_gl, 1), "unit": "Glookup/s", "frac": round(achieved_gl / peak_gl, 4),
@@ -343,6 +356,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--quick", action="store_true", help="profiling mode: timed steps only, at --nprobe")
+    ap.add_argument("--nprobe", type=int, default=0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, ws = dist_setup()

@@ -117,7 +117,8 @@ typedef struct {
     int32_t n_near;            /* hybrid: probes of rank < n_near are scanned fully (2) */
     int32_t efs;               /* hybrid: graph-search result capacity (64) */
     int32_t tau;               /* hybrid: full scan when >= tau results beat theta (8) */
-    int32_t cand_cap;          /* candidate store per query; 0 -> max(8R, 2048) */
+    int32_t cand_cap;          /* candidate store per query; 0 -> max(16R, 4096) */
+    int32_t rank_fp32;         /* 1: list scores on FP32 CUDA cores instead of BF16 tensor cores */
 } ksc_search_opts;
 
 /* k nearest neighbours of Q_dev [nq x d] with a fixed nprobe (1..nlist) and
@@ -150,6 +151,15 @@ int ksc_search_with_probes(ksc_index* ix, const float* Q_dev, int64_t nq, const 
  * ranking centroid, or -<q, c> for spherical indexes); scores may be NULL. */
 int ksc_rank_lists(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t P, int32_t* probes_dev,
                    float* scores_dev, void* stream);
+
+/* Raw list scores of step a1: scores_dev [nq x L] fp32 = ||c||^2 - 2<q, c>
+ * (L2; ||q||^2 omitted) or -<q, c> (spherical), c the ranking centroids.
+ * tensor_cores = 1: BF16 operands on the tensor cores (tcgen05, d <= 256);
+ * tensor_cores = 0 (or d > 256): FP32 CUDA cores.  err_dev [nq] (may be
+ * NULL) receives a bound on |score - exact score| for every list of the
+ * query; ranking re-scores exactly every list within twice that bound. */
+int ksc_list_scores(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t tensor_cores, float* scores_dev,
+                    float* err_dev, void* stream);
 
 /* Step a2 alone: quantised LUTs lut_dev [nq x P x M x 16] uint8, biases
  * bias_dev [nq x P] int32 and scales scale_dev [nq] fp32 for the given probes. */
@@ -193,6 +203,12 @@ int ksc_profile_read(ksc_index* ix, float* ms_host, int32_t n, int32_t* launches
  * registers (no memory traffic) on every SM and returns the rate reached in
  * 10^9 lookups per second (the integer-ALU ceiling of the a3 scan).  Blocking. */
 int ksc_lut16_peak(double* glookups_host, void* stream);
+
+/* Counters of the last search on this index (blocking read), stats_host[4]:
+ * [0] queries whose candidate store overflowed (redone exactly),
+ * [1] candidates kept by the scan's threshold filter (all queries),
+ * [2] most candidates kept for one query, [3] reserved (0). */
+int ksc_search_stats(ksc_index* ix, int64_t* stats_host);
 
 /* Message of the last failure on this thread ("" if none). */
 const char* ksc_last_error(void);

@@ -155,6 +155,120 @@ __device__ void block_select_smallest(Load load, int N, int K, uint64_t* out, ui
     __syncthreads();
 }
 
+// Exclusive prefix sum over the block (blockDim.x a multiple of 32, <= 1024);
+// warp_tot: 32 shared uint32.  Returns this thread's exclusive prefix.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_tot) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t t = lane < nw ? warp_tot[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < nw) warp_tot[lane] = t;  // inclusive warp totals
+    }
+    __syncthreads();
+    uint32_t r = x - v + (w > 0 ? warp_tot[w - 1] : 0);
+    __syncthreads();
+    return r;
+}
+
+// Histogram selection for keys whose high 32 bits are an order-preserving
+// integer distance.  hist_find locates, among N unique keys, the bin B (of
+// HIST_BINS bins of width 1 above the minimum distance; the last bin takes
+// everything beyond) that holds the K-th smallest key, with lt = the number
+// of keys in lower bins and inB = the keys in bin B.
+constexpr int HIST_BINS = 2048;
+struct HistSel {
+    uint32_t base;
+    int B, lt, inB;
+};
+
+__device__ __forceinline__ int hist_bin(uint64_t key, uint32_t base) {
+    uint32_t d = (uint32_t)(key >> 32) - base;
+    return d < (uint32_t)(HIST_BINS - 1) ? (int)d : HIST_BINS - 1;
+}
+
+template <class Load>
+__device__ void hist_find(Load load, int N, int K, uint32_t* hist, uint32_t* warp_tot, HistSel* hs) {
+    __shared__ uint32_t s_min;
+    if (threadIdx.x == 0) s_min = 0xffffffffu;
+    for (int b = threadIdx.x; b < HIST_BINS; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    uint32_t mn = 0xffffffffu;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) mn = min(mn, (uint32_t)(load(i) >> 32));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    if ((threadIdx.x & 31) == 0) atomicMin(&s_min, mn);
+    __syncthreads();
+    const uint32_t base = s_min;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) atomicAdd(&hist[hist_bin(load(i), base)], 1u);
+    __syncthreads();
+    const int per = HIST_BINS / blockDim.x;  // blockDim.x divides HIST_BINS
+    const int b0 = threadIdx.x * per;
+    uint32_t local = 0;
+    for (int b = b0; b < b0 + per; ++b) local += hist[b];
+    const uint32_t excl = block_exclusive_scan(local, warp_tot);
+    if (excl < (uint32_t)K && excl + local >= (uint32_t)K) {
+        uint32_t c = excl;
+        for (int b = b0; b < b0 + per; ++b) {
+            if (c + hist[b] >= (uint32_t)K) {
+                hs->base = base;
+                hs->B = b;
+                hs->lt = (int)c;
+                hs->inB = (int)hist[b];
+                break;
+            }
+            c += hist[b];
+        }
+    }
+    __syncthreads();
+}
+
+// K smallest of N unique distance keys, sorted, into out[0..K) (K <= N).
+// Keys of the bins up to B (K plus the ties of bin B) are gathered into buf
+// (cap keys, a power of two) and sorted; if they do not fit, the radix
+// select above runs instead.
+template <class Load>
+__device__ void block_select_hist(Load load, int N, int K, uint64_t* out, uint64_t* buf, int cap,
+                                  uint32_t* hist, uint32_t* warp_tot) {
+    __shared__ HistSel hs;
+    __shared__ int s_cnt;
+    if (K <= 0) return;
+    if (N <= 512 && N <= cap) {
+        block_select_smallest(load, N, K, out, buf, cap, hist);
+        return;
+    }
+    hist_find(load, N, K, hist, warp_tot, &hs);
+    const int need = hs.lt + hs.inB;
+    if (need > cap) {
+        block_select_smallest(load, N, K, out, buf, cap, hist);
+        return;
+    }
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        uint64_t k = load(i);
+        if (hist_bin(k, hs.base) <= hs.B) buf[atomicAdd(&s_cnt, 1)] = k;
+    }
+    __syncthreads();
+    const int S = pow2_ceil(need);
+    for (int i = need + threadIdx.x; i < S; i += blockDim.x) buf[i] = KEY_NONE;
+    __syncthreads();
+    block_bitonic_sort(buf, S);
+    for (int i = threadIdx.x; i < K; i += blockDim.x) out[i] = buf[i];
+    __syncthreads();
+}
+
 // ------------------------------------------------------------------ workspace
 // Grow-only device buffers owned by an index (one per role).  Growing
 // synchronises the stream before freeing the old buffer.

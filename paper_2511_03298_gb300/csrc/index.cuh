@@ -33,9 +33,14 @@ struct ksc_index {
     int32_t* graph = nullptr;      // [n x 32] optional
     int32_t* entry = nullptr;      // [L] optional
     int32_t* status = nullptr;     // device status word
+    unsigned long long* stats = nullptr;  // [4] counters of the last search
     // host mirrors
     std::vector<int64_t> h_boff;   // [L + 1]
     std::vector<int32_t> h_n;      // [L]
+    // tensor-core ranking: BF16 copy of c_rank [L x Kp], its TMA map, max ||c||
+    void* c_rank_bf16 = nullptr;
+    alignas(64) unsigned char map_c[128] = {};
+    float c_rank_max_norm = 0.f;
     // stage timing (ksc_profile_enable)
     bool prof = false;
     cudaEvent_t ev[KSC_NUM_STAGES + 1] = {};
@@ -43,7 +48,7 @@ struct ksc_index {
     int32_t launches = 0;
     // search workspace
     ksc::Buffer ws_scores, ws_probes, ws_lut, ws_bias, ws_scale, ws_range, ws_thr, ws_cnt,
-        ws_cand, ws_topr, ws_nprobe, ws_rerank, ws_items, ws_misc;
+        ws_cand, ws_topr, ws_nprobe, ws_rerank, ws_items, ws_misc, ws_qbf16, ws_err;
 };
 
 namespace ksc {
@@ -51,6 +56,12 @@ namespace ksc {
 // and the list of each vector (host copy), members in ascending id order.
 int pack_lists(ksc_index* ix, const uint8_t* codes_dev, const int32_t* assign_host, cudaStream_t st);
 int free_index_memory(ksc_index* ix);
+// Tensor-core list scores (rank_tc.cu): approximate scores [nq x L] and a
+// per-query bound err [nq] on their error.
+bool tc_rank_supported(const ksc_index* ix);
+int rank_scores_tc(ksc_index* ix, const float* Q, int64_t nq, float* scores, float* err, cudaStream_t st);
+// Per-query error bound of the list scores (tensor-core or FP32 path).
+int score_err(ksc_index* ix, const float* Q, int64_t nq, bool tensor_cores, float* err, cudaStream_t st);
 // Per-list 32-NN graphs and entry points for the hybrid search (Sec. 4.4).
 int build_graph(ksc_index* ix, cudaStream_t st);
 }  // namespace ksc

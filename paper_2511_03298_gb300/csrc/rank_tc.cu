@@ -1,0 +1,288 @@
+// Centroid ranking scores (Alg. 2 TopNClusters) on the 5th-generation tensor
+// cores: S = Q_bf16 . C_bf16^T accumulated in FP32 in tensor memory.
+//
+// One CTA computes a 128 x 256 tile (128 queries x 256 lists): TMA loads the
+// K-major BF16 operands into shared memory as 128-byte-swizzled boxes of 64
+// elements, one elected thread issues tcgen05.mma (M 128, N 256, K 16 per
+// instruction) into a 256-column TMEM accumulator, tcgen05.commit signals an
+// mbarrier, and the four warps read their 32 TMEM lanes back with
+// tcgen05.ld and write score = ||c||^2 - 2 <q, c> (L2) or -<q, c>.  These
+// scores are approximate (BF16 operands); the ranking kernel re-scores in
+// FP32 every list that the BF16 error bound cannot exclude.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <vector>
+
+#include "index.cuh"
+
+namespace ksc {
+
+constexpr int TC_M = 128, TC_N = 256, TC_KB = 64;  // tile rows, tile columns, K per TMA box
+constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;          // bounded mbarrier polls
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// Poll an mbarrier phase at most `limit` times; false if it never completed.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t limit) {
+    for (uint32_t i = 0; i < limit; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+        "l"(map), "r"(bar), "r"(x), "r"(y)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) |
+           (2ull << 61);
+}
+
+// Instruction descriptor of kind::f16: BF16 A and B (K-major), FP32 D, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+            d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// scores[q][c] for one 128 x 256 tile.  KB = number of 64-wide K boxes (Kp / 64).
+__global__ void __launch_bounds__(128, 1) k_rank_gemm_tc(const __grid_constant__ CUtensorMap mapA,
+                                                         const __grid_constant__ CUtensorMap mapB, int KB, int64_t nq,
+                                                         int L, const float* __restrict__ cn, int spherical,
+                                                         float* __restrict__ scores, int32_t* __restrict__ status) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ uint32_t tmem_base;
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const uint32_t sA = smem_u32(smem), sB = sA + KB * (TC_M * 128);
+    const uint32_t bar_tma = smem_u32(&bars[0]), bar_mma = smem_u32(&bars[1]);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * TC_M, n0 = blockIdx.x * TC_N;
+    if (threadIdx.x == 0) {
+        mbar_init(bar_tma, 1);
+        mbar_init(bar_mma, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(TC_N));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    bool ok = true;
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(bar_tma, (uint32_t)KB * (TC_M + TC_N) * 128);
+        for (int kb = 0; kb < KB; ++kb) {
+            tma_load_2d(sA + kb * (TC_M * 128), &mapA, bar_tma, kb * TC_KB, m0);
+            tma_load_2d(sB + kb * (TC_N * 128), &mapB, bar_tma, kb * TC_KB, n0);
+        }
+        ok = mbar_wait(bar_tma, 0, TC_WAIT_LIMIT);
+        if (ok) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t idesc = idesc_bf16(TC_M, TC_N);
+            for (int kb = 0; kb < KB; ++kb)
+#pragma unroll
+                for (int k = 0; k < TC_KB / 16; ++k) {
+                    const uint64_t a = smem_desc(sA + kb * (TC_M * 128) + k * 32);
+                    const uint64_t b = smem_desc(sB + kb * (TC_N * 128) + k * 32);
+                    tc_mma(tmem, a, b, idesc, (kb | k) != 0);
+                }
+            tc_commit(bar_mma);
+        } else {
+            atomicOr(status, 2);  // the operand copy never completed: wait (bounded) once more
+            mbar_wait(bar_tma, 0, TC_WAIT_LIMIT);
+        }
+    }
+    __syncthreads();
+    const bool done = __syncthreads_and(threadIdx.x == 0 ? ok : 1);
+    // warp-uniform decision (tcgen05.ld is a warp-collective instruction)
+    const bool mma_ok = done && __all_sync(0xffffffffu, mbar_wait(bar_mma, 0, TC_WAIT_LIMIT));
+    if (mma_ok) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int64_t q = (int64_t)m0 + warp * 32 + lane;
+        for (int c0 = 0; c0 < TC_N; c0 += 32) {
+            uint32_t r[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c0, r);
+            if (q < nq) {
+                float* row = scores + q * L;
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const int c = n0 + c0 + i;
+                    if (c < L) {
+                        const float dot = __uint_as_float(r[i]);
+                        row[c] = spherical ? -dot : fmaf(-2.f, dot, cn[c]);
+                    }
+                }
+            }
+        }
+    } else if (done && lane == 0) {
+        atomicOr(status, 2);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_N));
+}
+
+// rows of X (fp32 [n x d]) to BF16 [n x Kp], zero-padded K.
+__global__ void k_to_bf16(const float* __restrict__ X, int64_t n, int d, int Kp, __nv_bfloat16* __restrict__ out) {
+    int64_t tot = n * Kp;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = e / Kp;
+        int t = (int)(e - r * Kp);
+        out[e] = __float2bfloat16_rn(t < d ? X[r * d + t] : 0.f);
+    }
+}
+
+// Per-query bound on |given score - exact score| for every list:
+// rel * ||q|| * max||c|| (times 2 for L2, whose score carries -2 <q, c>) plus
+// (d + 8) 2^-23 (||q|| + max||c||)^2 for the FP32 rounding of ||c||^2 and of
+// the exact FP32 re-score.
+//  BF16 tensor cores: |<q~, c~> - <q, c>| <= (2u + u^2) sum |q_t c_t| + FP32
+//    accumulation, u = 2^-8, and sum |q_t c_t| <= ||q|| ||c|| (Cauchy-Schwarz).
+//  FP32 CUDA cores: a dot product of d terms errs by at most about d 2^-24
+//    of sum |q_t c_t|.
+__global__ void k_score_err(const float* __restrict__ Q, int64_t nq, int d, float cmax, int spherical, float rel,
+                            float* __restrict__ err) {
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    float s = 0.f;
+    for (int t = 0; t < d; ++t) s = fmaf(Q[q * d + t], Q[q * d + t], s);
+    const float qn = sqrtf(s);
+    const float e = rel * qn * cmax * 1.0001f;
+    // plus the FP32 rounding of ||c||^2 and of the exact re-score itself
+    const float r = (float)(d + 8) * 1.2e-7f * (qn + cmax) * (qn + cmax);
+    err[q] = (spherical ? e : 2.f * e) + r;
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+static int make_map(CUtensorMap* map, const void* base, int64_t rows, int Kp, int box_rows) {
+    auto fn = encode_fn();
+    if (!fn) {
+        set_error("cuTensorMapEncodeTiled is not available");
+        return KSC_ECUDA;
+    }
+    cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
+    cuuint32_t box[2] = {(cuuint32_t)TC_KB, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+        return KSC_ECUDA;
+    }
+    return KSC_OK;
+}
+
+bool tc_rank_supported(const ksc_index* ix) { return ix->d <= 256; }
+
+// Approximate scores [nq x L] with the tensor cores plus the per-query error
+// bound err [nq]; the caller re-scores exactly what the bound cannot exclude.
+int rank_scores_tc(ksc_index* ix, const float* Q, int64_t nq, float* scores, float* err, cudaStream_t st) {
+    const int Kp = (ix->d + TC_KB - 1) / TC_KB * TC_KB;
+    const int KB = Kp / TC_KB;
+    if (!ix->c_rank_bf16) {
+        KSC_CUDA(cudaMalloc(&ix->c_rank_bf16, sizeof(__nv_bfloat16) * (size_t)ix->L * Kp));
+        k_to_bf16<<<(unsigned)std::min<int64_t>(((int64_t)ix->L * Kp + 255) / 256, 4096), 256, 0, st>>>(
+            ix->c_rank, ix->L, ix->d, Kp, (__nv_bfloat16*)ix->c_rank_bf16);
+        KSC_LAUNCH_CHECK();
+        KSC_TRY(make_map(reinterpret_cast<CUtensorMap*>(ix->map_c), ix->c_rank_bf16, ix->L, Kp, TC_N));
+    }
+    KSC_TRY(ensure(ix->ws_qbf16, sizeof(__nv_bfloat16) * (size_t)nq * Kp, st));
+    __nv_bfloat16* qb = (__nv_bfloat16*)ix->ws_qbf16.p;
+    k_to_bf16<<<(unsigned)std::min<int64_t>((nq * Kp + 255) / 256, 4096), 256, 0, st>>>(Q, nq, ix->d, Kp, qb);
+    KSC_LAUNCH_CHECK();
+    CUtensorMap mapA;
+    KSC_TRY(make_map(&mapA, qb, nq, Kp, TC_M));
+    const size_t smem = (size_t)KB * (TC_M + TC_N) * 128 + 1024;
+    KSC_CUDA(cudaFuncSetAttribute(k_rank_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((ix->L + TC_N - 1) / TC_N, (unsigned)((nq + TC_M - 1) / TC_M));
+    k_rank_gemm_tc<<<grid, 128, smem, st>>>(mapA, *reinterpret_cast<const CUtensorMap*>(ix->map_c), KB, nq, ix->L,
+                                            ix->c_rank_sq, ix->spherical, scores, ix->status);
+    KSC_LAUNCH_CHECK();
+    ix->launches += 2;
+    return score_err(ix, Q, nq, true, err, st);
+}
+
+int score_err(ksc_index* ix, const float* Q, int64_t nq, bool tensor_cores, float* err, cudaStream_t st) {
+    if (ix->c_rank_max_norm <= 0.f) {
+        std::vector<float> cn(ix->L);
+        KSC_CUDA(cudaMemcpyAsync(cn.data(), ix->c_rank_sq, sizeof(float) * ix->L, cudaMemcpyDeviceToHost, st));
+        KSC_CUDA(cudaStreamSynchronize(st));
+        float m = 0.f;
+        for (float v : cn) m = v > m ? v : m;
+        ix->c_rank_max_norm = m > 0.f ? sqrtf(m) : 1e-30f;
+    }
+    const float rel = tensor_cores ? 0.0078125f + 6.2e-5f + (float)ix->d * 4.8e-7f : (float)(ix->d + 8) * 1.2e-7f;
+    k_score_err<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(Q, nq, ix->d, ix->c_rank_max_norm, ix->spherical,
+                                                              rel, err);
+    KSC_LAUNCH_CHECK();
+    ix->launches++;
+    return KSC_OK;
+}
+
+}  // namespace ksc

@@ -20,6 +20,8 @@ namespace ksc {
 constexpr int PRE_CAP = 8192;   // keys examined by the threshold pre-pass
 constexpr int SEL_CAP = 4096;   // bitonic buffer of the select kernels (>= KSC_MAX_RERANK)
 constexpr int MAX_NPROBE = 4096;
+constexpr int PRE_MULT = 8;      // the pre-pass looks at up to 8R keys of the nearest lists
+constexpr int PRE_BIN_CAP = 1024;
 
 // ------------------------------------------------------------------ a1: list scores
 // score[q][c] = ||c||^2 - 2<q,c> (L2, ||q||^2 dropped) or -<q,c> (spherical).
@@ -74,26 +76,137 @@ __global__ void __launch_bounds__(256) k_list_scores(const float* __restrict__ Q
     }
 }
 
-// P_q best lists per query by (score, list id).
-__global__ void __launch_bounds__(512) k_topP(const float* __restrict__ scores, int64_t nq, int L,
-                                              const int32_t* __restrict__ nprobe_q, int Pfix, int Pmax,
-                                              int32_t* __restrict__ probes, float* __restrict__ score_out,
-                                              const float* __restrict__ qnorm_add) {
-    extern __shared__ uint64_t sm_sel[];
-    __shared__ uint32_t hist[256];
-    __shared__ uint64_t outk[MAX_NPROBE];
+// P_q best lists per query.  `scores` may be approximate (each within err[q]
+// of the exact score; err = NULL means exact): a float histogram finds the
+// bin of the P-th smallest score, every list whose score can still be among
+// the P best (score <= upper edge of that bin + 2 err) is re-scored exactly in
+// FP32 (L2: sum_t (q_t - c_t)^2 in the direct form; spherical: -<q, c>), and
+// the P best by (exact score, list id) are kept.  If more than RS_CAP lists
+// qualify, every list is re-scored and sorted.
+constexpr int RS_CAP = 4096;
+__device__ __forceinline__ float exact_list_score(const float* __restrict__ qs, const float* __restrict__ c, int d,
+                                                  int spherical, int lane) {
+    float acc = 0.f;
+    if ((d & 3) == 0) {
+        for (int t = lane * 4; t < d; t += 128) {
+            float4 cv = __ldg(reinterpret_cast<const float4*>(c + t));
+            float4 qv = *reinterpret_cast<const float4*>(qs + t);
+            if (spherical) {
+                acc = fmaf(qv.x, cv.x, acc); acc = fmaf(qv.y, cv.y, acc);
+                acc = fmaf(qv.z, cv.z, acc); acc = fmaf(qv.w, cv.w, acc);
+            } else {
+                float e0 = qv.x - cv.x, e1 = qv.y - cv.y, e2 = qv.z - cv.z, e3 = qv.w - cv.w;
+                acc = fmaf(e0, e0, acc); acc = fmaf(e1, e1, acc); acc = fmaf(e2, e2, acc); acc = fmaf(e3, e3, acc);
+            }
+        }
+    } else {
+        for (int t = lane; t < d; t += 32) {
+            float cv = __ldg(c + t);
+            if (spherical) acc = fmaf(qs[t], cv, acc);
+            else { float e = qs[t] - cv; acc = fmaf(e, e, acc); }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return spherical ? -acc : acc;
+}
+
+__global__ void __launch_bounds__(256) k_rank_select(const float* __restrict__ scores, const float* __restrict__ err,
+                                                     const float* __restrict__ Q, const float* __restrict__ Cc,
+                                                     int64_t nq, int d, int L, int spherical,
+                                                     const int32_t* __restrict__ nprobe_q, int Pfix, int Pmax,
+                                                     int32_t* __restrict__ probes, float* __restrict__ score_out) {
+    extern __shared__ uint64_t cand[];  // RS_CAP keys
+    __shared__ uint32_t hist[HIST_BINS];
+    __shared__ uint32_t warp_tot[32];
+    __shared__ __align__(16) float qs[KSC_MAX_DIM];
+    __shared__ uint32_t s_mn, s_mx;
+    __shared__ int s_cnt, s_B;
     const int64_t q = blockIdx.x;
-    if (q >= nq) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     int P = nprobe_q ? nprobe_q[q] : Pfix;
     P = P < 1 ? 1 : (P > Pmax ? Pmax : P);
     const float* s = scores + q * L;
-    auto load = [&](int c) -> uint64_t { return ((uint64_t)ordered_f32(s[c]) << 32) | (uint32_t)c; };
-    block_select_smallest(load, L, P, outk, sm_sel, SEL_CAP, hist);
+    const float e2 = err ? 2.f * err[q] : 0.f;
+    for (int t = threadIdx.x; t < d; t += blockDim.x) qs[t] = Q[q * d + t];
+    if (threadIdx.x == 0) { s_mn = 0xffffffffu; s_mx = 0u; s_cnt = 0; s_B = -1; }
+    for (int b = threadIdx.x; b < HIST_BINS; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    uint32_t mn = 0xffffffffu, mx = 0u;
+    for (int c = threadIdx.x; c < L; c += blockDim.x) {
+        uint32_t u = ordered_f32(s[c]);
+        mn = min(mn, u);
+        mx = max(mx, u);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if (lane == 0) { atomicMin(&s_mn, mn); atomicMax(&s_mx, mx); }
+    __syncthreads();
+    const float fmn = unordered_f32(s_mn), fmx = unordered_f32(s_mx);
+    const float width = (fmx - fmn) / (float)(HIST_BINS - 1);
+    const float inv = width > 0.f ? 1.f / width : 0.f;
+    auto bin_of = [&](float v) -> int {
+        float f = (v - fmn) * inv;
+        return f < (float)(HIST_BINS - 1) ? (int)f : HIST_BINS - 1;
+    };
+    for (int c = threadIdx.x; c < L; c += blockDim.x) atomicAdd(&hist[bin_of(s[c])], 1u);
+    __syncthreads();
+    {
+        const int per = HIST_BINS / blockDim.x;
+        const int b0 = threadIdx.x * per;
+        uint32_t local = 0;
+        for (int b = b0; b < b0 + per; ++b) local += hist[b];
+        const uint32_t excl = block_exclusive_scan(local, warp_tot);
+        if (excl < (uint32_t)P && excl + local >= (uint32_t)P) {
+            uint32_t acc = excl;
+            for (int b = b0; b < b0 + per; ++b) {
+                if (acc + hist[b] >= (uint32_t)P) { s_B = b; break; }
+                acc += hist[b];
+            }
+        }
+    }
+    __syncthreads();
+    // every list that can still be among the P best
+    const float tau = (s_B >= HIST_BINS - 1) ? INFINITY : fmn + (float)(s_B + 1) * width + e2;
+    for (int c = threadIdx.x; c < L; c += blockDim.x) {
+        if (s[c] <= tau) {
+            int slot = atomicAdd(&s_cnt, 1);
+            if (slot < RS_CAP) cand[slot] = (uint64_t)(uint32_t)c;
+        }
+    }
+    __syncthreads();
+    int n = s_cnt;
+    if (n > RS_CAP) {
+        // degenerate score distribution: re-score every list if they fit,
+        // else the RS_CAP lists with the lowest given scores
+        if (L <= RS_CAP) {
+            n = L;
+            for (int c = threadIdx.x; c < L; c += blockDim.x) cand[c] = (uint64_t)(uint32_t)c;
+            __syncthreads();
+        } else {
+            n = RS_CAP;
+            auto load = [&](int c) -> uint64_t { return ((uint64_t)ordered_f32(s[c]) << 32) | (uint32_t)c; };
+            block_select_smallest(load, L, RS_CAP, cand, cand, RS_CAP, hist);
+            for (int i = threadIdx.x; i < RS_CAP; i += blockDim.x) cand[i] &= 0xffffffffull;
+            __syncthreads();
+        }
+    }
+    for (int i = w; i < n; i += nw) {
+        const int c = (int)(uint32_t)cand[i];
+        const float v = exact_list_score(qs, Cc + (int64_t)c * d, d, spherical, lane);
+        if (lane == 0) cand[i] = ((uint64_t)ordered_f32(v) << 32) | (uint32_t)c;
+    }
+    const int S = pow2_ceil(n < 2 ? 2 : n);
+    for (int i = n + threadIdx.x; i < S; i += blockDim.x) cand[i] = KEY_NONE;
+    __syncthreads();
+    block_bitonic_sort(cand, S);
     for (int r = threadIdx.x; r < Pmax; r += blockDim.x) {
         if (r < P) {
-            probes[q * Pmax + r] = (int32_t)(outk[r] & 0xffffffffu);
-            if (score_out) score_out[q * Pmax + r] = unordered_f32((uint32_t)(outk[r] >> 32)) +
-                                                     (qnorm_add ? qnorm_add[q] : 0.f);
+            probes[q * Pmax + r] = (int32_t)(cand[r] & 0xffffffffu);
+            if (score_out) score_out[q * Pmax + r] = unordered_f32((uint32_t)(cand[r] >> 32));
         } else {
             probes[q * Pmax + r] = -1;
             if (score_out) score_out[q * Pmax + r] = INFINITY;
@@ -101,20 +214,8 @@ __global__ void __launch_bounds__(512) k_topP(const float* __restrict__ scores, 
     }
 }
 
-__global__ void k_qnorm(const float* __restrict__ Q, int64_t nq, int d, int spherical, float* __restrict__ out) {
-    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (q >= nq) return;
-    float s = 0.f;
-    if (!spherical)
-        for (int t = 0; t < d; ++t) s = fmaf(Q[q * d + t], Q[q * d + t], s);
-    out[q] = s;
-}
-
 // ------------------------------------------------------------------ a2: quantised LUTs
-// One warp per (query, probe rank).  Entry e = j * 16 + i of the table; a
-// warp pass covers e = lane + 32 k, so lanes 0-15 hold subspace 2k and
-// lanes 16-31 subspace 2k+1 (M odd: the last pass has an idle half).
-// FP32 rule, every op separately rounded:
+// FP32 rule of the table entries, every op separately rounded:
 //   L2: acc += (q_t - c_t - C_jit)^2 over t ascending;  IP: acc += q_t C_jit, T = -acc
 __device__ __forceinline__ float lut_entry(const float* __restrict__ q, const float* __restrict__ cp,
                                            const float* __restrict__ cw, int j, int dsub, int ip) {
@@ -130,14 +231,6 @@ __device__ __forceinline__ float lut_entry(const float* __restrict__ q, const fl
         }
     }
     return ip ? -acc : acc;
-}
-
-__device__ __forceinline__ void half_minmax(float& mn, float& mx) {
-#pragma unroll
-    for (int o = 8; o > 0; o >>= 1) {
-        mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    }
 }
 
 struct LutArgs {
@@ -157,78 +250,115 @@ __device__ __forceinline__ int probes_of(const LutArgs& A, int64_t q) {
     return P < 1 ? 1 : (P > A.Pmax ? A.Pmax : P);
 }
 
-__global__ void k_lut_range(LutArgs A, uint32_t* __restrict__ range_bits) {
-    const int lane = threadIdx.x & 31;
-    const int64_t item = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    if (item >= A.nq * A.Pmax) return;
-    const int64_t q = item / A.Pmax;
-    const int r = (int)(item - q * A.Pmax);
-    if (r >= probes_of(A, q)) return;
-    const int p = A.probes[item];
-    if (p < 0 || p >= A.L) return;  // invalid probe ids are skipped
-    const float* qv = A.Q + q * A.d;
-    const float* cp = A.c_mean + (int64_t)p * A.d;
-    float R = 0.f;
-    for (int e0 = 0; e0 < A.M * PQ_K; e0 += 32) {
-        const int e = e0 + lane;
-        const int j = e >> 4, i = e & 15;
-        const bool ok = j < A.M;
-        float T = ok ? lut_entry(qv, cp, A.cb + ((int64_t)j * PQ_K + i) * A.dsub, j, A.dsub, A.ip) : 0.f;
-        float mn = T, mx = T;
-        half_minmax(mn, mx);
-        if (ok) R = fmaxf(R, __fsub_rn(mx, mn));
-    }
+// The 16 FP32 table entries of subspace j for (query, list), in registers;
+// cbs = the codebook in shared memory, row j (16 codewords) at j * cbs_ld.
+__device__ __forceinline__ void lut_row(const LutArgs& A, const float* __restrict__ qv, const float* __restrict__ cp,
+                                        const float* cbs, int cbs_ld, int j, float (&T)[PQ_K]) {
+    const float* cw = cbs + j * cbs_ld;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) R = fmaxf(R, __shfl_xor_sync(0xffffffffu, R, o));
-    if (lane == 0) atomicMax(&range_bits[q], __float_as_uint(R));  // R >= 0: bit order = value order
+    for (int i = 0; i < PQ_K; ++i) T[i] = lut_entry(qv, cp, cw + i * A.dsub, j, A.dsub, A.ip);
 }
 
-__global__ void __launch_bounds__(128) k_lut_quant(LutArgs A, const uint32_t* __restrict__ range_bits,
-                                                   uint8_t* __restrict__ lut, int32_t* __restrict__ bias,
-                                                   float* __restrict__ scale) {
-    __shared__ float mins[4][KSC_MAX_M];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int64_t item = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    if (item >= A.nq * A.Pmax) return;
-    const int64_t q = item / A.Pmax;
-    const int r = (int)(item - q * A.Pmax);
-    if (r >= probes_of(A, q)) return;
-    const int p = A.probes[item];
-    if (p < 0 || p >= A.L) return;
-    const float* qv = A.Q + q * A.d;
-    const float* cp = A.c_mean + (int64_t)p * A.d;
-    const float Rq = __uint_as_float(range_bits[q]);
-    const float a = (Rq == 0.f) ? 1.f : __fdiv_rn(255.f, Rq);
-    uint8_t* out = lut + item * (int64_t)A.M * PQ_K;
-    for (int e0 = 0; e0 < A.M * PQ_K; e0 += 32) {
-        const int e = e0 + lane;
-        const int j = e >> 4, i = e & 15;
-        const bool ok = j < A.M;
-        float T = ok ? lut_entry(qv, cp, A.cb + ((int64_t)j * PQ_K + i) * A.dsub, j, A.dsub, A.ip) : 0.f;
-        float mn = T, mx = T;
-        half_minmax(mn, mx);
-        if (ok) {
-            float h = __fadd_rn(__fmul_rn(__fsub_rn(T, mn), a), 0.5f);
-            float f = floorf(h);
-            out[e] = (uint8_t)(f > 255.f ? 255.f : f);
-            if (i == 0) mins[wib][j] = mn;
-        }
+// Codebook into shared memory with row stride 16 dsub + 1 (odd: lanes reading
+// rows j = lane hit distinct banks).
+__device__ __forceinline__ int stage_codebook(const LutArgs& A, float* cbs) {
+    const int ld = PQ_K * A.dsub + 1;
+    for (int e = threadIdx.x; e < A.M * PQ_K * A.dsub; e += blockDim.x) {
+        const int j = e / (PQ_K * A.dsub), rest = e - j * (PQ_K * A.dsub);
+        cbs[j * ld + rest] = A.cb[e];
     }
-    __syncwarp();
-    if (lane == 0) {
-        float S = 0.f;
-        if (A.ip) {
-            float dot = 0.f;
-            for (int t = 0; t < A.d; ++t) dot = __fadd_rn(dot, __fmul_rn(qv[t], cp[t]));
-            S = -dot;
+    __syncthreads();
+    return ld;
+}
+
+// Persistent; one warp per (query, probe rank) item, lane l owning subspaces
+// j = l + 32u.  Pass 1: the largest table range of the query, R_q (atomic max
+// over its probes).
+__global__ void __launch_bounds__(256) k_lut_range(LutArgs A, uint32_t* __restrict__ range_bits) {
+    extern __shared__ float cbs[];
+    const int lane = threadIdx.x & 31;
+    const int ld = stage_codebook(A, cbs);
+    const int64_t items = A.nq * A.Pmax;
+    for (int64_t item = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); item < items; item += (int64_t)gridDim.x * 8) {
+        const int64_t q = item / A.Pmax;
+        const int r = (int)(item - q * A.Pmax);
+        if (r >= probes_of(A, q)) continue;
+        const int p = A.probes[item];
+        if (p < 0 || p >= A.L) continue;  // invalid probe ids are skipped
+        const float* qv = A.Q + q * A.d;
+        const float* cp = A.c_mean + (int64_t)p * A.d;
+        float R = 0.f;
+        for (int j = lane; j < A.M; j += 32) {
+            float T[PQ_K];
+            lut_row(A, qv, cp, cbs, ld, j, T);
+            float mn = T[0], mx = T[0];
+#pragma unroll
+            for (int i = 1; i < PQ_K; ++i) { mn = fminf(mn, T[i]); mx = fmaxf(mx, T[i]); }
+            R = fmaxf(R, __fsub_rn(mx, mn));
         }
-        for (int j = 0; j < A.M; ++j) S = __fadd_rn(S, mins[wib][j]);
-        float bf = floorf(__fadd_rn(__fmul_rn(S, a), 0.5f));
-        bf = fminf(fmaxf(bf, -1073741824.f), 1073741823.f);
-        bias[item] = (int32_t)bf;
-        if (r == 0) scale[q] = a;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) R = fmaxf(R, __shfl_xor_sync(0xffffffffu, R, o));
+        if (lane == 0) atomicMax(&range_bits[q], __float_as_uint(R));  // R >= 0: bit order = value order
     }
 }
+
+// Pass 2: u8 tables Q = min(255, floor((T - m_j) a + 1/2)), a = 255 / R_q,
+// and the integer bias floor(S a + 1/2) with S = sum_j m_j (+ -<q, c_p> for IP)
+// summed in ascending j.
+__global__ void __launch_bounds__(256) k_lut_quant(LutArgs A, const uint32_t* __restrict__ range_bits,
+                                                   uint8_t* __restrict__ lut, int32_t* __restrict__ bias,
+                                                   float* __restrict__ scale) {
+    extern __shared__ float cbs[];
+    __shared__ float mins[8][KSC_MAX_M];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int ld = stage_codebook(A, cbs);
+    const int64_t items = A.nq * A.Pmax;
+    for (int64_t item = (int64_t)blockIdx.x * 8 + wib; item < items; item += (int64_t)gridDim.x * 8) {
+        const int64_t q = item / A.Pmax;
+        const int r = (int)(item - q * A.Pmax);
+        if (r >= probes_of(A, q)) continue;
+        const int p = A.probes[item];
+        if (p < 0 || p >= A.L) continue;
+        const float* qv = A.Q + q * A.d;
+        const float* cp = A.c_mean + (int64_t)p * A.d;
+        const float Rq = __uint_as_float(range_bits[q]);
+        const float a = (Rq == 0.f) ? 1.f : __fdiv_rn(255.f, Rq);
+        uint4* out = reinterpret_cast<uint4*>(lut + item * (int64_t)A.M * PQ_K);
+        for (int j = lane; j < A.M; j += 32) {
+            float T[PQ_K];
+            lut_row(A, qv, cp, cbs, ld, j, T);
+            float mn = T[0];
+#pragma unroll
+            for (int i = 1; i < PQ_K; ++i) mn = fminf(mn, T[i]);
+            uint32_t w[4] = {0, 0, 0, 0};
+#pragma unroll
+            for (int i = 0; i < PQ_K; ++i) {
+                float f = floorf(__fadd_rn(__fmul_rn(__fsub_rn(T[i], mn), a), 0.5f));
+                uint32_t b = (uint32_t)(f > 255.f ? 255.f : f);
+                w[i >> 2] |= b << (8 * (i & 3));
+            }
+            out[j] = make_uint4(w[0], w[1], w[2], w[3]);
+            mins[wib][j] = mn;
+        }
+        __syncwarp();
+        if (lane == 0) {
+            float S = 0.f;
+            if (A.ip) {
+                float dot = 0.f;
+                for (int t = 0; t < A.d; ++t) dot = __fadd_rn(dot, __fmul_rn(qv[t], cp[t]));
+                S = -dot;
+            }
+            for (int j = 0; j < A.M; ++j) S = __fadd_rn(S, mins[wib][j]);
+            float bf = floorf(__fadd_rn(__fmul_rn(S, a), 0.5f));
+            bf = fminf(fmaxf(bf, -1073741824.f), 1073741823.f);
+            bias[item] = (int32_t)bf;
+            if (r == 0) scale[q] = a;
+        }
+        __syncwarp();
+    }
+}
+
+static int launch_luts(const LutArgs& A, uint32_t* rb, uint8_t* lut, int32_t* bias, float* scale, cudaStream_t st);
 
 // ------------------------------------------------------------------ code access
 __device__ __forceinline__ int nibble_of(const uint8_t* __restrict__ blk, int M, int j, int v) {
@@ -283,7 +413,7 @@ __global__ void __launch_bounds__(256) k_prepass(ScanArgs A, int Rmax, uint64_t*
     __shared__ int s_count;
     const int64_t q = blockIdx.x;
     const int R = rerank_of(A.rerank_q, A.Rfix, A.Rmin, Rmax, q);
-    const int cap = min(4 * R, PRE_CAP);
+    const int cap = min(PRE_MULT * R, PRE_CAP);
     const int P = nprobe_of(A, q);
     if (threadIdx.x == 0) s_count = 0;
     __syncthreads();
@@ -311,6 +441,30 @@ __global__ void __launch_bounds__(256) k_prepass(ScanArgs A, int Rmax, uint64_t*
     const int count = s_count;
     if (count < R) {
         if (threadIdx.x == 0) thr[q] = KEY_NONE;
+        return;
+    }
+    // R-th smallest: histogram of the distances, then sort only the keys of
+    // the bin that holds it
+    __shared__ uint32_t hist[HIST_BINS];
+    __shared__ uint32_t warp_tot[32];
+    __shared__ HistSel hs;
+    __shared__ uint64_t binkeys[PRE_BIN_CAP];
+    __shared__ int s_nb;
+    auto load = [&](int i) -> uint64_t { return buf[i]; };
+    hist_find(load, count, R, hist, warp_tot, &hs);
+    if (hs.inB <= PRE_BIN_CAP) {
+        if (threadIdx.x == 0) s_nb = 0;
+        __syncthreads();
+        for (int i = threadIdx.x; i < count; i += blockDim.x) {
+            uint64_t k = buf[i];
+            if (hist_bin(k, hs.base) == hs.B) binkeys[atomicAdd(&s_nb, 1)] = k;
+        }
+        __syncthreads();
+        const int S2 = pow2_ceil(hs.inB);
+        for (int i = hs.inB + threadIdx.x; i < S2; i += blockDim.x) binkeys[i] = KEY_NONE;
+        __syncthreads();
+        block_bitonic_sort(binkeys, S2);
+        if (threadIdx.x == 0) thr[q] = binkeys[R - hs.lt - 1];
         return;
     }
     const int S = pow2_ceil(count);
@@ -579,19 +733,26 @@ __global__ void __launch_bounds__(128) k_lut16_peak(int iters, uint32_t seed, ui
 __global__ void __launch_bounds__(512) k_select(ScanArgs A, int Rmax, const int32_t* __restrict__ cnt,
                                                 const uint64_t* __restrict__ cand, int cap,
                                                 uint64_t* __restrict__ topr, int32_t* __restrict__ ncand,
-                                                int32_t* __restrict__ status) {
+                                                int32_t* __restrict__ status,
+                                                unsigned long long* __restrict__ stats) {
     extern __shared__ uint64_t sbuf[];
-    __shared__ uint32_t hist[256];
+    __shared__ uint32_t hist[HIST_BINS];
+    __shared__ uint32_t warp_tot[32];
     __shared__ int32_t s_pref[MAX_NPROBE + 1];
     const int64_t q = blockIdx.x;
     const int R = rerank_of(A.rerank_q, A.Rfix, A.Rmin, Rmax, q);
     const int n = cnt[q];
     uint64_t* out = topr + q * Rmax;
+    if (threadIdx.x == 0) {
+        atomicAdd(&stats[1], (unsigned long long)n);
+        atomicMax(&stats[2], (unsigned long long)n);
+        if (n > cap) atomicAdd(&stats[0], 1ull);
+    }
     if (n <= cap) {
         const uint64_t* cq = cand + q * cap;
         const int K = min(R, n);
         auto load = [&](int i) -> uint64_t { return cq[i]; };
-        block_select_smallest(load, n, K, out, sbuf, SEL_CAP, hist);
+        block_select_hist(load, n, K, out, sbuf, SEL_CAP, hist, warp_tot);
         for (int i = K + threadIdx.x; i < Rmax; i += blockDim.x) out[i] = KEY_NONE;
         if (threadIdx.x == 0 && ncand) ncand[q] = K;
         return;
@@ -721,6 +882,7 @@ struct Plan {
     const int32_t* nprobe_q;
     const int32_t* rerank_q;
     int G, TB, cap;
+    bool rank_exact;
 };
 
 static int choose_G(const ksc_index* ix, int64_t nq, int Pmax, int want) {
@@ -756,25 +918,44 @@ static int dispatch_scan(int S, const ScanArgs& A, const ScanOut& O, const int64
     return KSC_OK;
 }
 
-static int rank_lists(ksc_index* ix, const float* Q, int64_t nq, const int32_t* nprobe_q, int Pfix, int Pmax,
-                      int32_t* probes, float* score_out, cudaStream_t st) {
-    KSC_TRY(ensure(ix->ws_scores, sizeof(float) * nq * ix->L, st));
-    float* scores = (float*)ix->ws_scores.p;
+// List scores [nq x L] on the BF16 tensor cores or the FP32 CUDA cores, with
+// the per-query bound err [nq] on their distance from the exact scores.
+static int list_scores(ksc_index* ix, const float* Q, int64_t nq, bool exact, float* scores, float** err,
+                       cudaStream_t st) {
+    KSC_TRY(ensure(ix->ws_err, sizeof(float) * nq, st));
+    *err = (float*)ix->ws_err.p;
+    if (!exact && tc_rank_supported(ix)) return rank_scores_tc(ix, Q, nq, scores, *err, st);
     dim3 grid(blocks_for(ix->L, SC_T), blocks_for(nq, SC_T));
     k_list_scores<<<grid, 256, 0, st>>>(Q, nq, ix->d, ix->c_rank, ix->c_rank_sq, ix->L, ix->spherical, scores);
     ix->launches++;
     KSC_LAUNCH_CHECK();
-    float* qn = nullptr;
-    if (score_out) {
-        KSC_TRY(ensure(ix->ws_misc, sizeof(float) * nq, st));
-        qn = (float*)ix->ws_misc.p;
-        k_qnorm<<<blocks_for(nq, 256), 256, 0, st>>>(Q, nq, ix->d, ix->spherical, qn);
-        ix->launches++;
-    }
-    const size_t smem = SEL_CAP * sizeof(uint64_t);
-    cudaFuncSetAttribute(k_topP, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_topP<<<(unsigned)nq, 512, smem, st>>>(scores, nq, ix->L, nprobe_q, Pfix, Pmax, probes, score_out, qn);
+    return score_err(ix, Q, nq, false, *err, st);
+}
+
+static int rank_lists(ksc_index* ix, const float* Q, int64_t nq, const int32_t* nprobe_q, int Pfix, int Pmax,
+                      int32_t* probes, float* score_out, bool exact, cudaStream_t st) {
+    KSC_TRY(ensure(ix->ws_scores, sizeof(float) * nq * ix->L, st));
+    float* scores = (float*)ix->ws_scores.p;
+    float* err = nullptr;
+    KSC_TRY(list_scores(ix, Q, nq, exact, scores, &err, st));
+    const size_t smem = RS_CAP * sizeof(uint64_t);
+    cudaFuncSetAttribute(k_rank_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_rank_select<<<(unsigned)nq, 256, smem, st>>>(scores, err, Q, ix->c_rank, nq, ix->d, ix->L, ix->spherical,
+                                                   nprobe_q, Pfix, Pmax, probes, score_out);
     ix->launches++;
+    KSC_LAUNCH_CHECK();
+    return KSC_OK;
+}
+
+static int launch_luts(const LutArgs& A, uint32_t* rb, uint8_t* lut, int32_t* bias, float* scale, cudaStream_t st) {
+    const size_t smem = sizeof(float) * (size_t)A.M * (PQ_K * A.dsub + 1);
+    cudaFuncSetAttribute(k_lut_range, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_lut_quant, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int64_t items = A.nq * A.Pmax;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((items + 7) / 8, (int64_t)num_sms() * 8));
+    k_lut_range<<<grid, 256, smem, st>>>(A, rb);
+    KSC_LAUNCH_CHECK();
+    k_lut_quant<<<grid, 256, smem, st>>>(A, rb, lut, bias, scale);
     KSC_LAUNCH_CHECK();
     return KSC_OK;
 }
@@ -786,12 +967,8 @@ static int compute_luts(ksc_index* ix, const float* Q, int64_t nq, const int32_t
     KSC_CUDA(cudaMemsetAsync(rb, 0, sizeof(uint32_t) * nq, st));
     LutArgs A{Q, nq, ix->d, ix->M, ix->dsub, ix->metric == KSC_IP, Pmax, probes, nprobe_q, Pfix, ix->c_mean,
               ix->codebook, ix->L};
-    const int64_t threads = nq * Pmax * 32;
-    k_lut_range<<<blocks_for(threads, 128), 128, 0, st>>>(A, rb);
-    KSC_LAUNCH_CHECK();
-    k_lut_quant<<<blocks_for(threads, 128), 128, 0, st>>>(A, rb, lut, bias, scale);
+    KSC_TRY(launch_luts(A, rb, lut, bias, scale, st));
     ix->launches += 2;
-    KSC_LAUNCH_CHECK();
     return KSC_OK;
 }
 
@@ -816,7 +993,7 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
     KSC_TRY(ensure(ix->ws_thr, sizeof(uint64_t) * nq, st));
     uint64_t* thr = (uint64_t*)ix->ws_thr.p;
     {
-        const int cap = std::min(4 * pl.Rmax, PRE_CAP);
+        const int cap = std::min(PRE_MULT * pl.Rmax, PRE_CAP);
         const size_t smem = sizeof(uint64_t) * pow2_ceil(cap);
         cudaFuncSetAttribute(k_prepass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_prepass<<<(unsigned)nq, 256, smem, st>>>(A, pl.Rmax, thr);
@@ -865,7 +1042,8 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
     {
         const size_t smem = SEL_CAP * sizeof(uint64_t);
         cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_select<<<(unsigned)nq, 512, smem, st>>>(A, pl.Rmax, cnt, cand, pl.cap, topr, ncand_out, ix->status);
+        k_select<<<(unsigned)nq, 512, smem, st>>>(A, pl.Rmax, cnt, cand, pl.cap, topr, ncand_out, ix->status,
+                                                  ix->stats);
         ix->launches++;
         KSC_LAUNCH_CHECK();
     }
@@ -912,8 +1090,9 @@ static int make_plan(ksc_index* ix, int64_t nq, int k, int Pmax, int Rmax, const
         int TB = (int)(blocks / target);
         pl.TB = TB < 4 ? 4 : (TB > 64 ? 64 : TB);
     }
-    int cap = (opts && opts->cand_cap > 0) ? opts->cand_cap : std::max(8 * Rmax, 2048);
+    int cap = (opts && opts->cand_cap > 0) ? opts->cand_cap : std::max(16 * Rmax, 4096);
     pl.cap = std::max(cap, Rmax);
+    pl.rank_exact = opts && opts->rank_fp32;
     return KSC_OK;
 }
 
@@ -929,7 +1108,20 @@ int ksc_rank_lists(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t P, int
     KSC_CHECK_ARG(P >= 1 && P <= ix->L && P <= MAX_NPROBE, "P must be in [1, min(nlist, %d)]", MAX_NPROBE);
     if (nq == 0) return KSC_OK;
     KSC_CHECK_ARG(Q_dev && probes_dev, "null argument");
-    return rank_lists(ix, Q_dev, nq, nullptr, P, P, probes_dev, scores_dev, as_stream(stream));
+    return rank_lists(ix, Q_dev, nq, nullptr, P, P, probes_dev, scores_dev, false, as_stream(stream));
+}
+
+int ksc_list_scores(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t tensor_cores, float* scores_dev,
+                    float* err_dev, void* stream) {
+    KSC_CHECK_ARG(ix, "null index");
+    if (nq == 0) return KSC_OK;
+    KSC_CHECK_ARG(Q_dev && scores_dev, "null argument");
+    cudaStream_t st = as_stream(stream);
+    const bool exact = !tensor_cores || !tc_rank_supported(ix);
+    float* err = nullptr;
+    KSC_TRY(list_scores(ix, Q_dev, nq, exact, scores_dev, &err, st));
+    if (err_dev) KSC_CUDA(cudaMemcpyAsync(err_dev, err, sizeof(float) * nq, cudaMemcpyDeviceToDevice, st));
+    return KSC_OK;
 }
 
 int ksc_compute_luts(ksc_index* ix, const float* Q_dev, int64_t nq, const int32_t* probes_dev, int32_t P,
@@ -951,6 +1143,7 @@ int ksc_search_with_probes(ksc_index* ix, const float* Q_dev, int64_t nq, const 
     KSC_CHECK_ARG(Q_dev && probes_dev && ids_dev && dists_dev, "null argument");
     cudaStream_t st = as_stream(stream);
     KSC_CUDA(cudaMemsetAsync(ix->status, 0, sizeof(int32_t), st));
+    KSC_CUDA(cudaMemsetAsync(ix->stats, 0, sizeof(unsigned long long) * 4, st));
     ix->launches = 0;
     mark(ix, 0, st);
     return search_from_probes(ix, Q_dev, pl, probes_dev, ids_dev, dists_dev, cand_dev, ncand_dev, st);
@@ -967,9 +1160,10 @@ int ksc_search(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t k, int32_t
     KSC_CUDA(cudaMemsetAsync(ix->status, 0, sizeof(int32_t), st));
     KSC_TRY(ensure(ix->ws_probes, sizeof(int32_t) * nq * pl.Pmax, st));
     int32_t* probes = (int32_t*)ix->ws_probes.p;
+    KSC_CUDA(cudaMemsetAsync(ix->stats, 0, sizeof(unsigned long long) * 4, st));
     ix->launches = 0;
     mark(ix, 0, st);
-    KSC_TRY(rank_lists(ix, Q_dev, nq, nullptr, pl.Pmax, pl.Pmax, probes, nullptr, st));
+    KSC_TRY(rank_lists(ix, Q_dev, nq, nullptr, pl.Pmax, pl.Pmax, probes, nullptr, pl.rank_exact, st));
     return search_from_probes(ix, Q_dev, pl, probes, ids_dev, dists_dev, nullptr, nullptr, st);
 }
 
@@ -987,9 +1181,10 @@ int ksc_search_varprobe(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t k
     KSC_CUDA(cudaMemsetAsync(ix->status, 0, sizeof(int32_t), st));
     KSC_TRY(ensure(ix->ws_probes, sizeof(int32_t) * nq * pl.Pmax, st));
     int32_t* probes = (int32_t*)ix->ws_probes.p;
+    KSC_CUDA(cudaMemsetAsync(ix->stats, 0, sizeof(unsigned long long) * 4, st));
     ix->launches = 0;
     mark(ix, 0, st);
-    KSC_TRY(rank_lists(ix, Q_dev, nq, nprobe_dev, pl.Pmax, pl.Pmax, probes, nullptr, st));
+    KSC_TRY(rank_lists(ix, Q_dev, nq, nprobe_dev, pl.Pmax, pl.Pmax, probes, nullptr, pl.rank_exact, st));
     return search_from_probes(ix, Q_dev, pl, probes, ids_dev, dists_dev, nullptr, nullptr, st);
 }
 
@@ -1047,6 +1242,14 @@ int ksc_lut16_peak(double* glookups_host, void* stream) {
     return KSC_OK;
 }
 
+int ksc_search_stats(ksc_index* ix, int64_t* stats_host) {
+    KSC_CHECK_ARG(ix && stats_host, "null argument");
+    unsigned long long v[4];
+    KSC_CUDA(cudaMemcpy(v, ix->stats, sizeof(v), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < 4; ++i) stats_host[i] = (int64_t)v[i];
+    return KSC_OK;
+}
+
 int ksc_last_status(ksc_index* ix, int32_t* status_host) {
     KSC_CHECK_ARG(ix && status_host, "null argument");
     KSC_CUDA(cudaMemcpy(status_host, ix->status, sizeof(int32_t), cudaMemcpyDeviceToHost));
@@ -1098,10 +1301,5 @@ extern "C" int ksc_compute_luts_noalloc(ksc_index* ix, const float* Q_dev, int64
     KSC_CUDA(cudaMemsetAsync(rb, 0, sizeof(uint32_t) * nq, st));
     LutArgs A{Q_dev, nq, ix->d, ix->M, ix->dsub, ix->metric == KSC_IP, P, probes_dev, nullptr, P, ix->c_mean,
               ix->codebook, ix->L};
-    const int64_t threads = nq * P * 32;
-    k_lut_range<<<blocks_for(threads, 128), 128, 0, st>>>(A, rb);
-    KSC_LAUNCH_CHECK();
-    k_lut_quant<<<blocks_for(threads, 128), 128, 0, st>>>(A, rb, lut_dev, bias_dev, scale_dev);
-    KSC_LAUNCH_CHECK();
-    return KSC_OK;
+    return launch_luts(A, rb, lut_dev, bias_dev, scale_dev, st);
 }

@@ -40,7 +40,7 @@ class IndexArrays(C.Structure):
 
 class SearchOpts(C.Structure):
     _fields_ = [("lanes_per_query", C.c_int32), ("hybrid", C.c_int32), ("n_near", C.c_int32),
-                ("efs", C.c_int32), ("tau", C.c_int32), ("cand_cap", C.c_int32)]
+                ("efs", C.c_int32), ("tau", C.c_int32), ("cand_cap", C.c_int32), ("rank_fp32", C.c_int32)]
 
 
 _vp, _i32, _i64 = C.c_void_p, C.c_int32, C.c_int64
@@ -55,8 +55,10 @@ _SIGS = {
     "ksc_search_with_probes": [_vp, _vp, _i64, _vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp],
     "ksc_rank_lists": [_vp, _vp, _i64, _i32, _vp, _vp, _vp],
     "ksc_compute_luts": [_vp, _vp, _i64, _vp, _i32, _vp, _vp, _vp, _vp],
+    "ksc_list_scores": [_vp, _vp, _i64, _i32, _vp, _vp, _vp],
     "ksc_compute_luts_noalloc": [_vp, _vp, _i64, _vp, _i32, _vp, _vp, _vp, _vp],
     "ksc_last_status": [_vp, _vp],
+    "ksc_search_stats": [_vp, _vp],
     "ksc_profile_enable": [_vp, _i32],
     "ksc_profile_read": [_vp, _vp, _i32, _vp],
     "ksc_lut16_peak": [_vp, _vp],
@@ -117,8 +119,8 @@ def _hptr(a):
     return None if a is None else a.ctypes.data_as(C.c_void_p)
 
 
-def search_opts(lanes_per_query=0, hybrid=False, n_near=2, efs=64, tau=8, cand_cap=0):
-    return SearchOpts(lanes_per_query, int(hybrid), n_near, efs, tau, cand_cap)
+def search_opts(lanes_per_query=0, hybrid=False, n_near=2, efs=64, tau=8, cand_cap=0, rank_fp32=False):
+    return SearchOpts(lanes_per_query, int(hybrid), n_near, efs, tau, cand_cap, int(rank_fp32))
 
 
 class Index:
@@ -207,6 +209,17 @@ class Index:
                                     _dptr(scores), _stream(stream)))
         return probes, scores
 
+    def list_scores(self, Q, tensor_cores=True, stream=None):
+        """Raw step-a1 scores [nq x L] and their per-query error bound [nq]."""
+        torch = _torch()
+        nq = Q.shape[0]
+        L = self.info()["nlist"]
+        scores = torch.empty((nq, L), dtype=torch.float32, device=Q.device)
+        err = torch.empty((nq,), dtype=torch.float32, device=Q.device)
+        _check(lib().ksc_list_scores(self._h, _dptr(Q, torch.float32, "Q"), nq, int(tensor_cores), _dptr(scores),
+                                     _dptr(err), _stream(stream)))
+        return scores, err
+
     def compute_luts(self, Q, probes, stream=None):
         torch = _torch()
         nq, P = probes.shape
@@ -230,6 +243,12 @@ class Index:
         n = C.c_int32(0)
         _check(lib().ksc_profile_read(self._h, ms, len(self.STAGES), C.byref(n)))
         return {k: ms[i] for i, k in enumerate(self.STAGES)}, n.value
+
+    def search_stats(self):
+        """Counters of the last search: overflowed queries, candidates kept, max per query."""
+        v = (C.c_int64 * 4)()
+        _check(lib().ksc_search_stats(self._h, v))
+        return dict(overflow_queries=v[0], candidates=v[1], max_candidates=v[2])
 
     def last_status(self):
         s = C.c_int32(0)

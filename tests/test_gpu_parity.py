@@ -277,3 +277,32 @@ def test_full_size_sift_sampled_parity(torch, ksc):
     for qi in sample[:10]:
         ref, ref_s = oracle.rank(Q[qi], ix["c_rank"], False, P)
         assert len(np.intersect1d(ref, gp[qi])) >= P - 2
+
+
+@pytest.mark.parametrize("kind", ["small", "ip", "m50"])
+def test_tensor_core_list_scores_within_their_bound(torch, ksc, kind):
+    """tcgen05 BF16 scores stay within the per-query bound the ranking uses."""
+    ix, Q = small_index(kind)
+    g = gpu_index(ksc, ix)
+    s_tc, err = g.list_scores(torch.from_numpy(Q).cuda(), tensor_cores=True)
+    s_tc, err = s_tc.cpu().numpy().astype(np.float64), err.cpu().numpy().astype(np.float64)
+    C = ix["c_rank"].astype(np.float64)
+    Qd = Q.astype(np.float64)
+    exact = -(Qd @ C.T) if ix["spherical"] else (C * C).sum(1)[None] - 2.0 * (Qd @ C.T)
+    assert np.all(np.abs(s_tc - exact) <= err[:, None])
+    # and they are BF16-accurate, not garbage: mean error far below the bound
+    assert np.abs(s_tc - exact).mean() < 0.25 * err.mean()
+    s32, err32 = g.list_scores(torch.from_numpy(Q).cuda(), tensor_cores=False)
+    assert np.all(np.abs(s32.cpu().numpy() - exact) <= err32.cpu().numpy()[:, None])
+
+
+@pytest.mark.parametrize("kind", ["small", "ip", "m50"])
+def test_tensor_core_ranking_equals_fp32_ranking(torch, ksc, kind):
+    """Both score paths re-score every list their bound cannot exclude in
+    exact FP32, so the chosen probes -- and hence the results -- coincide."""
+    ix, Q = small_index(kind)
+    g = gpu_index(ksc, ix)
+    Qd = torch.from_numpy(Q).cuda()
+    a = g.search(Qd, 10, 9, 100)
+    b = g.search(Qd, 10, 9, 100, opts=ksc.search_opts(rank_fp32=True))
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
