@@ -27,7 +27,7 @@ sys.path.insert(0, ROOT)
 
 CFG = dict(workload="ivfpq-sift1m-shape", n=1_000_000, d=128, nq=10_000, nlist=1024, M=64, nbits=4, k=10,
            rerank=200, metric="l2")
-GRID = (8, 12, 16, 24, 32, 48, 64, 96, 128)
+GRID = (4, 6, 8, 10, 12, 16, 24, 32, 48, 64, 96, 128)
 METRIC = "QPS at recall@10\u22650.90 (1M\u00d7128, 1 GB300) vs plain path; ADC-scan HBM GB/s vs peak"
 TARGET_RECALL = 0.90
 L2_FLUSH_BYTES = 256 << 20
@@ -122,6 +122,18 @@ def exact_topk(torch, X, Q, k, chunk=512):
     return np.concatenate(out_i), np.concatenate(out_d)
 
 
+def kth_fp32(torch, Xd, Q, k=10, chunk=4096):
+    """True k-th neighbour distance per query, FP32 brute force on the GPU
+    (training labels only; integer data keeps these exact up to ~1e-7)."""
+    xn = (Xd * Xd).sum(1)
+    out = []
+    for b in range(0, Q.shape[0], chunk):
+        q = Q[b:b + chunk]
+        D = (q * q).sum(1, keepdim=True) - 2.0 * (q @ Xd.T) + xn[None]
+        out.append(torch.topk(D, k, dim=1, largest=False).values[:, k - 1])
+    return torch.cat(out).contiguous()
+
+
 def recall_at_10(torch, X, Q, ids, true_d, k=10):
     """A returned id counts when its exact distance <= the true 10th distance."""
     idt = torch.as_tensor(ids, device=X.device)
@@ -179,41 +191,85 @@ def run_ours(args, rank, ws):
     st = torch.cuda.current_stream()
     ids = torch.empty((CFG["nq"], k), dtype=torch.int64, device=dev)
     dists = torch.empty((CFG["nq"], k), dtype=torch.float32, device=dev)
-    ix.profile(True)
-    for _ in range(args.warmup):
-        ix.search(Qd, k, nprobe, R, out=(ids, dists))
-    torch.cuda.synchronize()
-    stage_ms = {s: [] for s in ksc.Index.STAGES}
-    step_ms = []
-    launches = 0
-    barrier(ws)
-    with Clocks(local) as clk:
-        for _ in range(args.steps):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(st)
-            ix.search(Qd, k, nprobe, R, out=(ids, dists))
-            e1.record(st)
-            e1.synchronize()
-            step_ms.append(e0.elapsed_time(e1))
-            prof, nl = ix.profile_read()
-            launches += nl
-            for s_, v in prof.items():
-                stage_ms[s_].append(v)
-    torch.cuda.synchronize()
-    barrier(ws)
-    ms = statistics.mean(step_ms)
-    ms_max = max_over_ranks(ms, ws)
-    value = CFG["nq"] * ws / (ms_max * 1e-3)
+
+    def timed(search, clk_dev=None):
+        """W warm-up + K timed steps of `search` (L2 flushed before each);
+        returns mean ms, per-stage ms, kernel launches, clocks."""
+        ix.profile(True)
+        for _ in range(args.warmup):
+            search()
+        torch.cuda.synchronize()
+        stage = {s_: [] for s_ in ksc.Index.STAGES}
+        times, nl_tot = [], 0
+        barrier(ws)
+        with Clocks(local) as clk:
+            for _ in range(args.steps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                search()
+                e1.record(st)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+                prof, nl = ix.profile_read()
+                nl_tot += nl
+                for s_, v in prof.items():
+                    stage[s_].append(v)
+        torch.cuda.synchronize()
+        barrier(ws)
+        ix.profile(False)
+        return statistics.mean(times), {s_: statistics.mean(v) for s_, v in stage.items()}, nl_tot, clk.summary()
+
+    plain_ms, plain_stage, plain_launches, plain_clk = timed(lambda: ix.search(Qd, k, nprobe, R, out=(ids, dists)))
     stats = ix.search_stats()
     if args.quick:
         if rank == 0:
-            print(json.dumps({"quick": True, "nprobe": nprobe, "ms_per_step": round(ms_max, 4),
-                              "value": round(value, 1), "stage_ms": {s_: round(statistics.mean(v), 4)
-                                                                      for s_, v in stage_ms.items()},
+            print(json.dumps({"quick": True, "nprobe": nprobe, "ms_per_step": round(plain_ms, 4),
+                              "value": round(CFG["nq"] / (plain_ms * 1e-3), 1),
+                              "stage_ms": {s_: round(v, 4) for s_, v in plain_stage.items()},
                               "search_stats": stats}))
         return None
+    # learned nprobe (the paper's adaptive search module, an MLP here):
+    # train on seeded training queries, tune Eq. 2 on a held-out split
+    learned = None
+    if not args.no_learned:
+        TV = synth.train_queries(5, args.ntrain + 5000)
+        Td = torch.from_numpy(TV[:args.ntrain]).to(dev)
+        Vd = torch.from_numpy(TV[args.ntrain:]).to(dev)
+        t0 = time.time()
+        loss = ix.train_predictor(Td, kth_fp32(torch, Xd, Td, k), epochs=8)
+        train_s = time.time() - t0
+        _, vd_true = exact_topk(torch, Xd, Vd, k)
+        best = None
+        for pmax in (16, 32, 64):
+            for pmin in (1, 2, 4):
+                for p0 in (0.0, 0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7):
+                    for p1 in (0.0, 0.5, 1.0, 2.0, 4.0):
+                        ix.set_predictor_params(pmin, pmax, R, R, p0, p1, 0.0, 0.0)
+                        vids, _, vnp, _ = ix.search_adaptive(Vd, k)
+                        rec = recall_at_10(torch, Xd, Vd, vids, vd_true, k)
+                        cost = float(vnp.double().mean().item())
+                        if rec >= TARGET_RECALL + 0.005 and (best is None or cost < best[0]):
+                            best = (cost, rec, pmin, pmax, p0, p1)
+        if best is not None:
+            ix.set_predictor_params(best[2], best[3], R, R, best[4], best[5], 0.0, 0.0)
+            lids, _, lnp, _ = ix.search_adaptive(Qd, k)
+            l_rec = recall_at_10(torch, Xd, Qd, lids, true_d, k)
+            l_ms, l_stage, l_launches, l_clk = timed(lambda: ix.search_adaptive(Qd, k))
+            learned = dict(ms=l_ms, stage=l_stage, launches=l_launches, clk=l_clk, recall=l_rec,
+                           mean_nprobe=float(lnp.double().mean().item()), nprobe_q=lnp.cpu().numpy(),
+                           params=dict(pmin=best[2], pmax=best[3], p0=best[4], p1=best[5]), train_loss=loss,
+                           train_s=round(train_s, 1), val_recall=best[1], stats=ix.search_stats())
+    use_learned = learned is not None and learned["recall"] >= TARGET_RECALL
+    if use_learned:
+        ms, stage_avg, launches, clocks = learned["ms"], learned["stage"], learned["launches"], learned["clk"]
+        stats = learned["stats"]
+    else:
+        ms, stage_avg, launches, clocks = plain_ms, plain_stage, plain_launches, plain_clk
+    ms_max = max_over_ranks(ms, ws)
+    value = CFG["nq"] * ws / (ms_max * 1e-3)
+    stage_ms = {s_: [v] for s_, v in stage_avg.items()}
     # end to end through the public API with host buffers
     Qpin = torch.from_numpy(Qh).pin_memory()
     ids_h = torch.empty((CFG["nq"], k), dtype=torch.int64).pin_memory()
@@ -226,22 +282,29 @@ def run_ours(args, rank, ws):
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(st)
         Qtmp.copy_(Qpin, non_blocking=True)
-        ix.search(Qtmp, k, nprobe, R, out=(ids, dists))
-        ids_h.copy_(ids, non_blocking=True)
-        d_h.copy_(dists, non_blocking=True)
+        if use_learned:
+            r_ids, r_d, _, _ = ix.search_adaptive(Qtmp, k)
+        else:
+            r_ids, r_d = ix.search(Qtmp, k, nprobe, R, out=(ids, dists))
+        ids_h.copy_(r_ids, non_blocking=True)
+        d_h.copy_(r_d, non_blocking=True)
         e1.record(st)
         e1.synchronize()
         if it >= args.warmup:
             e2e_ms.append(e0.elapsed_time(e1))
     e2e = CFG["nq"] * ws / (max_over_ranks(statistics.mean(e2e_ms), ws) * 1e-3)
-    ix.profile(False)
     # roofline of the dominant kernel (the LUT16 scan): lookups per launch
-    probes, _ = ix.rank_lists(Qd, nprobe, want_scores=False)
+    pmax_r = learned["params"]["pmax"] if use_learned else nprobe
+    probes, _ = ix.rank_lists(Qd, pmax_r, want_scores=False)
     sizes = np.bincount(ix.export()["assign"], minlength=CFG["nlist"]) if rank == 0 else None
     out = None
     if rank == 0:
         pr = probes.cpu().numpy()
-        pairs_vecs = int(sizes[pr].sum())
+        if use_learned:
+            used = np.arange(pr.shape[1])[None, :] < learned["nprobe_q"][:, None]
+            pairs_vecs = int((sizes[pr] * used).sum())
+        else:
+            pairs_vecs = int(sizes[pr].sum())
         lookups = pairs_vecs * CFG["M"]
         code_bytes = pairs_vecs * CFG["M"] // 2
         scan_ms = statistics.mean(stage_ms["scan"])
@@ -250,7 +313,15 @@ def run_ours(args, rank, ws):
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
             os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
         cpu = cpu_baseline(ix, X, Qh, nprobe, R, k, true_d) if (ws == 1 and not args.no_cpu) else None
-        clocks = clk.summary()
+        plain = {"value": round(CFG["nq"] / (plain_ms * 1e-3), 1), "ms_per_step": round(plain_ms, 4),
+                 "nprobe": nprobe, "rerank": R, "recall@10": recall,
+                 "stage_ms": {s_: round(v, 4) for s_, v in plain_stage.items()}}
+        lrn = None if learned is None else {
+            "value": round(CFG["nq"] / (learned["ms"] * 1e-3), 1), "ms_per_step": round(learned["ms"], 4),
+            "recall@10": round(learned["recall"], 4), "mean_nprobe": round(learned["mean_nprobe"], 3),
+            "eq2": learned["params"], "validation_recall@10": round(learned["val_recall"], 4),
+            "train_queries": args.ntrain, "train_loss": round(learned["train_loss"], 4),
+            "train_s": learned["train_s"], "vs_plain": round(plain_ms / learned["ms"], 3)}
         out = {
             "metric": METRIC,
             "value": round(value, 1), "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
@@ -261,7 +332,9 @@ def run_ours(args, rank, ws):
                        "nlist": CFG["nlist"], "M": CFG["M"], "nbits": 4, "k": k, "rerank": R,
                        "nprobe": nprobe, "recall@10": recall, "nprobe_sweep": sweep,
                        "l2": "flushed (256 MB write) before every timed step", "parallelism": "replica x%d" % ws},
-            "recall@10": recall,
+            "recall@10": round(learned["recall"], 4) if use_learned else recall,
+            "path": "learned nprobe (MLP + Eq. 2)" if use_learned else "plain fixed nprobe",
+            "plain": plain, "learned": lrn,
             "e2e": {"value": round(e2e, 1), "unit": "queries/s",
                     "h2d_bytes_per_step": int(Qh.nbytes), "d2h_bytes_per_step": int(ids_h.numel() * 12)},
             "gpu_launches": launches,
@@ -358,6 +431,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--quick", action="store_true", help="profiling mode: timed steps only, at --nprobe")
     ap.add_argument("--nprobe", type=int, default=0)
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-nprobe path")
+    ap.add_argument("--ntrain", type=int, default=100_000)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, ws = dist_setup()

@@ -183,6 +183,80 @@ int ksc_compute_luts(ksc_index* ix, const float* Q_dev, int64_t nq, const int32_
 int ksc_compute_luts_noalloc(ksc_index* ix, const float* Q_dev, int64_t nq, const int32_t* probes_dev,
                              int32_t P, uint8_t* lut_dev, int32_t* bias_dev, float* scale_dev, void* stream);
 
+/* ------------------------------------------------------------------ */
+/* Learned per-query nprobe / reorder (Sec. 4.2.1-4.2.2, Eq. 2)        */
+/* ------------------------------------------------------------------ */
+/* A small MLP stands in for the paper's gradient-boosted classifier.
+ * Features: the 32 smallest list distances of the query (ranking step) as
+ * d_i / mean(d) and d_1 / d_i (64 values).  Network 64 -> 64 -> 64 -> 2,
+ * ReLU, two sigmoid heads p_n (nprobe) and p_r (rerank), FP32 weights packed
+ * as W1[64x64], b1, W2[64x64], b2, W3[2x64], b3 (KSC_MLP_NPARAMS floats);
+ * inference rounds weights and activations to BF16.  Eq. 2 maps p to
+ *   P = min(Pmax, Pmin + ceil((Pmax - Pmin) * max(0, p - p0) * (p + p1)))
+ * and likewise R with (rmin, rmax, r0, r1). */
+#define KSC_MLP_NPARAMS 8450
+#define KSC_MLP_FEATURES 64
+
+typedef struct {
+    int32_t pmin, pmax;   /* nprobe range */
+    int32_t rmin, rmax;   /* rerank range */
+    float p0, p1;         /* Eq. 2 parameters of the nprobe head */
+    float r0, r1;         /* Eq. 2 parameters of the rerank head */
+} ksc_adaptive_params;
+
+typedef struct {
+    int32_t k;              /* neighbours used by the labels (10) */
+    int32_t target_hits;    /* a setting suffices when >= target_hits of them are found (9) */
+    int32_t rerank_label;   /* rerank while labelling nprobe (200) */
+    int32_t epochs;         /* training epochs (8) */
+    int32_t batch;          /* minibatch size (256) */
+    float lr;               /* Adam learning rate (1e-3) */
+    uint64_t seed;          /* weight initialisation and sample order */
+    const int32_t* grid_host;   /* ascending nprobe grid; NULL -> 4,6,8,12,16,24,32,48,64,96,128 */
+    int32_t ngrid;
+    const int32_t* rgrid_host;  /* ascending rerank grid; NULL -> 20,50,100,200,400 */
+    int32_t nrgrid;
+} ksc_train_opts;
+
+/* Train the predictor of this index on the queries Qtrain_dev [nt x d] whose
+ * true k-th neighbour distances are kth_dev [nt] (device; L2 distance, or
+ * similarity for IP).  Labels come from the plain search: for each query the
+ * smallest grid nprobe whose top-k holds at least target_hits ids with
+ * distance within the true k-th ("hard" = above the median of these labels),
+ * and likewise the smallest grid rerank at that nprobe.  Hand-written FP32
+ * forward / backward / Adam kernels.  Blocking.  Sets default Eq. 2
+ * parameters (grid ends, p0 = r0 = 0.3, p1 = r1 = 0.5); *loss_host (may be
+ * NULL) receives the last epoch's mean loss.  opts may be NULL. */
+int ksc_train_predictor(ksc_index* ix, const float* Qtrain_dev, int64_t nt, const float* kth_dev,
+                        const ksc_train_opts* opts, void* stream, float* loss_host);
+
+/* Set the Eq. 2 parameters used by ksc_search_adaptive. */
+int ksc_predictor_params(ksc_index* ix, const ksc_adaptive_params* prm);
+
+/* Copy the predictor weights out (w_host != NULL) and/or in (w_in_host !=
+ * NULL), KSC_MLP_NPARAMS floats each.  Blocking.  KSC_ESTATE if neither is
+ * given a trained model to read. */
+int ksc_predictor_weights(ksc_index* ix, float* w_host, const float* w_in_host);
+
+/* Search with per-query nprobe and rerank predicted by the trained MLP
+ * (KSC_ESTATE if none).  nprobe_dev / rerank_dev [nq] (may be NULL) receive
+ * the predicted values. */
+int ksc_search_adaptive(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t k, int64_t* ids_dev,
+                        float* dists_dev, int32_t* nprobe_dev, int32_t* rerank_dev,
+                        const ksc_search_opts* opts, void* stream);
+
+/* Predictor features of Q_dev: feats_dev [nq x 64]. */
+int ksc_query_features(ksc_index* ix, const float* Q_dev, int64_t nq, float* feats_dev, void* stream);
+
+/* Training kernels alone (for checks): loss and gradient of the mean
+ * binary cross-entropy of the two heads over x_dev [B x 64] with targets
+ * y_dev [B x 2] at weights w_dev; grad_dev [KSC_MLP_NPARAMS], loss_dev [1]. */
+int ksc_mlp_grad(const float* w_dev, const float* x_dev, const float* y_dev, int64_t B, float* grad_dev,
+                 float* loss_dev, void* stream);
+
+/* BF16 inference alone: prob_dev [B x 2]. */
+int ksc_mlp_forward(const float* w_dev, const float* x_dev, int64_t B, float* prob_dev, void* stream);
+
 /* Device status word of the last search on this index: 0 = clean, else a
  * bitwise OR of KSC_STATUS_* (blocking read). */
 #define KSC_STATUS_CAND_OVERFLOW 1  /* a query's candidate store overflowed and was redone exactly */

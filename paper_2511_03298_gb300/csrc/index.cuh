@@ -41,6 +41,9 @@ struct ksc_index {
     void* c_rank_bf16 = nullptr;
     alignas(64) unsigned char map_c[128] = {};
     float c_rank_max_norm = 0.f;
+    // learned nprobe / rerank predictor (Sec. 4.2.1-4.2.2)
+    float* mlp_w = nullptr;  // [KSC_MLP_NPARAMS] FP32
+    ksc_adaptive_params mlp_prm = {};
     // stage timing (ksc_profile_enable)
     bool prof = false;
     cudaEvent_t ev[KSC_NUM_STAGES + 1] = {};
@@ -48,7 +51,7 @@ struct ksc_index {
     int32_t launches = 0;
     // search workspace
     ksc::Buffer ws_scores, ws_probes, ws_lut, ws_bias, ws_scale, ws_range, ws_thr, ws_cnt,
-        ws_cand, ws_topr, ws_nprobe, ws_rerank, ws_items, ws_misc, ws_qbf16, ws_err;
+        ws_cand, ws_topr, ws_nprobe, ws_rerank, ws_items, ws_misc, ws_qbf16, ws_err, ws_feat, ws_rscore;
 };
 
 namespace ksc {
@@ -62,6 +65,16 @@ bool tc_rank_supported(const ksc_index* ix);
 int rank_scores_tc(ksc_index* ix, const float* Q, int64_t nq, float* scores, float* err, cudaStream_t st);
 // Per-query error bound of the list scores (tensor-core or FP32 path).
 int score_err(ksc_index* ix, const float* Q, int64_t nq, bool tensor_cores, float* err, cudaStream_t st);
+// Gather of rows src[idx[r]] (width d floats) into dst (index.cu).
+__global__ void k_gather_rows(const float* __restrict__ X, const int64_t* __restrict__ idx, int64_t cnt, int d,
+                              float* __restrict__ out);
+// MLP kernels (mlp.cu).
+int mlp_grad(const float* w, const float* x, const float* y, int64_t B, float* grad, float* loss, cudaStream_t st);
+int mlp_infer(const float* w, const float* x, int64_t B, const ksc_adaptive_params& prm, float* prob,
+              int32_t* nprobe, int32_t* rerank, cudaStream_t st);
+int mlp_features(const float* scores, int64_t nq, int ld, int spherical, float* feats, cudaStream_t st);
+int mlp_hits(const float* dists, int64_t nq, int k, const float* kth, int ip, int32_t* hits, cudaStream_t st);
+int mlp_adam(float* w, const float* g, float* m, float* v, int t, float lr, cudaStream_t st);
 // Per-list 32-NN graphs and entry points for the hybrid search (Sec. 4.4).
 int build_graph(ksc_index* ix, cudaStream_t st);
 }  // namespace ksc

@@ -1,0 +1,294 @@
+// Learned per-query nprobe / reorder (Sec. 4.2.1-4.2.2, Eq. 2): a small MLP
+// stands in for the paper's gradient-boosted classifier.
+//
+// Features (F = 64) from the ranking step: the 32 smallest list distances
+// d_1 <= ... <= d_32 (L2: ||q - c||^2; spherical: 1 - <q, c>) as d_i / mean(d)
+// and the ratios d_1 / d_i.  Network F -> 64 -> 64 -> 2, ReLU, two sigmoid
+// heads p_n (nprobe) and p_r (reorder), trained with binary cross-entropy on
+// "hard query" labels that the plain search generates, by hand-written FP32
+// forward / backward / Adam kernels.  Inference uses BF16-rounded weights and
+// activations with FP32 accumulation, then Eq. 2 maps p to nprobe and R.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "index.cuh"
+
+namespace ksc {
+
+constexpr int MLP_F = 64, MLP_H = 64, MLP_O = 2, MLP_FEAT_K = 32;
+constexpr int MLP_NPARAM = MLP_H * MLP_F + MLP_H + MLP_H * MLP_H + MLP_H + MLP_O * MLP_H + MLP_O;
+constexpr int MLP_TILE = 128;  // samples per CTA
+
+struct MlpW {  // views into a packed parameter vector (same packing as the oracle)
+    const float *W1, *b1, *W2, *b2, *W3, *b3;
+};
+__host__ __device__ inline MlpW mlp_views(const float* w) {
+    MlpW v;
+    v.W1 = w;
+    v.b1 = v.W1 + MLP_H * MLP_F;
+    v.W2 = v.b1 + MLP_H;
+    v.b2 = v.W2 + MLP_H * MLP_H;
+    v.W3 = v.b2 + MLP_H;
+    v.b3 = v.W3 + MLP_O * MLP_H;
+    return v;
+}
+
+// Features of one query from its sorted ranking scores s[0..32).
+__device__ __forceinline__ float feat_dist(float s, int spherical) { return spherical ? 1.f + s : s; }
+
+__global__ void k_features(const float* __restrict__ scores, int64_t nq, int ld, int spherical,
+                           float* __restrict__ feats) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    const float* s = scores + q * ld;
+    float mean = 0.f;
+    for (int i = 0; i < MLP_FEAT_K; ++i) mean += fmaxf(feat_dist(s[i], spherical), 0.f);
+    mean = mean / MLP_FEAT_K + 1e-12f;
+    const float d1 = fmaxf(feat_dist(s[0], spherical), 0.f) + 1e-12f;
+    float* f = feats + q * MLP_F;
+    for (int i = 0; i < MLP_FEAT_K; ++i) {
+        const float di = fmaxf(feat_dist(s[i], spherical), 0.f) + 1e-12f;
+        f[i] = di / mean;
+        f[MLP_FEAT_K + i] = d1 / di;
+    }
+}
+
+// out[r][a] = act(sum_f in[r][f] W[a][f] + b[a]) for r < rows; W [A x Fin].
+__device__ __forceinline__ void dense(const float* in, int rows, int Fin, const float* W, const float* b, int A,
+                                      float* z, float* h) {
+    for (int e = threadIdx.x; e < rows * A; e += blockDim.x) {
+        const int r = e / A, a = e - r * A;
+        float acc = b[a];
+        for (int f = 0; f < Fin; ++f) acc = fmaf(in[r * Fin + f], W[a * Fin + f], acc);
+        if (z) z[e] = acc;
+        if (h) h[e] = acc > 0.f ? acc : 0.f;
+    }
+}
+
+// One training pass over samples [0, B): loss (mean BCE over the batch, both
+// heads) and gradients accumulated into grad (zeroed by the caller).  CTA c
+// handles samples [c*128, c*128+128); the batch GEMMs run in shared memory.
+__global__ void __launch_bounds__(256) k_mlp_grad(const float* __restrict__ w, const float* __restrict__ x,
+                                                  const float* __restrict__ y, int64_t B, float* __restrict__ grad,
+                                                  float* __restrict__ loss) {
+    extern __shared__ float sm[];
+    float* sw = sm;                          // MLP_NPARAM
+    float* X = sw + MLP_NPARAM;              // 128 x 64
+    float* Z1 = X + MLP_TILE * MLP_F;        // 128 x 64 (pre-activation, then dZ1)
+    float* Z2 = Z1 + MLP_TILE * MLP_H;       // 128 x 64
+    float* H = Z2 + MLP_TILE * MLP_H;        // 128 x 64 scratch (H1, then H2, then dH)
+    float* D3 = H + MLP_TILE * MLP_H;        // 128 x 2
+    const int64_t r0 = (int64_t)blockIdx.x * MLP_TILE;
+    const int rows = (int)(B - r0 < MLP_TILE ? B - r0 : MLP_TILE);
+    for (int e = threadIdx.x; e < MLP_NPARAM; e += blockDim.x) sw[e] = w[e];
+    for (int e = threadIdx.x; e < rows * MLP_F; e += blockDim.x) X[e] = x[r0 * MLP_F + e];
+    __syncthreads();
+    const MlpW W = mlp_views(sw);
+    MlpW G = mlp_views(grad);
+    float* gW1 = const_cast<float*>(G.W1);
+    float* gb1 = const_cast<float*>(G.b1);
+    float* gW2 = const_cast<float*>(G.W2);
+    float* gb2 = const_cast<float*>(G.b2);
+    float* gW3 = const_cast<float*>(G.W3);
+    float* gb3 = const_cast<float*>(G.b3);
+    dense(X, rows, MLP_F, W.W1, W.b1, MLP_H, Z1, H);  // H = H1
+    __syncthreads();
+    dense(H, rows, MLP_H, W.W2, W.b2, MLP_H, Z2, nullptr);
+    __syncthreads();
+    // H2 overwrites H1 only after layer 2 consumed it
+    for (int e = threadIdx.x; e < rows * MLP_H; e += blockDim.x) H[e] = Z2[e] > 0.f ? Z2[e] : 0.f;
+    __syncthreads();
+    // output layer, loss and dZ3 = (p - y) / B
+    float lsum = 0.f;
+    for (int e = threadIdx.x; e < rows * MLP_O; e += blockDim.x) {
+        const int r = e / MLP_O, o = e - r * MLP_O;
+        float z = W.b3[o];
+        for (int f = 0; f < MLP_H; ++f) z = fmaf(H[r * MLP_H + f], W.W3[o * MLP_H + f], z);
+        const float t = y[(r0 + r) * MLP_O + o];
+        const float p = 1.f / (1.f + expf(-z));
+        lsum += fmaxf(z, 0.f) - z * t + log1pf(expf(-fabsf(z)));
+        D3[e] = (p - t) / (float)B;
+    }
+    __syncthreads();
+    // gW3 = D3^T H2, gb3 = sum D3
+    for (int e = threadIdx.x; e < MLP_O * MLP_H; e += blockDim.x) {
+        const int o = e / MLP_H, f = e - o * MLP_H;
+        float acc = 0.f;
+        for (int r = 0; r < rows; ++r) acc = fmaf(D3[r * MLP_O + o], H[r * MLP_H + f], acc);
+        atomicAdd(&gW3[e], acc);
+    }
+    if (threadIdx.x < MLP_O) {
+        float acc = 0.f;
+        for (int r = 0; r < rows; ++r) acc += D3[r * MLP_O + threadIdx.x];
+        atomicAdd(&gb3[threadIdx.x], acc);
+    }
+    __syncthreads();
+    // dZ2 = (D3 W3) * [Z2 > 0]  (into Z2)
+    for (int e = threadIdx.x; e < rows * MLP_H; e += blockDim.x) {
+        const int r = e / MLP_H, f = e - r * MLP_H;
+        float acc = 0.f;
+        for (int o = 0; o < MLP_O; ++o) acc = fmaf(D3[r * MLP_O + o], W.W3[o * MLP_H + f], acc);
+        Z2[e] = Z2[e] > 0.f ? acc : 0.f;
+    }
+    __syncthreads();
+    // H1 again (layer 1 activations) for gW2
+    for (int e = threadIdx.x; e < rows * MLP_H; e += blockDim.x) H[e] = Z1[e] > 0.f ? Z1[e] : 0.f;
+    __syncthreads();
+    for (int e = threadIdx.x; e < MLP_H * MLP_H; e += blockDim.x) {
+        const int a = e / MLP_H, f = e - a * MLP_H;
+        float acc = 0.f;
+        for (int r = 0; r < rows; ++r) acc = fmaf(Z2[r * MLP_H + a], H[r * MLP_H + f], acc);
+        atomicAdd(&gW2[e], acc);
+    }
+    for (int a = threadIdx.x; a < MLP_H; a += blockDim.x) {
+        float acc = 0.f;
+        for (int r = 0; r < rows; ++r) acc += Z2[r * MLP_H + a];
+        atomicAdd(&gb2[a], acc);
+    }
+    __syncthreads();
+    // dZ1 = (dZ2 W2) * [Z1 > 0]  (into Z1)
+    for (int e = threadIdx.x; e < rows * MLP_H; e += blockDim.x) {
+        const int r = e / MLP_H, f = e - r * MLP_H;
+        float acc = 0.f;
+        for (int a = 0; a < MLP_H; ++a) acc = fmaf(Z2[r * MLP_H + a], W.W2[a * MLP_H + f], acc);
+        H[e] = Z1[e] > 0.f ? acc : 0.f;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < MLP_H * MLP_F; e += blockDim.x) {
+        const int a = e / MLP_F, f = e - a * MLP_F;
+        float acc = 0.f;
+        for (int r = 0; r < rows; ++r) acc = fmaf(H[r * MLP_H + a], X[r * MLP_F + f], acc);
+        atomicAdd(&gW1[e], acc);
+    }
+    for (int a = threadIdx.x; a < MLP_H; a += blockDim.x) {
+        float acc = 0.f;
+        for (int r = 0; r < rows; ++r) acc += H[r * MLP_H + a];
+        atomicAdd(&gb1[a], acc);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    if ((threadIdx.x & 31) == 0 && loss) atomicAdd(loss, lsum / (float)B);
+}
+
+// Adam (Kingma & Ba 2015), bias-corrected, on every parameter.
+__global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, int n, float lr, float b1, float b2, float eps, float bc1, float bc2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+}
+
+__device__ __forceinline__ float bf(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
+// Eq. 2 with the line-broken product read literally:
+// P = min(Pmax, Pmin + ceil((Pmax - Pmin) * max(0, p - p0) * (p + p1))).
+__host__ __device__ inline int eq2(float p, int pmin, int pmax, float p0, float p1) {
+    const float relu = p - p0 > 0.f ? p - p0 : 0.f;
+    const float v = ceilf((float)(pmax - pmin) * relu * (p + p1));
+    const float r = (float)pmin + v;
+    return r > (float)pmax ? pmax : (r < (float)pmin ? pmin : (int)r);
+}
+
+// Inference: BF16 weights and activations, FP32 accumulation; probabilities
+// and the Eq. 2 parameters per query.
+__global__ void __launch_bounds__(256) k_mlp_infer(const float* __restrict__ w, const float* __restrict__ x,
+                                                   int64_t B, ksc_adaptive_params prm, float* __restrict__ prob,
+                                                   int32_t* __restrict__ nprobe, int32_t* __restrict__ rerank) {
+    extern __shared__ float sm[];
+    float* sw = sm;
+    float* X = sw + MLP_NPARAM;
+    float* H1 = X + MLP_TILE * MLP_F;
+    float* H2 = H1 + MLP_TILE * MLP_H;
+    const int64_t r0 = (int64_t)blockIdx.x * MLP_TILE;
+    const int rows = (int)(B - r0 < MLP_TILE ? B - r0 : MLP_TILE);
+    for (int e = threadIdx.x; e < MLP_NPARAM; e += blockDim.x) sw[e] = bf(w[e]);
+    for (int e = threadIdx.x; e < rows * MLP_F; e += blockDim.x) X[e] = bf(x[r0 * MLP_F + e]);
+    __syncthreads();
+    const MlpW W = mlp_views(sw);
+    dense(X, rows, MLP_F, W.W1, W.b1, MLP_H, nullptr, H1);
+    __syncthreads();
+    for (int e = threadIdx.x; e < rows * MLP_H; e += blockDim.x) H1[e] = bf(H1[e]);
+    __syncthreads();
+    dense(H1, rows, MLP_H, W.W2, W.b2, MLP_H, nullptr, H2);
+    __syncthreads();
+    for (int e = threadIdx.x; e < rows * MLP_H; e += blockDim.x) H2[e] = bf(H2[e]);
+    __syncthreads();
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+        float p[MLP_O];
+        for (int o = 0; o < MLP_O; ++o) {
+            float z = W.b3[o];
+            for (int f = 0; f < MLP_H; ++f) z = fmaf(H2[r * MLP_H + f], W.W3[o * MLP_H + f], z);
+            p[o] = 1.f / (1.f + expf(-z));
+            if (prob) prob[(r0 + r) * MLP_O + o] = p[o];
+        }
+        if (nprobe) nprobe[r0 + r] = eq2(p[0], prm.pmin, prm.pmax, prm.p0, prm.p1);
+        if (rerank) rerank[r0 + r] = eq2(p[1], prm.rmin, prm.rmax, prm.r0, prm.r1);
+    }
+}
+
+// Hits of a search result: how many of the k returned distances are at most
+// the query's true k-th distance (ties count), for the label rule.
+__global__ void k_hits(const float* __restrict__ dists, int64_t nq, int k, const float* __restrict__ kth, int ip,
+                       int32_t* __restrict__ hits) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    const float t = kth[q];
+    const float tol = 1e-5f * fabsf(t) + 1e-6f;
+    int h = 0;
+    for (int r = 0; r < k; ++r) {
+        const float dv = dists[q * k + r];
+        h += ip ? (dv >= t - tol) : (dv <= t + tol);
+    }
+    hits[q] = h;
+}
+
+static size_t grad_smem() { return sizeof(float) * (MLP_NPARAM + MLP_TILE * (MLP_F + 3 * MLP_H + MLP_O)); }
+static size_t infer_smem() { return sizeof(float) * (MLP_NPARAM + MLP_TILE * (MLP_F + 2 * MLP_H)); }
+
+int mlp_grad(const float* w, const float* x, const float* y, int64_t B, float* grad, float* loss, cudaStream_t st) {
+    KSC_CUDA(cudaMemsetAsync(grad, 0, sizeof(float) * MLP_NPARAM, st));
+    if (loss) KSC_CUDA(cudaMemsetAsync(loss, 0, sizeof(float), st));
+    KSC_CUDA(cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grad_smem()));
+    k_mlp_grad<<<(unsigned)((B + MLP_TILE - 1) / MLP_TILE), 256, grad_smem(), st>>>(w, x, y, B, grad, loss);
+    KSC_LAUNCH_CHECK();
+    return KSC_OK;
+}
+
+int mlp_infer(const float* w, const float* x, int64_t B, const ksc_adaptive_params& prm, float* prob,
+              int32_t* nprobe, int32_t* rerank, cudaStream_t st) {
+    KSC_CUDA(cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)infer_smem()));
+    k_mlp_infer<<<(unsigned)((B + MLP_TILE - 1) / MLP_TILE), 256, infer_smem(), st>>>(w, x, B, prm, prob, nprobe,
+                                                                                      rerank);
+    KSC_LAUNCH_CHECK();
+    return KSC_OK;
+}
+
+int mlp_features(const float* scores, int64_t nq, int ld, int spherical, float* feats, cudaStream_t st) {
+    k_features<<<(unsigned)((nq + 127) / 128), 128, 0, st>>>(scores, nq, ld, spherical, feats);
+    KSC_LAUNCH_CHECK();
+    return KSC_OK;
+}
+
+int mlp_hits(const float* dists, int64_t nq, int k, const float* kth, int ip, int32_t* hits, cudaStream_t st) {
+    k_hits<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(dists, nq, k, kth, ip, hits);
+    KSC_LAUNCH_CHECK();
+    return KSC_OK;
+}
+
+int mlp_adam(float* w, const float* g, float* m, float* v, int t, float lr, cudaStream_t st) {
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float bc1 = 1.f - powf(b1, (float)t), bc2 = 1.f - powf(b2, (float)t);
+    k_adam<<<(MLP_NPARAM + 255) / 256, 256, 0, st>>>(w, g, m, v, MLP_NPARAM, lr, b1, b2, 1e-8f, bc1, bc2);
+    KSC_LAUNCH_CHECK();
+    return KSC_OK;
+}
+
+}  // namespace ksc

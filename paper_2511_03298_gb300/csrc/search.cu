@@ -10,6 +10,7 @@
 //   a5 select   : R smallest (D, id) keys per query (radix select + bitonic)
 //   a6 rerank   : exact FP32 distances of the R candidates, top-k
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <vector>
 
@@ -552,12 +553,14 @@ __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t s) {
 // Eight lookups of one 16-entry u8 table t (4 registers, entry e in byte e)
 // for the eight 4-bit codes of w (code of vector n in bits 4n..4n+3):
 // lo = bytes T[c0..c3], hi = bytes T[c4..c7].  Two byte permutes fetch
-// T[c & 7] and T[8 + (c & 7)], a third picks per byte by bit 3 of c.
+// T[c & 7] and T[8 + (c & 7)], a third picks per byte by bit 3 of c.  A byte
+// permute reads only the low 16 bits of its selector, so both halves come
+// from one masked word and a shift.
 __device__ __forceinline__ void lut16x8(uint32_t w, const uint4& t, uint32_t& lo, uint32_t& hi) {
-    const uint32_t wh = w >> 16;
-    const uint32_t s0 = w & 0x7777u, s1 = wh & 0x7777u;
-    const uint32_t k0 = ((w >> 1) & 0x4444u) | 0x3210u;
-    const uint32_t k1 = ((wh >> 1) & 0x4444u) | 0x3210u;
+    const uint32_t s0 = w & 0x77777777u;                            // entry index within a half
+    const uint32_t s1 = s0 >> 16;
+    const uint32_t k0 = ((w >> 1) & 0x44444444u) | 0x32103210u;     // byte n of a (n) or of b (4 + n)
+    const uint32_t k1 = k0 >> 16;
     lo = prmt(prmt(t.x, t.y, s0), prmt(t.z, t.w, s0), k0);
     hi = prmt(prmt(t.x, t.y, s1), prmt(t.z, t.w, s1), k1);
 }
@@ -574,6 +577,24 @@ __device__ __forceinline__ void accum_chunk(const uint4& c, const uint4& t, uint
         acc[4 * k + 1] += prmt(lo, 0u, 0x4342u);
         acc[4 * k + 2] += prmt(hi, 0u, 0x4140u);
         acc[4 * k + 3] += prmt(hi, 0u, 0x4342u);
+    }
+}
+
+// Two subspaces at once: each lane sum takes both widened lookups in one
+// three-input add.
+__device__ __forceinline__ void accum_pair(const uint4& c0, const uint4& t0, const uint4& c1, const uint4& t1,
+                                           uint32_t (&acc)[16]) {
+    const uint32_t w0[4] = {c0.x, c0.y, c0.z, c0.w};
+    const uint32_t w1[4] = {c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        uint32_t lo0, hi0, lo1, hi1;
+        lut16x8(w0[k], t0, lo0, hi0);
+        lut16x8(w1[k], t1, lo1, hi1);
+        acc[4 * k + 0] += prmt(lo0, 0u, 0x4140u) + prmt(lo1, 0u, 0x4140u);
+        acc[4 * k + 1] += prmt(lo0, 0u, 0x4342u) + prmt(lo1, 0u, 0x4342u);
+        acc[4 * k + 2] += prmt(hi0, 0u, 0x4140u) + prmt(hi1, 0u, 0x4140u);
+        acc[4 * k + 3] += prmt(hi0, 0u, 0x4342u) + prmt(hi1, 0u, 0x4342u);
     }
 }
 
@@ -621,89 +642,197 @@ struct ScanOut {
     int cap;
 };
 
-// Persistent, cluster-major scan.  A warp takes one item = (list p, group of
-// QG = 32/G queries that probe p, tile of TB blocks); group lane g of query
-// slot s holds the sub-LUTs of subspaces j = g + G*u, u < SMAX, in registers.
+// Persistent, cluster-major scan with shared-memory staging of the codes.
+// A warp takes one item = (list p, group of QG = 32/G queries that probe p,
+// tile of at most TB blocks of p) and walks the tile in chunks of
+// SCAN_CHUNK blocks.  Lane 0 bulk-copies each chunk's codes (contiguous in
+// global memory) into the warp's own shared-memory buffer with cp.async.bulk,
+// completing the warp's mbarrier; two buffers alternate so that the next
+// chunk -- of this item or of the warp's next item -- is in flight while the
+// current one is scanned.  Group lane g of query slot s holds the sub-LUTs of
+// subspaces j = g + G*u (u < SMAX) in registers.  A key is formed only for a
+// vector whose distance reaches its query's threshold, so ids are read from
+// global memory only for those.  No CTA-wide barrier: warps run independently.
+constexpr int SCAN_WARPS = 8;
+constexpr int SCAN_CHUNK_BYTES = 4096;           // per buffer, per warp
+constexpr uint32_t SCAN_WAIT_LIMIT = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Poll an mbarrier phase at most SCAN_WAIT_LIMIT times; false if it never completed.
+__device__ __forceinline__ bool scan_wait(uint32_t bar, uint32_t parity) {
+    for (uint32_t i = 0; i < SCAN_WAIT_LIMIT; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+struct ScanItem {
+    int p, b0, b1;
+    int64_t g0, npairs;
+};
+
+__device__ __forceinline__ ScanItem locate_item(const ScanArgs& A, const int64_t* __restrict__ pair_off,
+                                                const int64_t* __restrict__ item_off, int L, int TB, int QG,
+                                                int64_t it) {
+    int lo = 0, hi = L - 1;  // last list p with item_off[p] <= it
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (item_off[mid] <= it) lo = mid; else hi = mid - 1;
+    }
+    ScanItem r;
+    r.p = lo;
+    const int nb = (A.list_n[lo] + 31) >> 5;
+    const int nt = (nb + TB - 1) / TB;
+    const int64_t local = it - item_off[lo];
+    const int64_t grp = local / nt;
+    const int tile = (int)(local - grp * nt);
+    r.b0 = tile * TB;
+    r.b1 = min(nb, r.b0 + TB);
+    r.g0 = pair_off[lo] + grp * QG;
+    r.npairs = pair_off[lo + 1] - r.g0;
+    return r;
+}
+
+// The chunk stream of one warp: items it0, it0 + stride, ...; each item's
+// blocks [b0, b1) in chunks of cb blocks.
+struct ChunkCursor {
+    int64_t it;
+    int c;  // chunk index within the item
+};
+
 template <int G, int SMAX>
-__global__ void __launch_bounds__(128) k_scan(ScanArgs A, ScanOut O, const int64_t* __restrict__ pair_off,
-                                              const int64_t* __restrict__ item_off, const uint32_t* __restrict__ pairs,
-                                              int L, int TB) {
+__global__ void __launch_bounds__(SCAN_WARPS * 32, (SMAX <= 4 ? 3 : (SMAX <= 8 ? 2 : 1))) k_scan(ScanArgs A, ScanOut O, const int64_t* __restrict__ pair_off,
+                                                          const int64_t* __restrict__ item_off,
+                                                          const uint32_t* __restrict__ pairs, int L, int TB,
+                                                          int32_t* __restrict__ status) {
     constexpr int QG = 32 / G;
     constexpr int V = 32 / G;
-    const int lane = threadIdx.x & 31;
+    extern __shared__ __align__(128) uint8_t bufs[];  // SCAN_WARPS x 2 x SCAN_CHUNK_BYTES
+    __shared__ __align__(8) uint64_t full[SCAN_WARPS][2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int slot = lane / G, g = lane % G;
-    const int64_t total = item_off[L];
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int M = A.M;
     const int S = (M + G - 1) / G;
-    for (int64_t it = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < total; it += warps) {
-        // locate the list: last p with item_off[p] <= it
-        int lo = 0, hi = L - 1;
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (item_off[mid] <= it) lo = mid; else hi = mid - 1;
-        }
-        const int p = lo;
-        const int nb = (A.list_n[p] + 31) >> 5;
-        const int nt = (nb + TB - 1) / TB;
-        const int64_t local = it - item_off[p];
-        const int64_t grp = local / nt;
-        const int tile = (int)(local - grp * nt);
-        const int64_t npairs = pair_off[p + 1] - pair_off[p];
-        const int64_t pi = grp * QG + slot;
-        const bool active = pi < npairs;
-        int64_t q = 0, li = 0;
+    const int blk_bytes = M * 16;
+    const int cb = SCAN_CHUNK_BYTES / blk_bytes;  // blocks per chunk (>= 1)
+    const int64_t total = item_off[L];
+    const int64_t stride = (int64_t)gridDim.x * SCAN_WARPS;
+    uint8_t* mybuf = bufs + (size_t)warp * 2 * SCAN_CHUNK_BYTES;
+    const uint32_t bar0 = smem_addr(&full[warp][0]), bar1 = smem_addr(&full[warp][1]);
+    if (lane == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    // lane 0: bulk copy of chunk (x, c) into buffer b
+    auto issue = [&](const ScanItem& x, int c, int b) {
+        const int c0 = x.b0 + c * cb, c1 = min(x.b1, c0 + cb);
+        const uint32_t bytes = (uint32_t)(c1 - c0) * blk_bytes;
+        const uint32_t bar = b ? bar1 : bar0;
+        const uint8_t* src = A.codes + (A.boff[x.p] + c0) * (int64_t)blk_bytes;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         smem_addr(mybuf + b * SCAN_CHUNK_BYTES)),
+                     "l"(src), "r"(bytes), "r"(bar)
+                     : "memory");
+    };
+    int64_t it = (int64_t)blockIdx.x * SCAN_WARPS + warp;
+    if (it >= total) return;
+    ScanItem x = locate_item(A, pair_off, item_off, L, TB, QG, it);
+    if (lane == 0) issue(x, 0, 0);
+    uint32_t phase[2] = {0u, 0u};
+    int b = 0;
+    bool failed = false;
+    while (true) {
+        // item set-up: LUTs, bias and threshold of this lane group's query
+        const int64_t pi = slot;
+        const bool active = pi < x.npairs;
+        int64_t q = 0;
         uint4 t[SMAX];
-        int32_t b = 0;
-        uint64_t th = 0;
+        int32_t bias = 0;
+        uint32_t thD = 0, thI = 0;
         if (active) {
-            uint32_t e = pairs[pair_off[p] + pi];
+            const uint32_t e = pairs[x.g0 + pi];
             q = e / A.Pmax;
-            li = e;
-            const uint4* lp = reinterpret_cast<const uint4*>(A.lut + li * (int64_t)M * PQ_K);
+            const uint4* lp = reinterpret_cast<const uint4*>(A.lut + (int64_t)e * M * PQ_K);
 #pragma unroll
             for (int u = 0; u < SMAX; ++u) {
                 const int j = g + G * u;
                 t[u] = (u < S && j < M) ? __ldg(lp + j) : make_uint4(0, 0, 0, 0);
             }
-            b = A.bias[li];
-            th = O.thr[q];
+            bias = A.bias[e];
+            const uint64_t th = O.thr[q];
+            thD = (uint32_t)(th >> 32);
+            thI = (uint32_t)th;
         } else {
 #pragma unroll
             for (int u = 0; u < SMAX; ++u) t[u] = make_uint4(0, 0, 0, 0);
         }
-        const int b0 = tile * TB, b1 = min(nb, b0 + TB);
-        for (int blk = b0; blk < b1; ++blk) {
-            const int64_t gb = A.boff[p] + blk;
-            const uint4* cp = reinterpret_cast<const uint4*>(A.codes + gb * M * 16);
-            uint32_t acc[16];
-#pragma unroll
-            for (int m = 0; m < 16; ++m) acc[m] = 0;
-#pragma unroll
-            for (int u = 0; u < SMAX; ++u) {
-                const int j = g + G * u;
-                if (u < S && j < M) {
-                    uint4 c = __ldg(cp + j);
-                    accum_chunk(c, t[u], acc);
-                }
+        const int nch = (x.b1 - x.b0 + cb - 1) / cb;
+        const int64_t next_it = it + stride;
+        for (int c = 0; c < nch; ++c) {
+            // prefetch the chunk after this one into the other buffer
+            if (lane == 0) {
+                if (c + 1 < nch) issue(x, c + 1, b ^ 1);
+                else if (next_it < total) issue(locate_item(A, pair_off, item_off, L, TB, QG, next_it), 0, b ^ 1);
             }
-            uint32_t sums[V];
-            reduce_scatter<G>(acc, lane, sums);
-            if (active) {
+            const bool ready = !failed && scan_wait(b ? bar1 : bar0, phase[b]);
+            phase[b] ^= 1u;
+            if (!ready) {
+                if (lane == 0 && !failed) atomicOr(status, 4);  // a chunk never arrived: the warp stops
+                failed = true;
+            } else {
+                const uint8_t* chunk = mybuf + b * SCAN_CHUNK_BYTES;
+                const int c0 = x.b0 + c * cb, nblk = min(x.b1, c0 + cb) - c0;
+                const int64_t gb0 = A.boff[x.p] + c0;
+                for (int blk = 0; blk < nblk; ++blk) {
+                    const uint4* cp = reinterpret_cast<const uint4*>(chunk + blk * blk_bytes);
+                    uint32_t acc[16];
 #pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    const int vi = V * g + v;
-                    const int32_t id = A.ids[gb * 32 + vi];
-                    if (id >= 0) {
-                        const uint64_t key = make_key(b + (int32_t)sums[v], id);
-                        if (key <= th) {
-                            int s = atomicAdd(&O.cnt[q], 1);
-                            if (s < O.cap) O.cand[q * O.cap + s] = key;
+                    for (int m = 0; m < 16; ++m) acc[m] = 0;
+#pragma unroll
+                    for (int u = 0; u + 1 < SMAX; u += 2) {
+                        const int j = g + G * u;
+                        if (u + 1 < S && j + G < M) accum_pair(cp[j], t[u], cp[j + G], t[u + 1], acc);
+                        else if (u < S && j < M) accum_chunk(cp[j], t[u], acc);
+                    }
+                    if (SMAX & 1) {
+                        const int u = SMAX - 1, j = g + G * u;
+                        if (u < S && j < M) accum_chunk(cp[j], t[u], acc);
+                    }
+                    uint32_t sums[V];
+                    reduce_scatter<G>(acc, lane, sums);
+                    if (active) {
+#pragma unroll
+                        for (int v = 0; v < V; ++v) {
+                            // high word of the key: (D + 2^31) as an unsigned integer
+                            const uint32_t Dk = (uint32_t)(bias + (int32_t)sums[v]) ^ 0x80000000u;
+                            if (Dk <= thD) {
+                                const int32_t id = A.ids[(gb0 + blk) * 32 + V * g + v];
+                                if (id >= 0 && (Dk < thD || (uint32_t)id <= thI)) {
+                                    const int sl = atomicAdd(&O.cnt[q], 1);
+                                    if (sl < O.cap) O.cand[q * O.cap + sl] = ((uint64_t)Dk << 32) | (uint32_t)id;
+                                }
+                            }
                         }
                     }
                 }
             }
+            __syncwarp();  // the whole warp is done with buffer b before lane 0 refills it
+            b ^= 1;
         }
+        if (next_it >= total || failed) break;
+        it = next_it;
+        x = locate_item(A, pair_off, item_off, L, TB, QG, it);
     }
 }
 
@@ -715,9 +844,11 @@ __global__ void __launch_bounds__(128) k_lut16_peak(int iters, uint32_t seed, ui
 #pragma unroll
     for (int m = 0; m < 16; ++m) acc[m] = 0;
     uint32_t w = seed ^ (blockIdx.x * blockDim.x + threadIdx.x);
-    for (int i = 0; i < iters; ++i) {
+    const uint4 t2 = make_uint4(t.y, t.z, t.w, t.x);
+    for (int i = 0; i < iters; i += 2) {
         uint4 c = make_uint4(w, w ^ 0x5a5a5a5au, w + 0x01234567u, w ^ 0xf0f0f0f0u);
-        accum_chunk(c, t, acc);
+        uint4 c2 = make_uint4(w ^ 0x0f0f0f0fu, w + 0x89abcdefu, w ^ 0x33333333u, w + 0x13579bdfu);
+        accum_pair(c, t, c2, t2, acc);
         w = w * 1664525u + 1013904223u;
     }
     uint32_t s = 0;
@@ -898,24 +1029,28 @@ static int choose_G(const ksc_index* ix, int64_t nq, int Pmax, int want) {
 }
 
 template <int G, int SMAX>
-static void launch_scan(const ScanArgs& A, const ScanOut& O, const int64_t* pair_off, const int64_t* item_off,
-                        const uint32_t* pairs, int L, int TB, cudaStream_t st) {
-    int grid = num_sms() * 8;
-    k_scan<G, SMAX><<<grid, 128, 0, st>>>(A, O, pair_off, item_off, pairs, L, TB);
+static int launch_scan(const ScanArgs& A, const ScanOut& O, const int64_t* pair_off, const int64_t* item_off,
+                       const uint32_t* pairs, int L, int TB, int32_t* status, cudaStream_t st) {
+    const size_t smem = (size_t)SCAN_WARPS * 2 * SCAN_CHUNK_BYTES;
+    KSC_CUDA(cudaFuncSetAttribute(k_scan<G, SMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    KSC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scan<G, SMAX>, SCAN_WARPS * 32, smem));
+    const int grid = num_sms() * (per_sm > 0 ? per_sm : 1);
+    k_scan<G, SMAX><<<grid, SCAN_WARPS * 32, smem, st>>>(A, O, pair_off, item_off, pairs, L, TB, status);
+    KSC_LAUNCH_CHECK();
+    return KSC_OK;
 }
 
 template <int G>
 static int dispatch_scan(int S, const ScanArgs& A, const ScanOut& O, const int64_t* pair_off,
-                         const int64_t* item_off, const uint32_t* pairs, int L, int TB, cudaStream_t st) {
-    if (S <= 2) launch_scan<G, 2>(A, O, pair_off, item_off, pairs, L, TB, st);
-    else if (S <= 4) launch_scan<G, 4>(A, O, pair_off, item_off, pairs, L, TB, st);
-    else if (S <= 8) launch_scan<G, 8>(A, O, pair_off, item_off, pairs, L, TB, st);
-    else if (S <= 16) launch_scan<G, 16>(A, O, pair_off, item_off, pairs, L, TB, st);
-    else {
-        set_error("M too large for %d lanes per query", G);
-        return KSC_EINVAL;
-    }
-    return KSC_OK;
+                         const int64_t* item_off, const uint32_t* pairs, int L, int TB, int32_t* status,
+                         cudaStream_t st) {
+    if (S <= 2) return launch_scan<G, 2>(A, O, pair_off, item_off, pairs, L, TB, status, st);
+    if (S <= 4) return launch_scan<G, 4>(A, O, pair_off, item_off, pairs, L, TB, status, st);
+    if (S <= 8) return launch_scan<G, 8>(A, O, pair_off, item_off, pairs, L, TB, status, st);
+    if (S <= 16) return launch_scan<G, 16>(A, O, pair_off, item_off, pairs, L, TB, status, st);
+    set_error("M too large for %d lanes per query", G);
+    return KSC_EINVAL;
 }
 
 // List scores [nq x L] on the BF16 tensor cores or the FP32 CUDA cores, with
@@ -1003,7 +1138,7 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
     mark(ix, 3, st);
     // work list
     const int L = ix->L;
-    const int QG = 32 / pl.G;
+    const int QC = 32 / pl.G;  // queries per scan item (one warp)
     const int TB = pl.TB;
     KSC_TRY(ensure(ix->ws_items, sizeof(int64_t) * 2 * (L + 1) + sizeof(int32_t) * 2 * L +
                                      sizeof(uint32_t) * nq * pl.Pmax + 64, st));
@@ -1015,7 +1150,7 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
     uint32_t* pairs = (uint32_t*)(fill + L);
     KSC_CUDA(cudaMemsetAsync(lcnt, 0, sizeof(int32_t) * L, st));
     k_count_pairs<<<blocks_for(nq * pl.Pmax, 256), 256, 0, st>>>(A, lcnt);
-    k_scan_lists<<<1, 1024, 0, st>>>(lcnt, ix->list_n, L, QG, TB, pair_off, item_off, fill);
+    k_scan_lists<<<1, 1024, 0, st>>>(lcnt, ix->list_n, L, QC, TB, pair_off, item_off, fill);
     k_fill_pairs<<<blocks_for(nq * pl.Pmax, 256), 256, 0, st>>>(A, pair_off, fill, pairs);
     ix->launches += 3;
     KSC_LAUNCH_CHECK();
@@ -1029,11 +1164,10 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
     ScanOut O{thr, cnt, cand, pl.cap};
     const int S = (M + pl.G - 1) / pl.G;
     int rc;
-    if (pl.G == 8) rc = dispatch_scan<8>(S, A, O, pair_off, item_off, pairs, L, TB, st);
-    else if (pl.G == 16) rc = dispatch_scan<16>(S, A, O, pair_off, item_off, pairs, L, TB, st);
-    else rc = dispatch_scan<32>(S, A, O, pair_off, item_off, pairs, L, TB, st);
+    if (pl.G == 8) rc = dispatch_scan<8>(S, A, O, pair_off, item_off, pairs, L, TB, ix->status, st);
+    else if (pl.G == 16) rc = dispatch_scan<16>(S, A, O, pair_off, item_off, pairs, L, TB, ix->status, st);
+    else rc = dispatch_scan<32>(S, A, O, pair_off, item_off, pairs, L, TB, ix->status, st);
     KSC_TRY(rc);
-    KSC_LAUNCH_CHECK();
     ix->launches++;
     mark(ix, 5, st);
     // select
@@ -1083,12 +1217,13 @@ static int make_plan(ksc_index* ix, int64_t nq, int k, int Pmax, int Rmax, const
     pl.rerank_q = nullptr;
     pl.G = choose_G(ix, nq, Pmax, opts ? opts->lanes_per_query : 0);
     {
-        // tile length: enough warp items to fill the GPU, at most 64 blocks
+        // tile length: enough warp items to fill the GPU (about 64 per SM), at
+        // most 64 blocks
         const int QG = 32 / pl.G;
-        const double blocks = (double)nq * Pmax * ((double)ix->nblocks / ix->L) / QG;
-        const double target = 32.0 * num_sms();
+        const double blocks = std::ceil((double)nq * Pmax / ix->L / QG) * ix->nblocks;
+        const double target = 64.0 * num_sms();
         int TB = (int)(blocks / target);
-        pl.TB = TB < 4 ? 4 : (TB > 64 ? 64 : TB);
+        pl.TB = TB < 2 ? 2 : (TB > 64 ? 64 : TB);
     }
     int cap = (opts && opts->cand_cap > 0) ? opts->cand_cap : std::max(16 * Rmax, 4096);
     pl.cap = std::max(cap, Rmax);
@@ -1303,3 +1438,299 @@ extern "C" int ksc_compute_luts_noalloc(ksc_index* ix, const float* Q_dev, int64
               ix->codebook, ix->L};
     return launch_luts(A, rb, lut_dev, bias_dev, scale_dev, st);
 }
+
+// ------------------------------------------------------------------ learned nprobe / rerank
+namespace ksc {
+static const int32_t DEF_GRID[] = {4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128};
+static const int32_t DEF_RGRID[] = {20, 50, 100, 200, 400};
+
+// Rank with P probes (P >= 32) and derive the predictor features.
+static int rank_and_features(ksc_index* ix, const float* Q, int64_t nq, int P, int32_t* probes, float* feats,
+                             cudaStream_t st) {
+    KSC_TRY(ensure(ix->ws_rscore, sizeof(float) * nq * P, st));
+    float* rs = (float*)ix->ws_rscore.p;
+    KSC_TRY(rank_lists(ix, Q, nq, nullptr, P, P, probes, rs, false, st));
+    KSC_TRY(mlp_features(rs, nq, P, ix->spherical, feats, st));
+    ix->launches++;
+    return KSC_OK;
+}
+
+static uint64_t mix64(uint64_t& s) {  // splitmix64 (Steele, Lea, Flood 2014)
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+static float median_of(std::vector<int32_t> v) {
+    if (v.empty()) return 0.f;
+    std::nth_element(v.begin(), v.begin() + v.size() / 2, v.end());
+    return (float)v[v.size() / 2];
+}
+
+// Smallest grid value per query whose search finds >= target hits; queries
+// that never reach it take the last grid value.
+static int label_queries(ksc_index* ix, const float* Q, int64_t nq, const float* kth, const int32_t* probes, int Pr,
+                         const std::vector<int32_t>& grid, bool over_rerank, const int32_t* nprobe_dev, int R_fixed,
+                         int k, int target, std::vector<int32_t>& label, cudaStream_t st) {
+    std::vector<int32_t> hits_h(nq);
+    int32_t* hits = nullptr;
+    int64_t* ids = nullptr;
+    float* dists = nullptr;
+    int32_t* cnst = nullptr;
+    int rc = KSC_OK;
+    label.assign(nq, -1);
+    do {
+        if (cudaMalloc(&hits, sizeof(int32_t) * nq) != cudaSuccess || cudaMalloc(&ids, sizeof(int64_t) * nq * k) != cudaSuccess ||
+            cudaMalloc(&dists, sizeof(float) * nq * k) != cudaSuccess || cudaMalloc(&cnst, sizeof(int32_t) * nq) != cudaSuccess) {
+            set_error("allocation failed while labelling");
+            rc = KSC_ENOMEM;
+            break;
+        }
+        for (int32_t gv : grid) {
+            Plan pl;
+            const int Rmax = over_rerank ? gv : R_fixed;
+            if ((rc = make_plan(ix, nq, k, Pr, Rmax, nullptr, pl))) break;
+            if (over_rerank) {
+                pl.nprobe_q = nprobe_dev;
+            } else {
+                std::vector<int32_t> c(nq, gv);
+                if (cudaMemcpy(cnst, c.data(), sizeof(int32_t) * nq, cudaMemcpyHostToDevice) != cudaSuccess) {
+                    rc = KSC_ECUDA;
+                    break;
+                }
+                pl.nprobe_q = cnst;
+            }
+            if ((rc = search_from_probes(ix, Q, pl, probes, ids, dists, nullptr, nullptr, st))) break;
+            if ((rc = mlp_hits(dists, nq, k, kth, ix->metric == KSC_IP, hits, st))) break;
+            if (cudaMemcpyAsync(hits_h.data(), hits, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess) {
+                set_error("label readback failed");
+                rc = KSC_ECUDA;
+                break;
+            }
+            for (int64_t q = 0; q < nq; ++q)
+                if (label[q] < 0 && hits_h[q] >= target) label[q] = gv;
+        }
+    } while (0);
+    for (auto& l : label)
+        if (l < 0) l = grid.back();
+    cudaFree(hits);
+    cudaFree(ids);
+    cudaFree(dists);
+    cudaFree(cnst);
+    return rc;
+}
+}  // namespace ksc
+
+extern "C" {
+
+int ksc_mlp_grad(const float* w_dev, const float* x_dev, const float* y_dev, int64_t B, float* grad_dev,
+                 float* loss_dev, void* stream) {
+    KSC_CHECK_ARG(w_dev && x_dev && y_dev && grad_dev && B > 0, "bad argument");
+    return mlp_grad(w_dev, x_dev, y_dev, B, grad_dev, loss_dev, as_stream(stream));
+}
+
+int ksc_mlp_forward(const float* w_dev, const float* x_dev, int64_t B, float* prob_dev, void* stream) {
+    KSC_CHECK_ARG(w_dev && x_dev && prob_dev && B > 0, "bad argument");
+    ksc_adaptive_params prm = {1, 1, 1, 1, 0.f, 0.f, 0.f, 0.f};
+    return mlp_infer(w_dev, x_dev, B, prm, prob_dev, nullptr, nullptr, as_stream(stream));
+}
+
+int ksc_query_features(ksc_index* ix, const float* Q_dev, int64_t nq, float* feats_dev, void* stream) {
+    KSC_CHECK_ARG(ix, "null index");
+    KSC_CHECK_ARG(ix->L >= 32, "the predictor needs at least 32 lists");
+    if (nq == 0) return KSC_OK;
+    KSC_CHECK_ARG(Q_dev && feats_dev, "null argument");
+    cudaStream_t st = as_stream(stream);
+    KSC_TRY(ensure(ix->ws_probes, sizeof(int32_t) * nq * 32, st));
+    return rank_and_features(ix, Q_dev, nq, 32, (int32_t*)ix->ws_probes.p, feats_dev, st);
+}
+
+int ksc_predictor_params(ksc_index* ix, const ksc_adaptive_params* prm) {
+    KSC_CHECK_ARG(ix && prm, "null argument");
+    KSC_CHECK_ARG(prm->pmin >= 1 && prm->pmin <= prm->pmax && prm->pmax <= ix->L && prm->pmax <= MAX_NPROBE,
+                  "nprobe range must satisfy 1 <= pmin <= pmax <= min(nlist, %d)", MAX_NPROBE);
+    KSC_CHECK_ARG(prm->rmin >= 1 && prm->rmin <= prm->rmax && prm->rmax <= KSC_MAX_RERANK, "bad rerank range");
+    ix->mlp_prm = *prm;
+    return KSC_OK;
+}
+
+int ksc_predictor_weights(ksc_index* ix, float* w_host, const float* w_in_host) {
+    KSC_CHECK_ARG(ix && (w_host || w_in_host), "null argument");
+    if (w_in_host) {
+        if (!ix->mlp_w) KSC_CUDA(cudaMalloc(&ix->mlp_w, sizeof(float) * KSC_MLP_NPARAMS));
+        KSC_CUDA(cudaMemcpy(ix->mlp_w, w_in_host, sizeof(float) * KSC_MLP_NPARAMS, cudaMemcpyHostToDevice));
+        if (ix->mlp_prm.pmax == 0) {
+            ix->mlp_prm = {DEF_GRID[0], std::min(DEF_GRID[10], ix->L), DEF_RGRID[0], DEF_RGRID[4], 0.3f, 0.5f,
+                           0.3f, 0.5f};
+            if (ix->mlp_prm.pmin > ix->mlp_prm.pmax) ix->mlp_prm.pmin = ix->mlp_prm.pmax;
+        }
+    }
+    if (w_host) {
+        if (!ix->mlp_w) {
+            set_error("no predictor has been trained or loaded");
+            return KSC_ESTATE;
+        }
+        KSC_CUDA(cudaMemcpy(w_host, ix->mlp_w, sizeof(float) * KSC_MLP_NPARAMS, cudaMemcpyDeviceToHost));
+    }
+    return KSC_OK;
+}
+
+int ksc_train_predictor(ksc_index* ix, const float* Qtrain_dev, int64_t nt, const float* kth_dev,
+                        const ksc_train_opts* opts, void* stream, float* loss_host) {
+    KSC_CHECK_ARG(ix && Qtrain_dev && kth_dev && nt > 0, "bad argument");
+    KSC_CHECK_ARG(ix->L >= 32, "the predictor needs at least 32 lists");
+    cudaStream_t st = as_stream(stream);
+    const int k = (opts && opts->k > 0) ? opts->k : 10;
+    const int target = (opts && opts->target_hits > 0) ? opts->target_hits : 9;
+    const int R_lab = (opts && opts->rerank_label > 0) ? opts->rerank_label : 200;
+    const int epochs = (opts && opts->epochs > 0) ? opts->epochs : 8;
+    const int batch = (opts && opts->batch > 0) ? opts->batch : 256;
+    const float lr = (opts && opts->lr > 0.f) ? opts->lr : 1e-3f;
+    uint64_t seed = (opts && opts->seed) ? opts->seed : 0x6d6c70ull;
+    std::vector<int32_t> grid, rgrid;
+    if (opts && opts->grid_host && opts->ngrid > 0) grid.assign(opts->grid_host, opts->grid_host + opts->ngrid);
+    else grid.assign(DEF_GRID, DEF_GRID + 11);
+    if (opts && opts->rgrid_host && opts->nrgrid > 0) rgrid.assign(opts->rgrid_host, opts->rgrid_host + opts->nrgrid);
+    else rgrid.assign(DEF_RGRID, DEF_RGRID + 5);
+    while (!grid.empty() && grid.back() > ix->L) grid.pop_back();
+    KSC_CHECK_ARG(!grid.empty() && !rgrid.empty(), "empty grid");
+    KSC_CHECK_ARG(rgrid.back() <= KSC_MAX_RERANK && R_lab >= k, "bad rerank grid");
+    const int Pr = std::min(std::max(grid.back(), 32), ix->L);
+    const int64_t chunk = 8192;
+    float* feats = nullptr;
+    float* Y = nullptr;
+    int32_t* probes = nullptr;
+    int32_t* lab_dev = nullptr;
+    float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr, *xb = nullptr, *yb = nullptr, *lossd = nullptr;
+    int64_t* idx = nullptr;
+    std::vector<int32_t> lab_n(nt), lab_r(nt);
+    int rc = KSC_OK;
+    const int steps = (int)((nt + batch - 1) / batch);
+#define T_CUDA(call) { cudaError_t e_ = (call); if (e_ != cudaSuccess) { set_error("%s: %s", #call, cudaGetErrorString(e_)); rc = KSC_ECUDA; break; } }
+    do {
+        T_CUDA(cudaMalloc(&feats, sizeof(float) * nt * KSC_MLP_FEATURES));
+        T_CUDA(cudaMalloc(&Y, sizeof(float) * nt * 2));
+        T_CUDA(cudaMalloc(&probes, sizeof(int32_t) * chunk * Pr));
+        T_CUDA(cudaMalloc(&lab_dev, sizeof(int32_t) * chunk));
+        // 1. labels from the plain search, chunk by chunk
+        for (int64_t c0 = 0; c0 < nt && rc == KSC_OK; c0 += chunk) {
+            const int64_t nc = std::min(chunk, nt - c0);
+            const float* Qc = Qtrain_dev + c0 * ix->d;
+            if ((rc = rank_and_features(ix, Qc, nc, Pr, probes, feats + c0 * KSC_MLP_FEATURES, st))) break;
+            std::vector<int32_t> ln, lr_;
+            if ((rc = label_queries(ix, Qc, nc, kth_dev + c0, probes, Pr, grid, false, nullptr, R_lab, k, target, ln,
+                                    st)))
+                break;
+            T_CUDA(cudaMemcpy(lab_dev, ln.data(), sizeof(int32_t) * nc, cudaMemcpyHostToDevice));
+            if ((rc = label_queries(ix, Qc, nc, kth_dev + c0, probes, Pr, rgrid, true, lab_dev, 0, k, target, lr_,
+                                    st)))
+                break;
+            std::copy(ln.begin(), ln.end(), lab_n.begin() + c0);
+            std::copy(lr_.begin(), lr_.end(), lab_r.begin() + c0);
+        }
+        if (rc) break;
+        const float med_n = median_of(lab_n), med_r = median_of(lab_r);
+        std::vector<float> yh(nt * 2);
+        for (int64_t q = 0; q < nt; ++q) {
+            yh[2 * q] = lab_n[q] > med_n ? 1.f : 0.f;
+            yh[2 * q + 1] = lab_r[q] > med_r ? 1.f : 0.f;
+        }
+        T_CUDA(cudaMemcpy(Y, yh.data(), sizeof(float) * nt * 2, cudaMemcpyHostToDevice));
+        // 2. weights: He-uniform from the seed, zero biases
+        std::vector<float> wh(KSC_MLP_NPARAMS, 0.f);
+        const int fan[3] = {KSC_MLP_FEATURES, 64, 64}, rows[3] = {64, 64, 2};
+        int off = 0;
+        for (int l = 0; l < 3; ++l) {
+            const float a = sqrtf(6.f / fan[l]);
+            for (int e = 0; e < rows[l] * fan[l]; ++e)
+                wh[off + e] = a * (2.f * (float)((mix64(seed) >> 11) * (1.0 / 9007199254740992.0)) - 1.f);
+            off += rows[l] * fan[l] + rows[l];
+        }
+        T_CUDA(cudaMalloc(&w, sizeof(float) * KSC_MLP_NPARAMS));
+        T_CUDA(cudaMalloc(&g, sizeof(float) * KSC_MLP_NPARAMS));
+        T_CUDA(cudaMalloc(&m, sizeof(float) * KSC_MLP_NPARAMS));
+        T_CUDA(cudaMalloc(&v, sizeof(float) * KSC_MLP_NPARAMS));
+        T_CUDA(cudaMalloc(&xb, sizeof(float) * batch * KSC_MLP_FEATURES));
+        T_CUDA(cudaMalloc(&yb, sizeof(float) * batch * 2));
+        T_CUDA(cudaMalloc(&idx, sizeof(int64_t) * nt));
+        T_CUDA(cudaMalloc(&lossd, sizeof(float) * steps));
+        T_CUDA(cudaMemcpy(w, wh.data(), sizeof(float) * KSC_MLP_NPARAMS, cudaMemcpyHostToDevice));
+        T_CUDA(cudaMemset(m, 0, sizeof(float) * KSC_MLP_NPARAMS));
+        T_CUDA(cudaMemset(v, 0, sizeof(float) * KSC_MLP_NPARAMS));
+        // 3. Adam over shuffled minibatches
+        std::vector<int64_t> perm(nt);
+        int t = 0;
+        for (int ep = 0; ep < epochs && rc == KSC_OK; ++ep) {
+            for (int64_t i = 0; i < nt; ++i) perm[i] = i;
+            for (int64_t i = nt - 1; i > 0; --i) std::swap(perm[i], perm[(int64_t)(mix64(seed) % (uint64_t)(i + 1))]);
+            T_CUDA(cudaMemcpyAsync(idx, perm.data(), sizeof(int64_t) * nt, cudaMemcpyHostToDevice, st));
+            for (int s_ = 0; s_ < steps; ++s_) {
+                const int64_t b0 = (int64_t)s_ * batch, nb = std::min<int64_t>(batch, nt - b0);
+                k_gather_rows<<<(unsigned)((nb * KSC_MLP_FEATURES + 255) / 256), 256, 0, st>>>(feats, idx + b0, nb,
+                                                                                             KSC_MLP_FEATURES, xb);
+                k_gather_rows<<<(unsigned)((nb * 2 + 255) / 256), 256, 0, st>>>(Y, idx + b0, nb, 2, yb);
+                if ((rc = mlp_grad(w, xb, yb, nb, g, lossd + s_, st))) break;
+                if ((rc = mlp_adam(w, g, m, v, ++t, lr, st))) break;
+            }
+            T_CUDA(cudaStreamSynchronize(st));  // perm is reused by the next epoch
+        }
+        if (rc) break;
+        if (loss_host) {
+            std::vector<float> lh(steps);
+            T_CUDA(cudaMemcpy(lh.data(), lossd, sizeof(float) * steps, cudaMemcpyDeviceToHost));
+            double sum = 0.0;
+            for (float x : lh) sum += x;
+            *loss_host = (float)(sum / steps);
+        }
+        if (ix->mlp_w) cudaFree(ix->mlp_w);
+        ix->mlp_w = w;
+        w = nullptr;
+        ix->mlp_prm = {grid.front(), grid.back(), rgrid.front(), rgrid.back(), 0.3f, 0.5f, 0.3f, 0.5f};
+    } while (0);
+#undef T_CUDA
+    cudaFree(feats); cudaFree(Y); cudaFree(probes); cudaFree(lab_dev); cudaFree(w); cudaFree(g); cudaFree(m);
+    cudaFree(v); cudaFree(xb); cudaFree(yb); cudaFree(idx); cudaFree(lossd);
+    return rc;
+}
+
+int ksc_search_adaptive(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t k, int64_t* ids_dev,
+                        float* dists_dev, int32_t* nprobe_dev, int32_t* rerank_dev, const ksc_search_opts* opts,
+                        void* stream) {
+    KSC_CHECK_ARG(ix, "null index");
+    if (!ix->mlp_w) {
+        set_error("no predictor has been trained or loaded");
+        return KSC_ESTATE;
+    }
+    const ksc_adaptive_params& prm = ix->mlp_prm;
+    const int Pr = std::min(std::max(prm.pmax, 32), ix->L);
+    Plan pl;
+    KSC_TRY(make_plan(ix, nq, k, Pr, prm.rmax, opts, pl));
+    if (nq == 0) return KSC_OK;
+    KSC_CHECK_ARG(Q_dev && ids_dev && dists_dev, "null argument");
+    cudaStream_t st = as_stream(stream);
+    KSC_CUDA(cudaMemsetAsync(ix->status, 0, sizeof(int32_t), st));
+    KSC_CUDA(cudaMemsetAsync(ix->stats, 0, sizeof(unsigned long long) * 4, st));
+    KSC_TRY(ensure(ix->ws_probes, sizeof(int32_t) * nq * Pr, st));
+    KSC_TRY(ensure(ix->ws_feat, sizeof(float) * nq * KSC_MLP_FEATURES, st));
+    KSC_TRY(ensure(ix->ws_nprobe, sizeof(int32_t) * nq, st));
+    KSC_TRY(ensure(ix->ws_rerank, sizeof(int32_t) * nq, st));
+    int32_t* probes = (int32_t*)ix->ws_probes.p;
+    float* feats = (float*)ix->ws_feat.p;
+    int32_t* np_q = (int32_t*)ix->ws_nprobe.p;
+    int32_t* r_q = (int32_t*)ix->ws_rerank.p;
+    ix->launches = 0;
+    mark(ix, 0, st);
+    KSC_TRY(rank_and_features(ix, Q_dev, nq, Pr, probes, feats, st));
+    KSC_TRY(mlp_infer(ix->mlp_w, feats, nq, prm, nullptr, np_q, r_q, st));
+    ix->launches++;
+    pl.nprobe_q = np_q;
+    pl.rerank_q = r_q;
+    KSC_TRY(search_from_probes(ix, Q_dev, pl, probes, ids_dev, dists_dev, nullptr, nullptr, st));
+    if (nprobe_dev) KSC_CUDA(cudaMemcpyAsync(nprobe_dev, np_q, sizeof(int32_t) * nq, cudaMemcpyDeviceToDevice, st));
+    if (rerank_dev) KSC_CUDA(cudaMemcpyAsync(rerank_dev, r_q, sizeof(int32_t) * nq, cudaMemcpyDeviceToDevice, st));
+    return KSC_OK;
+}
+
+}  // extern "C"

@@ -38,6 +38,17 @@ class IndexArrays(C.Structure):
                 ("codes", C.c_void_p), ("assign", C.c_void_p), ("graph", C.c_void_p), ("entry", C.c_void_p)]
 
 
+class AdaptiveParams(C.Structure):
+    _fields_ = [("pmin", C.c_int32), ("pmax", C.c_int32), ("rmin", C.c_int32), ("rmax", C.c_int32),
+                ("p0", C.c_float), ("p1", C.c_float), ("r0", C.c_float), ("r1", C.c_float)]
+
+
+class TrainOpts(C.Structure):
+    _fields_ = [("k", C.c_int32), ("target_hits", C.c_int32), ("rerank_label", C.c_int32), ("epochs", C.c_int32),
+                ("batch", C.c_int32), ("lr", C.c_float), ("seed", C.c_uint64), ("grid_host", C.c_void_p),
+                ("ngrid", C.c_int32), ("rgrid_host", C.c_void_p), ("nrgrid", C.c_int32)]
+
+
 class SearchOpts(C.Structure):
     _fields_ = [("lanes_per_query", C.c_int32), ("hybrid", C.c_int32), ("n_near", C.c_int32),
                 ("efs", C.c_int32), ("tau", C.c_int32), ("cand_cap", C.c_int32), ("rank_fp32", C.c_int32)]
@@ -62,6 +73,13 @@ _SIGS = {
     "ksc_profile_enable": [_vp, _i32],
     "ksc_profile_read": [_vp, _vp, _i32, _vp],
     "ksc_lut16_peak": [_vp, _vp],
+    "ksc_train_predictor": [_vp, _vp, _i64, _vp, _vp, _vp, _vp],
+    "ksc_predictor_params": [_vp, _vp],
+    "ksc_predictor_weights": [_vp, _vp, _vp],
+    "ksc_search_adaptive": [_vp, _vp, _i64, _i32, _vp, _vp, _vp, _vp, _vp, _vp],
+    "ksc_query_features": [_vp, _vp, _i64, _vp, _vp],
+    "ksc_mlp_grad": [_vp, _vp, _vp, _i64, _vp, _vp, _vp],
+    "ksc_mlp_forward": [_vp, _vp, _i64, _vp, _vp],
     "ksc_last_error": [],
     "ksc_version": [],
 }
@@ -231,6 +249,53 @@ class Index:
                                       _dptr(probes, torch.int32, "probes"), P, _dptr(lut), _dptr(bias),
                                       _dptr(scale), _stream(stream)))
         return lut, bias, scale
+
+    # ---------------------------------------------------------- learned predictor
+    def train_predictor(self, Qtrain, kth, k=10, target_hits=9, rerank_label=200, epochs=8, batch=256, lr=1e-3,
+                        seed=0, grid=None, rgrid=None, stream=None):
+        """Train the nprobe / rerank MLP on training queries and their true
+        k-th neighbour distances (device tensors).  Returns the mean loss of
+        the last epoch."""
+        torch = _torch()
+        g = None if grid is None else np.ascontiguousarray(grid, dtype=np.int32)
+        r = None if rgrid is None else np.ascontiguousarray(rgrid, dtype=np.int32)
+        opts = TrainOpts(k, target_hits, rerank_label, epochs, batch, lr, seed, _hptr(g),
+                         0 if g is None else len(g), _hptr(r), 0 if r is None else len(r))
+        loss = C.c_float(0)
+        _check(lib().ksc_train_predictor(self._h, _dptr(Qtrain, torch.float32, "Qtrain"), Qtrain.shape[0],
+                                         _dptr(kth, torch.float32, "kth"), C.byref(opts), _stream(stream),
+                                         C.byref(loss)))
+        return loss.value
+
+    def set_predictor_params(self, pmin, pmax, rmin, rmax, p0, p1, r0, r1):
+        _check(lib().ksc_predictor_params(self._h, C.byref(AdaptiveParams(pmin, pmax, rmin, rmax, p0, p1, r0, r1))))
+
+    def predictor_weights(self, set_to=None):
+        if set_to is not None:
+            w = np.ascontiguousarray(set_to, dtype=np.float32)
+            _check(lib().ksc_predictor_weights(self._h, None, _hptr(w)))
+            return w
+        w = np.zeros(8450, np.float32)
+        _check(lib().ksc_predictor_weights(self._h, _hptr(w), None))
+        return w
+
+    def search_adaptive(self, Q, k, opts=None, stream=None):
+        torch = _torch()
+        nq = Q.shape[0]
+        ids = torch.empty((nq, k), dtype=torch.int64, device=Q.device)
+        dists = torch.empty((nq, k), dtype=torch.float32, device=Q.device)
+        npb = torch.empty((nq,), dtype=torch.int32, device=Q.device)
+        rr = torch.empty((nq,), dtype=torch.int32, device=Q.device)
+        _check(lib().ksc_search_adaptive(self._h, _dptr(Q, torch.float32, "Q"), nq, k, _dptr(ids), _dptr(dists),
+                                         _dptr(npb), _dptr(rr), C.byref(opts) if opts else None, _stream(stream)))
+        return ids, dists, npb, rr
+
+    def query_features(self, Q, stream=None):
+        torch = _torch()
+        f = torch.empty((Q.shape[0], 64), dtype=torch.float32, device=Q.device)
+        _check(lib().ksc_query_features(self._h, _dptr(Q, torch.float32, "Q"), Q.shape[0], _dptr(f),
+                                        _stream(stream)))
+        return f
 
     STAGES = ("rank", "lut", "prepass", "worklist", "scan", "select", "rerank")
 

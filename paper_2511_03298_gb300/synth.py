@@ -4,9 +4,13 @@ These stand in for the paper's datasets (Table 5), which are not available:
   small  : 10k x 128 isotropic Gaussian mixture (100 centres U[-5,5], sigma 1), L2
   sift   : 1M x 128 non-negative integer vectors 0..255 from a 1000-component
            mixture with a skewed per-dimension scale s_t (SIFT1M / BIGANN shape),
-           L2; centres U[0, 96 s_t], noise 38 s_t, rounded and clipped (many
-           zeros, as in SIFT); the noise scale puts recall@10 = 0.90 at a
-           moderate nprobe, as on SIFT1M with 1024 lists
+           L2: 30 super-centres U[0, 96 s_t], 1000 component centres at
+           N(0, (10 s_t)^2) around them, points at N(0, (20 s_t)^2) around
+           those, rounded and clipped (many zeros, as in SIFT).  Components
+           crowd together unevenly, so list boundaries cut through dense
+           regions: the share of queries with 9 of 10 neighbours in their
+           first P of 1024 lists grows from ~1/4 at P = 1 to ~3/4 at P = 8,
+           as on SIFT1M
   glove  : 1.2M x 100 unit-norm anisotropic mixture, 2000 components with
            power-law weights (GLOVE-100 / TEXT-TO-IMAGE shape), inner product
   deep   : 10M x 96 unit-norm mixture, 10000 components with Zipf(1.1) weights
@@ -18,7 +22,7 @@ CPU oracle receive these arrays as inputs; this module computes nothing else.
 """
 import numpy as np
 
-GENERATOR_VERSION = 2
+GENERATOR_VERSION = 3
 
 CONFIGS = {
     1: dict(name="small", n=10_000, d=128, nq=100, L=64, M=64, k=10, R=100, nprobe=8, metric="l2",
@@ -46,7 +50,8 @@ def _mixture_params(cfg):
         return dict(mu=mu, w=np.full(100, 1 / 100))
     if cfg == 2:
         s = np.exp(rng.normal(0.0, 0.5, size=d))
-        mu = rng.uniform(0.0, 1.0, size=(1000, d)) * (96.0 * s)
+        sup = rng.uniform(0.0, 1.0, size=(30, d)) * (96.0 * s)
+        mu = sup[rng.integers(0, 30, 1000)] + rng.normal(size=(1000, d)) * (10.0 * s)
         return dict(mu=mu, s=s, w=np.full(1000, 1 / 1000))
     if cfg == 3:
         ncomp = 2000
@@ -72,7 +77,7 @@ def _draw(cfg, prm, n, rng, chunk=1 << 20):
         if cfg == 1:
             x = prm["mu"][comp] + eps
         elif cfg == 2:
-            x = np.clip(np.rint(prm["mu"][comp] + 38.0 * prm["s"] * eps), 0, 255)
+            x = np.clip(np.rint(prm["mu"][comp] + 20.0 * prm["s"] * eps), 0, 255)
         elif cfg == 3:
             x = _normalise(prm["mu"][comp] + prm["sig"][comp] * eps)
         else:
