@@ -307,7 +307,9 @@ def run_ours(args, rank, ws):
             pairs_vecs = int(sizes[pr].sum())
         lookups = pairs_vecs * CFG["M"]
         code_bytes = pairs_vecs * CFG["M"] // 2
-        scan_ms = statistics.mean(stage_ms["scan"])
+        # the scan runs in two launches (nearest lists, then the rest); the
+        # first stage also holds the small threshold kernel
+        scan_ms = statistics.mean(stage_ms["scan"]) + statistics.mean(stage_ms["near_scan"])
         peak_gl = ksc.lut16_peak()
         achieved_gl = lookups / (scan_ms * 1e-3) / 1e9
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(

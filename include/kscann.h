@@ -117,7 +117,7 @@ typedef struct {
     int32_t n_near;            /* hybrid: probes of rank < n_near are scanned fully (2) */
     int32_t efs;               /* hybrid: graph-search result capacity (64) */
     int32_t tau;               /* hybrid: full scan when >= tau results beat theta (8) */
-    int32_t cand_cap;          /* candidate store per query; 0 -> max(16R, 4096) */
+    int32_t cand_cap;          /* candidate store per query; 0 -> max(32R, 8192) */
     int32_t rank_fp32;         /* 1: list scores on FP32 CUDA cores instead of BF16 tensor cores */
 } ksc_search_opts;
 
@@ -264,8 +264,9 @@ int ksc_last_status(ksc_index* ix, int32_t* status_host);
 
 /* Stage timing of searches on this index (CUDA events recorded on the
  * search stream; off by default).  Stages, in order: 0 rank lists (a1),
- * 1 LUT build + quantise (a2), 2 threshold pre-pass, 3 work list, 4 LUT16
- * scan (a3), 5 candidate select (a5), 6 rerank (a6).  ksc_profile_read
+ * 1 work lists, 2 LUT build + quantise (a2), 3 LUT16 scan of each query's
+ * nearest list + candidate threshold, 4 LUT16 scan of the other probed lists
+ * (a3), 5 candidate select (a5), 6 rerank (a6).  ksc_profile_read
  * synchronises with the last profiled search and writes its per-stage
  * milliseconds into ms_host[0..n) (n <= 8) and the number of kernels it
  * launched into *launches_host (may be NULL). */

@@ -41,6 +41,7 @@ struct ksc_index {
     void* c_rank_bf16 = nullptr;
     alignas(64) unsigned char map_c[128] = {};
     float c_rank_max_norm = 0.f;
+    bool tc_fp16 = false;  // 16-bit operand type of the tensor-core ranking
     // learned nprobe / rerank predictor (Sec. 4.2.1-4.2.2)
     float* mlp_w = nullptr;  // [KSC_MLP_NPARAMS] FP32
     ksc_adaptive_params mlp_prm = {};

@@ -1,5 +1,6 @@
 // Centroid ranking scores (Alg. 2 TopNClusters) on the 5th-generation tensor
-// cores: S = Q_bf16 . C_bf16^T accumulated in FP32 in tensor memory.
+// cores: S = Q16 . C16^T (16-bit operands: FP16 when the centroids fit it,
+// else BF16) accumulated in FP32 in tensor memory.
 //
 // One CTA computes a 128 x 256 tile (128 queries x 256 lists): TMA loads the
 // K-major BF16 operands into shared memory as 128-byte-swizzled boxes of 64
@@ -7,11 +8,12 @@
 // instruction) into a 256-column TMEM accumulator, tcgen05.commit signals an
 // mbarrier, and the four warps read their 32 TMEM lanes back with
 // tcgen05.ld and write score = ||c||^2 - 2 <q, c> (L2) or -<q, c>.  These
-// scores are approximate (BF16 operands); the ranking kernel re-scores in
-// FP32 every list that the BF16 error bound cannot exclude.
+// scores are approximate (16-bit operands); the ranking kernel re-scores in
+// FP32 every list that their error bound cannot exclude.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 #include <cstdio>
@@ -64,9 +66,11 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
            (2ull << 61);
 }
 
-// Instruction descriptor of kind::f16: BF16 A and B (K-major), FP32 D, M x N.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// Instruction descriptor of kind::f16: A and B both FP16 (fmt 0) or both
+// BF16 (fmt 1), K-major, FP32 D, M x N.
+__host__ __device__ constexpr uint32_t idesc_f16kind(int fmt, int M, int N) {
+    return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
@@ -97,7 +101,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 __global__ void __launch_bounds__(128, 1) k_rank_gemm_tc(const __grid_constant__ CUtensorMap mapA,
                                                          const __grid_constant__ CUtensorMap mapB, int KB, int64_t nq,
                                                          int L, const float* __restrict__ cn, int spherical,
-                                                         float* __restrict__ scores, int32_t* __restrict__ status) {
+                                                         int fmt, float* __restrict__ scores,
+                                                         int32_t* __restrict__ status) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t bars[2];
     __shared__ uint32_t tmem_base;
@@ -130,7 +135,7 @@ __global__ void __launch_bounds__(128, 1) k_rank_gemm_tc(const __grid_constant__
         ok = mbar_wait(bar_tma, 0, TC_WAIT_LIMIT);
         if (ok) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t idesc = idesc_bf16(TC_M, TC_N);
+            const uint32_t idesc = idesc_f16kind(fmt, TC_M, TC_N);
             for (int kb = 0; kb < KB; ++kb)
 #pragma unroll
                 for (int k = 0; k < TC_KB / 16; ++k) {
@@ -174,13 +179,15 @@ __global__ void __launch_bounds__(128, 1) k_rank_gemm_tc(const __grid_constant__
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_N));
 }
 
-// rows of X (fp32 [n x d]) to BF16 [n x Kp], zero-padded K.
-__global__ void k_to_bf16(const float* __restrict__ X, int64_t n, int d, int Kp, __nv_bfloat16* __restrict__ out) {
+// rows of X (fp32 [n x d]) to 16-bit operands [n x Kp] (FP16 when fp16 is
+// set, else BF16; round to nearest), zero-padded K.
+__global__ void k_to_16(const float* __restrict__ X, int64_t n, int d, int Kp, int fp16, uint16_t* __restrict__ out) {
     int64_t tot = n * Kp;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
         int64_t r = e / Kp;
         int t = (int)(e - r * Kp);
-        out[e] = __float2bfloat16_rn(t < d ? X[r * d + t] : 0.f);
+        const float v = t < d ? X[r * d + t] : 0.f;
+        out[e] = fp16 ? __half_as_ushort(__float2half_rn(v)) : __bfloat16_as_ushort(__float2bfloat16_rn(v));
     }
 }
 
@@ -188,16 +195,26 @@ __global__ void k_to_bf16(const float* __restrict__ X, int64_t n, int d, int Kp,
 // rel * ||q|| * max||c|| (times 2 for L2, whose score carries -2 <q, c>) plus
 // (d + 8) 2^-23 (||q|| + max||c||)^2 for the FP32 rounding of ||c||^2 and of
 // the exact FP32 re-score.
-//  BF16 tensor cores: |<q~, c~> - <q, c>| <= (2u + u^2) sum |q_t c_t| + FP32
-//    accumulation, u = 2^-8, and sum |q_t c_t| <= ||q|| ||c|| (Cauchy-Schwarz).
+//  16-bit tensor-core operands: |<q~, c~> - <q, c>| <= (2u + u^2) sum |q_t c_t|
+//    + FP32 accumulation, u = 2^-11 (FP16) or 2^-8 (BF16), and
+//    sum |q_t c_t| <= ||q|| ||c|| (Cauchy-Schwarz).  FP16 is used when every
+//    centroid element is below 2^14 and a query element above 6e4 voids the
+//    bound (err = inf: every list is re-scored).
 //  FP32 CUDA cores: a dot product of d terms errs by at most about d 2^-24
 //    of sum |q_t c_t|.
 __global__ void k_score_err(const float* __restrict__ Q, int64_t nq, int d, float cmax, int spherical, float rel,
-                            float* __restrict__ err) {
+                            float qmax, float* __restrict__ err) {
     int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= nq) return;
-    float s = 0.f;
-    for (int t = 0; t < d; ++t) s = fmaf(Q[q * d + t], Q[q * d + t], s);
+    float s = 0.f, mx = 0.f;
+    for (int t = 0; t < d; ++t) {
+        s = fmaf(Q[q * d + t], Q[q * d + t], s);
+        mx = fmaxf(mx, fabsf(Q[q * d + t]));
+    }
+    if (mx > qmax) {  // an element the 16-bit operand cannot hold: no bound
+        err[q] = INFINITY;
+        return;
+    }
     const float qn = sqrtf(s);
     const float e = rel * qn * cmax * 1.0001f;
     // plus the FP32 rounding of ||c||^2 and of the exact re-score itself
@@ -218,7 +235,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-static int make_map(CUtensorMap* map, const void* base, int64_t rows, int Kp, int box_rows) {
+static int make_map(CUtensorMap* map, const void* base, int64_t rows, int Kp, int box_rows, bool fp16) {
     auto fn = encode_fn();
     if (!fn) {
         set_error("cuTensorMapEncodeTiled is not available");
@@ -228,7 +245,7 @@ static int make_map(CUtensorMap* map, const void* base, int64_t rows, int Kp, in
     cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
     cuuint32_t box[2] = {(cuuint32_t)TC_KB, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+    CUresult r = fn(map, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
@@ -246,23 +263,30 @@ int rank_scores_tc(ksc_index* ix, const float* Q, int64_t nq, float* scores, flo
     const int Kp = (ix->d + TC_KB - 1) / TC_KB * TC_KB;
     const int KB = Kp / TC_KB;
     if (!ix->c_rank_bf16) {
-        KSC_CUDA(cudaMalloc(&ix->c_rank_bf16, sizeof(__nv_bfloat16) * (size_t)ix->L * Kp));
-        k_to_bf16<<<(unsigned)std::min<int64_t>(((int64_t)ix->L * Kp + 255) / 256, 4096), 256, 0, st>>>(
-            ix->c_rank, ix->L, ix->d, Kp, (__nv_bfloat16*)ix->c_rank_bf16);
+        // operand type: FP16 (11-bit significand) when the centroids fit it
+        std::vector<float> ch((size_t)ix->L * ix->d);
+        KSC_CUDA(cudaMemcpy(ch.data(), ix->c_rank, sizeof(float) * ch.size(), cudaMemcpyDeviceToHost));
+        float mx = 0.f;
+        for (float v : ch) mx = fmaxf(mx, fabsf(v));
+        ix->tc_fp16 = mx < 16384.f;
+        KSC_CUDA(cudaMalloc(&ix->c_rank_bf16, sizeof(uint16_t) * (size_t)ix->L * Kp));
+        k_to_16<<<(unsigned)std::min<int64_t>(((int64_t)ix->L * Kp + 255) / 256, 4096), 256, 0, st>>>(
+            ix->c_rank, ix->L, ix->d, Kp, ix->tc_fp16, (uint16_t*)ix->c_rank_bf16);
         KSC_LAUNCH_CHECK();
-        KSC_TRY(make_map(reinterpret_cast<CUtensorMap*>(ix->map_c), ix->c_rank_bf16, ix->L, Kp, TC_N));
+        KSC_TRY(make_map(reinterpret_cast<CUtensorMap*>(ix->map_c), ix->c_rank_bf16, ix->L, Kp, TC_N, ix->tc_fp16));
     }
-    KSC_TRY(ensure(ix->ws_qbf16, sizeof(__nv_bfloat16) * (size_t)nq * Kp, st));
-    __nv_bfloat16* qb = (__nv_bfloat16*)ix->ws_qbf16.p;
-    k_to_bf16<<<(unsigned)std::min<int64_t>((nq * Kp + 255) / 256, 4096), 256, 0, st>>>(Q, nq, ix->d, Kp, qb);
+    KSC_TRY(ensure(ix->ws_qbf16, sizeof(uint16_t) * (size_t)nq * Kp, st));
+    uint16_t* qb = (uint16_t*)ix->ws_qbf16.p;
+    k_to_16<<<(unsigned)std::min<int64_t>((nq * Kp + 255) / 256, 4096), 256, 0, st>>>(Q, nq, ix->d, Kp, ix->tc_fp16,
+                                                                                     qb);
     KSC_LAUNCH_CHECK();
     CUtensorMap mapA;
-    KSC_TRY(make_map(&mapA, qb, nq, Kp, TC_M));
+    KSC_TRY(make_map(&mapA, qb, nq, Kp, TC_M, ix->tc_fp16));
     const size_t smem = (size_t)KB * (TC_M + TC_N) * 128 + 1024;
     KSC_CUDA(cudaFuncSetAttribute(k_rank_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((ix->L + TC_N - 1) / TC_N, (unsigned)((nq + TC_M - 1) / TC_M));
     k_rank_gemm_tc<<<grid, 128, smem, st>>>(mapA, *reinterpret_cast<const CUtensorMap*>(ix->map_c), KB, nq, ix->L,
-                                            ix->c_rank_sq, ix->spherical, scores, ix->status);
+                                            ix->c_rank_sq, ix->spherical, ix->tc_fp16 ? 0 : 1, scores, ix->status);
     KSC_LAUNCH_CHECK();
     ix->launches += 2;
     return score_err(ix, Q, nq, true, err, st);
@@ -277,9 +301,11 @@ int score_err(ksc_index* ix, const float* Q, int64_t nq, bool tensor_cores, floa
         for (float v : cn) m = v > m ? v : m;
         ix->c_rank_max_norm = m > 0.f ? sqrtf(m) : 1e-30f;
     }
-    const float rel = tensor_cores ? 0.0078125f + 6.2e-5f + (float)ix->d * 4.8e-7f : (float)(ix->d + 8) * 1.2e-7f;
+    const float u2 = ix->tc_fp16 ? 9.77e-4f + 1e-6f : 0.0078125f + 6.2e-5f;  // 2u + u^2
+    const float rel = tensor_cores ? u2 + (float)ix->d * 4.8e-7f : (float)(ix->d + 8) * 1.2e-7f;
+    const float qmax = (tensor_cores && ix->tc_fp16) ? 6.0e4f : INFINITY;
     k_score_err<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(Q, nq, ix->d, ix->c_rank_max_norm, ix->spherical,
-                                                              rel, err);
+                                                              rel, qmax, err);
     KSC_LAUNCH_CHECK();
     ix->launches++;
     return KSC_OK;

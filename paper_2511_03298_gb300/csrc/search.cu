@@ -18,11 +18,9 @@
 
 namespace ksc {
 
-constexpr int PRE_CAP = 8192;   // keys examined by the threshold pre-pass
 constexpr int SEL_CAP = 4096;   // bitonic buffer of the select kernels (>= KSC_MAX_RERANK)
 constexpr int MAX_NPROBE = 4096;
-constexpr int PRE_MULT = 8;      // the pre-pass looks at up to 8R keys of the nearest lists
-constexpr int PRE_BIN_CAP = 1024;
+constexpr int NEAR_RANKS = 1;    // probe ranks scanned before the threshold is set
 
 // ------------------------------------------------------------------ a1: list scores
 // score[q][c] = ||c||^2 - 2<q,c> (L2, ||q||^2 dropped) or -<q,c> (spherical).
@@ -244,7 +242,28 @@ struct LutArgs {
     const float* c_mean;
     const float* cb;
     int L;
+    // optional compact work: pairs e = q * Pmax + r, two ranges (NULL: every
+    // (q, r < P_q))
+    const uint32_t* pairs0;
+    const int64_t* npairs0;
+    const uint32_t* pairs1;
+    const int64_t* npairs1;
 };
+
+// Item i of the LUT pass: its (query, rank) flat index, or -1 if it does no work.
+__device__ __forceinline__ int64_t lut_item(const LutArgs& A, int64_t i, int64_t n0) {
+    if (A.pairs0) return i < n0 ? (int64_t)A.pairs0[i] : (int64_t)A.pairs1[i - n0];
+    return i;
+}
+
+__device__ __forceinline__ int64_t lut_items(const LutArgs& A, int64_t* n0) {
+    if (A.pairs0) {
+        *n0 = *A.npairs0;
+        return *n0 + *A.npairs1;
+    }
+    *n0 = 0;
+    return A.nq * A.Pmax;
+}
 
 __device__ __forceinline__ int probes_of(const LutArgs& A, int64_t q) {
     int P = A.nprobe_q ? A.nprobe_q[q] : A.Pfix;
@@ -279,8 +298,10 @@ __global__ void __launch_bounds__(256) k_lut_range(LutArgs A, uint32_t* __restri
     extern __shared__ float cbs[];
     const int lane = threadIdx.x & 31;
     const int ld = stage_codebook(A, cbs);
-    const int64_t items = A.nq * A.Pmax;
-    for (int64_t item = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); item < items; item += (int64_t)gridDim.x * 8) {
+    int64_t n0;
+    const int64_t items = lut_items(A, &n0);
+    for (int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); i < items; i += (int64_t)gridDim.x * 8) {
+        const int64_t item = lut_item(A, i, n0);
         const int64_t q = item / A.Pmax;
         const int r = (int)(item - q * A.Pmax);
         if (r >= probes_of(A, q)) continue;
@@ -313,8 +334,10 @@ __global__ void __launch_bounds__(256) k_lut_quant(LutArgs A, const uint32_t* __
     __shared__ float mins[8][KSC_MAX_M];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int ld = stage_codebook(A, cbs);
-    const int64_t items = A.nq * A.Pmax;
-    for (int64_t item = (int64_t)blockIdx.x * 8 + wib; item < items; item += (int64_t)gridDim.x * 8) {
+    int64_t n0;
+    const int64_t items = lut_items(A, &n0);
+    for (int64_t i = (int64_t)blockIdx.x * 8 + wib; i < items; i += (int64_t)gridDim.x * 8) {
+        const int64_t item = lut_item(A, i, n0);
         const int64_t q = item / A.Pmax;
         const int r = (int)(item - q * A.Pmax);
         if (r >= probes_of(A, q)) continue;
@@ -402,88 +425,78 @@ __device__ __forceinline__ int rerank_of(const int32_t* rerank_q, int Rfix, int 
     return R < Rmin ? Rmin : (R > Rmax ? Rmax : R);
 }
 
-// ------------------------------------------------------------------ threshold pre-pass
-// Per query: keys of the members of its best-ranked lists, in rank order,
-// up to cap = min(4R, PRE_CAP) of them; the R-th smallest of these bounds the
-// R-th smallest key of the whole search from above (any subset with at least
-// R members gives such a bound).  Fewer than R members in all probes: no
-// bound (all ones).
-__global__ void __launch_bounds__(256) k_prepass(ScanArgs A, int Rmax, uint64_t* __restrict__ thr) {
-    extern __shared__ uint64_t buf[];
-    __shared__ uint8_t slut[KSC_MAX_M * PQ_K];
-    __shared__ int s_count;
-    const int64_t q = blockIdx.x;
-    const int R = rerank_of(A.rerank_q, A.Rfix, A.Rmin, Rmax, q);
-    const int cap = min(PRE_MULT * R, PRE_CAP);
-    const int P = nprobe_of(A, q);
-    if (threadIdx.x == 0) s_count = 0;
-    __syncthreads();
-    for (int r = 0; r < P; ++r) {
-        int count = s_count;
-        if (count >= cap) break;
-        const int64_t item = q * A.Pmax + r;
-        const int p = A.probes[item];
-        if (p < 0 || p >= A.L) continue;  // uniform over the block
-        const int np_ = A.list_n[p];
-        const int take = min(np_, cap - count);
-        for (int e = threadIdx.x; e < A.M * PQ_K; e += blockDim.x) slut[e] = A.lut[item * A.M * PQ_K + e];
-        __syncthreads();
-        const int32_t b = A.bias[item];
-        for (int m = threadIdx.x; m < take; m += blockDim.x) {
-            const int64_t blk = A.boff[p] + (m >> 5);
-            const int v = m & 31;
-            int32_t D = scalar_dist(slut, b, A.codes + blk * A.M * 16, A.M, v);
-            buf[count + m] = make_key(D, A.ids[blk * 32 + v]);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) s_count = count + take;
-        __syncthreads();
-    }
-    const int count = s_count;
-    if (count < R) {
-        if (threadIdx.x == 0) thr[q] = KEY_NONE;
-        return;
-    }
-    // R-th smallest: histogram of the distances, then sort only the keys of
-    // the bin that holds it
+// ------------------------------------------------------------------ threshold
+// Per query, after the scan of its nearest list(s) with no filter: the R-th
+// smallest of the keys found so far bounds the R-th smallest key of the whole
+// search from above (any subset with at least R members gives such a bound);
+// the scan of the remaining lists keeps only keys at or below it.  Fewer than
+// R keys: no bound (all ones).  A histogram of the distances finds the bin of
+// the R-th key and only that bin is sorted; `scratch` (a row of R keys per
+// query) serves the radix fallback when the bin is too large.
+__global__ void __launch_bounds__(256) k_threshold(ScanArgs A, int Rmax, int32_t* __restrict__ cnt,
+                                                   uint64_t* __restrict__ cand, int cap,
+                                                   uint64_t* __restrict__ scratch, uint64_t* __restrict__ thr) {
+    extern __shared__ uint64_t buf[];  // SEL_CAP keys
     __shared__ uint32_t hist[HIST_BINS];
     __shared__ uint32_t warp_tot[32];
     __shared__ HistSel hs;
-    __shared__ uint64_t binkeys[PRE_BIN_CAP];
     __shared__ int s_nb;
-    auto load = [&](int i) -> uint64_t { return buf[i]; };
-    hist_find(load, count, R, hist, warp_tot, &hs);
-    if (hs.inB <= PRE_BIN_CAP) {
-        if (threadIdx.x == 0) s_nb = 0;
-        __syncthreads();
-        for (int i = threadIdx.x; i < count; i += blockDim.x) {
-            uint64_t k = buf[i];
-            if (hist_bin(k, hs.base) == hs.B) binkeys[atomicAdd(&s_nb, 1)] = k;
-        }
-        __syncthreads();
-        const int S2 = pow2_ceil(hs.inB);
-        for (int i = hs.inB + threadIdx.x; i < S2; i += blockDim.x) binkeys[i] = KEY_NONE;
-        __syncthreads();
-        block_bitonic_sort(binkeys, S2);
-        if (threadIdx.x == 0) thr[q] = binkeys[R - hs.lt - 1];
+    const int64_t q = blockIdx.x;
+    const int R = rerank_of(A.rerank_q, A.Rfix, A.Rmin, Rmax, q);
+    const int n = min(cnt[q], cap);
+    if (n < R) {
+        if (threadIdx.x == 0) thr[q] = KEY_NONE;
         return;
     }
-    const int S = pow2_ceil(count);
-    for (int i = count + threadIdx.x; i < S; i += blockDim.x) buf[i] = KEY_NONE;
+    uint64_t* cq = cand + q * cap;
+    auto load = [&](int i) -> uint64_t { return cq[i]; };
+    __shared__ uint64_t s_thr;
+    hist_find(load, n, R, hist, warp_tot, &hs);
+    if (hs.inB <= SEL_CAP) {
+        if (threadIdx.x == 0) s_nb = 0;
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const uint64_t k = cq[i];
+            if (hist_bin(k, hs.base) == hs.B) buf[atomicAdd(&s_nb, 1)] = k;
+        }
+        __syncthreads();
+        const int S = pow2_ceil(hs.inB);
+        for (int i = hs.inB + threadIdx.x; i < S; i += blockDim.x) buf[i] = KEY_NONE;
+        __syncthreads();
+        block_bitonic_sort(buf, S);
+        if (threadIdx.x == 0) s_thr = buf[R - hs.lt - 1];
+    } else {
+        uint64_t* out = scratch + q * Rmax;
+        block_select_smallest(load, n, R, out, buf, SEL_CAP, hist);
+        if (threadIdx.x == 0) s_thr = out[R - 1];
+    }
     __syncthreads();
-    block_bitonic_sort(buf, S);
-    if (threadIdx.x == 0) thr[q] = buf[R - 1];
+    const uint64_t t = s_thr;
+    if (threadIdx.x == 0) thr[q] = t;
+    if (cnt[q] > cap) return;  // overflowed: the final select redoes this query exactly
+    // keep only the R keys at or below the threshold: nothing above it can
+    // enter the final R
+    if (threadIdx.x == 0) s_nb = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const uint64_t k = cq[i];
+        if (k <= t) buf[atomicAdd(&s_nb, 1)] = k;
+    }
+    __syncthreads();
+    const int m = s_nb;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) cq[i] = buf[i];
+    if (threadIdx.x == 0) cnt[q] = m;
 }
 
 // ------------------------------------------------------------------ work list (cluster-major)
 // pairs of (query, probe rank) grouped by list; items = (list, query group,
 // block tile).
-__global__ void k_count_pairs(ScanArgs A, int32_t* __restrict__ cnt) {
+__global__ void k_count_pairs(ScanArgs A, int rlo, int rhi, int32_t* __restrict__ cnt) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= A.nq * A.Pmax) return;
     int64_t q = e / A.Pmax;
     int r = (int)(e - q * A.Pmax);
-    if (r >= nprobe_of(A, q)) return;
+    if (r < rlo || r >= rhi || r >= nprobe_of(A, q)) return;
     const int p = A.probes[e];
     if (p < 0 || p >= A.L) return;
     atomicAdd(&cnt[p], 1);
@@ -530,13 +543,13 @@ __global__ void __launch_bounds__(1024) k_scan_lists(const int32_t* __restrict__
     }
 }
 
-__global__ void k_fill_pairs(ScanArgs A, const int64_t* __restrict__ pair_off, int32_t* __restrict__ fill,
-                             uint32_t* __restrict__ pairs) {
+__global__ void k_fill_pairs(ScanArgs A, int rlo, int rhi, const int64_t* __restrict__ pair_off,
+                             int32_t* __restrict__ fill, uint32_t* __restrict__ pairs) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= A.nq * A.Pmax) return;
     int64_t q = e / A.Pmax;
     int r = (int)(e - q * A.Pmax);
-    if (r >= nprobe_of(A, q)) return;
+    if (r < rlo || r >= rhi || r >= nprobe_of(A, q)) return;
     int p = A.probes[e];
     if (p < 0 || p >= A.L) return;
     int slot = atomicAdd(&fill[p], 1);
@@ -770,7 +783,7 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32, (SMAX <= 4 ? 3 : (SMAX <= 8 ?
                 t[u] = (u < S && j < M) ? __ldg(lp + j) : make_uint4(0, 0, 0, 0);
             }
             bias = A.bias[e];
-            const uint64_t th = O.thr[q];
+            const uint64_t th = O.thr ? O.thr[q] : KEY_NONE;
             thD = (uint32_t)(th >> 32);
             thI = (uint32_t)th;
         } else {
@@ -811,19 +824,39 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32, (SMAX <= 4 ? 3 : (SMAX <= 8 ?
                     }
                     uint32_t sums[V];
                     reduce_scatter<G>(acc, lane, sums);
+                    // keys at or below the threshold, appended with one atomic per
+                    // lane group (query) and block
+                    uint64_t keep[V];
+                    uint32_t kmask = 0;
                     if (active) {
 #pragma unroll
                         for (int v = 0; v < V; ++v) {
                             // high word of the key: (D + 2^31) as an unsigned integer
                             const uint32_t Dk = (uint32_t)(bias + (int32_t)sums[v]) ^ 0x80000000u;
+                            keep[v] = (uint64_t)Dk << 32;
                             if (Dk <= thD) {
                                 const int32_t id = A.ids[(gb0 + blk) * 32 + V * g + v];
                                 if (id >= 0 && (Dk < thD || (uint32_t)id <= thI)) {
-                                    const int sl = atomicAdd(&O.cnt[q], 1);
-                                    if (sl < O.cap) O.cand[q * O.cap + sl] = ((uint64_t)Dk << 32) | (uint32_t)id;
+                                    keep[v] |= (uint32_t)id;
+                                    kmask |= 1u << v;
                                 }
                             }
                         }
+                    }
+                    const int nk = __popc(kmask);
+                    int incl = nk;
+#pragma unroll
+                    for (int o = 1; o < G; o <<= 1) {
+                        const int y = __shfl_up_sync(0xffffffffu, incl, o, G);
+                        if (g >= o) incl += y;
+                    }
+                    const int tot = __shfl_sync(0xffffffffu, incl, G - 1, G);
+                    int base = (g == G - 1 && tot > 0) ? atomicAdd(&O.cnt[q], tot) : 0;
+                    base = __shfl_sync(0xffffffffu, base, G - 1, G) + incl - nk;
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        const int at = base + __popc(kmask & ((1u << v) - 1u));
+                        if (((kmask >> v) & 1u) && at < O.cap) O.cand[q * O.cap + at] = keep[v];
                     }
                 }
             }
@@ -1107,72 +1140,109 @@ static int compute_luts(ksc_index* ix, const float* Q, int64_t nq, const int32_t
     return KSC_OK;
 }
 
-// a2 .. a6 for given probe lists.
+// Cluster-major work list of the (query, rank) pairs with rank in [rlo, rhi).
+struct WorkList {
+    int64_t* pair_off;  // [L + 1]
+    int64_t* item_off;  // [L + 1]
+    int32_t* cnt;       // [L]
+    int32_t* fill;      // [L]
+    uint32_t* pairs;    // [<= nq * (rhi - rlo)]
+};
+
+static int build_worklist(ksc_index* ix, const ScanArgs& A, int rlo, int rhi, int QG, int TB, WorkList& w,
+                          cudaStream_t st) {
+    const int L = ix->L;
+    const int64_t n = A.nq * A.Pmax;
+    KSC_CUDA(cudaMemsetAsync(w.cnt, 0, sizeof(int32_t) * L, st));
+    k_count_pairs<<<blocks_for(n, 256), 256, 0, st>>>(A, rlo, rhi, w.cnt);
+    k_scan_lists<<<1, 1024, 0, st>>>(w.cnt, ix->list_n, L, QG, TB, w.pair_off, w.item_off, w.fill);
+    k_fill_pairs<<<blocks_for(n, 256), 256, 0, st>>>(A, rlo, rhi, w.pair_off, w.fill, w.pairs);
+    ix->launches += 3;
+    KSC_LAUNCH_CHECK();
+    return KSC_OK;
+}
+
+static int run_scan(const Plan& pl, int M, const ScanArgs& A, const ScanOut& O, const WorkList& w, int L,
+                    int32_t* status, cudaStream_t st) {
+    const int S = (M + pl.G - 1) / pl.G;
+    if (pl.G == 8) return dispatch_scan<8>(S, A, O, w.pair_off, w.item_off, w.pairs, L, pl.TB, status, st);
+    if (pl.G == 16) return dispatch_scan<16>(S, A, O, w.pair_off, w.item_off, w.pairs, L, pl.TB, status, st);
+    return dispatch_scan<32>(S, A, O, w.pair_off, w.item_off, w.pairs, L, pl.TB, status, st);
+}
+
+// a2 .. a6 for given probe lists.  Stages: 1 work lists, 2 LUTs, 3 scan of
+// the nearest list(s) + threshold, 4 scan of the other lists, 5 select,
+// 6 rerank.
 static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, const int32_t* probes,
                               int64_t* ids, float* dists, uint64_t* cand_out, int32_t* ncand_out, cudaStream_t st) {
     const int64_t nq = pl.nq;
-    const int M = ix->M;
+    const int M = ix->M, L = ix->L;
+    const int QG = 32 / pl.G;
+    const int rA = std::min(NEAR_RANKS, pl.Pmax);
     KSC_TRY(ensure(ix->ws_lut, (size_t)nq * pl.Pmax * M * PQ_K, st));
     KSC_TRY(ensure(ix->ws_bias, sizeof(int32_t) * nq * pl.Pmax, st));
     KSC_TRY(ensure(ix->ws_scale, sizeof(float) * nq, st));
+    KSC_TRY(ensure(ix->ws_thr, sizeof(uint64_t) * nq, st));
+    KSC_TRY(ensure(ix->ws_cnt, sizeof(int32_t) * nq, st));
+    KSC_TRY(ensure(ix->ws_cand, sizeof(uint64_t) * nq * pl.cap, st));
+    KSC_TRY(ensure(ix->ws_topr, sizeof(uint64_t) * nq * pl.Rmax, st));
+    const size_t wl_head = sizeof(int64_t) * 2 * (L + 1) + sizeof(int32_t) * 2 * L;
+    KSC_TRY(ensure(ix->ws_items, 2 * wl_head + sizeof(uint32_t) * nq * pl.Pmax + 256, st));
     uint8_t* lut = (uint8_t*)ix->ws_lut.p;
     int32_t* bias = (int32_t*)ix->ws_bias.p;
     float* scale = (float*)ix->ws_scale.p;
-    mark(ix, 1, st);
-    KSC_TRY(compute_luts(ix, Q, nq, probes, pl.nprobe_q, pl.Pfix, pl.Pmax, lut, bias, scale, st));
-    mark(ix, 2, st);
-
-    ScanArgs A{M, pl.Pmax, nq, probes, pl.nprobe_q, pl.Pfix, pl.rerank_q, pl.Rfix, pl.k, lut, bias,
-               ix->list_boff, ix->list_n, ix->blk_codes, ix->blk_ids, ix->L};
-    // threshold pre-pass
-    KSC_TRY(ensure(ix->ws_thr, sizeof(uint64_t) * nq, st));
     uint64_t* thr = (uint64_t*)ix->ws_thr.p;
-    {
-        const int cap = std::min(PRE_MULT * pl.Rmax, PRE_CAP);
-        const size_t smem = sizeof(uint64_t) * pow2_ceil(cap);
-        cudaFuncSetAttribute(k_prepass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_prepass<<<(unsigned)nq, 256, smem, st>>>(A, pl.Rmax, thr);
-        ix->launches++;
-        KSC_LAUNCH_CHECK();
-    }
-    mark(ix, 3, st);
-    // work list
-    const int L = ix->L;
-    const int QC = 32 / pl.G;  // queries per scan item (one warp)
-    const int TB = pl.TB;
-    KSC_TRY(ensure(ix->ws_items, sizeof(int64_t) * 2 * (L + 1) + sizeof(int32_t) * 2 * L +
-                                     sizeof(uint32_t) * nq * pl.Pmax + 64, st));
-    char* wp = (char*)ix->ws_items.p;
-    int64_t* pair_off = (int64_t*)wp;
-    int64_t* item_off = pair_off + (L + 1);
-    int32_t* lcnt = (int32_t*)(item_off + (L + 1));
-    int32_t* fill = lcnt + L;
-    uint32_t* pairs = (uint32_t*)(fill + L);
-    KSC_CUDA(cudaMemsetAsync(lcnt, 0, sizeof(int32_t) * L, st));
-    k_count_pairs<<<blocks_for(nq * pl.Pmax, 256), 256, 0, st>>>(A, lcnt);
-    k_scan_lists<<<1, 1024, 0, st>>>(lcnt, ix->list_n, L, QC, TB, pair_off, item_off, fill);
-    k_fill_pairs<<<blocks_for(nq * pl.Pmax, 256), 256, 0, st>>>(A, pair_off, fill, pairs);
-    ix->launches += 3;
-    KSC_LAUNCH_CHECK();
-    mark(ix, 4, st);
-    // scan
-    KSC_TRY(ensure(ix->ws_cnt, sizeof(int32_t) * nq, st));
-    KSC_TRY(ensure(ix->ws_cand, sizeof(uint64_t) * nq * pl.cap, st));
     int32_t* cnt = (int32_t*)ix->ws_cnt.p;
     uint64_t* cand = (uint64_t*)ix->ws_cand.p;
-    KSC_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * nq, st));
-    ScanOut O{thr, cnt, cand, pl.cap};
-    const int S = (M + pl.G - 1) / pl.G;
-    int rc;
-    if (pl.G == 8) rc = dispatch_scan<8>(S, A, O, pair_off, item_off, pairs, L, TB, ix->status, st);
-    else if (pl.G == 16) rc = dispatch_scan<16>(S, A, O, pair_off, item_off, pairs, L, TB, ix->status, st);
-    else rc = dispatch_scan<32>(S, A, O, pair_off, item_off, pairs, L, TB, ix->status, st);
-    KSC_TRY(rc);
-    ix->launches++;
-    mark(ix, 5, st);
-    // select
-    KSC_TRY(ensure(ix->ws_topr, sizeof(uint64_t) * nq * pl.Rmax, st));
     uint64_t* topr = (uint64_t*)ix->ws_topr.p;
+    WorkList wa, wb;
+    {
+        char* wp = (char*)ix->ws_items.p;
+        WorkList* ws_[2] = {&wa, &wb};
+        for (WorkList* w : ws_) {
+            w->pair_off = (int64_t*)wp;
+            w->item_off = w->pair_off + (L + 1);
+            w->cnt = (int32_t*)(w->item_off + (L + 1));
+            w->fill = w->cnt + L;
+            wp += wl_head;
+        }
+        wa.pairs = (uint32_t*)wp;
+        wb.pairs = wa.pairs + nq * rA;
+    }
+    ScanArgs A{M, pl.Pmax, nq, probes, pl.nprobe_q, pl.Pfix, pl.rerank_q, pl.Rfix, pl.k, lut, bias,
+               ix->list_boff, ix->list_n, ix->blk_codes, ix->blk_ids, ix->L};
+    // 1. work lists: the nearest list of every query, and the rest
+    mark(ix, 1, st);
+    KSC_TRY(build_worklist(ix, A, 0, rA, QG, pl.TB, wa, st));
+    KSC_TRY(build_worklist(ix, A, rA, pl.Pmax, QG, pl.TB, wb, st));
+    // 2. quantised LUTs of every probed (query, list)
+    mark(ix, 2, st);
+    {
+        KSC_TRY(ensure(ix->ws_range, sizeof(uint32_t) * nq, st));
+        uint32_t* rb = (uint32_t*)ix->ws_range.p;
+        KSC_CUDA(cudaMemsetAsync(rb, 0, sizeof(uint32_t) * nq, st));
+        LutArgs LA{Q, nq, ix->d, M, ix->dsub, ix->metric == KSC_IP, pl.Pmax, probes, pl.nprobe_q, pl.Pfix,
+                   ix->c_mean, ix->codebook, ix->L, wa.pairs, wa.pair_off + L, wb.pairs, wb.pair_off + L};
+        KSC_TRY(launch_luts(LA, rb, lut, bias, scale, st));
+        ix->launches += 2;
+    }
+    // 3. scan of the nearest lists with no filter, then the threshold
+    mark(ix, 3, st);
+    KSC_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * nq, st));
+    KSC_TRY(run_scan(pl, M, A, ScanOut{nullptr, cnt, cand, pl.cap}, wa, L, ix->status, st));
+    {
+        const size_t smem = SEL_CAP * sizeof(uint64_t);
+        cudaFuncSetAttribute(k_threshold, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_threshold<<<(unsigned)nq, 256, smem, st>>>(A, pl.Rmax, cnt, cand, pl.cap, topr, thr);
+        KSC_LAUNCH_CHECK();
+        ix->launches += 2;
+    }
+    // 4. scan of the other lists, keeping keys at or below the threshold
+    mark(ix, 4, st);
+    KSC_TRY(run_scan(pl, M, A, ScanOut{thr, cnt, cand, pl.cap}, wb, L, ix->status, st));
+    ix->launches++;
+    // 5. the R best keys per query
+    mark(ix, 5, st);
     {
         const size_t smem = SEL_CAP * sizeof(uint64_t);
         cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1186,8 +1256,8 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
         ix->launches++;
         KSC_LAUNCH_CHECK();
     }
+    // 6. exact rerank
     mark(ix, 6, st);
-    // rerank
     {
         const size_t smem = sizeof(uint64_t) * pow2_ceil(pl.Rmax < 2 ? 2 : pl.Rmax);
         cudaFuncSetAttribute(k_rerank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1225,7 +1295,7 @@ static int make_plan(ksc_index* ix, int64_t nq, int k, int Pmax, int Rmax, const
         int TB = (int)(blocks / target);
         pl.TB = TB < 2 ? 2 : (TB > 64 ? 64 : TB);
     }
-    int cap = (opts && opts->cand_cap > 0) ? opts->cand_cap : std::max(16 * Rmax, 4096);
+    int cap = (opts && opts->cand_cap > 0) ? opts->cand_cap : std::max(32 * Rmax, 8192);
     pl.cap = std::max(cap, Rmax);
     pl.rank_exact = opts && opts->rank_fp32;
     return KSC_OK;

@@ -297,7 +297,7 @@ class Index:
                                         _stream(stream)))
         return f
 
-    STAGES = ("rank", "lut", "prepass", "worklist", "scan", "select", "rerank")
+    STAGES = ("rank", "worklist", "lut", "near_scan", "scan", "select", "rerank")
 
     def profile(self, on=True):
         _check(lib().ksc_profile_enable(self._h, int(on)))
