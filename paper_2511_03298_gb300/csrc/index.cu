@@ -315,12 +315,13 @@ static int alloc_copy(void** dst, const void* src, size_t bytes, cudaStream_t st
 int free_index_memory(ksc_index* ix) {
     void* ptrs[] = {ix->X, ix->c_rank, ix->c_rank_sq, ix->c_mean, ix->codebook, ix->list_boff, ix->list_n,
                     ix->blk_ids, ix->blk_codes, ix->assign, ix->graph, ix->entry, ix->status, ix->stats,
-                    ix->c_rank_bf16, ix->mlp_w};
+                    ix->c_rank_bf16, ix->mlp_w, ix->blk_list, ix->nbr_pos, ix->nbr_codes, ix->entry_pos};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     Buffer* bufs[] = {&ix->ws_scores, &ix->ws_probes, &ix->ws_lut, &ix->ws_bias, &ix->ws_scale, &ix->ws_range,
                       &ix->ws_thr, &ix->ws_cnt, &ix->ws_cand, &ix->ws_topr, &ix->ws_nprobe, &ix->ws_rerank,
-                      &ix->ws_items, &ix->ws_misc, &ix->ws_qbf16, &ix->ws_err, &ix->ws_feat, &ix->ws_rscore};
+                      &ix->ws_items, &ix->ws_misc, &ix->ws_qbf16, &ix->ws_err, &ix->ws_feat, &ix->ws_rscore,
+                      &ix->ws_full};
     for (Buffer* b : bufs) release(*b);
     for (int i = 0; i <= KSC_NUM_STAGES; ++i)
         if (ix->ev[i]) cudaEventDestroy(ix->ev[i]);
@@ -352,6 +353,11 @@ int pack_lists(ksc_index* ix, const uint8_t* codes_dev, const int32_t* assign_ho
     std::vector<int64_t> fill(L);
     for (int c = 0; c < L; ++c) fill[c] = ix->h_boff[c] * BLOCK_VECS;
     for (int64_t i = 0; i < n; ++i) ids[fill[assign_host[i]]++] = (int32_t)i;  // ascending id per list
+    std::vector<int32_t> blist(ix->nblocks);
+    for (int c = 0; c < L; ++c)
+        for (int64_t bb = ix->h_boff[c]; bb < ix->h_boff[c + 1]; ++bb) blist[bb] = c;
+    KSC_TRY(alloc_copy((void**)&ix->blk_list, blist.data(), sizeof(int32_t) * (ix->nblocks > 0 ? ix->nblocks : 1), st,
+                       cudaMemcpyHostToDevice));
     KSC_TRY(alloc_copy((void**)&ix->list_boff, ix->h_boff.data(), sizeof(int64_t) * (L + 1), st, cudaMemcpyHostToDevice));
     KSC_TRY(alloc_copy((void**)&ix->list_n, ix->h_n.data(), sizeof(int32_t) * L, st, cudaMemcpyHostToDevice));
     KSC_TRY(alloc_copy((void**)&ix->blk_ids, ids.data(), sizeof(int32_t) * ids.size(), st, cudaMemcpyHostToDevice));
@@ -492,6 +498,7 @@ int ksc_index_import(const ksc_index_arrays* a, void* stream, ksc_index** out) {
         if (a->graph && a->entry) {
             if ((rc = alloc_copy((void**)&ix->graph, a->graph, sizeof(int32_t) * ix->n * 32, st, cudaMemcpyHostToDevice))) break;
             if ((rc = alloc_copy((void**)&ix->entry, a->entry, sizeof(int32_t) * ix->L, st, cudaMemcpyHostToDevice))) break;
+            if ((rc = prepare_graph(ix, st))) break;
         }
         rc = finish_common(ix, st);
     } while (0);

@@ -30,8 +30,12 @@ struct ksc_index {
     int32_t* blk_ids = nullptr;    // [nblocks x 32] ids, -1 padding
     uint8_t* blk_codes = nullptr;  // [nblocks x M x 16]
     int32_t* assign = nullptr;     // [n]
-    int32_t* graph = nullptr;      // [n x 32] optional
-    int32_t* entry = nullptr;      // [L] optional
+    int32_t* blk_list = nullptr;   // [nblocks] list of each block
+    int32_t* graph = nullptr;      // [n x 32] optional: neighbours by id (interchange form)
+    int32_t* entry = nullptr;      // [L] optional: graph entry by id
+    int32_t* nbr_pos = nullptr;    // [nblocks x 32 x 32] neighbours as list positions
+    uint8_t* nbr_codes = nullptr;  // [nblocks x 32 x M x 16] neighbour codes, one block per node
+    int32_t* entry_pos = nullptr;  // [L] graph entry as a list position
     int32_t* status = nullptr;     // device status word
     unsigned long long* stats = nullptr;  // [4] counters of the last search
     // host mirrors
@@ -52,7 +56,7 @@ struct ksc_index {
     int32_t launches = 0;
     // search workspace
     ksc::Buffer ws_scores, ws_probes, ws_lut, ws_bias, ws_scale, ws_range, ws_thr, ws_cnt,
-        ws_cand, ws_topr, ws_nprobe, ws_rerank, ws_items, ws_misc, ws_qbf16, ws_err, ws_feat, ws_rscore;
+        ws_cand, ws_topr, ws_nprobe, ws_rerank, ws_items, ws_misc, ws_qbf16, ws_err, ws_feat, ws_rscore, ws_full;
 };
 
 namespace ksc {
@@ -78,4 +82,6 @@ int mlp_hits(const float* dists, int64_t nq, int k, const float* kth, int ip, in
 int mlp_adam(float* w, const float* g, float* m, float* v, int t, float lr, cudaStream_t st);
 // Per-list 32-NN graphs and entry points for the hybrid search (Sec. 4.4).
 int build_graph(ksc_index* ix, cudaStream_t st);
+// Search form (nbr_pos, nbr_codes, entry_pos) of graph / entry (hybrid.cu).
+int prepare_graph(ksc_index* ix, cudaStream_t st);
 }  // namespace ksc

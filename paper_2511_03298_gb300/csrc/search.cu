@@ -869,6 +869,186 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32, (SMAX <= 4 ? 3 : (SMAX <= 8 ?
     }
 }
 
+// ------------------------------------------------------------------ a4: hybrid graph search
+// Work lists from an explicit pair array (the lists marked for a full scan).
+__global__ void k_count_from(const uint32_t* __restrict__ src, const int64_t* __restrict__ nsrc,
+                             const int32_t* __restrict__ probes, int32_t* __restrict__ cnt) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= *nsrc) return;
+    atomicAdd(&cnt[probes[src[i]]], 1);
+}
+
+__global__ void k_fill_from(const uint32_t* __restrict__ src, const int64_t* __restrict__ nsrc,
+                            const int32_t* __restrict__ probes, const int64_t* __restrict__ pair_off,
+                            int32_t* __restrict__ fill, uint32_t* __restrict__ dst) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= *nsrc) return;
+    const uint32_t e = src[i];
+    const int p = probes[e];
+    dst[pair_off[p] + atomicAdd(&fill[p], 1)] = e;
+}
+
+struct GraphArgs {
+    const int32_t* nbr_pos;    // [nslots x 32] neighbour list positions, -1 padding
+    const uint8_t* nbr_codes;  // [nslots x M x 16] neighbour codes as one block per node
+    const int32_t* entry_pos;  // [L]
+    int efs, tau, vwords;
+    uint32_t* full_pairs;      // out: (query, rank) pairs whose list is scanned fully
+    int64_t* nfull;            // out: their count
+};
+
+constexpr int GS_WARPS = 4;
+constexpr int GS_N = 128;  // W (<= efs <= 96) plus 32 new keys, sorted together
+
+// 32 distances of one block for the lane group of the whole warp (G = 32):
+// lane l receives vector l's sum.
+template <int SMAX>
+__device__ __forceinline__ uint32_t block_sums32(const uint4* __restrict__ cp, const uint4 (&t)[SMAX], int M,
+                                                 int lane) {
+    uint32_t acc[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) acc[m] = 0;
+#pragma unroll
+    for (int u = 0; u < SMAX; ++u) {
+        const int j = lane + 32 * u;
+        if (j < M) accum_chunk(__ldg(cp + j), t[u], acc);
+    }
+    uint32_t out[1];
+    reduce_scatter<32>(acc, lane, out);
+    return out[0];
+}
+
+// One warp per (query, distant list): best-first search of the list's graph
+// with result set W of capacity efs (Sec. 4.4).  W is kept sorted in shared
+// memory with, per entry, its list position and whether it was expanded; an
+// expansion takes the smallest unexpanded entry, computes its 32
+// neighbours' keys with one LUT16 block, marks them visited, and keeps the
+// efs smallest of W and the unvisited neighbours.  The search ends when every
+// entry of W is expanded (equivalently: the best candidate is worse than
+// W's worst once W is full).  Then, with theta the query's threshold: at
+// least tau keys of W below theta -> the list is scanned fully later;
+// otherwise W's keys at or below theta join the candidates.
+template <int SMAX>
+__global__ void __launch_bounds__(GS_WARPS * 32) k_graph_search(ScanArgs A, ScanOut O, GraphArgs Gr,
+                                                                const uint32_t* __restrict__ pairs,
+                                                                const int64_t* __restrict__ npairs) {
+    extern __shared__ __align__(16) uint8_t gsm[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const size_t per_warp = (size_t)GS_N * 16 + (size_t)Gr.vwords * 4;
+    uint8_t* base_w = gsm + warp * per_warp;
+    uint64_t* wk = reinterpret_cast<uint64_t*>(base_w);             // keys
+    int32_t* wp = reinterpret_cast<int32_t*>(base_w + GS_N * 8);    // list positions
+    uint32_t* wf = reinterpret_cast<uint32_t*>(base_w + GS_N * 12); // expanded flags
+    uint32_t* vis = reinterpret_cast<uint32_t*>(base_w + GS_N * 16);
+    const int M = A.M;
+    const int64_t n_items = *npairs;
+    for (int64_t it = (int64_t)blockIdx.x * GS_WARPS + warp; it < n_items; it += (int64_t)gridDim.x * GS_WARPS) {
+        const uint32_t e = pairs[it];
+        const int64_t q = e / A.Pmax;
+        const int p = A.probes[e];
+        const int np_ = A.list_n[p];
+        const int ep = Gr.entry_pos[p];
+        if (ep < 0) continue;
+        uint4 t[SMAX];
+        const uint4* lp = reinterpret_cast<const uint4*>(A.lut + (int64_t)e * M * PQ_K);
+#pragma unroll
+        for (int u = 0; u < SMAX; ++u) {
+            const int j = lane + 32 * u;
+            t[u] = j < M ? __ldg(lp + j) : make_uint4(0, 0, 0, 0);
+        }
+        const int32_t bias = A.bias[e];
+        const uint64_t th = O.thr[q];
+        const int64_t slot0 = A.boff[p] * 32;
+        for (int w = lane; w < (np_ + 31) / 32; w += 32) vis[w] = 0u;
+        __syncwarp();
+        // entry: its block's 32 sums, keep the entry's
+        {
+            const int64_t gb = A.boff[p] + (ep >> 5);
+            const uint32_t sum = block_sums32<SMAX>(reinterpret_cast<const uint4*>(A.codes + gb * M * 16), t, M, lane);
+            if (lane == (ep & 31)) {
+                wk[0] = make_key(bias + (int32_t)sum, A.ids[slot0 + ep]);
+                wp[0] = ep;
+                wf[0] = 0;
+                vis[ep >> 5] = 1u << (ep & 31);
+            }
+            __syncwarp();
+        }
+        int wn = 1;
+        for (int guard = 0; guard <= np_; ++guard) {
+            // smallest unexpanded entry of the sorted W
+            int ui = -1;
+            for (int c = 0; c < wn && ui < 0; c += 32) {
+                const bool un = (c + lane < wn) && wf[c + lane] == 0;
+                const unsigned b = __ballot_sync(0xffffffffu, un);
+                if (b) ui = c + __ffs(b) - 1;
+            }
+            if (ui < 0) break;
+            const int upos = wp[ui];
+            __syncwarp();
+            if (lane == 0) wf[ui] = 1;
+            // expand: the 32 neighbours' keys in one block
+            const int64_t su = slot0 + upos;
+            const uint32_t sum =
+                block_sums32<SMAX>(reinterpret_cast<const uint4*>(Gr.nbr_codes + su * M * 16), t, M, lane);
+            const int pe = Gr.nbr_pos[su * 32 + lane];
+            uint64_t kn = KEY_NONE;
+            if (pe >= 0) {
+                const uint32_t bit = 1u << (pe & 31);
+                const uint32_t old = atomicOr(&vis[pe >> 5], bit);
+                if (!(old & bit)) kn = make_key(bias + (int32_t)sum, A.ids[slot0 + pe]);
+            }
+            wk[wn + lane] = kn;
+            wp[wn + lane] = pe;
+            wf[wn + lane] = 0;
+            // sort W and the new keys together; keep the efs smallest
+            const int N = wn + 32;
+            const int S = N <= 64 ? 64 : GS_N;
+            for (int i = N + lane; i < S; i += 32) wk[i] = KEY_NONE;
+            __syncwarp();
+            for (int k2 = 2; k2 <= S; k2 <<= 1)
+                for (int j = k2 >> 1; j > 0; j >>= 1) {
+                    for (int i = lane; i < S; i += 32) {
+                        const int ixj = i ^ j;
+                        if (ixj > i) {
+                            const uint64_t a = wk[i], b2 = wk[ixj];
+                            const bool up = (i & k2) == 0;
+                            if ((a > b2) == up) {
+                                wk[i] = b2;
+                                wk[ixj] = a;
+                                const int32_t tp = wp[i];
+                                wp[i] = wp[ixj];
+                                wp[ixj] = tp;
+                                const uint32_t tf = wf[i];
+                                wf[i] = wf[ixj];
+                                wf[ixj] = tf;
+                            }
+                        }
+                    }
+                    __syncwarp();
+                }
+            int valid = 0;
+            for (int c = 0; c < S; c += 32) valid += __popc(__ballot_sync(0xffffffffu, c + lane < S && wk[c + lane] != KEY_NONE));
+            wn = min(valid, Gr.efs);
+        }
+        // decide: full scan later, or W's keys join the candidates
+        int good = 0;
+        for (int c = 0; c < wn; c += 32) good += __popc(__ballot_sync(0xffffffffu, c + lane < wn && wk[c + lane] < th));
+        if (good >= Gr.tau) {
+            if (lane == 0) Gr.full_pairs[atomicAdd(reinterpret_cast<unsigned long long*>(Gr.nfull), 1ull)] = e;
+        } else {
+            for (int c = 0; c < wn; c += 32) {
+                const bool keep = c + lane < wn && wk[c + lane] <= th;
+                const unsigned b = __ballot_sync(0xffffffffu, keep);
+                int base = 0;
+                if (lane == 0 && b) base = atomicAdd(&O.cnt[q], __popc(b));
+                base = __shfl_sync(0xffffffffu, base, 0) + __popc(b & ((1u << lane) - 1u));
+                if (keep && base < O.cap) O.cand[q * O.cap + base] = wk[c + lane];
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // Register-only copy of the scan's lookup/accumulate instruction sequence
 // (no memory traffic): the lookup rate this formulation can reach on the GPU.
 __global__ void __launch_bounds__(128) k_lut16_peak(int iters, uint32_t seed, uint32_t* __restrict__ sink) {
@@ -1047,6 +1227,8 @@ struct Plan {
     const int32_t* rerank_q;
     int G, TB, cap;
     bool rank_exact;
+    bool hybrid;
+    int n_near, efs, tau;
 };
 
 static int choose_G(const ksc_index* ix, int64_t nq, int Pmax, int want) {
@@ -1178,7 +1360,7 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
     const int64_t nq = pl.nq;
     const int M = ix->M, L = ix->L;
     const int QG = 32 / pl.G;
-    const int rA = std::min(NEAR_RANKS, pl.Pmax);
+    const int rA = std::min(pl.hybrid ? pl.n_near : NEAR_RANKS, pl.Pmax);
     KSC_TRY(ensure(ix->ws_lut, (size_t)nq * pl.Pmax * M * PQ_K, st));
     KSC_TRY(ensure(ix->ws_bias, sizeof(int32_t) * nq * pl.Pmax, st));
     KSC_TRY(ensure(ix->ws_scale, sizeof(float) * nq, st));
@@ -1237,8 +1419,42 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
         KSC_LAUNCH_CHECK();
         ix->launches += 2;
     }
-    // 4. scan of the other lists, keeping keys at or below the threshold
+    // 4. scan of the other lists, keeping keys at or below the threshold;
+    //    hybrid: graph search of every other list first, full scans only of
+    //    the lists it marks (Sec. 4.4)
     mark(ix, 4, st);
+    if (pl.hybrid) {
+        KSC_TRY(ensure(ix->ws_full, sizeof(uint32_t) * nq * pl.Pmax + 64, st));
+        int64_t* nfull = (int64_t*)ix->ws_full.p;
+        uint32_t* full = (uint32_t*)(nfull + 2);
+        KSC_CUDA(cudaMemsetAsync(nfull, 0, sizeof(int64_t), st));
+        const int vwords = (((ix->max_list + 31) / 32) + 1) & ~1;  // even: keeps every warp's keys 8-byte aligned
+        GraphArgs Gr{ix->nbr_pos, ix->nbr_codes, ix->entry_pos, pl.efs, pl.tau, vwords, full, nfull};
+        const size_t smem = (size_t)GS_WARPS * ((size_t)GS_N * 16 + (size_t)vwords * 4);
+        KSC_CHECK_ARG(smem <= 200 * 1024, "lists too large for the hybrid search (%d members)", ix->max_list);
+        const int Sg = (M + 31) / 32;
+        const int grid = num_sms() * 8;
+        const ScanOut Og{thr, cnt, cand, pl.cap};
+#define KSC_GS(SM)                                                                                        \
+    do {                                                                                                  \
+        KSC_CUDA(cudaFuncSetAttribute(k_graph_search<SM>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                                      (int)smem));                                                        \
+        k_graph_search<SM><<<grid, GS_WARPS * 32, smem, st>>>(A, Og, Gr, wb.pairs, wb.pair_off + L);      \
+    } while (0)
+        if (Sg <= 2) KSC_GS(2);
+        else if (Sg <= 4) KSC_GS(4);
+        else KSC_GS(8);
+#undef KSC_GS
+        KSC_LAUNCH_CHECK();
+        // work list of the marked lists, then their scan
+        KSC_CUDA(cudaMemsetAsync(wb.cnt, 0, sizeof(int32_t) * L, st));
+        const int64_t nmax = nq * pl.Pmax;
+        k_count_from<<<blocks_for(nmax, 256), 256, 0, st>>>(full, nfull, probes, wb.cnt);
+        k_scan_lists<<<1, 1024, 0, st>>>(wb.cnt, ix->list_n, L, QG, pl.TB, wb.pair_off, wb.item_off, wb.fill);
+        k_fill_from<<<blocks_for(nmax, 256), 256, 0, st>>>(full, nfull, probes, wb.pair_off, wb.fill, wb.pairs);
+        KSC_LAUNCH_CHECK();
+        ix->launches += 4;
+    }
     KSC_TRY(run_scan(pl, M, A, ScanOut{thr, cnt, cand, pl.cap}, wb, L, ix->status, st));
     ix->launches++;
     // 5. the R best keys per query
@@ -1298,6 +1514,17 @@ static int make_plan(ksc_index* ix, int64_t nq, int k, int Pmax, int Rmax, const
     int cap = (opts && opts->cand_cap > 0) ? opts->cand_cap : std::max(32 * Rmax, 8192);
     pl.cap = std::max(cap, Rmax);
     pl.rank_exact = opts && opts->rank_fp32;
+    pl.hybrid = opts && opts->hybrid;
+    pl.n_near = (opts && opts->n_near > 0) ? opts->n_near : 2;
+    pl.efs = (opts && opts->efs > 0) ? opts->efs : 64;
+    pl.tau = (opts && opts->tau >= 0 && opts->hybrid) ? opts->tau : 8;
+    if (pl.hybrid) {
+        KSC_CHECK_ARG(pl.efs <= 96, "efs must be <= 96");
+        if (!ix->nbr_codes) {
+            set_error("the hybrid search needs an index built or imported with graphs");
+            return KSC_ESTATE;
+        }
+    }
     return KSC_OK;
 }
 
