@@ -118,7 +118,11 @@ typedef struct {
     int32_t efs;               /* hybrid: graph-search result capacity (64) */
     int32_t tau;               /* hybrid: full scan when >= tau results beat theta (8) */
     int32_t cand_cap;          /* candidate store per query; 0 -> max(32R, 8192) */
-    int32_t rank_fp32;         /* 1: list scores on FP32 CUDA cores instead of BF16 tensor cores */
+    int32_t rank_fp32;         /* 1: list scores on FP32 CUDA cores instead of 16-bit tensor cores */
+    int32_t precision;         /* re-rank: 0 FP32 over R; 1 BF16 rows / 2 FP8-e4m3 rows with a
+                                  per-row scale over R (the widened shortlist), then FP32
+                                  over the best rerank_final of them */
+    int32_t rerank_final;      /* precision 1/2: FP32 re-rank size; 0 -> max(k, R/2) */
 } ksc_search_opts;
 
 /* k nearest neighbours of Q_dev [nq x d] with a fixed nprobe (1..nlist) and
@@ -278,6 +282,13 @@ int ksc_profile_read(ksc_index* ix, float* ms_host, int32_t n, int32_t* launches
  * registers (no memory traffic) on every SM and returns the rate reached in
  * 10^9 lookups per second (the integer-ALU ceiling of the a3 scan).  Blocking. */
 int ksc_lut16_peak(double* glookups_host, void* stream);
+
+/* Diagnostic: distances of the pairs (query q, ids_dev[q][i]) [nq x c] in
+ * precision 0 (FP32 rows), 1 (BF16 rows) or 2 (FP8-e4m3 rows with a per-row
+ * scale), FP32 query and accumulation; out_dev [nq x c] (L2 squared distance
+ * or IP similarity; NaN for id < 0). */
+int ksc_pair_distances(ksc_index* ix, const float* Q_dev, int64_t nq, const int64_t* ids_dev, int32_t c,
+                       int32_t precision, float* out_dev, void* stream);
 
 /* Counters of the last search on this index (blocking read), stats_host[4]:
  * [0] queries whose candidate store overflowed (redone exactly),

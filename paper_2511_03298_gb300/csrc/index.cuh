@@ -36,6 +36,9 @@ struct ksc_index {
     int32_t* nbr_pos = nullptr;    // [nblocks x 32 x 32] neighbours as list positions
     uint8_t* nbr_codes = nullptr;  // [nblocks x 32 x M x 16] neighbour codes, one block per node
     int32_t* entry_pos = nullptr;  // [L] graph entry as a list position
+    void* X_bf16 = nullptr;        // [n x d] BF16 rows (precision variant, made on first use)
+    void* X_fp8 = nullptr;         // [n x d] FP8 e4m3 rows
+    float* X_scale = nullptr;      // [n] their per-row scales
     int32_t* status = nullptr;     // device status word
     unsigned long long* stats = nullptr;  // [4] counters of the last search
     // host mirrors
@@ -56,7 +59,7 @@ struct ksc_index {
     int32_t launches = 0;
     // search workspace
     ksc::Buffer ws_scores, ws_probes, ws_lut, ws_bias, ws_scale, ws_range, ws_thr, ws_cnt,
-        ws_cand, ws_topr, ws_nprobe, ws_rerank, ws_items, ws_misc, ws_qbf16, ws_err, ws_feat, ws_rscore, ws_full;
+        ws_cand, ws_topr, ws_nprobe, ws_rerank, ws_items, ws_misc, ws_qbf16, ws_err, ws_feat, ws_rscore, ws_full, ws_topr2;
 };
 
 namespace ksc {

@@ -14,6 +14,9 @@
 #include <cstdio>
 #include <vector>
 
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
 #include "index.cuh"
 
 namespace ksc {
@@ -1201,6 +1204,100 @@ __global__ void __launch_bounds__(256) k_rerank(const float* __restrict__ Q, con
     }
 }
 
+// ------------------------------------------------------------------ precision variant
+// Low-precision copies of X for the widened first re-rank: BF16 rows, or FP8
+// e4m3 rows with one FP32 scale per row (x ~ fp8(x / s) * s, s = max|x| / 448).
+__global__ void k_x_lowp(const float* __restrict__ X, int64_t n, int d, int prec, uint16_t* __restrict__ xb,
+                         uint8_t* __restrict__ x8, float* __restrict__ sc) {
+    const int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= n) return;
+    const float* x = X + r * d;
+    if (prec == 1) {
+        for (int t = lane; t < d; t += 32) xb[r * d + t] = __bfloat16_as_ushort(__float2bfloat16_rn(x[t]));
+        return;
+    }
+    float mx = 0.f;
+    for (int t = lane; t < d; t += 32) mx = fmaxf(mx, fabsf(x[t]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const float s = mx > 0.f ? mx / 448.f : 1.f;
+    if (lane == 0) sc[r] = s;
+    for (int t = lane; t < d; t += 32)
+        x8[r * d + t] = (uint8_t)__nv_cvt_float_to_fp8(x[t] / s, __NV_SATFINITE, __NV_E4M3);
+}
+
+__device__ __forceinline__ float lowp_elem(int prec, const uint16_t* xb, const uint8_t* x8, int64_t off) {
+    if (prec == 1) return __bfloat162float(__ushort_as_bfloat16(xb[off]));
+    __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)x8[off], __NV_E4M3);
+    return __half2float(__half(h));
+}
+
+// Distance of query row qs (shared) to row id in the given precision (0 FP32,
+// 1 BF16, 2 FP8 with row scale); one warp, result in every lane.
+__device__ __forceinline__ float lowp_dist(int prec, const float* __restrict__ qs, const float* __restrict__ X,
+                                           const uint16_t* __restrict__ xb, const uint8_t* __restrict__ x8,
+                                           const float* __restrict__ sc, int32_t id, int d, int ip, int lane) {
+    float acc = 0.f;
+    const float s = prec == 2 ? sc[id] : 1.f;
+    for (int t = lane; t < d; t += 32) {
+        const float xv = prec == 0 ? __ldg(X + (int64_t)id * d + t) : lowp_elem(prec, xb, x8, (int64_t)id * d + t) * s;
+        if (ip) acc = fmaf(qs[t], xv, acc);
+        else { const float e = qs[t] - xv; acc = fmaf(e, e, acc); }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return ip ? -acc : acc;
+}
+
+// Widened first re-rank: the R_w candidates (topr) by low-precision
+// distance, the best Rf of them (by (distance, id)) written as keys to out.
+__global__ void __launch_bounds__(256) k_rerank_lowp(const float* __restrict__ Q, int d, int ip, int prec,
+                                                     const uint16_t* __restrict__ xb, const uint8_t* __restrict__ x8,
+                                                     const float* __restrict__ sc, const uint64_t* __restrict__ topr,
+                                                     int Rmax, const int32_t* __restrict__ rerank_q, int Rfix,
+                                                     int Rmin, int Rf, uint64_t* __restrict__ out) {
+    extern __shared__ uint64_t keys[];
+    __shared__ __align__(16) float qs[KSC_MAX_DIM];
+    const int64_t q = blockIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int R = rerank_of(rerank_q, Rfix, Rmin, Rmax, q);
+    for (int t = threadIdx.x; t < d; t += blockDim.x) qs[t] = Q[q * d + t];
+    __syncthreads();
+    const uint64_t* cq = topr + q * Rmax;
+    for (int c = w; c < R; c += nw) {
+        const uint64_t kk = cq[c];
+        uint64_t o = KEY_NONE;
+        if (kk != KEY_NONE) {
+            const int32_t id = (int32_t)(kk & 0xffffffffu);
+            o = ((uint64_t)ordered_f32(lowp_dist(prec, qs, nullptr, xb, x8, sc, id, d, ip, lane)) << 32) | (uint32_t)id;
+        }
+        if (lane == 0) keys[c] = o;
+    }
+    const int S = pow2_ceil(R < 2 ? 2 : R);
+    for (int i = R + threadIdx.x; i < S; i += blockDim.x) keys[i] = KEY_NONE;
+    __syncthreads();
+    block_bitonic_sort(keys, S);
+    for (int i = threadIdx.x; i < Rf; i += blockDim.x) out[q * Rf + i] = i < R ? keys[i] : KEY_NONE;
+}
+
+// Diagnostic: distances of given (query, id) pairs in a precision.
+__global__ void k_pair_dist(const float* __restrict__ Q, int64_t nq, int d, int ip, int prec,
+                            const float* __restrict__ X, const uint16_t* __restrict__ xb,
+                            const uint8_t* __restrict__ x8, const float* __restrict__ sc,
+                            const int64_t* __restrict__ ids, int c, float* __restrict__ out) {
+    __shared__ __align__(16) float qs[KSC_MAX_DIM];
+    const int64_t q = blockIdx.x;
+    for (int t = threadIdx.x; t < d; t += blockDim.x) qs[t] = Q[q * d + t];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = w; i < c; i += nw) {
+        const int64_t id = ids[q * c + i];
+        const float v = id >= 0 ? lowp_dist(prec, qs, X, xb, x8, sc, (int32_t)id, d, ip, lane) : NAN;
+        if (lane == 0) out[q * c + i] = ip ? -v : v;
+    }
+}
+
 __global__ void k_copy_cands(const uint64_t* __restrict__ topr, int Rmax, int64_t nq, int R,
                              uint64_t* __restrict__ out) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1229,6 +1326,7 @@ struct Plan {
     bool rank_exact;
     bool hybrid;
     int n_near, efs, tau;
+    int prec, Rf;  // precision variant: first re-rank of R (= Rmax) in prec, then FP32 of the best Rf
 };
 
 static int choose_G(const ksc_index* ix, int64_t nq, int Pmax, int want) {
@@ -1319,6 +1417,24 @@ static int compute_luts(ksc_index* ix, const float* Q, int64_t nq, const int32_t
               ix->codebook, ix->L};
     KSC_TRY(launch_luts(A, rb, lut, bias, scale, st));
     ix->launches += 2;
+    return KSC_OK;
+}
+
+// BF16 / FP8 copies of X, made on first use.
+static int ensure_lowp(ksc_index* ix, int prec, cudaStream_t st) {
+    if (prec == 1 && !ix->X_bf16) {
+        KSC_CUDA(cudaMalloc(&ix->X_bf16, sizeof(uint16_t) * ix->n * ix->d));
+        k_x_lowp<<<(unsigned)((ix->n + 7) / 8), 256, 0, st>>>(ix->X, ix->n, ix->d, 1, (uint16_t*)ix->X_bf16, nullptr,
+                                                              nullptr);
+        KSC_LAUNCH_CHECK();
+    }
+    if (prec == 2 && !ix->X_fp8) {
+        KSC_CUDA(cudaMalloc(&ix->X_fp8, (size_t)ix->n * ix->d));
+        KSC_CUDA(cudaMalloc(&ix->X_scale, sizeof(float) * ix->n));
+        k_x_lowp<<<(unsigned)((ix->n + 7) / 8), 256, 0, st>>>(ix->X, ix->n, ix->d, 2, nullptr, (uint8_t*)ix->X_fp8,
+                                                              ix->X_scale);
+        KSC_LAUNCH_CHECK();
+    }
     return KSC_OK;
 }
 
@@ -1472,13 +1588,33 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
         ix->launches++;
         KSC_LAUNCH_CHECK();
     }
-    // 6. exact rerank
+    // 6. exact rerank (precision variant: a BF16 / FP8 re-rank of the widened
+    //    shortlist first, then FP32 of its best Rf)
     mark(ix, 6, st);
-    {
+    const uint64_t* rr_keys = topr;
+    int rr_R = pl.Rmax;
+    const int32_t* rr_q = pl.rerank_q;
+    if (pl.prec > 0) {
+        KSC_TRY(ensure_lowp(ix, pl.prec, st));
+        KSC_TRY(ensure(ix->ws_topr2, sizeof(uint64_t) * nq * pl.Rf, st));
+        uint64_t* topr2 = (uint64_t*)ix->ws_topr2.p;
         const size_t smem = sizeof(uint64_t) * pow2_ceil(pl.Rmax < 2 ? 2 : pl.Rmax);
+        cudaFuncSetAttribute(k_rerank_lowp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_rerank_lowp<<<(unsigned)nq, 256, smem, st>>>(Q, ix->d, ix->metric == KSC_IP, pl.prec,
+                                                       (const uint16_t*)ix->X_bf16, (const uint8_t*)ix->X_fp8,
+                                                       ix->X_scale, topr, pl.Rmax, pl.rerank_q, pl.Rfix, pl.k, pl.Rf,
+                                                       topr2);
+        KSC_LAUNCH_CHECK();
+        ix->launches++;
+        rr_keys = topr2;
+        rr_R = pl.Rf;
+        rr_q = nullptr;
+    }
+    {
+        const size_t smem = sizeof(uint64_t) * pow2_ceil(rr_R < 2 ? 2 : rr_R);
         cudaFuncSetAttribute(k_rerank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_rerank<<<(unsigned)nq, 256, smem, st>>>(Q, ix->X, ix->d, ix->metric == KSC_IP, topr, pl.Rmax, pl.rerank_q,
-                                                  pl.Rfix, pl.k, ids, dists);
+        k_rerank<<<(unsigned)nq, 256, smem, st>>>(Q, ix->X, ix->d, ix->metric == KSC_IP, rr_keys, rr_R, rr_q, rr_R,
+                                                  pl.k, ids, dists);
         ix->launches++;
         KSC_LAUNCH_CHECK();
     }
@@ -1514,6 +1650,13 @@ static int make_plan(ksc_index* ix, int64_t nq, int k, int Pmax, int Rmax, const
     int cap = (opts && opts->cand_cap > 0) ? opts->cand_cap : std::max(32 * Rmax, 8192);
     pl.cap = std::max(cap, Rmax);
     pl.rank_exact = opts && opts->rank_fp32;
+    pl.prec = opts ? opts->precision : 0;
+    KSC_CHECK_ARG(pl.prec >= 0 && pl.prec <= 2, "precision must be 0 (FP32), 1 (BF16) or 2 (FP8)");
+    pl.Rf = pl.Rmax;
+    if (pl.prec > 0) {
+        const int rf = (opts->rerank_final > 0) ? opts->rerank_final : std::max(k, Rmax / 2);
+        pl.Rf = std::min(std::max(rf, k), Rmax);
+    }
     pl.hybrid = opts && opts->hybrid;
     pl.n_near = (opts && opts->n_near > 0) ? opts->n_near : 2;
     pl.efs = (opts && opts->efs > 0) ? opts->efs : 64;
@@ -1671,6 +1814,21 @@ int ksc_lut16_peak(double* glookups_host, void* stream) {
     cudaFree(sink);
     KSC_CUDA(err);
     *glookups_host = (double)grid * 128 * iters * 32 / (ms * 1e-3) / 1e9;
+    return KSC_OK;
+}
+
+int ksc_pair_distances(ksc_index* ix, const float* Q_dev, int64_t nq, const int64_t* ids_dev, int32_t c,
+                       int32_t precision, float* out_dev, void* stream) {
+    KSC_CHECK_ARG(ix, "null index");
+    KSC_CHECK_ARG(precision >= 0 && precision <= 2, "precision must be 0, 1 or 2");
+    if (nq == 0 || c == 0) return KSC_OK;
+    KSC_CHECK_ARG(Q_dev && ids_dev && out_dev && c > 0, "bad argument");
+    cudaStream_t st = as_stream(stream);
+    KSC_TRY(ensure_lowp(ix, precision, st));
+    k_pair_dist<<<(unsigned)nq, 256, 0, st>>>(Q_dev, nq, ix->d, ix->metric == KSC_IP, precision, ix->X,
+                                              (const uint16_t*)ix->X_bf16, (const uint8_t*)ix->X_fp8, ix->X_scale,
+                                              ids_dev, c, out_dev);
+    KSC_LAUNCH_CHECK();
     return KSC_OK;
 }
 

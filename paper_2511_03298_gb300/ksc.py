@@ -51,7 +51,8 @@ class TrainOpts(C.Structure):
 
 class SearchOpts(C.Structure):
     _fields_ = [("lanes_per_query", C.c_int32), ("hybrid", C.c_int32), ("n_near", C.c_int32),
-                ("efs", C.c_int32), ("tau", C.c_int32), ("cand_cap", C.c_int32), ("rank_fp32", C.c_int32)]
+                ("efs", C.c_int32), ("tau", C.c_int32), ("cand_cap", C.c_int32), ("rank_fp32", C.c_int32),
+                ("precision", C.c_int32), ("rerank_final", C.c_int32)]
 
 
 _vp, _i32, _i64 = C.c_void_p, C.c_int32, C.c_int64
@@ -70,6 +71,7 @@ _SIGS = {
     "ksc_compute_luts_noalloc": [_vp, _vp, _i64, _vp, _i32, _vp, _vp, _vp, _vp],
     "ksc_last_status": [_vp, _vp],
     "ksc_search_stats": [_vp, _vp],
+    "ksc_pair_distances": [_vp, _vp, _i64, _vp, _i32, _i32, _vp, _vp],
     "ksc_profile_enable": [_vp, _i32],
     "ksc_profile_read": [_vp, _vp, _i32, _vp],
     "ksc_lut16_peak": [_vp, _vp],
@@ -137,8 +139,12 @@ def _hptr(a):
     return None if a is None else a.ctypes.data_as(C.c_void_p)
 
 
-def search_opts(lanes_per_query=0, hybrid=False, n_near=2, efs=64, tau=8, cand_cap=0, rank_fp32=False):
-    return SearchOpts(lanes_per_query, int(hybrid), n_near, efs, tau, cand_cap, int(rank_fp32))
+def search_opts(lanes_per_query=0, hybrid=False, n_near=2, efs=64, tau=8, cand_cap=0, rank_fp32=False,
+                precision=0, rerank_final=0):
+    """precision: 0 FP32 re-rank; 1 BF16 / 2 FP8 first re-rank of the widened
+    shortlist, then FP32 over the best rerank_final."""
+    return SearchOpts(lanes_per_query, int(hybrid), n_near, efs, tau, cand_cap, int(rank_fp32), precision,
+                      rerank_final)
 
 
 class Index:
@@ -308,6 +314,14 @@ class Index:
         n = C.c_int32(0)
         _check(lib().ksc_profile_read(self._h, ms, len(self.STAGES), C.byref(n)))
         return {k: ms[i] for i, k in enumerate(self.STAGES)}, n.value
+
+    def pair_distances(self, Q, ids, precision, stream=None):
+        torch = _torch()
+        out = torch.empty(ids.shape, dtype=torch.float32, device=Q.device)
+        _check(lib().ksc_pair_distances(self._h, _dptr(Q, torch.float32, "Q"), Q.shape[0],
+                                        _dptr(ids, torch.int64, "ids"), ids.shape[1], precision, _dptr(out),
+                                        _stream(stream)))
+        return out
 
     def search_stats(self):
         """Counters of the last search: overflowed queries, candidates kept, max per query."""
