@@ -123,6 +123,7 @@ typedef struct {
                                   per-row scale over R (the widened shortlist), then FP32
                                   over the best rerank_final of them */
     int32_t rerank_final;      /* precision 1/2: FP32 re-rank size; 0 -> max(k, R/2) */
+    int32_t tile_blocks;       /* scan: 32-vector blocks per work item; 0 auto */
 } ksc_search_opts;
 
 /* k nearest neighbours of Q_dev [nq x d] with a fixed nprobe (1..nlist) and
@@ -149,6 +150,39 @@ int ksc_search_with_probes(ksc_index* ix, const float* Q_dev, int64_t nq, const 
                            int32_t P, int32_t k, int32_t rerank, int64_t* ids_dev, float* dists_dev,
                            uint64_t* cand_dev, int32_t* ncand_dev,
                            const ksc_search_opts* opts, void* stream);
+
+/* ------------------------------------------------------------------ */
+/* Batched execution: captured plans and the autotuner                 */
+/* ------------------------------------------------------------------ */
+/* A plan fixes an index, batch size nq, k, nprobe, rerank and options,
+ * warms the index workspace and captures the whole search (every kernel and
+ * memset) into one CUDA graph that reads its queries from, and writes its
+ * results to, plan-owned device buffers.  adaptive = 1 captures
+ * ksc_search_adaptive (nprobe/rerank then ignored).  `stream` must not be the
+ * legacy default stream (capture is not allowed there).  Blocking. */
+typedef struct ksc_plan ksc_plan;
+int ksc_plan_create(ksc_index* ix, int64_t nq, int32_t k, int32_t nprobe, int32_t rerank, int32_t adaptive,
+                    const ksc_search_opts* opts, void* stream, ksc_plan** out);
+
+/* Replay a plan on `stream`: Q_dev [nq x d] is copied into the plan's input
+ * buffer (skipped when it is that buffer), the graph is launched and the
+ * results are copied to ids_dev / dists_dev (skipped when NULL or the plan's
+ * own buffers).  If the index workspace was reallocated since the capture
+ * (another search with larger shapes), the plan re-captures first. */
+int ksc_plan_execute(ksc_plan* plan, const float* Q_dev, int64_t* ids_dev, float* dists_dev, void* stream);
+
+/* The plan's own device buffers (input queries, output ids / distances). */
+int ksc_plan_buffers(ksc_plan* plan, float** Q_dev, int64_t** ids_dev, float** dists_dev);
+
+void ksc_plan_free(ksc_plan* plan);
+
+/* Autotuner: times the scan's lanes-per-query (8/16/32) and tile length
+ * (auto, 8, 16, 32, 64 blocks) on the batch Q_dev [nq x d] with the given k,
+ * nprobe, rerank and options, and writes the fastest into
+ * opts_inout->lanes_per_query / tile_blocks; *best_ms_host (may be NULL)
+ * receives its time per search.  Blocking. */
+int ksc_autotune(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t k, int32_t nprobe, int32_t rerank,
+                 ksc_search_opts* opts_inout, void* stream, float* best_ms_host);
 
 /* Step a1 alone (TopNClusters of Alg. 2): the P best lists per query,
  * probes_dev [nq x P] int32, scores_dev [nq x P] fp32 (L2 distance to the

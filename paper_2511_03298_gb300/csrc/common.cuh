@@ -277,6 +277,8 @@ struct Buffer {
     size_t bytes = 0;
 };
 int ensure(Buffer& b, size_t bytes, cudaStream_t st);
+// Count of workspace reallocations so far (captured plans compare it).
+unsigned long long workspace_generation();
 void release(Buffer& b);
 
 int num_sms();

@@ -5,6 +5,7 @@
 // K = 16 per subspace on residuals (Sec. 2.3), encoding, block packing
 // (Alg. 1 BuildBlocks).  All on the GPU in FP32 (sums in FP64); the list
 // ordering (a counting sort of the assignment) runs on the host.
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -25,8 +26,12 @@ void set_error(const char* fmt, ...) {
 }
 const char* get_error() { return g_err; }
 
+static std::atomic<unsigned long long> g_ws_gen{0};
+unsigned long long workspace_generation() { return g_ws_gen.load(); }
+
 int ensure(Buffer& b, size_t bytes, cudaStream_t st) {
     if (bytes <= b.bytes && b.p) return KSC_OK;
+    g_ws_gen++;
     if (b.p) {
         KSC_CUDA(cudaStreamSynchronize(st));
         KSC_CUDA(cudaFree(b.p));

@@ -20,7 +20,8 @@ namespace ksc {
 
 constexpr int MLP_F = 64, MLP_H = 64, MLP_O = 2, MLP_FEAT_K = 32;
 constexpr int MLP_NPARAM = MLP_H * MLP_F + MLP_H + MLP_H * MLP_H + MLP_H + MLP_O * MLP_H + MLP_O;
-constexpr int MLP_TILE = 128;  // samples per CTA
+constexpr int MLP_TILE = 128;  // samples per CTA (training)
+constexpr int MLP_ITILE = 16;  // queries per CTA (inference: many CTAs for a batch)
 
 struct MlpW {  // views into a packed parameter vector (same packing as the oracle)
     const float *W1, *b1, *W2, *b2, *W3, *b3;
@@ -205,10 +206,10 @@ __global__ void __launch_bounds__(256) k_mlp_infer(const float* __restrict__ w, 
     extern __shared__ float sm[];
     float* sw = sm;
     float* X = sw + MLP_NPARAM;
-    float* H1 = X + MLP_TILE * MLP_F;
-    float* H2 = H1 + MLP_TILE * MLP_H;
-    const int64_t r0 = (int64_t)blockIdx.x * MLP_TILE;
-    const int rows = (int)(B - r0 < MLP_TILE ? B - r0 : MLP_TILE);
+    float* H1 = X + MLP_ITILE * MLP_F;
+    float* H2 = H1 + MLP_ITILE * MLP_H;
+    const int64_t r0 = (int64_t)blockIdx.x * MLP_ITILE;
+    const int rows = (int)(B - r0 < MLP_ITILE ? B - r0 : MLP_ITILE);
     for (int e = threadIdx.x; e < MLP_NPARAM; e += blockDim.x) sw[e] = bf(w[e]);
     for (int e = threadIdx.x; e < rows * MLP_F; e += blockDim.x) X[e] = bf(x[r0 * MLP_F + e]);
     __syncthreads();
@@ -251,7 +252,7 @@ __global__ void k_hits(const float* __restrict__ dists, int64_t nq, int k, const
 }
 
 static size_t grad_smem() { return sizeof(float) * (MLP_NPARAM + MLP_TILE * (MLP_F + 3 * MLP_H + MLP_O)); }
-static size_t infer_smem() { return sizeof(float) * (MLP_NPARAM + MLP_TILE * (MLP_F + 2 * MLP_H)); }
+static size_t infer_smem() { return sizeof(float) * (MLP_NPARAM + MLP_ITILE * (MLP_F + 2 * MLP_H)); }
 
 int mlp_grad(const float* w, const float* x, const float* y, int64_t B, float* grad, float* loss, cudaStream_t st) {
     KSC_CUDA(cudaMemsetAsync(grad, 0, sizeof(float) * MLP_NPARAM, st));
@@ -265,8 +266,8 @@ int mlp_grad(const float* w, const float* x, const float* y, int64_t B, float* g
 int mlp_infer(const float* w, const float* x, int64_t B, const ksc_adaptive_params& prm, float* prob,
               int32_t* nprobe, int32_t* rerank, cudaStream_t st) {
     KSC_CUDA(cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)infer_smem()));
-    k_mlp_infer<<<(unsigned)((B + MLP_TILE - 1) / MLP_TILE), 256, infer_smem(), st>>>(w, x, B, prm, prob, nprobe,
-                                                                                      rerank);
+    k_mlp_infer<<<(unsigned)((B + MLP_ITILE - 1) / MLP_ITILE), 256, infer_smem(), st>>>(w, x, B, prm, prob, nprobe,
+                                                                                        rerank);
     KSC_LAUNCH_CHECK();
     return KSC_OK;
 }

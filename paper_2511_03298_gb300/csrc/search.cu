@@ -385,6 +385,90 @@ __global__ void __launch_bounds__(256) k_lut_quant(LutArgs A, const uint32_t* __
     }
 }
 
+// One CTA per query when all of its tables fit in shared memory: the FP32
+// tables of its P_q probes are computed once, their largest range gives the
+// scale, and they are quantised from shared memory (same FP32 rule, same
+// results as the two-pass kernels above).
+__global__ void __launch_bounds__(256) k_lut_fused(LutArgs A, int Pb, uint8_t* __restrict__ lut,
+                                                   int32_t* __restrict__ bias, float* __restrict__ scale) {
+    extern __shared__ float fsm[];
+    const int M = A.M;
+    const int ld = PQ_K * A.dsub + 1;
+    float* cbs = fsm;                                  // M x ld
+    float* T = cbs + M * ld;                           // Pb x M rows of 16, stride 17 (no bank conflicts)
+    float* mins = T + (size_t)Pb * M * (PQ_K + 1);     // Pb x M
+    float* qs = mins + Pb * M;                         // d
+    __shared__ float s_range;
+    __shared__ uint32_t s_rbits;
+    const int64_t q = blockIdx.x;
+    const int P = min(probes_of(A, q), Pb);
+    stage_codebook(A, cbs);  // ends with __syncthreads
+    for (int t = threadIdx.x; t < A.d; t += blockDim.x) qs[t] = A.Q[q * A.d + t];
+    if (threadIdx.x == 0) s_rbits = 0u;
+    __syncthreads();
+    float R = 0.f;
+    for (int row = threadIdx.x; row < P * M; row += blockDim.x) {
+        const int r = row / M, j = row - r * M;
+        const int p = A.probes[q * A.Pmax + r];
+        float* Tr = T + (size_t)row * (PQ_K + 1);
+        if (p < 0 || p >= A.L) {
+            for (int i = 0; i < PQ_K; ++i) Tr[i] = 0.f;
+            mins[row] = 0.f;
+            continue;
+        }
+        float Tv[PQ_K];
+        lut_row(A, qs, A.c_mean + (int64_t)p * A.d, cbs, ld, j, Tv);
+        float mn = Tv[0], mx = Tv[0];
+#pragma unroll
+        for (int i = 0; i < PQ_K; ++i) {
+            mn = fminf(mn, Tv[i]);
+            mx = fmaxf(mx, Tv[i]);
+            Tr[i] = Tv[i];
+        }
+        mins[row] = mn;
+        R = fmaxf(R, __fsub_rn(mx, mn));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) R = fmaxf(R, __shfl_xor_sync(0xffffffffu, R, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(&s_rbits, __float_as_uint(R));
+    __syncthreads();
+    const float Rq = __uint_as_float(s_rbits);
+    const float a = (Rq == 0.f) ? 1.f : __fdiv_rn(255.f, Rq);
+    for (int row = threadIdx.x; row < P * M; row += blockDim.x) {
+        const int r = row / M, j = row - r * M;
+        const float* Tr = T + (size_t)row * (PQ_K + 1);
+        const float mn = mins[row];
+        uint32_t w[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int i = 0; i < PQ_K; ++i) {
+            const float f = floorf(__fadd_rn(__fmul_rn(__fsub_rn(Tr[i], mn), a), 0.5f));
+            w[i >> 2] |= (uint32_t)(f > 255.f ? 255.f : f) << (8 * (i & 3));
+        }
+        reinterpret_cast<uint4*>(lut + (q * A.Pmax + r) * (int64_t)M * PQ_K)[j] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    for (int r = threadIdx.x; r < P; r += blockDim.x) {
+        const int p = A.probes[q * A.Pmax + r];
+        if (p < 0 || p >= A.L) continue;
+        float S = 0.f;
+        if (A.ip) {
+            const float* cp = A.c_mean + (int64_t)p * A.d;
+            float dot = 0.f;
+            for (int t = 0; t < A.d; ++t) dot = __fadd_rn(dot, __fmul_rn(qs[t], cp[t]));
+            S = -dot;
+        }
+        for (int j = 0; j < M; ++j) S = __fadd_rn(S, mins[r * M + j]);
+        float bf = floorf(__fadd_rn(__fmul_rn(S, a), 0.5f));
+        bf = fminf(fmaxf(bf, -1073741824.f), 1073741823.f);
+        bias[q * A.Pmax + r] = (int32_t)bf;
+    }
+    if (threadIdx.x == 0) scale[q] = a;
+    (void)s_range;
+}
+
+static size_t lut_fused_smem(int M, int dsub, int d, int Pb) {
+    return sizeof(float) * ((size_t)M * (PQ_K * dsub + 1) + (size_t)Pb * M * (PQ_K + 1) + (size_t)Pb * M + d);
+}
+
 static int launch_luts(const LutArgs& A, uint32_t* rb, uint8_t* lut, int32_t* bias, float* scale, cudaStream_t st);
 
 // ------------------------------------------------------------------ code access
@@ -1077,7 +1161,7 @@ __global__ void __launch_bounds__(128) k_lut16_peak(int iters, uint32_t seed, ui
 // R smallest candidate keys per query.  If the store overflowed, the query
 // is redone exactly: every key of every probed list is recomputed (scalar
 // lookups) inside the radix select.
-__global__ void __launch_bounds__(512) k_select(ScanArgs A, int Rmax, const int32_t* __restrict__ cnt,
+__global__ void __launch_bounds__(256) k_select(ScanArgs A, int Rmax, const int32_t* __restrict__ cnt, int sel_cap,
                                                 const uint64_t* __restrict__ cand, int cap,
                                                 uint64_t* __restrict__ topr, int32_t* __restrict__ ncand,
                                                 int32_t* __restrict__ status,
@@ -1099,7 +1183,7 @@ __global__ void __launch_bounds__(512) k_select(ScanArgs A, int Rmax, const int3
         const uint64_t* cq = cand + q * cap;
         const int K = min(R, n);
         auto load = [&](int i) -> uint64_t { return cq[i]; };
-        block_select_hist(load, n, K, out, sbuf, SEL_CAP, hist, warp_tot);
+        block_select_hist(load, n, K, out, sbuf, sel_cap, hist, warp_tot);
         for (int i = K + threadIdx.x; i < Rmax; i += blockDim.x) out[i] = KEY_NONE;
         if (threadIdx.x == 0 && ncand) ncand[q] = K;
         return;
@@ -1132,7 +1216,7 @@ __global__ void __launch_bounds__(512) k_select(ScanArgs A, int Rmax, const int3
         return make_key(D, A.ids[blk * 32 + v]);
     };
     const int K = min(R, N);
-    block_select_smallest(load, N, K, out, sbuf, SEL_CAP, hist);
+    block_select_smallest(load, N, K, out, sbuf, sel_cap, hist);
     for (int i = K + threadIdx.x; i < Rmax; i += blockDim.x) out[i] = KEY_NONE;
     if (threadIdx.x == 0 && ncand) ncand[q] = K;
 }
@@ -1154,6 +1238,37 @@ __global__ void __launch_bounds__(256) k_rerank(const float* __restrict__ Q, con
     __syncthreads();
     const uint64_t* cq = topr + q * Rmax;
     const bool vec4 = (d & 3) == 0;
+    if (vec4 && d <= 128) {
+        // one float4 per lane per row; four rows in flight per warp
+        const bool inl = lane * 4 < d;
+        const float4 qv = inl ? *reinterpret_cast<const float4*>(qs + lane * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int c0 = w * 4; c0 < R; c0 += nw * 4) {
+            float4 xv[4];
+            int32_t idv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint64_t kk = c0 + u < R ? cq[c0 + u] : KEY_NONE;
+                idv[u] = kk != KEY_NONE ? (int32_t)(kk & 0xffffffffu) : -1;
+                xv[u] = (idv[u] >= 0 && inl) ? __ldg(reinterpret_cast<const float4*>(X + (int64_t)idv[u] * d) + lane)
+                                             : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                float s = 0.f;
+                if (ip) {
+                    s = qv.x * xv[u].x + qv.y * xv[u].y + qv.z * xv[u].z + qv.w * xv[u].w;
+                } else {
+                    const float e0 = qv.x - xv[u].x, e1 = qv.y - xv[u].y, e2 = qv.z - xv[u].z, e3 = qv.w - xv[u].w;
+                    s = fmaf(e0, e0, fmaf(e1, e1, fmaf(e2, e2, e3 * e3)));
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                if (lane == 0 && c0 + u < R)
+                    keys[c0 + u] = idv[u] >= 0 ? (((uint64_t)ordered_f32(ip ? -s : s) << 32) | (uint32_t)idv[u])
+                                               : KEY_NONE;
+            }
+        }
+    } else
     for (int c = w; c < R; c += nw) {
         const uint64_t kk = cq[c];
         uint64_t outk = KEY_NONE;
@@ -1327,6 +1442,7 @@ struct Plan {
     bool hybrid;
     int n_near, efs, tau;
     int prec, Rf;  // precision variant: first re-rank of R (= Rmax) in prec, then FP32 of the best Rf
+    int Pq_max;    // bound on the per-query nprobe (<= Pmax)
 };
 
 static int choose_G(const ksc_index* ix, int64_t nq, int Pmax, int want) {
@@ -1521,8 +1637,16 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
         KSC_CUDA(cudaMemsetAsync(rb, 0, sizeof(uint32_t) * nq, st));
         LutArgs LA{Q, nq, ix->d, M, ix->dsub, ix->metric == KSC_IP, pl.Pmax, probes, pl.nprobe_q, pl.Pfix,
                    ix->c_mean, ix->codebook, ix->L, wa.pairs, wa.pair_off + L, wb.pairs, wb.pair_off + L};
-        KSC_TRY(launch_luts(LA, rb, lut, bias, scale, st));
-        ix->launches += 2;
+        const size_t fsm = lut_fused_smem(M, ix->dsub, ix->d, pl.Pq_max);
+        if (fsm <= 160 * 1024) {
+            KSC_CUDA(cudaFuncSetAttribute(k_lut_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
+            k_lut_fused<<<(unsigned)nq, 256, fsm, st>>>(LA, pl.Pq_max, lut, bias, scale);
+            KSC_LAUNCH_CHECK();
+            ix->launches++;
+        } else {
+            KSC_TRY(launch_luts(LA, rb, lut, bias, scale, st));
+            ix->launches += 2;
+        }
     }
     // 3. scan of the nearest lists with no filter, then the threshold
     mark(ix, 3, st);
@@ -1576,9 +1700,12 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
     // 5. the R best keys per query
     mark(ix, 5, st);
     {
-        const size_t smem = SEL_CAP * sizeof(uint64_t);
+        // shared buffer: the R best plus the ties of the histogram bin at the
+        // R-th key (radix select beyond it)
+        const int sel_cap = std::min(SEL_CAP, std::max(1024, pow2_ceil(2 * pl.Rmax)));
+        const size_t smem = sel_cap * sizeof(uint64_t);
         cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_select<<<(unsigned)nq, 512, smem, st>>>(A, pl.Rmax, cnt, cand, pl.cap, topr, ncand_out, ix->status,
+        k_select<<<(unsigned)nq, 256, smem, st>>>(A, pl.Rmax, cnt, sel_cap, cand, pl.cap, topr, ncand_out, ix->status,
                                                   ix->stats);
         ix->launches++;
         KSC_LAUNCH_CHECK();
@@ -1646,10 +1773,12 @@ static int make_plan(ksc_index* ix, int64_t nq, int k, int Pmax, int Rmax, const
         const double target = 64.0 * num_sms();
         int TB = (int)(blocks / target);
         pl.TB = TB < 2 ? 2 : (TB > 64 ? 64 : TB);
+        if (opts && opts->tile_blocks > 0) pl.TB = std::min(opts->tile_blocks, 1 << 20);
     }
     int cap = (opts && opts->cand_cap > 0) ? opts->cand_cap : std::max(32 * Rmax, 8192);
     pl.cap = std::max(cap, Rmax);
     pl.rank_exact = opts && opts->rank_fp32;
+    pl.Pq_max = Pmax;
     pl.prec = opts ? opts->precision : 0;
     KSC_CHECK_ARG(pl.prec >= 0 && pl.prec <= 2, "precision must be 0 (FP32), 1 (BF16) or 2 (FP8)");
     pl.Rf = pl.Rmax;
@@ -2182,6 +2311,7 @@ int ksc_search_adaptive(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t k
     ix->launches++;
     pl.nprobe_q = np_q;
     pl.rerank_q = r_q;
+    pl.Pq_max = std::min(prm.pmax, Pr);
     KSC_TRY(search_from_probes(ix, Q_dev, pl, probes, ids_dev, dists_dev, nullptr, nullptr, st));
     if (nprobe_dev) KSC_CUDA(cudaMemcpyAsync(nprobe_dev, np_q, sizeof(int32_t) * nq, cudaMemcpyDeviceToDevice, st));
     if (rerank_dev) KSC_CUDA(cudaMemcpyAsync(rerank_dev, r_q, sizeof(int32_t) * nq, cudaMemcpyDeviceToDevice, st));
@@ -2189,3 +2319,187 @@ int ksc_search_adaptive(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t k
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ captured plans, autotuner
+struct ksc_plan {
+    ksc_index* ix = nullptr;
+    int64_t nq = 0;
+    int32_t k = 0, nprobe = 0, rerank = 0, adaptive = 0;
+    ksc_search_opts opts = {};
+    bool has_opts = false;
+    float* Q = nullptr;
+    int64_t* ids = nullptr;
+    float* dists = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long gen = 0;
+};
+
+namespace ksc {
+static int plan_search(ksc_plan* pl, cudaStream_t st) {
+    const ksc_search_opts* o = pl->has_opts ? &pl->opts : nullptr;
+    if (pl->adaptive)
+        return ksc_search_adaptive(pl->ix, pl->Q, pl->nq, pl->k, pl->ids, pl->dists, nullptr, nullptr, o, st);
+    return ksc_search(pl->ix, pl->Q, pl->nq, pl->k, pl->nprobe, pl->rerank, pl->ids, pl->dists, o, st);
+}
+
+// Warm the workspace with one search, then capture the next into a graph.
+static int plan_capture(ksc_plan* pl, cudaStream_t st) {
+    if (pl->exec) { cudaGraphExecDestroy(pl->exec); pl->exec = nullptr; }
+    if (pl->graph) { cudaGraphDestroy(pl->graph); pl->graph = nullptr; }
+    const bool prof = pl->ix->prof;
+    pl->ix->prof = false;
+    int rc = plan_search(pl, st);
+    if (rc == KSC_OK) {
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) { set_error("warm-up failed: %s", cudaGetErrorString(e)); rc = KSC_ECUDA; }
+    }
+    if (rc == KSC_OK) {
+        pl->gen = workspace_generation();
+        cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            set_error("stream capture failed to start: %s", cudaGetErrorString(e));
+            rc = KSC_ECUDA;
+        } else {
+            rc = plan_search(pl, st);
+            cudaGraph_t g = nullptr;
+            e = cudaStreamEndCapture(st, &g);
+            if (rc == KSC_OK && e != cudaSuccess) {
+                set_error("stream capture failed: %s", cudaGetErrorString(e));
+                rc = KSC_ECUDA;
+            }
+            pl->graph = g;
+            if (rc == KSC_OK && workspace_generation() != pl->gen) {
+                set_error("workspace changed during capture");
+                rc = KSC_ESTATE;
+            }
+            if (rc == KSC_OK) {
+                e = cudaGraphInstantiate(&pl->exec, pl->graph, 0);
+                if (e != cudaSuccess) {
+                    set_error("graph instantiation failed: %s", cudaGetErrorString(e));
+                    rc = KSC_ECUDA;
+                }
+            }
+        }
+    }
+    pl->ix->prof = prof;
+    return rc;
+}
+}  // namespace ksc
+
+extern "C" {
+
+void ksc_plan_free(ksc_plan* pl) {
+    if (!pl) return;
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    if (pl->graph) cudaGraphDestroy(pl->graph);
+    cudaFree(pl->Q);
+    cudaFree(pl->ids);
+    cudaFree(pl->dists);
+    delete pl;
+}
+
+int ksc_plan_create(ksc_index* ix, int64_t nq, int32_t k, int32_t nprobe, int32_t rerank, int32_t adaptive,
+                    const ksc_search_opts* opts, void* stream, ksc_plan** out) {
+    KSC_CHECK_ARG(ix && out && nq > 0 && k >= 1, "bad argument");
+    KSC_CHECK_ARG(stream != nullptr, "plans need a non-default stream (graph capture)");
+    cudaStream_t st = as_stream(stream);
+    ksc_plan* pl = new ksc_plan();
+    pl->ix = ix;
+    pl->nq = nq;
+    pl->k = k;
+    pl->nprobe = nprobe;
+    pl->rerank = rerank;
+    pl->adaptive = adaptive;
+    if (opts) { pl->opts = *opts; pl->has_opts = true; }
+    int rc = KSC_OK;
+    if (cudaMalloc(&pl->Q, sizeof(float) * nq * ix->d) != cudaSuccess ||
+        cudaMalloc(&pl->ids, sizeof(int64_t) * nq * k) != cudaSuccess ||
+        cudaMalloc(&pl->dists, sizeof(float) * nq * k) != cudaSuccess) {
+        set_error("plan buffer allocation failed");
+        rc = KSC_ENOMEM;
+    }
+    if (rc == KSC_OK && cudaMemsetAsync(pl->Q, 0, sizeof(float) * nq * ix->d, st) != cudaSuccess) rc = KSC_ECUDA;
+    if (rc == KSC_OK) rc = plan_capture(pl, st);
+    if (rc != KSC_OK) {
+        ksc_plan_free(pl);
+        return rc;
+    }
+    *out = pl;
+    return KSC_OK;
+}
+
+int ksc_plan_buffers(ksc_plan* pl, float** Q_dev, int64_t** ids_dev, float** dists_dev) {
+    KSC_CHECK_ARG(pl, "null plan");
+    if (Q_dev) *Q_dev = pl->Q;
+    if (ids_dev) *ids_dev = pl->ids;
+    if (dists_dev) *dists_dev = pl->dists;
+    return KSC_OK;
+}
+
+int ksc_plan_execute(ksc_plan* pl, const float* Q_dev, int64_t* ids_dev, float* dists_dev, void* stream) {
+    KSC_CHECK_ARG(pl && pl->exec, "null plan");
+    cudaStream_t st = as_stream(stream);
+    KSC_CHECK_ARG(stream != nullptr, "plans need a non-default stream (graph capture)");
+    if (Q_dev && Q_dev != pl->Q)
+        KSC_CUDA(cudaMemcpyAsync(pl->Q, Q_dev, sizeof(float) * pl->nq * pl->ix->d, cudaMemcpyDeviceToDevice, st));
+    if (workspace_generation() != pl->gen) KSC_TRY(plan_capture(pl, st));
+    KSC_CUDA(cudaGraphLaunch(pl->exec, st));
+    if (ids_dev && ids_dev != pl->ids)
+        KSC_CUDA(cudaMemcpyAsync(ids_dev, pl->ids, sizeof(int64_t) * pl->nq * pl->k, cudaMemcpyDeviceToDevice, st));
+    if (dists_dev && dists_dev != pl->dists)
+        KSC_CUDA(cudaMemcpyAsync(dists_dev, pl->dists, sizeof(float) * pl->nq * pl->k, cudaMemcpyDeviceToDevice, st));
+    return KSC_OK;
+}
+
+int ksc_autotune(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t k, int32_t nprobe, int32_t rerank,
+                 ksc_search_opts* opts, void* stream, float* best_ms_host) {
+    KSC_CHECK_ARG(ix && Q_dev && opts && nq > 0, "bad argument");
+    cudaStream_t st = as_stream(stream);
+    int64_t* ids = nullptr;
+    float* dists = nullptr;
+    KSC_CUDA(cudaMalloc(&ids, sizeof(int64_t) * nq * k));
+    cudaError_t ea = cudaMalloc(&dists, sizeof(float) * nq * k);
+    if (ea != cudaSuccess) { cudaFree(ids); KSC_CUDA(ea); }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int Gs[3] = {8, 16, 32};
+    const int TBs[5] = {0, 8, 16, 32, 64};
+    ksc_search_opts best = *opts;
+    float best_ms = INFINITY;
+    int rc = KSC_OK;
+    for (int gi = 0; gi < 3 && rc == KSC_OK; ++gi) {
+        if ((ix->M + Gs[gi] - 1) / Gs[gi] > 16) continue;
+        for (int ti = 0; ti < 5 && rc == KSC_OK; ++ti) {
+            ksc_search_opts o = *opts;
+            o.lanes_per_query = Gs[gi];
+            o.tile_blocks = TBs[ti];
+            float ms = 0.f, tot = 0.f;
+            for (int rep = 0; rep < 4 && rc == KSC_OK; ++rep) {
+                cudaEventRecord(e0, st);
+                rc = ksc_search(ix, Q_dev, nq, k, nprobe, rerank, ids, dists, &o, st);
+                cudaEventRecord(e1, st);
+                if (cudaEventSynchronize(e1) != cudaSuccess) { set_error("autotune run failed"); rc = KSC_ECUDA; }
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep >= 1) tot += ms;  // the first run warms the workspace
+            }
+            if (rc == KSC_OK && tot / 3 < best_ms) {
+                best_ms = tot / 3;
+                best = o;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(ids);
+    cudaFree(dists);
+    if (rc != KSC_OK) return rc;
+    opts->lanes_per_query = best.lanes_per_query;
+    opts->tile_blocks = best.tile_blocks;
+    if (best_ms_host) *best_ms_host = best_ms;
+    return KSC_OK;
+}
+
+}  // extern "C"
+

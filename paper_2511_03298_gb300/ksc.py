@@ -52,7 +52,7 @@ class TrainOpts(C.Structure):
 class SearchOpts(C.Structure):
     _fields_ = [("lanes_per_query", C.c_int32), ("hybrid", C.c_int32), ("n_near", C.c_int32),
                 ("efs", C.c_int32), ("tau", C.c_int32), ("cand_cap", C.c_int32), ("rank_fp32", C.c_int32),
-                ("precision", C.c_int32), ("rerank_final", C.c_int32)]
+                ("precision", C.c_int32), ("rerank_final", C.c_int32), ("tile_blocks", C.c_int32)]
 
 
 _vp, _i32, _i64 = C.c_void_p, C.c_int32, C.c_int64
@@ -71,6 +71,11 @@ _SIGS = {
     "ksc_compute_luts_noalloc": [_vp, _vp, _i64, _vp, _i32, _vp, _vp, _vp, _vp],
     "ksc_last_status": [_vp, _vp],
     "ksc_search_stats": [_vp, _vp],
+    "ksc_plan_create": [_vp, _i64, _i32, _i32, _i32, _i32, _vp, _vp, _vp],
+    "ksc_plan_execute": [_vp, _vp, _vp, _vp, _vp],
+    "ksc_plan_buffers": [_vp, _vp, _vp, _vp],
+    "ksc_plan_free": [_vp],
+    "ksc_autotune": [_vp, _vp, _i64, _i32, _i32, _i32, _vp, _vp, _vp],
     "ksc_pair_distances": [_vp, _vp, _i64, _vp, _i32, _i32, _vp, _vp],
     "ksc_profile_enable": [_vp, _i32],
     "ksc_profile_read": [_vp, _vp, _i32, _vp],
@@ -104,6 +109,7 @@ def lib():
         L.ksc_last_error.restype = C.c_char_p
         L.ksc_version.restype = C.c_char_p
         L.ksc_index_free.restype = None
+        L.ksc_plan_free.restype = None
         _lib = L
     return _lib
 
@@ -140,11 +146,11 @@ def _hptr(a):
 
 
 def search_opts(lanes_per_query=0, hybrid=False, n_near=2, efs=64, tau=8, cand_cap=0, rank_fp32=False,
-                precision=0, rerank_final=0):
+                precision=0, rerank_final=0, tile_blocks=0):
     """precision: 0 FP32 re-rank; 1 BF16 / 2 FP8 first re-rank of the widened
     shortlist, then FP32 over the best rerank_final."""
     return SearchOpts(lanes_per_query, int(hybrid), n_near, efs, tau, cand_cap, int(rank_fp32), precision,
-                      rerank_final)
+                      rerank_final, tile_blocks)
 
 
 class Index:
@@ -303,6 +309,25 @@ class Index:
                                         _stream(stream)))
         return f
 
+    # ---------------------------------------------------------- plans, autotuner
+    def plan(self, nq, k, nprobe=1, rerank=0, adaptive=False, opts=None, stream=None):
+        """Capture a search of fixed shapes into a CUDA graph (see Plan)."""
+        torch = _torch()
+        st = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        _check(lib().ksc_plan_create(self._h, nq, k, nprobe, rerank, int(adaptive),
+                                     C.byref(opts) if opts else None, C.c_void_p(st.cuda_stream), C.byref(h)))
+        return Plan(h.value, self, nq, k)
+
+    def autotune(self, Q, k, nprobe, rerank, opts=None, stream=None):
+        """Fastest scan lanes-per-query / tile length for this batch: (opts, ms)."""
+        torch = _torch()
+        o = opts if opts is not None else search_opts()
+        ms = C.c_float(0)
+        _check(lib().ksc_autotune(self._h, _dptr(Q, torch.float32, "Q"), Q.shape[0], k, nprobe, rerank,
+                                  C.byref(o), _stream(stream), C.byref(ms)))
+        return o, ms.value
+
     STAGES = ("rank", "worklist", "lut", "near_scan", "scan", "select", "rerank")
 
     def profile(self, on=True):
@@ -333,6 +358,32 @@ class Index:
         s = C.c_int32(0)
         _check(lib().ksc_last_status(self._h, C.byref(s)))
         return s.value
+
+
+class Plan:
+    """A captured search: execute() copies queries in, replays the graph and
+    returns views of the plan's own result buffers."""
+
+    def __init__(self, handle, index, nq, k):
+        self._h = C.c_void_p(handle)
+        self.index = index  # keeps the index alive
+        self.nq, self.k = nq, k
+
+    def __del__(self):
+        if getattr(self, "_h", None) and self._h.value and _lib is not None:
+            _lib.ksc_plan_free(self._h)
+        self._h = C.c_void_p(None)
+
+    def execute(self, Q, ids=None, dists=None, stream=None):
+        torch = _torch()
+        st = stream if stream is not None else torch.cuda.current_stream()
+        if ids is None:
+            ids = torch.empty((self.nq, self.k), dtype=torch.int64, device=Q.device)
+        if dists is None:
+            dists = torch.empty((self.nq, self.k), dtype=torch.float32, device=Q.device)
+        _check(lib().ksc_plan_execute(self._h, _dptr(Q, torch.float32, "Q"), _dptr(ids), _dptr(dists),
+                                      C.c_void_p(st.cuda_stream)))
+        return ids, dists
 
 
 def build_index(X, nlist, M, nbits=4, metric="l2", spherical=False, perm=None, iters=20, seed=0x5EED,
