@@ -377,6 +377,123 @@ def cpu_baseline(ix, X, Qh, nprobe, R, k, true_d, budget_s=12.0):
                       % (n2, nprobe, R), "recall@10": round(rec, 4), "seconds": round(dt, 2)}
 
 
+def run_workload(args):
+    """Secondary workloads (one JSON line each, not the headline):
+    deep  -- 10M x 96 unit-norm, Zipf(1.1) components, nlist 8192, M 48,
+             k 100, rerank 1000, per-query nprobe U{4..256}, batches 1..16384
+             through the variable-nprobe path, plans (CUDA graphs) and the
+             autotuner; recall on a 1000-query sample.
+    glove -- 1.2M x 100 unit-norm, inner product, nlist 2048, M 50, k 10:
+             FP32 re-rank of R = 200 vs BF16 / FP8-e4m3 re-rank of a widened
+             shortlist (400, 800) before the FP32 re-rank of 100."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2511_03298_gb300 import ksc, synth
+    dev = torch.device("cuda", 0)
+    out = {"workload": args.workload, "data": "synthetic (seeded mixture)", "n_gpus": 1}
+    st = torch.cuda.Stream()
+    if args.workload == "deep":
+        c = synth.CONFIGS[4]
+        t0 = time.time()
+        X = synth.base(4)
+        gen_s = time.time() - t0
+        Xd = torch.from_numpy(X).to(dev)
+        del X
+        t0 = time.time()
+        ix = ksc.build_index(Xd, c["L"], c["M"], spherical=True, perm=synth.build_perm(4, c["n"]))
+        torch.cuda.synchronize()
+        out["build_s"] = round(time.time() - t0, 1)
+        out["gen_s"] = round(gen_s, 1)
+        k, R = c["k"], c["R"]
+        nq_max = 16384
+        Qh = synth.queries(4, nq_max)
+        Qd = torch.from_numpy(Qh).to(dev)
+        npb = torch.from_numpy(synth.per_query_nprobe(4, nq_max)).to(dev)
+        rr = torch.full((nq_max,), R, dtype=torch.int32, device=dev)
+        # recall on a sample (FP32 brute force on the GPU: measurement only)
+        ns = 1000
+        ids, _ = ix.search_varprobe(Qd[:ns], k, npb[:ns], rr[:ns], nprobe_max=256, rerank_max=R)
+        kth = kth_fp32(torch, Xd, Qd[:ns], k, chunk=64)
+        d = ((Xd[ids.clamp_min(0)] - Qd[:ns, None, :]) ** 2).sum(-1)
+        out["recall@100_sample1000"] = round(float(((d <= kth[:, None] + 1e-5) & (ids >= 0)).sum(1)
+                                                 .clamp_max(k).double().mean() / k), 4)
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        batches = {}
+        with torch.cuda.stream(st):
+            for B in (1, 16, 256, 1024, 4096, 16384):
+                q, nb = Qd[:B], npb[:B]
+                # tuned at the mean of the nprobe distribution
+                o = ix.autotune(q, k, 130, R)[0] if B >= 256 else ksc.search_opts()
+                fn = lambda: ix.search_varprobe(q, k, nb, rr[:B], nprobe_max=256, rerank_max=R, opts=o)
+                for _ in range(3):
+                    fn()
+                times = []
+                for _ in range(5):
+                    flush.zero_()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(st)
+                    fn()
+                    e1.record(st)
+                    e1.synchronize()
+                    times.append(e0.elapsed_time(e1))
+                ms = statistics.median(times)
+                ix.profile(True)
+                fn()
+                prof, _ = ix.profile_read()
+                ix.profile(False)
+                sts = ix.search_stats()
+                batches[B] = {"ms": round(ms, 4), "qps": round(B / (ms * 1e-3), 1),
+                              "candidates_per_query": round(sts["candidates"] / B, 1),
+                              "overflow_queries": sts["overflow_queries"],
+                              "lanes_per_query": o.lanes_per_query, "tile_blocks": o.tile_blocks,
+                              "stage_ms": {s_: round(v, 4) for s_, v in prof.items()}}
+        out["batches"] = batches
+        out["metric"] = "QPS per batch size (per-query nprobe U{4..256}, k 100, R 1000)"
+    elif args.workload == "glove":
+        c = synth.CONFIGS[3]
+        X = synth.base(3)
+        Xd = torch.from_numpy(X).to(dev)
+        ix = ksc.build_index(Xd, c["L"], c["M"], metric="ip", spherical=True, perm=synth.build_perm(3, c["n"]))
+        Qh = synth.queries(3)
+        Qd = torch.from_numpy(Qh).to(dev)
+        k = c["k"]
+        # inner-product ground truth: top-k similarity (FP32 on the GPU)
+        sims = []
+        for b in range(0, len(Qh), 2048):
+            sims.append(torch.topk(Qd[b:b + 2048] @ Xd.T, k, dim=1).values[:, k - 1])
+        kth = torch.cat(sims)
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        res = {}
+        for name, opts, Rw in (("fp32_R200", None, 200), ("bf16_Rw400_Rf100", ksc.search_opts(precision=1, rerank_final=100), 400),
+                               ("fp8_Rw800_Rf100", ksc.search_opts(precision=2, rerank_final=100), 800)):
+            for P in (8, 12, 16, 24, 32, 48, 64):
+                ids, dd = ix.search(Qd, k, P, Rw, opts=opts)
+                sim = (Xd[ids.clamp_min(0)] * Qd[:, None, :]).sum(-1)
+                rec = float(((sim >= kth[:, None] - 1e-5) & (ids >= 0)).sum(1).clamp_max(k).double().mean() / k)
+                if rec >= TARGET_RECALL:
+                    break
+            fn = lambda: ix.search(Qd, k, P, Rw, opts=opts)
+            for _ in range(3):
+                fn()
+            times = []
+            for _ in range(5):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                fn()
+                e1.record()
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+            ms = statistics.median(times)
+            res[name] = {"nprobe": P, "recall@10": round(rec, 4), "ms": round(ms, 4), "qps": round(len(Qh) / (ms * 1e-3), 1)}
+        out["variants"] = res
+        out["metric"] = "QPS at recall@10>=0.90 per re-rank precision (1.2M x 100, inner product)"
+    print(json.dumps(out))
+
+
 def run_reference(args, rank, ws):
     """The CPU oracle as the reference arm (FP64 except the 8-bit LUT rule),
     timed on the host cores: its own index over the full 1M base (FP64 Lloyd,
@@ -435,8 +552,13 @@ def main():
     ap.add_argument("--nprobe", type=int, default=0)
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-nprobe path")
     ap.add_argument("--ntrain", type=int, default=100_000)
+    ap.add_argument("--workload", default="sift", choices=["sift", "deep", "glove"],
+                    help="sift: the headline line; deep / glove: secondary workloads")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.workload != "sift":
+        run_workload(args)
+        return
     rank, ws = dist_setup()
     out = run_reference(args, rank, ws) if args.impl == "reference" else run_ours(args, rank, ws)
     if rank == 0 and out is not None:

@@ -23,7 +23,8 @@ namespace ksc {
 
 constexpr int SEL_CAP = 4096;   // bitonic buffer of the select kernels (>= KSC_MAX_RERANK)
 constexpr int MAX_NPROBE = 4096;
-constexpr int NEAR_RANKS = 1;    // probe ranks scanned before the threshold is set
+constexpr int NEAR_KEYS_PER_R = 4;  // keys of the unfiltered first scan: at least 4 R ...
+constexpr int NEAR_SHARE_DIV = 16;  // ... and at least 1/16 of the keys the query probes
 
 // ------------------------------------------------------------------ a1: list scores
 // score[q][c] = ||c||^2 - 2<q,c> (L2, ||q||^2 dropped) or -<q,c> (spherical).
@@ -578,15 +579,54 @@ __global__ void __launch_bounds__(256) k_threshold(ScanArgs A, int Rmax, int32_t
 // ------------------------------------------------------------------ work list (cluster-major)
 // pairs of (query, probe rank) grouped by list; items = (list, query group,
 // block tile).
-__global__ void k_count_pairs(ScanArgs A, int rlo, int rhi, int32_t* __restrict__ cnt) {
+// Phase boundary of each query's probe ranks: ranks below `split[q]` (or
+// below `rs` when split is null) are scanned first with no filter, the rest
+// after the threshold.  side 0 selects the first part, side 1 the rest.
+__device__ __forceinline__ bool in_part(const ScanArgs& A, int64_t q, int r, int rs, const int32_t* split, int side) {
+    if (r >= nprobe_of(A, q)) return false;
+    const int b = split ? split[q] : rs;
+    return side == 0 ? r < b : r >= b;
+}
+
+__global__ void k_count_pairs(ScanArgs A, int rs, const int32_t* __restrict__ split, int side,
+                              int32_t* __restrict__ cnt) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= A.nq * A.Pmax) return;
     int64_t q = e / A.Pmax;
     int r = (int)(e - q * A.Pmax);
-    if (r < rlo || r >= rhi || r >= nprobe_of(A, q)) return;
+    if (!in_part(A, q, r, rs, split, side)) return;
     const int p = A.probes[e];
     if (p < 0 || p >= A.L) return;
     atomicAdd(&cnt[p], 1);
+}
+
+// Per query, how many of its nearest lists the unfiltered first scan takes.
+// The R-th key of a first set of S keys sits near the R/S quantile of the
+// nearest keys, and the remaining lists are farther, so at most about
+// N * R / S of their N keys pass it: S = max(NEAR_KEYS_PER_R * R,
+// N / NEAR_SHARE_DIV) keeps that to a few R.  The first set is the fewest
+// nearest lists holding S keys (all probed lists if they hold fewer), with S
+// at most half the candidate store and never so many lists that their keys
+// exceed it (at least one list).
+__global__ void k_near_split(ScanArgs A, int Rmax, int cap, int32_t* __restrict__ split) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= A.nq) return;
+    const int P = nprobe_of(A, q);
+    const int32_t* pr = A.probes + q * A.Pmax;
+    int64_t total = 0;
+    for (int r = 0; r < P; ++r) total += (pr[r] >= 0 && pr[r] < A.L) ? A.list_n[pr[r]] : 0;
+    int64_t target = (int64_t)NEAR_KEYS_PER_R * rerank_of(A.rerank_q, A.Rfix, A.Rmin, Rmax, q);
+    target = max(target, total / NEAR_SHARE_DIV);
+    target = min(target, (int64_t)cap / 2);
+    int64_t acc = 0;
+    int r = 0;
+    while (r < P && acc < target) {
+        const int64_t n = (pr[r] >= 0 && pr[r] < A.L) ? A.list_n[pr[r]] : 0;
+        if (r > 0 && acc + n > cap) break;
+        acc += n;
+        ++r;
+    }
+    split[q] = r < 1 ? 1 : r;
 }
 
 // exclusive scans: pair_off = scan(cnt); item_off = scan(ceil(cnt/QG) * ntiles)
@@ -630,13 +670,14 @@ __global__ void __launch_bounds__(1024) k_scan_lists(const int32_t* __restrict__
     }
 }
 
-__global__ void k_fill_pairs(ScanArgs A, int rlo, int rhi, const int64_t* __restrict__ pair_off,
-                             int32_t* __restrict__ fill, uint32_t* __restrict__ pairs) {
+__global__ void k_fill_pairs(ScanArgs A, int rs, const int32_t* __restrict__ split, int side,
+                             const int64_t* __restrict__ pair_off, int32_t* __restrict__ fill,
+                             uint32_t* __restrict__ pairs) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= A.nq * A.Pmax) return;
     int64_t q = e / A.Pmax;
     int r = (int)(e - q * A.Pmax);
-    if (r < rlo || r >= rhi || r >= nprobe_of(A, q)) return;
+    if (!in_part(A, q, r, rs, split, side)) return;
     int p = A.probes[e];
     if (p < 0 || p >= A.L) return;
     int slot = atomicAdd(&fill[p], 1);
@@ -1554,23 +1595,24 @@ static int ensure_lowp(ksc_index* ix, int prec, cudaStream_t st) {
     return KSC_OK;
 }
 
-// Cluster-major work list of the (query, rank) pairs with rank in [rlo, rhi).
+// Cluster-major work list of the (query, rank) pairs of one part of the probe
+// ranks (the unfiltered first part or the rest).
 struct WorkList {
     int64_t* pair_off;  // [L + 1]
     int64_t* item_off;  // [L + 1]
     int32_t* cnt;       // [L]
     int32_t* fill;      // [L]
-    uint32_t* pairs;    // [<= nq * (rhi - rlo)]
+    uint32_t* pairs;    // [<= nq * Pmax]
 };
 
-static int build_worklist(ksc_index* ix, const ScanArgs& A, int rlo, int rhi, int QG, int TB, WorkList& w,
-                          cudaStream_t st) {
+static int build_worklist(ksc_index* ix, const ScanArgs& A, int rs, const int32_t* split, int side, int QG, int TB,
+                          WorkList& w, cudaStream_t st) {
     const int L = ix->L;
     const int64_t n = A.nq * A.Pmax;
     KSC_CUDA(cudaMemsetAsync(w.cnt, 0, sizeof(int32_t) * L, st));
-    k_count_pairs<<<blocks_for(n, 256), 256, 0, st>>>(A, rlo, rhi, w.cnt);
+    k_count_pairs<<<blocks_for(n, 256), 256, 0, st>>>(A, rs, split, side, w.cnt);
     k_scan_lists<<<1, 1024, 0, st>>>(w.cnt, ix->list_n, L, QG, TB, w.pair_off, w.item_off, w.fill);
-    k_fill_pairs<<<blocks_for(n, 256), 256, 0, st>>>(A, rlo, rhi, w.pair_off, w.fill, w.pairs);
+    k_fill_pairs<<<blocks_for(n, 256), 256, 0, st>>>(A, rs, split, side, w.pair_off, w.fill, w.pairs);
     ix->launches += 3;
     KSC_LAUNCH_CHECK();
     return KSC_OK;
@@ -1592,7 +1634,9 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
     const int64_t nq = pl.nq;
     const int M = ix->M, L = ix->L;
     const int QG = 32 / pl.G;
-    const int rA = std::min(pl.hybrid ? pl.n_near : NEAR_RANKS, pl.Pmax);
+    // hybrid: the n_near nearest lists are the fully scanned ones (Sec. 4.4);
+    // plain: a per-query split (k_near_split)
+    const int rA = std::min(pl.hybrid ? pl.n_near : 1, pl.Pmax);
     KSC_TRY(ensure(ix->ws_lut, (size_t)nq * pl.Pmax * M * PQ_K, st));
     KSC_TRY(ensure(ix->ws_bias, sizeof(int32_t) * nq * pl.Pmax, st));
     KSC_TRY(ensure(ix->ws_scale, sizeof(float) * nq, st));
@@ -1601,7 +1645,7 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
     KSC_TRY(ensure(ix->ws_cand, sizeof(uint64_t) * nq * pl.cap, st));
     KSC_TRY(ensure(ix->ws_topr, sizeof(uint64_t) * nq * pl.Rmax, st));
     const size_t wl_head = sizeof(int64_t) * 2 * (L + 1) + sizeof(int32_t) * 2 * L;
-    KSC_TRY(ensure(ix->ws_items, 2 * wl_head + sizeof(uint32_t) * nq * pl.Pmax + 256, st));
+    KSC_TRY(ensure(ix->ws_items, 2 * wl_head + sizeof(uint32_t) * nq * (2 * pl.Pmax + 1) + 256, st));
     uint8_t* lut = (uint8_t*)ix->ws_lut.p;
     int32_t* bias = (int32_t*)ix->ws_bias.p;
     float* scale = (float*)ix->ws_scale.p;
@@ -1621,14 +1665,20 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
             wp += wl_head;
         }
         wa.pairs = (uint32_t*)wp;
-        wb.pairs = wa.pairs + nq * rA;
+        wb.pairs = wa.pairs + nq * pl.Pmax;
     }
+    int32_t* split = pl.hybrid ? nullptr : (int32_t*)(wb.pairs + nq * pl.Pmax);
     ScanArgs A{M, pl.Pmax, nq, probes, pl.nprobe_q, pl.Pfix, pl.rerank_q, pl.Rfix, pl.k, lut, bias,
                ix->list_boff, ix->list_n, ix->blk_codes, ix->blk_ids, ix->L};
     // 1. work lists: the nearest list of every query, and the rest
     mark(ix, 1, st);
-    KSC_TRY(build_worklist(ix, A, 0, rA, QG, pl.TB, wa, st));
-    KSC_TRY(build_worklist(ix, A, rA, pl.Pmax, QG, pl.TB, wb, st));
+    if (split) {
+        k_near_split<<<blocks_for(nq, 256), 256, 0, st>>>(A, pl.Rmax, pl.cap, split);
+        KSC_LAUNCH_CHECK();
+        ix->launches++;
+    }
+    KSC_TRY(build_worklist(ix, A, rA, split, 0, QG, pl.TB, wa, st));
+    KSC_TRY(build_worklist(ix, A, rA, split, 1, QG, pl.TB, wb, st));
     // 2. quantised LUTs of every probed (query, list)
     mark(ix, 2, st);
     {
