@@ -219,22 +219,10 @@ __global__ void __launch_bounds__(256) k_rank_select(const float* __restrict__ s
 
 // ------------------------------------------------------------------ a2: quantised LUTs
 // FP32 rule of the table entries, every op separately rounded:
-//   L2: acc += (q_t - c_t - C_jit)^2 over t ascending;  IP: acc += q_t C_jit, T = -acc
-__device__ __forceinline__ float lut_entry(const float* __restrict__ q, const float* __restrict__ cp,
-                                           const float* __restrict__ cw, int j, int dsub, int ip) {
-    float acc = 0.f;
-    for (int t = 0; t < dsub; ++t) {
-        const int tt = j * dsub + t;
-        if (ip) {
-            acc = __fadd_rn(acc, __fmul_rn(q[tt], cw[t]));
-        } else {
-            float r = __fsub_rn(q[tt], cp[tt]);
-            float e = __fsub_rn(r, cw[t]);
-            acc = __fadd_rn(acc, __fmul_rn(e, e));
-        }
-    }
-    return ip ? -acc : acc;
-}
+//   L2: u_t = q_t - c_t, acc += (u_t - C_jit)^2 over t ascending
+//   IP: u_t = q_t,       acc += u_t C_jit,                        T = -acc
+// The row operand u (the dsub values of subspace j) is formed once per row;
+// each entry is then the same sequence of rounded ops as written above.
 
 struct LutArgs {
     const float* Q;
@@ -274,115 +262,191 @@ __device__ __forceinline__ int probes_of(const LutArgs& A, int64_t q) {
     return P < 1 ? 1 : (P > A.Pmax ? A.Pmax : P);
 }
 
-// The 16 FP32 table entries of subspace j for (query, list), in registers;
-// cbs = the codebook in shared memory, row j (16 codewords) at j * cbs_ld.
-__device__ __forceinline__ void lut_row(const LutArgs& A, const float* __restrict__ qv, const float* __restrict__ cp,
-                                        const float* cbs, int cbs_ld, int j, float (&T)[PQ_K]) {
-    const float* cw = cbs + j * cbs_ld;
-#pragma unroll
-    for (int i = 0; i < PQ_K; ++i) T[i] = lut_entry(qv, cp, cw + i * A.dsub, j, A.dsub, A.ip);
-}
+// Codebook row stride in shared memory.  dsub = 2: 34 floats (codewords
+// 8-byte aligned; a half-warp reading 16 consecutive rows with 8-byte loads
+// covers all 32 banks once); else 16 dsub + 1 (odd: 32 consecutive rows fall
+// in distinct banks).
+__host__ __device__ __forceinline__ int cb_ld(int dsub) { return dsub == 2 ? 34 : PQ_K * dsub + 1; }
 
-// Codebook into shared memory with row stride 16 dsub + 1 (odd: lanes reading
-// rows j = lane hit distinct banks).
-__device__ __forceinline__ int stage_codebook(const LutArgs& A, float* cbs) {
-    const int ld = PQ_K * A.dsub + 1;
-    for (int e = threadIdx.x; e < A.M * PQ_K * A.dsub; e += blockDim.x) {
-        const int j = e / (PQ_K * A.dsub), rest = e - j * (PQ_K * A.dsub);
-        cbs[j * ld + rest] = A.cb[e];
+__device__ __forceinline__ void stage_codebook(const LutArgs& A, float* cbs) {
+    const int ld = cb_ld(A.dsub), rowlen = PQ_K * A.dsub;
+    for (int e = threadIdx.x; e < A.M * rowlen; e += blockDim.x) {
+        const int j = e / rowlen;
+        cbs[j * ld + (e - j * rowlen)] = A.cb[e];
     }
     __syncthreads();
-    return ld;
 }
 
-// Persistent; one warp per (query, probe rank) item, lane l owning subspaces
-// j = l + 32u.  Pass 1: the largest table range of the query, R_q (atomic max
-// over its probes).
-__global__ void __launch_bounds__(256) k_lut_range(LutArgs A, uint32_t* __restrict__ range_bits) {
-    extern __shared__ float cbs[];
-    const int lane = threadIdx.x & 31;
-    const int ld = stage_codebook(A, cbs);
-    int64_t n0;
-    const int64_t items = lut_items(A, &n0);
-    for (int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); i < items; i += (int64_t)gridDim.x * 8) {
-        const int64_t item = lut_item(A, i, n0);
-        const int64_t q = item / A.Pmax;
-        const int r = (int)(item - q * A.Pmax);
-        if (r >= probes_of(A, q)) continue;
-        const int p = A.probes[item];
-        if (p < 0 || p >= A.L) continue;  // invalid probe ids are skipped
-        const float* qv = A.Q + q * A.d;
-        const float* cp = A.c_mean + (int64_t)p * A.d;
-        float R = 0.f;
-        for (int j = lane; j < A.M; j += 32) {
-            float T[PQ_K];
-            lut_row(A, qv, cp, cbs, ld, j, T);
-            float mn = T[0], mx = T[0];
-#pragma unroll
-            for (int i = 1; i < PQ_K; ++i) { mn = fminf(mn, T[i]); mx = fmaxf(mx, T[i]); }
-            R = fmaxf(R, __fsub_rn(mx, mn));
+// The 16 FP32 entries of one subspace: qj, cj = the query's and the list
+// centroid's values of the subspace, cw = its codebook row in shared memory.
+// DS = dsub when fixed at compile time (2: 8-byte loads; qj and cj 8-byte
+// aligned), 0 = read from dsub.
+template <int DS>
+__device__ __forceinline__ void row_table(int dsub, int ip, const float* __restrict__ qj,
+                                          const float* __restrict__ cj, const float* cw, float (&T)[PQ_K]) {
+    if constexpr (DS == 2) {
+        const float2 qv = *reinterpret_cast<const float2*>(qj);
+        float u0 = qv.x, u1 = qv.y;
+        if (!ip) {
+            const float2 cv = *reinterpret_cast<const float2*>(cj);
+            u0 = __fsub_rn(u0, cv.x);
+            u1 = __fsub_rn(u1, cv.y);
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) R = fmaxf(R, __shfl_xor_sync(0xffffffffu, R, o));
-        if (lane == 0) atomicMax(&range_bits[q], __float_as_uint(R));  // R >= 0: bit order = value order
+        for (int i = 0; i < PQ_K; ++i) {
+            const float2 c = *reinterpret_cast<const float2*>(cw + 2 * i);
+            float acc = 0.f;
+            if (ip) {
+                acc = __fadd_rn(acc, __fmul_rn(u0, c.x));
+                acc = __fadd_rn(acc, __fmul_rn(u1, c.y));
+                T[i] = -acc;
+            } else {
+                const float e0 = __fsub_rn(u0, c.x), e1 = __fsub_rn(u1, c.y);
+                acc = __fadd_rn(acc, __fmul_rn(e0, e0));
+                acc = __fadd_rn(acc, __fmul_rn(e1, e1));
+                T[i] = acc;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < PQ_K; ++i) T[i] = 0.f;
+        for (int t = 0; t < dsub; ++t) {
+            const float u = ip ? qj[t] : __fsub_rn(qj[t], cj[t]);
+#pragma unroll
+            for (int i = 0; i < PQ_K; ++i) {
+                const float c = cw[i * dsub + t];
+                if (ip) {
+                    T[i] = __fadd_rn(T[i], __fmul_rn(u, c));
+                } else {
+                    const float e = __fsub_rn(u, c);
+                    T[i] = __fadd_rn(T[i], __fmul_rn(e, e));
+                }
+            }
+        }
+        if (ip) {
+#pragma unroll
+            for (int i = 0; i < PQ_K; ++i) T[i] = -T[i];
+        }
+    }
+}
+
+// u8 entry min(255, floor((T - m) a + 1/2)) of four table entries, packed.
+__device__ __forceinline__ uint32_t quant4(const float* T, float mn, float a) {
+    uint32_t w = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float f = floorf(__fadd_rn(__fmul_rn(__fsub_rn(T[i], mn), a), 0.5f));
+        w |= (uint32_t)(f > 255.f ? 255.f : f) << (8 * i);
+    }
+    return w;
+}
+
+// Integer bias floor(S a + 1/2) of one (query, list), S = sum_j m_j in
+// ascending j (+ -<q, c_p> first for IP), clamped to +-2^30.
+__device__ __forceinline__ int32_t lut_bias(const LutArgs& A, const float* __restrict__ qv, const float* __restrict__ cp,
+                                            const float* mins, float a) {
+    float S = 0.f;
+    if (A.ip) {
+        float dot = 0.f;
+        for (int t = 0; t < A.d; ++t) dot = __fadd_rn(dot, __fmul_rn(qv[t], cp[t]));
+        S = -dot;
+    }
+    for (int j = 0; j < A.M; ++j) S = __fadd_rn(S, mins[j]);
+    float bf = floorf(__fadd_rn(__fmul_rn(S, a), 0.5f));
+    bf = fminf(fmaxf(bf, -1073741824.f), 1073741823.f);
+    return (int32_t)bf;
+}
+
+// Two-pass tables, one thread per (item, subspace row): a CTA takes tiles of
+// floor(256 / M) consecutive items.  Pass 1: the largest row range of each
+// query, R_q (max over its items: shared then global atomic max; R >= 0, so
+// the bit order is the value order).
+template <int DS>
+__global__ void __launch_bounds__(256) k_lut_range(LutArgs A, uint32_t* __restrict__ range_bits) {
+    extern __shared__ float cbs[];
+    __shared__ uint32_t s_R[256];
+    stage_codebook(A, cbs);
+    const int ld = cb_ld(A.dsub);
+    const int per = blockDim.x / A.M;
+    const int il = threadIdx.x / A.M, j = threadIdx.x - il * A.M;
+    int64_t n0;
+    const int64_t items = lut_items(A, &n0);
+    for (int64_t base = (int64_t)blockIdx.x * per; base < items; base += (int64_t)gridDim.x * per) {
+        if (threadIdx.x < per) s_R[threadIdx.x] = 0u;
+        __syncthreads();
+        const int64_t i = base + il;
+        if (il < per && i < items) {
+            const int64_t item = lut_item(A, i, n0);
+            const int64_t q = item / A.Pmax;
+            const int r = (int)(item - q * A.Pmax);
+            const int p = A.probes[item];
+            if (r < probes_of(A, q) && p >= 0 && p < A.L) {  // invalid probe ids are skipped
+                float T[PQ_K];
+                row_table<DS>(A.dsub, A.ip, A.Q + q * A.d + j * A.dsub, A.c_mean + (int64_t)p * A.d + j * A.dsub,
+                              cbs + j * ld, T);
+                float mn = T[0], mx = T[0];
+#pragma unroll
+                for (int e = 1; e < PQ_K; ++e) { mn = fminf(mn, T[e]); mx = fmaxf(mx, T[e]); }
+                atomicMax(&s_R[il], __float_as_uint(__fsub_rn(mx, mn)));
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < per && base + threadIdx.x < items && s_R[threadIdx.x] != 0u) {
+            const int64_t item = lut_item(A, base + threadIdx.x, n0);
+            atomicMax(&range_bits[item / A.Pmax], s_R[threadIdx.x]);
+        }
     }
 }
 
 // Pass 2: u8 tables Q = min(255, floor((T - m_j) a + 1/2)), a = 255 / R_q,
-// and the integer bias floor(S a + 1/2) with S = sum_j m_j (+ -<q, c_p> for IP)
-// summed in ascending j.
+// then the bias of each item from its row minima.
+template <int DS>
 __global__ void __launch_bounds__(256) k_lut_quant(LutArgs A, const uint32_t* __restrict__ range_bits,
                                                    uint8_t* __restrict__ lut, int32_t* __restrict__ bias,
                                                    float* __restrict__ scale) {
     extern __shared__ float cbs[];
-    __shared__ float mins[8][KSC_MAX_M];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int ld = stage_codebook(A, cbs);
+    __shared__ float s_min[256];
+    stage_codebook(A, cbs);
+    const int ld = cb_ld(A.dsub);
+    const int per = blockDim.x / A.M;
+    const int il = threadIdx.x / A.M, j = threadIdx.x - il * A.M;
     int64_t n0;
     const int64_t items = lut_items(A, &n0);
-    for (int64_t i = (int64_t)blockIdx.x * 8 + wib; i < items; i += (int64_t)gridDim.x * 8) {
-        const int64_t item = lut_item(A, i, n0);
-        const int64_t q = item / A.Pmax;
-        const int r = (int)(item - q * A.Pmax);
-        if (r >= probes_of(A, q)) continue;
-        const int p = A.probes[item];
-        if (p < 0 || p >= A.L) continue;
-        const float* qv = A.Q + q * A.d;
-        const float* cp = A.c_mean + (int64_t)p * A.d;
-        const float Rq = __uint_as_float(range_bits[q]);
-        const float a = (Rq == 0.f) ? 1.f : __fdiv_rn(255.f, Rq);
-        uint4* out = reinterpret_cast<uint4*>(lut + item * (int64_t)A.M * PQ_K);
-        for (int j = lane; j < A.M; j += 32) {
-            float T[PQ_K];
-            lut_row(A, qv, cp, cbs, ld, j, T);
-            float mn = T[0];
+    for (int64_t base = (int64_t)blockIdx.x * per; base < items; base += (int64_t)gridDim.x * per) {
+        const int64_t i = base + il;
+        if (il < per && i < items) {
+            const int64_t item = lut_item(A, i, n0);
+            const int64_t q = item / A.Pmax;
+            const int r = (int)(item - q * A.Pmax);
+            const int p = A.probes[item];
+            if (r < probes_of(A, q) && p >= 0 && p < A.L) {
+                const float Rq = __uint_as_float(range_bits[q]);
+                const float a = (Rq == 0.f) ? 1.f : __fdiv_rn(255.f, Rq);
+                float T[PQ_K];
+                row_table<DS>(A.dsub, A.ip, A.Q + q * A.d + j * A.dsub, A.c_mean + (int64_t)p * A.d + j * A.dsub,
+                              cbs + j * ld, T);
+                float mn = T[0];
 #pragma unroll
-            for (int i = 1; i < PQ_K; ++i) mn = fminf(mn, T[i]);
-            uint32_t w[4] = {0, 0, 0, 0};
-#pragma unroll
-            for (int i = 0; i < PQ_K; ++i) {
-                float f = floorf(__fadd_rn(__fmul_rn(__fsub_rn(T[i], mn), a), 0.5f));
-                uint32_t b = (uint32_t)(f > 255.f ? 255.f : f);
-                w[i >> 2] |= b << (8 * (i & 3));
+                for (int e = 1; e < PQ_K; ++e) mn = fminf(mn, T[e]);
+                reinterpret_cast<uint4*>(lut + item * (int64_t)A.M * PQ_K)[j] =
+                    make_uint4(quant4(T, mn, a), quant4(T + 4, mn, a), quant4(T + 8, mn, a), quant4(T + 12, mn, a));
+                s_min[threadIdx.x] = mn;
             }
-            out[j] = make_uint4(w[0], w[1], w[2], w[3]);
-            mins[wib][j] = mn;
         }
-        __syncwarp();
-        if (lane == 0) {
-            float S = 0.f;
-            if (A.ip) {
-                float dot = 0.f;
-                for (int t = 0; t < A.d; ++t) dot = __fadd_rn(dot, __fmul_rn(qv[t], cp[t]));
-                S = -dot;
+        __syncthreads();
+        if (threadIdx.x < per && base + threadIdx.x < items) {
+            const int64_t item = lut_item(A, base + threadIdx.x, n0);
+            const int64_t q = item / A.Pmax;
+            const int r = (int)(item - q * A.Pmax);
+            const int p = A.probes[item];
+            if (r < probes_of(A, q) && p >= 0 && p < A.L) {
+                const float Rq = __uint_as_float(range_bits[q]);
+                const float a = (Rq == 0.f) ? 1.f : __fdiv_rn(255.f, Rq);
+                bias[item] = lut_bias(A, A.Q + q * A.d, A.c_mean + (int64_t)p * A.d, s_min + threadIdx.x * A.M, a);
+                if (r == 0) scale[q] = a;
             }
-            for (int j = 0; j < A.M; ++j) S = __fadd_rn(S, mins[wib][j]);
-            float bf = floorf(__fadd_rn(__fmul_rn(S, a), 0.5f));
-            bf = fminf(fmaxf(bf, -1073741824.f), 1073741823.f);
-            bias[item] = (int32_t)bf;
-            if (r == 0) scale[q] = a;
         }
-        __syncwarp();
+        __syncthreads();
     }
 }
 
@@ -390,16 +454,16 @@ __global__ void __launch_bounds__(256) k_lut_quant(LutArgs A, const uint32_t* __
 // tables of its P_q probes are computed once, their largest range gives the
 // scale, and they are quantised from shared memory (same FP32 rule, same
 // results as the two-pass kernels above).
+template <int DS>
 __global__ void __launch_bounds__(256) k_lut_fused(LutArgs A, int Pb, uint8_t* __restrict__ lut,
                                                    int32_t* __restrict__ bias, float* __restrict__ scale) {
     extern __shared__ float fsm[];
     const int M = A.M;
-    const int ld = PQ_K * A.dsub + 1;
+    const int ld = cb_ld(A.dsub);
     float* cbs = fsm;                                  // M x ld
     float* T = cbs + M * ld;                           // Pb x M rows of 16, stride 17 (no bank conflicts)
     float* mins = T + (size_t)Pb * M * (PQ_K + 1);     // Pb x M
-    float* qs = mins + Pb * M;                         // d
-    __shared__ float s_range;
+    float* qs = mins + Pb * M;                         // d (8-byte aligned: every offset above is even)
     __shared__ uint32_t s_rbits;
     const int64_t q = blockIdx.x;
     const int P = min(probes_of(A, q), Pb);
@@ -418,7 +482,7 @@ __global__ void __launch_bounds__(256) k_lut_fused(LutArgs A, int Pb, uint8_t* _
             continue;
         }
         float Tv[PQ_K];
-        lut_row(A, qs, A.c_mean + (int64_t)p * A.d, cbs, ld, j, Tv);
+        row_table<DS>(A.dsub, A.ip, qs + j * A.dsub, A.c_mean + (int64_t)p * A.d + j * A.dsub, cbs + j * ld, Tv);
         float mn = Tv[0], mx = Tv[0];
 #pragma unroll
         for (int i = 0; i < PQ_K; ++i) {
@@ -439,36 +503,23 @@ __global__ void __launch_bounds__(256) k_lut_fused(LutArgs A, int Pb, uint8_t* _
         const int r = row / M, j = row - r * M;
         const float* Tr = T + (size_t)row * (PQ_K + 1);
         const float mn = mins[row];
-        uint32_t w[4] = {0, 0, 0, 0};
-#pragma unroll
-        for (int i = 0; i < PQ_K; ++i) {
-            const float f = floorf(__fadd_rn(__fmul_rn(__fsub_rn(Tr[i], mn), a), 0.5f));
-            w[i >> 2] |= (uint32_t)(f > 255.f ? 255.f : f) << (8 * (i & 3));
-        }
-        reinterpret_cast<uint4*>(lut + (q * A.Pmax + r) * (int64_t)M * PQ_K)[j] = make_uint4(w[0], w[1], w[2], w[3]);
+        reinterpret_cast<uint4*>(lut + (q * A.Pmax + r) * (int64_t)M * PQ_K)[j] =
+            make_uint4(quant4(Tr, mn, a), quant4(Tr + 4, mn, a), quant4(Tr + 8, mn, a), quant4(Tr + 12, mn, a));
     }
     for (int r = threadIdx.x; r < P; r += blockDim.x) {
         const int p = A.probes[q * A.Pmax + r];
         if (p < 0 || p >= A.L) continue;
-        float S = 0.f;
-        if (A.ip) {
-            const float* cp = A.c_mean + (int64_t)p * A.d;
-            float dot = 0.f;
-            for (int t = 0; t < A.d; ++t) dot = __fadd_rn(dot, __fmul_rn(qs[t], cp[t]));
-            S = -dot;
-        }
-        for (int j = 0; j < M; ++j) S = __fadd_rn(S, mins[r * M + j]);
-        float bf = floorf(__fadd_rn(__fmul_rn(S, a), 0.5f));
-        bf = fminf(fmaxf(bf, -1073741824.f), 1073741823.f);
-        bias[q * A.Pmax + r] = (int32_t)bf;
+        bias[q * A.Pmax + r] = lut_bias(A, qs, A.c_mean + (int64_t)p * A.d, mins + r * M, a);
     }
     if (threadIdx.x == 0) scale[q] = a;
-    (void)s_range;
 }
 
 static size_t lut_fused_smem(int M, int dsub, int d, int Pb) {
-    return sizeof(float) * ((size_t)M * (PQ_K * dsub + 1) + (size_t)Pb * M * (PQ_K + 1) + (size_t)Pb * M + d);
+    return sizeof(float) * ((size_t)M * cb_ld(dsub) + (size_t)Pb * M * (PQ_K + 1) + (size_t)Pb * M + d);
 }
+
+// 8-byte row loads need dsub = 2 and an 8-byte aligned query matrix.
+static bool lut_ds2(const LutArgs& A) { return A.dsub == 2 && (reinterpret_cast<uintptr_t>(A.Q) & 7) == 0; }
 
 static int launch_luts(const LutArgs& A, uint32_t* rb, uint8_t* lut, int32_t* bias, float* scale, cudaStream_t st);
 
@@ -1553,14 +1604,23 @@ static int rank_lists(ksc_index* ix, const float* Q, int64_t nq, const int32_t* 
 }
 
 static int launch_luts(const LutArgs& A, uint32_t* rb, uint8_t* lut, int32_t* bias, float* scale, cudaStream_t st) {
-    const size_t smem = sizeof(float) * (size_t)A.M * (PQ_K * A.dsub + 1);
-    cudaFuncSetAttribute(k_lut_range, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_lut_quant, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int64_t items = A.nq * A.Pmax;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((items + 7) / 8, (int64_t)num_sms() * 8));
-    k_lut_range<<<grid, 256, smem, st>>>(A, rb);
-    KSC_LAUNCH_CHECK();
-    k_lut_quant<<<grid, 256, smem, st>>>(A, rb, lut, bias, scale);
+    const size_t smem = sizeof(float) * (size_t)A.M * cb_ld(A.dsub);
+    const int per = 256 / A.M;
+    const int64_t tiles = (A.nq * A.Pmax + per - 1) / per;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)num_sms() * 8));
+    if (lut_ds2(A)) {
+        cudaFuncSetAttribute(k_lut_range<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_lut_quant<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_lut_range<2><<<grid, 256, smem, st>>>(A, rb);
+        KSC_LAUNCH_CHECK();
+        k_lut_quant<2><<<grid, 256, smem, st>>>(A, rb, lut, bias, scale);
+    } else {
+        cudaFuncSetAttribute(k_lut_range<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_lut_quant<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_lut_range<0><<<grid, 256, smem, st>>>(A, rb);
+        KSC_LAUNCH_CHECK();
+        k_lut_quant<0><<<grid, 256, smem, st>>>(A, rb, lut, bias, scale);
+    }
     KSC_LAUNCH_CHECK();
     return KSC_OK;
 }
@@ -1689,8 +1749,13 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
                    ix->c_mean, ix->codebook, ix->L, wa.pairs, wa.pair_off + L, wb.pairs, wb.pair_off + L};
         const size_t fsm = lut_fused_smem(M, ix->dsub, ix->d, pl.Pq_max);
         if (fsm <= 160 * 1024) {
-            KSC_CUDA(cudaFuncSetAttribute(k_lut_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
-            k_lut_fused<<<(unsigned)nq, 256, fsm, st>>>(LA, pl.Pq_max, lut, bias, scale);
+            if (lut_ds2(LA)) {
+                KSC_CUDA(cudaFuncSetAttribute(k_lut_fused<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
+                k_lut_fused<2><<<(unsigned)nq, 256, fsm, st>>>(LA, pl.Pq_max, lut, bias, scale);
+            } else {
+                KSC_CUDA(cudaFuncSetAttribute(k_lut_fused<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
+                k_lut_fused<0><<<(unsigned)nq, 256, fsm, st>>>(LA, pl.Pq_max, lut, bias, scale);
+            }
             KSC_LAUNCH_CHECK();
             ix->launches++;
         } else {

@@ -55,6 +55,12 @@ def small_index(kind):
         elif kind == "m50":  # d = 100, M = 50: subspaces not a multiple of the lane group
             X, Q, perm = mixture(4000, 100, 16, 13, ip=True)
             ix = oracle.build_index(X, 16, 50, True, perm, iters=5, ip=True)
+        elif kind == "ds4":  # d' = 4: the table kernels' general sub-vector path
+            X, Q, perm = mixture(3000, 64, 12, 14)
+            ix = oracle.build_index(X, 12, 16, False, perm, iters=5)
+        elif kind == "ds3ip":  # d' = 3, inner product
+            X, Q, perm = mixture(3000, 36, 10, 15, ip=True)
+            ix = oracle.build_index(X, 10, 12, True, perm, iters=5, ip=True)
         elif kind == "small":  # the 10k x 128 configuration
             X = synth.base(1)
             Q = synth.queries(1)
@@ -88,7 +94,7 @@ def check_results(ix, Q, ids, dists, ref_ids, ref_d, k):
             assert abs(exact - expect) <= RTOL * max(1.0, abs(expect)), (qi, r, exact, expect)
 
 
-@pytest.mark.parametrize("kind", ["l2", "ip", "m50"])
+@pytest.mark.parametrize("kind", ["l2", "ip", "m50", "ds4", "ds3ip"])
 def test_luts_bit_exact(torch, ksc, kind):
     ix, Q = small_index(kind)
     g = gpu_index(ksc, ix)
@@ -103,8 +109,30 @@ def test_luts_bit_exact(torch, ksc, kind):
         assert np.float32(a) == scale[qi], qi
 
 
+def test_luts_of_a_misaligned_query_matrix(torch, ksc):
+    """A query matrix at a 4-byte (not 8-byte) offset takes the tables' general
+    path; the tables are the same."""
+    ix, Q = small_index("l2")
+    g = gpu_index(ksc, ix)
+    probes = torch.from_numpy(oracle_probes(ix, Q, 7)).cuda()
+    Qa = torch.from_numpy(Q).cuda()
+    buf = torch.empty(Q.size + 1, dtype=torch.float32, device="cuda")
+    Qm = buf[1:].view(Q.shape)
+    Qm.copy_(Qa)
+    assert Qm.data_ptr() % 8 == 4
+    a = g.compute_luts(Qa, probes)
+    b = g.compute_luts(Qm, probes)
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+    s1 = g.search_with_probes(Qa, probes, 10, 100)
+    s2 = g.search_with_probes(Qm, probes, 10, 100)
+    for x, y in zip(s1, s2):
+        assert torch.equal(x, y)
+
+
 @pytest.mark.parametrize("kind,lanes", [("l2", 8), ("l2", 16), ("l2", 32), ("ip", 8), ("ip", 32),
-                                        ("m50", 8), ("m50", 16), ("m50", 32), ("small", 0)])
+                                        ("m50", 8), ("m50", 16), ("m50", 32), ("small", 0), ("ds4", 8),
+                                        ("ds3ip", 16)])
 def test_scan_candidates_bit_exact(torch, ksc, kind, lanes):
     ix, Q = small_index(kind)
     g = gpu_index(ksc, ix)
