@@ -112,7 +112,8 @@ int ksc_index_export(const ksc_index* ix, ksc_index_arrays* a);
 /* Search (Alg. 2, Alg. 3)                                             */
 /* ------------------------------------------------------------------ */
 typedef struct {
-    int32_t lanes_per_query;   /* scan kernel: 0 auto, or 8/16/32 lanes share a query */
+    int32_t lanes_per_query;   /* scan kernel: 0 auto; 4: each lane sums all subspaces of one block
+                                   (M <= 128); 8/16/32: lanes split the subspaces of a query */
     int32_t hybrid;            /* 1: hybrid intra-cluster search of Sec. 4.4 (needs graphs) */
     int32_t n_near;            /* hybrid: probes of rank < n_near are scanned fully (2) */
     int32_t efs;               /* hybrid: graph-search result capacity (64) */

@@ -269,6 +269,110 @@ __device__ void block_select_hist(Load load, int N, int K, uint64_t* out, uint64
     __syncthreads();
 }
 
+// Ascending bitonic sort of one key per lane across a warp.
+__device__ __forceinline__ uint64_t warp_sort_key(uint64_t v, int lane) {
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const uint64_t o = __shfl_xor_sync(0xffffffffu, v, j);
+            const bool keep_min = ((lane & k) == 0) == ((lane & j) == 0);
+            v = keep_min ? (o < v ? o : v) : (o > v ? o : v);
+        }
+    }
+    return v;
+}
+
+// K smallest of N unique keys held in shared memory (0 < K < N), in no
+// particular order: emit(i, key) for i in [0, K).  A histogram of HIST_BINS
+// bins of width 2^shift above the smallest distance (shift: the least that
+// fits the distance range) finds the bin B of the K-th key; the lt keys of
+// lower bins are emitted as found (indices [0, lt)), the keys of bin B are
+// sorted and their first K - lt follow.  *kth (shared) receives the K-th
+// smallest key.  Returns false, having emitted nothing, if bin B holds more
+// than bcap keys (bcap a power of two, bbuf its scratch).  All threads call.
+template <class Emit>
+__device__ bool block_topk_smem(const uint64_t* keys, int N, int K, Emit emit, uint64_t* bbuf, int bcap,
+                                uint32_t* hist, uint32_t* warp_tot, uint64_t* kth) {
+    __shared__ uint32_t s_min, s_max;
+    __shared__ int s_out, s_nb;
+    __shared__ HistSel hs;
+    if (threadIdx.x == 0) {
+        s_min = 0xffffffffu;
+        s_max = 0u;
+        s_out = 0;
+        s_nb = 0;
+    }
+    for (int b = threadIdx.x; b < HIST_BINS; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    uint32_t mn = 0xffffffffu, mx = 0u;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const uint32_t d = (uint32_t)(keys[i] >> 32);
+        mn = min(mn, d);
+        mx = max(mx, d);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&s_min, mn);
+        atomicMax(&s_max, mx);
+    }
+    __syncthreads();
+    const uint32_t base = s_min;
+    int shift = 0;
+    while (((s_max - base) >> shift) >= (uint32_t)HIST_BINS) ++shift;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) atomicAdd(&hist[((uint32_t)(keys[i] >> 32) - base) >> shift], 1u);
+    __syncthreads();
+    const int per = HIST_BINS / blockDim.x;  // blockDim.x divides HIST_BINS
+    const int b0 = threadIdx.x * per;
+    uint32_t local = 0;
+    for (int b = b0; b < b0 + per; ++b) local += hist[b];
+    const uint32_t excl = block_exclusive_scan(local, warp_tot);
+    if (excl < (uint32_t)K && excl + local >= (uint32_t)K) {
+        uint32_t c = excl;
+        for (int b = b0; b < b0 + per; ++b) {
+            if (c + hist[b] >= (uint32_t)K) {
+                hs.B = b;
+                hs.lt = (int)c;
+                hs.inB = (int)hist[b];
+                break;
+            }
+            c += hist[b];
+        }
+    }
+    __syncthreads();
+    const int B = hs.B, lt = hs.lt, inB = hs.inB;
+    if (inB > bcap) return false;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const uint64_t k = keys[i];
+        const int b = (int)(((uint32_t)(k >> 32) - base) >> shift);
+        if (b < B) emit(atomicAdd(&s_out, 1), k);
+        else if (b == B) bbuf[atomicAdd(&s_nb, 1)] = k;
+    }
+    __syncthreads();
+    const int need = K - lt;
+    if (inB <= 32) {
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            const uint64_t v = warp_sort_key(lane < inB ? bbuf[lane] : KEY_NONE, lane);
+            if (lane < need) emit(lt + lane, v);
+            if (lane == need - 1) *kth = v;
+        }
+    } else {
+        const int S = pow2_ceil(inB);
+        for (int i = inB + threadIdx.x; i < S; i += blockDim.x) bbuf[i] = KEY_NONE;
+        __syncthreads();
+        block_bitonic_sort(bbuf, S);
+        for (int i = threadIdx.x; i < need; i += blockDim.x) emit(lt + i, bbuf[i]);
+        if (threadIdx.x == 0) *kth = bbuf[need - 1];
+    }
+    __syncthreads();
+    return true;
+}
+
 // ------------------------------------------------------------------ workspace
 // Grow-only device buffers owned by an index (one per role).  Growing
 // synchronises the stream before freeing the old buffer.

@@ -155,21 +155,26 @@ __global__ void __launch_bounds__(128, 1) k_rank_gemm_tc(const __grid_constant__
     const bool mma_ok = done && __all_sync(0xffffffffu, mbar_wait(bar_mma, 0, TC_WAIT_LIMIT));
     if (mma_ok) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int64_t q = (int64_t)m0 + warp * 32 + lane;
+        // 32 x 32 sub-tiles go through the operand buffers (no longer read: the
+        // MMAs have completed) so that each store writes 32 consecutive
+        // columns of one row; row stride 33 keeps both sides free of bank conflicts
+        float* stage = reinterpret_cast<float*>(smem) + warp * (32 * 33);
+        const int64_t qb = (int64_t)m0 + warp * 32;
         for (int c0 = 0; c0 < TC_N; c0 += 32) {
             uint32_t r[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c0, r);
-            if (q < nq) {
-                float* row = scores + q * L;
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c0, r);  // lane = row, r[i] = column c0 + i
 #pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    const int c = n0 + c0 + i;
-                    if (c < L) {
-                        const float dot = __uint_as_float(r[i]);
-                        row[c] = spherical ? -dot : fmaf(-2.f, dot, cn[c]);
-                    }
+            for (int i = 0; i < 32; ++i) stage[lane * 33 + i] = __uint_as_float(r[i]);
+            __syncwarp();
+            const int c = n0 + c0 + lane;
+            if (c < L) {
+                const float cc = spherical ? 0.f : cn[c];
+                for (int rr = 0; rr < 32 && qb + rr < nq; ++rr) {
+                    const float dot = stage[rr * 33 + lane];
+                    scores[(qb + rr) * L + c] = spherical ? -dot : fmaf(-2.f, dot, cc);
                 }
             }
+            __syncwarp();
         }
     } else if (done && lane == 0) {
         atomicOr(status, 2);

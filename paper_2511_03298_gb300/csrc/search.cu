@@ -22,6 +22,11 @@
 namespace ksc {
 
 constexpr int SEL_CAP = 4096;   // bitonic buffer of the select kernels (>= KSC_MAX_RERANK)
+constexpr int SELS_BIN = 256;   // scratch for the keys of the K-th key's histogram bin
+
+// Keys the select kernels stage in shared memory: 8 R (a power of two, at
+// least 1024, at most SEL_CAP); also the size of their fallback buffers.
+static int sel_keys(int Rmax) { return std::min(SEL_CAP, std::max(1024, pow2_ceil(8 * Rmax))); }
 constexpr int MAX_NPROBE = 4096;
 constexpr int NEAR_KEYS_PER_R = 4;  // keys of the unfiltered first scan: at least 4 R ...
 constexpr int NEAR_SHARE_DIV = 16;  // ... and at least 1/16 of the keys the query probes
@@ -84,9 +89,11 @@ __global__ void __launch_bounds__(256) k_list_scores(const float* __restrict__ Q
 // bin of the P-th smallest score, every list whose score can still be among
 // the P best (score <= upper edge of that bin + 2 err) is re-scored exactly in
 // FP32 (L2: sum_t (q_t - c_t)^2 in the direct form; spherical: -<q, c>), and
-// the P best by (exact score, list id) are kept.  If more than RS_CAP lists
-// qualify, every list is re-scored and sorted.
-constexpr int RS_CAP = 4096;
+// the P best by (exact score, list id) are kept.  If more lists qualify than
+// the re-score buffer holds (4 Pmax, at least 1024, at most RS_CAP), every
+// list is re-scored when all fit, else those with the lowest given scores.
+constexpr int RS_CAP = 4096;     // largest re-score buffer
+constexpr int RS_SMEM_L = 8192;  // score rows up to this length are staged in shared memory
 __device__ __forceinline__ float exact_list_score(const float* __restrict__ qs, const float* __restrict__ c, int d,
                                                   int spherical, int lane) {
     float acc = 0.f;
@@ -118,8 +125,9 @@ __global__ void __launch_bounds__(256) k_rank_select(const float* __restrict__ s
                                                      const float* __restrict__ Q, const float* __restrict__ Cc,
                                                      int64_t nq, int d, int L, int spherical,
                                                      const int32_t* __restrict__ nprobe_q, int Pfix, int Pmax,
-                                                     int32_t* __restrict__ probes, float* __restrict__ score_out) {
-    extern __shared__ uint64_t cand[];  // RS_CAP keys
+                                                     int rs_cap, int32_t* __restrict__ probes,
+                                                     float* __restrict__ score_out) {
+    extern __shared__ uint64_t cand[];  // rs_cap keys, then the row's scores when L <= RS_SMEM_L
     __shared__ uint32_t hist[HIST_BINS];
     __shared__ uint32_t warp_tot[32];
     __shared__ __align__(16) float qs[KSC_MAX_DIM];
@@ -130,6 +138,12 @@ __global__ void __launch_bounds__(256) k_rank_select(const float* __restrict__ s
     int P = nprobe_q ? nprobe_q[q] : Pfix;
     P = P < 1 ? 1 : (P > Pmax ? Pmax : P);
     const float* s = scores + q * L;
+    if (L <= RS_SMEM_L) {
+        // the row is read from global memory once
+        float* ss = reinterpret_cast<float*>(cand + rs_cap);
+        for (int c = threadIdx.x; c < L; c += blockDim.x) ss[c] = s[c];
+        s = ss;
+    }
     const float e2 = err ? 2.f * err[q] : 0.f;
     for (int t = threadIdx.x; t < d; t += blockDim.x) qs[t] = Q[q * d + t];
     if (threadIdx.x == 0) { s_mn = 0xffffffffu; s_mx = 0u; s_cnt = 0; s_B = -1; }
@@ -177,23 +191,23 @@ __global__ void __launch_bounds__(256) k_rank_select(const float* __restrict__ s
     for (int c = threadIdx.x; c < L; c += blockDim.x) {
         if (s[c] <= tau) {
             int slot = atomicAdd(&s_cnt, 1);
-            if (slot < RS_CAP) cand[slot] = (uint64_t)(uint32_t)c;
+            if (slot < rs_cap) cand[slot] = (uint64_t)(uint32_t)c;
         }
     }
     __syncthreads();
     int n = s_cnt;
-    if (n > RS_CAP) {
+    if (n > rs_cap) {
         // degenerate score distribution: re-score every list if they fit,
-        // else the RS_CAP lists with the lowest given scores
-        if (L <= RS_CAP) {
+        // else the rs_cap lists with the lowest given scores
+        if (L <= rs_cap) {
             n = L;
             for (int c = threadIdx.x; c < L; c += blockDim.x) cand[c] = (uint64_t)(uint32_t)c;
             __syncthreads();
         } else {
-            n = RS_CAP;
+            n = rs_cap;
             auto load = [&](int c) -> uint64_t { return ((uint64_t)ordered_f32(s[c]) << 32) | (uint32_t)c; };
-            block_select_smallest(load, L, RS_CAP, cand, cand, RS_CAP, hist);
-            for (int i = threadIdx.x; i < RS_CAP; i += blockDim.x) cand[i] &= 0xffffffffull;
+            block_select_smallest(load, L, rs_cap, cand, cand, rs_cap, hist);
+            for (int i = threadIdx.x; i < rs_cap; i += blockDim.x) cand[i] &= 0xffffffffull;
             __syncthreads();
         }
     }
@@ -202,12 +216,21 @@ __global__ void __launch_bounds__(256) k_rank_select(const float* __restrict__ s
         const float v = exact_list_score(qs, Cc + (int64_t)c * d, d, spherical, lane);
         if (lane == 0) cand[i] = ((uint64_t)ordered_f32(v) << 32) | (uint32_t)c;
     }
-    const int S = pow2_ceil(n < 2 ? 2 : n);
-    for (int i = n + threadIdx.x; i < S; i += blockDim.x) cand[i] = KEY_NONE;
     __syncthreads();
-    block_bitonic_sort(cand, S);
+    if (n <= 32) {
+        if (w == 0) {
+            const uint64_t v = warp_sort_key(lane < n ? cand[lane] : KEY_NONE, lane);
+            cand[lane] = v;
+        }
+    } else {
+        const int S = pow2_ceil(n);
+        for (int i = n + threadIdx.x; i < S; i += blockDim.x) cand[i] = KEY_NONE;
+        __syncthreads();
+        block_bitonic_sort(cand, S);
+    }
+    __syncthreads();
     for (int r = threadIdx.x; r < Pmax; r += blockDim.x) {
-        if (r < P) {
+        if (r < P && r < n) {
             probes[q * Pmax + r] = (int32_t)(cand[r] & 0xffffffffu);
             if (score_out) score_out[q * Pmax + r] = unordered_f32((uint32_t)(cand[r] >> 32));
         } else {
@@ -573,13 +596,14 @@ __device__ __forceinline__ int rerank_of(const int32_t* rerank_q, int Rfix, int 
 // the R-th key and only that bin is sorted; `scratch` (a row of R keys per
 // query) serves the radix fallback when the bin is too large.
 __global__ void __launch_bounds__(256) k_threshold(ScanArgs A, int Rmax, int32_t* __restrict__ cnt,
-                                                   uint64_t* __restrict__ cand, int cap,
+                                                   uint64_t* __restrict__ cand, int cap, int nkeys,
                                                    uint64_t* __restrict__ scratch, uint64_t* __restrict__ thr) {
-    extern __shared__ uint64_t buf[];  // SEL_CAP keys
+    extern __shared__ uint64_t buf[];  // nkeys keys (the staged keys, or the fallback's buffer), SELS_BIN
     __shared__ uint32_t hist[HIST_BINS];
     __shared__ uint32_t warp_tot[32];
     __shared__ HistSel hs;
     __shared__ int s_nb;
+    __shared__ unsigned long long s_thr;
     const int64_t q = blockIdx.x;
     const int R = rerank_of(A.rerank_q, A.Rfix, A.Rmin, Rmax, q);
     const int n = min(cnt[q], cap);
@@ -587,11 +611,42 @@ __global__ void __launch_bounds__(256) k_threshold(ScanArgs A, int Rmax, int32_t
         if (threadIdx.x == 0) thr[q] = KEY_NONE;
         return;
     }
+    const bool ovf = cnt[q] > cap;  // overflowed: threshold only, the final select redoes this query exactly
     uint64_t* cq = cand + q * cap;
+    if (n <= nkeys) {
+        // staged once; nothing above the R-th key can enter the final R, so the
+        // R keys at or below it replace the store's contents
+        for (int i = threadIdx.x; i < n; i += blockDim.x) buf[i] = cq[i];
+        if (threadIdx.x == 0) s_thr = 0ull;
+        __syncthreads();
+        bool ok = true;
+        if (n == R) {
+            unsigned long long m = 0ull;
+            for (int i = threadIdx.x; i < n; i += blockDim.x) m = max(m, (unsigned long long)buf[i]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if ((threadIdx.x & 31) == 0) atomicMax(&s_thr, m);
+            __syncthreads();
+        } else {
+            uint64_t kth = 0;
+            auto emit = [&](int i, uint64_t k) {
+                if (!ovf) cq[i] = k;
+            };
+            ok = block_topk_smem(buf, n, R, emit, buf + nkeys, SELS_BIN, hist, warp_tot,
+                                 reinterpret_cast<uint64_t*>(&s_thr));
+            (void)kth;
+        }
+        if (ok) {
+            if (threadIdx.x == 0) {
+                thr[q] = s_thr;
+                if (!ovf) cnt[q] = R;
+            }
+            return;
+        }
+    }
     auto load = [&](int i) -> uint64_t { return cq[i]; };
-    __shared__ uint64_t s_thr;
     hist_find(load, n, R, hist, warp_tot, &hs);
-    if (hs.inB <= SEL_CAP) {
+    if (hs.inB <= nkeys) {
         if (threadIdx.x == 0) s_nb = 0;
         __syncthreads();
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -606,15 +661,13 @@ __global__ void __launch_bounds__(256) k_threshold(ScanArgs A, int Rmax, int32_t
         if (threadIdx.x == 0) s_thr = buf[R - hs.lt - 1];
     } else {
         uint64_t* out = scratch + q * Rmax;
-        block_select_smallest(load, n, R, out, buf, SEL_CAP, hist);
+        block_select_smallest(load, n, R, out, buf, nkeys, hist);
         if (threadIdx.x == 0) s_thr = out[R - 1];
     }
     __syncthreads();
     const uint64_t t = s_thr;
     if (threadIdx.x == 0) thr[q] = t;
-    if (cnt[q] > cap) return;  // overflowed: the final select redoes this query exactly
-    // keep only the R keys at or below the threshold: nothing above it can
-    // enter the final R
+    if (ovf) return;
     if (threadIdx.x == 0) s_nb = 0;
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -1048,6 +1101,166 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32, (SMAX <= 4 ? 3 : (SMAX <= 8 ?
     }
 }
 
+// ------------------------------------------------------------------ a3: LUT16 scan, one lane per block
+// Same warp items as k_scan with 4 lanes per query (list p, 8 queries that
+// probe p, tile [b0, b1) of p's blocks), but the 4 lanes of a query take 4
+// different blocks of each step and each sums all M subspaces of its block's
+// 32 vectors, so no cross-lane reduction is needed.  Lane = (slot s = lane & 7,
+// block bo = lane >> 3).  The item's 8 tables of subspace j sit side by side in
+// shared memory (T[j][s], 16 B each): the 8 lanes of a quarter-warp (same bo,
+// s = 0..7) read 128 contiguous bytes, and they share one block, so its code
+// chunk is a broadcast.  Codes arrive in steps of 4 blocks by cp.async.bulk
+// into two alternating buffers, as in k_scan.
+constexpr int S4_WARPS = 4;
+constexpr int S4_Q = 8;  // queries per item
+constexpr int S4_B = 4;  // blocks per step
+
+template <int MAXM>
+__host__ __device__ constexpr int s4_warp_bytes() { return MAXM * S4_Q * 16 + 2 * S4_B * MAXM * 16; }
+
+template <int MAXM>
+__global__ void __launch_bounds__(S4_WARPS * 32, MAXM <= 64 ? 3 : 1)
+    k_scan4(ScanArgs A, ScanOut O, const int64_t* __restrict__ pair_off, const int64_t* __restrict__ item_off,
+            const uint32_t* __restrict__ pairs, int L, int TB, int32_t* __restrict__ status) {
+    constexpr int TAB_BYTES = MAXM * S4_Q * 16;
+    constexpr int BUF_BYTES = S4_B * MAXM * 16;
+    extern __shared__ __align__(128) uint8_t sm4[];
+    __shared__ __align__(8) uint64_t full[S4_WARPS][2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int s = lane & 7, bo = lane >> 3;
+    const int M = A.M, blk_bytes = M * 16;
+    uint8_t* wb = sm4 + (size_t)warp * s4_warp_bytes<MAXM>();
+    uint4* tab = reinterpret_cast<uint4*>(wb);
+    uint8_t* cbuf = wb + TAB_BYTES;
+    const uint32_t bar0 = smem_addr(&full[warp][0]), bar1 = smem_addr(&full[warp][1]);
+    if (lane == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    auto issue = [&](const ScanItem& x, int c, int b) {
+        const int c0 = x.b0 + c * S4_B, c1 = min(x.b1, c0 + S4_B);
+        const uint32_t bytes = (uint32_t)(c1 - c0) * blk_bytes;
+        const uint32_t bar = b ? bar1 : bar0;
+        const uint8_t* src = A.codes + (A.boff[x.p] + c0) * (int64_t)blk_bytes;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         smem_addr(cbuf + b * BUF_BYTES)),
+                     "l"(src), "r"(bytes), "r"(bar)
+                     : "memory");
+    };
+    const int64_t total = item_off[L];
+    const int64_t stride = (int64_t)gridDim.x * S4_WARPS;
+    int64_t it = (int64_t)blockIdx.x * S4_WARPS + warp;
+    if (it >= total) return;
+    ScanItem x = locate_item(A, pair_off, item_off, L, TB, S4_Q, it);
+    if (lane == 0) issue(x, 0, 0);
+    uint32_t phase[2] = {0u, 0u};
+    int b = 0;
+    bool failed = false;
+    while (true) {
+        // the item's tables, transposed to T[j][s] (zeros for empty slots)
+        const int nslots = x.npairs < S4_Q ? (int)x.npairs : S4_Q;
+        for (int e = lane; e < S4_Q * M; e += 32) {
+            const int qs = e / M, j = e - qs * M;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (qs < nslots) v = __ldg(reinterpret_cast<const uint4*>(A.lut + (int64_t)pairs[x.g0 + qs] * M * PQ_K) + j);
+            tab[j * S4_Q + qs] = v;
+        }
+        const bool active = s < nslots;
+        int64_t q = 0;
+        int32_t bias = 0, lim = -1;
+        uint32_t thI = 0;
+        if (active) {
+            const uint32_t e = pairs[x.g0 + s];
+            q = e / A.Pmax;
+            bias = A.bias[e];
+            const uint64_t th = O.thr ? O.thr[q] : KEY_NONE;
+            thI = (uint32_t)th;
+            // key high word (bias + sum) + 2^31 <= thD  <=>  sum <= thD - 2^31 - bias
+            const int64_t l = (int64_t)(th >> 32) - 2147483648ll - bias;
+            lim = (int32_t)(l < -1 ? -1 : (l > 65536 ? 65536 : l));
+        }
+        const int listn = A.list_n[x.p];
+        const int64_t gb_list = A.boff[x.p];
+        __syncwarp();
+        const int nch = (x.b1 - x.b0 + S4_B - 1) / S4_B;
+        const int64_t next_it = it + stride;
+        for (int c = 0; c < nch; ++c) {
+            if (lane == 0) {
+                if (c + 1 < nch) issue(x, c + 1, b ^ 1);
+                else if (next_it < total) issue(locate_item(A, pair_off, item_off, L, TB, S4_Q, next_it), 0, b ^ 1);
+            }
+            const bool ready = !failed && scan_wait(b ? bar1 : bar0, phase[b]);
+            phase[b] ^= 1u;
+            if (!ready) {
+                if (lane == 0 && !failed) atomicOr(status, 4);  // a chunk never arrived: the warp stops
+                failed = true;
+            } else {
+                const int c0 = x.b0 + c * S4_B, nblk = min(x.b1, c0 + S4_B) - c0;
+                const int blk = c0 + bo;
+                uint32_t acc[16];
+#pragma unroll
+                for (int m = 0; m < 16; ++m) acc[m] = 0u;
+                uint32_t kmask = 0;
+                if (bo < nblk) {
+                    const uint4* cp = reinterpret_cast<const uint4*>(cbuf + b * BUF_BYTES + bo * blk_bytes);
+                    const uint4* tp = tab + s;
+                    int j = 0;
+                    for (; j + 1 < M; j += 2) accum_pair(cp[j], tp[j * S4_Q], cp[j + 1], tp[(j + 1) * S4_Q], acc);
+                    if (j < M) accum_chunk(cp[j], tp[j * S4_Q], acc);
+                    if (active) {
+                        const int nv = listn - blk * 32;
+                        const uint32_t vmask = nv >= 32 ? 0xffffffffu : ((1u << nv) - 1u);
+                        uint32_t lt = 0, eq = 0;
+#pragma unroll
+                        for (int m = 0; m < 16; ++m) {
+                            const int a0 = (int)(acc[m] & 0xffffu), a1 = (int)(acc[m] >> 16);
+                            lt |= ((uint32_t)(a0 < lim) << (2 * m)) | ((uint32_t)(a1 < lim) << (2 * m + 1));
+                            eq |= ((uint32_t)(a0 == lim) << (2 * m)) | ((uint32_t)(a1 == lim) << (2 * m + 1));
+                        }
+                        lt &= vmask;
+                        eq &= vmask;
+                        while (eq) {  // a key equal to the threshold's distance: its id decides
+                            const int v = __ffs(eq) - 1;
+                            eq &= eq - 1u;
+                            if ((uint32_t)A.ids[(gb_list + blk) * 32 + v] <= thI) lt |= 1u << v;
+                        }
+                        kmask = lt;
+                    }
+                }
+                // one atomic per query and step: counts of its 4 lanes
+                const int n = __popc(kmask);
+                const int n0 = __shfl_sync(0xffffffffu, n, s), n1 = __shfl_sync(0xffffffffu, n, s + 8);
+                const int n2 = __shfl_sync(0xffffffffu, n, s + 16), n3 = __shfl_sync(0xffffffffu, n, s + 24);
+                const int tot = n0 + n1 + n2 + n3;
+                int base = (bo == 0 && tot > 0) ? atomicAdd(&O.cnt[q], tot) : 0;
+                base = __shfl_sync(0xffffffffu, base, s) + (bo > 0 ? n0 : 0) + (bo > 1 ? n1 : 0) + (bo > 2 ? n2 : 0);
+                if (kmask) {
+                    const int32_t* idp = A.ids + (gb_list + blk) * 32;
+                    uint64_t* out = O.cand + q * O.cap;
+#pragma unroll
+                    for (int v = 0; v < 32; ++v) {
+                        if ((kmask >> v) & 1u) {
+                            const int at = base + __popc(kmask & ((1u << v) - 1u));
+                            const uint32_t sum = (v & 1) ? (acc[v >> 1] >> 16) : (acc[v >> 1] & 0xffffu);
+                            const uint32_t Dk = (uint32_t)(bias + (int32_t)sum) ^ 0x80000000u;
+                            if (at < O.cap) out[at] = ((uint64_t)Dk << 32) | (uint32_t)idp[v];
+                        }
+                    }
+                }
+            }
+            __syncwarp();  // the whole warp is done with buffer b (and the tables) before they are refilled
+            b ^= 1;
+        }
+        if (next_it >= total || failed) break;
+        it = next_it;
+        x = locate_item(A, pair_off, item_off, L, TB, S4_Q, it);
+    }
+}
+
 // ------------------------------------------------------------------ a4: hybrid graph search
 // Work lists from an explicit pair array (the lists marked for a full scan).
 __global__ void k_count_from(const uint32_t* __restrict__ src, const int64_t* __restrict__ nsrc,
@@ -1258,10 +1471,11 @@ __global__ void __launch_bounds__(256) k_select(ScanArgs A, int Rmax, const int3
                                                 uint64_t* __restrict__ topr, int32_t* __restrict__ ncand,
                                                 int32_t* __restrict__ status,
                                                 unsigned long long* __restrict__ stats) {
-    extern __shared__ uint64_t sbuf[];
+    extern __shared__ uint64_t sbuf[];  // sel_cap keys (staged keys, or the fallbacks' buffer), SELS_BIN
     __shared__ uint32_t hist[HIST_BINS];
     __shared__ uint32_t warp_tot[32];
     __shared__ int32_t s_pref[MAX_NPROBE + 1];
+    __shared__ uint64_t s_kth;
     const int64_t q = blockIdx.x;
     const int R = rerank_of(A.rerank_q, A.Rfix, A.Rmin, Rmax, q);
     const int n = cnt[q];
@@ -1272,10 +1486,23 @@ __global__ void __launch_bounds__(256) k_select(ScanArgs A, int Rmax, const int3
         if (n > cap) atomicAdd(&stats[0], 1ull);
     }
     if (n <= cap) {
+        // the R smallest, in no particular order (the re-rank does not need one)
         const uint64_t* cq = cand + q * cap;
         const int K = min(R, n);
-        auto load = [&](int i) -> uint64_t { return cq[i]; };
-        block_select_hist(load, n, K, out, sbuf, sel_cap, hist, warp_tot);
+        bool done = false;
+        if (n <= K) {
+            for (int i = threadIdx.x; i < n; i += blockDim.x) out[i] = cq[i];
+            done = true;
+        } else if (n <= sel_cap) {
+            for (int i = threadIdx.x; i < n; i += blockDim.x) sbuf[i] = cq[i];
+            __syncthreads();
+            auto emit = [&](int i, uint64_t k) { out[i] = k; };
+            done = block_topk_smem(sbuf, n, K, emit, sbuf + sel_cap, SELS_BIN, hist, warp_tot, &s_kth);
+        }
+        if (!done) {
+            auto load = [&](int i) -> uint64_t { return cq[i]; };
+            block_select_hist(load, n, K, out, sbuf, sel_cap, hist, warp_tot);
+        }
         for (int i = K + threadIdx.x; i < Rmax; i += blockDim.x) out[i] = KEY_NONE;
         if (threadIdx.x == 0 && ncand) ncand[q] = K;
         return;
@@ -1394,10 +1621,36 @@ __global__ void __launch_bounds__(256) k_rerank(const float* __restrict__ Q, con
         }
         if (lane == 0) keys[c] = outk;
     }
-    const int S = pow2_ceil(R < 2 ? 2 : R);
-    for (int i = R + threadIdx.x; i < S; i += blockDim.x) keys[i] = KEY_NONE;
     __syncthreads();
-    block_bitonic_sort(keys, S);
+    if (k <= 32) {
+        // k rounds of a warp minimum over the R keys (each taken key is retired)
+        if (w == 0) {
+            uint64_t mine = KEY_NONE;  // lane r keeps the r-th smallest
+            for (int r = 0; r < k; ++r) {
+                uint64_t m = KEY_NONE;
+                int at = -1;
+                for (int i = lane; i < R; i += 32) {
+                    if (keys[i] < m) { m = keys[i]; at = i; }
+                }
+                uint64_t g = m;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const uint64_t y = __shfl_xor_sync(0xffffffffu, g, o);
+                    g = y < g ? y : g;
+                }
+                if (g != KEY_NONE && m == g) keys[at] = KEY_NONE;  // keys are unique: one lane matches
+                __syncwarp();
+                if (lane == r) mine = g;
+            }
+            if (lane < k) keys[lane] = mine;
+        }
+        __syncthreads();
+    } else {
+        const int S = pow2_ceil(R < 2 ? 2 : R);
+        for (int i = R + threadIdx.x; i < S; i += blockDim.x) keys[i] = KEY_NONE;
+        __syncthreads();
+        block_bitonic_sort(keys, S);
+    }
     for (int r = threadIdx.x; r < k; r += blockDim.x) {
         const uint64_t kk = r < R ? keys[r] : KEY_NONE;
         if (kk == KEY_NONE) {
@@ -1505,13 +1758,17 @@ __global__ void k_pair_dist(const float* __restrict__ Q, int64_t nq, int d, int 
     }
 }
 
-__global__ void k_copy_cands(const uint64_t* __restrict__ topr, int Rmax, int64_t nq, int R,
-                             uint64_t* __restrict__ out) {
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= nq * R) return;
-    int64_t q = e / R;
-    int r = (int)(e - q * R);
-    out[e] = topr[q * Rmax + r];
+// Candidate export: each query's R selected keys, ascending (the select
+// leaves them unordered).  One CTA per query.
+__global__ void __launch_bounds__(256) k_copy_cands(const uint64_t* __restrict__ topr, int Rmax,
+                                                    uint64_t* __restrict__ out) {
+    extern __shared__ uint64_t cs[];
+    const int64_t q = blockIdx.x;
+    const int S = pow2_ceil(Rmax < 2 ? 2 : Rmax);
+    for (int i = threadIdx.x; i < S; i += blockDim.x) cs[i] = i < Rmax ? topr[q * Rmax + i] : KEY_NONE;
+    __syncthreads();
+    block_bitonic_sort(cs, S);
+    for (int i = threadIdx.x; i < Rmax; i += blockDim.x) out[q * Rmax + i] = cs[i];
 }
 
 // ------------------------------------------------------------------ host pipeline
@@ -1538,6 +1795,7 @@ struct Plan {
 };
 
 static int choose_G(const ksc_index* ix, int64_t nq, int Pmax, int want) {
+    if (want == 4 && ix->M <= 128) return 4;
     if (want == 8 || want == 16 || want == 32) {
         int S = (ix->M + want - 1) / want;
         if (S <= 16) return want;
@@ -1558,6 +1816,19 @@ static int launch_scan(const ScanArgs& A, const ScanOut& O, const int64_t* pair_
     KSC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scan<G, SMAX>, SCAN_WARPS * 32, smem));
     const int grid = num_sms() * (per_sm > 0 ? per_sm : 1);
     k_scan<G, SMAX><<<grid, SCAN_WARPS * 32, smem, st>>>(A, O, pair_off, item_off, pairs, L, TB, status);
+    KSC_LAUNCH_CHECK();
+    return KSC_OK;
+}
+
+template <int MAXM>
+static int launch_scan4(const ScanArgs& A, const ScanOut& O, const int64_t* pair_off, const int64_t* item_off,
+                        const uint32_t* pairs, int L, int TB, int32_t* status, cudaStream_t st) {
+    const size_t smem = (size_t)S4_WARPS * s4_warp_bytes<MAXM>();
+    KSC_CUDA(cudaFuncSetAttribute(k_scan4<MAXM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    KSC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scan4<MAXM>, S4_WARPS * 32, smem));
+    const int grid = num_sms() * (per_sm > 0 ? per_sm : 1);
+    k_scan4<MAXM><<<grid, S4_WARPS * 32, smem, st>>>(A, O, pair_off, item_off, pairs, L, TB, status);
     KSC_LAUNCH_CHECK();
     return KSC_OK;
 }
@@ -1594,10 +1865,12 @@ static int rank_lists(ksc_index* ix, const float* Q, int64_t nq, const int32_t* 
     float* scores = (float*)ix->ws_scores.p;
     float* err = nullptr;
     KSC_TRY(list_scores(ix, Q, nq, exact, scores, &err, st));
-    const size_t smem = RS_CAP * sizeof(uint64_t);
+    // re-score buffer: 4 Pmax lists (a power of two, at least 1024, at most RS_CAP)
+    const int rs_cap = std::min(RS_CAP, std::max(1024, pow2_ceil(4 * Pmax)));
+    const size_t smem = rs_cap * sizeof(uint64_t) + (ix->L <= RS_SMEM_L ? sizeof(float) * ix->L : 0);
     cudaFuncSetAttribute(k_rank_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_rank_select<<<(unsigned)nq, 256, smem, st>>>(scores, err, Q, ix->c_rank, nq, ix->d, ix->L, ix->spherical,
-                                                   nprobe_q, Pfix, Pmax, probes, score_out);
+                                                   nprobe_q, Pfix, Pmax, rs_cap, probes, score_out);
     ix->launches++;
     KSC_LAUNCH_CHECK();
     return KSC_OK;
@@ -1681,6 +1954,12 @@ static int build_worklist(ksc_index* ix, const ScanArgs& A, int rs, const int32_
 static int run_scan(const Plan& pl, int M, const ScanArgs& A, const ScanOut& O, const WorkList& w, int L,
                     int32_t* status, cudaStream_t st) {
     const int S = (M + pl.G - 1) / pl.G;
+    if (pl.G == 4) {
+        if (M <= 64) return launch_scan4<64>(A, O, w.pair_off, w.item_off, w.pairs, L, pl.TB, status, st);
+        if (M <= 128) return launch_scan4<128>(A, O, w.pair_off, w.item_off, w.pairs, L, pl.TB, status, st);
+        set_error("M too large for 4 lanes per query");
+        return KSC_EINVAL;
+    }
     if (pl.G == 8) return dispatch_scan<8>(S, A, O, w.pair_off, w.item_off, w.pairs, L, pl.TB, status, st);
     if (pl.G == 16) return dispatch_scan<16>(S, A, O, w.pair_off, w.item_off, w.pairs, L, pl.TB, status, st);
     return dispatch_scan<32>(S, A, O, w.pair_off, w.item_off, w.pairs, L, pl.TB, status, st);
@@ -1768,9 +2047,10 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
     KSC_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * nq, st));
     KSC_TRY(run_scan(pl, M, A, ScanOut{nullptr, cnt, cand, pl.cap}, wa, L, ix->status, st));
     {
-        const size_t smem = SEL_CAP * sizeof(uint64_t);
+        const int nkeys = sel_keys(pl.Rmax);
+        const size_t smem = (nkeys + SELS_BIN) * sizeof(uint64_t);
         cudaFuncSetAttribute(k_threshold, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_threshold<<<(unsigned)nq, 256, smem, st>>>(A, pl.Rmax, cnt, cand, pl.cap, topr, thr);
+        k_threshold<<<(unsigned)nq, 256, smem, st>>>(A, pl.Rmax, cnt, cand, pl.cap, nkeys, topr, thr);
         KSC_LAUNCH_CHECK();
         ix->launches += 2;
     }
@@ -1817,8 +2097,8 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
     {
         // shared buffer: the R best plus the ties of the histogram bin at the
         // R-th key (radix select beyond it)
-        const int sel_cap = std::min(SEL_CAP, std::max(1024, pow2_ceil(2 * pl.Rmax)));
-        const size_t smem = sel_cap * sizeof(uint64_t);
+        const int sel_cap = sel_keys(pl.Rmax);
+        const size_t smem = (sel_cap + SELS_BIN) * sizeof(uint64_t);
         cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_select<<<(unsigned)nq, 256, smem, st>>>(A, pl.Rmax, cnt, sel_cap, cand, pl.cap, topr, ncand_out, ix->status,
                                                   ix->stats);
@@ -1826,7 +2106,9 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
         KSC_LAUNCH_CHECK();
     }
     if (cand_out) {
-        k_copy_cands<<<blocks_for(nq * pl.Rmax, 256), 256, 0, st>>>(topr, pl.Rmax, nq, pl.Rmax, cand_out);
+        const size_t csm = sizeof(uint64_t) * pow2_ceil(pl.Rmax < 2 ? 2 : pl.Rmax);
+        KSC_CUDA(cudaFuncSetAttribute(k_copy_cands, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
+        k_copy_cands<<<(unsigned)nq, 256, csm, st>>>(topr, pl.Rmax, cand_out);
         ix->launches++;
         KSC_LAUNCH_CHECK();
     }
@@ -1888,6 +2170,7 @@ static int make_plan(ksc_index* ix, int64_t nq, int k, int Pmax, int Rmax, const
         const double target = 64.0 * num_sms();
         int TB = (int)(blocks / target);
         pl.TB = TB < 2 ? 2 : (TB > 64 ? 64 : TB);
+        if (pl.G == 4) pl.TB = (pl.TB + S4_B - 1) / S4_B * S4_B;  // whole steps of 4 blocks
         if (opts && opts->tile_blocks > 0) pl.TB = std::min(opts->tile_blocks, 1 << 20);
     }
     int cap = (opts && opts->cand_cap > 0) ? opts->cand_cap : std::max(32 * Rmax, 8192);
@@ -2579,13 +2862,13 @@ int ksc_autotune(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t k, int32
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int Gs[3] = {8, 16, 32};
+    const int Gs[4] = {4, 8, 16, 32};
     const int TBs[5] = {0, 8, 16, 32, 64};
     ksc_search_opts best = *opts;
     float best_ms = INFINITY;
     int rc = KSC_OK;
-    for (int gi = 0; gi < 3 && rc == KSC_OK; ++gi) {
-        if ((ix->M + Gs[gi] - 1) / Gs[gi] > 16) continue;
+    for (int gi = 0; gi < 4 && rc == KSC_OK; ++gi) {
+        if (Gs[gi] == 4 ? ix->M > 128 : (ix->M + Gs[gi] - 1) / Gs[gi] > 16) continue;
         for (int ti = 0; ti < 5 && rc == KSC_OK; ++ti) {
             ksc_search_opts o = *opts;
             o.lanes_per_query = Gs[gi];

@@ -63,7 +63,7 @@ def test_autotune_picks_an_exact_configuration(env):
     torch, ksc, g = env
     Q = torch.from_numpy(synth.queries(2, 1000)).cuda()
     opts, ms = g.autotune(Q, 10, 12, 200)
-    assert opts.lanes_per_query in (8, 16, 32) and opts.tile_blocks in (0, 8, 16, 32, 64) and ms > 0
+    assert opts.lanes_per_query in (4, 8, 16, 32) and opts.tile_blocks in (0, 8, 16, 32, 64) and ms > 0
     a = g.search(Q, 10, 12, 200)
     b = g.search(Q, 10, 12, 200, opts=opts)
     assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])

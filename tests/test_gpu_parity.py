@@ -130,9 +130,9 @@ def test_luts_of_a_misaligned_query_matrix(torch, ksc):
         assert torch.equal(x, y)
 
 
-@pytest.mark.parametrize("kind,lanes", [("l2", 8), ("l2", 16), ("l2", 32), ("ip", 8), ("ip", 32),
-                                        ("m50", 8), ("m50", 16), ("m50", 32), ("small", 0), ("ds4", 8),
-                                        ("ds3ip", 16)])
+@pytest.mark.parametrize("kind,lanes", [("l2", 4), ("l2", 8), ("l2", 16), ("l2", 32), ("ip", 4), ("ip", 8),
+                                        ("ip", 32), ("m50", 4), ("m50", 8), ("m50", 16), ("m50", 32), ("small", 0),
+                                        ("small", 4), ("ds4", 4), ("ds4", 8), ("ds3ip", 4), ("ds3ip", 16)])
 def test_scan_candidates_bit_exact(torch, ksc, kind, lanes):
     ix, Q = small_index(kind)
     g = gpu_index(ksc, ix)
