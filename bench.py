@@ -58,6 +58,24 @@ def max_over_ranks(v, ws):
     return float(t.item())
 
 
+def rank_queries(rank, nq):
+    """This rank's own query batch: rank 0 the standard 10k, rank r > 0 an
+    independent stream of the same distribution."""
+    from paper_2511_03298_gb300 import synth
+    return synth.queries(2, nq, stream=rank)
+
+
+def common_nprobe(own, ws):
+    """Operating point shared by all ranks: the largest of their own choices,
+    so every rank's batch reaches the recall target."""
+    return int(max_over_ranks(float(own), ws))
+
+
+def weak_value(nq, ws, ms_max):
+    """Whole-job queries/s: every rank's batch over the slowest rank's time."""
+    return nq * ws / (ms_max * 1e-3)
+
+
 class Clocks:
     """nvidia-smi samples of SM clock and throttle reasons during a region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -163,7 +181,7 @@ def run_ours(args, rank, ws):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     X = synth.base(2)
-    Qh = synth.queries(2)
+    Qh = rank_queries(rank, CFG["nq"])
     Xd = torch.from_numpy(X).to(dev)
     Qd = torch.from_numpy(Qh).to(dev)
     t0 = time.time()
@@ -186,6 +204,11 @@ def run_ours(args, rank, ws):
             if rec >= TARGET_RECALL:
                 nprobe = P
                 break
+        agreed = common_nprobe(nprobe, ws)
+        if agreed != nprobe:
+            ids, _ = ix.search(Qd, k, agreed, R)
+            sweep[agreed] = round(recall_at_10(torch, Xd, Qd, ids, true_d, k), 4)
+            nprobe = agreed
         recall = sweep[nprobe]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     st = torch.cuda.current_stream()
@@ -268,7 +291,7 @@ def run_ours(args, rank, ws):
     else:
         ms, stage_avg, launches, clocks = plain_ms, plain_stage, plain_launches, plain_clk
     ms_max = max_over_ranks(ms, ws)
-    value = CFG["nq"] * ws / (ms_max * 1e-3)
+    value = weak_value(CFG["nq"], ws, ms_max)
     stage_ms = {s_: [v] for s_, v in stage_avg.items()}
     # end to end through the public API with host buffers
     Qpin = torch.from_numpy(Qh).pin_memory()
@@ -292,7 +315,7 @@ def run_ours(args, rank, ws):
         e1.synchronize()
         if it >= args.warmup:
             e2e_ms.append(e0.elapsed_time(e1))
-    e2e = CFG["nq"] * ws / (max_over_ranks(statistics.mean(e2e_ms), ws) * 1e-3)
+    e2e = weak_value(CFG["nq"], ws, max_over_ranks(statistics.mean(e2e_ms), ws))
     # roofline of the dominant kernel (the LUT16 scan): lookups per launch
     pmax_r = learned["params"]["pmax"] if use_learned else nprobe
     probes, _ = ix.rank_lists(Qd, pmax_r, want_scores=False)

@@ -94,10 +94,12 @@ def base(cfg, n=None):
     return _draw(c, prm, CONFIGS[c]["n"] if n is None else n, rng)
 
 
-def queries(cfg, nq=None):
+def queries(cfg, nq=None, stream=0):
+    """Queries of config `cfg`; stream s > 0 gives an independent batch of the
+    same distribution (one per process of a multi-process run)."""
     c = 2 if cfg == 5 else cfg
     prm = _mixture_params(c)
-    rng = np.random.default_rng(2000 + c)
+    rng = np.random.default_rng(2000 + c if stream == 0 else [2000 + c, stream])
     return _draw(c, prm, CONFIGS[c]["nq"] if nq is None else nq, rng)
 
 
