@@ -846,6 +846,34 @@ __device__ __forceinline__ void accum_pair(const uint4& c0, const uint4& t0, con
 // Reduce-scatter of the 16 u16x2 sums over the G lanes of a group: after it,
 // group lane g holds the full sums of vectors V*g .. V*g+V-1 (V = 32/G) in
 // out[0..V) (u16 values).
+// The same lookups with the widening done by byte dot products (dp4a with a
+// one-hot byte selector adds byte b of the looked-up word to a 32-bit sum):
+// acc[v] is the sum of vector v.  The dot products issue on the FMA pipe, so
+// the integer pipe keeps only the selector and permute work.
+__device__ __forceinline__ void widen_add4(uint32_t x, uint32_t* acc) {
+    acc[0] = __dp4a(x, 0x00000001u, acc[0]);
+    acc[1] = __dp4a(x, 0x00000100u, acc[1]);
+    acc[2] = __dp4a(x, 0x00010000u, acc[2]);
+    acc[3] = __dp4a(x, 0x01000000u, acc[3]);
+}
+
+__device__ __forceinline__ void accum_chunk32(const uint4& c, const uint4& t, uint32_t (&acc)[32]) {
+    const uint32_t w[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        uint32_t lo, hi;
+        lut16x8(w[k], t, lo, hi);
+        widen_add4(lo, acc + 8 * k);
+        widen_add4(hi, acc + 8 * k + 4);
+    }
+}
+
+__device__ __forceinline__ void accum_pair32(const uint4& c0, const uint4& t0, const uint4& c1, const uint4& t1,
+                                             uint32_t (&acc)[32]) {
+    accum_chunk32(c0, t0, acc);
+    accum_chunk32(c1, t1, acc);
+}
+
 template <int G>
 __device__ __forceinline__ void reduce_scatter(uint32_t (&acc)[16], int lane, uint32_t (&out)[32 / G]) {
     constexpr int V = 32 / G;
@@ -953,7 +981,7 @@ struct ChunkCursor {
 };
 
 template <int G, int SMAX>
-__global__ void __launch_bounds__(SCAN_WARPS * 32, (SMAX <= 4 ? 3 : (SMAX <= 8 ? 2 : 1))) k_scan(ScanArgs A, ScanOut O, const int64_t* __restrict__ pair_off,
+__global__ void __launch_bounds__(SCAN_WARPS * 32, (SMAX <= 2 ? 3 : (SMAX <= 8 ? 2 : 1))) k_scan(ScanArgs A, ScanOut O, const int64_t* __restrict__ pair_off,
                                                           const int64_t* __restrict__ item_off,
                                                           const uint32_t* __restrict__ pairs, int L, int TB,
                                                           int32_t* __restrict__ status) {
@@ -1041,19 +1069,23 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32, (SMAX <= 4 ? 3 : (SMAX <= 8 ?
                 const int64_t gb0 = A.boff[x.p] + c0;
                 for (int blk = 0; blk < nblk; ++blk) {
                     const uint4* cp = reinterpret_cast<const uint4*>(chunk + blk * blk_bytes);
-                    uint32_t acc[16];
+                    uint32_t a32[32];
 #pragma unroll
-                    for (int m = 0; m < 16; ++m) acc[m] = 0;
+                    for (int m = 0; m < 32; ++m) a32[m] = 0;
 #pragma unroll
                     for (int u = 0; u + 1 < SMAX; u += 2) {
                         const int j = g + G * u;
-                        if (u + 1 < S && j + G < M) accum_pair(cp[j], t[u], cp[j + G], t[u + 1], acc);
-                        else if (u < S && j < M) accum_chunk(cp[j], t[u], acc);
+                        if (u + 1 < S && j + G < M) accum_pair32(cp[j], t[u], cp[j + G], t[u + 1], a32);
+                        else if (u < S && j < M) accum_chunk32(cp[j], t[u], a32);
                     }
                     if (SMAX & 1) {
                         const int u = SMAX - 1, j = g + G * u;
-                        if (u < S && j < M) accum_chunk(cp[j], t[u], acc);
+                        if (u < S && j < M) accum_chunk32(cp[j], t[u], a32);
                     }
+                    // partial sums < 2^16: pack vector pairs for the reduction
+                    uint32_t acc[16];
+#pragma unroll
+                    for (int m = 0; m < 16; ++m) acc[m] = prmt(a32[2 * m], a32[2 * m + 1], 0x5410u);
                     uint32_t sums[V];
                     reduce_scatter<G>(acc, lane, sums);
                     // keys at or below the threshold, appended with one atomic per
@@ -1201,25 +1233,24 @@ __global__ void __launch_bounds__(S4_WARPS * 32, MAXM <= 64 ? 3 : 1)
             } else {
                 const int c0 = x.b0 + c * S4_B, nblk = min(x.b1, c0 + S4_B) - c0;
                 const int blk = c0 + bo;
-                uint32_t acc[16];
+                uint32_t acc[32];  // sum of vector v of the block
 #pragma unroll
-                for (int m = 0; m < 16; ++m) acc[m] = 0u;
+                for (int m = 0; m < 32; ++m) acc[m] = 0u;
                 uint32_t kmask = 0;
                 if (bo < nblk) {
                     const uint4* cp = reinterpret_cast<const uint4*>(cbuf + b * BUF_BYTES + bo * blk_bytes);
                     const uint4* tp = tab + s;
                     int j = 0;
-                    for (; j + 1 < M; j += 2) accum_pair(cp[j], tp[j * S4_Q], cp[j + 1], tp[(j + 1) * S4_Q], acc);
-                    if (j < M) accum_chunk(cp[j], tp[j * S4_Q], acc);
+                    for (; j + 1 < M; j += 2) accum_pair32(cp[j], tp[j * S4_Q], cp[j + 1], tp[(j + 1) * S4_Q], acc);
+                    if (j < M) accum_chunk32(cp[j], tp[j * S4_Q], acc);
                     if (active) {
                         const int nv = listn - blk * 32;
                         const uint32_t vmask = nv >= 32 ? 0xffffffffu : ((1u << nv) - 1u);
                         uint32_t lt = 0, eq = 0;
 #pragma unroll
-                        for (int m = 0; m < 16; ++m) {
-                            const int a0 = (int)(acc[m] & 0xffffu), a1 = (int)(acc[m] >> 16);
-                            lt |= ((uint32_t)(a0 < lim) << (2 * m)) | ((uint32_t)(a1 < lim) << (2 * m + 1));
-                            eq |= ((uint32_t)(a0 == lim) << (2 * m)) | ((uint32_t)(a1 == lim) << (2 * m + 1));
+                        for (int v = 0; v < 32; ++v) {
+                            lt |= (uint32_t)((int)acc[v] < lim) << v;
+                            eq |= (uint32_t)((int)acc[v] == lim) << v;
                         }
                         lt &= vmask;
                         eq &= vmask;
@@ -1245,8 +1276,7 @@ __global__ void __launch_bounds__(S4_WARPS * 32, MAXM <= 64 ? 3 : 1)
                     for (int v = 0; v < 32; ++v) {
                         if ((kmask >> v) & 1u) {
                             const int at = base + __popc(kmask & ((1u << v) - 1u));
-                            const uint32_t sum = (v & 1) ? (acc[v >> 1] >> 16) : (acc[v >> 1] & 0xffffu);
-                            const uint32_t Dk = (uint32_t)(bias + (int32_t)sum) ^ 0x80000000u;
+                            const uint32_t Dk = (uint32_t)(bias + (int32_t)acc[v]) ^ 0x80000000u;
                             if (at < O.cap) out[at] = ((uint64_t)Dk << 32) | (uint32_t)idp[v];
                         }
                     }
@@ -1445,20 +1475,20 @@ __global__ void __launch_bounds__(GS_WARPS * 32) k_graph_search(ScanArgs A, Scan
 // (no memory traffic): the lookup rate this formulation can reach on the GPU.
 __global__ void __launch_bounds__(128) k_lut16_peak(int iters, uint32_t seed, uint32_t* __restrict__ sink) {
     uint4 t = make_uint4(seed, seed * 3u + 1u, seed * 5u + 7u, seed * 9u + 3u);
-    uint32_t acc[16];
+    uint32_t acc[32];
 #pragma unroll
-    for (int m = 0; m < 16; ++m) acc[m] = 0;
+    for (int m = 0; m < 32; ++m) acc[m] = 0;
     uint32_t w = seed ^ (blockIdx.x * blockDim.x + threadIdx.x);
     const uint4 t2 = make_uint4(t.y, t.z, t.w, t.x);
     for (int i = 0; i < iters; i += 2) {
         uint4 c = make_uint4(w, w ^ 0x5a5a5a5au, w + 0x01234567u, w ^ 0xf0f0f0f0u);
         uint4 c2 = make_uint4(w ^ 0x0f0f0f0fu, w + 0x89abcdefu, w ^ 0x33333333u, w + 0x13579bdfu);
-        accum_pair(c, t, c2, t2, acc);
+        accum_pair32(c, t, c2, t2, acc);
         w = w * 1664525u + 1013904223u;
     }
     uint32_t s = 0;
 #pragma unroll
-    for (int m = 0; m < 16; ++m) s ^= acc[m];
+    for (int m = 0; m < 32; ++m) s ^= acc[m];
     if (s == 0x12345678u) sink[0] = s;  // keeps the loop alive
 }
 
@@ -2163,13 +2193,14 @@ static int make_plan(ksc_index* ix, int64_t nq, int k, int Pmax, int Rmax, const
     pl.rerank_q = nullptr;
     pl.G = choose_G(ix, nq, Pmax, opts ? opts->lanes_per_query : 0);
     {
-        // tile length: enough warp items to fill the GPU (about 64 per SM), at
-        // most 64 blocks
+        // tile length: about 256 warp items per SM (short tiles balance the
+        // persistent warps; each item still amortises its set-up over 4 to 32
+        // blocks)
         const int QG = 32 / pl.G;
         const double blocks = std::ceil((double)nq * Pmax / ix->L / QG) * ix->nblocks;
-        const double target = 64.0 * num_sms();
+        const double target = 256.0 * num_sms();
         int TB = (int)(blocks / target);
-        pl.TB = TB < 2 ? 2 : (TB > 64 ? 64 : TB);
+        pl.TB = TB < 4 ? 4 : (TB > 32 ? 32 : TB);
         if (pl.G == 4) pl.TB = (pl.TB + S4_B - 1) / S4_B * S4_B;  // whole steps of 4 blocks
         if (opts && opts->tile_blocks > 0) pl.TB = std::min(opts->tile_blocks, 1 << 20);
     }
