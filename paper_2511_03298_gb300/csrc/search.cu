@@ -473,10 +473,11 @@ __global__ void __launch_bounds__(256) k_lut_quant(LutArgs A, const uint32_t* __
     }
 }
 
-// One CTA per query when all of its tables fit in shared memory: the FP32
-// tables of its P_q probes are computed once, their largest range gives the
-// scale, and they are quantised from shared memory (same FP32 rule, same
-// results as the two-pass kernels above).
+// Persistent CTAs, one query at a time, when all of a query's tables fit in
+// shared memory: the codebook is staged once per CTA; the FP32 tables of the
+// query's P_q probes are computed once, their largest range gives the scale,
+// and they are quantised from shared memory (same FP32 rule, same results as
+// the two-pass kernels above).
 template <int DS>
 __global__ void __launch_bounds__(256) k_lut_fused(LutArgs A, int Pb, uint8_t* __restrict__ lut,
                                                    int32_t* __restrict__ bias, float* __restrict__ scale) {
@@ -488,9 +489,9 @@ __global__ void __launch_bounds__(256) k_lut_fused(LutArgs A, int Pb, uint8_t* _
     float* mins = T + (size_t)Pb * M * (PQ_K + 1);     // Pb x M
     float* qs = mins + Pb * M;                         // d (8-byte aligned: every offset above is even)
     __shared__ uint32_t s_rbits;
-    const int64_t q = blockIdx.x;
+    stage_codebook(A, cbs);  // once per CTA; ends with __syncthreads
+    for (int64_t q = blockIdx.x; q < A.nq; q += gridDim.x) {
     const int P = min(probes_of(A, q), Pb);
-    stage_codebook(A, cbs);  // ends with __syncthreads
     for (int t = threadIdx.x; t < A.d; t += blockDim.x) qs[t] = A.Q[q * A.d + t];
     if (threadIdx.x == 0) s_rbits = 0u;
     __syncthreads();
@@ -535,6 +536,8 @@ __global__ void __launch_bounds__(256) k_lut_fused(LutArgs A, int Pb, uint8_t* _
         bias[q * A.Pmax + r] = lut_bias(A, qs, A.c_mean + (int64_t)p * A.d, mins + r * M, a);
     }
     if (threadIdx.x == 0) scale[q] = a;
+    __syncthreads();  // the next query reuses the shared tables
+    }
 }
 
 static size_t lut_fused_smem(int M, int dsub, int d, int Pb) {
@@ -1694,6 +1697,112 @@ __global__ void __launch_bounds__(256) k_rerank(const float* __restrict__ Q, con
     }
 }
 
+// One warp per query (8 per CTA) when k <= 32, R <= RW_MAXR, d <= 128 and
+// d % 4 == 0: lane l holds query coordinates 4l..4l+3; each step gathers 8
+// candidate rows (one 16-byte load per lane and row) and sums the 8 partial
+// dot products across the warp in a halving exchange (9 shuffles for 8 rows);
+// the k best keys are then taken by k rounds of a warp minimum.  Same
+// distance rule as k_rerank (L2 direct difference squares, IP -<q, x>), FP32.
+constexpr int RW_WARPS = 8;
+constexpr int RW_MAXR = 512;
+
+__global__ void __launch_bounds__(RW_WARPS * 32) k_rerank_w(const float* __restrict__ Q, const float* __restrict__ X,
+                                                            int d, int ip, const uint64_t* __restrict__ topr,
+                                                            int Rmax, const int32_t* __restrict__ rerank_q, int Rfix,
+                                                            int k, int64_t nq, int64_t* __restrict__ out_ids,
+                                                            float* __restrict__ out_d) {
+    extern __shared__ uint64_t wkeys[];  // RW_WARPS x Rmax
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t q = (int64_t)blockIdx.x * RW_WARPS + w;
+    if (q >= nq) return;
+    uint64_t* keys = wkeys + (size_t)w * Rmax;
+    const int R = rerank_of(rerank_q, Rfix, k, Rmax, q);
+    const bool inl = lane * 4 < d;
+    float4 qv = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (inl) {  // the query matrix may be only 4-byte aligned
+        const float* qp = Q + q * d + lane * 4;
+        qv = make_float4(qp[0], qp[1], qp[2], qp[3]);
+    }
+    const uint64_t* cq = topr + q * Rmax;
+    // row of the sum this lane holds after the exchange
+    const int myrow = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+    for (int c0 = 0; c0 < R; c0 += 8) {
+        float4 xv[8];
+        int32_t idv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const uint64_t kk = c0 + u < R ? cq[c0 + u] : KEY_NONE;
+            idv[u] = kk != KEY_NONE ? (int32_t)(kk & 0xffffffffu) : -1;
+            xv[u] = (idv[u] >= 0 && inl) ? __ldg(reinterpret_cast<const float4*>(X + (int64_t)idv[u] * d) + lane)
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        float a[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (ip) {
+                a[u] = qv.x * xv[u].x + qv.y * xv[u].y + qv.z * xv[u].z + qv.w * xv[u].w;
+            } else {
+                const float e0 = qv.x - xv[u].x, e1 = qv.y - xv[u].y, e2 = qv.z - xv[u].z, e3 = qv.w - xv[u].w;
+                a[u] = fmaf(e0, e0, fmaf(e1, e1, fmaf(e2, e2, e3 * e3)));
+            }
+        }
+        // halving exchange: 8 rows over 32 lanes
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const bool up = lane & 16;
+            const float send = up ? a[i] : a[i + 4], keep = up ? a[i + 4] : a[i];
+            a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const bool up = lane & 8;
+            const float send = up ? a[i] : a[i + 2], keep = up ? a[i + 2] : a[i];
+            a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+        }
+        {
+            const bool up = lane & 4;
+            const float send = up ? a[0] : a[1], keep = up ? a[1] : a[0];
+            a[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+        }
+        a[0] += __shfl_xor_sync(0xffffffffu, a[0], 2);
+        a[0] += __shfl_xor_sync(0xffffffffu, a[0], 1);
+        const int c = c0 + myrow;
+        if ((lane & 3) == 0 && c < R) {
+            const uint64_t kk = cq[c];
+            keys[c] = kk != KEY_NONE ? (((uint64_t)ordered_f32(ip ? -a[0] : a[0]) << 32) | (kk & 0xffffffffull))
+                                     : KEY_NONE;
+        }
+    }
+    __syncwarp();
+    uint64_t mine = KEY_NONE;  // lane r keeps the r-th smallest
+    for (int r = 0; r < k; ++r) {
+        uint64_t m = KEY_NONE;
+        int at = -1;
+        for (int i = lane; i < R; i += 32) {
+            if (keys[i] < m) { m = keys[i]; at = i; }
+        }
+        uint64_t g = m;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const uint64_t y = __shfl_xor_sync(0xffffffffu, g, o);
+            g = y < g ? y : g;
+        }
+        if (g != KEY_NONE && m == g) keys[at] = KEY_NONE;  // keys are unique: one lane matches
+        __syncwarp();
+        if (lane == r) mine = g;
+    }
+    if (lane < k) {
+        if (mine == KEY_NONE) {
+            out_ids[q * k + lane] = -1;
+            out_d[q * k + lane] = ip ? -INFINITY : INFINITY;
+        } else {
+            out_ids[q * k + lane] = (int64_t)(mine & 0xffffffffu);
+            const float dist = unordered_f32((uint32_t)(mine >> 32));
+            out_d[q * k + lane] = ip ? -dist : dist;
+        }
+    }
+}
+
 // ------------------------------------------------------------------ precision variant
 // Low-precision copies of X for the widened first re-rank: BF16 rows, or FP8
 // e4m3 rows with one FP32 scale per row (x ~ fp8(x / s) * s, s = max|x| / 448).
@@ -2058,13 +2167,13 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
                    ix->c_mean, ix->codebook, ix->L, wa.pairs, wa.pair_off + L, wb.pairs, wb.pair_off + L};
         const size_t fsm = lut_fused_smem(M, ix->dsub, ix->d, pl.Pq_max);
         if (fsm <= 160 * 1024) {
-            if (lut_ds2(LA)) {
-                KSC_CUDA(cudaFuncSetAttribute(k_lut_fused<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
-                k_lut_fused<2><<<(unsigned)nq, 256, fsm, st>>>(LA, pl.Pq_max, lut, bias, scale);
-            } else {
-                KSC_CUDA(cudaFuncSetAttribute(k_lut_fused<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
-                k_lut_fused<0><<<(unsigned)nq, 256, fsm, st>>>(LA, pl.Pq_max, lut, bias, scale);
-            }
+            const bool ds2 = lut_ds2(LA);
+            auto kf = ds2 ? k_lut_fused<2> : k_lut_fused<0>;
+            KSC_CUDA(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
+            int per_sm = 0;
+            KSC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kf, 256, fsm));
+            const int64_t grid = std::min<int64_t>(nq, (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1));
+            kf<<<(unsigned)grid, 256, fsm, st>>>(LA, pl.Pq_max, lut, bias, scale);
             KSC_LAUNCH_CHECK();
             ix->launches++;
         } else {
@@ -2164,7 +2273,14 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
         rr_R = pl.Rf;
         rr_q = nullptr;
     }
-    {
+    if (pl.k <= 32 && rr_R <= RW_MAXR && ix->d <= 128 && (ix->d & 3) == 0) {
+        const size_t smem = sizeof(uint64_t) * RW_WARPS * rr_R;
+        cudaFuncSetAttribute(k_rerank_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_rerank_w<<<(unsigned)((nq + RW_WARPS - 1) / RW_WARPS), RW_WARPS * 32, smem, st>>>(
+            Q, ix->X, ix->d, ix->metric == KSC_IP, rr_keys, rr_R, rr_q, rr_R, pl.k, nq, ids, dists);
+        ix->launches++;
+        KSC_LAUNCH_CHECK();
+    } else {
         const size_t smem = sizeof(uint64_t) * pow2_ceil(rr_R < 2 ? 2 : rr_R);
         cudaFuncSetAttribute(k_rerank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_rerank<<<(unsigned)nq, 256, smem, st>>>(Q, ix->X, ix->d, ix->metric == KSC_IP, rr_keys, rr_R, rr_q, rr_R,
