@@ -182,92 +182,7 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* w
     return r;
 }
 
-// Histogram selection for keys whose high 32 bits are an order-preserving
-// integer distance.  hist_find locates, among N unique keys, the bin B (of
-// HIST_BINS bins of width 1 above the minimum distance; the last bin takes
-// everything beyond) that holds the K-th smallest key, with lt = the number
-// of keys in lower bins and inB = the keys in bin B.
-constexpr int HIST_BINS = 2048;
-struct HistSel {
-    uint32_t base;
-    int B, lt, inB;
-};
-
-__device__ __forceinline__ int hist_bin(uint64_t key, uint32_t base) {
-    uint32_t d = (uint32_t)(key >> 32) - base;
-    return d < (uint32_t)(HIST_BINS - 1) ? (int)d : HIST_BINS - 1;
-}
-
-template <class Load>
-__device__ void hist_find(Load load, int N, int K, uint32_t* hist, uint32_t* warp_tot, HistSel* hs) {
-    __shared__ uint32_t s_min;
-    if (threadIdx.x == 0) s_min = 0xffffffffu;
-    for (int b = threadIdx.x; b < HIST_BINS; b += blockDim.x) hist[b] = 0;
-    __syncthreads();
-    uint32_t mn = 0xffffffffu;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) mn = min(mn, (uint32_t)(load(i) >> 32));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-    if ((threadIdx.x & 31) == 0) atomicMin(&s_min, mn);
-    __syncthreads();
-    const uint32_t base = s_min;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) atomicAdd(&hist[hist_bin(load(i), base)], 1u);
-    __syncthreads();
-    const int per = HIST_BINS / blockDim.x;  // blockDim.x divides HIST_BINS
-    const int b0 = threadIdx.x * per;
-    uint32_t local = 0;
-    for (int b = b0; b < b0 + per; ++b) local += hist[b];
-    const uint32_t excl = block_exclusive_scan(local, warp_tot);
-    if (excl < (uint32_t)K && excl + local >= (uint32_t)K) {
-        uint32_t c = excl;
-        for (int b = b0; b < b0 + per; ++b) {
-            if (c + hist[b] >= (uint32_t)K) {
-                hs->base = base;
-                hs->B = b;
-                hs->lt = (int)c;
-                hs->inB = (int)hist[b];
-                break;
-            }
-            c += hist[b];
-        }
-    }
-    __syncthreads();
-}
-
-// K smallest of N unique distance keys, sorted, into out[0..K) (K <= N).
-// Keys of the bins up to B (K plus the ties of bin B) are gathered into buf
-// (cap keys, a power of two) and sorted; if they do not fit, the radix
-// select above runs instead.
-template <class Load>
-__device__ void block_select_hist(Load load, int N, int K, uint64_t* out, uint64_t* buf, int cap,
-                                  uint32_t* hist, uint32_t* warp_tot) {
-    __shared__ HistSel hs;
-    __shared__ int s_cnt;
-    if (K <= 0) return;
-    if (N <= 512 && N <= cap) {
-        block_select_smallest(load, N, K, out, buf, cap, hist);
-        return;
-    }
-    hist_find(load, N, K, hist, warp_tot, &hs);
-    const int need = hs.lt + hs.inB;
-    if (need > cap) {
-        block_select_smallest(load, N, K, out, buf, cap, hist);
-        return;
-    }
-    if (threadIdx.x == 0) s_cnt = 0;
-    __syncthreads();
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        uint64_t k = load(i);
-        if (hist_bin(k, hs.base) <= hs.B) buf[atomicAdd(&s_cnt, 1)] = k;
-    }
-    __syncthreads();
-    const int S = pow2_ceil(need);
-    for (int i = need + threadIdx.x; i < S; i += blockDim.x) buf[i] = KEY_NONE;
-    __syncthreads();
-    block_bitonic_sort(buf, S);
-    for (int i = threadIdx.x; i < K; i += blockDim.x) out[i] = buf[i];
-    __syncthreads();
-}
+constexpr int HIST_BINS = 2048;  // bins of the list-ranking select's score histogram
 
 // Ascending bitonic sort of one key per lane across a warp.
 __device__ __forceinline__ uint64_t warp_sort_key(uint64_t v, int lane) {
@@ -283,94 +198,203 @@ __device__ __forceinline__ uint64_t warp_sort_key(uint64_t v, int lane) {
     return v;
 }
 
-// K smallest of N unique keys held in shared memory (0 < K < N), in no
-// particular order: emit(i, key) for i in [0, K).  A histogram of HIST_BINS
-// bins of width 2^shift above the smallest distance (shift: the least that
-// fits the distance range) finds the bin B of the K-th key; the lt keys of
-// lower bins are emitted as found (indices [0, lt)), the keys of bin B are
-// sorted and their first K - lt follow.  *kth (shared) receives the K-th
-// smallest key.  Returns false, having emitted nothing, if bin B holds more
-// than bcap keys (bcap a power of two, bbuf its scratch).  All threads call.
-template <class Emit>
-__device__ bool block_topk_smem(const uint64_t* keys, int N, int K, Emit emit, uint64_t* bbuf, int bcap,
-                                uint32_t* hist, uint32_t* warp_tot, uint64_t* kth) {
-    __shared__ uint32_t s_min, s_max;
-    __shared__ int s_out, s_nb;
-    __shared__ HistSel hs;
-    if (threadIdx.x == 0) {
-        s_min = 0xffffffffu;
-        s_max = 0u;
-        s_out = 0;
-        s_nb = 0;
-    }
-    for (int b = threadIdx.x; b < HIST_BINS; b += blockDim.x) hist[b] = 0;
-    __syncthreads();
-    uint32_t mn = 0xffffffffu, mx = 0u;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        const uint32_t d = (uint32_t)(keys[i] >> 32);
-        mn = min(mn, d);
-        mx = max(mx, d);
+// K smallest (0 < K < N) of N unique 64-bit keys given by load(i), by one
+// warp, in no particular order: emit(i, key) for i in [0, K); returns the K-th
+// smallest.  Radix refinement: a histogram of 256 bins of width 2^shift over
+// the undecided key range [lo, hi] (shift: the least that fits) locates the
+// bin of the K-th key; the keys of lower bins are emitted and the range
+// narrows to that bin, until it holds at most 32 keys, which are sorted across
+// the warp.  Keys are unique, so a range of fewer than 256 keys ends it.
+// hist: 256 words and bb: 32 keys of the warp's own shared memory.  All 32
+// lanes call.
+template <class Load, class Emit>
+__device__ uint64_t warp_topk(Load load, int N, int K, Emit emit, uint32_t* hist, uint64_t* bb) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t below = (1u << lane) - 1u;
+    uint64_t lo = KEY_NONE, hi = 0ull;
+    for (int i = lane; i < N; i += 32) {
+        const uint64_t k = load(i);
+        lo = k < lo ? k : lo;
+        hi = k > hi ? k : hi;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        const uint64_t a = __shfl_xor_sync(0xffffffffu, lo, o), b = __shfl_xor_sync(0xffffffffu, hi, o);
+        lo = a < lo ? a : lo;
+        hi = b > hi ? b : hi;
     }
-    if ((threadIdx.x & 31) == 0) {
-        atomicMin(&s_min, mn);
-        atomicMax(&s_max, mx);
-    }
-    __syncthreads();
-    const uint32_t base = s_min;
-    int shift = 0;
-    while (((s_max - base) >> shift) >= (uint32_t)HIST_BINS) ++shift;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) atomicAdd(&hist[((uint32_t)(keys[i] >> 32) - base) >> shift], 1u);
-    __syncthreads();
-    const int per = HIST_BINS / blockDim.x;  // blockDim.x divides HIST_BINS
-    const int b0 = threadIdx.x * per;
-    uint32_t local = 0;
-    for (int b = b0; b < b0 + per; ++b) local += hist[b];
-    const uint32_t excl = block_exclusive_scan(local, warp_tot);
-    if (excl < (uint32_t)K && excl + local >= (uint32_t)K) {
-        uint32_t c = excl;
-        for (int b = b0; b < b0 + per; ++b) {
-            if (c + hist[b] >= (uint32_t)K) {
-                hs.B = b;
-                hs.lt = (int)c;
-                hs.inB = (int)hist[b];
-                break;
+    int out = 0, need = K;
+    while (true) {
+        int shift = 0;
+        while (((hi - lo) >> shift) >= 256ull) ++shift;
+        for (int b = lane; b < 256; b += 32) hist[b] = 0u;
+        __syncwarp();
+        for (int i = lane; i < N; i += 32) {
+            const uint64_t k = load(i);
+            if (k >= lo && k <= hi) atomicAdd(&hist[(uint32_t)((k - lo) >> shift)], 1u);
+        }
+        __syncwarp();
+        uint32_t c[8], local = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            c[j] = hist[8 * lane + j];
+            local += c[j];
+        }
+        uint32_t incl = local;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const uint32_t excl = incl - local;
+        int B = -1, lt = 0, inB = 0;
+        if (excl < (uint32_t)need && (uint32_t)need <= incl) {
+            uint32_t acc = excl;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                if (B < 0 && acc + c[j] >= (uint32_t)need) {
+                    B = 8 * lane + j;
+                    lt = (int)acc;
+                    inB = (int)c[j];
+                }
+                acc += c[j];
             }
-            c += hist[b];
         }
+        const int owner = __ffs(__ballot_sync(0xffffffffu, B >= 0)) - 1;
+        B = __shfl_sync(0xffffffffu, B, owner);
+        lt = __shfl_sync(0xffffffffu, lt, owner);  // keys of the range below bin B
+        inB = __shfl_sync(0xffffffffu, inB, owner);
+        const uint64_t blo = lo + ((uint64_t)B << shift);
+        const uint64_t bhi = (hi - blo < (1ull << shift)) ? hi : blo + ((1ull << shift) - 1ull);
+        const bool last = inB <= 32;
+        int nb = 0;
+        for (int i0 = 0; i0 < N; i0 += 32) {
+            const int i = i0 + lane;
+            const uint64_t k = i < N ? load(i) : 0ull;
+            const bool e = i < N && k >= lo && k < blo;
+            const bool g = last && i < N && k >= blo && k <= bhi;
+            const uint32_t me = __ballot_sync(0xffffffffu, e), mg = __ballot_sync(0xffffffffu, g);
+            if (e) emit(out + __popc(me & below), k);
+            if (g) bb[nb + __popc(mg & below)] = k;
+            out += __popc(me);
+            nb += __popc(mg);
+        }
+        need -= lt;
+        if (last) {
+            __syncwarp();
+            const uint64_t v = warp_sort_key(lane < inB ? bb[lane] : KEY_NONE, lane);
+            if (lane < need) emit(out + lane, v);
+            const uint64_t kth = __shfl_sync(0xffffffffu, v, need - 1);
+            __syncwarp();
+            return kth;
+        }
+        lo = blo;
+        hi = bhi;
+        __syncwarp();
+    }
+}
+
+// The same radix refinement by a whole CTA (blockDim.x a multiple of 32):
+// block-wide range, histogram and emission (positions from a shared counter,
+// so in no particular order), the bin search and the final sort of at most 32
+// keys by warp 0.  For queries with many keys.  All threads call; every
+// thread gets the K-th smallest.
+template <class Load, class Emit>
+__device__ uint64_t block_topk(Load load, int N, int K, Emit emit, uint32_t* hist, uint64_t* bb) {
+    __shared__ unsigned long long s_lo, s_hi, s_kth;
+    __shared__ int s_B, s_lt, s_inB, s_out, s_nb;
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        s_lo = KEY_NONE;
+        s_hi = 0ull;
+        s_out = 0;
     }
     __syncthreads();
-    const int B = hs.B, lt = hs.lt, inB = hs.inB;
-    if (inB > bcap) return false;
+    uint64_t lo = KEY_NONE, hi = 0ull;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        const uint64_t k = keys[i];
-        const int b = (int)(((uint32_t)(k >> 32) - base) >> shift);
-        if (b < B) emit(atomicAdd(&s_out, 1), k);
-        else if (b == B) bbuf[atomicAdd(&s_nb, 1)] = k;
+        const uint64_t k = load(i);
+        lo = k < lo ? k : lo;
+        hi = k > hi ? k : hi;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t a = __shfl_xor_sync(0xffffffffu, lo, o), b = __shfl_xor_sync(0xffffffffu, hi, o);
+        lo = a < lo ? a : lo;
+        hi = b > hi ? b : hi;
+    }
+    if (lane == 0) {
+        atomicMin(&s_lo, (unsigned long long)lo);
+        atomicMax(&s_hi, (unsigned long long)hi);
     }
     __syncthreads();
-    const int need = K - lt;
-    if (inB <= 32) {
-        if (threadIdx.x < 32) {
-            const int lane = threadIdx.x;
-            const uint64_t v = warp_sort_key(lane < inB ? bbuf[lane] : KEY_NONE, lane);
-            if (lane < need) emit(lt + lane, v);
-            if (lane == need - 1) *kth = v;
-        }
-    } else {
-        const int S = pow2_ceil(inB);
-        for (int i = inB + threadIdx.x; i < S; i += blockDim.x) bbuf[i] = KEY_NONE;
+    lo = s_lo;
+    hi = s_hi;
+    int need = K;
+    while (true) {
+        int shift = 0;
+        while (((hi - lo) >> shift) >= 256ull) ++shift;
+        for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0u;
+        if (threadIdx.x == 0) s_nb = 0;
         __syncthreads();
-        block_bitonic_sort(bbuf, S);
-        for (int i = threadIdx.x; i < need; i += blockDim.x) emit(lt + i, bbuf[i]);
-        if (threadIdx.x == 0) *kth = bbuf[need - 1];
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            const uint64_t k = load(i);
+            if (k >= lo && k <= hi) atomicAdd(&hist[(uint32_t)((k - lo) >> shift)], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            uint32_t c[8], local = 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                c[j] = hist[8 * lane + j];
+                local += c[j];
+            }
+            uint32_t incl = local;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const uint32_t excl = incl - local;
+            if (excl < (uint32_t)need && (uint32_t)need <= incl) {
+                uint32_t acc = excl;
+                int B = -1;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    if (B < 0 && acc + c[j] >= (uint32_t)need) {
+                        B = 8 * lane + j;
+                        s_B = B;
+                        s_lt = (int)acc;
+                        s_inB = (int)c[j];
+                    }
+                    acc += c[j];
+                }
+            }
+        }
+        __syncthreads();
+        const int B = s_B, lt = s_lt, inB = s_inB;
+        const uint64_t blo = lo + ((uint64_t)B << shift);
+        const uint64_t bhi = (hi - blo < (1ull << shift)) ? hi : blo + ((1ull << shift) - 1ull);
+        const bool last = inB <= 32;
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            const uint64_t k = load(i);
+            if (k >= lo && k < blo) emit(atomicAdd(&s_out, 1), k);
+            else if (last && k >= blo && k <= bhi) bb[atomicAdd(&s_nb, 1)] = k;
+        }
+        __syncthreads();
+        need -= lt;
+        if (last) {
+            if (threadIdx.x < 32) {
+                const uint64_t v = warp_sort_key(lane < inB ? bb[lane] : KEY_NONE, lane);
+                if (lane < need) emit(s_out + lane, v);
+                if (lane == need - 1) s_kth = v;
+            }
+            __syncthreads();
+            return s_kth;
+        }
+        lo = blo;
+        hi = bhi;
+        __syncthreads();
     }
-    __syncthreads();
-    return true;
 }
 
 // ------------------------------------------------------------------ workspace

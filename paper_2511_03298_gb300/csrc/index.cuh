@@ -59,7 +59,8 @@ struct ksc_index {
     int32_t launches = 0;
     // search workspace
     ksc::Buffer ws_scores, ws_probes, ws_lut, ws_bias, ws_scale, ws_range, ws_thr, ws_cnt,
-        ws_cand, ws_topr, ws_nprobe, ws_rerank, ws_items, ws_misc, ws_qbf16, ws_err, ws_feat, ws_rscore, ws_full, ws_topr2;
+        ws_cand, ws_topr, ws_nprobe, ws_rerank, ws_items, ws_misc, ws_qbf16, ws_err, ws_feat, ws_rscore, ws_full, ws_topr2,
+        ws_redo;
 };
 
 namespace ksc {

@@ -22,10 +22,9 @@
 namespace ksc {
 
 constexpr int SEL_CAP = 4096;   // bitonic buffer of the select kernels (>= KSC_MAX_RERANK)
-constexpr int SELS_BIN = 256;   // scratch for the keys of the K-th key's histogram bin
 
-// Keys the select kernels stage in shared memory: 8 R (a power of two, at
-// least 1024, at most SEL_CAP); also the size of their fallback buffers.
+// Shared buffer of the exact select of overflowed queries: 8 R keys (a power
+// of two, at least 1024, at most SEL_CAP; it sorts the R best).
 static int sel_keys(int Rmax) { return std::min(SEL_CAP, std::max(1024, pow2_ceil(8 * Rmax))); }
 constexpr int MAX_NPROBE = 4096;
 constexpr int NEAR_KEYS_PER_R = 4;  // keys of the unfiltered first scan: at least 4 R ...
@@ -595,92 +594,89 @@ __device__ __forceinline__ int rerank_of(const int32_t* rerank_q, int Rfix, int 
 // smallest of the keys found so far bounds the R-th smallest key of the whole
 // search from above (any subset with at least R members gives such a bound);
 // the scan of the remaining lists keeps only keys at or below it.  Fewer than
-// R keys: no bound (all ones).  A histogram of the distances finds the bin of
-// the R-th key and only that bin is sorted; `scratch` (a row of R keys per
-// query) serves the radix fallback when the bin is too large.
-__global__ void __launch_bounds__(256) k_threshold(ScanArgs A, int Rmax, int32_t* __restrict__ cnt,
-                                                   uint64_t* __restrict__ cand, int cap, int nkeys,
-                                                   uint64_t* __restrict__ scratch, uint64_t* __restrict__ thr) {
-    extern __shared__ uint64_t buf[];  // nkeys keys (the staged keys, or the fallback's buffer), SELS_BIN
-    __shared__ uint32_t hist[HIST_BINS];
-    __shared__ uint32_t warp_tot[32];
-    __shared__ HistSel hs;
-    __shared__ int s_nb;
-    __shared__ unsigned long long s_thr;
+// R keys: no bound (all ones).  One warp per query.  Nothing above the R-th
+// key can enter the final R, so the store keeps only the R keys at or below it
+// (gathered in `scratch`, a row of Rmax keys per query, then copied back),
+// unless it overflowed (the final select then redoes the query).
+constexpr int SW_WARPS = 8;        // queries per CTA of the warp selection kernels
+constexpr int SW_MAX_KEYS = 2048;  // expected keys per query up to which a warp selects
+
+__global__ void __launch_bounds__(SW_WARPS * 32) k_threshold(ScanArgs A, int Rmax, int32_t* __restrict__ cnt,
+                                                             uint64_t* __restrict__ cand, int cap,
+                                                             uint64_t* __restrict__ scratch,
+                                                             uint64_t* __restrict__ thr) {
+    __shared__ uint32_t hist[SW_WARPS][256];
+    __shared__ uint64_t bb[SW_WARPS][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t q = (int64_t)blockIdx.x * SW_WARPS + w;
+    if (q >= A.nq) return;
+    const int R = rerank_of(A.rerank_q, A.Rfix, A.Rmin, Rmax, q);
+    const int n0 = cnt[q];
+    const int n = min(n0, cap);  // an overflowed store still bounds the R-th key
+    const bool ovf = n0 > cap;
+    uint64_t* cq = cand + q * cap;
+    uint64_t t = KEY_NONE;
+    if (n == R) {
+        uint64_t m = 0ull;
+        for (int i = lane; i < n; i += 32) m = cq[i] > m ? cq[i] : m;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const uint64_t y = __shfl_xor_sync(0xffffffffu, m, o);
+            m = y > m ? y : m;
+        }
+        t = m;
+    } else if (n > R) {
+        uint64_t* sq = scratch + q * Rmax;
+        auto load = [&](int i) -> uint64_t { return cq[i]; };
+        auto emit = [&](int i, uint64_t k) {
+            if (!ovf) sq[i] = k;
+        };
+        t = warp_topk(load, n, R, emit, hist[w], bb[w]);
+        if (!ovf) {
+            __syncwarp();
+            for (int i = lane; i < R; i += 32) cq[i] = sq[i];
+            if (lane == 0) cnt[q] = R;
+        }
+    }
+    if (lane == 0) thr[q] = t;
+}
+
+// The same with one CTA per query, for queries with many keys.
+__global__ void __launch_bounds__(256) k_threshold_cta(ScanArgs A, int Rmax, int32_t* __restrict__ cnt,
+                                                       uint64_t* __restrict__ cand, int cap,
+                                                       uint64_t* __restrict__ scratch,
+                                                       uint64_t* __restrict__ thr) {
+    __shared__ uint32_t hist[256];
+    __shared__ uint64_t bb[32];
+    __shared__ unsigned long long s_m;
     const int64_t q = blockIdx.x;
     const int R = rerank_of(A.rerank_q, A.Rfix, A.Rmin, Rmax, q);
-    const int n = min(cnt[q], cap);
-    if (n < R) {
-        if (threadIdx.x == 0) thr[q] = KEY_NONE;
-        return;
-    }
-    const bool ovf = cnt[q] > cap;  // overflowed: threshold only, the final select redoes this query exactly
+    const int n0 = cnt[q];
+    const int n = min(n0, cap);
+    const bool ovf = n0 > cap;
     uint64_t* cq = cand + q * cap;
-    if (n <= nkeys) {
-        // staged once; nothing above the R-th key can enter the final R, so the
-        // R keys at or below it replace the store's contents
-        for (int i = threadIdx.x; i < n; i += blockDim.x) buf[i] = cq[i];
-        if (threadIdx.x == 0) s_thr = 0ull;
+    uint64_t t = KEY_NONE;
+    if (n == R) {
+        if (threadIdx.x == 0) s_m = 0ull;
         __syncthreads();
-        bool ok = true;
-        if (n == R) {
-            unsigned long long m = 0ull;
-            for (int i = threadIdx.x; i < n; i += blockDim.x) m = max(m, (unsigned long long)buf[i]);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-            if ((threadIdx.x & 31) == 0) atomicMax(&s_thr, m);
-            __syncthreads();
-        } else {
-            uint64_t kth = 0;
-            auto emit = [&](int i, uint64_t k) {
-                if (!ovf) cq[i] = k;
-            };
-            ok = block_topk_smem(buf, n, R, emit, buf + nkeys, SELS_BIN, hist, warp_tot,
-                                 reinterpret_cast<uint64_t*>(&s_thr));
-            (void)kth;
-        }
-        if (ok) {
-            if (threadIdx.x == 0) {
-                thr[q] = s_thr;
-                if (!ovf) cnt[q] = R;
-            }
-            return;
+        unsigned long long m = 0ull;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) m = cq[i] > m ? cq[i] : m;
+        atomicMax(&s_m, m);
+        __syncthreads();
+        t = s_m;
+    } else if (n > R) {
+        uint64_t* sq = scratch + q * Rmax;
+        auto load = [&](int i) -> uint64_t { return cq[i]; };
+        auto emit = [&](int i, uint64_t k) {
+            if (!ovf) sq[i] = k;
+        };
+        t = block_topk(load, n, R, emit, hist, bb);
+        if (!ovf) {
+            for (int i = threadIdx.x; i < R; i += blockDim.x) cq[i] = sq[i];
+            if (threadIdx.x == 0) cnt[q] = R;
         }
     }
-    auto load = [&](int i) -> uint64_t { return cq[i]; };
-    hist_find(load, n, R, hist, warp_tot, &hs);
-    if (hs.inB <= nkeys) {
-        if (threadIdx.x == 0) s_nb = 0;
-        __syncthreads();
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const uint64_t k = cq[i];
-            if (hist_bin(k, hs.base) == hs.B) buf[atomicAdd(&s_nb, 1)] = k;
-        }
-        __syncthreads();
-        const int S = pow2_ceil(hs.inB);
-        for (int i = hs.inB + threadIdx.x; i < S; i += blockDim.x) buf[i] = KEY_NONE;
-        __syncthreads();
-        block_bitonic_sort(buf, S);
-        if (threadIdx.x == 0) s_thr = buf[R - hs.lt - 1];
-    } else {
-        uint64_t* out = scratch + q * Rmax;
-        block_select_smallest(load, n, R, out, buf, nkeys, hist);
-        if (threadIdx.x == 0) s_thr = out[R - 1];
-    }
-    __syncthreads();
-    const uint64_t t = s_thr;
     if (threadIdx.x == 0) thr[q] = t;
-    if (ovf) return;
-    if (threadIdx.x == 0) s_nb = 0;
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const uint64_t k = cq[i];
-        if (k <= t) buf[atomicAdd(&s_nb, 1)] = k;
-    }
-    __syncthreads();
-    const int m = s_nb;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) cq[i] = buf[i];
-    if (threadIdx.x == 0) cnt[q] = m;
 }
 
 // ------------------------------------------------------------------ work list (cluster-major)
@@ -1496,81 +1492,131 @@ __global__ void __launch_bounds__(128) k_lut16_peak(int iters, uint32_t seed, ui
 }
 
 // ------------------------------------------------------------------ a5: select
-// R smallest candidate keys per query.  If the store overflowed, the query
-// is redone exactly: every key of every probed list is recomputed (scalar
-// lookups) inside the radix select.
-__global__ void __launch_bounds__(256) k_select(ScanArgs A, int Rmax, const int32_t* __restrict__ cnt, int sel_cap,
-                                                const uint64_t* __restrict__ cand, int cap,
-                                                uint64_t* __restrict__ topr, int32_t* __restrict__ ncand,
-                                                int32_t* __restrict__ status,
-                                                unsigned long long* __restrict__ stats) {
-    extern __shared__ uint64_t sbuf[];  // sel_cap keys (staged keys, or the fallbacks' buffer), SELS_BIN
-    __shared__ uint32_t hist[HIST_BINS];
-    __shared__ uint32_t warp_tot[32];
-    __shared__ int32_t s_pref[MAX_NPROBE + 1];
-    __shared__ uint64_t s_kth;
+// R smallest candidate keys per query, in no particular order (the re-rank
+// does not need one); one warp per query.  A query whose store overflowed is
+// put on the redo list for k_select_redo.
+__global__ void __launch_bounds__(SW_WARPS * 32) k_select(ScanArgs A, int Rmax, const int32_t* __restrict__ cnt,
+                                                          const uint64_t* __restrict__ cand, int cap,
+                                                          uint64_t* __restrict__ topr, int32_t* __restrict__ ncand,
+                                                          int32_t* __restrict__ status,
+                                                          unsigned long long* __restrict__ stats,
+                                                          int32_t* __restrict__ redo) {
+    __shared__ uint32_t hist[SW_WARPS][256];
+    __shared__ uint64_t bb[SW_WARPS][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t q = (int64_t)blockIdx.x * SW_WARPS + w;
+    if (q >= A.nq) return;
+    const int R = rerank_of(A.rerank_q, A.Rfix, A.Rmin, Rmax, q);
+    const int n = cnt[q];
+    if (lane == 0) {
+        atomicAdd(&stats[1], (unsigned long long)n);
+        atomicMax(&stats[2], (unsigned long long)n);
+    }
+    if (n > cap) {
+        if (lane == 0) {
+            atomicAdd(&stats[0], 1ull);
+            atomicOr(status, KSC_STATUS_CAND_OVERFLOW);
+            redo[1 + atomicAdd(&redo[0], 1)] = (int32_t)q;
+        }
+        return;
+    }
+    const uint64_t* cq = cand + q * cap;
+    uint64_t* out = topr + q * Rmax;
+    const int K = min(R, n);
+    if (n <= K) {
+        for (int i = lane; i < n; i += 32) out[i] = cq[i];
+    } else {
+        auto load = [&](int i) -> uint64_t { return cq[i]; };
+        auto emit = [&](int i, uint64_t k) { out[i] = k; };
+        warp_topk(load, n, K, emit, hist[w], bb[w]);
+    }
+    for (int i = K + lane; i < Rmax; i += 32) out[i] = KEY_NONE;
+    if (lane == 0 && ncand) ncand[q] = K;
+}
+
+// The same with one CTA per query, for queries with many candidates.
+__global__ void __launch_bounds__(256) k_select_cta(ScanArgs A, int Rmax, const int32_t* __restrict__ cnt,
+                                                    const uint64_t* __restrict__ cand, int cap,
+                                                    uint64_t* __restrict__ topr, int32_t* __restrict__ ncand,
+                                                    int32_t* __restrict__ status,
+                                                    unsigned long long* __restrict__ stats,
+                                                    int32_t* __restrict__ redo) {
+    __shared__ uint32_t hist[256];
+    __shared__ uint64_t bb[32];
     const int64_t q = blockIdx.x;
     const int R = rerank_of(A.rerank_q, A.Rfix, A.Rmin, Rmax, q);
     const int n = cnt[q];
-    uint64_t* out = topr + q * Rmax;
     if (threadIdx.x == 0) {
         atomicAdd(&stats[1], (unsigned long long)n);
         atomicMax(&stats[2], (unsigned long long)n);
-        if (n > cap) atomicAdd(&stats[0], 1ull);
     }
-    if (n <= cap) {
-        // the R smallest, in no particular order (the re-rank does not need one)
-        const uint64_t* cq = cand + q * cap;
-        const int K = min(R, n);
-        bool done = false;
-        if (n <= K) {
-            for (int i = threadIdx.x; i < n; i += blockDim.x) out[i] = cq[i];
-            done = true;
-        } else if (n <= sel_cap) {
-            for (int i = threadIdx.x; i < n; i += blockDim.x) sbuf[i] = cq[i];
-            __syncthreads();
-            auto emit = [&](int i, uint64_t k) { out[i] = k; };
-            done = block_topk_smem(sbuf, n, K, emit, sbuf + sel_cap, SELS_BIN, hist, warp_tot, &s_kth);
+    if (n > cap) {
+        if (threadIdx.x == 0) {
+            atomicAdd(&stats[0], 1ull);
+            atomicOr(status, KSC_STATUS_CAND_OVERFLOW);
+            redo[1 + atomicAdd(&redo[0], 1)] = (int32_t)q;
         }
-        if (!done) {
-            auto load = [&](int i) -> uint64_t { return cq[i]; };
-            block_select_hist(load, n, K, out, sbuf, sel_cap, hist, warp_tot);
-        }
-        for (int i = K + threadIdx.x; i < Rmax; i += blockDim.x) out[i] = KEY_NONE;
-        if (threadIdx.x == 0 && ncand) ncand[q] = K;
         return;
     }
-    if (threadIdx.x == 0) atomicOr(status, KSC_STATUS_CAND_OVERFLOW);
-    const int P = nprobe_of(A, q);
-    if (threadIdx.x == 0) {
-        int acc = 0;
-        for (int r = 0; r < P; ++r) {
-            s_pref[r] = acc;
-            const int p = A.probes[q * A.Pmax + r];
-            acc += (p >= 0 && p < A.L) ? A.list_n[p] : 0;
-        }
-        s_pref[P] = acc;
+    const uint64_t* cq = cand + q * cap;
+    uint64_t* out = topr + q * Rmax;
+    const int K = min(R, n);
+    if (n <= K) {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) out[i] = cq[i];
+    } else {
+        auto load = [&](int i) -> uint64_t { return cq[i]; };
+        auto emit = [&](int i, uint64_t k) { out[i] = k; };
+        block_topk(load, n, K, emit, hist, bb);
     }
-    __syncthreads();
-    const int N = s_pref[P];
-    auto load = [&](int i) -> uint64_t {
-        int lo = 0, hi = P - 1;
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (s_pref[mid] <= i) lo = mid; else hi = mid - 1;
-        }
-        const int64_t item = q * A.Pmax + lo;
-        const int p = A.probes[item];
-        const int m = i - s_pref[lo];
-        const int64_t blk = A.boff[p] + (m >> 5);
-        const int v = m & 31;
-        int32_t D = scalar_dist(A.lut + item * A.M * PQ_K, A.bias[item], A.codes + blk * A.M * 16, A.M, v);
-        return make_key(D, A.ids[blk * 32 + v]);
-    };
-    const int K = min(R, N);
-    block_select_smallest(load, N, K, out, sbuf, sel_cap, hist);
     for (int i = K + threadIdx.x; i < Rmax; i += blockDim.x) out[i] = KEY_NONE;
     if (threadIdx.x == 0 && ncand) ncand[q] = K;
+}
+
+// Queries whose candidate store overflowed, redone exactly: every key of every
+// probed list is recomputed (scalar lookups) inside the radix select.  A
+// persistent grid walks the redo list (usually empty).
+__global__ void __launch_bounds__(256) k_select_redo(ScanArgs A, int Rmax, int sel_cap, uint64_t* __restrict__ topr,
+                                                     int32_t* __restrict__ ncand, const int32_t* __restrict__ redo) {
+    extern __shared__ uint64_t sbuf[];  // sel_cap keys
+    __shared__ uint32_t hist[256];
+    __shared__ int32_t s_pref[MAX_NPROBE + 1];
+    const int nredo = redo[0];
+    for (int r0 = blockIdx.x; r0 < nredo; r0 += gridDim.x) {
+        const int64_t q = redo[1 + r0];
+        const int R = rerank_of(A.rerank_q, A.Rfix, A.Rmin, Rmax, q);
+        uint64_t* out = topr + q * Rmax;
+        const int P = nprobe_of(A, q);
+        __syncthreads();  // s_pref of the previous query is no longer read
+        if (threadIdx.x == 0) {
+            int acc = 0;
+            for (int r = 0; r < P; ++r) {
+                s_pref[r] = acc;
+                const int p = A.probes[q * A.Pmax + r];
+                acc += (p >= 0 && p < A.L) ? A.list_n[p] : 0;
+            }
+            s_pref[P] = acc;
+        }
+        __syncthreads();
+        const int N = s_pref[P];
+        auto load = [&](int i) -> uint64_t {
+            int lo = 0, hi = P - 1;
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (s_pref[mid] <= i) lo = mid; else hi = mid - 1;
+            }
+            const int64_t item = q * A.Pmax + lo;
+            const int p = A.probes[item];
+            const int m = i - s_pref[lo];
+            const int64_t blk = A.boff[p] + (m >> 5);
+            const int v = m & 31;
+            int32_t D = scalar_dist(A.lut + item * A.M * PQ_K, A.bias[item], A.codes + blk * A.M * 16, A.M, v);
+            return make_key(D, A.ids[blk * 32 + v]);
+        };
+        const int K = min(R, N);
+        block_select_smallest(load, N, K, out, sbuf, sel_cap, hist);
+        for (int i = K + threadIdx.x; i < Rmax; i += blockDim.x) out[i] = KEY_NONE;
+        if (threadIdx.x == 0 && ncand) ncand[q] = K;
+    }
 }
 
 // ------------------------------------------------------------------ a6: rerank
@@ -2185,14 +2231,15 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
     mark(ix, 3, st);
     KSC_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * nq, st));
     KSC_TRY(run_scan(pl, M, A, ScanOut{nullptr, cnt, cand, pl.cap}, wa, L, ix->status, st));
-    {
-        const int nkeys = sel_keys(pl.Rmax);
-        const size_t smem = (nkeys + SELS_BIN) * sizeof(uint64_t);
-        cudaFuncSetAttribute(k_threshold, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_threshold<<<(unsigned)nq, 256, smem, st>>>(A, pl.Rmax, cnt, cand, pl.cap, nkeys, topr, thr);
-        KSC_LAUNCH_CHECK();
-        ix->launches += 2;
-    }
+    // expected keys per query of the unfiltered scan: max(4 R, N / 16), N from
+    // the mean list length; a warp per query up to SW_MAX_KEYS, else a CTA
+    if (std::max(4.0 * pl.Rmax, (double)pl.Pmax * ix->n / L / 16.0) <= SW_MAX_KEYS)
+        k_threshold<<<(unsigned)((nq + SW_WARPS - 1) / SW_WARPS), SW_WARPS * 32, 0, st>>>(A, pl.Rmax, cnt, cand,
+                                                                                           pl.cap, topr, thr);
+    else
+        k_threshold_cta<<<(unsigned)nq, 256, 0, st>>>(A, pl.Rmax, cnt, cand, pl.cap, topr, thr);
+    KSC_LAUNCH_CHECK();
+    ix->launches += 2;
     // 4. scan of the other lists, keeping keys at or below the threshold;
     //    hybrid: graph search of every other list first, full scans only of
     //    the lists it marks (Sec. 4.4)
@@ -2234,15 +2281,25 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
     // 5. the R best keys per query
     mark(ix, 5, st);
     {
-        // shared buffer: the R best plus the ties of the histogram bin at the
-        // R-th key (radix select beyond it)
-        const int sel_cap = sel_keys(pl.Rmax);
-        const size_t smem = (sel_cap + SELS_BIN) * sizeof(uint64_t);
-        cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_select<<<(unsigned)nq, 256, smem, st>>>(A, pl.Rmax, cnt, sel_cap, cand, pl.cap, topr, ncand_out, ix->status,
-                                                  ix->stats);
-        ix->launches++;
+        KSC_TRY(ensure(ix->ws_redo, sizeof(int32_t) * (nq + 1), st));
+        int32_t* redo = (int32_t*)ix->ws_redo.p;
+        KSC_CUDA(cudaMemsetAsync(redo, 0, sizeof(int32_t), st));
+        // candidates per query: the R kept by the threshold plus a few R more
+        if (4 * pl.Rmax <= SW_MAX_KEYS)
+            k_select<<<(unsigned)((nq + SW_WARPS - 1) / SW_WARPS), SW_WARPS * 32, 0, st>>>(
+                A, pl.Rmax, cnt, cand, pl.cap, topr, ncand_out, ix->status, ix->stats, redo);
+        else
+            k_select_cta<<<(unsigned)nq, 256, 0, st>>>(A, pl.Rmax, cnt, cand, pl.cap, topr, ncand_out, ix->status,
+                                                       ix->stats, redo);
         KSC_LAUNCH_CHECK();
+        // overflowed queries (usually none): radix select over recomputed keys,
+        // the R best plus their sort in a buffer of sel_cap keys
+        const int sel_cap = sel_keys(pl.Rmax);
+        const size_t smem = sel_cap * sizeof(uint64_t);
+        KSC_CUDA(cudaFuncSetAttribute(k_select_redo, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_select_redo<<<num_sms() * 2, 256, smem, st>>>(A, pl.Rmax, sel_cap, topr, ncand_out, redo);
+        KSC_LAUNCH_CHECK();
+        ix->launches += 2;
     }
     if (cand_out) {
         const size_t csm = sizeof(uint64_t) * pow2_ceil(pl.Rmax < 2 ? 2 : pl.Rmax);
