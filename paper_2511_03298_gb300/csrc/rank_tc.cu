@@ -227,6 +227,37 @@ __global__ void k_score_err(const float* __restrict__ Q, int64_t nq, int d, floa
     err[q] = (spherical ? e : 2.f * e) + r;
 }
 
+// Queries to 16-bit operands [nq x Kp] (zero-padded K) and, in the same pass,
+// the per-query bound of k_score_err.  One warp per query (coalesced rows).
+__global__ void k_q16_err(const float* __restrict__ Q, int64_t nq, int d, int Kp, int fp16, float cmax,
+                          int spherical, float rel, float qmax, uint16_t* __restrict__ out,
+                          float* __restrict__ err) {
+    const int lane = threadIdx.x & 31;
+    const int64_t q = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (q >= nq) return;
+    float s = 0.f, mx = 0.f;
+    for (int t = lane; t < Kp; t += 32) {
+        const float v = t < d ? Q[q * d + t] : 0.f;
+        s = fmaf(v, v, s);
+        mx = fmaxf(mx, fabsf(v));
+        out[q * Kp + t] = fp16 ? __half_as_ushort(__float2half_rn(v)) : __bfloat16_as_ushort(__float2bfloat16_rn(v));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if (lane != 0) return;
+    if (mx > qmax) {  // an element the 16-bit operand cannot hold: no bound
+        err[q] = INFINITY;
+        return;
+    }
+    const float qn = sqrtf(s);
+    const float e = rel * qn * cmax * 1.0001f;
+    const float r = (float)(d + 8) * 1.2e-7f * (qn + cmax) * (qn + cmax);
+    err[q] = (spherical ? e : 2.f * e) + r;
+}
+
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
@@ -264,6 +295,8 @@ bool tc_rank_supported(const ksc_index* ix) { return ix->d <= 256; }
 
 // Approximate scores [nq x L] with the tensor cores plus the per-query error
 // bound err [nq]; the caller re-scores exactly what the bound cannot exclude.
+static int err_params(ksc_index* ix, bool tensor_cores, float* rel, float* qmax, cudaStream_t st);
+
 int rank_scores_tc(ksc_index* ix, const float* Q, int64_t nq, float* scores, float* err, cudaStream_t st) {
     const int Kp = (ix->d + TC_KB - 1) / TC_KB * TC_KB;
     const int KB = Kp / TC_KB;
@@ -282,8 +315,10 @@ int rank_scores_tc(ksc_index* ix, const float* Q, int64_t nq, float* scores, flo
     }
     KSC_TRY(ensure(ix->ws_qbf16, sizeof(uint16_t) * (size_t)nq * Kp, st));
     uint16_t* qb = (uint16_t*)ix->ws_qbf16.p;
-    k_to_16<<<(unsigned)std::min<int64_t>((nq * Kp + 255) / 256, 4096), 256, 0, st>>>(Q, nq, ix->d, Kp, ix->tc_fp16,
-                                                                                     qb);
+    float rel, qmax;
+    KSC_TRY(err_params(ix, true, &rel, &qmax, st));
+    k_q16_err<<<(unsigned)((nq + 7) / 8), 256, 0, st>>>(Q, nq, ix->d, Kp, ix->tc_fp16, ix->c_rank_max_norm,
+                                                         ix->spherical, rel, qmax, qb, err);
     KSC_LAUNCH_CHECK();
     CUtensorMap mapA;
     KSC_TRY(make_map(&mapA, qb, nq, Kp, TC_M, ix->tc_fp16));
@@ -294,10 +329,12 @@ int rank_scores_tc(ksc_index* ix, const float* Q, int64_t nq, float* scores, flo
                                             ix->c_rank_sq, ix->spherical, ix->tc_fp16 ? 0 : 1, scores, ix->status);
     KSC_LAUNCH_CHECK();
     ix->launches += 2;
-    return score_err(ix, Q, nq, true, err, st);
+    return KSC_OK;
 }
 
-int score_err(ksc_index* ix, const float* Q, int64_t nq, bool tensor_cores, float* err, cudaStream_t st) {
+// Constants of the score bound: max ||c|| (once per index), the relative
+// rounding of the operand type and the largest representable query element.
+static int err_params(ksc_index* ix, bool tensor_cores, float* rel, float* qmax, cudaStream_t st) {
     if (ix->c_rank_max_norm <= 0.f) {
         std::vector<float> cn(ix->L);
         KSC_CUDA(cudaMemcpyAsync(cn.data(), ix->c_rank_sq, sizeof(float) * ix->L, cudaMemcpyDeviceToHost, st));
@@ -307,8 +344,14 @@ int score_err(ksc_index* ix, const float* Q, int64_t nq, bool tensor_cores, floa
         ix->c_rank_max_norm = m > 0.f ? sqrtf(m) : 1e-30f;
     }
     const float u2 = ix->tc_fp16 ? 9.77e-4f + 1e-6f : 0.0078125f + 6.2e-5f;  // 2u + u^2
-    const float rel = tensor_cores ? u2 + (float)ix->d * 4.8e-7f : (float)(ix->d + 8) * 1.2e-7f;
-    const float qmax = (tensor_cores && ix->tc_fp16) ? 6.0e4f : INFINITY;
+    *rel = tensor_cores ? u2 + (float)ix->d * 4.8e-7f : (float)(ix->d + 8) * 1.2e-7f;
+    *qmax = (tensor_cores && ix->tc_fp16) ? 6.0e4f : INFINITY;
+    return KSC_OK;
+}
+
+int score_err(ksc_index* ix, const float* Q, int64_t nq, bool tensor_cores, float* err, cudaStream_t st) {
+    float rel, qmax;
+    KSC_TRY(err_params(ix, tensor_cores, &rel, &qmax, st));
     k_score_err<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(Q, nq, ix->d, ix->c_rank_max_norm, ix->spherical,
                                                               rel, qmax, err);
     KSC_LAUNCH_CHECK();

@@ -26,6 +26,11 @@ constexpr int SEL_CAP = 4096;   // bitonic buffer of the select kernels (>= KSC_
 // Shared buffer of the exact select of overflowed queries: 8 R keys (a power
 // of two, at least 1024, at most SEL_CAP; it sorts the R best).
 static int sel_keys(int Rmax) { return std::min(SEL_CAP, std::max(1024, pow2_ceil(8 * Rmax))); }
+
+// Per-query kernels come in two shapes: a warp per query (many queries: the
+// GPU is full of warps) or a CTA per query (few queries: eight warps share
+// each one).  The warp shape pays off once the batch fills every SM's warps.
+static bool warp_per_query(int64_t nq) { return nq >= 8 * (int64_t)num_sms(); }
 constexpr int MAX_NPROBE = 4096;
 constexpr int NEAR_KEYS_PER_R = 4;  // keys of the unfiltered first scan: at least 4 R ...
 constexpr int NEAR_SHARE_DIV = 16;  // ... and at least 1/16 of the keys the query probes
@@ -125,15 +130,19 @@ __global__ void __launch_bounds__(256) k_rank_select(const float* __restrict__ s
                                                      int64_t nq, int d, int L, int spherical,
                                                      const int32_t* __restrict__ nprobe_q, int Pfix, int Pmax,
                                                      int rs_cap, int32_t* __restrict__ probes,
-                                                     float* __restrict__ score_out) {
+                                                     float* __restrict__ score_out, const int32_t* __restrict__ list) {
     extern __shared__ uint64_t cand[];  // rs_cap keys, then the row's scores when L <= RS_SMEM_L
     __shared__ uint32_t hist[HIST_BINS];
     __shared__ uint32_t warp_tot[32];
     __shared__ __align__(16) float qs[KSC_MAX_DIM];
     __shared__ uint32_t s_mn, s_mx;
     __shared__ int s_cnt, s_B;
-    const int64_t q = blockIdx.x;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    // every query, or (list != NULL) the list[0] queries list[1..]
+    const int64_t count = list ? list[0] : nq;
+    for (int64_t e = blockIdx.x; e < count; e += gridDim.x) {
+    const int64_t q = list ? list[1 + e] : e;
+    __syncthreads();  // the previous query's shared state is no longer read
     int P = nprobe_q ? nprobe_q[q] : Pfix;
     P = P < 1 ? 1 : (P > Pmax ? Pmax : P);
     const float* s = scores + q * L;
@@ -232,6 +241,170 @@ __global__ void __launch_bounds__(256) k_rank_select(const float* __restrict__ s
         if (r < P && r < n) {
             probes[q * Pmax + r] = (int32_t)(cand[r] & 0xffffffffu);
             if (score_out) score_out[q * Pmax + r] = unordered_f32((uint32_t)(cand[r] >> 32));
+        } else {
+            probes[q * Pmax + r] = -1;
+            if (score_out) score_out[q * Pmax + r] = INFINITY;
+        }
+    }
+    }
+}
+
+// Warp bitonic sort, ascending, of S (a power of two) keys in shared memory.
+__device__ __forceinline__ void warp_bitonic_smem(uint64_t* s, int S, int lane) {
+    for (int k = 2; k <= S; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = lane; i < S; i += 32) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const uint64_t a = s[i], b = s[ixj];
+                    if ((a > b) == ((i & k) == 0)) {
+                        s[i] = b;
+                        s[ixj] = a;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// One warp per query (RSW_WARPS per CTA) for L <= RSW_MAX_L: the row of given
+// scores is staged in the warp's shared memory and the P-th smallest given
+// score s_P found by radix refinement over (score, list) keys.  Every list of
+// the exact top P has a given score <= s_P + 2 err (P lists have given scores
+// <= s_P, so the exact P-th score is at most s_P + err).  Those lists are
+// re-scored exactly in FP32 (8 at a time, as in the re-rank) and the P best by
+// (score, id) are sorted.  A query with more than RSW_CAND such lists is put on
+// `redo` for k_rank_select.
+constexpr int RSW_WARPS = 4;
+constexpr int RSW_MAX_L = 2048;
+constexpr int RSW_CAND = 128;
+
+__global__ void __launch_bounds__(RSW_WARPS * 32) k_rank_select_w(const float* __restrict__ scores,
+                                                                  const float* __restrict__ err,
+                                                                  const float* __restrict__ Q,
+                                                                  const float* __restrict__ Cc, int64_t nq, int d,
+                                                                  int L, int spherical,
+                                                                  const int32_t* __restrict__ nprobe_q, int Pfix,
+                                                                  int Pmax, int32_t* __restrict__ probes,
+                                                                  float* __restrict__ score_out,
+                                                                  int32_t* __restrict__ redo) {
+    extern __shared__ uint64_t rsm[];  // RSW_WARPS x RSW_CAND keys, then RSW_WARPS x L scores
+    __shared__ uint32_t hist[RSW_WARPS][256];
+    __shared__ uint64_t bb[RSW_WARPS][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t q = (int64_t)blockIdx.x * RSW_WARPS + w;
+    if (q >= nq) return;
+    uint64_t* ck = rsm + w * RSW_CAND;
+    float* ss = reinterpret_cast<float*>(rsm + RSW_WARPS * RSW_CAND) + (size_t)w * L;
+    int P = nprobe_q ? nprobe_q[q] : Pfix;
+    P = P < 1 ? 1 : (P > Pmax ? Pmax : P);
+    const float* row = scores + q * L;
+    for (int c = lane; c < L; c += 32) ss[c] = row[c];
+    __syncwarp();
+    float tau = INFINITY;
+    if (P < L) {
+        auto load = [&](int c) -> uint64_t { return ((uint64_t)ordered_f32(ss[c]) << 32) | (uint32_t)c; };
+        auto none = [](int, uint64_t) {};
+        const uint64_t kP = warp_topk(load, L, P, none, hist[w], bb[w]);
+        tau = unordered_f32((uint32_t)(kP >> 32)) + (err ? 2.f * err[q] : 0.f);
+    }
+    // the lists that can still be among the P best
+    const uint32_t below = (1u << lane) - 1u;
+    int n = 0;
+    for (int c0 = 0; c0 < L; c0 += 32) {
+        const int c = c0 + lane;
+        const bool in = c < L && ss[c] <= tau;
+        const uint32_t m = __ballot_sync(0xffffffffu, in);
+        const int at = n + __popc(m & below);
+        if (in && at < RSW_CAND) ck[at] = (uint64_t)(uint32_t)c;
+        n += __popc(m);
+    }
+    if (n > RSW_CAND) {
+        if (lane == 0) redo[1 + atomicAdd(&redo[0], 1)] = (int32_t)q;
+        return;
+    }
+    __syncwarp();
+    // exact FP32 scores, 8 lists at a time
+    const float* qv = Q + q * d;
+    const bool vec = (d & 3) == 0 && d <= 128;
+    const int myrow = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+    for (int i0 = 0; i0 < n; i0 += 8) {
+        float a[8];
+        if (vec) {
+            const bool inl = lane * 4 < d;
+            float4 q4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (inl) q4 = make_float4(qv[lane * 4], qv[lane * 4 + 1], qv[lane * 4 + 2], qv[lane * 4 + 3]);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int c = i0 + u < n ? (int)(uint32_t)ck[i0 + u] : -1;
+                const float4 cv = (c >= 0 && inl) ? __ldg(reinterpret_cast<const float4*>(Cc + (int64_t)c * d) + lane)
+                                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+                if (spherical) {
+                    a[u] = fmaf(q4.w, cv.w, fmaf(q4.z, cv.z, fmaf(q4.y, cv.y, q4.x * cv.x)));
+                } else {
+                    const float e0 = q4.x - cv.x, e1 = q4.y - cv.y, e2 = q4.z - cv.z, e3 = q4.w - cv.w;
+                    a[u] = fmaf(e3, e3, fmaf(e2, e2, fmaf(e1, e1, e0 * e0)));
+                }
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int c = i0 + u < n ? (int)(uint32_t)ck[i0 + u] : -1;
+                float acc = 0.f;
+                if (c >= 0) {
+                    for (int t = lane; t < d; t += 32) {
+                        const float x = __ldg(Cc + (int64_t)c * d + t);
+                        if (spherical) acc = fmaf(qv[t], x, acc);
+                        else { const float e = qv[t] - x; acc = fmaf(e, e, acc); }
+                    }
+                }
+                a[u] = acc;
+            }
+        }
+        // halving exchange: lane ends with the sum of row myrow
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const bool up = lane & 16;
+            const float send = up ? a[i] : a[i + 4], keep = up ? a[i + 4] : a[i];
+            a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const bool up = lane & 8;
+            const float send = up ? a[i] : a[i + 2], keep = up ? a[i + 2] : a[i];
+            a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+        }
+        {
+            const bool up = lane & 4;
+            const float send = up ? a[0] : a[1], keep = up ? a[1] : a[0];
+            a[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+        }
+        a[0] += __shfl_xor_sync(0xffffffffu, a[0], 2);
+        a[0] += __shfl_xor_sync(0xffffffffu, a[0], 1);
+        __syncwarp();
+        const int i = i0 + myrow;
+        if ((lane & 3) == 0 && i < n) {
+            const uint32_t c = (uint32_t)ck[i];
+            ck[i] = ((uint64_t)ordered_f32(spherical ? -a[0] : a[0]) << 32) | c;
+        }
+        __syncwarp();
+    }
+    // the P best in order
+    if (n <= 32) {
+        const uint64_t v = warp_sort_key(lane < n ? ck[lane] : KEY_NONE, lane);
+        ck[lane] = v;
+    } else {
+        const int S = pow2_ceil(n);
+        for (int i = n + lane; i < S; i += 32) ck[i] = KEY_NONE;
+        __syncwarp();
+        warp_bitonic_smem(ck, S, lane);
+    }
+    __syncwarp();
+    for (int r = lane; r < Pmax; r += 32) {
+        if (r < P && r < n) {
+            probes[q * Pmax + r] = (int32_t)(ck[r] & 0xffffffffu);
+            if (score_out) score_out[q * Pmax + r] = unordered_f32((uint32_t)(ck[r] >> 32));
         } else {
             probes[q * Pmax + r] = -1;
             if (score_out) score_out[q * Pmax + r] = INFINITY;
@@ -2050,13 +2223,29 @@ static int rank_lists(ksc_index* ix, const float* Q, int64_t nq, const int32_t* 
     float* scores = (float*)ix->ws_scores.p;
     float* err = nullptr;
     KSC_TRY(list_scores(ix, Q, nq, exact, scores, &err, st));
-    // re-score buffer: 4 Pmax lists (a power of two, at least 1024, at most RS_CAP)
+    // re-score buffer of the CTA kernel: 4 Pmax lists (a power of two, at least 1024, at most RS_CAP)
     const int rs_cap = std::min(RS_CAP, std::max(1024, pow2_ceil(4 * Pmax)));
     const size_t smem = rs_cap * sizeof(uint64_t) + (ix->L <= RS_SMEM_L ? sizeof(float) * ix->L : 0);
-    cudaFuncSetAttribute(k_rank_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_rank_select<<<(unsigned)nq, 256, smem, st>>>(scores, err, Q, ix->c_rank, nq, ix->d, ix->L, ix->spherical,
-                                                   nprobe_q, Pfix, Pmax, rs_cap, probes, score_out);
-    ix->launches++;
+    KSC_CUDA(cudaFuncSetAttribute(k_rank_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (ix->L <= RSW_MAX_L && Pmax <= 4 * RSW_CAND / 8 && warp_per_query(nq)) {
+        // a warp per query; queries with too many lists inside the bound go to the CTA kernel
+        KSC_TRY(ensure(ix->ws_redo, sizeof(int32_t) * (nq + 1), st));
+        int32_t* redo = (int32_t*)ix->ws_redo.p;
+        KSC_CUDA(cudaMemsetAsync(redo, 0, sizeof(int32_t), st));
+        const size_t wsm = sizeof(uint64_t) * RSW_WARPS * RSW_CAND + sizeof(float) * RSW_WARPS * ix->L;
+        KSC_CUDA(cudaFuncSetAttribute(k_rank_select_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm));
+        k_rank_select_w<<<(unsigned)((nq + RSW_WARPS - 1) / RSW_WARPS), RSW_WARPS * 32, wsm, st>>>(
+            scores, err, Q, ix->c_rank, nq, ix->d, ix->L, ix->spherical, nprobe_q, Pfix, Pmax, probes, score_out,
+            redo);
+        KSC_LAUNCH_CHECK();
+        k_rank_select<<<num_sms() * 2, 256, smem, st>>>(scores, err, Q, ix->c_rank, nq, ix->d, ix->L, ix->spherical,
+                                                        nprobe_q, Pfix, Pmax, rs_cap, probes, score_out, redo);
+        ix->launches += 2;
+    } else {
+        k_rank_select<<<(unsigned)nq, 256, smem, st>>>(scores, err, Q, ix->c_rank, nq, ix->d, ix->L, ix->spherical,
+                                                       nprobe_q, Pfix, Pmax, rs_cap, probes, score_out, nullptr);
+        ix->launches++;
+    }
     KSC_LAUNCH_CHECK();
     return KSC_OK;
 }
@@ -2233,7 +2422,7 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
     KSC_TRY(run_scan(pl, M, A, ScanOut{nullptr, cnt, cand, pl.cap}, wa, L, ix->status, st));
     // expected keys per query of the unfiltered scan: max(4 R, N / 16), N from
     // the mean list length; a warp per query up to SW_MAX_KEYS, else a CTA
-    if (std::max(4.0 * pl.Rmax, (double)pl.Pmax * ix->n / L / 16.0) <= SW_MAX_KEYS)
+    if (std::max(4.0 * pl.Rmax, (double)pl.Pmax * ix->n / L / 16.0) <= SW_MAX_KEYS && warp_per_query(nq))
         k_threshold<<<(unsigned)((nq + SW_WARPS - 1) / SW_WARPS), SW_WARPS * 32, 0, st>>>(A, pl.Rmax, cnt, cand,
                                                                                            pl.cap, topr, thr);
     else
@@ -2285,7 +2474,7 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
         int32_t* redo = (int32_t*)ix->ws_redo.p;
         KSC_CUDA(cudaMemsetAsync(redo, 0, sizeof(int32_t), st));
         // candidates per query: the R kept by the threshold plus a few R more
-        if (4 * pl.Rmax <= SW_MAX_KEYS)
+        if (4 * pl.Rmax <= SW_MAX_KEYS && warp_per_query(nq))
             k_select<<<(unsigned)((nq + SW_WARPS - 1) / SW_WARPS), SW_WARPS * 32, 0, st>>>(
                 A, pl.Rmax, cnt, cand, pl.cap, topr, ncand_out, ix->status, ix->stats, redo);
         else
@@ -2330,7 +2519,7 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
         rr_R = pl.Rf;
         rr_q = nullptr;
     }
-    if (pl.k <= 32 && rr_R <= RW_MAXR && ix->d <= 128 && (ix->d & 3) == 0) {
+    if (pl.k <= 32 && rr_R <= RW_MAXR && ix->d <= 128 && (ix->d & 3) == 0 && warp_per_query(nq)) {
         const size_t smem = sizeof(uint64_t) * RW_WARPS * rr_R;
         cudaFuncSetAttribute(k_rerank_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_rerank_w<<<(unsigned)((nq + RW_WARPS - 1) / RW_WARPS), RW_WARPS * 32, smem, st>>>(

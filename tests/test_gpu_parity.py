@@ -334,3 +334,31 @@ def test_tensor_core_ranking_equals_fp32_ranking(torch, ksc, kind):
     a = g.search(Qd, 10, 9, 100)
     b = g.search(Qd, 10, 9, 100, opts=ksc.search_opts(rank_fp32=True))
     assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+
+
+def test_warp_shaped_kernels_bit_exact(torch, ksc):
+    """Batches of at least 8 queries per SM take the warp-per-query threshold,
+    select, ranking and re-rank kernels; smaller ones the CTA-per-query ones.
+    Both give the oracle's candidates, and a query's result does not depend on
+    which shape served it."""
+    ix, Q = small_index("l2")
+    g = gpu_index(ksc, ix)
+    reps = 1600 // len(Q) + 1
+    Qb = np.tile(Q, (reps, 1))
+    P, R, k = 5, 150, 10
+    probes = oracle_probes(ix, Q, P)
+    pb = np.tile(probes, (reps, 1))
+    big = g.search_with_probes(torch.from_numpy(Qb).cuda(), torch.from_numpy(pb).cuda(), k, R)
+    small = g.search_with_probes(torch.from_numpy(Q).cuda(), torch.from_numpy(probes).cuda(), k, R)
+    cand_b = big[2].cpu().numpy().view(np.uint64)
+    for qi in range(len(Q)):
+        Ql, b, _ = oracle.lut_q8(Q[qi], ix, probes[qi])
+        ref = oracle.scan_topr(ix, probes[qi], Ql, b, R)
+        assert np.array_equal(cand_b[qi, :len(ref)], ref), qi
+        assert np.array_equal(cand_b[qi + len(Q) * (reps - 1)], cand_b[qi])
+    for x, y in zip(small, big):
+        assert torch.equal(x, y[:len(Q)])
+    # ranking: the warp and CTA shapes return the same lists
+    pr_b, sc_b = g.rank_lists(torch.from_numpy(Qb).cuda(), 9)
+    pr_s, sc_s = g.rank_lists(torch.from_numpy(Q).cuda(), 9)
+    assert torch.equal(pr_b[:len(Q)], pr_s)
