@@ -855,60 +855,77 @@ __global__ void __launch_bounds__(256) k_threshold_cta(ScanArgs A, int Rmax, int
 // ------------------------------------------------------------------ work list (cluster-major)
 // pairs of (query, probe rank) grouped by list; items = (list, query group,
 // block tile).
-// Phase boundary of each query's probe ranks: ranks below `split[q]` (or
-// below `rs` when split is null) are scanned first with no filter, the rest
-// after the threshold.  side 0 selects the first part, side 1 the rest.
-__device__ __forceinline__ bool in_part(const ScanArgs& A, int64_t q, int r, int rs, const int32_t* split, int side) {
-    if (r >= nprobe_of(A, q)) return false;
-    const int b = split ? split[q] : rs;
-    return side == 0 ? r < b : r >= b;
+// Work lists of both parts of every query's probe ranks, in one pass: a warp
+// per query finds the end of the unfiltered first part and counts the pairs
+// of each part per list.  First part (plain search): the fewest nearest lists
+// holding S = max(NEAR_KEYS_PER_R * R, N / NEAR_SHARE_DIV) keys, N = the keys
+// the query probes.  The R-th key of a first set of S keys sits near the R/S
+// quantile of the nearest keys and the remaining lists are farther, so at most
+// about N R / S of their keys pass it: a few R.  S is at most half the
+// candidate store, and the first part never holds more keys than the store
+// (at least one list).  Hybrid search: the first `rs` ranks.  split[q] (plain
+// only) records the boundary for k_fill_parts.
+__device__ __forceinline__ int64_t list_size(const ScanArgs& A, int p) {
+    return (p >= 0 && p < A.L) ? A.list_n[p] : 0;
 }
 
-__global__ void k_count_pairs(ScanArgs A, int rs, const int32_t* __restrict__ split, int side,
-                              int32_t* __restrict__ cnt) {
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= A.nq * A.Pmax) return;
-    int64_t q = e / A.Pmax;
-    int r = (int)(e - q * A.Pmax);
-    if (!in_part(A, q, r, rs, split, side)) return;
-    const int p = A.probes[e];
-    if (p < 0 || p >= A.L) return;
-    atomicAdd(&cnt[p], 1);
-}
-
-// Per query, how many of its nearest lists the unfiltered first scan takes.
-// The R-th key of a first set of S keys sits near the R/S quantile of the
-// nearest keys, and the remaining lists are farther, so at most about
-// N * R / S of their N keys pass it: S = max(NEAR_KEYS_PER_R * R,
-// N / NEAR_SHARE_DIV) keeps that to a few R.  The first set is the fewest
-// nearest lists holding S keys (all probed lists if they hold fewer), with S
-// at most half the candidate store and never so many lists that their keys
-// exceed it (at least one list).
-__global__ void k_near_split(ScanArgs A, int Rmax, int cap, int32_t* __restrict__ split) {
-    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__global__ void k_count_parts(ScanArgs A, int Rmax, int cap, int rs, int32_t* __restrict__ split,
+                              int32_t* __restrict__ cntA, int32_t* __restrict__ cntB) {
+    const int lane = threadIdx.x & 31;
+    const int64_t q = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
     if (q >= A.nq) return;
     const int P = nprobe_of(A, q);
     const int32_t* pr = A.probes + q * A.Pmax;
-    int64_t total = 0;
-    for (int r = 0; r < P; ++r) total += (pr[r] >= 0 && pr[r] < A.L) ? A.list_n[pr[r]] : 0;
-    int64_t target = (int64_t)NEAR_KEYS_PER_R * rerank_of(A.rerank_q, A.Rfix, A.Rmin, Rmax, q);
-    target = max(target, total / NEAR_SHARE_DIV);
-    target = min(target, (int64_t)cap / 2);
-    int64_t acc = 0;
-    int r = 0;
-    while (r < P && acc < target) {
-        const int64_t n = (pr[r] >= 0 && pr[r] < A.L) ? A.list_n[pr[r]] : 0;
-        if (r > 0 && acc + n > cap) break;
-        acc += n;
-        ++r;
+    int b = rs;
+    if (split) {
+        long long total = 0;
+        for (int r = lane; r < P; r += 32) total += list_size(A, pr[r]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
+        long long target = (long long)NEAR_KEYS_PER_R * rerank_of(A.rerank_q, A.Rfix, A.Rmin, Rmax, q);
+        target = max(target, total / NEAR_SHARE_DIV);
+        target = min(target, (long long)cap / 2);
+        // first rank r whose keys-before reach the target, or (r > 0) whose list
+        // would overflow the store
+        long long acc = 0;
+        int bnd = P;
+        for (int r0 = 0; r0 < P; r0 += 32) {
+            const int r = r0 + lane;
+            const long long n = r < P ? list_size(A, pr[r]) : 0;
+            long long incl = n;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const long long before = acc + incl - n;
+            const bool stop = r < P && (before >= target || (r > 0 && before + n > cap));
+            const uint32_t m = __ballot_sync(0xffffffffu, stop);
+            if (m) {
+                bnd = r0 + __ffs(m) - 1;
+                break;
+            }
+            acc += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        b = bnd < 1 ? 1 : bnd;
+        if (lane == 0) split[q] = b;
     }
-    split[q] = r < 1 ? 1 : r;
+    for (int r = lane; r < P; r += 32) {
+        const int p = pr[r];
+        if (p >= 0 && p < A.L) atomicAdd(r < b ? &cntA[p] : &cntB[p], 1);
+    }
 }
 
 // exclusive scans: pair_off = scan(cnt); item_off = scan(ceil(cnt/QG) * ntiles)
-__global__ void __launch_bounds__(1024) k_scan_lists(const int32_t* __restrict__ cnt, const int32_t* __restrict__ list_n,
-                                                     int L, int QG, int TB, int64_t* __restrict__ pair_off,
-                                                     int64_t* __restrict__ item_off, int32_t* __restrict__ fill) {
+// Several work lists at once: CTA i scans cnt + i L into pair_off / item_off +
+// i (L + 1) and clears fill + i L.
+__global__ void __launch_bounds__(1024) k_scan_lists(const int32_t* __restrict__ cnt0, const int32_t* __restrict__ list_n,
+                                                     int L, int QG, int TB, int64_t* __restrict__ pair_off0,
+                                                     int64_t* __restrict__ item_off0, int32_t* __restrict__ fill0) {
+    const int32_t* cnt = cnt0 + (size_t)blockIdx.x * L;
+    int64_t* pair_off = pair_off0 + (size_t)blockIdx.x * (L + 1);
+    int64_t* item_off = item_off0 + (size_t)blockIdx.x * (L + 1);
+    int32_t* fill = fill0 + (size_t)blockIdx.x * L;
     __shared__ int64_t s_p[1024], s_i[1024];
     const int per = (L + 1023) / 1024;
     const int c0 = threadIdx.x * per;
@@ -946,18 +963,20 @@ __global__ void __launch_bounds__(1024) k_scan_lists(const int32_t* __restrict__
     }
 }
 
-__global__ void k_fill_pairs(ScanArgs A, int rs, const int32_t* __restrict__ split, int side,
-                             const int64_t* __restrict__ pair_off, int32_t* __restrict__ fill,
-                             uint32_t* __restrict__ pairs) {
+__global__ void k_fill_parts(ScanArgs A, int rs, const int32_t* __restrict__ split,
+                             const int64_t* __restrict__ offA, int32_t* __restrict__ fillA, uint32_t* __restrict__ pairsA,
+                             const int64_t* __restrict__ offB, int32_t* __restrict__ fillB,
+                             uint32_t* __restrict__ pairsB) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= A.nq * A.Pmax) return;
     int64_t q = e / A.Pmax;
     int r = (int)(e - q * A.Pmax);
-    if (!in_part(A, q, r, rs, split, side)) return;
-    int p = A.probes[e];
+    if (r >= nprobe_of(A, q)) return;
+    const int p = A.probes[e];
     if (p < 0 || p >= A.L) return;
-    int slot = atomicAdd(&fill[p], 1);
-    pairs[pair_off[p] + slot] = (uint32_t)e;  // e = q * Pmax + r
+    const bool first = r < (split ? split[q] : rs);
+    const int slot = atomicAdd(first ? &fillA[p] : &fillB[p], 1);
+    (first ? pairsA : pairsB)[(first ? offA : offB)[p] + slot] = (uint32_t)e;  // e = q * Pmax + r
 }
 
 // ------------------------------------------------------------------ a3: LUT16 scan
@@ -2312,19 +2331,6 @@ struct WorkList {
     uint32_t* pairs;    // [<= nq * Pmax]
 };
 
-static int build_worklist(ksc_index* ix, const ScanArgs& A, int rs, const int32_t* split, int side, int QG, int TB,
-                          WorkList& w, cudaStream_t st) {
-    const int L = ix->L;
-    const int64_t n = A.nq * A.Pmax;
-    KSC_CUDA(cudaMemsetAsync(w.cnt, 0, sizeof(int32_t) * L, st));
-    k_count_pairs<<<blocks_for(n, 256), 256, 0, st>>>(A, rs, split, side, w.cnt);
-    k_scan_lists<<<1, 1024, 0, st>>>(w.cnt, ix->list_n, L, QG, TB, w.pair_off, w.item_off, w.fill);
-    k_fill_pairs<<<blocks_for(n, 256), 256, 0, st>>>(A, rs, split, side, w.pair_off, w.fill, w.pairs);
-    ix->launches += 3;
-    KSC_LAUNCH_CHECK();
-    return KSC_OK;
-}
-
 static int run_scan(const Plan& pl, int M, const ScanArgs& A, const ScanOut& O, const WorkList& w, int L,
                     int32_t* status, cudaStream_t st) {
     const int S = (M + pl.G - 1) / pl.G;
@@ -2348,7 +2354,7 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
     const int M = ix->M, L = ix->L;
     const int QG = 32 / pl.G;
     // hybrid: the n_near nearest lists are the fully scanned ones (Sec. 4.4);
-    // plain: a per-query split (k_near_split)
+    // plain: a per-query split (k_count_parts)
     const int rA = std::min(pl.hybrid ? pl.n_near : 1, pl.Pmax);
     KSC_TRY(ensure(ix->ws_lut, (size_t)nq * pl.Pmax * M * PQ_K, st));
     KSC_TRY(ensure(ix->ws_bias, sizeof(int32_t) * nq * pl.Pmax, st));
@@ -2357,7 +2363,7 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
     KSC_TRY(ensure(ix->ws_cnt, sizeof(int32_t) * nq, st));
     KSC_TRY(ensure(ix->ws_cand, sizeof(uint64_t) * nq * pl.cap, st));
     KSC_TRY(ensure(ix->ws_topr, sizeof(uint64_t) * nq * pl.Rmax, st));
-    const size_t wl_head = sizeof(int64_t) * 2 * (L + 1) + sizeof(int32_t) * 2 * L;
+    const size_t wl_head = sizeof(int64_t) * 2 * (L + 1) + sizeof(int32_t) * 2 * L;  // per work list
     KSC_TRY(ensure(ix->ws_items, 2 * wl_head + sizeof(uint32_t) * nq * (2 * pl.Pmax + 1) + 256, st));
     uint8_t* lut = (uint8_t*)ix->ws_lut.p;
     int32_t* bias = (int32_t*)ix->ws_bias.p;
@@ -2366,18 +2372,23 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
     int32_t* cnt = (int32_t*)ix->ws_cnt.p;
     uint64_t* cand = (uint64_t*)ix->ws_cand.p;
     uint64_t* topr = (uint64_t*)ix->ws_topr.p;
+    // both work lists side by side: pair_off [2][L+1], item_off [2][L+1],
+    // cnt [2][L], fill [2][L], then the pairs
     WorkList wa, wb;
     {
-        char* wp = (char*)ix->ws_items.p;
-        WorkList* ws_[2] = {&wa, &wb};
-        for (WorkList* w : ws_) {
-            w->pair_off = (int64_t*)wp;
-            w->item_off = w->pair_off + (L + 1);
-            w->cnt = (int32_t*)(w->item_off + (L + 1));
-            w->fill = w->cnt + L;
-            wp += wl_head;
-        }
-        wa.pairs = (uint32_t*)wp;
+        int64_t* po = (int64_t*)ix->ws_items.p;
+        int64_t* io = po + 2 * (L + 1);
+        int32_t* cn = (int32_t*)(io + 2 * (L + 1));
+        int32_t* fl = cn + 2 * L;
+        wa.pair_off = po;
+        wb.pair_off = po + (L + 1);
+        wa.item_off = io;
+        wb.item_off = io + (L + 1);
+        wa.cnt = cn;
+        wb.cnt = cn + L;
+        wa.fill = fl;
+        wb.fill = fl + L;
+        wa.pairs = (uint32_t*)(fl + 2 * L);
         wb.pairs = wa.pairs + nq * pl.Pmax;
     }
     int32_t* split = pl.hybrid ? nullptr : (int32_t*)(wb.pairs + nq * pl.Pmax);
@@ -2385,13 +2396,13 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
                ix->list_boff, ix->list_n, ix->blk_codes, ix->blk_ids, ix->L};
     // 1. work lists: the nearest list of every query, and the rest
     mark(ix, 1, st);
-    if (split) {
-        k_near_split<<<blocks_for(nq, 256), 256, 0, st>>>(A, pl.Rmax, pl.cap, split);
-        KSC_LAUNCH_CHECK();
-        ix->launches++;
-    }
-    KSC_TRY(build_worklist(ix, A, rA, split, 0, QG, pl.TB, wa, st));
-    KSC_TRY(build_worklist(ix, A, rA, split, 1, QG, pl.TB, wb, st));
+    KSC_CUDA(cudaMemsetAsync(wa.cnt, 0, sizeof(int32_t) * 2 * L, st));
+    k_count_parts<<<(unsigned)((nq + 7) / 8), 256, 0, st>>>(A, pl.Rmax, pl.cap, rA, split, wa.cnt, wb.cnt);
+    k_scan_lists<<<2, 1024, 0, st>>>(wa.cnt, ix->list_n, L, QG, pl.TB, wa.pair_off, wa.item_off, wa.fill);
+    k_fill_parts<<<blocks_for(nq * pl.Pmax, 256), 256, 0, st>>>(A, rA, split, wa.pair_off, wa.fill, wa.pairs,
+                                                                wb.pair_off, wb.fill, wb.pairs);
+    KSC_LAUNCH_CHECK();
+    ix->launches += 3;
     // 2. quantised LUTs of every probed (query, list)
     mark(ix, 2, st);
     {
