@@ -1142,13 +1142,23 @@ struct ScanItem {
     int64_t g0, npairs;
 };
 
+// Item `it` of a work list, by the whole warp: the last list p with
+// item_off[p] <= it is found by a 32-way search (each round one load per lane
+// and a ballot; two rounds for 1024 lists), then the item's query group and
+// tile.  All 32 lanes call and get the same item.
 __device__ __forceinline__ ScanItem locate_item(const ScanArgs& A, const int64_t* __restrict__ pair_off,
                                                 const int64_t* __restrict__ item_off, int L, int TB, int QG,
                                                 int64_t it) {
-    int lo = 0, hi = L - 1;  // last list p with item_off[p] <= it
+    const int lane = threadIdx.x & 31;
+    int lo = 0, hi = L - 1;  // invariant: item_off[lo] <= it < item_off[hi + 1]
     while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (item_off[mid] <= it) lo = mid; else hi = mid - 1;
+        const int step = (hi - lo + 32) / 32;  // ceil((hi - lo + 1) / 32)
+        const int pos = min(lo + lane * step, hi);
+        const uint32_t m = __ballot_sync(0xffffffffu, item_off[pos] <= it);  // a prefix of lanes; lane 0 holds
+        const int last = 31 - __clz(m);
+        const int nlo = min(lo + last * step, hi);
+        hi = (last < 31 && lo + (last + 1) * step <= hi) ? lo + (last + 1) * step - 1 : hi;
+        lo = nlo;
     }
     ScanItem r;
     r.p = lo;
@@ -1211,7 +1221,7 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32, (SMAX <= 2 ? 3 : (SMAX <= 8 ?
     };
     int64_t it = (int64_t)blockIdx.x * SCAN_WARPS + warp;
     if (it >= total) return;
-    ScanItem x = locate_item(A, pair_off, item_off, L, TB, QG, it);
+    ScanItem x = locate_item(A, pair_off, item_off, L, TB, QG, it), nx = x;
     if (lane == 0) issue(x, 0, 0);
     uint32_t phase[2] = {0u, 0u};
     int b = 0;
@@ -1245,9 +1255,10 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32, (SMAX <= 2 ? 3 : (SMAX <= 8 ?
         const int64_t next_it = it + stride;
         for (int c = 0; c < nch; ++c) {
             // prefetch the chunk after this one into the other buffer
+            if (c + 1 == nch && next_it < total) nx = locate_item(A, pair_off, item_off, L, TB, QG, next_it);
             if (lane == 0) {
                 if (c + 1 < nch) issue(x, c + 1, b ^ 1);
-                else if (next_it < total) issue(locate_item(A, pair_off, item_off, L, TB, QG, next_it), 0, b ^ 1);
+                else if (next_it < total) issue(nx, 0, b ^ 1);
             }
             const bool ready = !failed && scan_wait(b ? bar1 : bar0, phase[b]);
             phase[b] ^= 1u;
@@ -1320,7 +1331,7 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32, (SMAX <= 2 ? 3 : (SMAX <= 8 ?
         }
         if (next_it >= total || failed) break;
         it = next_it;
-        x = locate_item(A, pair_off, item_off, L, TB, QG, it);
+        x = nx;
     }
 }
 
@@ -1378,7 +1389,7 @@ __global__ void __launch_bounds__(S4_WARPS * 32, MAXM <= 64 ? 3 : 1)
     const int64_t stride = (int64_t)gridDim.x * S4_WARPS;
     int64_t it = (int64_t)blockIdx.x * S4_WARPS + warp;
     if (it >= total) return;
-    ScanItem x = locate_item(A, pair_off, item_off, L, TB, S4_Q, it);
+    ScanItem x = locate_item(A, pair_off, item_off, L, TB, S4_Q, it), nx = x;
     if (lane == 0) issue(x, 0, 0);
     uint32_t phase[2] = {0u, 0u};
     int b = 0;
@@ -1412,9 +1423,10 @@ __global__ void __launch_bounds__(S4_WARPS * 32, MAXM <= 64 ? 3 : 1)
         const int nch = (x.b1 - x.b0 + S4_B - 1) / S4_B;
         const int64_t next_it = it + stride;
         for (int c = 0; c < nch; ++c) {
+            if (c + 1 == nch && next_it < total) nx = locate_item(A, pair_off, item_off, L, TB, S4_Q, next_it);
             if (lane == 0) {
                 if (c + 1 < nch) issue(x, c + 1, b ^ 1);
-                else if (next_it < total) issue(locate_item(A, pair_off, item_off, L, TB, S4_Q, next_it), 0, b ^ 1);
+                else if (next_it < total) issue(nx, 0, b ^ 1);
             }
             const bool ready = !failed && scan_wait(b ? bar1 : bar0, phase[b]);
             phase[b] ^= 1u;
@@ -1478,7 +1490,7 @@ __global__ void __launch_bounds__(S4_WARPS * 32, MAXM <= 64 ? 3 : 1)
         }
         if (next_it >= total || failed) break;
         it = next_it;
-        x = locate_item(A, pair_off, item_off, L, TB, S4_Q, it);
+        x = nx;
     }
 }
 
