@@ -1119,6 +1119,7 @@ struct ScanOut {
 // global memory only for those.  No CTA-wide barrier: warps run independently.
 constexpr int SCAN_WARPS = 8;
 constexpr int SCAN_CHUNK_BYTES = 4096;           // per buffer, per warp
+constexpr int SCAN_BUF_KEYS = 128;               // kept keys buffered per (warp, query slot)
 constexpr uint32_t SCAN_WAIT_LIMIT = 1u << 22;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -1190,8 +1191,14 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32, (SMAX <= 2 ? 3 : (SMAX <= 8 ?
     constexpr int V = 32 / G;
     extern __shared__ __align__(128) uint8_t bufs[];  // SCAN_WARPS x 2 x SCAN_CHUNK_BYTES
     __shared__ __align__(8) uint64_t full[SCAN_WARPS][2];
+    // kept keys of the warp's current item, per query slot, flushed to the
+    // candidate store with one atomic per slot when a slot fills and when the
+    // item ends (so a block's atomic latency is not on the scan's path)
+    __shared__ uint64_t kbuf[SCAN_WARPS][QG][SCAN_BUF_KEYS];
+    __shared__ int kcnt[SCAN_WARPS][QG];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int slot = lane / G, g = lane % G;
+    if (lane < QG) kcnt[warp][lane] = 0;
     const int M = A.M;
     const int S = (M + G - 1) / G;
     const int blk_bytes = M * 16;
@@ -1251,6 +1258,24 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32, (SMAX <= 2 ? 3 : (SMAX <= 8 ?
 #pragma unroll
             for (int u = 0; u < SMAX; ++u) t[u] = make_uint4(0, 0, 0, 0);
         }
+        // all lanes: each lane group writes its slot's buffered keys; a buffered
+        // entry holds (distance word, vector slot in blk_ids), the id is
+        // looked up here, many at once
+        auto flush = [&]() {
+            const int n = kcnt[warp][slot];
+            int base = 0;
+            if (g == 0 && n > 0) base = atomicAdd(&O.cnt[q], n);
+            base = __shfl_sync(0xffffffffu, base, 0, G);
+            for (int i = g; i < n; i += G) {
+                const uint64_t e = kbuf[warp][slot][i];
+                const uint32_t id = (uint32_t)A.ids[(uint32_t)e];
+                if (base + i < O.cap) O.cand[q * O.cap + base + i] = (e & 0xffffffff00000000ull) | id;
+            }
+            __syncwarp();
+            if (g == 0) kcnt[warp][slot] = 0;
+            __syncwarp();
+        };
+        const int listn = A.list_n[x.p];
         const int nch = (x.b1 - x.b0 + cb - 1) / cb;
         const int64_t next_it = it + stride;
         for (int c = 0; c < nch; ++c) {
@@ -1290,45 +1315,44 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32, (SMAX <= 2 ? 3 : (SMAX <= 8 ?
                     for (int m = 0; m < 16; ++m) acc[m] = prmt(a32[2 * m], a32[2 * m + 1], 0x5410u);
                     uint32_t sums[V];
                     reduce_scatter<G>(acc, lane, sums);
-                    // keys at or below the threshold, appended with one atomic per
-                    // lane group (query) and block
+                    // keys at or below the threshold (padding, only at a list's
+                    // tail, excluded by the list length); the id is needed now
+                    // only on a tie with the threshold's distance
                     uint64_t keep[V];
                     uint32_t kmask = 0;
                     if (active) {
+                        const int nv = listn - (c0 + blk) * 32;
+                        const uint32_t vslot = (uint32_t)((gb0 + blk) * 32 + V * g);
 #pragma unroll
                         for (int v = 0; v < V; ++v) {
                             // high word of the key: (D + 2^31) as an unsigned integer
                             const uint32_t Dk = (uint32_t)(bias + (int32_t)sums[v]) ^ 0x80000000u;
-                            keep[v] = (uint64_t)Dk << 32;
-                            if (Dk <= thD) {
-                                const int32_t id = A.ids[(gb0 + blk) * 32 + V * g + v];
-                                if (id >= 0 && (Dk < thD || (uint32_t)id <= thI)) {
-                                    keep[v] |= (uint32_t)id;
-                                    kmask |= 1u << v;
-                                }
-                            }
+                            keep[v] = ((uint64_t)Dk << 32) | (vslot + v);
+                            if (V * g + v < nv &&
+                                (Dk < thD || (Dk == thD && (uint32_t)A.ids[vslot + v] <= thI)))
+                                kmask |= 1u << v;
                         }
                     }
-                    const int nk = __popc(kmask);
-                    int incl = nk;
+                    // into the slot's buffer, which always has room for a whole
+                    // block (32 keys): each lane reserves its keys with a shared
+                    // atomic; a slot left with less room is flushed
+                    if (__any_sync(0xffffffffu, kmask != 0u)) {
+                        if (kmask) {
+                            const int pos = atomicAdd(&kcnt[warp][slot], __popc(kmask));
 #pragma unroll
-                    for (int o = 1; o < G; o <<= 1) {
-                        const int y = __shfl_up_sync(0xffffffffu, incl, o, G);
-                        if (g >= o) incl += y;
-                    }
-                    const int tot = __shfl_sync(0xffffffffu, incl, G - 1, G);
-                    int base = (g == G - 1 && tot > 0) ? atomicAdd(&O.cnt[q], tot) : 0;
-                    base = __shfl_sync(0xffffffffu, base, G - 1, G) + incl - nk;
-#pragma unroll
-                    for (int v = 0; v < V; ++v) {
-                        const int at = base + __popc(kmask & ((1u << v) - 1u));
-                        if (((kmask >> v) & 1u) && at < O.cap) O.cand[q * O.cap + at] = keep[v];
+                            for (int v = 0; v < V; ++v)
+                                if ((kmask >> v) & 1u)
+                                    kbuf[warp][slot][pos + __popc(kmask & ((1u << v) - 1u))] = keep[v];
+                        }
+                        __syncwarp();
+                        if (__any_sync(0xffffffffu, kcnt[warp][slot] > SCAN_BUF_KEYS - 32)) flush();
                     }
                 }
             }
             __syncwarp();  // the whole warp is done with buffer b before lane 0 refills it
             b ^= 1;
         }
+        if (__any_sync(0xffffffffu, kcnt[warp][slot] > 0)) flush();
         if (next_it >= total || failed) break;
         it = next_it;
         x = nx;
