@@ -375,7 +375,8 @@ def run_ours(args, rank, ws):
             "recall@10": round(learned["recall"], 4), "mean_nprobe": round(learned["mean_nprobe"], 3),
             "eq2": learned["params"], "validation_recall@10": round(learned["val_recall"], 4),
             "train_queries": args.ntrain, "train_loss": round(learned["train_loss"], 4),
-            "train_s": learned["train_s"], "vs_plain": round(plain_ms / learned["ms"], 3)}
+            "train_s": learned["train_s"], "vs_plain": round(plain_ms / learned["ms"], 3),
+            "stage_ms": {s_: round(v, 4) for s_, v in learned["stage"].items()}}
         out = {
             "metric": METRIC,
             "value": round(value, 1), "unit": "queries/s", "n_gpus": ws, "steps": args.steps,

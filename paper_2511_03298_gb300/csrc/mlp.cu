@@ -21,7 +21,7 @@ namespace ksc {
 constexpr int MLP_F = 64, MLP_H = 64, MLP_O = 2, MLP_FEAT_K = 32;
 constexpr int MLP_NPARAM = MLP_H * MLP_F + MLP_H + MLP_H * MLP_H + MLP_H + MLP_O * MLP_H + MLP_O;
 constexpr int MLP_TILE = 128;  // samples per CTA (training)
-constexpr int MLP_ITILE = 16;  // queries per CTA (inference: many CTAs for a batch)
+constexpr int MLP_ITILE = 32;  // queries per tile of the inference kernel (one warp's rows)
 
 struct MlpW {  // views into a packed parameter vector (same packing as the oracle)
     const float *W1, *b1, *W2, *b2, *W3, *b3;
@@ -198,40 +198,57 @@ __host__ __device__ inline int eq2(float p, int pmin, int pmax, float p0, float 
     return r > (float)pmax ? pmax : (r < (float)pmin ? pmin : (int)r);
 }
 
+// One layer for a tile of rows: thread e computes unit a = e / rows of row
+// r = e % rows, so a warp shares one weight row (broadcast) and reads 32
+// activation rows of stride MLP_LDI (odd: distinct banks).  Accumulation in
+// ascending input order, as in dense().
+constexpr int MLP_LDI = MLP_F + 1;  // (MLP_F == MLP_H)
+__device__ __forceinline__ void dense_rows(const float* in, int rows, int Fin, const float* W, const float* b, int A,
+                                           float* out, bool relu_bf) {
+    for (int e = threadIdx.x; e < rows * A; e += blockDim.x) {
+        const int a = e / rows, r = e - a * rows;
+        float acc = b[a];
+        for (int f = 0; f < Fin; ++f) acc = fmaf(in[r * MLP_LDI + f], W[a * Fin + f], acc);
+        out[r * MLP_LDI + a] = relu_bf ? bf(acc > 0.f ? acc : 0.f) : acc;
+    }
+}
+
 // Inference: BF16 weights and activations, FP32 accumulation; probabilities
-// and the Eq. 2 parameters per query.
+// and the Eq. 2 parameters per query.  Persistent CTAs over tiles of
+// MLP_ITILE queries.
 __global__ void __launch_bounds__(256) k_mlp_infer(const float* __restrict__ w, const float* __restrict__ x,
                                                    int64_t B, ksc_adaptive_params prm, float* __restrict__ prob,
                                                    int32_t* __restrict__ nprobe, int32_t* __restrict__ rerank) {
     extern __shared__ float sm[];
     float* sw = sm;
     float* X = sw + MLP_NPARAM;
-    float* H1 = X + MLP_ITILE * MLP_F;
-    float* H2 = H1 + MLP_ITILE * MLP_H;
-    const int64_t r0 = (int64_t)blockIdx.x * MLP_ITILE;
-    const int rows = (int)(B - r0 < MLP_ITILE ? B - r0 : MLP_ITILE);
+    float* H1 = X + MLP_ITILE * MLP_LDI;
+    float* H2 = H1 + MLP_ITILE * MLP_LDI;
     for (int e = threadIdx.x; e < MLP_NPARAM; e += blockDim.x) sw[e] = bf(w[e]);
-    for (int e = threadIdx.x; e < rows * MLP_F; e += blockDim.x) X[e] = bf(x[r0 * MLP_F + e]);
-    __syncthreads();
     const MlpW W = mlp_views(sw);
-    dense(X, rows, MLP_F, W.W1, W.b1, MLP_H, nullptr, H1);
-    __syncthreads();
-    for (int e = threadIdx.x; e < rows * MLP_H; e += blockDim.x) H1[e] = bf(H1[e]);
-    __syncthreads();
-    dense(H1, rows, MLP_H, W.W2, W.b2, MLP_H, nullptr, H2);
-    __syncthreads();
-    for (int e = threadIdx.x; e < rows * MLP_H; e += blockDim.x) H2[e] = bf(H2[e]);
-    __syncthreads();
-    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
-        float p[MLP_O];
-        for (int o = 0; o < MLP_O; ++o) {
-            float z = W.b3[o];
-            for (int f = 0; f < MLP_H; ++f) z = fmaf(H2[r * MLP_H + f], W.W3[o * MLP_H + f], z);
-            p[o] = 1.f / (1.f + expf(-z));
-            if (prob) prob[(r0 + r) * MLP_O + o] = p[o];
+    for (int64_t r0 = (int64_t)blockIdx.x * MLP_ITILE; r0 < B; r0 += (int64_t)gridDim.x * MLP_ITILE) {
+        const int rows = (int)(B - r0 < MLP_ITILE ? B - r0 : MLP_ITILE);
+        for (int e = threadIdx.x; e < rows * MLP_F; e += blockDim.x) {
+            const int r = e / MLP_F, f = e - r * MLP_F;
+            X[r * MLP_LDI + f] = bf(x[(r0 + r) * MLP_F + f]);
         }
-        if (nprobe) nprobe[r0 + r] = eq2(p[0], prm.pmin, prm.pmax, prm.p0, prm.p1);
-        if (rerank) rerank[r0 + r] = eq2(p[1], prm.rmin, prm.rmax, prm.r0, prm.r1);
+        __syncthreads();
+        dense_rows(X, rows, MLP_F, W.W1, W.b1, MLP_H, H1, true);
+        __syncthreads();
+        dense_rows(H1, rows, MLP_H, W.W2, W.b2, MLP_H, H2, true);
+        __syncthreads();
+        for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+            float p[MLP_O];
+            for (int o = 0; o < MLP_O; ++o) {
+                float z = W.b3[o];
+                for (int f = 0; f < MLP_H; ++f) z = fmaf(H2[r * MLP_LDI + f], W.W3[o * MLP_H + f], z);
+                p[o] = 1.f / (1.f + expf(-z));
+                if (prob) prob[(r0 + r) * MLP_O + o] = p[o];
+            }
+            if (nprobe) nprobe[r0 + r] = eq2(p[0], prm.pmin, prm.pmax, prm.p0, prm.p1);
+            if (rerank) rerank[r0 + r] = eq2(p[1], prm.rmin, prm.rmax, prm.r0, prm.r1);
+        }
+        __syncthreads();  // the tile buffers are reused
     }
 }
 
@@ -252,7 +269,7 @@ __global__ void k_hits(const float* __restrict__ dists, int64_t nq, int k, const
 }
 
 static size_t grad_smem() { return sizeof(float) * (MLP_NPARAM + MLP_TILE * (MLP_F + 3 * MLP_H + MLP_O)); }
-static size_t infer_smem() { return sizeof(float) * (MLP_NPARAM + MLP_ITILE * (MLP_F + 2 * MLP_H)); }
+static size_t infer_smem() { return sizeof(float) * (MLP_NPARAM + 3 * MLP_ITILE * MLP_LDI); }
 
 int mlp_grad(const float* w, const float* x, const float* y, int64_t B, float* grad, float* loss, cudaStream_t st) {
     KSC_CUDA(cudaMemsetAsync(grad, 0, sizeof(float) * MLP_NPARAM, st));
@@ -266,8 +283,12 @@ int mlp_grad(const float* w, const float* x, const float* y, int64_t B, float* g
 int mlp_infer(const float* w, const float* x, int64_t B, const ksc_adaptive_params& prm, float* prob,
               int32_t* nprobe, int32_t* rerank, cudaStream_t st) {
     KSC_CUDA(cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)infer_smem()));
-    k_mlp_infer<<<(unsigned)((B + MLP_ITILE - 1) / MLP_ITILE), 256, infer_smem(), st>>>(w, x, B, prm, prob, nprobe,
-                                                                                        rerank);
+    // persistent over row tiles: the weights are staged once per CTA
+    int per_sm = 0;
+    KSC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_infer, 256, infer_smem()));
+    const int64_t tiles = (B + MLP_ITILE - 1) / MLP_ITILE;
+    const int64_t grid = std::min<int64_t>(tiles, (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1));
+    k_mlp_infer<<<(unsigned)(grid > 0 ? grid : 1), 256, infer_smem(), st>>>(w, x, B, prm, prob, nprobe, rerank);
     KSC_LAUNCH_CHECK();
     return KSC_OK;
 }

@@ -97,6 +97,7 @@ __global__ void __launch_bounds__(256) k_list_scores(const float* __restrict__ Q
 // the re-score buffer holds (4 Pmax, at least 1024, at most RS_CAP), every
 // list is re-scored when all fit, else those with the lowest given scores.
 constexpr int RS_CAP = 4096;     // largest re-score buffer
+constexpr int FEAT_K = 32;       // list distances of the predictor's features
 constexpr int RS_SMEM_L = 8192;  // score rows up to this length are staged in shared memory
 __device__ __forceinline__ float exact_list_score(const float* __restrict__ qs, const float* __restrict__ c, int d,
                                                   int spherical, int lane) {
@@ -288,7 +289,8 @@ __global__ void __launch_bounds__(RSW_WARPS * 32) k_rank_select_w(const float* _
                                                                   const int32_t* __restrict__ nprobe_q, int Pfix,
                                                                   int Pmax, int32_t* __restrict__ probes,
                                                                   float* __restrict__ score_out,
-                                                                  int32_t* __restrict__ redo) {
+                                                                  int32_t* __restrict__ redo,
+                                                                  float* __restrict__ feat) {
     extern __shared__ uint64_t rsm[];  // RSW_WARPS x RSW_CAND keys, then RSW_WARPS x L scores
     __shared__ uint32_t hist[RSW_WARPS][256];
     __shared__ uint64_t bb[RSW_WARPS][32];
@@ -303,8 +305,28 @@ __global__ void __launch_bounds__(RSW_WARPS * 32) k_rank_select_w(const float* _
     for (int c = lane; c < L; c += 32) ss[c] = row[c];
     __syncwarp();
     float tau = INFINITY;
-    if (P < L) {
-        auto load = [&](int c) -> uint64_t { return ((uint64_t)ordered_f32(ss[c]) << 32) | (uint32_t)c; };
+    auto load = [&](int c) -> uint64_t { return ((uint64_t)ordered_f32(ss[c]) << 32) | (uint32_t)c; };
+    if (feat) {
+        // the K = max(P, FEAT_K) smallest given scores, sorted: the predictor's
+        // distances (+ ||q||^2 for L2, which the score leaves out) and s_P
+        const int K = min(max(P, FEAT_K), L);
+        auto emit = [&](int i, uint64_t k) { ck[i] = k; };
+        if (K < L) warp_topk(load, L, K, emit, hist[w], bb[w]);
+        else for (int c = lane; c < L; c += 32) ck[c] = load(c);
+        const int S = pow2_ceil(K);
+        for (int i = K + lane; i < S; i += 32) ck[i] = KEY_NONE;
+        __syncwarp();
+        warp_bitonic_smem(ck, S, lane);
+        float qq = 0.f;
+        if (!spherical) {
+            for (int t = lane; t < d; t += 32) qq = fmaf(Q[q * d + t], Q[q * d + t], qq);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) qq += __shfl_xor_sync(0xffffffffu, qq, o);
+        }
+        feat[q * FEAT_K + lane] = unordered_f32((uint32_t)(ck[lane] >> 32)) + qq;
+        if (P < L) tau = unordered_f32((uint32_t)(ck[P - 1] >> 32)) + (err ? 2.f * err[q] : 0.f);
+        __syncwarp();
+    } else if (P < L) {
         auto none = [](int, uint64_t) {};
         const uint64_t kP = warp_topk(load, L, P, none, hist[w], bb[w]);
         tau = unordered_f32((uint32_t)(kP >> 32)) + (err ? 2.f * err[q] : 0.f);
@@ -410,6 +432,35 @@ __global__ void __launch_bounds__(RSW_WARPS * 32) k_rank_select_w(const float* _
             if (score_out) score_out[q * Pmax + r] = INFINITY;
         }
     }
+}
+
+// The predictor's distances (Sec. 4.2.1): per query the FEAT_K smallest list
+// scores, ascending, from the given score matrix (the tensor-core scores,
+// within their bound of the exact ones); for L2 the query's squared norm,
+// which the ranking score leaves out, is added back.  One warp per query.
+__global__ void __launch_bounds__(256) k_feat_scores(const float* __restrict__ scores, const float* __restrict__ Q,
+                                                     int d, int spherical, int64_t nq, int L,
+                                                     float* __restrict__ out) {
+    __shared__ uint32_t hist[8][256];
+    __shared__ uint64_t bb[8][32];
+    __shared__ uint64_t kk[8][FEAT_K];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t q = (int64_t)blockIdx.x * 8 + w;
+    if (q >= nq) return;
+    const float* row = scores + q * L;
+    auto load = [&](int c) -> uint64_t { return ((uint64_t)ordered_f32(row[c]) << 32) | (uint32_t)c; };
+    auto emit = [&](int i, uint64_t k) { kk[w][i] = k; };
+    if (L > FEAT_K) warp_topk(load, L, FEAT_K, emit, hist[w], bb[w]);
+    else kk[w][lane] = load(lane);  // L == FEAT_K (the predictor needs 32 lists)
+    float qq = 0.f;
+    if (!spherical) {
+        for (int t = lane; t < d; t += 32) qq = fmaf(Q[q * d + t], Q[q * d + t], qq);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) qq += __shfl_xor_sync(0xffffffffu, qq, o);
+    }
+    __syncwarp();
+    const uint64_t v = warp_sort_key(kk[w][lane], lane);
+    out[q * FEAT_K + lane] = unordered_f32((uint32_t)(v >> 32)) + qq;
 }
 
 // ------------------------------------------------------------------ a2: quantised LUTs
@@ -651,19 +702,21 @@ __global__ void __launch_bounds__(256) k_lut_quant(LutArgs A, const uint32_t* __
 // and they are quantised from shared memory (same FP32 rule, same results as
 // the two-pass kernels above).
 template <int DS>
-__global__ void __launch_bounds__(256) k_lut_fused(LutArgs A, int Pb, uint8_t* __restrict__ lut,
+__global__ void __launch_bounds__(256) k_lut_fused(LutArgs A, int Pb, int Pm, uint8_t* __restrict__ lut,
                                                    int32_t* __restrict__ bias, float* __restrict__ scale) {
     extern __shared__ float fsm[];
     const int M = A.M;
     const int ld = cb_ld(A.dsub);
-    float* cbs = fsm;                                  // M x ld
-    float* T = cbs + M * ld;                           // Pb x M rows of 16, stride 17 (no bank conflicts)
-    float* mins = T + (size_t)Pb * M * (PQ_K + 1);     // Pb x M
-    float* qs = mins + Pb * M;                         // d (8-byte aligned: every offset above is even)
+    float* cbs = fsm;                                            // M x ld
+    float* T = cbs + M * ld;                                     // Pb x M rows of 16, stride 17 (no bank conflicts)
+    float* mins = T + (((size_t)Pb * M * (PQ_K + 1) + 3) & ~(size_t)3);  // Pm x M
+    float* qs = mins + (((size_t)Pm * M + 3) & ~(size_t)3);      // d (each region a multiple of 16 bytes)
     __shared__ uint32_t s_rbits;
     stage_codebook(A, cbs);  // once per CTA; ends with __syncthreads
     for (int64_t q = blockIdx.x; q < A.nq; q += gridDim.x) {
-    const int P = min(probes_of(A, q), Pb);
+    // a query with more than Pb probes recomputes its tables instead of storing them
+    const int P = min(probes_of(A, q), Pm);
+    const bool stored = P <= Pb;
     for (int t = threadIdx.x; t < A.d; t += blockDim.x) qs[t] = A.Q[q * A.d + t];
     if (threadIdx.x == 0) s_rbits = 0u;
     __syncthreads();
@@ -673,7 +726,8 @@ __global__ void __launch_bounds__(256) k_lut_fused(LutArgs A, int Pb, uint8_t* _
         const int p = A.probes[q * A.Pmax + r];
         float* Tr = T + (size_t)row * (PQ_K + 1);
         if (p < 0 || p >= A.L) {
-            for (int i = 0; i < PQ_K; ++i) Tr[i] = 0.f;
+            if (stored)
+                for (int i = 0; i < PQ_K; ++i) Tr[i] = 0.f;
             mins[row] = 0.f;
             continue;
         }
@@ -684,7 +738,7 @@ __global__ void __launch_bounds__(256) k_lut_fused(LutArgs A, int Pb, uint8_t* _
         for (int i = 0; i < PQ_K; ++i) {
             mn = fminf(mn, Tv[i]);
             mx = fmaxf(mx, Tv[i]);
-            Tr[i] = Tv[i];
+            if (stored) Tr[i] = Tv[i];
         }
         mins[row] = mn;
         R = fmaxf(R, __fsub_rn(mx, mn));
@@ -697,10 +751,20 @@ __global__ void __launch_bounds__(256) k_lut_fused(LutArgs A, int Pb, uint8_t* _
     const float a = (Rq == 0.f) ? 1.f : __fdiv_rn(255.f, Rq);
     for (int row = threadIdx.x; row < P * M; row += blockDim.x) {
         const int r = row / M, j = row - r * M;
-        const float* Tr = T + (size_t)row * (PQ_K + 1);
         const float mn = mins[row];
+        float Tv[PQ_K];
+        if (stored) {
+            const float* Tr = T + (size_t)row * (PQ_K + 1);
+#pragma unroll
+            for (int i = 0; i < PQ_K; ++i) Tv[i] = Tr[i];
+        } else {
+            const int p = A.probes[q * A.Pmax + r];
+            if (p < 0 || p >= A.L) continue;
+            row_table<DS>(A.dsub, A.ip, qs + j * A.dsub, A.c_mean + (int64_t)p * A.d + j * A.dsub, cbs + j * ld,
+                          Tv);
+        }
         reinterpret_cast<uint4*>(lut + (q * A.Pmax + r) * (int64_t)M * PQ_K)[j] =
-            make_uint4(quant4(Tr, mn, a), quant4(Tr + 4, mn, a), quant4(Tr + 8, mn, a), quant4(Tr + 12, mn, a));
+            make_uint4(quant4(Tv, mn, a), quant4(Tv + 4, mn, a), quant4(Tv + 8, mn, a), quant4(Tv + 12, mn, a));
     }
     for (int r = threadIdx.x; r < P; r += blockDim.x) {
         const int p = A.probes[q * A.Pmax + r];
@@ -712,8 +776,9 @@ __global__ void __launch_bounds__(256) k_lut_fused(LutArgs A, int Pb, uint8_t* _
     }
 }
 
-static size_t lut_fused_smem(int M, int dsub, int d, int Pb) {
-    return sizeof(float) * ((size_t)M * cb_ld(dsub) + (size_t)Pb * M * (PQ_K + 1) + (size_t)Pb * M + d);
+static size_t lut_fused_smem(int M, int dsub, int d, int Pb, int Pm) {
+    return sizeof(float) * ((size_t)M * cb_ld(dsub) + (((size_t)Pb * M * (PQ_K + 1) + 3) & ~(size_t)3) +
+                            (((size_t)Pm * M + 3) & ~(size_t)3) + d);
 }
 
 // 8-byte row loads need dsub = 2 and an 8-byte aligned query matrix.
@@ -2272,8 +2337,10 @@ static int list_scores(ksc_index* ix, const float* Q, int64_t nq, bool exact, fl
     return score_err(ix, Q, nq, false, *err, st);
 }
 
+// The Pmax best lists of every query (exact ranking); feat (optional, L >=
+// FEAT_K) receives each query's FEAT_K smallest given list distances.
 static int rank_lists(ksc_index* ix, const float* Q, int64_t nq, const int32_t* nprobe_q, int Pfix, int Pmax,
-                      int32_t* probes, float* score_out, bool exact, cudaStream_t st) {
+                      int32_t* probes, float* score_out, bool exact, cudaStream_t st, float* feat = nullptr) {
     KSC_TRY(ensure(ix->ws_scores, sizeof(float) * nq * ix->L, st));
     float* scores = (float*)ix->ws_scores.p;
     float* err = nullptr;
@@ -2291,7 +2358,8 @@ static int rank_lists(ksc_index* ix, const float* Q, int64_t nq, const int32_t* 
         KSC_CUDA(cudaFuncSetAttribute(k_rank_select_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm));
         k_rank_select_w<<<(unsigned)((nq + RSW_WARPS - 1) / RSW_WARPS), RSW_WARPS * 32, wsm, st>>>(
             scores, err, Q, ix->c_rank, nq, ix->d, ix->L, ix->spherical, nprobe_q, Pfix, Pmax, probes, score_out,
-            redo);
+            redo, feat);
+        feat = nullptr;  // written
         KSC_LAUNCH_CHECK();
         k_rank_select<<<num_sms() * 2, 256, smem, st>>>(scores, err, Q, ix->c_rank, nq, ix->d, ix->L, ix->spherical,
                                                         nprobe_q, Pfix, Pmax, rs_cap, probes, score_out, redo);
@@ -2302,6 +2370,11 @@ static int rank_lists(ksc_index* ix, const float* Q, int64_t nq, const int32_t* 
         ix->launches++;
     }
     KSC_LAUNCH_CHECK();
+    if (feat) {
+        k_feat_scores<<<(unsigned)((nq + 7) / 8), 256, 0, st>>>(scores, Q, ix->d, ix->spherical, nq, ix->L, feat);
+        KSC_LAUNCH_CHECK();
+        ix->launches++;
+    }
     return KSC_OK;
 }
 
@@ -2447,15 +2520,19 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
         KSC_CUDA(cudaMemsetAsync(rb, 0, sizeof(uint32_t) * nq, st));
         LutArgs LA{Q, nq, ix->d, M, ix->dsub, ix->metric == KSC_IP, pl.Pmax, probes, pl.nprobe_q, pl.Pfix,
                    ix->c_mean, ix->codebook, ix->L, wa.pairs, wa.pair_off + L, wb.pairs, wb.pair_off + L};
-        const size_t fsm = lut_fused_smem(M, ix->dsub, ix->d, pl.Pq_max);
-        if (fsm <= 160 * 1024) {
+        // tables stored for up to Pb probes per query (per-query nprobe: 8, the
+        // rest of a larger query recomputed), so that more CTAs fit per SM
+        const int Pb = pl.nprobe_q ? std::min(pl.Pq_max, 8) : pl.Pq_max;
+        const size_t fsm = lut_fused_smem(M, ix->dsub, ix->d, Pb, pl.Pq_max);
+        // one CTA per query at a time: worth it once every SM has queries to take
+        if (fsm <= 160 * 1024 && nq >= 2 * (int64_t)num_sms()) {
             const bool ds2 = lut_ds2(LA);
             auto kf = ds2 ? k_lut_fused<2> : k_lut_fused<0>;
             KSC_CUDA(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
             int per_sm = 0;
             KSC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kf, 256, fsm));
             const int64_t grid = std::min<int64_t>(nq, (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1));
-            kf<<<(unsigned)grid, 256, fsm, st>>>(LA, pl.Pq_max, lut, bias, scale);
+            kf<<<(unsigned)grid, 256, fsm, st>>>(LA, Pb, pl.Pq_max, lut, bias, scale);
             KSC_LAUNCH_CHECK();
             ix->launches++;
         } else {
@@ -2585,6 +2662,19 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
     return KSC_OK;
 }
 
+// Tile length of the scan's warp items for an expected P probes per query:
+// about 256 items per SM (short tiles balance the persistent warps; each item
+// still amortises its set-up over 4 to 32 blocks).
+static void set_tiles(const ksc_index* ix, Plan& pl, int64_t nq, double P, const ksc_search_opts* opts) {
+    const int QG = 32 / pl.G;
+    const double blocks = std::ceil((double)nq * P / ix->L / QG) * ix->nblocks;
+    const double target = 256.0 * num_sms();
+    int TB = (int)(blocks / target);
+    pl.TB = TB < 4 ? 4 : (TB > 32 ? 32 : TB);
+    if (pl.G == 4) pl.TB = (pl.TB + S4_B - 1) / S4_B * S4_B;  // whole steps of 4 blocks
+    if (opts && opts->tile_blocks > 0) pl.TB = std::min(opts->tile_blocks, 1 << 20);
+}
+
 static int make_plan(ksc_index* ix, int64_t nq, int k, int Pmax, int Rmax, const ksc_search_opts* opts, Plan& pl) {
     KSC_CHECK_ARG(nq >= 0, "nq < 0");
     KSC_CHECK_ARG(k >= 1 && k <= KSC_MAX_K, "k must be in [1, %d]", KSC_MAX_K);
@@ -2601,18 +2691,7 @@ static int make_plan(ksc_index* ix, int64_t nq, int k, int Pmax, int Rmax, const
     pl.nprobe_q = nullptr;
     pl.rerank_q = nullptr;
     pl.G = choose_G(ix, nq, Pmax, opts ? opts->lanes_per_query : 0);
-    {
-        // tile length: about 256 warp items per SM (short tiles balance the
-        // persistent warps; each item still amortises its set-up over 4 to 32
-        // blocks)
-        const int QG = 32 / pl.G;
-        const double blocks = std::ceil((double)nq * Pmax / ix->L / QG) * ix->nblocks;
-        const double target = 256.0 * num_sms();
-        int TB = (int)(blocks / target);
-        pl.TB = TB < 4 ? 4 : (TB > 32 ? 32 : TB);
-        if (pl.G == 4) pl.TB = (pl.TB + S4_B - 1) / S4_B * S4_B;  // whole steps of 4 blocks
-        if (opts && opts->tile_blocks > 0) pl.TB = std::min(opts->tile_blocks, 1 << 20);
-    }
+    set_tiles(ix, pl, nq, Pmax, opts);
     int cap = (opts && opts->cand_cap > 0) ? opts->cand_cap : std::max(32 * Rmax, 8192);
     pl.cap = std::max(cap, Rmax);
     pl.rank_exact = opts && opts->rank_fp32;
@@ -2720,6 +2799,7 @@ int ksc_search_varprobe(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t k
     cudaStream_t st = as_stream(stream);
     pl.nprobe_q = nprobe_dev;
     pl.rerank_q = rerank_dev;
+    set_tiles(ix, pl, nq, 0.5 * pl.Pmax, opts);  // per-query nprobe: about half the largest on average
     KSC_CUDA(cudaMemsetAsync(ix->status, 0, sizeof(int32_t), st));
     KSC_TRY(ensure(ix->ws_probes, sizeof(int32_t) * nq * pl.Pmax, st));
     int32_t* probes = (int32_t*)ix->ws_probes.p;
@@ -2867,12 +2947,14 @@ static const int32_t DEF_GRID[] = {4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128};
 static const int32_t DEF_RGRID[] = {20, 50, 100, 200, 400};
 
 // Rank with P probes (P >= 32) and derive the predictor features.
+// The P best lists of every query (exact ranking) and the predictor's
+// features, from the FEAT_K smallest given list scores (L >= FEAT_K).
 static int rank_and_features(ksc_index* ix, const float* Q, int64_t nq, int P, int32_t* probes, float* feats,
                              cudaStream_t st) {
-    KSC_TRY(ensure(ix->ws_rscore, sizeof(float) * nq * P, st));
+    KSC_TRY(ensure(ix->ws_rscore, sizeof(float) * nq * FEAT_K, st));
     float* rs = (float*)ix->ws_rscore.p;
-    KSC_TRY(rank_lists(ix, Q, nq, nullptr, P, P, probes, rs, false, st));
-    KSC_TRY(mlp_features(rs, nq, P, ix->spherical, feats, st));
+    KSC_TRY(rank_lists(ix, Q, nq, nullptr, P, P, probes, nullptr, false, st, rs));
+    KSC_TRY(mlp_features(rs, nq, FEAT_K, ix->spherical, feats, st));
     ix->launches++;
     return KSC_OK;
 }
@@ -2965,8 +3047,8 @@ int ksc_query_features(ksc_index* ix, const float* Q_dev, int64_t nq, float* fea
     if (nq == 0) return KSC_OK;
     KSC_CHECK_ARG(Q_dev && feats_dev, "null argument");
     cudaStream_t st = as_stream(stream);
-    KSC_TRY(ensure(ix->ws_probes, sizeof(int32_t) * nq * 32, st));
-    return rank_and_features(ix, Q_dev, nq, 32, (int32_t*)ix->ws_probes.p, feats_dev, st);
+    KSC_TRY(ensure(ix->ws_probes, sizeof(int32_t) * nq, st));
+    return rank_and_features(ix, Q_dev, nq, 1, (int32_t*)ix->ws_probes.p, feats_dev, st);
 }
 
 int ksc_predictor_params(ksc_index* ix, const ksc_adaptive_params* prm) {
@@ -3126,7 +3208,7 @@ int ksc_search_adaptive(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t k
         return KSC_ESTATE;
     }
     const ksc_adaptive_params& prm = ix->mlp_prm;
-    const int Pr = std::min(std::max(prm.pmax, 32), ix->L);
+    const int Pr = std::min(std::max(prm.pmax, 1), ix->L);  // the lists a query may probe
     Plan pl;
     KSC_TRY(make_plan(ix, nq, k, Pr, prm.rmax, opts, pl));
     if (nq == 0) return KSC_OK;
@@ -3150,6 +3232,7 @@ int ksc_search_adaptive(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t k
     pl.nprobe_q = np_q;
     pl.rerank_q = r_q;
     pl.Pq_max = std::min(prm.pmax, Pr);
+    set_tiles(ix, pl, nq, 0.5 * (prm.pmin + prm.pmax), opts);
     KSC_TRY(search_from_probes(ix, Q_dev, pl, probes, ids_dev, dists_dev, nullptr, nullptr, st));
     if (nprobe_dev) KSC_CUDA(cudaMemcpyAsync(nprobe_dev, np_q, sizeof(int32_t) * nq, cudaMemcpyDeviceToDevice, st));
     if (rerank_dev) KSC_CUDA(cudaMemcpyAsync(rerank_dev, r_q, sizeof(int32_t) * nq, cudaMemcpyDeviceToDevice, st));
