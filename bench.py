@@ -290,58 +290,101 @@ def run_ours(args, rank, ws):
                            mean_nprobe=float(lnp.double().mean().item()), nprobe_q=lnp.cpu().numpy(),
                            params=dict(pmin=best[2], pmax=best[3], p0=best[4], p1=best[5]), train_loss=loss,
                            train_s=round(train_s, 1), val_recall=best[1], stats=ix.search_stats())
-    # headline: the faster of the two paths that reach the recall target (the
-    # plain one does by construction), the same choice on every rank
-    own = learned is not None and learned["recall"] >= TARGET_RECALL and learned["ms"] < plain_ms
-    use_learned = -max_over_ranks(-float(own), ws) > 0.5
-    if use_learned:
-        ms, stage_avg, launches, clocks = learned["ms"], learned["stage"], learned["launches"], learned["clk"]
-        stats = learned["stats"]
-    else:
-        ms, stage_avg, launches, clocks = plain_ms, plain_stage, plain_launches, plain_clk
-    ms_max = max_over_ranks(ms, ws)
+    # the same steps without per-stage events, and replayed from CUDA graphs
+    # (ksc_plan: the whole search captured once)
+    gst = torch.cuda.Stream()  # graph capture needs a stream of its own
+
+    def timed_bare(fn, s_):
+        """The same steps without per-stage events: mean ms, clocks."""
+        with torch.cuda.stream(s_):
+            for _ in range(args.warmup):
+                fn()
+            torch.cuda.synchronize()
+            ts = []
+            barrier(ws)
+            with Clocks(local) as clk:
+                for _ in range(args.steps):
+                    flush.zero_()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(s_)
+                    fn()
+                    e1.record(s_)
+                    e1.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+            barrier(ws)
+        return statistics.mean(ts), clk.summary()
+
+    # every way to run a step: direct calls, or the whole search replayed from a
+    # CUDA graph (ksc_plan); the learned path only if it reaches the target
+    variants = {"plain direct": timed_bare(lambda: ix.search(Qd, k, nprobe, R, opts=sopts, out=(ids, dists)), st)}
+    with torch.cuda.stream(gst):
+        pplan = ix.plan(CFG["nq"], k, nprobe=nprobe, rerank=R, opts=sopts)
+    variants["plain graph"] = timed_bare(lambda: pplan.execute(Qd, ids, dists), gst)
+    lplan = None
+    ok_learned = learned is not None and learned["recall"] >= TARGET_RECALL
+    if -max_over_ranks(-float(ok_learned), ws) > 0.5:  # on every rank, or on none
+        variants["learned direct"] = timed_bare(lambda: ix.search_adaptive(Qd, k), st)
+        with torch.cuda.stream(gst):
+            lplan = ix.plan(CFG["nq"], k, adaptive=True)
+        variants["learned graph"] = timed_bare(lambda: lplan.execute(Qd, ids, dists), gst)
+    torch.cuda.synchronize()
+    # headline: the fastest variant, the same choice on every rank (by the
+    # slowest rank's time of each)
+    names = sorted(variants)
+    worst = [max_over_ranks(variants[n_][0], ws) for n_ in names]
+    head = names[int(np.argmin(worst))]
+    use_learned = head.startswith("learned")
+    use_graph = head.endswith("graph")
+    ms_max = worst[names.index(head)]
+    clocks = variants[head][1]
     value = weak_value(CFG["nq"], ws, ms_max)
+    if use_learned:
+        stage_avg, launches, stats = learned["stage"], learned["launches"], learned["stats"]
+    else:
+        stage_avg, launches, stats = plain_stage, plain_launches, stats
     stage_ms = {s_: [v] for s_, v in stage_avg.items()}
-    # end to end through the public API with host buffers
+    # end to end through the same public API with host buffers
     Qpin = torch.from_numpy(Qh).pin_memory()
     ids_h = torch.empty((CFG["nq"], k), dtype=torch.int64).pin_memory()
     d_h = torch.empty((CFG["nq"], k), dtype=torch.float32).pin_memory()
     Qtmp = torch.empty_like(Qd)
     e2e_ms = []
-    for it in range(args.warmup + args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        Qtmp.copy_(Qpin, non_blocking=True)
-        if use_learned:
-            r_ids, r_d, _, _ = ix.search_adaptive(Qtmp, k)
-        else:
-            r_ids, r_d = ix.search(Qtmp, k, nprobe, R, opts=sopts, out=(ids, dists))
-        ids_h.copy_(r_ids, non_blocking=True)
-        d_h.copy_(r_d, non_blocking=True)
-        e1.record(st)
-        e1.synchronize()
-        if it >= args.warmup:
-            e2e_ms.append(e0.elapsed_time(e1))
+    es = gst if use_graph else st
+    with torch.cuda.stream(es):
+        for it in range(args.warmup + args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(es)
+            Qtmp.copy_(Qpin, non_blocking=True)
+            if use_graph:
+                r_ids, r_d = (lplan if use_learned else pplan).execute(Qtmp, ids, dists)
+            elif use_learned:
+                r_ids, r_d, _, _ = ix.search_adaptive(Qtmp, k)
+            else:
+                r_ids, r_d = ix.search(Qtmp, k, nprobe, R, opts=sopts, out=(ids, dists))
+            ids_h.copy_(r_ids, non_blocking=True)
+            d_h.copy_(r_d, non_blocking=True)
+            e1.record(es)
+            e1.synchronize()
+            if it >= args.warmup:
+                e2e_ms.append(e0.elapsed_time(e1))
     e2e = weak_value(CFG["nq"], ws, max_over_ranks(statistics.mean(e2e_ms), ws))
-    # roofline of the dominant kernel (the LUT16 scan): lookups per launch
-    pmax_r = learned["params"]["pmax"] if use_learned else nprobe
-    probes, _ = ix.rank_lists(Qd, pmax_r, want_scores=False)
+    # roofline of the dominant kernel (the LUT16 scan), taken on the plain
+    # step of this run (same kernel; its DRAM traffic was captured with ncu on
+    # that step): lookups per search
+    probes, _ = ix.rank_lists(Qd, nprobe, want_scores=False)
     sizes = np.bincount(ix.export()["assign"], minlength=CFG["nlist"]) if rank == 0 else None
     out = None
     if rank == 0:
         pr = probes.cpu().numpy()
-        if use_learned:
-            used = np.arange(pr.shape[1])[None, :] < learned["nprobe_q"][:, None]
-            pairs_vecs = int((sizes[pr] * used).sum())
-        else:
-            pairs_vecs = int(sizes[pr].sum())
+        pairs_vecs = int(sizes[pr].sum())
         lookups = pairs_vecs * CFG["M"]
         code_bytes = pairs_vecs * CFG["M"] // 2
         # the scan runs in two launches (nearest lists, then the rest); the
-        # first stage also holds the small threshold kernel
-        scan_ms = statistics.mean(stage_ms["scan"]) + statistics.mean(stage_ms["near_scan"])
+        # first stage also holds the threshold kernel between them
+        scan_ms = plain_stage["scan"] + plain_stage["near_scan"]
         peak_gl = ksc.lut16_peak()
         achieved_gl = lookups / (scan_ms * 1e-3) / 1e9
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
@@ -388,7 +431,9 @@ def run_ours(args, rank, ws):
                        "nprobe": nprobe, "recall@10": recall, "nprobe_sweep": sweep,
                        "l2": "flushed (256 MB write) before every timed step", "parallelism": "replica x%d" % ws},
             "recall@10": round(learned["recall"], 4) if use_learned else recall,
-            "path": "learned nprobe (MLP + Eq. 2)" if use_learned else "plain fixed nprobe",
+            "path": ("learned nprobe (MLP + Eq. 2)" if use_learned else "plain fixed nprobe") +
+                    (", replayed from a CUDA graph (ksc_plan)" if use_graph else ", direct calls"),
+            "variants_ms": {n_: round(w_, 4) for n_, w_ in zip(names, worst)},
             "plain": plain, "learned": lrn,
             "e2e": {"value": round(e2e, 1), "unit": "queries/s",
                     "h2d_bytes_per_step": int(Qh.nbytes), "d2h_bytes_per_step": int(ids_h.numel() * 12)},
@@ -401,7 +446,8 @@ def run_ours(args, rank, ws):
                          "lookups_per_launch": lookups,
                          # DRAM read + write of the scan's two launches per search, from the
                          # ncu capture of the plain nprobe-8 step (profiles/k_scan_*.md)
-                         "traffic": SCAN_TRAFFIC_BYTES if (not use_learned and nprobe == 8 and not sopts) else None,
+                         "traffic": SCAN_TRAFFIC_BYTES if (nprobe == 8 and not sopts) else None,
+                         "step": "plain nprobe %d search of this run" % nprobe,
                          "code_bytes_per_launch": code_bytes,
                          "effective_code_GBps": round(code_bytes / (scan_ms * 1e-3) / 1e9, 1),
                          "hbm_peak_gbs": peaks.get("hbm_gbs")},
