@@ -2,7 +2,7 @@
 
 Workload (SIFT1M-shaped synthetic stand-in): 1,000,000 x 128 non-negative
 integer vectors 0..255, 10,000 queries, nlist 1024, M 64 x 4-bit, k 10,
-rerank 200; nprobe = the smallest of the grid 8..128 whose recall@10 (ties
+rerank 200; nprobe = the smallest of the grid 4..128 whose recall@10 (ties
 counted, FP64 ground truth) reaches 0.90.  One step = one search of the
 whole 10k-query batch (rank lists, LUTs, scan, select, rerank), inputs
 resident in HBM.  L2 is flushed (256 MB write) before every timed step.
@@ -27,13 +27,13 @@ sys.path.insert(0, ROOT)
 
 CFG = dict(workload="ivfpq-sift1m-shape", n=1_000_000, d=128, nq=10_000, nlist=1024, M=64, nbits=4, k=10,
            rerank=200, metric="l2")
-GRID = (4, 6, 8, 10, 12, 16, 24, 32, 48, 64, 96, 128)
+GRID = (4, 5, 6, 7, 8, 9, 10, 12, 14, 16, 20, 24, 32, 48, 64, 96, 128)
 METRIC = "QPS at recall@10\u22650.90 (1M\u00d7128, 1 GB300) vs plain path; ADC-scan HBM GB/s vs peak"
 TARGET_RECALL = 0.90
 L2_FLUSH_BYTES = 256 << 20
-# DRAM bytes (read + write) of k_scan's two launches in one plain nprobe-8 search,
-# from ncu --set full (profiles/k_scan_ivfpq_sift1m_nq10k_nprobe8.md)
-SCAN_TRAFFIC_BYTES = 204_086_000
+# DRAM bytes (read + write) of k_scan's two launches in one plain search at the
+# given nprobe, from ncu --set full (profiles/k_scan_ivfpq_sift1m_nq10k_nprobe<P>.md)
+SCAN_TRAFFIC_BYTES = {7: 190_934_000}
 
 
 def dist_setup():
@@ -445,8 +445,8 @@ def run_ours(args, rank, ws):
                          "peak_source": "measured: ksc_lut16_peak (same instruction sequence, registers only)",
                          "lookups_per_launch": lookups,
                          # DRAM read + write of the scan's two launches per search, from the
-                         # ncu capture of the plain nprobe-8 step (profiles/k_scan_*.md)
-                         "traffic": SCAN_TRAFFIC_BYTES if (nprobe == 8 and not sopts) else None,
+                         # ncu capture of the plain step (profiles/k_scan_*.md)
+                         "traffic": None if sopts else SCAN_TRAFFIC_BYTES.get(nprobe),
                          "step": "plain nprobe %d search of this run" % nprobe,
                          "code_bytes_per_launch": code_bytes,
                          "effective_code_GBps": round(code_bytes / (scan_ms * 1e-3) / 1e9, 1),
