@@ -207,15 +207,29 @@ __device__ __forceinline__ uint64_t warp_sort_key(uint64_t v, int lane) {
 // the warp.  Keys are unique, so a range of fewer than 256 keys ends it.
 // hist: 256 words and bb: 32 keys of the warp's own shared memory.  All 32
 // lanes call.
+// Each pass reads TOPK_U keys per lane before using them, so that that many
+// loads per lane are in flight (the keys usually come from global memory).
+constexpr int TOPK_U = 8;
+
 template <class Load, class Emit>
 __device__ uint64_t warp_topk(Load load, int N, int K, Emit emit, uint32_t* hist, uint64_t* bb) {
     const int lane = threadIdx.x & 31;
     const uint32_t below = (1u << lane) - 1u;
     uint64_t lo = KEY_NONE, hi = 0ull;
-    for (int i = lane; i < N; i += 32) {
-        const uint64_t k = load(i);
-        lo = k < lo ? k : lo;
-        hi = k > hi ? k : hi;
+    for (int i0 = 0; i0 < N; i0 += 32 * TOPK_U) {
+        uint64_t k[TOPK_U];
+#pragma unroll
+        for (int u = 0; u < TOPK_U; ++u) {
+            const int i = i0 + 32 * u + lane;
+            k[u] = i < N ? load(i) : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < TOPK_U; ++u) {
+            if (i0 + 32 * u + lane < N) {
+                lo = k[u] < lo ? k[u] : lo;
+                hi = k[u] > hi ? k[u] : hi;
+            }
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -229,9 +243,17 @@ __device__ uint64_t warp_topk(Load load, int N, int K, Emit emit, uint32_t* hist
         while (((hi - lo) >> shift) >= 256ull) ++shift;
         for (int b = lane; b < 256; b += 32) hist[b] = 0u;
         __syncwarp();
-        for (int i = lane; i < N; i += 32) {
-            const uint64_t k = load(i);
-            if (k >= lo && k <= hi) atomicAdd(&hist[(uint32_t)((k - lo) >> shift)], 1u);
+        for (int i0 = 0; i0 < N; i0 += 32 * TOPK_U) {
+            uint64_t k[TOPK_U];
+#pragma unroll
+            for (int u = 0; u < TOPK_U; ++u) {
+                const int i = i0 + 32 * u + lane;
+                k[u] = i < N ? load(i) : KEY_NONE;
+            }
+#pragma unroll
+            for (int u = 0; u < TOPK_U; ++u)
+                if (i0 + 32 * u + lane < N && k[u] >= lo && k[u] <= hi)
+                    atomicAdd(&hist[(uint32_t)((k[u] - lo) >> shift)], 1u);
         }
         __syncwarp();
         uint32_t c[8], local = 0;
@@ -268,16 +290,24 @@ __device__ uint64_t warp_topk(Load load, int N, int K, Emit emit, uint32_t* hist
         const uint64_t bhi = (hi - blo < (1ull << shift)) ? hi : blo + ((1ull << shift) - 1ull);
         const bool last = inB <= 32;
         int nb = 0;
-        for (int i0 = 0; i0 < N; i0 += 32) {
-            const int i = i0 + lane;
-            const uint64_t k = i < N ? load(i) : 0ull;
-            const bool e = i < N && k >= lo && k < blo;
-            const bool g = last && i < N && k >= blo && k <= bhi;
-            const uint32_t me = __ballot_sync(0xffffffffu, e), mg = __ballot_sync(0xffffffffu, g);
-            if (e) emit(out + __popc(me & below), k);
-            if (g) bb[nb + __popc(mg & below)] = k;
-            out += __popc(me);
-            nb += __popc(mg);
+        for (int i0 = 0; i0 < N; i0 += 32 * TOPK_U) {
+            uint64_t k[TOPK_U];
+#pragma unroll
+            for (int u = 0; u < TOPK_U; ++u) {
+                const int i = i0 + 32 * u + lane;
+                k[u] = i < N ? load(i) : 0ull;
+            }
+#pragma unroll
+            for (int u = 0; u < TOPK_U; ++u) {
+                const int i = i0 + 32 * u + lane;
+                const bool e = i < N && k[u] >= lo && k[u] < blo;
+                const bool g = last && i < N && k[u] >= blo && k[u] <= bhi;
+                const uint32_t me = __ballot_sync(0xffffffffu, e), mg = __ballot_sync(0xffffffffu, g);
+                if (e) emit(out + __popc(me & below), k[u]);
+                if (g) bb[nb + __popc(mg & below)] = k[u];
+                out += __popc(me);
+                nb += __popc(mg);
+            }
         }
         need -= lt;
         if (last) {

@@ -935,7 +935,8 @@ __device__ __forceinline__ int64_t list_size(const ScanArgs& A, int p) {
 }
 
 __global__ void k_count_parts(ScanArgs A, int Rmax, int cap, int rs, int32_t* __restrict__ split,
-                              int32_t* __restrict__ cntA, int32_t* __restrict__ cntB) {
+                              int32_t* __restrict__ cntA, int32_t* __restrict__ cntB,
+                              int32_t* __restrict__ near_cnt) {
     const int lane = threadIdx.x & 31;
     const int64_t q = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
     if (q >= A.nq) return;
@@ -975,10 +976,25 @@ __global__ void k_count_parts(ScanArgs A, int Rmax, int cap, int rs, int32_t* __
         b = bnd < 1 ? 1 : bnd;
         if (lane == 0) split[q] = b;
     }
+    long long nn = 0;
     for (int r = lane; r < P; r += 32) {
         const int p = pr[r];
         if (p >= 0 && p < A.L) atomicAdd(r < b ? &cntA[p] : &cntB[p], 1);
+        if (r < b) nn += list_size(A, p);
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+    // the unfiltered scan writes every key of the first part at a fixed place
+    if (lane == 0) near_cnt[q] = (int32_t)(nn < 0x7fffffffll ? nn : 0x7fffffffll);
+}
+
+// Place of the first key of probe rank r in query q's unfiltered store: the
+// keys of its lower ranks come first.
+__device__ __forceinline__ int64_t near_offset(const ScanArgs& A, int64_t q, int r) {
+    const int32_t* pr = A.probes + q * A.Pmax;
+    int64_t off = 0;
+    for (int r2 = 0; r2 < r; ++r2) off += list_size(A, pr[r2]);
+    return off;
 }
 
 // exclusive scans: pair_off = scan(cnt); item_off = scan(ceil(cnt/QG) * ntiles)
@@ -1181,7 +1197,11 @@ struct ScanOut {
 // current one is scanned.  Group lane g of query slot s holds the sub-LUTs of
 // subspaces j = g + G*u (u < SMAX) in registers.  A key is formed only for a
 // vector whose distance reaches its query's threshold, so ids are read from
-// global memory only for those.  No CTA-wide barrier: warps run independently.
+// global memory only for those.  With no threshold (the first part of every
+// query, O.thr null) every key is kept and written straight to its fixed place
+// in the store (near_offset of its probe rank + its index in the list; the
+// count is preset by k_count_parts), its id loaded before the block's lookups.
+// No CTA-wide barrier: warps run independently.
 constexpr int SCAN_WARPS = 8;
 constexpr int SCAN_CHUNK_BYTES = 4096;           // per buffer, per warp
 constexpr int SCAN_BUF_KEYS = 128;               // kept keys buffered per (warp, query slot)
@@ -1247,7 +1267,7 @@ struct ChunkCursor {
     int c;  // chunk index within the item
 };
 
-template <int G, int SMAX>
+template <int G, int SMAX, bool DIRECT>
 __global__ void __launch_bounds__(SCAN_WARPS * 32, (SMAX <= 2 ? 3 : (SMAX <= 8 ? 2 : 1))) k_scan(ScanArgs A, ScanOut O, const int64_t* __restrict__ pair_off,
                                                           const int64_t* __restrict__ item_off,
                                                           const uint32_t* __restrict__ pairs, int L, int TB,
@@ -1263,6 +1283,7 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32, (SMAX <= 2 ? 3 : (SMAX <= 8 ?
     __shared__ int kcnt[SCAN_WARPS][QG];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int slot = lane / G, g = lane % G;
+    constexpr bool direct = DIRECT;  // no threshold (O.thr null): keys to fixed places
     if (lane < QG) kcnt[warp][lane] = 0;
     const int M = A.M;
     const int S = (M + G - 1) / G;
@@ -1306,9 +1327,11 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32, (SMAX <= 2 ? 3 : (SMAX <= 8 ?
         uint4 t[SMAX];
         int32_t bias = 0;
         uint32_t thD = 0, thI = 0;
+        int64_t noff = 0;
         if (active) {
             const uint32_t e = pairs[x.g0 + pi];
             q = e / A.Pmax;
+            if (direct) noff = near_offset(A, q, (int)(e - q * A.Pmax));
             const uint4* lp = reinterpret_cast<const uint4*>(A.lut + (int64_t)e * M * PQ_K);
 #pragma unroll
             for (int u = 0; u < SMAX; ++u) {
@@ -1331,10 +1354,18 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32, (SMAX <= 2 ? 3 : (SMAX <= 8 ?
             int base = 0;
             if (g == 0 && n > 0) base = atomicAdd(&O.cnt[q], n);
             base = __shfl_sync(0xffffffffu, base, 0, G);
-            for (int i = g; i < n; i += G) {
-                const uint64_t e = kbuf[warp][slot][i];
-                const uint32_t id = (uint32_t)A.ids[(uint32_t)e];
-                if (base + i < O.cap) O.cand[q * O.cap + base + i] = (e & 0xffffffff00000000ull) | id;
+            for (int i0 = g; i0 < n; i0 += 4 * G) {  // four id loads in flight per lane
+                uint64_t e[4];
+                uint32_t id[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) e[u] = i0 + u * G < n ? kbuf[warp][slot][i0 + u * G] : 0ull;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) id[u] = i0 + u * G < n ? (uint32_t)A.ids[(uint32_t)e[u]] : 0u;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int i = i0 + u * G;
+                    if (i < n && base + i < O.cap) O.cand[q * O.cap + base + i] = (e[u] & 0xffffffff00000000ull) | id[u];
+                }
             }
             __syncwarp();
             if (g == 0) kcnt[warp][slot] = 0;
@@ -1361,6 +1392,12 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32, (SMAX <= 2 ? 3 : (SMAX <= 8 ?
                 const int64_t gb0 = A.boff[x.p] + c0;
                 for (int blk = 0; blk < nblk; ++blk) {
                     const uint4* cp = reinterpret_cast<const uint4*>(chunk + blk * blk_bytes);
+                    const uint32_t vslot = (uint32_t)((gb0 + blk) * 32 + V * g);
+                    uint32_t idv[V];
+                    if (direct && active) {
+#pragma unroll
+                        for (int v = 0; v < V; ++v) idv[v] = (uint32_t)A.ids[vslot + v];
+                    }
                     uint32_t a32[32];
 #pragma unroll
                     for (int m = 0; m < 32; ++m) a32[m] = 0;
@@ -1380,6 +1417,19 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32, (SMAX <= 2 ? 3 : (SMAX <= 8 ?
                     for (int m = 0; m < 16; ++m) acc[m] = prmt(a32[2 * m], a32[2 * m + 1], 0x5410u);
                     uint32_t sums[V];
                     reduce_scatter<G>(acc, lane, sums);
+                    if (direct) {
+                        if (active) {
+                            const int nv = listn - (c0 + blk) * 32;
+                            const int64_t pos = noff + (int64_t)(c0 + blk) * 32 + V * g;
+                            uint64_t* out = O.cand + q * O.cap;
+#pragma unroll
+                            for (int v = 0; v < V; ++v) {
+                                const uint32_t Dk = (uint32_t)(bias + (int32_t)sums[v]) ^ 0x80000000u;
+                                if (V * g + v < nv && pos + v < O.cap) out[pos + v] = ((uint64_t)Dk << 32) | idv[v];
+                            }
+                        }
+                        continue;
+                    }
                     // keys at or below the threshold (padding, only at a list's
                     // tail, excluded by the list length); the id is needed now
                     // only on a tie with the threshold's distance
@@ -1387,7 +1437,6 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32, (SMAX <= 2 ? 3 : (SMAX <= 8 ?
                     uint32_t kmask = 0;
                     if (active) {
                         const int nv = listn - (c0 + blk) * 32;
-                        const uint32_t vslot = (uint32_t)((gb0 + blk) * 32 + V * g);
 #pragma unroll
                         for (int v = 0; v < V; ++v) {
                             // high word of the key: (D + 2^31) as an unsigned integer
@@ -1452,6 +1501,7 @@ __global__ void __launch_bounds__(S4_WARPS * 32, MAXM <= 64 ? 3 : 1)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int s = lane & 7, bo = lane >> 3;
     const int M = A.M, blk_bytes = M * 16;
+    const bool direct = O.thr == nullptr;
     uint8_t* wb = sm4 + (size_t)warp * s4_warp_bytes<MAXM>();
     uint4* tab = reinterpret_cast<uint4*>(wb);
     uint8_t* cbuf = wb + TAB_BYTES;
@@ -1493,12 +1543,13 @@ __global__ void __launch_bounds__(S4_WARPS * 32, MAXM <= 64 ? 3 : 1)
             tab[j * S4_Q + qs] = v;
         }
         const bool active = s < nslots;
-        int64_t q = 0;
+        int64_t q = 0, noff = 0;
         int32_t bias = 0, lim = -1;
         uint32_t thI = 0;
         if (active) {
             const uint32_t e = pairs[x.g0 + s];
             q = e / A.Pmax;
+            if (direct) noff = near_offset(A, q, (int)(e - q * A.Pmax));
             bias = A.bias[e];
             const uint64_t th = O.thr ? O.thr[q] : KEY_NONE;
             thI = (uint32_t)th;
@@ -1535,7 +1586,18 @@ __global__ void __launch_bounds__(S4_WARPS * 32, MAXM <= 64 ? 3 : 1)
                     int j = 0;
                     for (; j + 1 < M; j += 2) accum_pair32(cp[j], tp[j * S4_Q], cp[j + 1], tp[(j + 1) * S4_Q], acc);
                     if (j < M) accum_chunk32(cp[j], tp[j * S4_Q], acc);
-                    if (active) {
+                    if (direct && active) {
+                        // no threshold: every key of the block to its fixed place
+                        const int nv = listn - blk * 32;
+                        const int64_t pos = noff + (int64_t)blk * 32;
+                        const int32_t* idp = A.ids + (gb_list + blk) * 32;
+                        uint64_t* out = O.cand + q * O.cap;
+#pragma unroll
+                        for (int v = 0; v < 32; ++v) {
+                            const uint32_t Dk = (uint32_t)(bias + (int32_t)acc[v]) ^ 0x80000000u;
+                            if (v < nv && pos + v < O.cap) out[pos + v] = ((uint64_t)Dk << 32) | (uint32_t)idp[v];
+                        }
+                    } else if (active) {
                         const int nv = listn - blk * 32;
                         const uint32_t vmask = nv >= 32 ? 0xffffffffu : ((1u << nv) - 1u);
                         uint32_t lt = 0, eq = 0;
@@ -1554,7 +1616,8 @@ __global__ void __launch_bounds__(S4_WARPS * 32, MAXM <= 64 ? 3 : 1)
                         kmask = lt;
                     }
                 }
-                // one atomic per query and step: counts of its 4 lanes
+                // one atomic per query and step: counts of its 4 lanes (kmask
+                // stays empty with no threshold: those keys are already placed)
                 const int n = __popc(kmask);
                 const int n0 = __shfl_sync(0xffffffffu, n, s), n1 = __shfl_sync(0xffffffffu, n, s + 8);
                 const int n2 = __shfl_sync(0xffffffffu, n, s + 16), n3 = __shfl_sync(0xffffffffu, n, s + 24);
@@ -2289,11 +2352,12 @@ template <int G, int SMAX>
 static int launch_scan(const ScanArgs& A, const ScanOut& O, const int64_t* pair_off, const int64_t* item_off,
                        const uint32_t* pairs, int L, int TB, int32_t* status, cudaStream_t st) {
     const size_t smem = (size_t)SCAN_WARPS * 2 * SCAN_CHUNK_BYTES;
-    KSC_CUDA(cudaFuncSetAttribute(k_scan<G, SMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    auto kern = O.thr ? k_scan<G, SMAX, false> : k_scan<G, SMAX, true>;
+    KSC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    KSC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scan<G, SMAX>, SCAN_WARPS * 32, smem));
+    KSC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SCAN_WARPS * 32, smem));
     const int grid = num_sms() * (per_sm > 0 ? per_sm : 1);
-    k_scan<G, SMAX><<<grid, SCAN_WARPS * 32, smem, st>>>(A, O, pair_off, item_off, pairs, L, TB, status);
+    kern<<<grid, SCAN_WARPS * 32, smem, st>>>(A, O, pair_off, item_off, pairs, L, TB, status);
     KSC_LAUNCH_CHECK();
     return KSC_OK;
 }
@@ -2506,7 +2570,7 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
     // 1. work lists: the nearest list of every query, and the rest
     mark(ix, 1, st);
     KSC_CUDA(cudaMemsetAsync(wa.cnt, 0, sizeof(int32_t) * 2 * L, st));
-    k_count_parts<<<(unsigned)((nq + 7) / 8), 256, 0, st>>>(A, pl.Rmax, pl.cap, rA, split, wa.cnt, wb.cnt);
+    k_count_parts<<<(unsigned)((nq + 7) / 8), 256, 0, st>>>(A, pl.Rmax, pl.cap, rA, split, wa.cnt, wb.cnt, cnt);
     k_scan_lists<<<2, 1024, 0, st>>>(wa.cnt, ix->list_n, L, QG, pl.TB, wa.pair_off, wa.item_off, wa.fill);
     k_fill_parts<<<blocks_for(nq * pl.Pmax, 256), 256, 0, st>>>(A, rA, split, wa.pair_off, wa.fill, wa.pairs,
                                                                 wb.pair_off, wb.fill, wb.pairs);
@@ -2542,7 +2606,6 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
     }
     // 3. scan of the nearest lists with no filter, then the threshold
     mark(ix, 3, st);
-    KSC_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * nq, st));
     KSC_TRY(run_scan(pl, M, A, ScanOut{nullptr, cnt, cand, pl.cap}, wa, L, ix->status, st));
     // expected keys per query of the unfiltered scan: max(4 R, N / 16), N from
     // the mean list length; a warp per query up to SW_MAX_KEYS, else a CTA
