@@ -547,10 +547,10 @@ __device__ __forceinline__ void row_table(int dsub, int ip, const float* __restr
                 acc = __fadd_rn(acc, __fmul_rn(u1, c.y));
                 T[i] = -acc;
             } else {
+                // 0 + e0^2 is e0^2 exactly (a square is +0 or more), so the sum
+                // from 0 needs one addition
                 const float e0 = __fsub_rn(u0, c.x), e1 = __fsub_rn(u1, c.y);
-                acc = __fadd_rn(acc, __fmul_rn(e0, e0));
-                acc = __fadd_rn(acc, __fmul_rn(e1, e1));
-                T[i] = acc;
+                T[i] = __fadd_rn(__fmul_rn(e0, e0), __fmul_rn(e1, e1));
             }
         }
     } else {
@@ -577,14 +577,13 @@ __device__ __forceinline__ void row_table(int dsub, int ip, const float* __restr
 }
 
 // u8 entry min(255, floor((T - m) a + 1/2)) of four table entries, packed.
+// T >= m, so the argument of floor is positive (or NaN, which converts to 0
+// either way) and a conversion rounding down gives floor directly.
 __device__ __forceinline__ uint32_t quant4(const float* T, float mn, float a) {
-    uint32_t w = 0;
+    uint32_t v[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const float f = floorf(__fadd_rn(__fmul_rn(__fsub_rn(T[i], mn), a), 0.5f));
-        w |= (uint32_t)(f > 255.f ? 255.f : f) << (8 * i);
-    }
-    return w;
+    for (int i = 0; i < 4; ++i) v[i] = min(__float2uint_rd(__fadd_rn(__fmul_rn(__fsub_rn(T[i], mn), a), 0.5f)), 255u);
+    return __byte_perm(__byte_perm(v[0], v[1], 0x0040), __byte_perm(v[2], v[3], 0x0040), 0x5410);
 }
 
 // Integer bias floor(S a + 1/2) of one (query, list), S = sum_j m_j in
@@ -700,85 +699,138 @@ __global__ void __launch_bounds__(256) k_lut_quant(LutArgs A, const uint32_t* __
 // shared memory: the codebook is staged once per CTA; the FP32 tables of the
 // query's P_q probes are computed once, their largest range gives the scale,
 // and they are quantised from shared memory (same FP32 rule, same results as
-// the two-pass kernels above).
+// the two-pass kernels above).  Rows of 16 entries sit 20 floats apart (16-byte
+// aligned; 8 consecutive rows of a 128-bit access fall in distinct banks).  A
+// thread walks rows (r, j) = (probe rank, subspace) by a fixed step, no
+// division.  Two barriers per query: the next query's vector is loaded into
+// the other of two buffers while this one is quantised.
+constexpr int LUT_TROW = 20;
+
 template <int DS>
 __global__ void __launch_bounds__(256) k_lut_fused(LutArgs A, int Pb, int Pm, uint8_t* __restrict__ lut,
                                                    int32_t* __restrict__ bias, float* __restrict__ scale) {
-    extern __shared__ float fsm[];
+    extern __shared__ __align__(16) float fsm[];
     const int M = A.M;
     const int ld = cb_ld(A.dsub);
-    float* cbs = fsm;                                            // M x ld
-    float* T = cbs + M * ld;                                     // Pb x M rows of 16, stride 17 (no bank conflicts)
-    float* mins = T + (((size_t)Pb * M * (PQ_K + 1) + 3) & ~(size_t)3);  // Pm x M
-    float* qs = mins + (((size_t)Pm * M + 3) & ~(size_t)3);      // d (each region a multiple of 16 bytes)
-    __shared__ uint32_t s_rbits;
-    stage_codebook(A, cbs);  // once per CTA; ends with __syncthreads
-    for (int64_t q = blockIdx.x; q < A.nq; q += gridDim.x) {
-    // a query with more than Pb probes recomputes its tables instead of storing them
-    const int P = min(probes_of(A, q), Pm);
-    const bool stored = P <= Pb;
-    for (int t = threadIdx.x; t < A.d; t += blockDim.x) qs[t] = A.Q[q * A.d + t];
-    if (threadIdx.x == 0) s_rbits = 0u;
-    __syncthreads();
-    float R = 0.f;
-    for (int row = threadIdx.x; row < P * M; row += blockDim.x) {
-        const int r = row / M, j = row - r * M;
-        const int p = A.probes[q * A.Pmax + r];
-        float* Tr = T + (size_t)row * (PQ_K + 1);
-        if (p < 0 || p >= A.L) {
-            if (stored)
-                for (int i = 0; i < PQ_K; ++i) Tr[i] = 0.f;
-            mins[row] = 0.f;
-            continue;
+    const int dpad = (A.d + 3) & ~3;
+    float* cbs = fsm;                                                  // M x ld
+    float* T = cbs + (((size_t)M * ld + 3) & ~(size_t)3);              // Pb x M rows, LUT_TROW apart
+    float* mins = T + (size_t)Pb * M * LUT_TROW;                       // Pm x M
+    float* qsb = mins + (((size_t)Pm * M + 3) & ~(size_t)3);           // 2 x dpad
+    __shared__ uint32_t s_rbits[2];
+    const int r0 = threadIdx.x / M, j0 = threadIdx.x - r0 * M;         // first row of this thread
+    const int dr = blockDim.x / M, dj = blockDim.x - dr * M;           // step of blockDim.x rows
+    int64_t q = blockIdx.x;
+    if (q < A.nq)
+        for (int t = threadIdx.x; t < A.d; t += blockDim.x) qsb[t] = A.Q[q * A.d + t];
+    if (threadIdx.x == 0) s_rbits[0] = 0u;
+    stage_codebook(A, cbs);  // ends with __syncthreads
+    for (int buf = 0; q < A.nq; q += gridDim.x, buf ^= 1) {
+        const float* qs = qsb + buf * dpad;
+        // a query with more than Pb probes recomputes its tables instead of storing them
+        const int P = min(probes_of(A, q), Pm);
+        const bool stored = P <= Pb;
+        const int32_t* pr = A.probes + q * A.Pmax;
+        float R = 0.f;
+        {
+            int r = r0, j = j0;
+            for (int row = threadIdx.x; row < P * M; row += blockDim.x) {
+                const int p = pr[r];
+                float* Tr = T + (size_t)row * LUT_TROW;
+                if (p < 0 || p >= A.L) {
+                    if (stored)
+#pragma unroll
+                        for (int i = 0; i < PQ_K; i += 4) *reinterpret_cast<float4*>(Tr + i) = make_float4(0.f, 0.f, 0.f, 0.f);
+                    mins[row] = 0.f;
+                } else {
+                    float Tv[PQ_K];
+                    row_table<DS>(A.dsub, A.ip, qs + j * A.dsub, A.c_mean + (int64_t)p * A.d + j * A.dsub,
+                                  cbs + j * ld, Tv);
+                    float mn = Tv[0], mx = Tv[0];
+#pragma unroll
+                    for (int i = 1; i < PQ_K; ++i) {
+                        mn = fminf(mn, Tv[i]);
+                        mx = fmaxf(mx, Tv[i]);
+                    }
+                    if (stored)
+#pragma unroll
+                        for (int i = 0; i < PQ_K; i += 4)
+                            *reinterpret_cast<float4*>(Tr + i) = make_float4(Tv[i], Tv[i + 1], Tv[i + 2], Tv[i + 3]);
+                    mins[row] = mn;
+                    R = fmaxf(R, __fsub_rn(mx, mn));
+                }
+                j += dj;
+                r += dr;
+                if (j >= M) {
+                    j -= M;
+                    ++r;
+                }
+            }
         }
-        float Tv[PQ_K];
-        row_table<DS>(A.dsub, A.ip, qs + j * A.dsub, A.c_mean + (int64_t)p * A.d + j * A.dsub, cbs + j * ld, Tv);
-        float mn = Tv[0], mx = Tv[0];
 #pragma unroll
-        for (int i = 0; i < PQ_K; ++i) {
-            mn = fminf(mn, Tv[i]);
-            mx = fmaxf(mx, Tv[i]);
-            if (stored) Tr[i] = Tv[i];
+        for (int o = 16; o > 0; o >>= 1) R = fmaxf(R, __shfl_xor_sync(0xffffffffu, R, o));
+        if ((threadIdx.x & 31) == 0) atomicMax(&s_rbits[buf], __float_as_uint(R));
+        __syncthreads();
+        const float Rq = __uint_as_float(s_rbits[buf]);
+        const float a = (Rq == 0.f) ? 1.f : __fdiv_rn(255.f, Rq);
+        // the next query's vector into the other buffer (its last readers
+        // passed the barrier above)
+        const int64_t qn = q + gridDim.x;
+        float* qs_next = qsb + (buf ^ 1) * dpad;
+        const bool pre = qn < A.nq && threadIdx.x < A.d;
+        const float nx = pre ? A.Q[qn * A.d + threadIdx.x] : 0.f;
+        if (threadIdx.x == 0) s_rbits[buf ^ 1] = 0u;
+        {
+            int r = r0, j = j0;
+            for (int row = threadIdx.x; row < P * M; row += blockDim.x) {
+                const float mn = mins[row];
+                float Tv[PQ_K];
+                bool ok = true;
+                if (stored) {
+                    const float* Tr = T + (size_t)row * LUT_TROW;
+#pragma unroll
+                    for (int i = 0; i < PQ_K; i += 4) {
+                        const float4 v = *reinterpret_cast<const float4*>(Tr + i);
+                        Tv[i] = v.x;
+                        Tv[i + 1] = v.y;
+                        Tv[i + 2] = v.z;
+                        Tv[i + 3] = v.w;
+                    }
+                } else {
+                    const int p = pr[r];
+                    ok = p >= 0 && p < A.L;
+                    if (ok)
+                        row_table<DS>(A.dsub, A.ip, qs + j * A.dsub, A.c_mean + (int64_t)p * A.d + j * A.dsub,
+                                      cbs + j * ld, Tv);
+                }
+                if (ok)
+                    reinterpret_cast<uint4*>(lut + (q * A.Pmax + r) * (int64_t)M * PQ_K)[j] = make_uint4(
+                        quant4(Tv, mn, a), quant4(Tv + 4, mn, a), quant4(Tv + 8, mn, a), quant4(Tv + 12, mn, a));
+                j += dj;
+                r += dr;
+                if (j >= M) {
+                    j -= M;
+                    ++r;
+                }
+            }
         }
-        mins[row] = mn;
-        R = fmaxf(R, __fsub_rn(mx, mn));
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) R = fmaxf(R, __shfl_xor_sync(0xffffffffu, R, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(&s_rbits, __float_as_uint(R));
-    __syncthreads();
-    const float Rq = __uint_as_float(s_rbits);
-    const float a = (Rq == 0.f) ? 1.f : __fdiv_rn(255.f, Rq);
-    for (int row = threadIdx.x; row < P * M; row += blockDim.x) {
-        const int r = row / M, j = row - r * M;
-        const float mn = mins[row];
-        float Tv[PQ_K];
-        if (stored) {
-            const float* Tr = T + (size_t)row * (PQ_K + 1);
-#pragma unroll
-            for (int i = 0; i < PQ_K; ++i) Tv[i] = Tr[i];
-        } else {
-            const int p = A.probes[q * A.Pmax + r];
+        // biases by the last threads (those with the fewest rows above)
+        for (int r = blockDim.x - 1 - threadIdx.x; r < P; r += blockDim.x) {
+            const int p = pr[r];
             if (p < 0 || p >= A.L) continue;
-            row_table<DS>(A.dsub, A.ip, qs + j * A.dsub, A.c_mean + (int64_t)p * A.d + j * A.dsub, cbs + j * ld,
-                          Tv);
+            bias[q * A.Pmax + r] = lut_bias(A, qs, A.c_mean + (int64_t)p * A.d, mins + r * M, a);
         }
-        reinterpret_cast<uint4*>(lut + (q * A.Pmax + r) * (int64_t)M * PQ_K)[j] =
-            make_uint4(quant4(Tv, mn, a), quant4(Tv + 4, mn, a), quant4(Tv + 8, mn, a), quant4(Tv + 12, mn, a));
-    }
-    for (int r = threadIdx.x; r < P; r += blockDim.x) {
-        const int p = A.probes[q * A.Pmax + r];
-        if (p < 0 || p >= A.L) continue;
-        bias[q * A.Pmax + r] = lut_bias(A, qs, A.c_mean + (int64_t)p * A.d, mins + r * M, a);
-    }
-    if (threadIdx.x == 0) scale[q] = a;
-    __syncthreads();  // the next query reuses the shared tables
+        if (threadIdx.x == 0) scale[q] = a;
+        if (pre) qs_next[threadIdx.x] = nx;
+        if (qn < A.nq)
+            for (int t = threadIdx.x + blockDim.x; t < A.d; t += blockDim.x) qs_next[t] = A.Q[qn * A.d + t];
+        __syncthreads();  // the next query reuses the shared tables
     }
 }
 
 static size_t lut_fused_smem(int M, int dsub, int d, int Pb, int Pm) {
-    return sizeof(float) * ((size_t)M * cb_ld(dsub) + (((size_t)Pb * M * (PQ_K + 1) + 3) & ~(size_t)3) +
-                            (((size_t)Pm * M + 3) & ~(size_t)3) + d);
+    return sizeof(float) * ((((size_t)M * cb_ld(dsub) + 3) & ~(size_t)3) + (size_t)Pb * M * LUT_TROW +
+                            (((size_t)Pm * M + 3) & ~(size_t)3) + 2 * (((size_t)d + 3) & ~(size_t)3));
 }
 
 // 8-byte row loads need dsub = 2 and an 8-byte aligned query matrix.
@@ -1267,7 +1319,7 @@ struct ChunkCursor {
     int c;  // chunk index within the item
 };
 
-template <int G, int SMAX, bool DIRECT>
+template <int G, int SMAX, bool DIRECT, bool FULL>
 __global__ void __launch_bounds__(SCAN_WARPS * 32, (SMAX <= 2 ? 3 : (SMAX <= 8 ? 2 : 1))) k_scan(ScanArgs A, ScanOut O, const int64_t* __restrict__ pair_off,
                                                           const int64_t* __restrict__ item_off,
                                                           const uint32_t* __restrict__ pairs, int L, int TB,
@@ -1325,8 +1377,8 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32, (SMAX <= 2 ? 3 : (SMAX <= 8 ?
         const bool active = pi < x.npairs;
         int64_t q = 0;
         uint4 t[SMAX];
-        int32_t bias = 0;
-        uint32_t thD = 0, thI = 0;
+        int32_t bias = 0, lim = -1;
+        uint32_t thI = 0;
         int64_t noff = 0;
         if (active) {
             const uint32_t e = pairs[x.g0 + pi];
@@ -1336,12 +1388,15 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32, (SMAX <= 2 ? 3 : (SMAX <= 8 ?
 #pragma unroll
             for (int u = 0; u < SMAX; ++u) {
                 const int j = g + G * u;
-                t[u] = (u < S && j < M) ? __ldg(lp + j) : make_uint4(0, 0, 0, 0);
+                t[u] = (FULL || (u < S && j < M)) ? __ldg(lp + j) : make_uint4(0, 0, 0, 0);
             }
             bias = A.bias[e];
             const uint64_t th = O.thr ? O.thr[q] : KEY_NONE;
-            thD = (uint32_t)(th >> 32);
             thI = (uint32_t)th;
+            // key high word (bias + sum) + 2^31 vs the threshold's: sum < lim
+            // passes, sum == lim is decided by the id (sums are below 2^24)
+            const int64_t l = (int64_t)(th >> 32) - 2147483648ll - bias;
+            lim = (int32_t)(l < -1 ? -1 : (l > (1 << 24) ? (1 << 24) : l));
         } else {
 #pragma unroll
             for (int u = 0; u < SMAX; ++u) t[u] = make_uint4(0, 0, 0, 0);
@@ -1404,12 +1459,12 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32, (SMAX <= 2 ? 3 : (SMAX <= 8 ?
 #pragma unroll
                     for (int u = 0; u + 1 < SMAX; u += 2) {
                         const int j = g + G * u;
-                        if (u + 1 < S && j + G < M) accum_pair32(cp[j], t[u], cp[j + G], t[u + 1], a32);
+                        if (FULL || (u + 1 < S && j + G < M)) accum_pair32(cp[j], t[u], cp[j + G], t[u + 1], a32);
                         else if (u < S && j < M) accum_chunk32(cp[j], t[u], a32);
                     }
                     if (SMAX & 1) {
                         const int u = SMAX - 1, j = g + G * u;
-                        if (u < S && j < M) accum_chunk32(cp[j], t[u], a32);
+                        if (FULL || (u < S && j < M)) accum_chunk32(cp[j], t[u], a32);
                     }
                     // partial sums < 2^16: pack vector pairs for the reduction
                     uint32_t acc[16];
@@ -1431,32 +1486,41 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32, (SMAX <= 2 ? 3 : (SMAX <= 8 ?
                         continue;
                     }
                     // keys at or below the threshold (padding, only at a list's
-                    // tail, excluded by the list length); the id is needed now
-                    // only on a tie with the threshold's distance
-                    uint64_t keep[V];
+                    // tail, excluded by the list length); an id is read only
+                    // on a tie with the threshold's distance
                     uint32_t kmask = 0;
                     if (active) {
-                        const int nv = listn - (c0 + blk) * 32;
+                        const int nv = listn - (c0 + blk) * 32 - V * g;  // valid vectors of this lane
+                        const uint32_t vm = nv >= V ? (1u << V) - 1u : (nv > 0 ? (1u << nv) - 1u : 0u);
+                        uint32_t eq = 0;
 #pragma unroll
                         for (int v = 0; v < V; ++v) {
-                            // high word of the key: (D + 2^31) as an unsigned integer
-                            const uint32_t Dk = (uint32_t)(bias + (int32_t)sums[v]) ^ 0x80000000u;
-                            keep[v] = ((uint64_t)Dk << 32) | (vslot + v);
-                            if (V * g + v < nv &&
-                                (Dk < thD || (Dk == thD && (uint32_t)A.ids[vslot + v] <= thI)))
-                                kmask |= 1u << v;
+                            kmask |= (uint32_t)((int)sums[v] < lim) << v;
+                            eq |= (uint32_t)((int)sums[v] == lim) << v;
+                        }
+                        kmask &= vm;
+                        eq &= vm;
+                        while (eq) {
+                            const int v = __ffs(eq) - 1;
+                            eq &= eq - 1u;
+                            if ((uint32_t)A.ids[vslot + v] <= thI) kmask |= 1u << v;
                         }
                     }
                     // into the slot's buffer, which always has room for a whole
                     // block (32 keys): each lane reserves its keys with a shared
-                    // atomic; a slot left with less room is flushed
+                    // atomic; a slot left with less room is flushed.  Entry:
+                    // high word (D + 2^31) as an unsigned integer, low word the
+                    // vector's slot (the id is looked up at the flush)
                     if (__any_sync(0xffffffffu, kmask != 0u)) {
                         if (kmask) {
                             const int pos = atomicAdd(&kcnt[warp][slot], __popc(kmask));
 #pragma unroll
                             for (int v = 0; v < V; ++v)
-                                if ((kmask >> v) & 1u)
-                                    kbuf[warp][slot][pos + __popc(kmask & ((1u << v) - 1u))] = keep[v];
+                                if ((kmask >> v) & 1u) {
+                                    const uint32_t Dk = (uint32_t)(bias + (int32_t)sums[v]) ^ 0x80000000u;
+                                    kbuf[warp][slot][pos + __popc(kmask & ((1u << v) - 1u))] =
+                                        ((uint64_t)Dk << 32) | (vslot + v);
+                                }
                         }
                         __syncwarp();
                         if (__any_sync(0xffffffffu, kcnt[warp][slot] > SCAN_BUF_KEYS - 32)) flush();
@@ -2352,7 +2416,10 @@ template <int G, int SMAX>
 static int launch_scan(const ScanArgs& A, const ScanOut& O, const int64_t* pair_off, const int64_t* item_off,
                        const uint32_t* pairs, int L, int TB, int32_t* status, cudaStream_t st) {
     const size_t smem = (size_t)SCAN_WARPS * 2 * SCAN_CHUNK_BYTES;
-    auto kern = O.thr ? k_scan<G, SMAX, false> : k_scan<G, SMAX, true>;
+    // M = G SMAX: every lane has SMAX subspaces, no per-subspace guards
+    const bool full = A.M == G * SMAX;
+    auto kern = O.thr ? (full ? k_scan<G, SMAX, false, true> : k_scan<G, SMAX, false, false>)
+                      : (full ? k_scan<G, SMAX, true, true> : k_scan<G, SMAX, true, false>);
     KSC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     KSC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SCAN_WARPS * 32, smem));
