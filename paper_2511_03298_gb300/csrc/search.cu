@@ -1051,10 +1051,12 @@ __device__ __forceinline__ int64_t near_offset(const ScanArgs& A, int64_t q, int
 
 // exclusive scans: pair_off = scan(cnt); item_off = scan(ceil(cnt/QG) * ntiles)
 // Several work lists at once: CTA i scans cnt + i L into pair_off / item_off +
-// i (L + 1) and clears fill + i L.
+// i (L + 1) and clears fill + i L; the first list's tiles are TB0 blocks long,
+// the others' TB1.
 __global__ void __launch_bounds__(1024) k_scan_lists(const int32_t* __restrict__ cnt0, const int32_t* __restrict__ list_n,
-                                                     int L, int QG, int TB, int64_t* __restrict__ pair_off0,
+                                                     int L, int QG, int TB0, int TB1, int64_t* __restrict__ pair_off0,
                                                      int64_t* __restrict__ item_off0, int32_t* __restrict__ fill0) {
+    const int TB = blockIdx.x == 0 ? TB0 : TB1;  // tile length of this CTA's work list
     const int32_t* cnt = cnt0 + (size_t)blockIdx.x * L;
     int64_t* pair_off = pair_off0 + (size_t)blockIdx.x * (L + 1);
     int64_t* item_off = item_off0 + (size_t)blockIdx.x * (L + 1);
@@ -1286,7 +1288,7 @@ struct ScanItem {
 // tile.  All 32 lanes call and get the same item.
 __device__ __forceinline__ ScanItem locate_item(const ScanArgs& A, const int64_t* __restrict__ pair_off,
                                                 const int64_t* __restrict__ item_off, int L, int TB, int QG,
-                                                int64_t it) {
+                                                int64_t it, int unit = 1) {
     const int lane = threadIdx.x & 31;
     int lo = 0, hi = L - 1;  // invariant: item_off[lo] <= it < item_off[hi + 1]
     while (lo < hi) {
@@ -1305,8 +1307,11 @@ __device__ __forceinline__ ScanItem locate_item(const ScanArgs& A, const int64_t
     const int64_t local = it - item_off[lo];
     const int64_t grp = local / nt;
     const int tile = (int)(local - grp * nt);
-    r.b0 = tile * TB;
-    r.b1 = min(nb, r.b0 + TB);
+    // the list's nt tiles of near-equal length in whole units (no tile is
+    // empty: there are at least nt units)
+    const int nu = (nb + unit - 1) / unit;
+    r.b0 = (int)((int64_t)tile * nu / nt) * unit;
+    r.b1 = min(nb, (int)((int64_t)(tile + 1) * nu / nt) * unit);
     r.g0 = pair_off[lo] + grp * QG;
     r.npairs = pair_off[lo + 1] - r.g0;
     return r;
@@ -1592,7 +1597,7 @@ __global__ void __launch_bounds__(S4_WARPS * 32, MAXM <= 64 ? 3 : 1)
     const int64_t stride = (int64_t)gridDim.x * S4_WARPS;
     int64_t it = (int64_t)blockIdx.x * S4_WARPS + warp;
     if (it >= total) return;
-    ScanItem x = locate_item(A, pair_off, item_off, L, TB, S4_Q, it), nx = x;
+    ScanItem x = locate_item(A, pair_off, item_off, L, TB, S4_Q, it, S4_B), nx = x;
     if (lane == 0) issue(x, 0, 0);
     uint32_t phase[2] = {0u, 0u};
     int b = 0;
@@ -1627,7 +1632,7 @@ __global__ void __launch_bounds__(S4_WARPS * 32, MAXM <= 64 ? 3 : 1)
         const int nch = (x.b1 - x.b0 + S4_B - 1) / S4_B;
         const int64_t next_it = it + stride;
         for (int c = 0; c < nch; ++c) {
-            if (c + 1 == nch && next_it < total) nx = locate_item(A, pair_off, item_off, L, TB, S4_Q, next_it);
+            if (c + 1 == nch && next_it < total) nx = locate_item(A, pair_off, item_off, L, TB, S4_Q, next_it, S4_B);
             if (lane == 0) {
                 if (c + 1 < nch) issue(x, c + 1, b ^ 1);
                 else if (next_it < total) issue(nx, 0, b ^ 1);
@@ -2391,7 +2396,7 @@ struct Plan {
     int k, Pmax, Rmax, Pfix, Rfix;
     const int32_t* nprobe_q;
     const int32_t* rerank_q;
-    int G, TB, cap;
+    int G, TB, TBa, cap;  // TB: tile blocks of the filtered scan, TBa: of the unfiltered first part
     bool rank_exact;
     bool hybrid;
     int n_near, efs, tau;
@@ -2569,20 +2574,21 @@ struct WorkList {
     int32_t* cnt;       // [L]
     int32_t* fill;      // [L]
     uint32_t* pairs;    // [<= nq * Pmax]
+    int TB;             // blocks per item tile
 };
 
 static int run_scan(const Plan& pl, int M, const ScanArgs& A, const ScanOut& O, const WorkList& w, int L,
                     int32_t* status, cudaStream_t st) {
     const int S = (M + pl.G - 1) / pl.G;
     if (pl.G == 4) {
-        if (M <= 64) return launch_scan4<64>(A, O, w.pair_off, w.item_off, w.pairs, L, pl.TB, status, st);
-        if (M <= 128) return launch_scan4<128>(A, O, w.pair_off, w.item_off, w.pairs, L, pl.TB, status, st);
+        if (M <= 64) return launch_scan4<64>(A, O, w.pair_off, w.item_off, w.pairs, L, w.TB, status, st);
+        if (M <= 128) return launch_scan4<128>(A, O, w.pair_off, w.item_off, w.pairs, L, w.TB, status, st);
         set_error("M too large for 4 lanes per query");
         return KSC_EINVAL;
     }
-    if (pl.G == 8) return dispatch_scan<8>(S, A, O, w.pair_off, w.item_off, w.pairs, L, pl.TB, status, st);
-    if (pl.G == 16) return dispatch_scan<16>(S, A, O, w.pair_off, w.item_off, w.pairs, L, pl.TB, status, st);
-    return dispatch_scan<32>(S, A, O, w.pair_off, w.item_off, w.pairs, L, pl.TB, status, st);
+    if (pl.G == 8) return dispatch_scan<8>(S, A, O, w.pair_off, w.item_off, w.pairs, L, w.TB, status, st);
+    if (pl.G == 16) return dispatch_scan<16>(S, A, O, w.pair_off, w.item_off, w.pairs, L, w.TB, status, st);
+    return dispatch_scan<32>(S, A, O, w.pair_off, w.item_off, w.pairs, L, w.TB, status, st);
 }
 
 // a2 .. a6 for given probe lists.  Stages: 1 work lists, 2 LUTs, 3 scan of
@@ -2638,7 +2644,9 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
     mark(ix, 1, st);
     KSC_CUDA(cudaMemsetAsync(wa.cnt, 0, sizeof(int32_t) * 2 * L, st));
     k_count_parts<<<(unsigned)((nq + 7) / 8), 256, 0, st>>>(A, pl.Rmax, pl.cap, rA, split, wa.cnt, wb.cnt, cnt);
-    k_scan_lists<<<2, 1024, 0, st>>>(wa.cnt, ix->list_n, L, QG, pl.TB, wa.pair_off, wa.item_off, wa.fill);
+    wa.TB = pl.TBa;
+    wb.TB = pl.TB;
+    k_scan_lists<<<2, 1024, 0, st>>>(wa.cnt, ix->list_n, L, QG, wa.TB, wb.TB, wa.pair_off, wa.item_off, wa.fill);
     k_fill_parts<<<blocks_for(nq * pl.Pmax, 256), 256, 0, st>>>(A, rA, split, wa.pair_off, wa.fill, wa.pairs,
                                                                 wb.pair_off, wb.fill, wb.pairs);
     KSC_LAUNCH_CHECK();
@@ -2714,7 +2722,7 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
         KSC_CUDA(cudaMemsetAsync(wb.cnt, 0, sizeof(int32_t) * L, st));
         const int64_t nmax = nq * pl.Pmax;
         k_count_from<<<blocks_for(nmax, 256), 256, 0, st>>>(full, nfull, probes, wb.cnt);
-        k_scan_lists<<<1, 1024, 0, st>>>(wb.cnt, ix->list_n, L, QG, pl.TB, wb.pair_off, wb.item_off, wb.fill);
+        k_scan_lists<<<1, 1024, 0, st>>>(wb.cnt, ix->list_n, L, QG, wb.TB, wb.TB, wb.pair_off, wb.item_off, wb.fill);
         k_fill_from<<<blocks_for(nmax, 256), 256, 0, st>>>(full, nfull, probes, wb.pair_off, wb.fill, wb.pairs);
         KSC_LAUNCH_CHECK();
         ix->launches += 4;
@@ -2792,17 +2800,29 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
     return KSC_OK;
 }
 
-// Tile length of the scan's warp items for an expected P probes per query:
-// about 256 items per SM (short tiles balance the persistent warps; each item
-// still amortises its set-up over 4 to 32 blocks).
+// Tile lengths of the scan's warp items for an expected P probes per query.
+// Short tiles balance the persistent warps, long ones amortise an item's
+// set-up: about 220 items per SM for the filtered scan, and for the smaller
+// unfiltered first part (its share from the split rule of k_count_parts:
+// max(4 R, N / 16) keys, rounded up to whole lists) about 120, each within
+// 4 to 32 blocks (on the 1M x 128 workload at nprobe 7: tiles of 14 and 6
+// blocks; filtered tiles of 12 to 17 blocks ran within 1% of each other).
 static void set_tiles(const ksc_index* ix, Plan& pl, int64_t nq, double P, const ksc_search_opts* opts) {
     const int QG = 32 / pl.G;
+    const double nbar = (double)ix->n / ix->L;
     const double blocks = std::ceil((double)nq * P / ix->L / QG) * ix->nblocks;
-    const double target = 256.0 * num_sms();
-    int TB = (int)(blocks / target);
-    pl.TB = TB < 4 ? 4 : (TB > 32 ? 32 : TB);
-    if (pl.G == 4) pl.TB = (pl.TB + S4_B - 1) / S4_B * S4_B;  // whole steps of 4 blocks
-    if (opts && opts->tile_blocks > 0) pl.TB = std::min(opts->tile_blocks, 1 << 20);
+    const double keys = std::max(P * nbar, 1.0);
+    const double near =
+        std::min(1.0, (std::max((double)NEAR_KEYS_PER_R * pl.Rmax, keys / NEAR_SHARE_DIV) + 0.5 * nbar) / keys);
+    auto tile = [&](double b, double per_sm) {
+        int t = (int)(b / (per_sm * num_sms()));
+        t = t < 4 ? 4 : (t > 32 ? 32 : t);
+        if (pl.G == 4) t = (t + S4_B - 1) / S4_B * S4_B;  // whole steps of 4 blocks
+        return t;
+    };
+    pl.TB = tile(blocks * (1.0 - near), 220.0);
+    pl.TBa = tile(blocks * near, 120.0);
+    if (opts && opts->tile_blocks > 0) pl.TB = pl.TBa = std::min(opts->tile_blocks, 1 << 20);
 }
 
 static int make_plan(ksc_index* ix, int64_t nq, int k, int Pmax, int Rmax, const ksc_search_opts* opts, Plan& pl) {
