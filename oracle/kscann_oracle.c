@@ -767,3 +767,197 @@ int orc_adam_step(double* w, const double* g, double* m, double* v, int64_t np, 
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Predictive cluster pruning (Sec. 4.2.3, Table 4; Alg. 2 f_prune)    */
+/* ------------------------------------------------------------------ */
+/*
+ * Per-list statistics of the members' offsets r_x = x - c_p from the list's
+ * mean centroid (FP64), PRUNE_NSTAT values per list:
+ *   0 n_p, 1 radius rho = max |r_x|, 2 mean mu of |r_x|, 3 population std
+ *   sigma of |r_x| (two passes), 4..7 the distance histogram: fractions of
+ *   members with |r_x| in [0, rho/4], (rho/4, rho/2], (rho/2, 3rho/4],
+ *   (3rho/4, rho], 8 outlier fraction (|r_x| > mu + 2 sigma), 9, 10 the
+ *   variances lambda_1, lambda_2 along the two principal axes, 11 zero.
+ * Vectors per list (3 x d): the principal axes v_1, v_2 of the offsets'
+ * second moment (1/n_p) sum r_x r_x^T by `iters` power iterations each
+ * (v_1 from (1,..,1)/sqrt(d); v_2 from (+1,-1,+1,..)/sqrt(d), with v_1
+ * projected out of the start and of every iterate), and the outlier
+ * direction, the mean offset of the outliers (zero when there are none).
+ * An empty list has all zeros.
+ */
+#define PRUNE_NSTAT 12
+#define PRUNE_NFEAT 16
+
+static void unit_or_keep(double* v, const double* w, int32_t d) {
+    double nn = 0.0;
+    for (int t = 0; t < d; ++t) nn += w[t] * w[t];
+    if (nn > 0.0) { double s = 1.0 / sqrt(nn); for (int t = 0; t < d; ++t) v[t] = w[t] * s; }
+}
+
+int orc_prune_stats(const float* X, int64_t n, int32_t d, const float* c_mean, int32_t L,
+                    const int32_t* assign, int32_t iters, double* stats, double* vecs) {
+    memset(stats, 0, sizeof(double) * (size_t)L * PRUNE_NSTAT);
+    memset(vecs, 0, sizeof(double) * (size_t)L * 3 * d);
+    int64_t* cnt = (int64_t*)calloc((size_t)L + 1, sizeof(int64_t));
+    for (int64_t i = 0; i < n; ++i) cnt[assign[i] + 1]++;
+    for (int32_t p = 0; p < L; ++p) cnt[p + 1] += cnt[p];
+    int64_t* mem = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int64_t* fill = (int64_t*)calloc((size_t)L, sizeof(int64_t));
+    for (int64_t i = 0; i < n; ++i) { int32_t p = assign[i]; mem[cnt[p] + fill[p]++] = i; }
+#pragma omp parallel for schedule(dynamic)
+    for (int32_t p = 0; p < L; ++p) {
+        const int64_t np_ = cnt[p + 1] - cnt[p];
+        if (np_ == 0) continue;
+        const int64_t* ids = mem + cnt[p];
+        const float* c = c_mean + (int64_t)p * d;
+        double* r = (double*)malloc(sizeof(double) * (size_t)np_ * d);
+        double* dist = (double*)malloc(sizeof(double) * (size_t)np_);
+        for (int64_t m = 0; m < np_; ++m) {
+            double s = 0.0;
+            for (int t = 0; t < d; ++t) {
+                double e = (double)X[ids[m] * d + t] - (double)c[t];
+                r[m * d + t] = e;
+                s += e * e;
+            }
+            dist[m] = sqrt(s);
+        }
+        double rho = 0.0, mu = 0.0, var = 0.0;
+        for (int64_t m = 0; m < np_; ++m) { if (dist[m] > rho) rho = dist[m]; mu += dist[m]; }
+        mu /= (double)np_;
+        for (int64_t m = 0; m < np_; ++m) var += (dist[m] - mu) * (dist[m] - mu);
+        const double sigma = sqrt(var / (double)np_);
+        int64_t hist[4] = {0, 0, 0, 0}, nout = 0;
+        double* st = stats + (int64_t)p * PRUNE_NSTAT;
+        double* v1 = vecs + (int64_t)p * 3 * d;
+        double* v2 = v1 + d;
+        double* od = v2 + d;
+        for (int64_t m = 0; m < np_; ++m) {
+            int b = 0;
+            if (dist[m] > 0.75 * rho) b = 3;
+            else if (dist[m] > 0.5 * rho) b = 2;
+            else if (dist[m] > 0.25 * rho) b = 1;
+            hist[b]++;
+            if (dist[m] > mu + 2.0 * sigma) {
+                nout++;
+                for (int t = 0; t < d; ++t) od[t] += r[m * d + t];
+            }
+        }
+        if (nout > 0) for (int t = 0; t < d; ++t) od[t] /= (double)nout;
+        /* power iterations */
+        double* w = (double*)malloc(sizeof(double) * d);
+        for (int t = 0; t < d; ++t) v1[t] = 1.0 / sqrt((double)d);
+        for (int it = 0; it < iters; ++it) {
+            for (int t = 0; t < d; ++t) w[t] = 0.0;
+            for (int64_t m = 0; m < np_; ++m) {
+                double a = 0.0;
+                for (int t = 0; t < d; ++t) a += r[m * d + t] * v1[t];
+                for (int t = 0; t < d; ++t) w[t] += a * r[m * d + t];
+            }
+            unit_or_keep(v1, w, d);
+        }
+        for (int t = 0; t < d; ++t) w[t] = ((t & 1) ? -1.0 : 1.0) / sqrt((double)d);
+        {
+            double a = 0.0;
+            for (int t = 0; t < d; ++t) a += w[t] * v1[t];
+            for (int t = 0; t < d; ++t) w[t] -= a * v1[t];
+            unit_or_keep(v2, w, d);
+        }
+        for (int it = 0; it < iters; ++it) {
+            for (int t = 0; t < d; ++t) w[t] = 0.0;
+            for (int64_t m = 0; m < np_; ++m) {
+                double a = 0.0;
+                for (int t = 0; t < d; ++t) a += r[m * d + t] * v2[t];
+                for (int t = 0; t < d; ++t) w[t] += a * r[m * d + t];
+            }
+            double a = 0.0;
+            for (int t = 0; t < d; ++t) a += w[t] * v1[t];
+            for (int t = 0; t < d; ++t) w[t] -= a * v1[t];
+            unit_or_keep(v2, w, d);
+        }
+        double l1 = 0.0, l2 = 0.0;
+        for (int64_t m = 0; m < np_; ++m) {
+            double a1 = 0.0, a2 = 0.0;
+            for (int t = 0; t < d; ++t) { a1 += r[m * d + t] * v1[t]; a2 += r[m * d + t] * v2[t]; }
+            l1 += a1 * a1;
+            l2 += a2 * a2;
+        }
+        st[0] = (double)np_;
+        st[1] = rho;
+        st[2] = mu;
+        st[3] = sigma;
+        for (int b = 0; b < 4; ++b) st[4 + b] = (double)hist[b] / (double)np_;
+        st[8] = (double)nout / (double)np_;
+        st[9] = l1 / (double)np_;
+        st[10] = l2 / (double)np_;
+        free(w); free(r); free(dist);
+    }
+    free(cnt); free(mem); free(fill);
+    return 0;
+}
+
+/*
+ * Features of (query q, probe rank r < P_q), PRUNE_NFEAT values, FP64, from
+ * the list statistics above.  p = probes[r], c = its mean centroid,
+ * D = |q - c|, u = (q - c) / max(D, 1e-9), D0 = |q - c_{probes[0]}| and
+ * g = max(D0, 1e-9) (distances relative to the nearest probe's):
+ *   0 D / max(rho, 1e-9)    1 D / g       2 (D - rho) / g   3 log(1 + n_p)
+ *   4 rho / g   5 mu / g   6 sigma / g   7..10 the histogram   11 outliers
+ *   12 lambda_1 <v_1, u>^2 / g^2   13 lambda_2 <v_2, u>^2 / g^2
+ *   14 <outlier direction, u> / g   15 D0 / max(rho of probes[0], 1e-9).
+ * Rows r >= P_q and invalid list ids are zero.
+ */
+int orc_prune_features(const float* Q, int64_t nq, int32_t d, const float* c_mean, int32_t L,
+                       const int32_t* probes, int32_t Pmax, const int32_t* nprobe, int32_t P,
+                       const double* stats, const double* vecs, double* feats) {
+    memset(feats, 0, sizeof(double) * (size_t)nq * Pmax * PRUNE_NFEAT);
+#pragma omp parallel for schedule(static)
+    for (int64_t q = 0; q < nq; ++q) {
+        int32_t Pq = nprobe ? nprobe[q] : P;
+        if (Pq < 1) Pq = 1;
+        if (Pq > Pmax) Pq = Pmax;
+        const float* qv = Q + q * d;
+        const int32_t* pr = probes + q * Pmax;
+        double D0 = 0.0, rho0 = 0.0;
+        if (pr[0] >= 0 && pr[0] < L) {
+            for (int t = 0; t < d; ++t) { double e = (double)qv[t] - c_mean[(int64_t)pr[0] * d + t]; D0 += e * e; }
+            D0 = sqrt(D0);
+            rho0 = stats[(int64_t)pr[0] * PRUNE_NSTAT + 1];
+        }
+        const double g = D0 > 1e-9 ? D0 : 1e-9;
+        for (int32_t r = 0; r < Pq; ++r) {
+            const int32_t p = pr[r];
+            if (p < 0 || p >= L) continue;
+            const double* st = stats + (int64_t)p * PRUNE_NSTAT;
+            const double* v1 = vecs + (int64_t)p * 3 * d;
+            const double* v2 = v1 + d;
+            const double* od = v2 + d;
+            double D = 0.0;
+            for (int t = 0; t < d; ++t) { double e = (double)qv[t] - c_mean[(int64_t)p * d + t]; D += e * e; }
+            D = sqrt(D);
+            const double Dg = D > 1e-9 ? D : 1e-9;
+            double a1 = 0.0, a2 = 0.0, ao = 0.0;
+            for (int t = 0; t < d; ++t) {
+                double u = ((double)qv[t] - c_mean[(int64_t)p * d + t]) / Dg;
+                a1 += v1[t] * u;
+                a2 += v2[t] * u;
+                ao += od[t] * u;
+            }
+            double* f = feats + (q * Pmax + r) * PRUNE_NFEAT;
+            f[0] = D / (st[1] > 1e-9 ? st[1] : 1e-9);
+            f[1] = D / g;
+            f[2] = (D - st[1]) / g;
+            f[3] = log(1.0 + st[0]);
+            f[4] = st[1] / g;
+            f[5] = st[2] / g;
+            f[6] = st[3] / g;
+            for (int b = 0; b < 4; ++b) f[7 + b] = st[4 + b];
+            f[11] = st[8];
+            f[12] = st[9] * a1 * a1 / (g * g);
+            f[13] = st[10] * a2 * a2 / (g * g);
+            f[14] = ao / g;
+            f[15] = D0 / (rho0 > 1e-9 ? rho0 : 1e-9);
+        }
+    }
+    return 0;
+}

@@ -19,6 +19,7 @@ tests/test_oracle_pins.py):
   recall        Sec. 5.4 Recall@10                                 pinned
   eq2           Eq. 2                                              pinned
   mlp_*         Sec. 4.2.1-4.2.2 predictor (MLP stand-in)          pinned
+  prune_*       Sec. 4.2.3 / Table 4 cluster pruning, Alg. 2       pinned
 """
 import ctypes as C
 import os
@@ -44,7 +45,7 @@ K = 16
 def lib():
     global _lib
     if _lib is None:
-        path = LIB if os.path.exists(LIB) else build()
+        path = build()  # compiles only when the source is newer than the library
         L = C.CDLL(path)
         sig = {
             "orc_kmeans": (C.c_int, [_f32p, _i64, _i32, _i32, _i64p, _i64, _i32, _i32, _f64p, _vp]),
@@ -74,6 +75,9 @@ def lib():
             "orc_mlp_forward": (C.c_int, [_f64p, _i32, _i32, _i32, _f64p, _i64, _f64p]),
             "orc_mlp_grad": (C.c_double, [_f64p, _i32, _i32, _i32, _f64p, _f64p, _i64, _f64p]),
             "orc_adam_step": (C.c_int, [_f64p, _f64p, _f64p, _f64p, _i64, _i32, _f64, _f64, _f64, _f64]),
+            "orc_prune_stats": (C.c_int, [_f32p, _i64, _i32, _f32p, _i32, _i32p, _i32, _f64p, _f64p]),
+            "orc_prune_features": (C.c_int, [_f32p, _i64, _i32, _f32p, _i32, _i32p, _i32, _vp, _i32,
+                                             _f64p, _f64p, _f64p]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -299,3 +303,76 @@ def mlp_grad(w, F, H1, H2, x, y):
 def adam_step(w, g, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
     """In place on w, m, v (float64 arrays)."""
     lib().orc_adam_step(w, _c(g, np.float64), m, v, len(w), t, lr, beta1, beta2, eps)
+
+
+# -------------------------------------------------------------- cluster pruning
+PRUNE_NSTAT, PRUNE_NFEAT = 12, 16
+PRUNE_H = 32  # hidden units of the pruning classifier (F -> 32 -> 32 -> 2, head 0 used)
+
+
+def prune_stats(X, c_mean, assign, iters=30):
+    """Per-list statistics [L x 12] and vectors [L x 3 x d] (Sec. 4.2.3, Table 4):
+    size, radius, mean / std of the member distances to the mean centroid, the
+    distance histogram (4 bins over [0, radius]), the outlier fraction (beyond
+    mean + 2 std), the variances along the two principal axes; the axes and the
+    mean outlier offset."""
+    X = _c(X, np.float32)
+    c_mean = _c(c_mean, np.float32)
+    L, d = c_mean.shape
+    st = np.zeros((L, PRUNE_NSTAT), np.float64)
+    vec = np.zeros((L, 3, d), np.float64)
+    lib().orc_prune_stats(X, X.shape[0], d, c_mean, L, _c(assign, np.int32), int(iters), st, vec)
+    return st, vec
+
+
+def prune_features(Q, c_mean, probes, stats, vecs, P=None, nprobe=None):
+    """Features [nq x Pmax x 16] of every (query, probe rank < P_q) (Table 4)."""
+    Q = _c(Q, np.float32)
+    probes = _c(probes, np.int32)
+    nq, Pmax = probes.shape
+    c_mean = _c(c_mean, np.float32)
+    npb = None if nprobe is None else _c(nprobe, np.int32)
+    out = np.zeros((nq, Pmax, PRUNE_NFEAT), np.float64)
+    lib().orc_prune_features(Q, nq, Q.shape[1], c_mean, c_mean.shape[0], probes, Pmax, _ptr(npb),
+                             int(P if P is not None else Pmax), _c(stats, np.float64), _c(vecs, np.float64), out)
+    return out
+
+
+def prune_prob(feats, mu, sd, w):
+    """Keep probability of every row: the classifier's head 0 on the
+    standardised features (f - mu) / sd (Alg. 2 f_prune)."""
+    F = feats.shape[-1]
+    x = (np.asarray(feats, np.float64).reshape(-1, F) - mu) / sd
+    return mlp_forward(w, F, PRUNE_H, PRUNE_H, x)[:, 0].reshape(feats.shape[:-1])
+
+
+def prune_keep(prob, theta, P=None, nprobe=None):
+    """Alg. 2: a probe is searched when f_prune > theta; the nearest probe
+    (rank 0) is always searched.  Returns the kept probe ranks per query."""
+    nq, Pmax = prob.shape
+    out = []
+    for q in range(nq):
+        Pq = int(nprobe[q]) if nprobe is not None else int(P if P is not None else Pmax)
+        Pq = min(max(Pq, 1), Pmax)
+        out.append([r for r in range(Pq) if r == 0 or prob[q, r] > theta])
+    return out
+
+
+def prune_labels(ids, dists, kth, assign, probes, P, ip=False, tol=1e-5):
+    """Training label of (query, probe rank): 1 when the list holds one of the
+    query's true k nearest neighbours that the search returned (distance at
+    most the true k-th, up to tol relative)."""
+    nq, Pmax = probes.shape
+    y = np.zeros((nq, Pmax), np.float64)
+    for q in range(nq):
+        t = kth[q]
+        tl = tol * abs(t) + 1e-6
+        lists = set()
+        for i, dv in zip(ids[q], dists[q]):
+            if i < 0:
+                continue
+            if (dv >= t - tl) if ip else (dv <= t + tl):
+                lists.add(int(assign[i]))
+        for r in range(min(P, Pmax)):
+            y[q, r] = 1.0 if int(probes[q, r]) in lists else 0.0
+    return y
