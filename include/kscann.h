@@ -296,6 +296,99 @@ int ksc_mlp_grad(const float* w_dev, const float* x_dev, const float* y_dev, int
 /* BF16 inference alone: prob_dev [B x 2]. */
 int ksc_mlp_forward(const float* w_dev, const float* x_dev, int64_t B, float* prob_dev, void* stream);
 
+/* ------------------------------------------------------------------ */
+/* Predictive cluster pruning (Sec. 4.2.3, Table 4; Alg. 2 f_prune)    */
+/* ------------------------------------------------------------------ */
+/* A classifier per (query, probed list) predicts whether the list holds one
+ * of the query's true nearest neighbours; Alg. 2 searches a list only when
+ * f_prune > theta.  Here the nearest probe (rank 0) is always searched and
+ * the others are dropped before the work lists are built, so the scan runs
+ * unchanged on the shorter per-query probe lists (no divergence in it).
+ *
+ * Per-list statistics (build time, KSC_PRUNE_STATS floats per list) of the
+ * members' offsets r = x - c from the list's mean centroid: 0 size n,
+ * 1 radius rho = max |r|, 2 mean mu and 3 population std sigma of |r|,
+ * 4..7 the distance histogram (fractions in [0, rho/4], (rho/4, rho/2],
+ * (rho/2, 3 rho/4], (3 rho/4, rho]), 8 the outlier fraction (|r| > mu + 2
+ * sigma), 9, 10 the variances along the two principal axes, 11 zero; and
+ * 3 vectors of d floats per list: the principal axes v1, v2 of the
+ * offsets' second moment (30 power iterations each, v1 from (1,..,1),
+ * v2 from (+1,-1,+1,..) with v1 projected out) and the mean outlier offset.
+ *
+ * Features of (q, rank r) (KSC_PRUNE_FEATURES floats), with p the list,
+ * D = |q - c_p|, u = (q - c_p) / D, D0 = |q - c_{rank 0}|, g = max(D0, 1e-9):
+ * D / rho, D / g, (D - rho) / g, log(1 + n), rho / g, mu / g, sigma / g,
+ * the 4 histogram fractions, the outlier fraction, lambda1 <v1, u>^2 / g^2,
+ * lambda2 <v2, u>^2 / g^2, <outlier offset, u> / g, D0 / rho_{rank 0}.
+ *
+ * Model (KSC_PRUNE_MODEL floats): MLP weights W1[32x16], b1, W2[32x32], b2,
+ * W3[2x32], b3 (KSC_PRUNE_NPARAMS; ReLU, sigmoid; head 0 is the keep
+ * probability), then the per-feature means and standard deviations that
+ * standardise the features before the MLP.  FP32 inference. */
+#define KSC_PRUNE_STATS 12
+#define KSC_PRUNE_FEATURES 16
+#define KSC_PRUNE_NPARAMS 1666
+#define KSC_PRUNE_MODEL (KSC_PRUNE_NPARAMS + 2 * KSC_PRUNE_FEATURES)
+
+/* Compute the per-list statistics of this index (iters power iterations per
+ * axis, <= 0: 30).  Done by ksc_train_pruner when missing.  d <= 1024. */
+int ksc_pruner_stats(ksc_index* ix, int32_t iters, void* stream);
+
+/* Copy out the statistics stats_host [L x KSC_PRUNE_STATS], the vectors
+ * vecs_host [L x 3 x d] and the model model_host [KSC_PRUNE_MODEL] (host
+ * buffers, each may be NULL).  Blocking.  KSC_ESTATE when a requested part
+ * has not been computed or trained. */
+int ksc_pruner_export(ksc_index* ix, float* stats_host, float* vecs_host, float* model_host);
+
+/* Set the model from model_host [KSC_PRUNE_MODEL] (host).  Blocking. */
+int ksc_pruner_import_model(ksc_index* ix, const float* model_host);
+
+/* Features, keep probabilities and pruned probe lists for given probes.
+ * probes_dev [nq x Pmax] list ids by rank (device); the query's probes are
+ * the first nprobe_dev[q] (device, may be NULL: P for every query).  Outputs
+ * (device, each may be NULL): feats_dev [nq x Pmax x KSC_PRUNE_FEATURES]
+ * (rows at rank >= the query's nprobe are zero), prob_dev [nq x Pmax] (keep
+ * probability; needs a model), probes_out_dev [nq x Pmax] the kept probes in
+ * rank order then -1, nprobe_out_dev [nq] their number (rank 0 and every
+ * rank with probability > theta; needs a model).  Needs the statistics
+ * (KSC_ESTATE otherwise). */
+int ksc_prune_probes(ksc_index* ix, const float* Q_dev, int64_t nq, const int32_t* probes_dev, int32_t Pmax,
+                     const int32_t* nprobe_dev, int32_t P, float theta, float* feats_dev, float* prob_dev,
+                     int32_t* probes_out_dev, int32_t* nprobe_out_dev, void* stream);
+
+/* Training labels: label_dev [nq x Pmax] = 1 where the list probes_dev[q][r]
+ * (r < P) holds one of the returned ids_dev [nq x k] whose distance
+ * dists_dev [nq x k] is within the true k-th kth_dev [nq] (L2: at most it,
+ * IP: at least it, both up to 1e-5 relative + 1e-6), else 0 (device). */
+int ksc_prune_labels(ksc_index* ix, const int64_t* ids_dev, const float* dists_dev, int64_t nq, int32_t k,
+                     const float* kth_dev, const int32_t* probes_dev, int32_t Pmax, int32_t P, float* label_dev,
+                     void* stream);
+
+/* Train the pruning model on the queries Qtrain_dev [nt x d] with true k-th
+ * distances kth_dev [nt]: each query's P nearest lists are searched with
+ * rerank R, labelled as in ksc_prune_labels and featurised; the features are
+ * standardised over all rows; the MLP is trained with binary cross-entropy
+ * (both heads on the label) by the FP32 kernels and Adam.  opts: epochs (4),
+ * batch (1024 rows), lr (1e-3), seed; other fields unused; may be NULL.
+ * Blocking.  *loss_host (may be NULL) receives the mean loss of the last
+ * epoch. */
+int ksc_train_pruner(ksc_index* ix, const float* Qtrain_dev, int64_t nt, const float* kth_dev, int32_t k,
+                     int32_t P, int32_t R, const ksc_train_opts* opts, void* stream, float* loss_host);
+
+/* ksc_search with pruning: the nprobe nearest lists of each query, then
+ * those the model keeps at theta (as ksc_prune_probes), then the search of
+ * the kept lists.  nprobe_out_dev [nq] (device, may be NULL) receives the
+ * number of lists searched per query.  KSC_ESTATE without a model. */
+int ksc_search_pruned(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t k, int32_t nprobe, int32_t rerank,
+                      float theta, int64_t* ids_dev, float* dists_dev, int32_t* nprobe_out_dev,
+                      const ksc_search_opts* opts, void* stream);
+
+/* Loss and gradient of the pruning MLP (16 -> 32 -> 32 -> 2, mean binary
+ * cross-entropy of both heads) over x_dev [B x 16], y_dev [B x 2] at w_dev
+ * [KSC_PRUNE_NPARAMS]; grad_dev [KSC_PRUNE_NPARAMS], loss_dev [1] (device). */
+int ksc_prune_mlp_grad(const float* w_dev, const float* x_dev, const float* y_dev, int64_t B, float* grad_dev,
+                       float* loss_dev, void* stream);
+
 /* Device status word of the last search on this index: 0 = clean, else a
  * bitwise OR of KSC_STATUS_* (blocking read). */
 #define KSC_STATUS_CAND_OVERFLOW 1  /* a query's candidate store overflowed and was redone exactly */

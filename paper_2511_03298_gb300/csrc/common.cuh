@@ -22,6 +22,14 @@ const char* get_error();
         }                                     \
     } while (0)
 
+#define KSC_CHECK_STATE(cond, ...)            \
+    do {                                      \
+        if (!(cond)) {                        \
+            ::ksc::set_error(__VA_ARGS__);    \
+            return KSC_ESTATE;                \
+        }                                     \
+    } while (0)
+
 #define KSC_CUDA(call)                                                                  \
     do {                                                                                \
         cudaError_t e_ = (call);                                                        \

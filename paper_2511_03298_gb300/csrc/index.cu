@@ -321,13 +321,13 @@ int free_index_memory(ksc_index* ix) {
     void* ptrs[] = {ix->X, ix->c_rank, ix->c_rank_sq, ix->c_mean, ix->codebook, ix->list_boff, ix->list_n,
                     ix->blk_ids, ix->blk_codes, ix->assign, ix->graph, ix->entry, ix->status, ix->stats,
                     ix->c_rank_bf16, ix->mlp_w, ix->blk_list, ix->nbr_pos, ix->nbr_codes, ix->entry_pos,
-                    ix->X_bf16, ix->X_fp8, ix->X_scale};
+                    ix->X_bf16, ix->X_fp8, ix->X_scale, ix->pr_stats, ix->pr_vecs, ix->pr_model};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     Buffer* bufs[] = {&ix->ws_scores, &ix->ws_probes, &ix->ws_lut, &ix->ws_bias, &ix->ws_scale, &ix->ws_range,
                       &ix->ws_thr, &ix->ws_cnt, &ix->ws_cand, &ix->ws_topr, &ix->ws_nprobe, &ix->ws_rerank,
                       &ix->ws_items, &ix->ws_misc, &ix->ws_qbf16, &ix->ws_err, &ix->ws_feat, &ix->ws_rscore,
-                      &ix->ws_full, &ix->ws_topr2, &ix->ws_redo};
+                      &ix->ws_full, &ix->ws_topr2, &ix->ws_redo, &ix->ws_pprobes, &ix->ws_pn};
     for (Buffer* b : bufs) release(*b);
     for (int i = 0; i <= KSC_NUM_STAGES; ++i)
         if (ix->ev[i]) cudaEventDestroy(ix->ev[i]);

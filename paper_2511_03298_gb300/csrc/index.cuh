@@ -52,6 +52,11 @@ struct ksc_index {
     // learned nprobe / rerank predictor (Sec. 4.2.1-4.2.2)
     float* mlp_w = nullptr;  // [KSC_MLP_NPARAMS] FP32
     ksc_adaptive_params mlp_prm = {};
+    // predictive cluster pruning (Sec. 4.2.3): per-list statistics, vectors, model
+    float* pr_stats = nullptr;  // [L x KSC_PRUNE_STATS]
+    float* pr_vecs = nullptr;   // [L x 3 x d] v1, v2, mean outlier offset
+    float* pr_model = nullptr;  // [KSC_PRUNE_MODEL] weights, feature means, feature stds
+    bool pr_have_stats = false;
     // stage timing (ksc_profile_enable)
     bool prof = false;
     cudaEvent_t ev[KSC_NUM_STAGES + 1] = {};
@@ -60,7 +65,7 @@ struct ksc_index {
     // search workspace
     ksc::Buffer ws_scores, ws_probes, ws_lut, ws_bias, ws_scale, ws_range, ws_thr, ws_cnt,
         ws_cand, ws_topr, ws_nprobe, ws_rerank, ws_items, ws_misc, ws_qbf16, ws_err, ws_feat, ws_rscore, ws_full, ws_topr2,
-        ws_redo;
+        ws_redo, ws_pprobes, ws_pn;
 };
 
 namespace ksc {
@@ -84,6 +89,20 @@ int mlp_infer(const float* w, const float* x, int64_t B, const ksc_adaptive_para
 int mlp_features(const float* scores, int64_t nq, int ld, int spherical, float* feats, cudaStream_t st);
 int mlp_hits(const float* dists, int64_t nq, int k, const float* kth, int ip, int32_t* hits, cudaStream_t st);
 int mlp_adam(float* w, const float* g, float* m, float* v, int t, float lr, cudaStream_t st);
+int mlp_adam_n(float* w, const float* g, float* m, float* v, int n, int t, float lr, cudaStream_t st);
+int prune_mlp_grad(const float* w, const float* x, const float* y, int64_t B, float* grad, float* loss,
+                   cudaStream_t st);
+// Predictive cluster pruning (prune.cu): per-list statistics; features /
+// keep probabilities / pruned probe lists of (query, rank) rows; labels;
+// feature standardisation (moments into the model) and training targets.
+int prune_stats(ksc_index* ix, int iters, cudaStream_t st);
+int prune_rows(ksc_index* ix, const float* Q, int64_t nq, const int32_t* probes, int Pmax, const int32_t* nprobe,
+               int P, float theta, float* feats, float* prob, int32_t* probes_out, int32_t* nprobe_out,
+               cudaStream_t st);
+int prune_labels(ksc_index* ix, const int64_t* ids, const float* dists, int64_t nq, int k, const float* kth,
+                 const int32_t* probes, int Pmax, int P, float* label, cudaStream_t st);
+int prune_standardise(float* x, int64_t rows, float* model, cudaStream_t st);
+int prune_targets(const float* lab, int64_t rows, float* y, cudaStream_t st);
 // Per-list 32-NN graphs and entry points for the hybrid search (Sec. 4.4).
 int build_graph(ksc_index* ix, cudaStream_t st);
 // Search form (nbr_pos, nbr_codes, entry_pos) of graph / entry (hybrid.cu).

@@ -26,16 +26,23 @@ constexpr int MLP_ITILE = 32;  // queries per tile of the inference kernel (one 
 struct MlpW {  // views into a packed parameter vector (same packing as the oracle)
     const float *W1, *b1, *W2, *b2, *W3, *b3;
 };
-__host__ __device__ inline MlpW mlp_views(const float* w) {
+// Network F -> H -> H -> 2: parameter count and views.
+template <int F, int H>
+constexpr int mlp_nparam() {
+    return H * F + H + H * H + H + MLP_O * H + MLP_O;
+}
+template <int F, int H>
+__host__ __device__ inline MlpW mlp_views_t(const float* w) {
     MlpW v;
     v.W1 = w;
-    v.b1 = v.W1 + MLP_H * MLP_F;
-    v.W2 = v.b1 + MLP_H;
-    v.b2 = v.W2 + MLP_H * MLP_H;
-    v.W3 = v.b2 + MLP_H;
-    v.b3 = v.W3 + MLP_O * MLP_H;
+    v.b1 = v.W1 + H * F;
+    v.W2 = v.b1 + H;
+    v.b2 = v.W2 + H * H;
+    v.W3 = v.b2 + H;
+    v.b3 = v.W3 + MLP_O * H;
     return v;
 }
+__host__ __device__ inline MlpW mlp_views(const float* w) { return mlp_views_t<MLP_F, MLP_H>(w); }
 
 // Features of one query from its sorted ranking scores s[0..32).
 __device__ __forceinline__ float feat_dist(float s, int spherical) { return spherical ? 1.f + s : s; }
@@ -72,42 +79,45 @@ __device__ __forceinline__ void dense(const float* in, int rows, int Fin, const 
 // One training pass over samples [0, B): loss (mean BCE over the batch, both
 // heads) and gradients accumulated into grad (zeroed by the caller).  CTA c
 // handles samples [c*128, c*128+128); the batch GEMMs run in shared memory.
+// Network FN -> HN -> HN -> 2.
+template <int FN, int HN>
 __global__ void __launch_bounds__(256) k_mlp_grad(const float* __restrict__ w, const float* __restrict__ x,
                                                   const float* __restrict__ y, int64_t B, float* __restrict__ grad,
                                                   float* __restrict__ loss) {
+    constexpr int NP = mlp_nparam<FN, HN>();
     extern __shared__ float sm[];
-    float* sw = sm;                          // MLP_NPARAM
-    float* X = sw + MLP_NPARAM;              // 128 x 64
-    float* Z1 = X + MLP_TILE * MLP_F;        // 128 x 64 (pre-activation, then dZ1)
-    float* Z2 = Z1 + MLP_TILE * MLP_H;       // 128 x 64
-    float* H = Z2 + MLP_TILE * MLP_H;        // 128 x 64 scratch (H1, then H2, then dH)
-    float* D3 = H + MLP_TILE * MLP_H;        // 128 x 2
+    float* sw = sm;                    // NP
+    float* X = sw + NP;                // 128 x FN
+    float* Z1 = X + MLP_TILE * FN;     // 128 x HN (pre-activation, then dZ1)
+    float* Z2 = Z1 + MLP_TILE * HN;    // 128 x HN
+    float* Hb = Z2 + MLP_TILE * HN;    // 128 x HN scratch (H1, then H2, then dH)
+    float* D3 = Hb + MLP_TILE * HN;    // 128 x 2
     const int64_t r0 = (int64_t)blockIdx.x * MLP_TILE;
     const int rows = (int)(B - r0 < MLP_TILE ? B - r0 : MLP_TILE);
-    for (int e = threadIdx.x; e < MLP_NPARAM; e += blockDim.x) sw[e] = w[e];
-    for (int e = threadIdx.x; e < rows * MLP_F; e += blockDim.x) X[e] = x[r0 * MLP_F + e];
+    for (int e = threadIdx.x; e < NP; e += blockDim.x) sw[e] = w[e];
+    for (int e = threadIdx.x; e < rows * FN; e += blockDim.x) X[e] = x[r0 * FN + e];
     __syncthreads();
-    const MlpW W = mlp_views(sw);
-    MlpW G = mlp_views(grad);
+    const MlpW W = mlp_views_t<FN, HN>(sw);
+    MlpW G = mlp_views_t<FN, HN>(grad);
     float* gW1 = const_cast<float*>(G.W1);
     float* gb1 = const_cast<float*>(G.b1);
     float* gW2 = const_cast<float*>(G.W2);
     float* gb2 = const_cast<float*>(G.b2);
     float* gW3 = const_cast<float*>(G.W3);
     float* gb3 = const_cast<float*>(G.b3);
-    dense(X, rows, MLP_F, W.W1, W.b1, MLP_H, Z1, H);  // H = H1
+    dense(X, rows, FN, W.W1, W.b1, HN, Z1, Hb);  // Hb = H1
     __syncthreads();
-    dense(H, rows, MLP_H, W.W2, W.b2, MLP_H, Z2, nullptr);
+    dense(Hb, rows, HN, W.W2, W.b2, HN, Z2, nullptr);
     __syncthreads();
     // H2 overwrites H1 only after layer 2 consumed it
-    for (int e = threadIdx.x; e < rows * MLP_H; e += blockDim.x) H[e] = Z2[e] > 0.f ? Z2[e] : 0.f;
+    for (int e = threadIdx.x; e < rows * HN; e += blockDim.x) Hb[e] = Z2[e] > 0.f ? Z2[e] : 0.f;
     __syncthreads();
     // output layer, loss and dZ3 = (p - y) / B
     float lsum = 0.f;
     for (int e = threadIdx.x; e < rows * MLP_O; e += blockDim.x) {
         const int r = e / MLP_O, o = e - r * MLP_O;
         float z = W.b3[o];
-        for (int f = 0; f < MLP_H; ++f) z = fmaf(H[r * MLP_H + f], W.W3[o * MLP_H + f], z);
+        for (int f = 0; f < HN; ++f) z = fmaf(Hb[r * HN + f], W.W3[o * HN + f], z);
         const float t = y[(r0 + r) * MLP_O + o];
         const float p = 1.f / (1.f + expf(-z));
         lsum += fmaxf(z, 0.f) - z * t + log1pf(expf(-fabsf(z)));
@@ -115,10 +125,10 @@ __global__ void __launch_bounds__(256) k_mlp_grad(const float* __restrict__ w, c
     }
     __syncthreads();
     // gW3 = D3^T H2, gb3 = sum D3
-    for (int e = threadIdx.x; e < MLP_O * MLP_H; e += blockDim.x) {
-        const int o = e / MLP_H, f = e - o * MLP_H;
+    for (int e = threadIdx.x; e < MLP_O * HN; e += blockDim.x) {
+        const int o = e / HN, f = e - o * HN;
         float acc = 0.f;
-        for (int r = 0; r < rows; ++r) acc = fmaf(D3[r * MLP_O + o], H[r * MLP_H + f], acc);
+        for (int r = 0; r < rows; ++r) acc = fmaf(D3[r * MLP_O + o], Hb[r * HN + f], acc);
         atomicAdd(&gW3[e], acc);
     }
     if (threadIdx.x < MLP_O) {
@@ -128,45 +138,45 @@ __global__ void __launch_bounds__(256) k_mlp_grad(const float* __restrict__ w, c
     }
     __syncthreads();
     // dZ2 = (D3 W3) * [Z2 > 0]  (into Z2)
-    for (int e = threadIdx.x; e < rows * MLP_H; e += blockDim.x) {
-        const int r = e / MLP_H, f = e - r * MLP_H;
+    for (int e = threadIdx.x; e < rows * HN; e += blockDim.x) {
+        const int r = e / HN, f = e - r * HN;
         float acc = 0.f;
-        for (int o = 0; o < MLP_O; ++o) acc = fmaf(D3[r * MLP_O + o], W.W3[o * MLP_H + f], acc);
+        for (int o = 0; o < MLP_O; ++o) acc = fmaf(D3[r * MLP_O + o], W.W3[o * HN + f], acc);
         Z2[e] = Z2[e] > 0.f ? acc : 0.f;
     }
     __syncthreads();
     // H1 again (layer 1 activations) for gW2
-    for (int e = threadIdx.x; e < rows * MLP_H; e += blockDim.x) H[e] = Z1[e] > 0.f ? Z1[e] : 0.f;
+    for (int e = threadIdx.x; e < rows * HN; e += blockDim.x) Hb[e] = Z1[e] > 0.f ? Z1[e] : 0.f;
     __syncthreads();
-    for (int e = threadIdx.x; e < MLP_H * MLP_H; e += blockDim.x) {
-        const int a = e / MLP_H, f = e - a * MLP_H;
+    for (int e = threadIdx.x; e < HN * HN; e += blockDim.x) {
+        const int a = e / HN, f = e - a * HN;
         float acc = 0.f;
-        for (int r = 0; r < rows; ++r) acc = fmaf(Z2[r * MLP_H + a], H[r * MLP_H + f], acc);
+        for (int r = 0; r < rows; ++r) acc = fmaf(Z2[r * HN + a], Hb[r * HN + f], acc);
         atomicAdd(&gW2[e], acc);
     }
-    for (int a = threadIdx.x; a < MLP_H; a += blockDim.x) {
+    for (int a = threadIdx.x; a < HN; a += blockDim.x) {
         float acc = 0.f;
-        for (int r = 0; r < rows; ++r) acc += Z2[r * MLP_H + a];
+        for (int r = 0; r < rows; ++r) acc += Z2[r * HN + a];
         atomicAdd(&gb2[a], acc);
     }
     __syncthreads();
     // dZ1 = (dZ2 W2) * [Z1 > 0]  (into Z1)
-    for (int e = threadIdx.x; e < rows * MLP_H; e += blockDim.x) {
-        const int r = e / MLP_H, f = e - r * MLP_H;
+    for (int e = threadIdx.x; e < rows * HN; e += blockDim.x) {
+        const int r = e / HN, f = e - r * HN;
         float acc = 0.f;
-        for (int a = 0; a < MLP_H; ++a) acc = fmaf(Z2[r * MLP_H + a], W.W2[a * MLP_H + f], acc);
-        H[e] = Z1[e] > 0.f ? acc : 0.f;
+        for (int a = 0; a < HN; ++a) acc = fmaf(Z2[r * HN + a], W.W2[a * HN + f], acc);
+        Hb[e] = Z1[e] > 0.f ? acc : 0.f;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < MLP_H * MLP_F; e += blockDim.x) {
-        const int a = e / MLP_F, f = e - a * MLP_F;
+    for (int e = threadIdx.x; e < HN * FN; e += blockDim.x) {
+        const int a = e / FN, f = e - a * FN;
         float acc = 0.f;
-        for (int r = 0; r < rows; ++r) acc = fmaf(H[r * MLP_H + a], X[r * MLP_F + f], acc);
+        for (int r = 0; r < rows; ++r) acc = fmaf(Hb[r * HN + a], X[r * FN + f], acc);
         atomicAdd(&gW1[e], acc);
     }
-    for (int a = threadIdx.x; a < MLP_H; a += blockDim.x) {
+    for (int a = threadIdx.x; a < HN; a += blockDim.x) {
         float acc = 0.f;
-        for (int r = 0; r < rows; ++r) acc += H[r * MLP_H + a];
+        for (int r = 0; r < rows; ++r) acc += Hb[r * HN + a];
         atomicAdd(&gb1[a], acc);
     }
 #pragma unroll
@@ -268,16 +278,34 @@ __global__ void k_hits(const float* __restrict__ dists, int64_t nq, int k, const
     hits[q] = h;
 }
 
-static size_t grad_smem() { return sizeof(float) * (MLP_NPARAM + MLP_TILE * (MLP_F + 3 * MLP_H + MLP_O)); }
+template <int F, int H>
+static size_t grad_smem() {
+    return sizeof(float) * (mlp_nparam<F, H>() + MLP_TILE * (F + 3 * H + MLP_O));
+}
 static size_t infer_smem() { return sizeof(float) * (MLP_NPARAM + 3 * MLP_ITILE * MLP_LDI); }
 
-int mlp_grad(const float* w, const float* x, const float* y, int64_t B, float* grad, float* loss, cudaStream_t st) {
-    KSC_CUDA(cudaMemsetAsync(grad, 0, sizeof(float) * MLP_NPARAM, st));
+template <int F, int H>
+static int mlp_grad_t(const float* w, const float* x, const float* y, int64_t B, float* grad, float* loss,
+                      cudaStream_t st) {
+    KSC_CUDA(cudaMemsetAsync(grad, 0, sizeof(float) * mlp_nparam<F, H>(), st));
     if (loss) KSC_CUDA(cudaMemsetAsync(loss, 0, sizeof(float), st));
-    KSC_CUDA(cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grad_smem()));
-    k_mlp_grad<<<(unsigned)((B + MLP_TILE - 1) / MLP_TILE), 256, grad_smem(), st>>>(w, x, y, B, grad, loss);
+    KSC_CUDA(cudaFuncSetAttribute(k_mlp_grad<F, H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)grad_smem<F, H>()));
+    k_mlp_grad<F, H><<<(unsigned)((B + MLP_TILE - 1) / MLP_TILE), 256, grad_smem<F, H>(), st>>>(w, x, y, B, grad,
+                                                                                              loss);
     KSC_LAUNCH_CHECK();
     return KSC_OK;
+}
+
+int mlp_grad(const float* w, const float* x, const float* y, int64_t B, float* grad, float* loss, cudaStream_t st) {
+    return mlp_grad_t<MLP_F, MLP_H>(w, x, y, B, grad, loss, st);
+}
+
+// The pruning classifier's network (Sec. 4.2.3): 16 -> 32 -> 32 -> 2.
+int prune_mlp_grad(const float* w, const float* x, const float* y, int64_t B, float* grad, float* loss,
+                   cudaStream_t st) {
+    static_assert(mlp_nparam<KSC_PRUNE_FEATURES, 32>() == KSC_PRUNE_NPARAMS, "pruning network size");
+    return mlp_grad_t<KSC_PRUNE_FEATURES, 32>(w, x, y, B, grad, loss, st);
 }
 
 int mlp_infer(const float* w, const float* x, int64_t B, const ksc_adaptive_params& prm, float* prob,
@@ -305,12 +333,16 @@ int mlp_hits(const float* dists, int64_t nq, int k, const float* kth, int ip, in
     return KSC_OK;
 }
 
-int mlp_adam(float* w, const float* g, float* m, float* v, int t, float lr, cudaStream_t st) {
+int mlp_adam_n(float* w, const float* g, float* m, float* v, int n, int t, float lr, cudaStream_t st) {
     const float b1 = 0.9f, b2 = 0.999f;
     const float bc1 = 1.f - powf(b1, (float)t), bc2 = 1.f - powf(b2, (float)t);
-    k_adam<<<(MLP_NPARAM + 255) / 256, 256, 0, st>>>(w, g, m, v, MLP_NPARAM, lr, b1, b2, 1e-8f, bc1, bc2);
+    k_adam<<<(n + 255) / 256, 256, 0, st>>>(w, g, m, v, n, lr, b1, b2, 1e-8f, bc1, bc2);
     KSC_LAUNCH_CHECK();
     return KSC_OK;
+}
+
+int mlp_adam(float* w, const float* g, float* m, float* v, int t, float lr, cudaStream_t st) {
+    return mlp_adam_n(w, g, m, v, MLP_NPARAM, t, lr, st);
 }
 
 }  // namespace ksc

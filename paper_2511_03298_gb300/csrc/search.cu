@@ -3574,3 +3574,196 @@ int ksc_autotune(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t k, int32
 
 }  // extern "C"
 
+
+// ------------------------------------------------------------------ predictive cluster pruning
+// Sec. 4.2.3, Table 4, Alg. 2 f_prune: statistics, features and the
+// classifier live in prune.cu; here are the entry points that tie them to the
+// ranking, the plain search (labels) and the search of the kept lists.
+extern "C" {
+
+int ksc_pruner_stats(ksc_index* ix, int32_t iters, void* stream) {
+    KSC_CHECK_ARG(ix, "null index");
+    return prune_stats(ix, iters, as_stream(stream));
+}
+
+int ksc_pruner_export(ksc_index* ix, float* stats_host, float* vecs_host, float* model_host) {
+    KSC_CHECK_ARG(ix, "null index");
+    if (stats_host || vecs_host) KSC_CHECK_STATE(ix->pr_have_stats, "the pruning statistics have not been computed");
+    if (model_host) KSC_CHECK_STATE(ix->pr_model, "no pruning model");
+    KSC_CUDA(cudaDeviceSynchronize());
+    if (stats_host)
+        KSC_CUDA(cudaMemcpy(stats_host, ix->pr_stats, sizeof(float) * ix->L * KSC_PRUNE_STATS, cudaMemcpyDeviceToHost));
+    if (vecs_host)
+        KSC_CUDA(cudaMemcpy(vecs_host, ix->pr_vecs, sizeof(float) * ix->L * 3 * ix->d, cudaMemcpyDeviceToHost));
+    if (model_host)
+        KSC_CUDA(cudaMemcpy(model_host, ix->pr_model, sizeof(float) * KSC_PRUNE_MODEL, cudaMemcpyDeviceToHost));
+    return KSC_OK;
+}
+
+int ksc_pruner_import_model(ksc_index* ix, const float* model_host) {
+    KSC_CHECK_ARG(ix && model_host, "null argument");
+    if (!ix->pr_model) KSC_CUDA(cudaMalloc(&ix->pr_model, sizeof(float) * KSC_PRUNE_MODEL));
+    KSC_CUDA(cudaMemcpy(ix->pr_model, model_host, sizeof(float) * KSC_PRUNE_MODEL, cudaMemcpyHostToDevice));
+    return KSC_OK;
+}
+
+int ksc_prune_probes(ksc_index* ix, const float* Q_dev, int64_t nq, const int32_t* probes_dev, int32_t Pmax,
+                     const int32_t* nprobe_dev, int32_t P, float theta, float* feats_dev, float* prob_dev,
+                     int32_t* probes_out_dev, int32_t* nprobe_out_dev, void* stream) {
+    KSC_CHECK_ARG(ix && nq >= 0 && Pmax >= 1 && (nprobe_dev || (P >= 1 && P <= Pmax)), "bad argument");
+    if (nq == 0) return KSC_OK;
+    KSC_CHECK_ARG(Q_dev && probes_dev, "null argument");
+    return prune_rows(ix, Q_dev, nq, probes_dev, Pmax, nprobe_dev, P, theta, feats_dev, prob_dev, probes_out_dev,
+                      nprobe_out_dev, as_stream(stream));
+}
+
+int ksc_prune_labels(ksc_index* ix, const int64_t* ids_dev, const float* dists_dev, int64_t nq, int32_t k,
+                     const float* kth_dev, const int32_t* probes_dev, int32_t Pmax, int32_t P, float* label_dev,
+                     void* stream) {
+    KSC_CHECK_ARG(ix && nq >= 0 && k >= 1 && Pmax >= 1 && P >= 0, "bad argument");
+    if (nq == 0) return KSC_OK;
+    KSC_CHECK_ARG(ids_dev && dists_dev && kth_dev && probes_dev && label_dev, "null argument");
+    return prune_labels(ix, ids_dev, dists_dev, nq, k, kth_dev, probes_dev, Pmax, P, label_dev, as_stream(stream));
+}
+
+int ksc_prune_mlp_grad(const float* w_dev, const float* x_dev, const float* y_dev, int64_t B, float* grad_dev,
+                       float* loss_dev, void* stream) {
+    KSC_CHECK_ARG(w_dev && x_dev && y_dev && grad_dev && B > 0, "bad argument");
+    return prune_mlp_grad(w_dev, x_dev, y_dev, B, grad_dev, loss_dev, as_stream(stream));
+}
+
+int ksc_search_pruned(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t k, int32_t nprobe, int32_t rerank,
+                      float theta, int64_t* ids_dev, float* dists_dev, int32_t* nprobe_out_dev,
+                      const ksc_search_opts* opts, void* stream) {
+    KSC_CHECK_ARG(ix, "null index");
+    KSC_CHECK_STATE(ix->pr_have_stats && ix->pr_model, "no pruning model: train one with ksc_train_pruner");
+    Plan pl;
+    KSC_TRY(make_plan(ix, nq, k, nprobe, rerank, opts, pl));
+    if (nq == 0) return KSC_OK;  // empty batch: pointers may be NULL
+    KSC_CHECK_ARG(Q_dev && ids_dev && dists_dev, "null argument");
+    cudaStream_t st = as_stream(stream);
+    KSC_CUDA(cudaMemsetAsync(ix->status, 0, sizeof(int32_t), st));
+    KSC_TRY(ensure(ix->ws_probes, sizeof(int32_t) * nq * pl.Pmax, st));
+    KSC_TRY(ensure(ix->ws_pprobes, sizeof(int32_t) * nq * pl.Pmax, st));
+    KSC_TRY(ensure(ix->ws_pn, sizeof(int32_t) * nq, st));
+    int32_t* probes = (int32_t*)ix->ws_probes.p;
+    int32_t* kept = (int32_t*)ix->ws_pprobes.p;
+    int32_t* pn = (int32_t*)ix->ws_pn.p;
+    KSC_CUDA(cudaMemsetAsync(ix->stats, 0, sizeof(unsigned long long) * 4, st));
+    ix->launches = 0;
+    mark(ix, 0, st);
+    KSC_TRY(rank_lists(ix, Q_dev, nq, nullptr, pl.Pmax, pl.Pmax, probes, nullptr, pl.rank_exact, st));
+    // Alg. 2: keep rank 0 and the ranks with f_prune > theta, in rank order
+    KSC_TRY(prune_rows(ix, Q_dev, nq, probes, pl.Pmax, nullptr, pl.Pmax, theta, nullptr, nullptr, kept, pn, st));
+    ix->launches++;
+    pl.nprobe_q = pn;
+    set_tiles(ix, pl, nq, 0.75 * pl.Pmax, opts);
+    if (nprobe_out_dev)
+        KSC_CUDA(cudaMemcpyAsync(nprobe_out_dev, pn, sizeof(int32_t) * nq, cudaMemcpyDeviceToDevice, st));
+    return search_from_probes(ix, Q_dev, pl, kept, ids_dev, dists_dev, nullptr, nullptr, st);
+}
+
+#define T_CUDA(call) { cudaError_t e_ = (call); if (e_ != cudaSuccess) { set_error("%s: %s", #call, cudaGetErrorString(e_)); rc = KSC_ECUDA; break; } }
+int ksc_train_pruner(ksc_index* ix, const float* Qtrain_dev, int64_t nt, const float* kth_dev, int32_t k,
+                     int32_t P, int32_t R, const ksc_train_opts* opts, void* stream, float* loss_host) {
+    KSC_CHECK_ARG(ix && Qtrain_dev && kth_dev && nt > 0, "bad argument");
+    KSC_CHECK_ARG(k >= 1 && k <= KSC_MAX_K && R >= k && R <= KSC_MAX_RERANK, "bad k or rerank");
+    KSC_CHECK_ARG(P >= 1 && P <= ix->L && P <= MAX_NPROBE, "bad nprobe");
+    cudaStream_t st = as_stream(stream);
+    if (!ix->pr_have_stats) KSC_TRY(prune_stats(ix, 30, st));
+    const int epochs = (opts && opts->epochs > 0) ? opts->epochs : 4;
+    const int batch = (opts && opts->batch > 0) ? opts->batch : 1024;
+    const float lr = (opts && opts->lr > 0.f) ? opts->lr : 1e-3f;
+    uint64_t seed = (opts && opts->seed) ? opts->seed : 0x707275ull;
+    const int64_t chunk = 8192, rows = nt * P;
+    const int NF = KSC_PRUNE_FEATURES, NP = KSC_PRUNE_NPARAMS;
+    float *feats = nullptr, *lab = nullptr, *Y = nullptr, *dists = nullptr, *model = nullptr;
+    float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr, *xb = nullptr, *yb = nullptr, *lossd = nullptr;
+    int32_t* probes = nullptr;
+    int64_t *ids = nullptr, *idx = nullptr;
+    int rc = KSC_OK;
+    const int steps = (int)((rows + batch - 1) / batch);
+    do {
+        T_CUDA(cudaMalloc(&feats, sizeof(float) * rows * NF));
+        T_CUDA(cudaMalloc(&lab, sizeof(float) * rows));
+        T_CUDA(cudaMalloc(&Y, sizeof(float) * rows * 2));
+        T_CUDA(cudaMalloc(&probes, sizeof(int32_t) * chunk * P));
+        T_CUDA(cudaMalloc(&ids, sizeof(int64_t) * chunk * k));
+        T_CUDA(cudaMalloc(&dists, sizeof(float) * chunk * k));
+        T_CUDA(cudaMalloc(&model, sizeof(float) * KSC_PRUNE_MODEL));
+        // 1. rows of the P nearest lists of every training query: labels from
+        //    the plain search of those lists, features
+        for (int64_t c0 = 0; c0 < nt && rc == KSC_OK; c0 += chunk) {
+            const int64_t nc = std::min(chunk, nt - c0);
+            const float* Qc = Qtrain_dev + c0 * ix->d;
+            if ((rc = rank_lists(ix, Qc, nc, nullptr, P, P, probes, nullptr, false, st))) break;
+            Plan pl;
+            if ((rc = make_plan(ix, nc, k, P, R, nullptr, pl))) break;
+            if ((rc = search_from_probes(ix, Qc, pl, probes, ids, dists, nullptr, nullptr, st))) break;
+            if ((rc = prune_labels(ix, ids, dists, nc, k, kth_dev + c0, probes, P, P, lab + c0 * P, st))) break;
+            if ((rc = prune_rows(ix, Qc, nc, probes, P, nullptr, P, 0.f, feats + c0 * P * NF, nullptr, nullptr,
+                                 nullptr, st)))
+                break;
+        }
+        if (rc) break;
+        // 2. standardised features, targets
+        if ((rc = prune_standardise(feats, rows, model, st))) break;
+        if ((rc = prune_targets(lab, rows, Y, st))) break;
+        // 3. weights: He-uniform from the seed, zero biases
+        std::vector<float> wh(NP, 0.f);
+        const int fan[3] = {NF, 32, 32}, nrow[3] = {32, 32, 2};
+        int off = 0;
+        for (int l = 0; l < 3; ++l) {
+            const float a = sqrtf(6.f / fan[l]);
+            for (int e = 0; e < nrow[l] * fan[l]; ++e)
+                wh[off + e] = a * (2.f * (float)((mix64(seed) >> 11) * (1.0 / 9007199254740992.0)) - 1.f);
+            off += nrow[l] * fan[l] + nrow[l];
+        }
+        T_CUDA(cudaMalloc(&w, sizeof(float) * NP));
+        T_CUDA(cudaMalloc(&g, sizeof(float) * NP));
+        T_CUDA(cudaMalloc(&m, sizeof(float) * NP));
+        T_CUDA(cudaMalloc(&v, sizeof(float) * NP));
+        T_CUDA(cudaMalloc(&xb, sizeof(float) * batch * NF));
+        T_CUDA(cudaMalloc(&yb, sizeof(float) * batch * 2));
+        T_CUDA(cudaMalloc(&idx, sizeof(int64_t) * rows));
+        T_CUDA(cudaMalloc(&lossd, sizeof(float) * steps));
+        T_CUDA(cudaMemcpy(w, wh.data(), sizeof(float) * NP, cudaMemcpyHostToDevice));
+        T_CUDA(cudaMemset(m, 0, sizeof(float) * NP));
+        T_CUDA(cudaMemset(v, 0, sizeof(float) * NP));
+        // 4. Adam over shuffled minibatches of rows
+        std::vector<int64_t> perm(rows);
+        int t = 0;
+        for (int ep = 0; ep < epochs && rc == KSC_OK; ++ep) {
+            for (int64_t i = 0; i < rows; ++i) perm[i] = i;
+            for (int64_t i = rows - 1; i > 0; --i) std::swap(perm[i], perm[(int64_t)(mix64(seed) % (uint64_t)(i + 1))]);
+            T_CUDA(cudaMemcpyAsync(idx, perm.data(), sizeof(int64_t) * rows, cudaMemcpyHostToDevice, st));
+            for (int s_ = 0; s_ < steps; ++s_) {
+                const int64_t b0 = (int64_t)s_ * batch, nb = std::min<int64_t>(batch, rows - b0);
+                k_gather_rows<<<(unsigned)((nb * NF + 255) / 256), 256, 0, st>>>(feats, idx + b0, nb, NF, xb);
+                k_gather_rows<<<(unsigned)((nb * 2 + 255) / 256), 256, 0, st>>>(Y, idx + b0, nb, 2, yb);
+                if ((rc = prune_mlp_grad(w, xb, yb, nb, g, lossd + s_, st))) break;
+                if ((rc = mlp_adam_n(w, g, m, v, NP, ++t, lr, st))) break;
+            }
+            T_CUDA(cudaStreamSynchronize(st));  // perm is reused by the next epoch
+        }
+        if (rc) break;
+        if (loss_host) {
+            std::vector<float> lh(steps);
+            T_CUDA(cudaMemcpy(lh.data(), lossd, sizeof(float) * steps, cudaMemcpyDeviceToHost));
+            double sum = 0.0;
+            for (float x : lh) sum += x;
+            *loss_host = (float)(sum / steps);
+        }
+        T_CUDA(cudaMemcpy(model, w, sizeof(float) * NP, cudaMemcpyDeviceToDevice));
+        if (ix->pr_model) cudaFree(ix->pr_model);
+        ix->pr_model = model;
+        model = nullptr;
+    } while (0);
+    void* tmp[] = {feats, lab, Y, dists, model, w, g, m, v, xb, yb, lossd, probes, ids, idx};
+    for (void* p : tmp)
+        if (p) cudaFree(p);
+    return rc;
+}
+#undef T_CUDA
+
+}  // extern "C"

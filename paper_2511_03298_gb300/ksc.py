@@ -87,6 +87,14 @@ _SIGS = {
     "ksc_query_features": [_vp, _vp, _i64, _vp, _vp],
     "ksc_mlp_grad": [_vp, _vp, _vp, _i64, _vp, _vp, _vp],
     "ksc_mlp_forward": [_vp, _vp, _i64, _vp, _vp],
+    "ksc_pruner_stats": [_vp, _i32, _vp],
+    "ksc_pruner_export": [_vp, _vp, _vp, _vp],
+    "ksc_pruner_import_model": [_vp, _vp],
+    "ksc_prune_probes": [_vp, _vp, _i64, _vp, _i32, _vp, _i32, C.c_float, _vp, _vp, _vp, _vp, _vp],
+    "ksc_prune_labels": [_vp, _vp, _vp, _i64, _i32, _vp, _vp, _i32, _i32, _vp, _vp],
+    "ksc_train_pruner": [_vp, _vp, _i64, _vp, _i32, _i32, _i32, _vp, _vp, _vp],
+    "ksc_search_pruned": [_vp, _vp, _i64, _i32, _i32, _i32, C.c_float, _vp, _vp, _vp, _vp, _vp],
+    "ksc_prune_mlp_grad": [_vp, _vp, _vp, _i64, _vp, _vp, _vp],
     "ksc_last_error": [],
     "ksc_version": [],
 }
@@ -309,6 +317,91 @@ class Index:
                                         _stream(stream)))
         return f
 
+    # ---------------------------------------------------------- cluster pruning (Sec. 4.2.3)
+    PRUNE_STATS, PRUNE_FEATURES, PRUNE_NPARAMS = 12, 16, 1666
+    PRUNE_MODEL = PRUNE_NPARAMS + 2 * PRUNE_FEATURES
+
+    def pruner_stats(self, iters=30, stream=None):
+        """Per-list statistics of the pruning features (build time)."""
+        _check(lib().ksc_pruner_stats(self._h, iters, _stream(stream)))
+
+    def pruner_export(self, model=True):
+        """Statistics [L x 12], vectors [L x 3 x d] and, if trained, the model."""
+        inf = self.info()
+        st = np.zeros((inf["nlist"], self.PRUNE_STATS), np.float32)
+        vec = np.zeros((inf["nlist"], 3, inf["d"]), np.float32)
+        mdl = np.zeros(self.PRUNE_MODEL, np.float32) if model else None
+        _check(lib().ksc_pruner_export(self._h, _hptr(st), _hptr(vec), _hptr(mdl)))
+        return st, vec, mdl
+
+    def pruner_model(self, set_to=None):
+        """Set (set_to: weights, feature means, feature stds) or read the model."""
+        if set_to is not None:
+            m = np.ascontiguousarray(set_to, dtype=np.float32)
+            assert m.size == self.PRUNE_MODEL
+            _check(lib().ksc_pruner_import_model(self._h, _hptr(m)))
+            return m
+        m = np.zeros(self.PRUNE_MODEL, np.float32)
+        _check(lib().ksc_pruner_export(self._h, None, None, _hptr(m)))
+        return m
+
+    def prune_probes(self, Q, probes, P=None, nprobe=None, theta=0.5, feats=False, prob=False, kept=True,
+                     stream=None):
+        """Features / keep probabilities / kept probes (rank order, -1 after)
+        and their count for given probes [nq x Pmax]; returns a dict."""
+        torch = _torch()
+        nq, Pmax = probes.shape
+        dev = Q.device
+        out = {}
+        if feats:
+            out["feats"] = torch.empty((nq, Pmax, self.PRUNE_FEATURES), dtype=torch.float32, device=dev)
+        if prob:
+            out["prob"] = torch.empty((nq, Pmax), dtype=torch.float32, device=dev)
+        if kept:
+            out["probes"] = torch.empty((nq, Pmax), dtype=torch.int32, device=dev)
+            out["nprobe"] = torch.empty((nq,), dtype=torch.int32, device=dev)
+        _check(lib().ksc_prune_probes(self._h, _dptr(Q, torch.float32, "Q"), nq, _dptr(probes, torch.int32, "probes"),
+                                      Pmax, _dptr(nprobe, torch.int32, "nprobe"), int(P or Pmax), float(theta),
+                                      _dptr(out.get("feats")), _dptr(out.get("prob")), _dptr(out.get("probes")),
+                                      _dptr(out.get("nprobe")), _stream(stream)))
+        return out
+
+    def prune_labels(self, ids, dists, kth, probes, P, stream=None):
+        torch = _torch()
+        nq, Pmax = probes.shape
+        lab = torch.empty((nq, Pmax), dtype=torch.float32, device=ids.device)
+        _check(lib().ksc_prune_labels(self._h, _dptr(ids, torch.int64, "ids"), _dptr(dists, torch.float32, "dists"),
+                                      nq, ids.shape[1], _dptr(kth, torch.float32, "kth"),
+                                      _dptr(probes, torch.int32, "probes"), Pmax, int(P), _dptr(lab),
+                                      _stream(stream)))
+        return lab
+
+    def train_pruner(self, Qtrain, kth, k=10, P=16, R=200, epochs=4, batch=1024, lr=1e-3, seed=0, stream=None):
+        """Train the pruning classifier on training queries and their true
+        k-th neighbour distances (device tensors).  Returns the mean loss of
+        the last epoch."""
+        torch = _torch()
+        opts = TrainOpts(k, 0, 0, epochs, batch, lr, seed, None, 0, None, 0)
+        loss = C.c_float(0)
+        _check(lib().ksc_train_pruner(self._h, _dptr(Qtrain, torch.float32, "Qtrain"), Qtrain.shape[0],
+                                      _dptr(kth, torch.float32, "kth"), k, P, R, C.byref(opts), _stream(stream),
+                                      C.byref(loss)))
+        return loss.value
+
+    def search_pruned(self, Q, k, nprobe, rerank, theta, opts=None, out=None, stream=None):
+        """ksc_search with the lists the pruning model rejects at theta
+        dropped; returns ids, dists and the lists searched per query."""
+        torch = _torch()
+        nq = Q.shape[0]
+        ids, dists = out if out is not None else (
+            torch.empty((nq, k), dtype=torch.int64, device=Q.device),
+            torch.empty((nq, k), dtype=torch.float32, device=Q.device))
+        npb = torch.empty((nq,), dtype=torch.int32, device=Q.device)
+        _check(lib().ksc_search_pruned(self._h, _dptr(Q, torch.float32, "Q"), nq, k, nprobe, rerank, float(theta),
+                                       _dptr(ids), _dptr(dists), _dptr(npb), C.byref(opts) if opts else None,
+                                       _stream(stream)))
+        return ids, dists, npb
+
     # ---------------------------------------------------------- plans, autotuner
     def plan(self, nq, k, nprobe=1, rerank=0, adaptive=False, opts=None, stream=None):
         """Capture a search of fixed shapes into a CUDA graph (see Plan)."""
@@ -416,6 +509,16 @@ def index_import(arrs, metric="l2", spherical=False, stream=None):
     h = C.c_void_p()
     _check(lib().ksc_index_import(C.byref(a), _stream(stream), C.byref(h)))
     return Index(h.value)
+
+
+def prune_mlp_grad(w, x, y, stream=None):
+    """Loss and gradient of the pruning MLP (16 -> 32 -> 32 -> 2) on device tensors."""
+    torch = _torch()
+    g = torch.empty(Index.PRUNE_NPARAMS, dtype=torch.float32, device=x.device)
+    loss = torch.empty(1, dtype=torch.float32, device=x.device)
+    _check(lib().ksc_prune_mlp_grad(_dptr(w, torch.float32, "w"), _dptr(x, torch.float32, "x"),
+                                    _dptr(y, torch.float32, "y"), x.shape[0], _dptr(g), _dptr(loss), _stream(stream)))
+    return loss, g
 
 
 def lut16_peak(stream=None):
