@@ -267,7 +267,8 @@ def run_ours(args, rank, ws):
         Td = torch.from_numpy(TV[:args.ntrain]).to(dev)
         Vd = torch.from_numpy(TV[args.ntrain:]).to(dev)
         t0 = time.time()
-        loss = ix.train_predictor(Td, kth_fp32(torch, Xd, Td, k), epochs=8)
+        kth_t = kth_fp32(torch, Xd, Td, k)
+        loss = ix.train_predictor(Td, kth_t, epochs=8)
         train_s = time.time() - t0
         _, vd_true = exact_topk(torch, Xd, Vd, k)
         best = None
@@ -303,6 +304,42 @@ def run_ours(args, rank, ws):
                            params=dict(pmin=best[2], pmax=best[3], p0=best[4], p1=best[5], rmin=rbest[2], rmax=R,
                                        r0=rbest[3], r1=rbest[4]),
                            train_loss=loss, train_s=round(train_s, 1), val_recall=rbest[1], stats=ix.search_stats())
+    # predictive cluster pruning (Sec. 4.2.3) inside the learned search (Alg. 2
+    # order): the classifier trained on the same training queries, its
+    # threshold and the nprobe head's Eq. 2 parameters tuned together on the
+    # validation split for the fewest lists searched at the target recall
+    pruned = None
+    learned_state = None
+    if learned is not None and not args.no_prune:
+        lp = learned["params"]
+        learned_state = (lp["pmin"], lp["pmax"], lp["rmin"], lp["rmax"], lp["p0"], lp["p1"], lp["r0"], lp["r1"])
+        t0 = time.time()
+        ploss = ix.train_pruner(Td, kth_t, k=k, P=lp["pmax"], R=R, epochs=4)
+        ptrain_s = time.time() - t0
+        pb = None
+        for th in (0.05, 0.1, 0.15, 0.2, 0.3):
+            ix.pruner_theta(th)
+            for p0 in (0.0, 0.1, 0.2, 0.3, 0.4, 0.5):
+                for p1 in (0.0, 0.5, 1.0, 2.0, 4.0):
+                    ix.set_predictor_params(lp["pmin"], lp["pmax"], lp["rmin"], lp["rmax"], p0, p1, lp["r0"], lp["r1"])
+                    vids, _, vnp, _ = ix.search_adaptive(Vd, k)
+                    rec = recall_at_10(torch, Xd, Vd, vids, vd_true, k)
+                    cost = float(vnp.double().mean().item())
+                    if rec >= TARGET_RECALL + 0.005 and (pb is None or cost < pb[0]):
+                        pb = (cost, rec, th, p0, p1)
+        if pb is not None:
+            pruned_state = (lp["pmin"], lp["pmax"], lp["rmin"], lp["rmax"], pb[3], pb[4], lp["r0"], lp["r1"])
+            ix.pruner_theta(pb[2])
+            ix.set_predictor_params(*pruned_state)
+            pids, _, pnp, prr = ix.search_adaptive(Qd, k)
+            p_rec = recall_at_10(torch, Xd, Qd, pids, true_d, k)
+            p_ms, p_stage, p_launches, p_clk = timed(lambda: ix.search_adaptive(Qd, k))
+            pruned = dict(ms=p_ms, stage=p_stage, launches=p_launches, recall=p_rec, theta=pb[2], state=pruned_state,
+                          mean_lists=float(pnp.double().mean().item()), mean_rerank=float(prr.double().mean().item()),
+                          params=dict(pmin=lp["pmin"], pmax=lp["pmax"], p0=pb[3], p1=pb[4]), train_loss=ploss,
+                          train_s=round(ptrain_s, 1), val_recall=pb[1], stats=ix.search_stats())
+        ix.pruner_theta(-1.0)
+        ix.set_predictor_params(*learned_state)
     # the same steps without per-stage events, and replayed from CUDA graphs
     # (ksc_plan: the whole search captured once)
     gst = torch.cuda.Stream()  # graph capture needs a stream of its own
@@ -341,18 +378,39 @@ def run_ours(args, rank, ws):
         with torch.cuda.stream(gst):
             lplan = ix.plan(CFG["nq"], k, adaptive=True)
         variants["learned graph"] = timed_bare(lambda: lplan.execute(Qd, ids, dists), gst)
+    prplan = None
+    ok_pruned = pruned is not None and pruned["recall"] >= TARGET_RECALL
+    if -max_over_ranks(-float(ok_pruned), ws) > 0.5:
+        ix.pruner_theta(pruned["theta"])
+        ix.set_predictor_params(*pruned["state"])
+        variants["pruned direct"] = timed_bare(lambda: ix.search_adaptive(Qd, k), st)
+        with torch.cuda.stream(gst):
+            prplan = ix.plan(CFG["nq"], k, adaptive=True)
+        variants["pruned graph"] = timed_bare(lambda: prplan.execute(Qd, ids, dists), gst)
     torch.cuda.synchronize()
     # headline: the fastest variant, the same choice on every rank (by the
     # slowest rank's time of each)
     names = sorted(variants)
     worst = [max_over_ranks(variants[n_][0], ws) for n_ in names]
     head = names[int(np.argmin(worst))]
-    use_learned = head.startswith("learned")
+    use_pruned = head.startswith("pruned")
+    use_learned = head.startswith("learned") or use_pruned
     use_graph = head.endswith("graph")
+    # the index state of the chosen path for the end-to-end leg (a plan
+    # re-captures itself after a state change)
+    if pruned is not None:
+        if use_pruned:
+            ix.pruner_theta(pruned["theta"])
+            ix.set_predictor_params(*pruned["state"])
+        elif learned_state is not None:
+            ix.pruner_theta(-1.0)
+            ix.set_predictor_params(*learned_state)
     ms_max = worst[names.index(head)]
     clocks = variants[head][1]
     value = weak_value(CFG["nq"], ws, ms_max)
-    if use_learned:
+    if use_pruned:
+        stage_avg, launches, stats = pruned["stage"], pruned["launches"], pruned["stats"]
+    elif use_learned:
         stage_avg, launches, stats = learned["stage"], learned["launches"], learned["stats"]
     else:
         stage_avg, launches, stats = plain_stage, plain_launches, stats
@@ -372,7 +430,7 @@ def run_ours(args, rank, ws):
             e0.record(es)
             Qtmp.copy_(Qpin, non_blocking=True)
             if use_graph:
-                r_ids, r_d = (lplan if use_learned else pplan).execute(Qtmp, ids, dists)
+                r_ids, r_d = (prplan if use_pruned else (lplan if use_learned else pplan)).execute(Qtmp, ids, dists)
             elif use_learned:
                 r_ids, r_d, _, _ = ix.search_adaptive(Qtmp, k)
             else:
@@ -434,6 +492,13 @@ def run_ours(args, rank, ws):
             "train_queries": args.ntrain, "train_loss": round(learned["train_loss"], 4),
             "train_s": learned["train_s"], "vs_plain": round(plain_ms / learned["ms"], 3),
             "stage_ms": {s_: round(v, 4) for s_, v in learned["stage"].items()}}
+        prn = None if pruned is None else {
+            "value": round(CFG["nq"] / (pruned["ms"] * 1e-3), 1), "ms_per_step": round(pruned["ms"], 4),
+            "recall@10": round(pruned["recall"], 4), "mean_lists_searched": round(pruned["mean_lists"], 3),
+            "mean_rerank": round(pruned["mean_rerank"], 1), "theta": pruned["theta"], "eq2": pruned["params"],
+            "validation_recall@10": round(pruned["val_recall"], 4), "train_loss": round(pruned["train_loss"], 4),
+            "train_s": pruned["train_s"], "vs_learned": round(learned["ms"] / pruned["ms"], 3),
+            "stage_ms": {s_: round(v, 4) for s_, v in pruned["stage"].items()}}
         out = {
             "metric": METRIC,
             "value": round(value, 1), "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
@@ -444,11 +509,13 @@ def run_ours(args, rank, ws):
                        "nlist": CFG["nlist"], "M": CFG["M"], "nbits": 4, "k": k, "rerank": R,
                        "nprobe": nprobe, "recall@10": recall, "nprobe_sweep": sweep,
                        "l2": "flushed (256 MB write) before every timed step", "parallelism": "replica x%d" % ws},
-            "recall@10": round(learned["recall"], 4) if use_learned else recall,
-            "path": ("learned nprobe (MLP + Eq. 2)" if use_learned else "plain fixed nprobe") +
+            "recall@10": round(pruned["recall"], 4) if use_pruned else (
+                round(learned["recall"], 4) if use_learned else recall),
+            "path": ("learned nprobe (MLP + Eq. 2) + predictive cluster pruning" if use_pruned else
+                     ("learned nprobe (MLP + Eq. 2)" if use_learned else "plain fixed nprobe")) +
                     (", replayed from a CUDA graph (ksc_plan)" if use_graph else ", direct calls"),
             "variants_ms": {n_: round(w_, 4) for n_, w_ in zip(names, worst)},
-            "plain": plain, "learned": lrn,
+            "plain": plain, "learned": lrn, "pruned": prn,
             "e2e": {"value": round(e2e, 1), "unit": "queries/s",
                     "h2d_bytes_per_step": int(Qh.nbytes), "d2h_bytes_per_step": int(ids_h.numel() * 12)},
             "gpu_launches": launches,
@@ -668,6 +735,7 @@ def main():
     ap.add_argument("--quick", action="store_true", help="profiling mode: timed steps only, at --nprobe")
     ap.add_argument("--nprobe", type=int, default=0)
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-nprobe path")
+    ap.add_argument("--no-prune", action="store_true", help="skip predictive cluster pruning")
     ap.add_argument("--ntrain", type=int, default=100_000)
     ap.add_argument("--lanes", type=int, default=0, help="scan lanes per query (0 auto; 4, 8, 16, 32)")
     ap.add_argument("--tile-blocks", type=int, default=0, help="scan tile length in blocks (0 auto)")

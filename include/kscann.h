@@ -348,7 +348,8 @@ int ksc_pruner_import_model(ksc_index* ix, const float* model_host);
  * the first nprobe_dev[q] (device, may be NULL: P for every query).  Outputs
  * (device, each may be NULL): feats_dev [nq x Pmax x KSC_PRUNE_FEATURES]
  * (rows at rank >= the query's nprobe are zero), prob_dev [nq x Pmax] (keep
- * probability; needs a model), probes_out_dev [nq x Pmax] the kept probes in
+ * probability; needs a model; rows at rank >= the query's nprobe are left
+ * unwritten), probes_out_dev [nq x Pmax] the kept probes in
  * rank order then -1, nprobe_out_dev [nq] their number (rank 0 and every
  * rank with probability > theta; needs a model).  Needs the statistics
  * (KSC_ESTATE otherwise). */
@@ -382,6 +383,13 @@ int ksc_train_pruner(ksc_index* ix, const float* Qtrain_dev, int64_t nt, const f
 int ksc_search_pruned(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t k, int32_t nprobe, int32_t rerank,
                       float theta, int64_t* ids_dev, float* dists_dev, int32_t* nprobe_out_dev,
                       const ksc_search_opts* opts, void* stream);
+
+/* Pruning inside ksc_search_adaptive (Alg. 2 order: predicted nprobe, then
+ * f_prune > theta over those lists; nprobe_dev there receives the number of
+ * lists searched).  theta < 0, the default, turns it off; KSC_ESTATE for
+ * theta >= 0 without statistics and model.  Captured adaptive plans
+ * re-capture before their next execution. */
+int ksc_pruner_theta(ksc_index* ix, float theta);
 
 /* Loss and gradient of the pruning MLP (16 -> 32 -> 32 -> 2, mean binary
  * cross-entropy of both heads) over x_dev [B x 16], y_dev [B x 2] at w_dev

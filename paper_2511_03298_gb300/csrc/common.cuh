@@ -445,6 +445,9 @@ struct Buffer {
 int ensure(Buffer& b, size_t bytes, cudaStream_t st);
 // Count of workspace reallocations so far (captured plans compare it).
 unsigned long long workspace_generation();
+// Makes captured plans re-capture before their next execution (state they
+// baked in, such as a buffer address or a parameter, has changed).
+void bump_workspace_generation();
 void release(Buffer& b);
 
 int num_sms();

@@ -28,6 +28,7 @@ const char* get_error() { return g_err; }
 
 static std::atomic<unsigned long long> g_ws_gen{0};
 unsigned long long workspace_generation() { return g_ws_gen.load(); }
+void bump_workspace_generation() { g_ws_gen++; }
 
 int ensure(Buffer& b, size_t bytes, cudaStream_t st) {
     if (bytes <= b.bytes && b.p) return KSC_OK;
@@ -327,7 +328,7 @@ int free_index_memory(ksc_index* ix) {
     Buffer* bufs[] = {&ix->ws_scores, &ix->ws_probes, &ix->ws_lut, &ix->ws_bias, &ix->ws_scale, &ix->ws_range,
                       &ix->ws_thr, &ix->ws_cnt, &ix->ws_cand, &ix->ws_topr, &ix->ws_nprobe, &ix->ws_rerank,
                       &ix->ws_items, &ix->ws_misc, &ix->ws_qbf16, &ix->ws_err, &ix->ws_feat, &ix->ws_rscore,
-                      &ix->ws_full, &ix->ws_topr2, &ix->ws_redo, &ix->ws_pprobes, &ix->ws_pn};
+                      &ix->ws_full, &ix->ws_topr2, &ix->ws_redo, &ix->ws_pprobes, &ix->ws_pn, &ix->ws_pprob};
     for (Buffer* b : bufs) release(*b);
     for (int i = 0; i <= KSC_NUM_STAGES; ++i)
         if (ix->ev[i]) cudaEventDestroy(ix->ev[i]);

@@ -57,6 +57,7 @@ struct ksc_index {
     float* pr_vecs = nullptr;   // [L x 3 x d] v1, v2, mean outlier offset
     float* pr_model = nullptr;  // [KSC_PRUNE_MODEL] weights, feature means, feature stds
     bool pr_have_stats = false;
+    float pr_theta = -1.f;      // applied by the adaptive search when >= 0
     // stage timing (ksc_profile_enable)
     bool prof = false;
     cudaEvent_t ev[KSC_NUM_STAGES + 1] = {};
@@ -65,7 +66,7 @@ struct ksc_index {
     // search workspace
     ksc::Buffer ws_scores, ws_probes, ws_lut, ws_bias, ws_scale, ws_range, ws_thr, ws_cnt,
         ws_cand, ws_topr, ws_nprobe, ws_rerank, ws_items, ws_misc, ws_qbf16, ws_err, ws_feat, ws_rscore, ws_full, ws_topr2,
-        ws_redo, ws_pprobes, ws_pn;
+        ws_redo, ws_pprobes, ws_pn, ws_pprob;
 };
 
 namespace ksc {

@@ -8,6 +8,7 @@
 // outliers and their mean offset, two principal axes) and a few dot products
 // with the query; the classifier is an MLP 16 -> 32 -> 32 -> 2 (head 0 used)
 // trained by the FP32 kernels of mlp.cu.
+#include <algorithm>
 #include <cmath>
 
 #include "index.cuh"
@@ -252,6 +253,7 @@ int prune_stats(ksc_index* ix, int iters, cudaStream_t st) {
     if (iters <= 0) iters = 30;
     if (!ix->pr_stats) KSC_CUDA(cudaMalloc(&ix->pr_stats, sizeof(float) * ix->L * PR_NSTAT));
     if (!ix->pr_vecs) KSC_CUDA(cudaMalloc(&ix->pr_vecs, sizeof(float) * ix->L * 3 * ix->d));
+    bump_workspace_generation();
     float* dscr = nullptr;
     KSC_CUDA(cudaMalloc(&dscr, sizeof(float) * ix->nblocks * 32 + 16));
     const size_t smem = sizeof(float) * (size_t)(4 + PR_WARPS) * ix->d;
@@ -299,158 +301,192 @@ struct PruneArgs {
     int32_t* nprobe_out;
 };
 
-// One warp per query.  Rows r < P_q are taken 32 at a time: the warp forms
-// the four dot products of each row together (|q - c|^2, <v1, q - c>,
-// <v2, q - c>, <outlier offset, q - c>), lane r & 31 keeps them, then each
-// lane turns its row into the 16 features, runs the MLP on them (weights in
-// shared memory, read by all lanes at once) and the warp appends the kept
-// probes in rank order by ballot.
+// Persistent CTAs (the model staged once per CTA in shared memory), each
+// taking groups of QB = 256 / Pmax queries, i.e. up to 256 (query, rank) rows:
+//  1. a warp per query forms the dot products of its rows over d with the
+//     lanes across d (coalesced; two rows per step, so their loads overlap):
+//     |q - c_p|^2, |q - c_{rank 0}|^2, <v1, q - c_p>, <v2, q - c_p>,
+//     <outlier offset, q - c_p>, kept in shared memory per row;
+//  2. a thread per row turns them into its 16 features and runs the MLP (all
+//     threads read the same weight at a time: a shared-memory broadcast).
+// Rows r >= P_q are skipped.  Keep probability into prob, features into feats.
+constexpr int PR_ROWS = 256;  // rows per group = threads per CTA
+
 template <int DPL>
-__global__ void __launch_bounds__(PR_WARPS * 32) k_prune_rows(PruneArgs A) {
-    __shared__ float sw[KSC_PRUNE_MODEL];
+__global__ void __launch_bounds__(PR_ROWS, 2) k_prune_rows(PruneArgs A) {
+    __shared__ __align__(16) float sm[KSC_PRUNE_MODEL];
+    __shared__ float sx[PR_NF][PR_ROWS];  // each row's standardised features
+    __shared__ float sdot[5][PR_ROWS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (A.model)
-        for (int e = threadIdx.x; e < KSC_PRUNE_MODEL; e += blockDim.x) sw[e] = A.model[e];
+    if (A.model) {
+        for (int e = threadIdx.x; e < KSC_PRUNE_MODEL; e += blockDim.x) sm[e] = A.model[e];
+        __syncthreads();
+        if (threadIdx.x < PR_NF) sm[PR_NP + PR_NF + threadIdx.x] = 1.f / sm[PR_NP + PR_NF + threadIdx.x];
+    }
     __syncthreads();
-    const int64_t q = (int64_t)blockIdx.x * PR_WARPS + warp;
-    if (q >= A.nq) return;
-    const int d = A.d;
-    int Pq = A.nprobe ? A.nprobe[q] : A.P;
-    Pq = Pq < 1 ? 1 : (Pq > A.Pmax ? A.Pmax : Pq);
-    const int32_t* pr = A.probes + q * A.Pmax;
-    float qv[DPL];
-#pragma unroll
-    for (int i = 0; i < DPL; ++i) {
-        const int t = lane + 32 * i;
-        qv[i] = t < d ? A.Q[q * d + t] : 0.f;
-    }
-    // the nearest probe: D0 and its radius
-    float D0 = 0.f, rho0 = 0.f;
-    {
-        const int p0 = pr[0];
-        if (p0 >= 0 && p0 < A.L) {
-            float s = 0.f;
-#pragma unroll
-            for (int i = 0; i < DPL; ++i) {
-                const int t = lane + 32 * i;
-                if (t < d) {
-                    const float e = __fsub_rn(qv[i], A.c_mean[(int64_t)p0 * d + t]);
-                    s = fmaf(e, e, s);
-                }
-            }
-            D0 = sqrtf(warp_sum_f(s));
-            rho0 = A.stats[(int64_t)p0 * PR_NSTAT + 1];
-        }
-    }
-    const float g = fmaxf(D0, 1e-9f);
-    const float* W1 = sw;
+    const float* W1 = sm;
     const float* b1 = W1 + PR_H * PR_NF;
     const float* W2 = b1 + PR_H;
     const float* b2 = W2 + PR_H * PR_H;
-    const float* W3 = b2 + PR_H;
-    const float* b3 = W3 + 2 * PR_H;
-    const float* mu = sw + PR_NP;
-    const float* sd = mu + PR_NF;
-    int kept = 0;
-    for (int r0 = 0; r0 < Pq; r0 += 32) {
-        float mD2 = 0.f, m1 = 0.f, m2 = 0.f, mo = 0.f;
-        const int nr = min(32, Pq - r0);
-        for (int j = 0; j < nr; ++j) {
-            const int p = pr[r0 + j];
-            if (p < 0 || p >= A.L) continue;
-            const float* cp = A.c_mean + (int64_t)p * d;
-            const float* vp = A.vecs + (int64_t)p * 3 * d;
-            float s = 0.f, a1 = 0.f, a2 = 0.f, ao = 0.f;
+    const float* W3 = b2 + PR_H;  // row 0 = head 0
+    const float* mu = sm + PR_NP;
+    const float* inv = mu + PR_NF;  // 1 / std
+    const int d = A.d, Pmax = A.Pmax;
+    const int QB = PR_ROWS / Pmax;  // >= 1 (Pmax <= PR_ROWS)
+    const int64_t ngroups = (A.nq + QB - 1) / QB;
+    for (int64_t grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+        const int64_t q0 = grp * QB;
+        // 1. dot products, a warp per query
+        for (int qi = warp; qi < QB; qi += PR_ROWS / 32) {
+            const int64_t q = q0 + qi;
+            if (q >= A.nq) break;
+            int Pq = A.nprobe ? A.nprobe[q] : A.P;
+            Pq = Pq < 1 ? 1 : (Pq > Pmax ? Pmax : Pq);
+            const int32_t* pr = A.probes + q * Pmax;
+            const int p0 = pr[0];
+            const bool ok0 = p0 >= 0 && p0 < A.L;
+            float qv[DPL], e0s = 0.f;
 #pragma unroll
             for (int i = 0; i < DPL; ++i) {
                 const int t = lane + 32 * i;
-                if (t < d) {
-                    const float e = __fsub_rn(qv[i], cp[t]);
-                    s = fmaf(e, e, s);
-                    a1 = fmaf(vp[t], e, a1);
-                    a2 = fmaf(vp[d + t], e, a2);
-                    ao = fmaf(vp[2 * d + t], e, ao);
+                qv[i] = t < d ? A.Q[q * d + t] : 0.f;
+                if (t < d && ok0) {
+                    const float e0 = __fsub_rn(qv[i], A.c_mean[(int64_t)p0 * d + t]);
+                    e0s = fmaf(e0, e0, e0s);
                 }
             }
-            s = warp_sum_f(s);
-            a1 = warp_sum_f(a1);
-            a2 = warp_sum_f(a2);
-            ao = warp_sum_f(ao);
-            if (lane == j) {
-                mD2 = s;
-                m1 = a1;
-                m2 = a2;
-                mo = ao;
+            e0s = warp_sum_f(e0s);
+            for (int r = 0; r < Pq; r += 2) {
+                float v[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int rr = r + h;
+                    const int p = rr < Pq ? pr[rr] : -1;
+                    if (p < 0 || p >= A.L) continue;
+                    const float* cp = A.c_mean + (int64_t)p * d;
+                    const float* vp = A.vecs + (int64_t)p * 3 * d;
+#pragma unroll
+                    for (int i = 0; i < DPL; ++i) {
+                        const int t = lane + 32 * i;
+                        if (t < d) {
+                            const float e = __fsub_rn(qv[i], cp[t]);
+                            v[h][0] = fmaf(e, e, v[h][0]);
+                            v[h][1] = fmaf(vp[t], e, v[h][1]);
+                            v[h][2] = fmaf(vp[d + t], e, v[h][2]);
+                            v[h][3] = fmaf(vp[2 * d + t], e, v[h][3]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) v[h][c] = warp_sum_f(v[h][c]);
+                if (lane == 0) {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        if (r + h >= Pq) break;
+                        const int row = qi * Pmax + r + h;
+                        sdot[0][row] = v[h][0];
+                        sdot[1][row] = e0s;
+                        sdot[2][row] = v[h][1];
+                        sdot[3][row] = v[h][2];
+                        sdot[4][row] = v[h][3];
+                    }
+                }
             }
         }
-        const int r = r0 + lane;
-        bool keep = false;
-        if (lane < nr) {
-            const int p = pr[r];
+        __syncthreads();
+        // 2. features and the MLP, a thread per row
+        const int t = threadIdx.x;
+        const int qi = t / Pmax, r = t - qi * Pmax;
+        const int64_t q = q0 + qi;
+        if (qi < QB && q < A.nq) {
+            int Pq = A.nprobe ? A.nprobe[q] : A.P;
+            Pq = Pq < 1 ? 1 : (Pq > Pmax ? Pmax : Pq);
+            const int64_t row = q * Pmax + r;
             float f[PR_NF];
 #pragma unroll
             for (int e = 0; e < PR_NF; ++e) f[e] = 0.f;
+            const int32_t* pr = A.probes + q * Pmax;
+            const int p = r < Pq ? pr[r] : -1, p0 = pr[0];
             if (p >= 0 && p < A.L) {
+                const bool ok0 = p0 >= 0 && p0 < A.L;
                 const float* stp = A.stats + (int64_t)p * PR_NSTAT;
-                const float D = sqrtf(mD2), Dg = fmaxf(D, 1e-9f), rho = stp[1];
-                const float u1 = m1 / Dg, u2 = m2 / Dg, uo = mo / Dg;
+                const float D0 = ok0 ? sqrtf(sdot[1][t]) : 0.f;
+                const float rho0 = ok0 ? A.stats[(int64_t)p0 * PR_NSTAT + 1] : 0.f;
+                const float ig = 1.f / fmaxf(D0, 1e-9f);
+                const float D = sqrtf(sdot[0][t]), iD = 1.f / fmaxf(D, 1e-9f), rho = stp[1];
+                const float u1 = sdot[2][t] * iD * ig, u2 = sdot[3][t] * iD * ig;
                 f[0] = D / fmaxf(rho, 1e-9f);
-                f[1] = D / g;
-                f[2] = (D - rho) / g;
-                f[3] = logf(1.f + stp[0]);
-                f[4] = rho / g;
-                f[5] = stp[2] / g;
-                f[6] = stp[3] / g;
+                f[1] = D * ig;
+                f[2] = (D - rho) * ig;
+                f[3] = __logf(1.f + stp[0]);
+                f[4] = rho * ig;
+                f[5] = stp[2] * ig;
+                f[6] = stp[3] * ig;
                 f[7] = stp[4];
                 f[8] = stp[5];
                 f[9] = stp[6];
                 f[10] = stp[7];
                 f[11] = stp[8];
-                f[12] = stp[9] * u1 * u1 / (g * g);
-                f[13] = stp[10] * u2 * u2 / (g * g);
-                f[14] = uo / g;
+                f[12] = stp[9] * u1 * u1;
+                f[13] = stp[10] * u2 * u2;
+                f[14] = sdot[4][t] * iD * ig;
                 f[15] = D0 / fmaxf(rho0, 1e-9f);
             }
             if (A.feats) {
-                float* fo = A.feats + (q * A.Pmax + r) * PR_NF;
 #pragma unroll
-                for (int e = 0; e < PR_NF; ++e) fo[e] = f[e];
+                for (int e = 0; e < PR_NF; e += 4)
+                    *reinterpret_cast<float4*>(A.feats + row * PR_NF + e) = make_float4(f[e], f[e + 1], f[e + 2], f[e + 3]);
             }
-            if (A.model) {
+            if (A.model && r < Pq) {
 #pragma unroll
-                for (int e = 0; e < PR_NF; ++e) f[e] = (f[e] - mu[e]) / sd[e];
+                for (int e = 0; e < PR_NF; ++e) sx[e][t] = (f[e] - mu[e]) * inv[e];
+                // layer 1 input by input (ascending), all 32 units in registers
                 float h1[PR_H];
 #pragma unroll
-                for (int a = 0; a < PR_H; ++a) {
-                    float acc = b1[a];
+                for (int a = 0; a < PR_H; ++a) h1[a] = b1[a];
+#pragma unroll 1
+                for (int e = 0; e < PR_NF; ++e) {
+                    const float x = sx[e][t];
 #pragma unroll
-                    for (int e = 0; e < PR_NF; ++e) acc = fmaf(f[e], W1[a * PR_NF + e], acc);
-                    h1[a] = fmaxf(acc, 0.f);
+                    for (int a = 0; a < PR_H; ++a) h1[a] = fmaf(x, W1[a * PR_NF + e], h1[a]);
                 }
-                float z = b3[0];
+                float zz = W3[2 * PR_H];
+#pragma unroll 1
                 for (int a = 0; a < PR_H; ++a) {
                     float acc = b2[a];
 #pragma unroll
-                    for (int e = 0; e < PR_H; ++e) acc = fmaf(h1[e], W2[a * PR_H + e], acc);
-                    z = fmaf(fmaxf(acc, 0.f), W3[a], z);
+                    for (int e = 0; e < PR_H; ++e) acc = fmaf(fmaxf(h1[e], 0.f), W2[a * PR_H + e], acc);
+                    zz = fmaf(fmaxf(acc, 0.f), W3[a], zz);
                 }
-                const float pk = 1.f / (1.f + expf(-z));
-                if (A.prob) A.prob[q * A.Pmax + r] = pk;
-                keep = r == 0 || pk > A.theta;
+                A.prob[row] = 1.f / (1.f + __expf(-zz));
             }
         }
-        if (A.probes_out) {
-            const uint32_t m = __ballot_sync(0xffffffffu, keep);
-            if (keep) A.probes_out[q * A.Pmax + kept + __popc(m & ((1u << lane) - 1u))] = pr[r];
-            kept += __popc(m);
-        }
+        __syncthreads();  // sdot is refilled by the next group
     }
-    if (A.probes_out) {
-        for (int r = kept + lane; r < A.Pmax; r += 32) A.probes_out[q * A.Pmax + r] = -1;
-        if (lane == 0 && A.nprobe_out) A.nprobe_out[q] = kept;
+}
+
+// Kept probes: one warp per query, 32 ranks at a time by ballot (rank 0 and
+// every rank whose keep probability exceeds theta), in rank order, then -1.
+__global__ void k_prune_compact(const int32_t* __restrict__ probes, int64_t nq, int Pmax,
+                                const int32_t* __restrict__ nprobe, int P, const float* __restrict__ prob,
+                                float theta, int32_t* __restrict__ probes_out, int32_t* __restrict__ nprobe_out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (q >= nq) return;
+    int Pq = nprobe ? nprobe[q] : P;
+    Pq = Pq < 1 ? 1 : (Pq > Pmax ? Pmax : Pq);
+    int kept = 0;
+    for (int r0 = 0; r0 < Pq; r0 += 32) {
+        const int r = r0 + lane;
+        const bool keep = r < Pq && (r == 0 || prob[q * Pmax + r] > theta);
+        const uint32_t m = __ballot_sync(0xffffffffu, keep);
+        if (keep) probes_out[q * Pmax + kept + __popc(m & ((1u << lane) - 1u))] = probes[q * Pmax + r];
+        kept += __popc(m);
     }
-    if (A.feats)  // rows beyond the query's nprobe
-        for (int e = Pq * PR_NF + lane; e < A.Pmax * PR_NF; e += 32) A.feats[q * A.Pmax * PR_NF + e] = 0.f;
+    for (int r = kept + lane; r < Pmax; r += 32) probes_out[q * Pmax + r] = -1;
+    if (lane == 0 && nprobe_out) nprobe_out[q] = kept;
 }
 
 int prune_rows(ksc_index* ix, const float* Q, int64_t nq, const int32_t* probes, int Pmax, const int32_t* nprobe,
@@ -461,14 +497,26 @@ int prune_rows(ksc_index* ix, const float* Q, int64_t nq, const int32_t* probes,
     KSC_CHECK_STATE(!need_model || ix->pr_model, "no pruning model");
     KSC_CHECK_ARG(!nprobe_out || probes_out, "nprobe_out needs probes_out");
     if (nq == 0) return KSC_OK;
+    if (probes_out && !prob) {  // the probabilities only feed the compaction
+        KSC_TRY(ensure(ix->ws_pprob, sizeof(float) * nq * Pmax, st));
+        prob = (float*)ix->ws_pprob.p;
+    }
     PruneArgs A{Q, nq, ix->d, ix->L, ix->c_mean, probes, Pmax, nprobe, P, ix->pr_stats, ix->pr_vecs,
                 need_model ? ix->pr_model : nullptr, theta, feats, prob, probes_out, nprobe_out};
-    const unsigned grid = (unsigned)((nq + PR_WARPS - 1) / PR_WARPS);
-    if (ix->d <= 128) k_prune_rows<4><<<grid, PR_WARPS * 32, 0, st>>>(A);
-    else if (ix->d <= 256) k_prune_rows<8><<<grid, PR_WARPS * 32, 0, st>>>(A);
-    else if (ix->d <= 512) k_prune_rows<16><<<grid, PR_WARPS * 32, 0, st>>>(A);
-    else k_prune_rows<32><<<grid, PR_WARPS * 32, 0, st>>>(A);
+    KSC_CHECK_ARG(Pmax <= PR_ROWS, "pruning needs nprobe <= %d", PR_ROWS);
+    const int QB = PR_ROWS / Pmax;
+    const int64_t groups = (nq + QB - 1) / QB;
+    const unsigned grid = (unsigned)std::min<int64_t>(groups, (int64_t)num_sms() * 2);  // 2 CTAs fit per SM
+    if (ix->d <= 128) k_prune_rows<4><<<grid, PR_ROWS, 0, st>>>(A);
+    else if (ix->d <= 256) k_prune_rows<8><<<grid, PR_ROWS, 0, st>>>(A);
+    else if (ix->d <= 512) k_prune_rows<16><<<grid, PR_ROWS, 0, st>>>(A);
+    else k_prune_rows<32><<<grid, PR_ROWS, 0, st>>>(A);
     KSC_LAUNCH_CHECK();
+    if (probes_out) {
+        k_prune_compact<<<(unsigned)((nq + 7) / 8), 256, 0, st>>>(probes, nq, Pmax, nprobe, P, prob, theta,
+                                                                   probes_out, nprobe_out);
+        KSC_LAUNCH_CHECK();
+    }
     return KSC_OK;
 }
 

@@ -3382,8 +3382,21 @@ int ksc_search_adaptive(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t k
     pl.nprobe_q = np_q;
     pl.rerank_q = r_q;
     pl.Pq_max = std::min(prm.pmax, Pr);
+    const int32_t* sprobes = probes;
+    if (ix->pr_theta >= 0.f && ix->pr_model && ix->pr_have_stats) {
+        // Alg. 2: predictive pruning of the predicted nprobe lists
+        KSC_TRY(ensure(ix->ws_pprobes, sizeof(int32_t) * nq * Pr, st));
+        KSC_TRY(ensure(ix->ws_pn, sizeof(int32_t) * nq, st));
+        int32_t* kept = (int32_t*)ix->ws_pprobes.p;
+        int32_t* pn = (int32_t*)ix->ws_pn.p;
+        KSC_TRY(prune_rows(ix, Q_dev, nq, probes, Pr, np_q, Pr, ix->pr_theta, nullptr, nullptr, kept, pn, st));
+        ix->launches += 2;
+        sprobes = kept;
+        np_q = pn;
+        pl.nprobe_q = pn;
+    }
     set_tiles(ix, pl, nq, 0.5 * (prm.pmin + prm.pmax), opts);
-    KSC_TRY(search_from_probes(ix, Q_dev, pl, probes, ids_dev, dists_dev, nullptr, nullptr, st));
+    KSC_TRY(search_from_probes(ix, Q_dev, pl, sprobes, ids_dev, dists_dev, nullptr, nullptr, st));
     if (nprobe_dev) KSC_CUDA(cudaMemcpyAsync(nprobe_dev, np_q, sizeof(int32_t) * nq, cudaMemcpyDeviceToDevice, st));
     if (rerank_dev) KSC_CUDA(cudaMemcpyAsync(rerank_dev, r_q, sizeof(int32_t) * nq, cudaMemcpyDeviceToDevice, st));
     return KSC_OK;
@@ -3604,6 +3617,15 @@ int ksc_pruner_import_model(ksc_index* ix, const float* model_host) {
     KSC_CHECK_ARG(ix && model_host, "null argument");
     if (!ix->pr_model) KSC_CUDA(cudaMalloc(&ix->pr_model, sizeof(float) * KSC_PRUNE_MODEL));
     KSC_CUDA(cudaMemcpy(ix->pr_model, model_host, sizeof(float) * KSC_PRUNE_MODEL, cudaMemcpyHostToDevice));
+    bump_workspace_generation();
+    return KSC_OK;
+}
+
+int ksc_pruner_theta(ksc_index* ix, float theta) {
+    KSC_CHECK_ARG(ix, "null index");
+    KSC_CHECK_STATE(theta < 0.f || (ix->pr_have_stats && ix->pr_model), "no pruning model");
+    ix->pr_theta = theta;
+    bump_workspace_generation();
     return KSC_OK;
 }
 
@@ -3758,6 +3780,7 @@ int ksc_train_pruner(ksc_index* ix, const float* Qtrain_dev, int64_t nt, const f
         if (ix->pr_model) cudaFree(ix->pr_model);
         ix->pr_model = model;
         model = nullptr;
+        bump_workspace_generation();
     } while (0);
     void* tmp[] = {feats, lab, Y, dists, model, w, g, m, v, xb, yb, lossd, probes, ids, idx};
     for (void* p : tmp)

@@ -95,6 +95,7 @@ _SIGS = {
     "ksc_train_pruner": [_vp, _vp, _i64, _vp, _i32, _i32, _i32, _vp, _vp, _vp],
     "ksc_search_pruned": [_vp, _vp, _i64, _i32, _i32, _i32, C.c_float, _vp, _vp, _vp, _vp, _vp],
     "ksc_prune_mlp_grad": [_vp, _vp, _vp, _i64, _vp, _vp, _vp],
+    "ksc_pruner_theta": [_vp, C.c_float],
     "ksc_last_error": [],
     "ksc_version": [],
 }
@@ -387,6 +388,10 @@ class Index:
                                       _dptr(kth, torch.float32, "kth"), k, P, R, C.byref(opts), _stream(stream),
                                       C.byref(loss)))
         return loss.value
+
+    def pruner_theta(self, theta):
+        """Pruning threshold of the adaptive search (< 0: off)."""
+        _check(lib().ksc_pruner_theta(self._h, float(theta)))
 
     def search_pruned(self, Q, k, nprobe, rerank, theta, opts=None, out=None, stream=None):
         """ksc_search with the lists the pruning model rejects at theta

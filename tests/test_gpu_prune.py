@@ -190,3 +190,41 @@ def test_trained_pruner_drops_lists_and_keeps_recall(env):
     print("pruned: mean lists %.2f of %d, recall %.4f (unpruned %.4f), loss %.4f" % (mean_p, P, rec, rec_full, loss))
     assert mean_p < 0.8 * P
     assert rec >= rec_full - 0.03
+
+
+def test_adaptive_search_prunes_its_predicted_lists(env):
+    torch, ksc, ix, Q, g = env
+    k, R = 10, 100
+    T = synth.queries(1, 2000, stream=8)
+    _, tdist = oracle.exact_knn(T, ix["X"], k)
+    Td = torch.from_numpy(T).cuda()
+    kth = torch.from_numpy(tdist[:, k - 1].astype(np.float32)).cuda()
+    g.train_predictor(Td, kth, k=k, epochs=2)
+    g.train_pruner(Td, kth, k=k, P=16, R=R, epochs=2, batch=512)
+    # fixed rerank depth, so the pruned lists alone decide the result
+    g.set_predictor_params(2, 16, R, R, 0.2, 0.5, 0.0, 0.0)
+    Qd = torch.from_numpy(Q).cuda()
+    g.pruner_theta(-1.0)
+    _, _, npred, _ = g.search_adaptive(Qd, k)
+    theta = 0.3
+    g.pruner_theta(theta)
+    ids, dists, nsearch, _ = g.search_adaptive(Qd, k)
+    probes = g.rank_lists(Qd, 16, want_scores=False)[0]
+    kept = g.prune_probes(Qd, probes, nprobe=npred, theta=theta)
+    np.testing.assert_array_equal(nsearch.cpu().numpy(), kept["nprobe"].cpu().numpy())
+    assert np.all(nsearch.cpu().numpy() <= npred.cpu().numpy())
+    i2, d2 = g.search_with_probes(Qd, kept["probes"], k, R)[:2]
+    assert torch.equal(ids, i2) and torch.equal(dists, d2)
+    # a captured adaptive plan (capture needs a stream of its own) follows
+    # the threshold too, re-capturing after it changes
+    torch.cuda.synchronize()
+    s_ = torch.cuda.Stream()
+    with torch.cuda.stream(s_):
+        pl = g.plan(len(Q), k, adaptive=True)
+        i3, d3 = [t.clone() for t in pl.execute(Qd)]
+        g.pruner_theta(-1.0)
+        i4, d4 = [t.clone() for t in pl.execute(Qd)]
+    s_.synchronize()
+    assert torch.equal(i3, ids) and torch.equal(d3, dists)
+    i5, d5, _, _ = g.search_adaptive(Qd, k)
+    assert torch.equal(i4, i5) and torch.equal(d4, d5)
