@@ -961,3 +961,34 @@ int orc_prune_features(const float* Q, int64_t nq, int32_t d, const float* c_mea
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Component filtration (Sec. 4.3; Alg. 1 / Alg. 2 FilterComponents)  */
+/* ------------------------------------------------------------------ */
+/*
+ * Per dimension t of X [n x d] (FP64, two passes): mean mu_t, population
+ * standard deviation sigma_t, and frac[t] = the fraction of the n values that
+ * are 0 or within one standard deviation of the mean (|x - mu_t| <= sigma_t).
+ * Dimensions whose fraction exceeds the threshold carry little information
+ * and are dropped (oracle.py: component_keep).
+ */
+int orc_component_stats(const float* X, int64_t n, int32_t d, double* mu, double* sigma, double* frac) {
+#pragma omp parallel for schedule(static)
+    for (int32_t t = 0; t < d; ++t) {
+        double s = 0.0;
+        for (int64_t i = 0; i < n; ++i) s += (double)X[i * d + t];
+        const double m = n > 0 ? s / (double)n : 0.0;
+        double v = 0.0;
+        for (int64_t i = 0; i < n; ++i) { double e = (double)X[i * d + t] - m; v += e * e; }
+        const double sd = n > 0 ? sqrt(v / (double)n) : 0.0;
+        int64_t c = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            const double x = (double)X[i * d + t];
+            if (x == 0.0 || fabs(x - m) <= sd) c++;
+        }
+        mu[t] = m;
+        sigma[t] = sd;
+        frac[t] = n > 0 ? (double)c / (double)n : 1.0;
+    }
+    return 0;
+}

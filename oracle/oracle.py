@@ -20,6 +20,7 @@ tests/test_oracle_pins.py):
   eq2           Eq. 2                                              pinned
   mlp_*         Sec. 4.2.1-4.2.2 predictor (MLP stand-in)          pinned
   prune_*       Sec. 4.2.3 / Table 4 cluster pruning, Alg. 2       pinned
+  component_*   Sec. 4.3 component filtration, Alg. 1 / Alg. 2     pinned
 """
 import ctypes as C
 import os
@@ -78,6 +79,7 @@ def lib():
             "orc_prune_stats": (C.c_int, [_f32p, _i64, _i32, _f32p, _i32, _i32p, _i32, _f64p, _f64p]),
             "orc_prune_features": (C.c_int, [_f32p, _i64, _i32, _f32p, _i32, _i32p, _i32, _vp, _i32,
                                              _f64p, _f64p, _f64p]),
+            "orc_component_stats": (C.c_int, [_f32p, _i64, _i32, _f64p, _f64p, _f64p]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -376,3 +378,37 @@ def prune_labels(ids, dists, kth, assign, probes, P, ip=False, tol=1e-5):
         for r in range(min(P, Pmax)):
             y[q, r] = 1.0 if int(probes[q, r]) in lists else 0.0
     return y
+
+
+# -------------------------------------------------------------- component filtration
+def component_stats(X):
+    """Per-dimension mean, std and the fraction of values that are 0 or within
+    one std of the mean (Sec. 4.3), FP64."""
+    X = _c(X, np.float32)
+    n, d = X.shape
+    mu, sd, fr = np.zeros(d), np.zeros(d), np.zeros(d)
+    lib().orc_component_stats(X, n, d, mu, sd, fr)
+    return mu, sd, fr
+
+
+def component_keep(frac, threshold):
+    """Dimensions kept by FilterComponents (Alg. 1): those whose fraction is
+    at most the threshold, ascending."""
+    return np.nonzero(np.asarray(frac) <= threshold)[0].astype(np.int32)
+
+
+def component_dims(kept, M):
+    """The kept dimensions followed by -1 (a zero dimension) up to a multiple
+    of M, so that the M subspaces divide the filtered vectors."""
+    kept = np.asarray(kept, np.int32)
+    dp = -(-len(kept) // M) * M
+    return np.concatenate([kept, -np.ones(dp - len(kept), np.int32)])
+
+
+def filter_rows(A, dims):
+    """A[:, dims] with zeros at the -1 entries."""
+    A = np.asarray(A, np.float32)
+    out = np.zeros((A.shape[0], len(dims)), np.float32)
+    sel = dims >= 0
+    out[:, sel] = A[:, dims[sel]]
+    return out

@@ -15,9 +15,15 @@ These stand in for the paper's datasets (Table 5), which are not available:
            power-law weights (GLOVE-100 / TEXT-TO-IMAGE shape), inner product
   deep   : 10M x 96 unit-norm mixture, 10000 components with Zipf(1.1) weights
            (DEEP10M shape), L2 on normalised data
+  fashion: 60k x 784 28x28 image-like vectors, integers 0..255 (FASHION-MNIST
+           shape, L2): 100 smooth templates (sums of 3-6 Gaussian bumps on the
+           inner 24x24 pixels), each image a template times a brightness
+           U[0.7, 1.3] plus N(0, 25^2) pixel noise, rounded and clipped; the
+           2-pixel border frame is 0 except for stray pixels (probability
+           0.002, U{1..40}), like the uniform backgrounds of Sec. 4.3
 Queries come from the same mixture with their own seed.  Seeds: base 1000+c,
 queries 2000+c, training queries 3000+c, per-query nprobe 4000+c, build
-permutation 5000+c (c = config number 1..5).  Both the CUDA library and the
+permutation 5000+c (c = config number 1..6).  Both the CUDA library and the
 CPU oracle receive these arrays as inputs; this module computes nothing else.
 """
 import numpy as np
@@ -33,6 +39,8 @@ CONFIGS = {
             metric="ip", spherical=True),
     4: dict(name="deep", n=10_000_000, d=96, nq=16_384, L=8192, M=48, k=100, R=1000, nprobe=64,
             metric="l2", spherical=True),
+    6: dict(name="fashion", n=60_000, d=784, nq=10_000, L=256, M=196, k=10, R=100, nprobe=8,
+            metric="l2", spherical=False),
 }
 NPROBE_GRID = (8, 12, 16, 24, 32, 48, 64, 96, 128)
 
@@ -64,6 +72,19 @@ def _mixture_params(cfg):
         mu = _normalise(rng.normal(size=(ncomp, d)))
         w = np.arange(1, ncomp + 1, dtype=np.float64) ** -1.1
         return dict(mu=mu, w=w / w.sum())
+    if cfg == 6:
+        ncomp = 100
+        yy, xx = np.mgrid[0:28, 0:28]
+        tpl = np.zeros((ncomp, 28, 28))
+        for c_ in range(ncomp):
+            for _ in range(rng.integers(3, 7)):
+                cy, cx = rng.uniform(5.0, 22.0, size=2)
+                sy, sx = rng.uniform(2.0, 6.0, size=2)
+                tpl[c_] += rng.uniform(100.0, 255.0) * np.exp(-0.5 * (((yy - cy) / sy) ** 2 + ((xx - cx) / sx) ** 2))
+        inner = np.zeros((28, 28), bool)
+        inner[2:26, 2:26] = True
+        tpl = np.clip(tpl, 0.0, 255.0) * inner
+        return dict(mu=tpl.reshape(ncomp, d), inner=inner.reshape(d), w=np.full(ncomp, 1 / ncomp))
     raise ValueError(cfg)
 
 
@@ -80,6 +101,11 @@ def _draw(cfg, prm, n, rng, chunk=1 << 20):
             x = np.clip(np.rint(prm["mu"][comp] + 20.0 * prm["s"] * eps), 0, 255)
         elif cfg == 3:
             x = _normalise(prm["mu"][comp] + prm["sig"][comp] * eps)
+        elif cfg == 6:
+            bright = rng.uniform(0.7, 1.3, size=(m, 1))
+            x = np.clip(np.rint(prm["mu"][comp] * bright + 25.0 * eps), 0, 255) * prm["inner"]
+            stray = (rng.uniform(size=(m, d)) < 0.002) & ~prm["inner"]
+            x = np.where(stray, rng.integers(1, 41, size=(m, d)), x)
         else:
             x = _normalise(prm["mu"][comp] + 0.05 * eps)
         out[b:b + m] = x
