@@ -68,6 +68,10 @@ typedef struct {
                                   min(n, 65536).  NULL: the library draws one (seed). */
     uint64_t seed;             /* used when perm_host is NULL */
     int32_t build_graph;       /* 1: build the per-list 32-NN graphs of Sec. 4.4 */
+    float filter_threshold;    /* component filtration (Sec. 4.3), 0 = off: dimensions in which
+                                  more than this fraction of the values are 0 or within one
+                                  standard deviation of the mean are dropped (see
+                                  ksc_index_dims) */
 } ksc_build_opts;
 
 /* Build an IVF-PQ index from X_dev [n x d] fp32 (device).  nlist = L IVF lists,
@@ -396,6 +400,33 @@ int ksc_pruner_theta(ksc_index* ix, float theta);
  * [KSC_PRUNE_NPARAMS]; grad_dev [KSC_PRUNE_NPARAMS], loss_dev [1] (device). */
 int ksc_prune_mlp_grad(const float* w_dev, const float* x_dev, const float* y_dev, int64_t B, float* grad_dev,
                        float* loss_dev, void* stream);
+
+/* ------------------------------------------------------------------ */
+/* Component filtration (Sec. 4.3; Alg. 1 / Alg. 2 FilterComponents)  */
+/* ------------------------------------------------------------------ */
+/* With ksc_build_opts.filter_threshold > 0 the build keeps the dimensions
+ * whose fraction (ksc_component_stats) is at most the threshold, in
+ * ascending order, and builds the index on those: the sub-vector width stays
+ * d / M, so the filtered index has ceil(kept / (d / M)) subspaces, the last
+ * completed with zero dimensions.  Queries are still passed with all d
+ * dimensions; every search drops the same ones before ranking, tables and
+ * scan, and re-ranks with the full query against the full vectors (Alg. 2).
+ * ksc_index_info and ksc_index_export then describe the filtered (working)
+ * index, whose X holds the kept dimensions.  Not with ksc_index_import or
+ * ksc_compute_luts_noalloc (KSC_EUNSUPPORTED). */
+
+/* The working dimension list of the index: d_full_host receives the query
+ * width d; dims_host (may be NULL) receives, for each working dimension, the
+ * query dimension it takes (-1: a zero padding dimension).  Without
+ * filtration the list is 0..d-1.  Blocking. */
+int ksc_index_dims(ksc_index* ix, int32_t* dims_host, int32_t* d_full_host);
+
+/* Per-dimension statistics of X_dev [n x d] (device): mean mu_dev, population
+ * standard deviation sd_dev and the fraction of values that are 0 or within
+ * one standard deviation of the mean frac_dev ([d] doubles each, device),
+ * FP64 with a fixed summation order. */
+int ksc_component_stats(const float* X_dev, int64_t n, int32_t d, double* mu_dev, double* sd_dev, double* frac_dev,
+                        void* stream);
 
 /* Device status word of the last search on this index: 0 = clean, else a
  * bitwise OR of KSC_STATUS_* (blocking read). */

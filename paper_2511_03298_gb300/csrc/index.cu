@@ -322,13 +322,14 @@ int free_index_memory(ksc_index* ix) {
     void* ptrs[] = {ix->X, ix->c_rank, ix->c_rank_sq, ix->c_mean, ix->codebook, ix->list_boff, ix->list_n,
                     ix->blk_ids, ix->blk_codes, ix->assign, ix->graph, ix->entry, ix->status, ix->stats,
                     ix->c_rank_bf16, ix->mlp_w, ix->blk_list, ix->nbr_pos, ix->nbr_codes, ix->entry_pos,
-                    ix->X_bf16, ix->X_fp8, ix->X_scale, ix->pr_stats, ix->pr_vecs, ix->pr_model};
+                    ix->X_bf16, ix->X_fp8, ix->X_scale, ix->pr_stats, ix->pr_vecs, ix->pr_model, ix->dims,
+                    ix->X_rr};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     Buffer* bufs[] = {&ix->ws_scores, &ix->ws_probes, &ix->ws_lut, &ix->ws_bias, &ix->ws_scale, &ix->ws_range,
                       &ix->ws_thr, &ix->ws_cnt, &ix->ws_cand, &ix->ws_topr, &ix->ws_nprobe, &ix->ws_rerank,
                       &ix->ws_items, &ix->ws_misc, &ix->ws_qbf16, &ix->ws_err, &ix->ws_feat, &ix->ws_rscore,
-                      &ix->ws_full, &ix->ws_topr2, &ix->ws_redo, &ix->ws_pprobes, &ix->ws_pn, &ix->ws_pprob};
+                      &ix->ws_full, &ix->ws_topr2, &ix->ws_redo, &ix->ws_pprobes, &ix->ws_pn, &ix->ws_pprob, &ix->ws_qf};
     for (Buffer* b : bufs) release(*b);
     for (int i = 0; i <= KSC_NUM_STAGES; ++i)
         if (ix->ev[i]) cudaEventDestroy(ix->ev[i]);
@@ -541,9 +542,73 @@ int ksc_index_export(const ksc_index* ix, ksc_index_arrays* a) {
     return KSC_OK;
 }
 
+// Component filtration (Sec. 4.3; Alg. 1 FilterComponents): the index is
+// built on the kept dimensions -- the sub-vector width d / M is kept, so the
+// filtered index has ceil(kept / (d / M)) subspaces, the last completed with
+// zero dimensions -- and holds the full vectors for the re-rank.
+static int build_filtered(const float* X_dev, int64_t n, int32_t d, int32_t nlist, int32_t M, int32_t nbits,
+                          ksc_metric metric, const ksc_build_opts* opts, void* stream, ksc_index** out) {
+    KSC_TRY(check_shape(n, d, nlist, M));
+    cudaStream_t st = as_stream(stream);
+    const double thr = opts->filter_threshold;
+    std::vector<double> frac(d);
+    double* stats = nullptr;
+    KSC_CUDA(cudaMalloc(&stats, sizeof(double) * 3 * d));
+    int rc = component_stats(X_dev, n, d, stats, stats + d, stats + 2 * d, st);
+    if (rc == KSC_OK && cudaMemcpy(frac.data(), stats + 2 * d, sizeof(double) * d, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        set_error("reading the component statistics failed");
+        rc = KSC_ECUDA;
+    }
+    cudaFree(stats);
+    KSC_TRY(rc);
+    std::vector<int32_t> dims;
+    for (int t = 0; t < d; ++t)
+        if (frac[t] <= thr) dims.push_back(t);
+    KSC_CHECK_ARG(!dims.empty(), "component filtration kept no dimension (threshold %g)", thr);
+    const int dsub = d / M;
+    const int Mf = (int)((dims.size() + dsub - 1) / dsub);
+    while ((int)dims.size() < Mf * dsub) dims.push_back(-1);
+    const int dw = Mf * dsub;
+    float* Xw = nullptr;
+    int32_t* dims_dev = nullptr;
+    KSC_CUDA(cudaMalloc(&dims_dev, sizeof(int32_t) * dw));
+    cudaError_t e = cudaMemcpy(dims_dev, dims.data(), sizeof(int32_t) * dw, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&Xw, sizeof(float) * n * dw);
+    if (e != cudaSuccess) {
+        cudaFree(dims_dev);
+        set_error("component filtration: %s", cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? KSC_ENOMEM : KSC_ECUDA;
+    }
+    rc = gather_dims(X_dev, n, d, dims_dev, dw, Xw, st);
+    ksc_build_opts inner = *opts;
+    inner.filter_threshold = 0.f;
+    ksc_index* ix = nullptr;
+    if (rc == KSC_OK) rc = ksc_build_index(Xw, n, dw, nlist, Mf, nbits, metric, &inner, stream, &ix);
+    cudaStreamSynchronize(st);
+    cudaFree(Xw);
+    if (rc == KSC_OK) {
+        ix->dims = dims_dev;
+        dims_dev = nullptr;
+        ix->h_dims = dims;
+        ix->d_rr = d;
+        e = cudaMalloc(&ix->X_rr, sizeof(float) * n * d);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ix->X_rr, X_dev, sizeof(float) * n * d, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) {
+            set_error("component filtration: %s", cudaGetErrorString(e));
+            rc = e == cudaErrorMemoryAllocation ? KSC_ENOMEM : KSC_ECUDA;
+            ksc_index_free(ix);
+            ix = nullptr;
+        }
+    }
+    if (dims_dev) cudaFree(dims_dev);
+    if (rc == KSC_OK) *out = ix;
+    return rc;
+}
+
 int ksc_build_index(const float* X_dev, int64_t n, int32_t d, int32_t nlist, int32_t M, int32_t nbits,
                     ksc_metric metric, const ksc_build_opts* opts, void* stream, ksc_index** out) {
     KSC_CHECK_ARG(X_dev && out, "null argument");
+    if (opts && opts->filter_threshold > 0.f) return build_filtered(X_dev, n, d, nlist, M, nbits, metric, opts, stream, out);
     if (nbits != 4) {
         set_error("only 4-bit PQ codes (K = 16) are supported, got nbits = %d", nbits);
         return KSC_EUNSUPPORTED;
@@ -643,3 +708,17 @@ int ksc_build_index(const float* X_dev, int64_t n, int32_t d, int32_t nlist, int
 }
 
 }  // extern "C"
+
+extern "C" int ksc_index_dims(ksc_index* ix, int32_t* dims_host, int32_t* d_full_host) {
+    KSC_CHECK_ARG(ix && d_full_host, "null argument");
+    *d_full_host = ix->X_rr ? ix->d_rr : ix->d;
+    if (dims_host)
+        for (int j = 0; j < ix->d; ++j) dims_host[j] = ix->X_rr ? ix->h_dims[j] : j;
+    return KSC_OK;
+}
+
+extern "C" int ksc_component_stats(const float* X_dev, int64_t n, int32_t d, double* mu_dev, double* sd_dev,
+                                   double* frac_dev, void* stream) {
+    KSC_CHECK_ARG(X_dev && mu_dev && sd_dev && frac_dev && n > 0 && d > 0, "bad argument");
+    return ksc::component_stats(X_dev, n, d, mu_dev, sd_dev, frac_dev, ksc::as_stream(stream));
+}

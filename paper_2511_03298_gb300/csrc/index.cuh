@@ -58,6 +58,12 @@ struct ksc_index {
     float* pr_model = nullptr;  // [KSC_PRUNE_MODEL] weights, feature means, feature stds
     bool pr_have_stats = false;
     float pr_theta = -1.f;      // applied by the adaptive search when >= 0
+    // component filtration (Sec. 4.3): the index lives on the kept dimensions
+    // (d, X); queries arrive with d_rr dimensions and the re-rank reads X_rr
+    int32_t* dims = nullptr;     // [d] query dimension of each working one (-1: zero)
+    std::vector<int32_t> h_dims;
+    float* X_rr = nullptr;       // [n x d_rr] full vectors (null: no filtration)
+    int32_t d_rr = 0;
     // stage timing (ksc_profile_enable)
     bool prof = false;
     cudaEvent_t ev[KSC_NUM_STAGES + 1] = {};
@@ -66,8 +72,14 @@ struct ksc_index {
     // search workspace
     ksc::Buffer ws_scores, ws_probes, ws_lut, ws_bias, ws_scale, ws_range, ws_thr, ws_cnt,
         ws_cand, ws_topr, ws_nprobe, ws_rerank, ws_items, ws_misc, ws_qbf16, ws_err, ws_feat, ws_rscore, ws_full, ws_topr2,
-        ws_redo, ws_pprobes, ws_pn, ws_pprob;
+        ws_redo, ws_pprobes, ws_pn, ws_pprob, ws_qf;
 };
+
+// The vectors the exact re-rank reads and their width: the full vectors when
+// component filtration dropped dimensions (Alg. 2 re-ranks with the
+// unfiltered query), else X.
+inline const float* rr_X(const ksc_index* ix) { return ix->X_rr ? ix->X_rr : ix->X; }
+inline int rr_d(const ksc_index* ix) { return ix->X_rr ? ix->d_rr : ix->d; }
 
 namespace ksc {
 // Fill blk_ids / blk_codes / list tables from unpacked codes [n x M] (device)
@@ -104,6 +116,9 @@ int prune_labels(ksc_index* ix, const int64_t* ids, const float* dists, int64_t 
                  const int32_t* probes, int Pmax, int P, float* label, cudaStream_t st);
 int prune_standardise(float* x, int64_t rows, float* model, cudaStream_t st);
 int prune_targets(const float* lab, int64_t rows, float* y, cudaStream_t st);
+// Component filtration (filter.cu): column statistics, dimension gather.
+int component_stats(const float* X, int64_t n, int d, double* mu, double* sd, double* frac, cudaStream_t st);
+int gather_dims(const float* A, int64_t rows, int d, const int32_t* dims, int dw, float* out, cudaStream_t st);
 // Per-list 32-NN graphs and entry points for the hybrid search (Sec. 4.4).
 int build_graph(ksc_index* ix, cudaStream_t st);
 // Search form (nbr_pos, nbr_codes, entry_pos) of graph / entry (hybrid.cu).

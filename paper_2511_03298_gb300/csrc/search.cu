@@ -2548,18 +2548,19 @@ static int compute_luts(ksc_index* ix, const float* Q, int64_t nq, const int32_t
     return KSC_OK;
 }
 
-// BF16 / FP8 copies of X, made on first use.
+// BF16 / FP8 copies of the re-rank vectors, made on first use.
 static int ensure_lowp(ksc_index* ix, int prec, cudaStream_t st) {
+    const int dr = rr_d(ix);
     if (prec == 1 && !ix->X_bf16) {
-        KSC_CUDA(cudaMalloc(&ix->X_bf16, sizeof(uint16_t) * ix->n * ix->d));
-        k_x_lowp<<<(unsigned)((ix->n + 7) / 8), 256, 0, st>>>(ix->X, ix->n, ix->d, 1, (uint16_t*)ix->X_bf16, nullptr,
+        KSC_CUDA(cudaMalloc(&ix->X_bf16, sizeof(uint16_t) * ix->n * dr));
+        k_x_lowp<<<(unsigned)((ix->n + 7) / 8), 256, 0, st>>>(rr_X(ix), ix->n, dr, 1, (uint16_t*)ix->X_bf16, nullptr,
                                                               nullptr);
         KSC_LAUNCH_CHECK();
     }
     if (prec == 2 && !ix->X_fp8) {
-        KSC_CUDA(cudaMalloc(&ix->X_fp8, (size_t)ix->n * ix->d));
+        KSC_CUDA(cudaMalloc(&ix->X_fp8, (size_t)ix->n * dr));
         KSC_CUDA(cudaMalloc(&ix->X_scale, sizeof(float) * ix->n));
-        k_x_lowp<<<(unsigned)((ix->n + 7) / 8), 256, 0, st>>>(ix->X, ix->n, ix->d, 2, nullptr, (uint8_t*)ix->X_fp8,
+        k_x_lowp<<<(unsigned)((ix->n + 7) / 8), 256, 0, st>>>(rr_X(ix), ix->n, dr, 2, nullptr, (uint8_t*)ix->X_fp8,
                                                               ix->X_scale);
         KSC_LAUNCH_CHECK();
     }
@@ -2594,8 +2595,25 @@ static int run_scan(const Plan& pl, int M, const ScanArgs& A, const ScanOut& O, 
 // a2 .. a6 for given probe lists.  Stages: 1 work lists, 2 LUTs, 3 scan of
 // the nearest list(s) + threshold, 4 scan of the other lists, 5 select,
 // 6 rerank.
+// Queries in the index's working dimensions: with component filtration
+// (Sec. 4.3, Alg. 2 FilterComponents) the kept dimensions of Q, gathered into
+// a workspace buffer (zeros in the padding); otherwise Q itself.
+static int work_queries(ksc_index* ix, const float* Q, int64_t nq, cudaStream_t st, const float** Qw) {
+    *Qw = Q;
+    if (!ix->dims || nq == 0) return KSC_OK;
+    KSC_TRY(ensure(ix->ws_qf, sizeof(float) * nq * ix->d, st));
+    KSC_TRY(gather_dims(Q, nq, ix->d_rr, ix->dims, ix->d, (float*)ix->ws_qf.p, st));
+    ix->launches++;
+    *Qw = (const float*)ix->ws_qf.p;
+    return KSC_OK;
+}
+
+// Q: the queries in the index's (working) dimensions; Qr: the same queries
+// with all their dimensions for the re-rank (null: Q; they differ only under
+// component filtration).
 static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, const int32_t* probes,
-                              int64_t* ids, float* dists, uint64_t* cand_out, int32_t* ncand_out, cudaStream_t st) {
+                              int64_t* ids, float* dists, uint64_t* cand_out, int32_t* ncand_out, cudaStream_t st,
+                              const float* Qr = nullptr) {
     const int64_t nq = pl.nq;
     const int M = ix->M, L = ix->L;
     const int QG = 32 / pl.G;
@@ -2760,8 +2778,12 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
         KSC_LAUNCH_CHECK();
     }
     // 6. exact rerank (precision variant: a BF16 / FP8 re-rank of the widened
-    //    shortlist first, then FP32 of its best Rf)
+    //    shortlist first, then FP32 of its best Rf), with the full queries and
+    //    vectors (Alg. 2: q_init)
     mark(ix, 6, st);
+    if (!Qr) Qr = Q;
+    const float* Xr = rr_X(ix);
+    const int dr = rr_d(ix);
     const uint64_t* rr_keys = topr;
     int rr_R = pl.Rmax;
     const int32_t* rr_q = pl.rerank_q;
@@ -2771,7 +2793,7 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
         uint64_t* topr2 = (uint64_t*)ix->ws_topr2.p;
         const size_t smem = sizeof(uint64_t) * pow2_ceil(pl.Rmax < 2 ? 2 : pl.Rmax);
         cudaFuncSetAttribute(k_rerank_lowp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_rerank_lowp<<<(unsigned)nq, 256, smem, st>>>(Q, ix->d, ix->metric == KSC_IP, pl.prec,
+        k_rerank_lowp<<<(unsigned)nq, 256, smem, st>>>(Qr, dr, ix->metric == KSC_IP, pl.prec,
                                                        (const uint16_t*)ix->X_bf16, (const uint8_t*)ix->X_fp8,
                                                        ix->X_scale, topr, pl.Rmax, pl.rerank_q, pl.Rfix, pl.k, pl.Rf,
                                                        topr2);
@@ -2781,17 +2803,17 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
         rr_R = pl.Rf;
         rr_q = nullptr;
     }
-    if (pl.k <= 32 && rr_R <= RW_MAXR && ix->d <= 128 && (ix->d & 3) == 0 && warp_per_query(nq)) {
+    if (pl.k <= 32 && rr_R <= RW_MAXR && dr <= 128 && (dr & 3) == 0 && warp_per_query(nq)) {
         const size_t smem = sizeof(uint64_t) * RW_WARPS * rr_R;
         cudaFuncSetAttribute(k_rerank_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_rerank_w<<<(unsigned)((nq + RW_WARPS - 1) / RW_WARPS), RW_WARPS * 32, smem, st>>>(
-            Q, ix->X, ix->d, ix->metric == KSC_IP, rr_keys, rr_R, rr_q, rr_R, pl.k, nq, ids, dists);
+            Qr, Xr, dr, ix->metric == KSC_IP, rr_keys, rr_R, rr_q, rr_R, pl.k, nq, ids, dists);
         ix->launches++;
         KSC_LAUNCH_CHECK();
     } else {
         const size_t smem = sizeof(uint64_t) * pow2_ceil(rr_R < 2 ? 2 : rr_R);
         cudaFuncSetAttribute(k_rerank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_rerank<<<(unsigned)nq, 256, smem, st>>>(Q, ix->X, ix->d, ix->metric == KSC_IP, rr_keys, rr_R, rr_q, rr_R,
+        k_rerank<<<(unsigned)nq, 256, smem, st>>>(Qr, Xr, dr, ix->metric == KSC_IP, rr_keys, rr_R, rr_q, rr_R,
                                                   pl.k, ids, dists);
         ix->launches++;
         KSC_LAUNCH_CHECK();
@@ -2879,7 +2901,10 @@ int ksc_rank_lists(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t P, int
     KSC_CHECK_ARG(P >= 1 && P <= ix->L && P <= MAX_NPROBE, "P must be in [1, min(nlist, %d)]", MAX_NPROBE);
     if (nq == 0) return KSC_OK;
     KSC_CHECK_ARG(Q_dev && probes_dev, "null argument");
-    return rank_lists(ix, Q_dev, nq, nullptr, P, P, probes_dev, scores_dev, false, as_stream(stream));
+    cudaStream_t st = as_stream(stream);
+    const float* Qw;
+    KSC_TRY(work_queries(ix, Q_dev, nq, st, &Qw));
+    return rank_lists(ix, Qw, nq, nullptr, P, P, probes_dev, scores_dev, false, st);
 }
 
 int ksc_list_scores(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t tensor_cores, float* scores_dev,
@@ -2890,7 +2915,9 @@ int ksc_list_scores(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t tenso
     cudaStream_t st = as_stream(stream);
     const bool exact = !tensor_cores || !tc_rank_supported(ix);
     float* err = nullptr;
-    KSC_TRY(list_scores(ix, Q_dev, nq, exact, scores_dev, &err, st));
+    const float* Qw;
+    KSC_TRY(work_queries(ix, Q_dev, nq, st, &Qw));
+    KSC_TRY(list_scores(ix, Qw, nq, exact, scores_dev, &err, st));
     if (err_dev) KSC_CUDA(cudaMemcpyAsync(err_dev, err, sizeof(float) * nq, cudaMemcpyDeviceToDevice, st));
     return KSC_OK;
 }
@@ -2901,7 +2928,10 @@ int ksc_compute_luts(ksc_index* ix, const float* Q_dev, int64_t nq, const int32_
     KSC_CHECK_ARG(P >= 1 && P <= ix->L, "P must be in [1, nlist]");
     if (nq == 0) return KSC_OK;
     KSC_CHECK_ARG(Q_dev && probes_dev && lut_dev && bias_dev && scale_dev, "null argument");
-    return compute_luts(ix, Q_dev, nq, probes_dev, nullptr, P, P, lut_dev, bias_dev, scale_dev, as_stream(stream));
+    cudaStream_t st = as_stream(stream);
+    const float* Qw;
+    KSC_TRY(work_queries(ix, Q_dev, nq, st, &Qw));
+    return compute_luts(ix, Qw, nq, probes_dev, nullptr, P, P, lut_dev, bias_dev, scale_dev, st);
 }
 
 int ksc_search_with_probes(ksc_index* ix, const float* Q_dev, int64_t nq, const int32_t* probes_dev, int32_t P,
@@ -2917,7 +2947,9 @@ int ksc_search_with_probes(ksc_index* ix, const float* Q_dev, int64_t nq, const 
     KSC_CUDA(cudaMemsetAsync(ix->stats, 0, sizeof(unsigned long long) * 4, st));
     ix->launches = 0;
     mark(ix, 0, st);
-    return search_from_probes(ix, Q_dev, pl, probes_dev, ids_dev, dists_dev, cand_dev, ncand_dev, st);
+    const float* Qw;
+    KSC_TRY(work_queries(ix, Q_dev, nq, st, &Qw));
+    return search_from_probes(ix, Qw, pl, probes_dev, ids_dev, dists_dev, cand_dev, ncand_dev, st, Q_dev);
 }
 
 int ksc_search(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t k, int32_t nprobe, int32_t rerank,
@@ -2934,8 +2966,10 @@ int ksc_search(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t k, int32_t
     KSC_CUDA(cudaMemsetAsync(ix->stats, 0, sizeof(unsigned long long) * 4, st));
     ix->launches = 0;
     mark(ix, 0, st);
-    KSC_TRY(rank_lists(ix, Q_dev, nq, nullptr, pl.Pmax, pl.Pmax, probes, nullptr, pl.rank_exact, st));
-    return search_from_probes(ix, Q_dev, pl, probes, ids_dev, dists_dev, nullptr, nullptr, st);
+    const float* Qw;
+    KSC_TRY(work_queries(ix, Q_dev, nq, st, &Qw));
+    KSC_TRY(rank_lists(ix, Qw, nq, nullptr, pl.Pmax, pl.Pmax, probes, nullptr, pl.rank_exact, st));
+    return search_from_probes(ix, Qw, pl, probes, ids_dev, dists_dev, nullptr, nullptr, st, Q_dev);
 }
 
 int ksc_search_varprobe(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t k, const int32_t* nprobe_dev,
@@ -2956,8 +2990,10 @@ int ksc_search_varprobe(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t k
     KSC_CUDA(cudaMemsetAsync(ix->stats, 0, sizeof(unsigned long long) * 4, st));
     ix->launches = 0;
     mark(ix, 0, st);
-    KSC_TRY(rank_lists(ix, Q_dev, nq, nprobe_dev, pl.Pmax, pl.Pmax, probes, nullptr, pl.rank_exact, st));
-    return search_from_probes(ix, Q_dev, pl, probes, ids_dev, dists_dev, nullptr, nullptr, st);
+    const float* Qw;
+    KSC_TRY(work_queries(ix, Q_dev, nq, st, &Qw));
+    KSC_TRY(rank_lists(ix, Qw, nq, nprobe_dev, pl.Pmax, pl.Pmax, probes, nullptr, pl.rank_exact, st));
+    return search_from_probes(ix, Qw, pl, probes, ids_dev, dists_dev, nullptr, nullptr, st, Q_dev);
 }
 
 int ksc_profile_enable(ksc_index* ix, int32_t on) {
@@ -3022,7 +3058,7 @@ int ksc_pair_distances(ksc_index* ix, const float* Q_dev, int64_t nq, const int6
     KSC_CHECK_ARG(Q_dev && ids_dev && out_dev && c > 0, "bad argument");
     cudaStream_t st = as_stream(stream);
     KSC_TRY(ensure_lowp(ix, precision, st));
-    k_pair_dist<<<(unsigned)nq, 256, 0, st>>>(Q_dev, nq, ix->d, ix->metric == KSC_IP, precision, ix->X,
+    k_pair_dist<<<(unsigned)nq, 256, 0, st>>>(Q_dev, nq, rr_d(ix), ix->metric == KSC_IP, precision, rr_X(ix),
                                               (const uint16_t*)ix->X_bf16, (const uint8_t*)ix->X_fp8, ix->X_scale,
                                               ids_dev, c, out_dev);
     KSC_LAUNCH_CHECK();
@@ -3068,6 +3104,10 @@ extern "C" int ksc_compute_luts_noalloc(ksc_index* ix, const float* Q_dev, int64
                                         int32_t P, uint8_t* lut_dev, int32_t* bias_dev, float* scale_dev,
                                         void* stream) {
     KSC_CHECK_ARG(ix, "null index");
+    if (ix->dims) {
+        set_error("ksc_compute_luts_noalloc needs an index without component filtration");
+        return KSC_EUNSUPPORTED;
+    }
     KSC_CHECK_ARG(P >= 1 && P <= ix->L, "P must be in [1, nlist]");
     KSC_CHECK_ARG(nq >= 0 && nq <= KSC_NOALLOC_MAX_NQ,
                   "nq = %lld exceeds the fixed scratch of ksc_compute_luts_noalloc (at most %d queries per call)",
@@ -3124,7 +3164,8 @@ static float median_of(std::vector<int32_t> v) {
 
 // Smallest grid value per query whose search finds >= target hits; queries
 // that never reach it take the last grid value.
-static int label_queries(ksc_index* ix, const float* Q, int64_t nq, const float* kth, const int32_t* probes, int Pr,
+static int label_queries(ksc_index* ix, const float* Q, const float* Qr, int64_t nq, const float* kth,
+                         const int32_t* probes, int Pr,
                          const std::vector<int32_t>& grid, bool over_rerank, const int32_t* nprobe_dev, int R_fixed,
                          int k, int target, std::vector<int32_t>& label, cudaStream_t st) {
     std::vector<int32_t> hits_h(nq);
@@ -3155,7 +3196,7 @@ static int label_queries(ksc_index* ix, const float* Q, int64_t nq, const float*
                 }
                 pl.nprobe_q = cnst;
             }
-            if ((rc = search_from_probes(ix, Q, pl, probes, ids, dists, nullptr, nullptr, st))) break;
+            if ((rc = search_from_probes(ix, Q, pl, probes, ids, dists, nullptr, nullptr, st, Qr))) break;
             if ((rc = mlp_hits(dists, nq, k, kth, ix->metric == KSC_IP, hits, st))) break;
             if (cudaMemcpyAsync(hits_h.data(), hits, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
                 cudaStreamSynchronize(st) != cudaSuccess) {
@@ -3198,7 +3239,9 @@ int ksc_query_features(ksc_index* ix, const float* Q_dev, int64_t nq, float* fea
     KSC_CHECK_ARG(Q_dev && feats_dev, "null argument");
     cudaStream_t st = as_stream(stream);
     KSC_TRY(ensure(ix->ws_probes, sizeof(int32_t) * nq, st));
-    return rank_and_features(ix, Q_dev, nq, 1, (int32_t*)ix->ws_probes.p, feats_dev, st);
+    const float* Qw;
+    KSC_TRY(work_queries(ix, Q_dev, nq, st, &Qw));
+    return rank_and_features(ix, Qw, nq, 1, (int32_t*)ix->ws_probes.p, feats_dev, st);
 }
 
 int ksc_predictor_params(ksc_index* ix, const ksc_adaptive_params* prm) {
@@ -3271,15 +3314,17 @@ int ksc_train_predictor(ksc_index* ix, const float* Qtrain_dev, int64_t nt, cons
         // 1. labels from the plain search, chunk by chunk
         for (int64_t c0 = 0; c0 < nt && rc == KSC_OK; c0 += chunk) {
             const int64_t nc = std::min(chunk, nt - c0);
-            const float* Qc = Qtrain_dev + c0 * ix->d;
-            if ((rc = rank_and_features(ix, Qc, nc, Pr, probes, feats + c0 * KSC_MLP_FEATURES, st))) break;
+            const float* Qc = Qtrain_dev + c0 * rr_d(ix);
+            const float* Qcw;
+            if ((rc = work_queries(ix, Qc, nc, st, &Qcw))) break;
+            if ((rc = rank_and_features(ix, Qcw, nc, Pr, probes, feats + c0 * KSC_MLP_FEATURES, st))) break;
             std::vector<int32_t> ln, lr_;
-            if ((rc = label_queries(ix, Qc, nc, kth_dev + c0, probes, Pr, grid, false, nullptr, R_lab, k, target, ln,
-                                    st)))
+            if ((rc = label_queries(ix, Qcw, Qc, nc, kth_dev + c0, probes, Pr, grid, false, nullptr, R_lab, k, target,
+                                    ln, st)))
                 break;
             T_CUDA(cudaMemcpy(lab_dev, ln.data(), sizeof(int32_t) * nc, cudaMemcpyHostToDevice));
-            if ((rc = label_queries(ix, Qc, nc, kth_dev + c0, probes, Pr, rgrid, true, lab_dev, 0, k, target, lr_,
-                                    st)))
+            if ((rc = label_queries(ix, Qcw, Qc, nc, kth_dev + c0, probes, Pr, rgrid, true, lab_dev, 0, k, target,
+                                    lr_, st)))
                 break;
             std::copy(ln.begin(), ln.end(), lab_n.begin() + c0);
             std::copy(lr_.begin(), lr_.end(), lab_r.begin() + c0);
@@ -3376,7 +3421,9 @@ int ksc_search_adaptive(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t k
     int32_t* r_q = (int32_t*)ix->ws_rerank.p;
     ix->launches = 0;
     mark(ix, 0, st);
-    KSC_TRY(rank_and_features(ix, Q_dev, nq, Pr, probes, feats, st));
+    const float* Qw;
+    KSC_TRY(work_queries(ix, Q_dev, nq, st, &Qw));
+    KSC_TRY(rank_and_features(ix, Qw, nq, Pr, probes, feats, st));
     KSC_TRY(mlp_infer(ix->mlp_w, feats, nq, prm, nullptr, np_q, r_q, st));
     ix->launches++;
     pl.nprobe_q = np_q;
@@ -3389,14 +3436,14 @@ int ksc_search_adaptive(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t k
         KSC_TRY(ensure(ix->ws_pn, sizeof(int32_t) * nq, st));
         int32_t* kept = (int32_t*)ix->ws_pprobes.p;
         int32_t* pn = (int32_t*)ix->ws_pn.p;
-        KSC_TRY(prune_rows(ix, Q_dev, nq, probes, Pr, np_q, Pr, ix->pr_theta, nullptr, nullptr, kept, pn, st));
+        KSC_TRY(prune_rows(ix, Qw, nq, probes, Pr, np_q, Pr, ix->pr_theta, nullptr, nullptr, kept, pn, st));
         ix->launches += 2;
         sprobes = kept;
         np_q = pn;
         pl.nprobe_q = pn;
     }
     set_tiles(ix, pl, nq, 0.5 * (prm.pmin + prm.pmax), opts);
-    KSC_TRY(search_from_probes(ix, Q_dev, pl, sprobes, ids_dev, dists_dev, nullptr, nullptr, st));
+    KSC_TRY(search_from_probes(ix, Qw, pl, sprobes, ids_dev, dists_dev, nullptr, nullptr, st, Q_dev));
     if (nprobe_dev) KSC_CUDA(cudaMemcpyAsync(nprobe_dev, np_q, sizeof(int32_t) * nq, cudaMemcpyDeviceToDevice, st));
     if (rerank_dev) KSC_CUDA(cudaMemcpyAsync(rerank_dev, r_q, sizeof(int32_t) * nq, cudaMemcpyDeviceToDevice, st));
     return KSC_OK;
@@ -3497,13 +3544,13 @@ int ksc_plan_create(ksc_index* ix, int64_t nq, int32_t k, int32_t nprobe, int32_
     pl->adaptive = adaptive;
     if (opts) { pl->opts = *opts; pl->has_opts = true; }
     int rc = KSC_OK;
-    if (cudaMalloc(&pl->Q, sizeof(float) * nq * ix->d) != cudaSuccess ||
+    if (cudaMalloc(&pl->Q, sizeof(float) * nq * rr_d(ix)) != cudaSuccess ||
         cudaMalloc(&pl->ids, sizeof(int64_t) * nq * k) != cudaSuccess ||
         cudaMalloc(&pl->dists, sizeof(float) * nq * k) != cudaSuccess) {
         set_error("plan buffer allocation failed");
         rc = KSC_ENOMEM;
     }
-    if (rc == KSC_OK && cudaMemsetAsync(pl->Q, 0, sizeof(float) * nq * ix->d, st) != cudaSuccess) rc = KSC_ECUDA;
+    if (rc == KSC_OK && cudaMemsetAsync(pl->Q, 0, sizeof(float) * nq * rr_d(ix), st) != cudaSuccess) rc = KSC_ECUDA;
     if (rc == KSC_OK) rc = plan_capture(pl, st);
     if (rc != KSC_OK) {
         ksc_plan_free(pl);
@@ -3526,7 +3573,7 @@ int ksc_plan_execute(ksc_plan* pl, const float* Q_dev, int64_t* ids_dev, float* 
     cudaStream_t st = as_stream(stream);
     KSC_CHECK_ARG(stream != nullptr, "plans need a non-default stream (graph capture)");
     if (Q_dev && Q_dev != pl->Q)
-        KSC_CUDA(cudaMemcpyAsync(pl->Q, Q_dev, sizeof(float) * pl->nq * pl->ix->d, cudaMemcpyDeviceToDevice, st));
+        KSC_CUDA(cudaMemcpyAsync(pl->Q, Q_dev, sizeof(float) * pl->nq * rr_d(pl->ix), cudaMemcpyDeviceToDevice, st));
     if (workspace_generation() != pl->gen) KSC_TRY(plan_capture(pl, st));
     KSC_CUDA(cudaGraphLaunch(pl->exec, st));
     if (ids_dev && ids_dev != pl->ids)
@@ -3635,8 +3682,11 @@ int ksc_prune_probes(ksc_index* ix, const float* Q_dev, int64_t nq, const int32_
     KSC_CHECK_ARG(ix && nq >= 0 && Pmax >= 1 && (nprobe_dev || (P >= 1 && P <= Pmax)), "bad argument");
     if (nq == 0) return KSC_OK;
     KSC_CHECK_ARG(Q_dev && probes_dev, "null argument");
-    return prune_rows(ix, Q_dev, nq, probes_dev, Pmax, nprobe_dev, P, theta, feats_dev, prob_dev, probes_out_dev,
-                      nprobe_out_dev, as_stream(stream));
+    cudaStream_t st = as_stream(stream);
+    const float* Qw;
+    KSC_TRY(work_queries(ix, Q_dev, nq, st, &Qw));
+    return prune_rows(ix, Qw, nq, probes_dev, Pmax, nprobe_dev, P, theta, feats_dev, prob_dev, probes_out_dev,
+                      nprobe_out_dev, st);
 }
 
 int ksc_prune_labels(ksc_index* ix, const int64_t* ids_dev, const float* dists_dev, int64_t nq, int32_t k,
@@ -3674,15 +3724,17 @@ int ksc_search_pruned(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t k, 
     KSC_CUDA(cudaMemsetAsync(ix->stats, 0, sizeof(unsigned long long) * 4, st));
     ix->launches = 0;
     mark(ix, 0, st);
-    KSC_TRY(rank_lists(ix, Q_dev, nq, nullptr, pl.Pmax, pl.Pmax, probes, nullptr, pl.rank_exact, st));
+    const float* Qw;
+    KSC_TRY(work_queries(ix, Q_dev, nq, st, &Qw));
+    KSC_TRY(rank_lists(ix, Qw, nq, nullptr, pl.Pmax, pl.Pmax, probes, nullptr, pl.rank_exact, st));
     // Alg. 2: keep rank 0 and the ranks with f_prune > theta, in rank order
-    KSC_TRY(prune_rows(ix, Q_dev, nq, probes, pl.Pmax, nullptr, pl.Pmax, theta, nullptr, nullptr, kept, pn, st));
+    KSC_TRY(prune_rows(ix, Qw, nq, probes, pl.Pmax, nullptr, pl.Pmax, theta, nullptr, nullptr, kept, pn, st));
     ix->launches++;
     pl.nprobe_q = pn;
     set_tiles(ix, pl, nq, 0.75 * pl.Pmax, opts);
     if (nprobe_out_dev)
         KSC_CUDA(cudaMemcpyAsync(nprobe_out_dev, pn, sizeof(int32_t) * nq, cudaMemcpyDeviceToDevice, st));
-    return search_from_probes(ix, Q_dev, pl, kept, ids_dev, dists_dev, nullptr, nullptr, st);
+    return search_from_probes(ix, Qw, pl, kept, ids_dev, dists_dev, nullptr, nullptr, st, Q_dev);
 }
 
 #define T_CUDA(call) { cudaError_t e_ = (call); if (e_ != cudaSuccess) { set_error("%s: %s", #call, cudaGetErrorString(e_)); rc = KSC_ECUDA; break; } }
@@ -3717,13 +3769,15 @@ int ksc_train_pruner(ksc_index* ix, const float* Qtrain_dev, int64_t nt, const f
         //    the plain search of those lists, features
         for (int64_t c0 = 0; c0 < nt && rc == KSC_OK; c0 += chunk) {
             const int64_t nc = std::min(chunk, nt - c0);
-            const float* Qc = Qtrain_dev + c0 * ix->d;
-            if ((rc = rank_lists(ix, Qc, nc, nullptr, P, P, probes, nullptr, false, st))) break;
+            const float* Qc = Qtrain_dev + c0 * rr_d(ix);
+            const float* Qcw;
+            if ((rc = work_queries(ix, Qc, nc, st, &Qcw))) break;
+            if ((rc = rank_lists(ix, Qcw, nc, nullptr, P, P, probes, nullptr, false, st))) break;
             Plan pl;
             if ((rc = make_plan(ix, nc, k, P, R, nullptr, pl))) break;
-            if ((rc = search_from_probes(ix, Qc, pl, probes, ids, dists, nullptr, nullptr, st))) break;
+            if ((rc = search_from_probes(ix, Qcw, pl, probes, ids, dists, nullptr, nullptr, st, Qc))) break;
             if ((rc = prune_labels(ix, ids, dists, nc, k, kth_dev + c0, probes, P, P, lab + c0 * P, st))) break;
-            if ((rc = prune_rows(ix, Qc, nc, probes, P, nullptr, P, 0.f, feats + c0 * P * NF, nullptr, nullptr,
+            if ((rc = prune_rows(ix, Qcw, nc, probes, P, nullptr, P, 0.f, feats + c0 * P * NF, nullptr, nullptr,
                                  nullptr, st)))
                 break;
         }

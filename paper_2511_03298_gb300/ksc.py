@@ -28,7 +28,7 @@ class KscError(RuntimeError):
 
 class BuildOpts(C.Structure):
     _fields_ = [("kmeans_iters", C.c_int32), ("spherical", C.c_int32), ("perm_host", C.c_void_p),
-                ("seed", C.c_uint64), ("build_graph", C.c_int32)]
+                ("seed", C.c_uint64), ("build_graph", C.c_int32), ("filter_threshold", C.c_float)]
 
 
 class IndexArrays(C.Structure):
@@ -96,6 +96,8 @@ _SIGS = {
     "ksc_search_pruned": [_vp, _vp, _i64, _i32, _i32, _i32, C.c_float, _vp, _vp, _vp, _vp, _vp],
     "ksc_prune_mlp_grad": [_vp, _vp, _vp, _i64, _vp, _vp, _vp],
     "ksc_pruner_theta": [_vp, C.c_float],
+    "ksc_index_dims": [_vp, _vp, _vp],
+    "ksc_component_stats": [_vp, _i64, _i32, _vp, _vp, _vp, _vp],
     "ksc_last_error": [],
     "ksc_version": [],
 }
@@ -184,6 +186,15 @@ class Index:
         a = IndexArrays()
         _check(lib().ksc_index_info(self._h, C.byref(a)))
         return dict(n=a.n, d=a.d, nlist=a.nlist, M=a.M, metric=a.metric, spherical=a.spherical)
+
+    def dims(self):
+        """(query width d, working dimension list: the query dimension of each
+        working one, -1 for a zero padding dimension)."""
+        inf = self.info()
+        dfull = C.c_int32(0)
+        dims = np.zeros(inf["d"], np.int32)
+        _check(lib().ksc_index_dims(self._h, _hptr(dims), C.byref(dfull)))
+        return dfull.value, dims
 
     def export(self, with_graph=False):
         inf = self.info()
@@ -485,11 +496,12 @@ class Plan:
 
 
 def build_index(X, nlist, M, nbits=4, metric="l2", spherical=False, perm=None, iters=20, seed=0x5EED,
-                build_graph=False, stream=None):
+                build_graph=False, filter_threshold=0.0, stream=None):
+    """filter_threshold > 0: component filtration (Sec. 4.3) before the build."""
     torch = _torch()
     n, d = X.shape
     perm_np = None if perm is None else np.ascontiguousarray(perm, dtype=np.int64)
-    opts = BuildOpts(iters, int(spherical), _hptr(perm_np), seed, int(build_graph))
+    opts = BuildOpts(iters, int(spherical), _hptr(perm_np), seed, int(build_graph), float(filter_threshold))
     h = C.c_void_p()
     _check(lib().ksc_build_index(_dptr(X, torch.float32, "X"), n, d, nlist, M, nbits,
                                  KSC_IP if metric == "ip" else KSC_L2, C.byref(opts), _stream(stream),
@@ -524,6 +536,17 @@ def prune_mlp_grad(w, x, y, stream=None):
     _check(lib().ksc_prune_mlp_grad(_dptr(w, torch.float32, "w"), _dptr(x, torch.float32, "x"),
                                     _dptr(y, torch.float32, "y"), x.shape[0], _dptr(g), _dptr(loss), _stream(stream)))
     return loss, g
+
+
+def component_stats(X, stream=None):
+    """Per-dimension mean, std and fraction of zero or within-one-std values
+    of a device matrix (FP64 device tensors)."""
+    torch = _torch()
+    n, d = X.shape
+    out = [torch.empty(d, dtype=torch.float64, device=X.device) for _ in range(3)]
+    _check(lib().ksc_component_stats(_dptr(X, torch.float32, "X"), n, d, *[_dptr(o) for o in out],
+                                     _stream(stream)))
+    return tuple(out)
 
 
 def lut16_peak(stream=None):
