@@ -39,7 +39,7 @@ CONFIGS = {
             metric="ip", spherical=True),
     4: dict(name="deep", n=10_000_000, d=96, nq=16_384, L=8192, M=48, k=100, R=1000, nprobe=64,
             metric="l2", spherical=True),
-    6: dict(name="fashion", n=60_000, d=784, nq=10_000, L=256, M=196, k=10, R=100, nprobe=8,
+    6: dict(name="fashion", n=60_000, d=784, nq=10_000, L=256, M=196, k=10, R=200, nprobe=8,
             metric="l2", spherical=False),
 }
 NPROBE_GRID = (8, 12, 16, 24, 32, 48, 64, 96, 128)
