@@ -33,7 +33,7 @@ TARGET_RECALL = 0.90
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of k_scan's two launches in one plain search at the
 # given nprobe, from ncu --set full (profiles/k_scan_ivfpq_sift1m_nq10k_nprobe<P>.md)
-SCAN_TRAFFIC_BYTES = {7: 190_184_960}
+SCAN_TRAFFIC_BYTES = {7: 190_171_648}
 
 
 def dist_setup():
