@@ -571,7 +571,10 @@ def run_workload(args):
              FP32 re-rank of R = 200 vs BF16 / FP8-e4m3 re-rank of a widened
              shortlist (400, 800) before the FP32 re-rank of 100.
     fashion -- 60k x 784 image-like, L2, nlist 256, M 196, k 10, rerank 200:
-             component filtration (Sec. 4.3) on vs off at recall@10 >= 0.99."""
+             component filtration (Sec. 4.3) on vs off at recall@10 >= 0.99.
+    latency -- the 1M x 128 index at nprobe 7, rerank 200: single-query
+             searches replayed from CUDA graphs on 1, 2, 4, 8 streams, one
+             index view per stream."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -729,6 +732,66 @@ def run_workload(args):
         out["variants"] = res
         out["speedup"] = round(res["filtered"]["qps"] / res["unfiltered"]["qps"], 3)
         out["metric"] = "QPS at recall@10>=0.99 with and without component filtration (60k x 784, L2)"
+    elif args.workload == "latency":
+        # single-query searches (batch 1), each replayed from a CUDA graph
+        # (ksc_plan), on S streams at once through S handles on one index
+        # (ksc_index_view): per-query device time and the throughput of S
+        # streams, on the 1M x 128 index at the plain operating point
+        c = synth.CONFIGS[2]
+        X = synth.base(2)
+        Xd = torch.from_numpy(X).to(dev)
+        ix = ksc.build_index(Xd, c["L"], c["M"], perm=synth.build_perm(2, c["n"]))
+        k, R, P, nq = 10, 200, 7, 2000
+        Qd = torch.from_numpy(synth.queries(2, nq)).to(dev)
+        ids_all, _ = ix.search(Qd, k, P, R)
+        kth = kth_fp32(torch, Xd, Qd, k)
+        dd = ((Xd[ids_all.clamp_min(0)] - Qd[:, None, :]) ** 2).sum(-1)
+        out["recall@10"] = round(float(((dd <= kth[:, None] * (1 + 1e-5) + 1e-3) & (ids_all >= 0)).sum(1)
+                                       .clamp_max(k).double().mean() / k), 4)
+        res = {}
+        for S in (1, 2, 4, 8):
+            hs = [ix] + [ix.view() for _ in range(S - 1)]
+            sts = [torch.cuda.Stream() for _ in range(S)]
+            pls = []
+            for h, s_ in zip(hs, sts):
+                with torch.cuda.stream(s_):
+                    pls.append(h.plan(1, k, nprobe=P, rerank=R))
+                    for j in range(3):
+                        pls[-1].execute(Qd[j:j + 1])
+            torch.cuda.synchronize()
+            cur = torch.cuda.current_stream()
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record(cur)
+            for s_ in sts:
+                s_.wait_event(t0)
+            ev = []
+            h0 = time.time()
+            for q in range(nq):
+                i = q % S
+                with torch.cuda.stream(sts[i]):
+                    a_ = torch.cuda.Event(enable_timing=True)
+                    b_ = torch.cuda.Event(enable_timing=True)
+                    a_.record(sts[i])
+                    pls[i].execute(Qd[q:q + 1])
+                    b_.record(sts[i])
+                    ev.append((a_, b_))
+            host_s = time.time() - h0
+            for s_ in sts:
+                cur.wait_stream(s_)
+            t1.record(cur)
+            t1.synchronize()
+            total = t0.elapsed_time(t1)
+            lat = sorted(a_.elapsed_time(b_) for a_, b_ in ev)
+            res[str(S)] = {"qps": round(nq / (total * 1e-3), 1), "p50_ms": round(lat[nq // 2], 4),
+                           "p99_ms": round(lat[int(nq * 0.99)], 4), "mean_ms": round(statistics.mean(lat), 4),
+                           "host_us_per_query": round(host_s / nq * 1e6, 1)}
+            del pls
+            del hs[1:]
+        out["streams"] = res
+        out["config"] = {"n": c["n"], "d": c["d"], "nlist": c["L"], "M": c["M"], "k": k, "nprobe": P, "rerank": R,
+                         "queries": nq}
+        out["metric"] = "single-query (batch 1) device time and throughput on S streams (1M x 128)"
     print(json.dumps(out))
 
 
@@ -793,7 +856,7 @@ def main():
     ap.add_argument("--ntrain", type=int, default=100_000)
     ap.add_argument("--lanes", type=int, default=0, help="scan lanes per query (0 auto; 4, 8, 16, 32)")
     ap.add_argument("--tile-blocks", type=int, default=0, help="scan tile length in blocks (0 auto)")
-    ap.add_argument("--workload", default="sift", choices=["sift", "deep", "glove", "fashion"],
+    ap.add_argument("--workload", default="sift", choices=["sift", "deep", "glove", "fashion", "latency"],
                     help="sift: the headline line; deep / glove: secondary workloads")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

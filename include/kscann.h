@@ -22,8 +22,9 @@
  *  - Distances returned: L2 -> squared Euclidean distance, ascending;
  *    IP -> inner product (similarity), descending.  Ties -> lower id.
  *    Fewer than k results: id -1 and dist +inf (L2) / -inf (IP).
- *  - An index is read-only during search; searches on different streams may
- *    run concurrently only with distinct workspaces (see ksc_search_opts).
+ *  - A handle owns one search workspace: searches through one handle must
+ *    not overlap on the GPU.  Searches on different streams may run at the
+ *    same time through different handles on the same data (ksc_index_view).
  */
 #ifndef KSCANN_H
 #define KSCANN_H
@@ -462,6 +463,15 @@ int ksc_pair_distances(ksc_index* ix, const float* Q_dev, int64_t nq, const int6
  * [1] candidates kept by the scan's threshold filter (all queries),
  * [2] most candidates kept for one query, [3] reserved (0). */
 int ksc_search_stats(ksc_index* ix, int64_t* stats_host);
+
+/* A second handle on the index data of ix (device arrays, models and
+ * statistics shared, not copied) with its own search workspace, status word,
+ * counters and stage events, so that searches on different streams can run
+ * at the same time, one handle each (e.g. single-query searches on several
+ * streams).  Free every view (ksc_index_free) before the handle it came from.
+ * A view does not train or set models or statistics (KSC_ESTATE); do not
+ * retrain the index while views of it exist. */
+int ksc_index_view(ksc_index* ix, ksc_index** out);
 
 /* Message of the last failure on this thread ("" if none). */
 const char* ksc_last_error(void);

@@ -318,7 +318,34 @@ static int alloc_copy(void** dst, const void* src, size_t bytes, cudaStream_t st
     return KSC_OK;
 }
 
+// The search workspace buffers of a handle.
+static int workspace_buffers(ksc_index* ix, Buffer** out) {
+    Buffer* bufs[] = {&ix->ws_scores, &ix->ws_probes, &ix->ws_lut, &ix->ws_bias, &ix->ws_scale, &ix->ws_range,
+                      &ix->ws_thr, &ix->ws_cnt, &ix->ws_cand, &ix->ws_topr, &ix->ws_nprobe, &ix->ws_rerank,
+                      &ix->ws_items, &ix->ws_misc, &ix->ws_qbf16, &ix->ws_err, &ix->ws_feat, &ix->ws_rscore,
+                      &ix->ws_full, &ix->ws_topr2, &ix->ws_redo, &ix->ws_pprobes, &ix->ws_pn, &ix->ws_pprob, &ix->ws_qf};
+    const int n = (int)(sizeof(bufs) / sizeof(bufs[0]));
+    for (int i = 0; i < n; ++i) out[i] = bufs[i];
+    return n;
+}
+
 int free_index_memory(ksc_index* ix) {
+    Buffer* bufs[64];
+    const int nb = workspace_buffers(ix, bufs);
+    if (ix->parent) {
+        // a view: its own workspace, status, counters and events, and what it
+        // allocated lazily itself (not the same pointer as its source's)
+        const ksc_index* s = ix->parent;
+        void* own[] = {ix->status, ix->stats, ix->c_rank_bf16 != s->c_rank_bf16 ? ix->c_rank_bf16 : nullptr,
+                       ix->X_bf16 != s->X_bf16 ? ix->X_bf16 : nullptr, ix->X_fp8 != s->X_fp8 ? ix->X_fp8 : nullptr,
+                       ix->X_scale != s->X_scale ? ix->X_scale : nullptr};
+        for (void* p : own)
+            if (p) cudaFree(p);
+        for (int i = 0; i < nb; ++i) release(*bufs[i]);
+        for (int i = 0; i <= KSC_NUM_STAGES; ++i)
+            if (ix->ev[i]) cudaEventDestroy(ix->ev[i]);
+        return KSC_OK;
+    }
     void* ptrs[] = {ix->X, ix->c_rank, ix->c_rank_sq, ix->c_mean, ix->codebook, ix->list_boff, ix->list_n,
                     ix->blk_ids, ix->blk_codes, ix->assign, ix->graph, ix->entry, ix->status, ix->stats,
                     ix->c_rank_bf16, ix->mlp_w, ix->blk_list, ix->nbr_pos, ix->nbr_codes, ix->entry_pos,
@@ -326,11 +353,7 @@ int free_index_memory(ksc_index* ix) {
                     ix->X_rr};
     for (void* p : ptrs)
         if (p) cudaFree(p);
-    Buffer* bufs[] = {&ix->ws_scores, &ix->ws_probes, &ix->ws_lut, &ix->ws_bias, &ix->ws_scale, &ix->ws_range,
-                      &ix->ws_thr, &ix->ws_cnt, &ix->ws_cand, &ix->ws_topr, &ix->ws_nprobe, &ix->ws_rerank,
-                      &ix->ws_items, &ix->ws_misc, &ix->ws_qbf16, &ix->ws_err, &ix->ws_feat, &ix->ws_rscore,
-                      &ix->ws_full, &ix->ws_topr2, &ix->ws_redo, &ix->ws_pprobes, &ix->ws_pn, &ix->ws_pprob, &ix->ws_qf};
-    for (Buffer* b : bufs) release(*b);
+    for (int i = 0; i < nb; ++i) release(*bufs[i]);
     for (int i = 0; i <= KSC_NUM_STAGES; ++i)
         if (ix->ev[i]) cudaEventDestroy(ix->ev[i]);
     return KSC_OK;
@@ -721,4 +744,35 @@ extern "C" int ksc_component_stats(const float* X_dev, int64_t n, int32_t d, dou
                                    double* frac_dev, void* stream) {
     KSC_CHECK_ARG(X_dev && mu_dev && sd_dev && frac_dev && n > 0 && d > 0, "bad argument");
     return ksc::component_stats(X_dev, n, d, mu_dev, sd_dev, frac_dev, ksc::as_stream(stream));
+}
+
+// A second handle on the same index data with its own search workspace,
+// status word, counters and stage events, so that searches on different
+// streams can run at the same time (one handle each).
+extern "C" int ksc_index_view(ksc_index* ix, ksc_index** out) {
+    KSC_CHECK_ARG(ix && out, "null argument");
+    ksc_index* v = new ksc_index(*ix);  // the shared arrays, models and host mirrors
+    v->parent = ix;
+    ksc::Buffer* bufs[64];
+    const int nb = workspace_buffers(v, bufs);
+    for (int i = 0; i < nb; ++i) *bufs[i] = ksc::Buffer{};
+    for (int i = 0; i <= KSC_NUM_STAGES; ++i) {
+        v->ev[i] = nullptr;
+        v->ev_used[i] = false;
+    }
+    v->prof = false;
+    v->launches = 0;
+    v->status = nullptr;
+    v->stats = nullptr;
+    cudaError_t e = cudaMalloc(&v->status, sizeof(int32_t) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&v->stats, sizeof(unsigned long long) * 4);
+    if (e == cudaSuccess) e = cudaMemset(v->status, 0, sizeof(int32_t) * 4);
+    if (e == cudaSuccess) e = cudaMemset(v->stats, 0, sizeof(unsigned long long) * 4);
+    if (e != cudaSuccess) {
+        ksc::set_error("ksc_index_view: %s", cudaGetErrorString(e));
+        ksc_index_free(v);
+        return e == cudaErrorMemoryAllocation ? KSC_ENOMEM : KSC_ECUDA;
+    }
+    *out = v;
+    return KSC_OK;
 }

@@ -64,6 +64,8 @@ struct ksc_index {
     std::vector<int32_t> h_dims;
     float* X_rr = nullptr;       // [n x d_rr] full vectors (null: no filtration)
     int32_t d_rr = 0;
+    // a view (ksc_index_view): the handle it came from, whose arrays it shares
+    const ksc_index* parent = nullptr;
     // stage timing (ksc_profile_enable)
     bool prof = false;
     cudaEvent_t ev[KSC_NUM_STAGES + 1] = {};

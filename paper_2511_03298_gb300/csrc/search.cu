@@ -3254,6 +3254,7 @@ int ksc_predictor_params(ksc_index* ix, const ksc_adaptive_params* prm) {
 }
 
 int ksc_predictor_weights(ksc_index* ix, float* w_host, const float* w_in_host) {
+    KSC_CHECK_STATE(!ix || !w_in_host || !ix->parent, "models are set on the index, not on a view of it");
     KSC_CHECK_ARG(ix && (w_host || w_in_host), "null argument");
     if (w_in_host) {
         if (!ix->mlp_w) KSC_CUDA(cudaMalloc(&ix->mlp_w, sizeof(float) * KSC_MLP_NPARAMS));
@@ -3276,6 +3277,7 @@ int ksc_predictor_weights(ksc_index* ix, float* w_host, const float* w_in_host) 
 
 int ksc_train_predictor(ksc_index* ix, const float* Qtrain_dev, int64_t nt, const float* kth_dev,
                         const ksc_train_opts* opts, void* stream, float* loss_host) {
+    KSC_CHECK_STATE(!ix || !ix->parent, "the predictor is trained on an index, not on a view of it");
     KSC_CHECK_ARG(ix && Qtrain_dev && kth_dev && nt > 0, "bad argument");
     KSC_CHECK_ARG(ix->L >= 32, "the predictor needs at least 32 lists");
     cudaStream_t st = as_stream(stream);
@@ -3642,6 +3644,7 @@ int ksc_autotune(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t k, int32
 extern "C" {
 
 int ksc_pruner_stats(ksc_index* ix, int32_t iters, void* stream) {
+    KSC_CHECK_STATE(!ix || !ix->parent, "the pruning statistics belong to the index, not to a view of it");
     KSC_CHECK_ARG(ix, "null index");
     return prune_stats(ix, iters, as_stream(stream));
 }
@@ -3661,6 +3664,7 @@ int ksc_pruner_export(ksc_index* ix, float* stats_host, float* vecs_host, float*
 }
 
 int ksc_pruner_import_model(ksc_index* ix, const float* model_host) {
+    KSC_CHECK_STATE(!ix || !ix->parent, "models are set on the index, not on a view of it");
     KSC_CHECK_ARG(ix && model_host, "null argument");
     if (!ix->pr_model) KSC_CUDA(cudaMalloc(&ix->pr_model, sizeof(float) * KSC_PRUNE_MODEL));
     KSC_CUDA(cudaMemcpy(ix->pr_model, model_host, sizeof(float) * KSC_PRUNE_MODEL, cudaMemcpyHostToDevice));
@@ -3740,6 +3744,7 @@ int ksc_search_pruned(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t k, 
 #define T_CUDA(call) { cudaError_t e_ = (call); if (e_ != cudaSuccess) { set_error("%s: %s", #call, cudaGetErrorString(e_)); rc = KSC_ECUDA; break; } }
 int ksc_train_pruner(ksc_index* ix, const float* Qtrain_dev, int64_t nt, const float* kth_dev, int32_t k,
                      int32_t P, int32_t R, const ksc_train_opts* opts, void* stream, float* loss_host) {
+    KSC_CHECK_STATE(!ix || !ix->parent, "the pruner is trained on an index, not on a view of it");
     KSC_CHECK_ARG(ix && Qtrain_dev && kth_dev && nt > 0, "bad argument");
     KSC_CHECK_ARG(k >= 1 && k <= KSC_MAX_K && R >= k && R <= KSC_MAX_RERANK, "bad k or rerank");
     KSC_CHECK_ARG(P >= 1 && P <= ix->L && P <= MAX_NPROBE, "bad nprobe");

@@ -97,6 +97,7 @@ _SIGS = {
     "ksc_prune_mlp_grad": [_vp, _vp, _vp, _i64, _vp, _vp, _vp],
     "ksc_pruner_theta": [_vp, C.c_float],
     "ksc_index_dims": [_vp, _vp, _vp],
+    "ksc_index_view": [_vp, _vp],
     "ksc_component_stats": [_vp, _i64, _i32, _vp, _vp, _vp, _vp],
     "ksc_last_error": [],
     "ksc_version": [],
@@ -186,6 +187,15 @@ class Index:
         a = IndexArrays()
         _check(lib().ksc_index_info(self._h, C.byref(a)))
         return dict(n=a.n, d=a.d, nlist=a.nlist, M=a.M, metric=a.metric, spherical=a.spherical)
+
+    def view(self):
+        """Another handle on the same index data with its own workspace, for
+        searches on another stream at the same time (freed before this one)."""
+        h = C.c_void_p()
+        _check(lib().ksc_index_view(self._h, C.byref(h)))
+        v = Index(h.value)
+        v._source = self  # keeps this handle alive until the view is freed
+        return v
 
     def dims(self):
         """(query width d, working dimension list: the query dimension of each
