@@ -992,3 +992,23 @@ int orc_component_stats(const float* X, int64_t n, int32_t d, double* mu, double
     }
     return 0;
 }
+
+/*
+ * Regression variant of the learned nprobe / reorder heads (the
+ * regression-head variant of Sec. 4.2.2's predictor): the head's output p in
+ * [0, 1] is read as the normalised log of the setting,
+ *   u = clamp(p (1 + b) + a, 0, 1),  v = lo (hi / lo)^u,
+ *   P = clamp(ceil(v - 1e-3), lo, hi)
+ * (a value within 1e-3 above an integer counts as that integer, so the
+ * rounding of the power cannot push an exact integer to the next one).
+ */
+int32_t orc_reg_map(double p, int32_t lo, int32_t hi, double a, double b) {
+    double u = p * (1.0 + b) + a;
+    if (u < 0.0) u = 0.0;
+    if (u > 1.0) u = 1.0;
+    double v = (double)lo * pow((double)hi / (double)lo, u);
+    double r = ceil(v - 1e-3);
+    if (r < lo) r = lo;
+    if (r > hi) r = hi;
+    return (int32_t)r;
+}

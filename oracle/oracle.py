@@ -18,6 +18,7 @@ tests/test_oracle_pins.py):
   exact_knn     brute force (ground truth)                         pinned
   recall        Sec. 5.4 Recall@10                                 pinned
   eq2           Eq. 2                                              pinned
+  reg_map       regression-head mapping (predictor variant)        pinned
   mlp_*         Sec. 4.2.1-4.2.2 predictor (MLP stand-in)          pinned
   prune_*       Sec. 4.2.3 / Table 4 cluster pruning, Alg. 2       pinned
   component_*   Sec. 4.3 component filtration, Alg. 1 / Alg. 2     pinned
@@ -80,6 +81,7 @@ def lib():
             "orc_prune_features": (C.c_int, [_f32p, _i64, _i32, _f32p, _i32, _i32p, _i32, _vp, _i32,
                                              _f64p, _f64p, _f64p]),
             "orc_component_stats": (C.c_int, [_f32p, _i64, _i32, _f64p, _f64p, _f64p]),
+            "orc_reg_map": (C.c_int32, [_f64, _i32, _i32, _f64, _f64]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -282,6 +284,16 @@ def recall(Q, X, ids, true_d, k=10, ip=False):
 # -------------------------------------------------------------- learned part
 def eq2(p, pmin, pmax, p0, p1):
     return lib().orc_eq2(float(p), int(pmin), int(pmax), float(p0), float(p1))
+
+
+def reg_map(p, lo, hi, a=0.0, b=0.0):
+    """Regression heads: p read as the normalised log of the setting."""
+    return lib().orc_reg_map(float(p), int(lo), int(hi), float(a), float(b))
+
+
+def reg_target(v, lo, hi):
+    """Training target of a regression head: the normalised log of a label."""
+    return (np.log(np.asarray(v, np.float64)) - np.log(lo)) / (np.log(hi) - np.log(lo))
 
 
 def mlp_nparams(F, H1, H2):

@@ -364,3 +364,16 @@ def test_adam_first_step_closed_form(orc):
     orc.adam_step(w, g, m, v, 1, lr=0.01)
     # t = 1: m_hat = g, v_hat = g^2  ->  w1 = w0 - lr g / (|g| + eps)
     np.testing.assert_allclose(w, w0 - 0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=1e-15)
+
+
+def test_regression_mapping_endpoints_and_inverse():
+    import oracle as o
+    lo, hi = 4, 64
+    assert o.reg_map(0.0, lo, hi) == lo and o.reg_map(1.0, lo, hi) == hi
+    assert o.reg_map(-3.0, lo, hi) == lo and o.reg_map(7.0, lo, hi) == hi
+    # the target of an exact setting maps back to it: 4 * 16^(1/2) = 16, 4 * 16^(1/4) = 8
+    for v in (4, 8, 16, 32, 64):
+        assert o.reg_map(float(o.reg_target(v, lo, hi)), lo, hi) == v
+    # between grid points: the next integer up; shift and scale move u
+    assert o.reg_map(0.6, lo, hi) == 22  # 4 * 16^0.6 = 21.11
+    assert o.reg_map(0.5, lo, hi, a=0.25) == 32 and o.reg_map(0.5, lo, hi, b=-0.5) == 8
