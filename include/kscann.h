@@ -246,6 +246,10 @@ typedef struct {
     int32_t rmin, rmax;   /* rerank range */
     float p0, p1;         /* Eq. 2 parameters of the nprobe head */
     float r0, r1;         /* Eq. 2 parameters of the rerank head */
+    int32_t regression;   /* 1: regression heads (ksc_train_opts.regression): p is the
+                             normalised log of the setting, u = clamp(p (1 + p1) + p0, 0, 1),
+                             P = clamp(ceil(pmin (pmax / pmin)^u - 1e-3), pmin, pmax), and
+                             likewise R with (rmin, rmax, r0, r1); 0: Eq. 2 */
 } ksc_adaptive_params;
 
 typedef struct {
@@ -260,6 +264,9 @@ typedef struct {
     int32_t ngrid;
     const int32_t* rgrid_host;  /* ascending rerank grid; NULL -> 20,50,100,200,400 */
     int32_t nrgrid;
+    int32_t regression;     /* 1: regression heads trained on soft targets, the normalised
+                               logs (log label - log grid min) / (log grid max - log grid min);
+                               sets ksc_adaptive_params.regression (0: "hard" labels, Eq. 2) */
 } ksc_train_opts;
 
 /* Train the predictor of this index on the queries Qtrain_dev [nt x d] whose

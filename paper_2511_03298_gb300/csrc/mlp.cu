@@ -208,6 +208,16 @@ __host__ __device__ inline int eq2(float p, int pmin, int pmax, float p0, float 
     return r > (float)pmax ? pmax : (r < (float)pmin ? pmin : (int)r);
 }
 
+// Regression heads: p is the normalised log of the setting,
+// u = clamp(p (1 + b) + a, 0, 1), P = clamp(ceil(lo (hi / lo)^u - 1e-3), lo, hi)
+// (a value within 1e-3 above an integer counts as that integer).
+__device__ inline int regmap(float p, int lo, int hi, float a, float b) {
+    const float u = fminf(fmaxf(p * (1.f + b) + a, 0.f), 1.f);
+    const float v = (float)lo * powf((float)hi / (float)lo, u);
+    const float r = ceilf(v - 1e-3f);
+    return r > (float)hi ? hi : (r < (float)lo ? lo : (int)r);
+}
+
 // One layer for a tile of rows: thread e computes unit a = e / rows of row
 // r = e % rows, so a warp shares one weight row (broadcast) and reads 32
 // activation rows of stride MLP_LDI (odd: distinct banks).  Accumulation in
@@ -255,8 +265,12 @@ __global__ void __launch_bounds__(256) k_mlp_infer(const float* __restrict__ w, 
                 p[o] = 1.f / (1.f + expf(-z));
                 if (prob) prob[(r0 + r) * MLP_O + o] = p[o];
             }
-            if (nprobe) nprobe[r0 + r] = eq2(p[0], prm.pmin, prm.pmax, prm.p0, prm.p1);
-            if (rerank) rerank[r0 + r] = eq2(p[1], prm.rmin, prm.rmax, prm.r0, prm.r1);
+            if (nprobe)
+                nprobe[r0 + r] = prm.regression ? regmap(p[0], prm.pmin, prm.pmax, prm.p0, prm.p1)
+                                                : eq2(p[0], prm.pmin, prm.pmax, prm.p0, prm.p1);
+            if (rerank)
+                rerank[r0 + r] = prm.regression ? regmap(p[1], prm.rmin, prm.rmax, prm.r0, prm.r1)
+                                                : eq2(p[1], prm.rmin, prm.rmax, prm.r0, prm.r1);
         }
         __syncthreads();  // the tile buffers are reused
     }

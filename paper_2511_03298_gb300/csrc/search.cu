@@ -3288,6 +3288,7 @@ int ksc_train_predictor(ksc_index* ix, const float* Qtrain_dev, int64_t nt, cons
     const int batch = (opts && opts->batch > 0) ? opts->batch : 256;
     const float lr = (opts && opts->lr > 0.f) ? opts->lr : 1e-3f;
     uint64_t seed = (opts && opts->seed) ? opts->seed : 0x6d6c70ull;
+    const bool regression = opts && opts->regression;
     std::vector<int32_t> grid, rgrid;
     if (opts && opts->grid_host && opts->ngrid > 0) grid.assign(opts->grid_host, opts->grid_host + opts->ngrid);
     else grid.assign(DEF_GRID, DEF_GRID + 11);
@@ -3334,9 +3335,19 @@ int ksc_train_predictor(ksc_index* ix, const float* Qtrain_dev, int64_t nt, cons
         if (rc) break;
         const float med_n = median_of(lab_n), med_r = median_of(lab_r);
         std::vector<float> yh(nt * 2);
+        // regression heads: soft targets, the normalised log of the label
+        auto soft = [](int32_t v, int32_t lo, int32_t hi) {
+            return hi > lo ? (float)((std::log((double)v) - std::log((double)lo)) / (std::log((double)hi) - std::log((double)lo)))
+                           : 0.f;
+        };
         for (int64_t q = 0; q < nt; ++q) {
-            yh[2 * q] = lab_n[q] > med_n ? 1.f : 0.f;
-            yh[2 * q + 1] = lab_r[q] > med_r ? 1.f : 0.f;
+            if (regression) {
+                yh[2 * q] = soft(lab_n[q], grid.front(), grid.back());
+                yh[2 * q + 1] = soft(lab_r[q], rgrid.front(), rgrid.back());
+            } else {
+                yh[2 * q] = lab_n[q] > med_n ? 1.f : 0.f;
+                yh[2 * q + 1] = lab_r[q] > med_r ? 1.f : 0.f;
+            }
         }
         T_CUDA(cudaMemcpy(Y, yh.data(), sizeof(float) * nt * 2, cudaMemcpyHostToDevice));
         // 2. weights: He-uniform from the seed, zero biases
@@ -3388,7 +3399,11 @@ int ksc_train_predictor(ksc_index* ix, const float* Qtrain_dev, int64_t nt, cons
         if (ix->mlp_w) cudaFree(ix->mlp_w);
         ix->mlp_w = w;
         w = nullptr;
-        ix->mlp_prm = {grid.front(), grid.back(), rgrid.front(), rgrid.back(), 0.3f, 0.5f, 0.3f, 0.5f};
+        ix->mlp_prm = regression
+                          ? ksc_adaptive_params{grid.front(), grid.back(), rgrid.front(), rgrid.back(), 0.f, 0.f, 0.f,
+                                                0.f, 1}
+                          : ksc_adaptive_params{grid.front(), grid.back(), rgrid.front(), rgrid.back(), 0.3f, 0.5f,
+                                                0.3f, 0.5f, 0};
     } while (0);
 #undef T_CUDA
     cudaFree(feats); cudaFree(Y); cudaFree(probes); cudaFree(lab_dev); cudaFree(w); cudaFree(g); cudaFree(m);

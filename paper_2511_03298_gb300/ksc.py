@@ -40,13 +40,14 @@ class IndexArrays(C.Structure):
 
 class AdaptiveParams(C.Structure):
     _fields_ = [("pmin", C.c_int32), ("pmax", C.c_int32), ("rmin", C.c_int32), ("rmax", C.c_int32),
-                ("p0", C.c_float), ("p1", C.c_float), ("r0", C.c_float), ("r1", C.c_float)]
+                ("p0", C.c_float), ("p1", C.c_float), ("r0", C.c_float), ("r1", C.c_float),
+                ("regression", C.c_int32)]
 
 
 class TrainOpts(C.Structure):
     _fields_ = [("k", C.c_int32), ("target_hits", C.c_int32), ("rerank_label", C.c_int32), ("epochs", C.c_int32),
                 ("batch", C.c_int32), ("lr", C.c_float), ("seed", C.c_uint64), ("grid_host", C.c_void_p),
-                ("ngrid", C.c_int32), ("rgrid_host", C.c_void_p), ("nrgrid", C.c_int32)]
+                ("ngrid", C.c_int32), ("rgrid_host", C.c_void_p), ("nrgrid", C.c_int32), ("regression", C.c_int32)]
 
 
 class SearchOpts(C.Structure):
@@ -294,7 +295,7 @@ class Index:
 
     # ---------------------------------------------------------- learned predictor
     def train_predictor(self, Qtrain, kth, k=10, target_hits=9, rerank_label=200, epochs=8, batch=256, lr=1e-3,
-                        seed=0, grid=None, rgrid=None, stream=None):
+                        seed=0, grid=None, rgrid=None, regression=False, stream=None):
         """Train the nprobe / rerank MLP on training queries and their true
         k-th neighbour distances (device tensors).  Returns the mean loss of
         the last epoch."""
@@ -302,15 +303,18 @@ class Index:
         g = None if grid is None else np.ascontiguousarray(grid, dtype=np.int32)
         r = None if rgrid is None else np.ascontiguousarray(rgrid, dtype=np.int32)
         opts = TrainOpts(k, target_hits, rerank_label, epochs, batch, lr, seed, _hptr(g),
-                         0 if g is None else len(g), _hptr(r), 0 if r is None else len(r))
+                         0 if g is None else len(g), _hptr(r), 0 if r is None else len(r), int(regression))
         loss = C.c_float(0)
         _check(lib().ksc_train_predictor(self._h, _dptr(Qtrain, torch.float32, "Qtrain"), Qtrain.shape[0],
                                          _dptr(kth, torch.float32, "kth"), C.byref(opts), _stream(stream),
                                          C.byref(loss)))
         return loss.value
 
-    def set_predictor_params(self, pmin, pmax, rmin, rmax, p0, p1, r0, r1):
-        _check(lib().ksc_predictor_params(self._h, C.byref(AdaptiveParams(pmin, pmax, rmin, rmax, p0, p1, r0, r1))))
+    def set_predictor_params(self, pmin, pmax, rmin, rmax, p0, p1, r0, r1, regression=False):
+        """regression: the heads' outputs are normalised logs of the settings
+        (a model trained with regression=True) instead of Eq. 2's input."""
+        _check(lib().ksc_predictor_params(self._h, C.byref(AdaptiveParams(pmin, pmax, rmin, rmax, p0, p1, r0, r1,
+                                                                           int(regression)))))
 
     def predictor_weights(self, set_to=None):
         if set_to is not None:

@@ -170,3 +170,48 @@ def test_learned_nprobe_beats_fixed_nprobe_at_equal_recall(env, trained):
     print("fixed nprobe %d vs learned mean nprobe %.2f at recall %.4f (pmax %d, p0 %.1f, p1 %.1f)"
           % (fixed, mean_np, rec, best[1], best[2], best[3]))
     assert rec >= target and mean_np < fixed
+
+
+def test_regression_heads_follow_the_oracle_mapping_and_gain(env, trained):
+    """Regression variant (soft targets, log-linear mapping): the device's
+    settings equal the oracle's mapping of the same probabilities, and the
+    variant also needs fewer probes than fixed nprobe at recall 0.90."""
+    torch, ksc = env
+    g, X, Q, Vq, _ = trained
+    T = synth.train_queries(5, 32_000)[:30_000]
+    loss = g.train_predictor(torch.from_numpy(T).cuda(), _kth(torch, X, T), epochs=8, regression=True)
+    assert np.isfinite(loss) and loss < 2 * np.log(2)
+    g.set_predictor_params(4, 64, 20, 400, 0.1, 0.2, 0.0, 0.1, regression=True)
+    Qd = torch.from_numpy(Q).cuda()
+    ids, dists, npb, rr = g.search_adaptive(Qd, 10)
+    feats = g.query_features(Qd)
+    w = torch.tensor(g.predictor_weights(), device="cuda")
+    p = torch.empty((len(Q), 2), dtype=torch.float32, device="cuda")
+    st = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert ksc.lib().ksc_mlp_forward(_ptr(w), _ptr(feats), len(Q), _ptr(p), st) == 0
+    torch.cuda.synchronize()
+    p = p.cpu().numpy().astype(np.float64)
+    npb, rr = npb.cpu().numpy(), rr.cpu().numpy()
+    ref_n = np.array([oracle.reg_map(v, 4, 64, 0.1, 0.2) for v in p[:, 0]])
+    ref_r = np.array([oracle.reg_map(v, 20, 400, 0.0, 0.1) for v in p[:, 1]])
+    assert np.abs(npb - ref_n).max() <= 1 and (npb == ref_n).mean() >= 0.99
+    assert np.abs(rr - ref_r).max() <= 1 and (rr == ref_r).mean() >= 0.99
+    assert len(np.unique(npb)) > 3  # the heads spread the queries over the range
+    Vd = torch.from_numpy(Vq).cuda()
+    kq, kv = _kth(torch, X, Q), _kth(torch, X, Vq)
+    fixed = next(P for P in range(1, 65) if _recall(torch, X, Q, g.search(Qd, 10, P, 200)[0], kq) >= 0.90)
+    best = None
+    for p0 in (-0.2, -0.1, 0.0, 0.1, 0.2, 0.3):
+        for p1 in (-0.5, 0.0, 0.5, 1.0):
+            g.set_predictor_params(1, 32, 200, 200, p0, p1, 0.0, 0.0, regression=True)
+            vi, _, vn, _ = g.search_adaptive(Vd, 10)
+            if _recall(torch, X, Vq, vi, kv) >= 0.905:
+                cost = float(vn.double().mean().item())
+                if best is None or cost < best[0]:
+                    best = (cost, p0, p1)
+    assert best is not None
+    g.set_predictor_params(1, 32, 200, 200, best[1], best[2], 0.0, 0.0, regression=True)
+    ids, _, npb, _ = g.search_adaptive(Qd, 10)
+    rec, mean_np = _recall(torch, X, Q, ids, kq), float(npb.double().mean().item())
+    print("regression heads: fixed nprobe %d vs mean nprobe %.2f at recall %.4f" % (fixed, mean_np, rec))
+    assert rec >= 0.90 and mean_np < fixed
