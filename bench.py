@@ -247,8 +247,8 @@ def run_ours(args, rank, ws):
         ix.profile(False)
         return statistics.mean(times), {s_: statistics.mean(v) for s_, v in stage.items()}, nl_tot, clk.summary()
 
-    sopts = ksc.search_opts(lanes_per_query=args.lanes, tile_blocks=args.tile_blocks) \
-        if (args.lanes or args.tile_blocks) else None
+    sopts = ksc.search_opts(lanes_per_query=args.lanes, tile_blocks=args.tile_blocks, scan_tc=args.scan_tc) \
+        if (args.lanes or args.tile_blocks or args.scan_tc) else None
     plain_ms, plain_stage, plain_launches, plain_clk = timed(
         lambda: ix.search(Qd, k, nprobe, R, opts=sopts, out=(ids, dists)))
     stats = ix.search_stats()
@@ -295,9 +295,9 @@ def run_ours(args, rank, ws):
                         if rec >= TARGET_RECALL + 0.005 and mr < rbest[0]:
                             rbest = (mr, rec, rmin, r0, r1)
             ix.set_predictor_params(best[2], best[3], rbest[2], R, best[4], best[5], rbest[3], rbest[4])
-            lids, _, lnp, lrr = ix.search_adaptive(Qd, k)
+            lids, _, lnp, lrr = ix.search_adaptive(Qd, k, opts=sopts)
             l_rec = recall_at_10(torch, Xd, Qd, lids, true_d, k)
-            l_ms, l_stage, l_launches, l_clk = timed(lambda: ix.search_adaptive(Qd, k))
+            l_ms, l_stage, l_launches, l_clk = timed(lambda: ix.search_adaptive(Qd, k, opts=sopts))
             learned = dict(ms=l_ms, stage=l_stage, launches=l_launches, clk=l_clk, recall=l_rec,
                            mean_nprobe=float(lnp.double().mean().item()), nprobe_q=lnp.cpu().numpy(),
                            mean_rerank=float(lrr.double().mean().item()),
@@ -331,9 +331,9 @@ def run_ours(args, rank, ws):
             pruned_state = (lp["pmin"], lp["pmax"], lp["rmin"], lp["rmax"], pb[3], pb[4], lp["r0"], lp["r1"])
             ix.pruner_theta(pb[2])
             ix.set_predictor_params(*pruned_state)
-            pids, _, pnp, prr = ix.search_adaptive(Qd, k)
+            pids, _, pnp, prr = ix.search_adaptive(Qd, k, opts=sopts)
             p_rec = recall_at_10(torch, Xd, Qd, pids, true_d, k)
-            p_ms, p_stage, p_launches, p_clk = timed(lambda: ix.search_adaptive(Qd, k))
+            p_ms, p_stage, p_launches, p_clk = timed(lambda: ix.search_adaptive(Qd, k, opts=sopts))
             pruned = dict(ms=p_ms, stage=p_stage, launches=p_launches, recall=p_rec, theta=pb[2], state=pruned_state,
                           mean_lists=float(pnp.double().mean().item()), mean_rerank=float(prr.double().mean().item()),
                           params=dict(pmin=lp["pmin"], pmax=lp["pmax"], p0=pb[3], p1=pb[4]), train_loss=ploss,
@@ -374,18 +374,18 @@ def run_ours(args, rank, ws):
     lplan = None
     ok_learned = learned is not None and learned["recall"] >= TARGET_RECALL
     if -max_over_ranks(-float(ok_learned), ws) > 0.5:  # on every rank, or on none
-        variants["learned direct"] = timed_bare(lambda: ix.search_adaptive(Qd, k), st)
+        variants["learned direct"] = timed_bare(lambda: ix.search_adaptive(Qd, k, opts=sopts), st)
         with torch.cuda.stream(gst):
-            lplan = ix.plan(CFG["nq"], k, adaptive=True)
+            lplan = ix.plan(CFG["nq"], k, adaptive=True, opts=sopts)
         variants["learned graph"] = timed_bare(lambda: lplan.execute(Qd, ids, dists), gst)
     prplan = None
     ok_pruned = pruned is not None and pruned["recall"] >= TARGET_RECALL
     if -max_over_ranks(-float(ok_pruned), ws) > 0.5:
         ix.pruner_theta(pruned["theta"])
         ix.set_predictor_params(*pruned["state"])
-        variants["pruned direct"] = timed_bare(lambda: ix.search_adaptive(Qd, k), st)
+        variants["pruned direct"] = timed_bare(lambda: ix.search_adaptive(Qd, k, opts=sopts), st)
         with torch.cuda.stream(gst):
-            prplan = ix.plan(CFG["nq"], k, adaptive=True)
+            prplan = ix.plan(CFG["nq"], k, adaptive=True, opts=sopts)
         variants["pruned graph"] = timed_bare(lambda: prplan.execute(Qd, ids, dists), gst)
     torch.cuda.synchronize()
     # headline: the fastest variant, the same choice on every rank (by the
@@ -856,6 +856,7 @@ def main():
     ap.add_argument("--ntrain", type=int, default=100_000)
     ap.add_argument("--lanes", type=int, default=0, help="scan lanes per query (0 auto; 4, 8, 16, 32)")
     ap.add_argument("--tile-blocks", type=int, default=0, help="scan tile length in blocks (0 auto)")
+    ap.add_argument("--scan-tc", type=int, default=0, help="1: the scan on the tensor cores")
     ap.add_argument("--workload", default="sift", choices=["sift", "deep", "glove", "fashion", "latency"],
                     help="sift: the headline line; deep / glove: secondary workloads")
     args = ap.parse_args()

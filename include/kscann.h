@@ -130,6 +130,9 @@ typedef struct {
                                   over the best rerank_final of them */
     int32_t rerank_final;      /* precision 1/2: FP32 re-rank size; 0 -> max(k, R/2) */
     int32_t tile_blocks;       /* scan: 32-vector blocks per work item; 0 auto */
+    int32_t scan_tc;           /* 1: the scan on the tensor cores (one-hot codes x FP16 tables,
+                                  FP32 sums of integers: the same keys as the byte-permute scan;
+                                  M <= 128, not with hybrid); 0: byte permutes on the CUDA cores */
 } ksc_search_opts;
 
 /* k nearest neighbours of Q_dev [nq x d] with a fixed nprobe (1..nlist) and
