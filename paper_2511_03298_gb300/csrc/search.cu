@@ -1731,17 +1731,18 @@ __global__ void __launch_bounds__(S4_WARPS * 32, MAXM <= 64 ? 3 : 1)
 // column), eight subspaces (64 columns) per chunk, and the MMAs read it there.
 // B, the item's tables, is staged once per item into shared memory (K-major,
 // 128-byte swizzle, boxes of 64 K entries) and read by every tile of the item.
-// Roles: two warpgroups take the item's tiles in turn (even / odd), each
-// expanding its tile's chunks into its own ring of TMEM slots and, once the
-// tile's product is complete, reading its accumulator (lane = vector, column
-// = query) and testing / writing the keys; one more warp issues the MMAs.
-// mbarriers: a chunk written (128 arrivals), a chunk read (tcgen05.commit),
-// a tile's product complete (tcgen05.commit).  Every wait is bounded.
+// Roles: two warpgroups expand alternate chunks of every tile, each into its
+// own ring of TMEM slots, and split the tile's epilogue (reading the
+// accumulator: lane = vector, column = query; testing / writing the keys) by
+// 16-column groups; one more warp issues the MMAs.  mbarriers: a chunk
+// written (128 arrivals), a chunk read (tcgen05.commit), a tile's product
+// complete (tcgen05.commit), an accumulator read by both warpgroups (256
+// arrivals).  Every wait is bounded.
 constexpr int TCS_NT = 64;        // queries per item (B rows, MMA N <= 64)
 constexpr int TCS_SLOTS = 3;      // TMEM chunk slots per warpgroup
 constexpr int TCS_THREADS = 288;  // two warpgroups + the MMA warp
 constexpr int TCS_TMEM_COLS = 512;
-constexpr int TCS_D_COL = 0;      // accumulators: warpgroup g at column g * TCS_NT
+constexpr int TCS_D_COL = 0;      // two accumulators, tiles alternating: accumulator b at column b * TCS_NT
 constexpr int TCS_A_COL = 2 * TCS_NT;  // chunk slots: (g * TCS_SLOTS + s) * 64 after the accumulators
 constexpr uint32_t TCS_WAIT = 1u << 22;
 static_assert(TCS_A_COL + 2 * TCS_SLOTS * 64 <= TCS_TMEM_COLS, "tensor memory columns");
