@@ -480,6 +480,33 @@ def run_ours(args, rank, ws):
                   "GBps": round(sbytes / (sms * 1e-3) / 1e9, 1),
                   "frac_of_hbm": round(sbytes / (sms * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6800.0), 4),
                   "l2": "flushed before each search"}
+        # the opt-in tensor-core scan on the plain step: its results against the
+        # plain search's and its two scan stages (L2 flushed before each search)
+        tcs = None
+        if not args.scan_tc:
+            try:
+                to = ksc.search_opts(scan_tc=True)
+                r0 = ix.search(Qd, k, nprobe, R)
+                r1 = ix.search(Qd, k, nprobe, R, opts=to)
+                same = bool(torch.equal(r0[0], r1[0]) and torch.equal(r0[1], r1[1]))
+                ix.profile(True)
+                tn, tsc = [], []
+                for it in range(args.warmup + 5):
+                    flush.zero_()
+                    ix.search(Qd, k, nprobe, R, opts=to)
+                    pp, _ = ix.profile_read()
+                    if it >= args.warmup:
+                        tn.append(pp["near_scan"])
+                        tsc.append(pp["scan"])
+                ix.profile(False)
+                tcs = {"kernel": "k_scan_tc (opt-in: ksc_search_opts.scan_tc)", "results_equal_plain": same,
+                       "status": ix.last_status(), "near_scan_ms": round(statistics.median(tn), 4),
+                       "scan_ms": round(statistics.median(tsc), 4),
+                       "plain_near_scan_ms": round(plain_stage["near_scan"], 4),
+                       "plain_scan_ms": round(plain_stage["scan"], 4)}
+            except Exception as ex:  # reported, never fatal to the benchmark line
+                ix.profile(False)
+                tcs = {"error": str(ex)[:200]}
         cpu = cpu_baseline(ix, X, Qh, nprobe, R, k, true_d) if (ws == 1 and not args.no_cpu) else None
         plain = {"value": round(CFG["nq"] / (plain_ms * 1e-3), 1), "ms_per_step": round(plain_ms, 4),
                  "nprobe": nprobe, "rerank": R, "recall@10": recall,
@@ -533,6 +560,7 @@ def run_ours(args, rank, ws):
                          "effective_code_GBps": round(code_bytes / (scan_ms * 1e-3) / 1e9, 1),
                          "hbm_peak_gbs": peaks.get("hbm_gbs")},
             "scan_stream": stream,
+            "scan_tc": tcs,
             "clocks": clocks,
             "build_s": round(build_s, 2),
             "cpu_baseline": cpu,
