@@ -56,3 +56,37 @@ def test_argument_errors_before_device_work(lib):
     assert rc == -1 and b"M" in lib.ksc_last_error()
     with pytest.raises(ksc.KscError):
         ksc._check(-1)
+
+
+def test_struct_layouts_match_the_binding(tmp_path):
+    """Every option / array struct of include/kscann.h has the size and field
+    offsets of its ctypes mirror in the binding (a field added on one side
+    only fails here: a missing name does not compile, a missing trailing
+    field changes the size)."""
+    import shutil
+    import subprocess
+    from paper_2511_03298_gb300 import ksc
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"ksc_build_opts": ksc.BuildOpts, "ksc_index_arrays": ksc.IndexArrays,
+               "ksc_adaptive_params": ksc.AdaptiveParams, "ksc_train_opts": ksc.TrainOpts,
+               "ksc_search_opts": ksc.SearchOpts}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "kscann.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append('  printf("%s %%zu\\n", sizeof(%s));' % (name, name))
+        for fname, _ in cls._fields_:
+            lines.append('  printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (name, fname, name, fname))
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                 check=True).stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == C.sizeof(cls), name
+        for fname, _ in cls._fields_:
+            assert int(got["%s.%s" % (name, fname)]) == getattr(cls, fname).offset, (name, fname)
