@@ -2991,12 +2991,13 @@ static int ensure_lowp(ksc_index* ix, int prec, cudaStream_t st) {
 }
 
 // Queries per item of the tensor-core scan for M subspaces: the item's tables
-// (M x 16 FP16 entries per query) fit in 192 KB of shared memory; 0: too many
-// subspaces.
+// (M x 16 FP16 entries per query) and the transposed codes fit in 200 KB of
+// shared memory; 0: not supported (each lane stages at most 4 x 32 code rows
+// of a block, so M <= 128).
 static int tcs_nt(int M) {
-    const int Mc = (M + 3) / 4;
+    if (M < 1 || M > 128) return 0;
     for (int nt = TCS_NT; nt >= 16; nt -= 16)
-        if ((size_t)Mc * nt * 128 <= 192 * 1024) return nt;
+        if (tcs_smem_bytes(M, nt) <= 200 * 1024) return nt;
     return 0;
 }
 
