@@ -201,16 +201,17 @@ def test_regression_heads_follow_the_oracle_mapping_and_gain(env, trained):
     kq, kv = _kth(torch, X, Q), _kth(torch, X, Vq)
     fixed = next(P for P in range(1, 65) if _recall(torch, X, Q, g.search(Qd, 10, P, 200)[0], kq) >= 0.90)
     best = None
-    for p0 in (-0.2, -0.1, 0.0, 0.1, 0.2, 0.3):
-        for p1 in (-0.5, 0.0, 0.5, 1.0):
-            g.set_predictor_params(1, 32, 200, 200, p0, p1, 0.0, 0.0, regression=True)
-            vi, _, vn, _ = g.search_adaptive(Vd, 10)
-            if _recall(torch, X, Vq, vi, kv) >= 0.905:
-                cost = float(vn.double().mean().item())
-                if best is None or cost < best[0]:
-                    best = (cost, p0, p1)
+    for pmax in (16, 32, 64):
+        for p0 in (-0.3, -0.2, -0.1, 0.0, 0.1, 0.2, 0.3):
+            for p1 in (-0.5, 0.0, 0.5, 1.0):
+                g.set_predictor_params(1, pmax, 200, 200, p0, p1, 0.0, 0.0, regression=True)
+                vi, _, vn, _ = g.search_adaptive(Vd, 10)
+                if _recall(torch, X, Vq, vi, kv) >= 0.905:
+                    cost = float(vn.double().mean().item())
+                    if best is None or cost < best[0]:
+                        best = (cost, pmax, p0, p1)
     assert best is not None
-    g.set_predictor_params(1, 32, 200, 200, best[1], best[2], 0.0, 0.0, regression=True)
+    g.set_predictor_params(1, best[1], 200, 200, best[2], best[3], 0.0, 0.0, regression=True)
     ids, _, npb, _ = g.search_adaptive(Qd, 10)
     rec, mean_np = _recall(torch, X, Q, ids, kq), float(npb.double().mean().item())
     print("regression heads: fixed nprobe %d vs mean nprobe %.2f at recall %.4f" % (fixed, mean_np, rec))
