@@ -113,6 +113,23 @@ int ksc_index_info(const ksc_index* ix, ksc_index_arrays* a);
  * ksc_index_info (pointers left NULL are skipped).  Blocking. */
 int ksc_index_export(const ksc_index* ix, ksc_index_arrays* a);
 
+/* Persistence (not in the paper: an index built once is reused).  Write the
+ * index to the file at `path`: the interchange arrays (as ksc_index_export)
+ * and, where the index holds them, the intra-list graph, the learned
+ * predictor (weights and parameters), the pruning statistics, model and
+ * threshold, and the component-filtration state (kept dimensions and full
+ * vectors).  Little-endian binary with a 64-byte header; a view writes the
+ * index it came from.  Blocking.  KSC_EINVAL if the file cannot be written
+ * (then nothing is left at `path`). */
+int ksc_index_save(const ksc_index* ix, const char* path);
+
+/* Read a file written by ksc_index_save into a new index (free it with
+ * ksc_index_free).  The whole file is checked on the host -- header, exact
+ * size, and every code, list, neighbour and dimension index in it -- before
+ * any device work: KSC_EINVAL for a missing, truncated, corrupt or foreign
+ * file.  Blocking. */
+int ksc_index_load(const char* path, void* stream, ksc_index** out);
+
 /* ------------------------------------------------------------------ */
 /* Search (Alg. 2, Alg. 3)                                             */
 /* ------------------------------------------------------------------ */

@@ -64,6 +64,8 @@ _SIGS = {
     "ksc_index_import": [_vp, _vp, _vp],
     "ksc_index_info": [_vp, _vp],
     "ksc_index_export": [_vp, _vp],
+    "ksc_index_save": [_vp, C.c_char_p],
+    "ksc_index_load": [C.c_char_p, _vp, _vp],
     "ksc_search": [_vp, _vp, _i64, _i32, _i32, _i32, _vp, _vp, _vp, _vp],
     "ksc_search_varprobe": [_vp, _vp, _i64, _i32, _vp, _i32, _vp, _i32, _vp, _vp, _vp, _vp],
     "ksc_search_with_probes": [_vp, _vp, _i64, _vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp],
@@ -224,6 +226,10 @@ class Index:
         _check(lib().ksc_index_export(self._h, C.byref(a)))
         out.update(inf)
         return out
+
+    def save(self, path):
+        """Write the index (and its graph, models and filtration state) to a file."""
+        _check(lib().ksc_index_save(self._h, os.fsencode(path)))
 
     def search(self, Q, k, nprobe, rerank, opts=None, out=None, stream=None):
         torch = _torch()
@@ -522,6 +528,13 @@ def build_index(X, nlist, M, nbits=4, metric="l2", spherical=False, perm=None, i
     _check(lib().ksc_build_index(_dptr(X, torch.float32, "X"), n, d, nlist, M, nbits,
                                  KSC_IP if metric == "ip" else KSC_L2, C.byref(opts), _stream(stream),
                                  C.byref(h)))
+    return Index(h.value)
+
+
+def index_load(path, stream=None):
+    """An index read from a file written by Index.save."""
+    h = C.c_void_p()
+    _check(lib().ksc_index_load(os.fsencode(path), _stream(stream), C.byref(h)))
     return Index(h.value)
 
 

@@ -4,6 +4,8 @@ import ctypes as C
 import os
 import re
 
+import numpy as np
+
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -90,3 +92,44 @@ def test_struct_layouts_match_the_binding(tmp_path):
         assert int(got[name]) == C.sizeof(cls), name
         for fname, _ in cls._fields_:
             assert int(got["%s.%s" % (name, fname)]) == getattr(cls, fname).offset, (name, fname)
+
+
+def _index_file(path, n=64, d=8, nlist=4, M=4, flags=0, codes=None, assign=None, magic=b"KSCIDX01", cut=0):
+    """A file in the layout ksc_index_save writes: a 64-byte little-endian
+    header (magic, n, d, nlist, M, metric, spherical, flags, full dimensions,
+    size of ksc_adaptive_params, 4 reserved) and the interchange arrays."""
+    import struct
+    from paper_2511_03298_gb300 import ksc
+    rng = np.random.default_rng(1)
+    hdr = struct.pack("<8sq8i4i", magic, n, d, nlist, M, 0, 0, flags, 0, C.sizeof(ksc.AdaptiveParams), 0, 0, 0, 0)
+    assert len(hdr) == 64
+    codes = rng.integers(0, 16, (n, M)).astype(np.uint8) if codes is None else codes
+    assign = (np.arange(n) % nlist).astype(np.int32) if assign is None else assign
+    body = b"".join(a.tobytes() for a in (
+        rng.normal(size=(n, d)).astype(np.float32), rng.normal(size=(nlist, d)).astype(np.float32),
+        rng.normal(size=(nlist, d)).astype(np.float32), rng.normal(size=(M, 16, d // M)).astype(np.float32),
+        codes, assign))
+    data = hdr + body
+    open(path, "wb").write(data[:len(data) - cut])
+    return path
+
+
+def test_index_load_rejects_bad_files_before_device_work(lib, tmp_path):
+    """ksc_index_load checks the whole file on the host: every case below
+    returns KSC_EINVAL without touching the device."""
+    h = C.c_void_p()
+    load = lambda p: lib.ksc_index_load(os.fsencode(str(p)), None, C.byref(h))
+    assert load(tmp_path / "missing.ksc") == -1 and b"cannot open" in lib.ksc_last_error()
+    assert load(_index_file(tmp_path / "magic.ksc", magic=b"NOTANIDX")) == -1
+    assert b"not an index file" in lib.ksc_last_error()
+    assert load(_index_file(tmp_path / "short.ksc", cut=4)) == -1 and b"bytes" in lib.ksc_last_error()
+    bad_codes = np.zeros((64, 4), np.uint8)
+    bad_codes[7, 2] = 16
+    assert load(_index_file(tmp_path / "codes.ksc", codes=bad_codes)) == -1 and b"code" in lib.ksc_last_error()
+    bad_assign = (np.arange(64) % 4).astype(np.int32)
+    bad_assign[9] = 4
+    assert load(_index_file(tmp_path / "lists.ksc", assign=bad_assign)) == -1 and b"list" in lib.ksc_last_error()
+    assert load(_index_file(tmp_path / "flags.ksc", flags=64)) == -1 and b"sections" in lib.ksc_last_error()
+    assert lib.ksc_index_load(None, None, C.byref(h)) == -1
+    assert lib.ksc_index_save(None, b"x") == -1
+    assert h.value is None
