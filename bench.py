@@ -34,6 +34,7 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of k_scan's two launches in one plain search at the
 # given nprobe, from ncu --set full (profiles/k_scan_ivfpq_sift1m_nq10k_nprobe<P>.md)
 SCAN_TRAFFIC_BYTES = {7: 190_171_648}
+HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e, nominal
 
 
 def dist_setup():
@@ -479,7 +480,28 @@ def run_ours(args, rank, ws):
         stream = {"queries": Bs, "nprobe": Ps, "code_bytes": sbytes, "scan_ms": round(sms, 4),
                   "GBps": round(sbytes / (sms * 1e-3) / 1e9, 1),
                   "frac_of_hbm": round(sbytes / (sms * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6800.0), 4),
+                  "frac_of_nominal": round(sbytes / (sms * 1e-3) / 1e9 / HBM_NOMINAL_GBS, 4),
                   "l2": "flushed before each search"}
+        # a read-only streaming rate of this run (a 2 GB reduction), the third
+        # denominator of the streaming figure
+        try:
+            rbuf = torch.ones(1 << 29, dtype=torch.float32, device=Qd.device)
+            rs = []
+            for it in range(args.warmup + 5):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                rbuf.sum()
+                e1.record()
+                e1.synchronize()
+                if it >= args.warmup:
+                    rs.append(e0.elapsed_time(e1))
+            read_gbs = rbuf.numel() * 4 / (statistics.median(rs) * 1e-3) / 1e9
+            del rbuf
+            stream["read_stream_GBps"] = round(read_gbs, 1)
+            stream["frac_of_read_stream"] = round(sbytes / (sms * 1e-3) / 1e9 / read_gbs, 4)
+        except Exception as ex:  # reported, never fatal
+            stream["read_stream_error"] = str(ex)[:200]
         # the opt-in tensor-core scan on the plain step: its results against the
         # plain search's and its two scan stages (L2 flushed before each search)
         tcs = None
@@ -558,7 +580,17 @@ def run_ours(args, rank, ws):
                          "step": "plain nprobe %d search of this run" % nprobe,
                          "code_bytes_per_launch": code_bytes,
                          "effective_code_GBps": round(code_bytes / (scan_ms * 1e-3) / 1e9, 1),
-                         "hbm_peak_gbs": peaks.get("hbm_gbs")},
+                         "hbm_peak_gbs": peaks.get("hbm_gbs"),
+                         # the index's codes once; DRAM traffic above them is candidate keys
+                         # and L2 misses of lists re-read by many queries
+                         "unique_code_bytes": CFG["n"] * CFG["M"] // 2,
+                         "traffic_over_unique_code_bytes": None if sopts or SCAN_TRAFFIC_BYTES.get(nprobe) is None
+                         else round(SCAN_TRAFFIC_BYTES[nprobe] / (CFG["n"] * CFG["M"] / 2), 2)},
+            # re-rank of the plain step: R gathered rows of d floats per query
+            "rerank_hbm": {"bytes": CFG["nq"] * R * CFG["d"] * 4, "ms": round(plain_stage["rerank"], 4),
+                           "GBps": round(CFG["nq"] * R * CFG["d"] * 4 / (plain_stage["rerank"] * 1e-3) / 1e9, 1),
+                           "frac_of_hbm": round(CFG["nq"] * R * CFG["d"] * 4 / (plain_stage["rerank"] * 1e-3) / 1e9
+                                                / peaks.get("hbm_gbs", 6800.0), 4)},
             "scan_stream": stream,
             "scan_tc": tcs,
             "clocks": clocks,
@@ -566,6 +598,25 @@ def run_ours(args, rank, ws):
             "cpu_baseline": cpu,
         }
     return out
+
+
+def cpu_model():
+    """The host CPU as /proc/cpuinfo names it (model name on x86, the
+    implementer / part codes on Arm), or None."""
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+    except OSError:
+        return None
+    fields = {}
+    for line in info:
+        if ":" in line:
+            k_, v_ = line.split(":", 1)
+            fields.setdefault(k_.strip(), v_.strip())
+    if "model name" in fields:
+        return fields["model name"]
+    if "CPU part" in fields:
+        return "Arm implementer %s part %s" % (fields.get("CPU implementer", "?"), fields["CPU part"])
+    return None
 
 
 def cpu_baseline(ix, X, Qh, nprobe, R, k, true_d, budget_s=12.0):
@@ -585,6 +636,7 @@ def cpu_baseline(ix, X, Qh, nprobe, R, k, true_d, budget_s=12.0):
     dt = time.time() - t0
     rec = oracle.recall(Qh[:n2], X, res["ids"], true_d[:n2], 10)
     return {"value": round(n2 / dt, 1), "unit": "queries/s", "cores": cores, "kind": "oracle",
+            "cpu": cpu_model(),
             "sample": "first %d of the 10k queries, same index / nprobe %d / rerank %d (OpenMP over queries)"
                       % (n2, nprobe, R), "recall@10": round(rec, 4), "seconds": round(dt, 2)}
 
