@@ -635,8 +635,13 @@ def cpu_baseline(ix, X, Qh, nprobe, R, k, true_d, budget_s=12.0):
     res = oracle.search(oix, Qh[:n2], nprobe, R, k, nthreads=cores)
     dt = time.time() - t0
     rec = oracle.recall(Qh[:n2], X, res["ids"], true_d[:n2], 10)
+    # one core, for reference (a small sample)
+    n1 = 32
+    t0 = time.time()
+    oracle.search(oix, Qh[:n1], nprobe, R, k, nthreads=1)
+    one_core = n1 / (time.time() - t0)
     return {"value": round(n2 / dt, 1), "unit": "queries/s", "cores": cores, "kind": "oracle",
-            "cpu": cpu_model(),
+            "cpu": cpu_model(), "one_core_value": round(one_core, 1),
             "sample": "first %d of the 10k queries, same index / nprobe %d / rerank %d (OpenMP over queries)"
                       % (n2, nprobe, R), "recall@10": round(rec, 4), "seconds": round(dt, 2)}
 
