@@ -306,23 +306,148 @@ def test_hybrid_reduces_to_full_scan_and_graph_only(orc):
     # tau = 0: every distant probe is scanned fully -> the plain scan
     k0, nf = orc.hybrid_topr(ix, g, entry, probes, Q, bias, 100, n_near=2, efs=64, tau=0)
     assert np.array_equal(k0, full) and nf == 5
-    # efs >= list size on the 32-NN graph: the search visits the connected
-    # component of the entry; where that is the whole list, W = the list.
-    big = int(np.diff(ix["list_off"]).max())
-    W = orc.graph_search(ix, g, entry[probes[3]], Q[3], bias[3], big + 1)
-    n3 = ix["list_off"][probes[3] + 1] - ix["list_off"][probes[3]]
-    if len(W) == n3:
-        mem = ix["list_ids"][ix["list_off"][probes[3]]:ix["list_off"][probes[3] + 1]]
-        D = bias[3] + Q[3][np.arange(ix["M"])[None, :], ix["codes"][mem]].astype(np.int64).sum(1)
-        ref = np.sort(np.array([((int(a) + (1 << 31)) << 32) | int(b) for a, b in zip(D, mem)], np.uint64))
-        assert np.array_equal(W, ref)
-    # tau = infinity: graph only; the union is near lists + each graph result set
-    kinf, nf = orc.hybrid_topr(ix, g, entry, probes, Q, bias, 10_000, n_near=2, efs=16, tau=1 << 30)
+    # efs >= every list: each distant probe's graph result is the entry's
+    # reachable set (a BFS in the test); tau = infinity takes only those sets,
+    # so the expectation needs no call of the oracle's graph search.
+    big = int(np.diff(ix["list_off"]).max()) + 1
+    kinf, nf = orc.hybrid_topr(ix, g, entry, probes, Q, bias, 10_000, n_near=2, efs=big, tau=1 << 30)
     assert nf == 2
-    expect = list(orc.scan_topr(ix, probes[:2], Q[:2], bias[:2], 10_000))
+    expect = list(full_keys(ix, probes[0], Q[0], bias[0])) + list(full_keys(ix, probes[1], Q[1], bias[1]))
     for pi in range(2, 5):
-        expect += list(orc.graph_search(ix, g, entry[probes[pi]], Q[pi], bias[pi], 16))
+        reach = reachable(g, entry[probes[pi]])
+        expect += list(member_keys(ix, reach, Q[pi], bias[pi]))
     assert np.array_equal(kinf, np.sort(np.array(expect, np.uint64)))
+
+
+def reachable(g, e):
+    """Nodes reachable from e along the graph's out-edges (BFS)."""
+    seen, todo = {int(e)}, [int(e)]
+    while todo:
+        u = todo.pop()
+        for v in g[u]:
+            if v >= 0 and int(v) not in seen:
+                seen.add(int(v))
+                todo.append(int(v))
+    return np.array(sorted(seen), np.int64)
+
+
+def member_keys(ix, ids, Qp, bias_p):
+    """Sorted candidate keys ((D + 2^31) << 32) | id of the given vectors,
+    D = bias + sum_j Q[j][code_j] (Alg. 3 distance) computed with numpy."""
+    ids = np.asarray(ids, np.int64)
+    D = int(bias_p) + Qp[np.arange(ix["M"])[None, :], ix["codes"][ids]].astype(np.int64).sum(1)
+    return np.sort(np.array([((int(a) + (1 << 31)) << 32) | int(b) for a, b in zip(D, ids)], np.uint64))
+
+
+def full_keys(ix, c, Qp, bias_p):
+    return member_keys(ix, ix["list_ids"][ix["list_off"][c]:ix["list_off"][c + 1]], Qp, bias_p)
+
+
+def test_graph_search_large_pool_returns_the_reachable_set(orc):
+    """With a result capacity efs at least the number of nodes reachable from
+    the entry, best-first search (Sec. 4.4) never stops early and never
+    evicts: W is exactly the reachable set. The fixture holds lists whose
+    32-NN graph is connected (W = the whole list) and one whose entry reaches
+    only part of it; with efs below the reachable count, |W| = efs."""
+    ix, rng = tiny_index(orc, n=1200, L=6)
+    g, entry = orc.build_graph(ix)
+    q = rng.normal(size=ix["d"]).astype(np.float32)
+    allp = np.arange(ix["L"], dtype=np.int32)
+    Q, bias, _ = orc.lut_q8(q, ix, allp)
+    whole = partial = 0
+    for c in range(ix["L"]):
+        mem = ix["list_ids"][ix["list_off"][c]:ix["list_off"][c + 1]]
+        reach = reachable(g, entry[c])
+        assert set(reach.tolist()) <= set(mem.tolist())
+        whole += len(reach) == len(mem)
+        partial += len(reach) < len(mem)
+        for efs in (len(reach), len(reach) + 7):
+            W = orc.graph_search(ix, g, entry[c], Q[c], bias[c], efs)
+            assert np.array_equal(W, member_keys(ix, reach, Q[c], bias[c]))
+        for efs in (1, 5, len(reach) // 2):
+            W = orc.graph_search(ix, g, entry[c], Q[c], bias[c], efs)
+            assert len(W) == min(efs, len(reach))
+            assert set(orc.key_id(W).tolist()) <= set(reach.tolist())
+    assert whole >= 1 and partial >= 1
+
+
+# A hand-made graph with one subspace (M = 1): node i has code i, and the
+# probe's table row gives node i the distance TAB[i], so every key is set by
+# hand. Edges in adjacency order; -1 pads to 32 neighbours.
+HAND_TAB = [50, 40, 60, 70, 30, 55, 45, 10]
+HAND_EDGES = {0: [1, 2, 3], 1: [4, 5], 2: [], 3: [], 4: [6, 0], 5: [], 6: [7], 7: [6, 5]}
+
+
+def hand_graph(n_extra=0):
+    n = 8 + n_extra
+    g = -np.ones((n, 32), np.int32)
+    for u, vs in HAND_EDGES.items():
+        g[u, :len(vs)] = vs
+    return g
+
+
+def hand_key(D, i):
+    return ((D + (1 << 31)) << 32) | i
+
+
+def test_graph_search_hand_trace(orc):
+    """Best-first search of Sec. 4.4 traced by hand on an 8-node graph, efs 3.
+
+    From entry 0 (50): expand 0 -> W {0:50, 1:40, 2:60}; node 3 (70) is not
+    below max W, skipped. Expand 1 (40 < max 60) -> 4 (30) enters, 60 is
+    evicted: W {0, 1, 4}; 5 (55) is not below 50. Expand 4 -> 6 (45) enters,
+    50 evicted: W {1, 4, 6}. Pop 6: W is full and 6 is its own maximum; the
+    stop test asks for a key above the maximum, so 6 is expanded -> 7 (10)
+    enters, 45 evicted: W {1, 4, 7}. Expand 7 (no new node). Pop 2 (60 > 40):
+    stop. Result: nodes 7, 4, 1."""
+    n = 8
+    ix = {"codes": np.arange(n, dtype=np.uint8)[:, None].copy(), "M": 1, "n": n}
+    Qp = np.zeros((1, 16), np.uint8)
+    Qp[0, :n] = HAND_TAB
+    W = orc.graph_search(ix, hand_graph(), 0, Qp, 0, 3)
+    assert W.tolist() == [hand_key(10, 7), hand_key(30, 4), hand_key(40, 1)]
+    # efs 1: expand 0 -> 1 (40) replaces 0; pop 1 (= max W, expanded) -> 4
+    # (30) replaces 1; pop 4, its new neighbour 6 (45) is not below 30; no
+    # candidate is left.
+    W1 = orc.graph_search(ix, hand_graph(), 0, Qp, 0, 1)
+    assert W1.tolist() == [hand_key(30, 4)]
+    # bias shifts every key's distance, not the order
+    Wb = orc.graph_search(ix, hand_graph(), 0, Qp, -25, 3)
+    assert Wb.tolist() == [hand_key(-15, 7), hand_key(5, 4), hand_key(15, 1)]
+
+
+def test_hybrid_hand_example(orc):
+    """The hybrid of Sec. 4.4 on hand-made lists: list 0 (nodes 8..11, near,
+    distances 20, 35, 42, 90) is scanned fully; list 1 is the hand graph
+    above with efs 3, whose graph result is nodes {7, 4, 1} (10, 30, 40).
+
+    R = 2: theta = the 2nd key of the near list (35, node 9); two graph
+    results lie below it, so tau = 2 scans list 1 fully and tau = 3 does not.
+    R = 12: fewer than R near keys, theta = +inf, all 3 results count: tau =
+    3 gives the union of both whole lists, tau = 4 the near list plus {7, 4, 1}."""
+    n = 12
+    codes = np.arange(n, dtype=np.uint8)[:, None].copy()
+    ix = {"codes": codes, "M": 1, "n": n,
+          "list_off": np.array([0, 4, 12], np.int64),
+          "list_ids": np.array([8, 9, 10, 11, 0, 1, 2, 3, 4, 5, 6, 7], np.int32)}
+    g = hand_graph(n_extra=4)
+    entry = np.array([8, 0], np.int32)
+    probes = np.array([0, 1], np.int32)
+    Q = np.zeros((2, 1, 16), np.uint8)
+    Q[0, 0, 8:12] = [20, 35, 42, 90]
+    Q[1, 0, :8] = HAND_TAB
+    bias = np.zeros(2, np.int32)
+    near = [hand_key(20, 8), hand_key(35, 9), hand_key(42, 10), hand_key(90, 11)]
+    graph_only = sorted(near + [hand_key(10, 7), hand_key(30, 4), hand_key(40, 1)])
+    whole = sorted(near + [hand_key(d, i) for i, d in enumerate(HAND_TAB)])
+    k, nf = orc.hybrid_topr(ix, g, entry, probes, Q, bias, 2, n_near=1, efs=3, tau=2)
+    assert nf == 2 and k.tolist() == whole[:2]
+    k, nf = orc.hybrid_topr(ix, g, entry, probes, Q, bias, 2, n_near=1, efs=3, tau=3)
+    assert nf == 1 and k.tolist() == graph_only[:2]
+    k, nf = orc.hybrid_topr(ix, g, entry, probes, Q, bias, 12, n_near=1, efs=3, tau=3)
+    assert nf == 2 and k.tolist() == whole
+    k, nf = orc.hybrid_topr(ix, g, entry, probes, Q, bias, 12, n_near=1, efs=3, tau=4)
+    assert nf == 1 and k.tolist() == graph_only
 
 
 # ---------------------------------------------------------------- learned part
