@@ -102,7 +102,10 @@ typedef struct {
 } ksc_index_arrays;
 
 /* Create an index from host arrays (copied; the caller keeps ownership).
- * Blocking. */
+ * Before any device work the arrays are checked on the host: every code
+ * below 16, every assignment in [0, nlist), and, with a graph, every
+ * neighbour -1 or a row of the same list and every entry -1 or a row of its
+ * list; KSC_EINVAL otherwise.  Blocking. */
 int ksc_index_import(const ksc_index_arrays* a, void* stream, ksc_index** out);
 
 /* Query the sizes of an index: fills n, d, nlist, M, metric, spherical of *a

@@ -506,6 +506,31 @@ int ksc_index_import(const ksc_index_arrays* a, void* stream, ksc_index** out) {
                   "null argument");
     KSC_TRY(check_shape(a->n, a->d, a->nlist, a->M));
     KSC_CHECK_ARG(a->metric == KSC_L2 || a->metric == KSC_IP, "bad metric");
+    // Every index the device code follows is checked here, on the host,
+    // before any device work: codes address 16-entry tables, lists address
+    // the list arrays, and the graph preparation and search take a neighbour
+    // (or a list's entry) as a position inside its own list, so a neighbour
+    // of another list would address codes and visited bits outside the list.
+    const int64_t ncodes = a->n * a->M;
+    for (int64_t i = 0; i < ncodes; ++i)
+        KSC_CHECK_ARG(a->codes[i] < PQ_K, "code %lld is out of range", (long long)i);
+    for (int64_t i = 0; i < a->n; ++i)
+        KSC_CHECK_ARG(a->assign[i] >= 0 && a->assign[i] < a->nlist, "assignment of row %lld out of range",
+                      (long long)i);
+    if (a->graph && a->entry) {
+        for (int64_t u = 0; u < a->n; ++u)
+            for (int e = 0; e < 32; ++e) {
+                const int32_t v = a->graph[u * 32 + e];
+                KSC_CHECK_ARG(v >= -1 && v < a->n, "neighbour %d of row %lld is out of range", e, (long long)u);
+                KSC_CHECK_ARG(v < 0 || a->assign[v] == a->assign[u],
+                              "neighbour %d of row %lld is in another list", e, (long long)u);
+            }
+        for (int32_t p = 0; p < a->nlist; ++p) {
+            const int32_t v = a->entry[p];
+            KSC_CHECK_ARG(v >= -1 && v < a->n, "graph entry of list %d is out of range", p);
+            KSC_CHECK_ARG(v < 0 || a->assign[v] == p, "graph entry of list %d is not in the list", p);
+        }
+    }
     cudaStream_t st = as_stream(stream);
     ksc_index* ix = new ksc_index();
     ix->n = a->n;

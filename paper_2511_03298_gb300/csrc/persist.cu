@@ -202,7 +202,8 @@ int ksc_index_load(const char* path, void* stream, ksc_index** out) {
                     get(file.f, pr_model.data(), s.pr_model) && get(file.f, &theta, s.pr_theta) &&
                     get(file.f, dims.data(), s.dims) && get(file.f, X_full.data(), s.X_full);
     KSC_CHECK_ARG(ok, "%s: read failed", path);
-    // every index the device code will follow
+    // index ranges; list membership of neighbours and entries is checked by
+    // ksc_index_import below, still before any device work
     for (uint8_t c : codes) KSC_CHECK_ARG(c < PQ_K, "%s: a code is out of range", path);
     for (int32_t p : assign) KSC_CHECK_ARG(p >= 0 && p < h.nlist, "%s: a list index is out of range", path);
     for (int32_t v : graph) KSC_CHECK_ARG(v >= -1 && v < h.n, "%s: a neighbour index is out of range", path);

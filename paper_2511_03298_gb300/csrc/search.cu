@@ -9,6 +9,7 @@
 //                 u16x2 lane sums, cross-lane reduce-scatter
 //   a5 select   : R smallest (D, id) keys per query (radix select + bitonic)
 //   a6 rerank   : exact FP32 distances of the R candidates, top-k
+#include <atomic>
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -2433,14 +2434,14 @@ static int launch_luts(const LutArgs& A, uint32_t* rb, uint8_t* lut, int32_t* bi
     const int64_t tiles = (A.nq * A.Pmax + per - 1) / per;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)num_sms() * 8));
     if (lut_ds2(A)) {
-        cudaFuncSetAttribute(k_lut_range<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_lut_quant<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        KSC_CUDA(cudaFuncSetAttribute(k_lut_range<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        KSC_CUDA(cudaFuncSetAttribute(k_lut_quant<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_lut_range<2><<<grid, 256, smem, st>>>(A, rb);
         KSC_LAUNCH_CHECK();
         k_lut_quant<2><<<grid, 256, smem, st>>>(A, rb, lut, bias, scale);
     } else {
-        cudaFuncSetAttribute(k_lut_range<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_lut_quant<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        KSC_CUDA(cudaFuncSetAttribute(k_lut_range<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        KSC_CUDA(cudaFuncSetAttribute(k_lut_quant<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_lut_range<0><<<grid, 256, smem, st>>>(A, rb);
         KSC_LAUNCH_CHECK();
         k_lut_quant<0><<<grid, 256, smem, st>>>(A, rb, lut, bias, scale);
@@ -3018,8 +3019,10 @@ static __device__ __align__(256) uint32_t g_noalloc_range[KSC_NOALLOC_MAX_NQ];
 namespace ksc {
 // Device address of g_noalloc_range per device ordinal, looked up on the first
 // call made with that device current (host code cannot use the symbol itself:
-// in host code it names a host-side stand-in, not device memory).
-static void* g_noalloc_addr[64] = {};
+// in host code it names a host-side stand-in, not device memory).  Atomic, so
+// that host threads making their first call on one device at the same time
+// do not race on the cache (they store the same address).
+static std::atomic<void*> g_noalloc_addr[64] = {};
 }  // namespace ksc
 
 extern "C" int ksc_compute_luts_noalloc(ksc_index* ix, const float* Q_dev, int64_t nq, const int32_t* probes_dev,
@@ -3039,12 +3042,12 @@ extern "C" int ksc_compute_luts_noalloc(ksc_index* ix, const float* Q_dev, int64
     int dev = 0;
     KSC_CUDA(cudaGetDevice(&dev));
     KSC_CHECK_ARG(dev >= 0 && dev < 64, "device ordinal %d out of range", dev);
-    if (!g_noalloc_addr[dev]) {
-        void* addr = nullptr;
+    void* addr = g_noalloc_addr[dev].load(std::memory_order_acquire);
+    if (!addr) {
         KSC_CUDA(cudaGetSymbolAddress(&addr, g_noalloc_range));
-        g_noalloc_addr[dev] = addr;
+        g_noalloc_addr[dev].store(addr, std::memory_order_release);
     }
-    uint32_t* rb = static_cast<uint32_t*>(g_noalloc_addr[dev]);
+    uint32_t* rb = static_cast<uint32_t*>(addr);
     cudaStream_t st = as_stream(stream);
     // the array keeps the previous call's ranges: clear this call's slots
     KSC_CUDA(cudaMemsetAsync(rb, 0, sizeof(uint32_t) * nq, st));

@@ -133,3 +133,55 @@ def test_index_load_rejects_bad_files_before_device_work(lib, tmp_path):
     assert lib.ksc_index_load(None, None, C.byref(h)) == -1
     assert lib.ksc_index_save(None, b"x") == -1
     assert h.value is None
+
+
+def test_index_import_rejects_foreign_neighbours_before_device_work(lib):
+    """ksc_index_import checks on the host that a graph's neighbours and a
+    list's entry lie in that list (the device search follows them as
+    positions inside the list), and that codes and assignments are in range:
+    KSC_EINVAL before any device work."""
+    from paper_2511_03298_gb300 import ksc
+    rng = np.random.default_rng(2)
+    n, d, nlist, M = 64, 8, 4, 4
+    X = rng.normal(size=(n, d)).astype(np.float32)
+    cr = rng.normal(size=(nlist, d)).astype(np.float32)
+    cb = rng.normal(size=(M, 16, d // M)).astype(np.float32)
+    assign = (np.arange(n) % nlist).astype(np.int32)
+    # neighbours: the other members of the row's own list, -1 padded
+    graph = -np.ones((n, 32), np.int32)
+    for u in range(n):
+        mem = [v for v in range(n) if assign[v] == assign[u] and v != u]
+        graph[u, :len(mem)] = mem
+    entry = np.arange(nlist, dtype=np.int32)  # row p is in list p
+
+    def attempt(codes, assign, graph, entry):
+        a = ksc.IndexArrays(n=n, d=d, nlist=nlist, M=M, metric=0, spherical=0)
+        keep = [X, cr, cr, cb, codes, assign, graph, entry]
+        for name, arr in zip(("X", "c_rank", "c_mean", "codebook", "codes", "assign", "graph", "entry"), keep):
+            setattr(a, name, None if arr is None else arr.ctypes.data)
+        h = C.c_void_p()
+        rc = lib.ksc_index_import(C.byref(a), None, C.byref(h))
+        assert h.value is None
+        return rc, lib.ksc_last_error()
+
+    codes = rng.integers(0, 16, (n, M)).astype(np.uint8)
+    g = graph.copy()
+    g[5, 3] = 6  # row 6 is in list 2, row 5 in list 1
+    rc, msg = attempt(codes, assign, g, entry)
+    assert rc == -1 and b"another list" in msg
+    e = entry.copy()
+    e[2] = 7  # row 7 is in list 3
+    rc, msg = attempt(codes, assign, graph, e)
+    assert rc == -1 and b"not in the list" in msg
+    g = graph.copy()
+    g[0, 0] = n
+    rc, msg = attempt(codes, assign, g, entry)
+    assert rc == -1 and b"out of range" in msg
+    c = codes.copy()
+    c[3, 1] = 16
+    rc, msg = attempt(c, assign, graph, entry)
+    assert rc == -1 and b"code" in msg
+    a2 = assign.copy()
+    a2[10] = nlist
+    rc, msg = attempt(codes, a2, None, None)
+    assert rc == -1 and b"assignment" in msg

@@ -63,3 +63,47 @@ def test_noalloc_rejects_batches_beyond_its_scratch(env):
     rc = lib.ksc_compute_luts_noalloc(ix.handle, C.c_void_p(16), 65537, C.c_void_p(16), 4, C.c_void_p(16),
                                       C.c_void_p(16), C.c_void_p(16), None)
     assert rc == -1 and b"exceeds the fixed scratch" in lib.ksc_last_error()
+
+
+def test_noalloc_first_call_on_a_fresh_index_allocates_nothing(env):
+    """A second index with sub-vectors of width 4 (d 32, M 8) runs the generic
+    table kernels rather than the width-2 ones.  Its first table call goes
+    through the allocation-free entry point, before the allocating one has
+    given it any workspace: the device's free memory is the same before and
+    after the call, and the tables equal the allocating entry point's
+    afterwards.  The module holding the scratch array is already loaded by
+    the first index's calls, so loading it does not count here."""
+    torch, ksc, ix_o, ix, rng = env
+    q0 = torch.from_numpy(ix_o["X"][:4].copy()).cuda()
+    p0 = torch.zeros((4, 2), dtype=torch.int32, device="cuda")
+    p0[:, 1] = 1
+    _luts(torch, ksc, ix, q0, p0, noalloc=True)  # module and scratch address resolved
+    X = ix_o["X"]
+    ix_o8 = oracle.build_index(X, 16, 8, False, rng.permutation(len(X)).astype(np.int64), iters=4)
+    ix8 = ksc.index_import(ix_o8)
+    assert ix8.info()["M"] == 8 and ix8.info()["d"] // 8 == 4
+    for nq, P in [(200, 5), (64, 11)]:
+        Q = (X[rng.integers(0, len(X), nq)] + rng.normal(size=(nq, 32))).astype(np.float32)
+        probes = np.stack([oracle.rank(q, ix_o8["c_rank"], False, P)[0] for q in Q]).astype(np.int32)
+        Qd = torch.from_numpy(Q).cuda()
+        pd = torch.from_numpy(probes).cuda()
+        lut = torch.full((nq, P, 8, 16), 7, dtype=torch.uint8, device="cuda")
+        bias = torch.full((nq, P), -5, dtype=torch.int32, device="cuda")
+        scale = torch.full((nq,), -1.0, dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        st = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        rc = ksc.lib().ksc_compute_luts_noalloc(ix8.handle, C.c_void_p(Qd.data_ptr()), nq, C.c_void_p(pd.data_ptr()),
+                                                P, C.c_void_p(lut.data_ptr()), C.c_void_p(bias.data_ptr()),
+                                                C.c_void_p(scale.data_ptr()), st)
+        assert rc == 0, ksc.lib().ksc_last_error()
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+        got = (lut.cpu().numpy(), bias.cpu().numpy(), scale.cpu().numpy())
+        ref = _luts(torch, ksc, ix8, Qd, pd, noalloc=False)
+        for r, g in zip(ref, got):
+            assert np.array_equal(r, g)
+        # and the oracle's tables for the first query (the generic path is
+        # pinned independently of the allocating entry point)
+        Qo, bo, _ = oracle.lut_q8(Q[0], ix_o8, probes[0])
+        assert np.array_equal(got[0][0], Qo) and np.array_equal(got[1][0], bo)
