@@ -459,8 +459,7 @@ def run_ours(args, rank, ws):
         scan_ms = plain_stage["scan"] + plain_stage["near_scan"]
         peak_gl = ksc.lut16_peak()
         achieved_gl = lookups / (scan_ms * 1e-3) / 1e9
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
+        peaks = measured_peaks()
         # streaming form of the scan (few queries, each list read once from
         # DRAM): 8 queries at nprobe 128, L2 flushed before each search; code
         # bytes of the probed lists over the time of the two scan stages
@@ -603,6 +602,16 @@ def run_ours(args, rank, ws):
             "build_s": round(build_s, 2),
             "cpu_baseline": cpu,
         }
+        if ws == 1 and not args.no_extra:
+            # the other configurations, compact (not the headline): the 10M x 96
+            # index (streaming scan, batches with per-query nprobe) and the
+            # 1.2M x 100 inner-product index (re-rank precision variants)
+            for name, fn in (("deep", lambda: deep_workload(torch, ksc, synth, dev, flush, args)),
+                             ("glove", lambda: glove_workload(torch, ksc, synth, dev, flush))):
+                try:
+                    out[name] = fn()
+                except Exception as ex:  # reported, never fatal to the headline line
+                    out[name] = {"error": str(ex)[:300]}
     return out
 
 
@@ -652,6 +661,149 @@ def cpu_baseline(ix, X, Qh, nprobe, R, k, true_d, budget_s=12.0):
                       % (n2, nprobe, R), "recall@10": round(rec, 4), "seconds": round(dt, 2)}
 
 
+def stage_median(ix, fn, flush, warm, reps):
+    """Per-stage library times (median over `reps` calls, L2 flushed before
+    each) and the median wall time of the call on the current stream."""
+    import torch
+    for _ in range(warm):
+        fn()
+    ix.profile(True)
+    st, tot = [], []
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        e1.synchronize()
+        pp, _ = ix.profile_read()
+        st.append(pp)
+        tot.append(e0.elapsed_time(e1))
+    ix.profile(False)
+    return {k_: statistics.median([p_[k_] for p_ in st]) for k_ in st[0]}, statistics.median(tot)
+
+
+def deep_workload(torch, ksc, synth, dev, flush, args, batches=(16, 1024, 16384), stream_batches=(16, 64, 256),
+                  stream_reps=5, stream_nprobe=256):
+    """The 10M x 96 configuration (unit-norm, Zipf(1.1) components, nlist 8192,
+    M 48, k 100, rerank 1000), built on the GPU.
+
+    stream: the scan where it streams its codes from DRAM (the 240 MB code
+    array is larger than L2): batches of 16 .. 256 queries at nprobe 256, L2
+    flushed before each search.  Per-(query, list) code bytes (each pair reads
+    its list's n_p M / 2 bytes) over the time of the two scan stages, against
+    the measured HBM copy peak; the unique code bytes those pairs touch (the
+    DRAM bytes of an ideal cluster-major schedule) beside them.
+    batches: per-query nprobe U{4..256}, the variable-nprobe path, autotuned
+    from 256 queries up; recall@100 on a 1000-query sample."""
+    c = synth.CONFIGS[4]
+    out = {}
+    t0 = time.time()
+    X = synth.base(4)
+    out["gen_s"] = round(time.time() - t0, 1)
+    Xd = torch.from_numpy(X).to(dev)
+    del X
+    t0 = time.time()
+    ix = ksc.build_index(Xd, c["L"], c["M"], spherical=True, perm=synth.build_perm(4, c["n"]))
+    torch.cuda.synchronize()
+    out["build_s"] = round(time.time() - t0, 1)
+    k, R, M = c["k"], c["R"], c["M"]
+    sizes = np.bincount(ix.export(fields=("assign",))["assign"], minlength=c["L"])
+    peaks = measured_peaks()
+    nq_max = max(list(batches) + list(stream_batches) + [1000])
+    Qh = synth.queries(4, nq_max)
+    Qd = torch.from_numpy(Qh).to(dev)
+    stream = {}
+    for B in stream_batches:
+        q = Qd[:B].contiguous()
+        pr = ix.rank_lists(q, stream_nprobe, want_scores=False)[0].cpu().numpy()
+        cb = int(sizes[pr].sum()) * M // 2
+        ub = int(sizes[np.unique(pr)].sum()) * M // 2
+        stg, tot = stage_median(ix, lambda: ix.search(q, k, stream_nprobe, R), flush, 3, stream_reps)
+        sms = stg["near_scan"] + stg["scan"]
+        gbs = cb / (sms * 1e-3) / 1e9
+        stream[str(B)] = {"nprobe": stream_nprobe, "code_bytes": cb, "unique_code_bytes": ub,
+                          "scan_ms": round(sms, 4), "search_ms": round(tot, 4), "GBps": round(gbs, 1),
+                          "frac_of_hbm": round(gbs / peaks["hbm_gbs"], 4),
+                          "frac_of_nominal": round(gbs / HBM_NOMINAL_GBS, 4),
+                          "stage_ms": {k_: round(v_, 4) for k_, v_ in stg.items()}}
+    if stream:
+        out["scan_stream_deep"] = {"l2": "flushed (256 MB write) before each search", "rerank": R, "k": k,
+                                   "batches": stream, "hbm_peak_gbs": peaks["hbm_gbs"],
+                                   "peak_source": peaks.get("source")}
+    if batches:
+        npb = torch.from_numpy(synth.per_query_nprobe(4, nq_max)).to(dev)
+        rr = torch.full((nq_max,), R, dtype=torch.int32, device=dev)
+        ns = 1000
+        ids, _ = ix.search_varprobe(Qd[:ns], k, npb[:ns], rr[:ns], nprobe_max=256, rerank_max=R)
+        kth = kth_fp32(torch, Xd, Qd[:ns], k, chunk=64)
+        d = ((Xd[ids.clamp_min(0)] - Qd[:ns, None, :]) ** 2).sum(-1)
+        out["recall@100_sample1000"] = round(float(((d <= kth[:, None] + 1e-5) & (ids >= 0)).sum(1)
+                                                 .clamp_max(k).double().mean() / k), 4)
+        res = {}
+        for B in batches:
+            q, nb = Qd[:B], npb[:B]
+            # tuned at the mean of the nprobe distribution
+            o = ix.autotune(q, k, 130, R)[0] if B >= 256 else ksc.search_opts()
+            fn = lambda: ix.search_varprobe(q, k, nb, rr[:B], nprobe_max=256, rerank_max=R, opts=o)
+            stg, ms = stage_median(ix, fn, flush, 3, 5)
+            sts = ix.search_stats()
+            res[str(B)] = {"ms": round(ms, 4), "qps": round(B / (ms * 1e-3), 1),
+                           "candidates_per_query": round(sts["candidates"] / B, 1),
+                           "overflow_queries": sts["overflow_queries"],
+                           "lanes_per_query": o.lanes_per_query, "tile_blocks": o.tile_blocks,
+                           "stage_ms": {s_: round(v, 4) for s_, v in stg.items()}}
+        out["batches"] = res
+    del ix, Xd
+    torch.cuda.empty_cache()
+    return out
+
+
+def glove_workload(torch, ksc, synth, dev, flush):
+    """The 1.2M x 100 inner-product configuration (nlist 2048, M 50, k 10):
+    FP32 re-rank of R = 200 against BF16 / FP8-e4m3 re-rank of a widened
+    shortlist (400, 800) before the FP32 re-rank of the best 100, each at the
+    smallest nprobe reaching recall@10 0.90."""
+    c = synth.CONFIGS[3]
+    X = synth.base(3)
+    Xd = torch.from_numpy(X).to(dev)
+    del X
+    ix = ksc.build_index(Xd, c["L"], c["M"], metric="ip", spherical=True, perm=synth.build_perm(3, c["n"]))
+    Qh = synth.queries(3)
+    Qd = torch.from_numpy(Qh).to(dev)
+    k = c["k"]
+    sims = []
+    for b in range(0, len(Qh), 2048):
+        sims.append(torch.topk(Qd[b:b + 2048] @ Xd.T, k, dim=1).values[:, k - 1])
+    kth = torch.cat(sims)
+    res = {}
+    for name, opts, Rw in (("fp32_R200", None, 200),
+                           ("bf16_Rw400_Rf100", ksc.search_opts(precision=1, rerank_final=100), 400),
+                           ("fp8_Rw800_Rf100", ksc.search_opts(precision=2, rerank_final=100), 800)):
+        for P in (8, 12, 16, 24, 32, 48, 64):
+            ids, dd = ix.search(Qd, k, P, Rw, opts=opts)
+            sim = (Xd[ids.clamp_min(0)] * Qd[:, None, :]).sum(-1)
+            rec = float(((sim >= kth[:, None] - 1e-5) & (ids >= 0)).sum(1).clamp_max(k).double().mean() / k)
+            if rec >= TARGET_RECALL:
+                break
+        stg, ms = stage_median(ix, lambda: ix.search(Qd, k, P, Rw, opts=opts), flush, 3, 5)
+        res[name] = {"nprobe": P, "recall@10": round(rec, 4), "ms": round(ms, 4), "qps": round(len(Qh) / (ms * 1e-3), 1),
+                     "rerank_ms": round(stg["rerank"], 4)}
+    del ix, Xd
+    torch.cuda.empty_cache()
+    return {"variants": res, "n": c["n"], "d": c["d"], "nlist": c["L"], "M": c["M"], "metric_space": "inner product"}
+
+
+def measured_peaks():
+    """The measured peaks of the GB300s, else the fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        pk = json.load(open(path))
+        pk["source"] = "measured (MEASURED_PEAKS.json)"
+        return pk
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
+
+
 def run_workload(args):
     """Secondary workloads (one JSON line each, not the headline):
     deep  -- 10M x 96 unit-norm, Zipf(1.1) components, nlist 8192, M 48,
@@ -673,103 +825,16 @@ def run_workload(args):
     dev = torch.device("cuda", 0)
     out = {"workload": args.workload, "data": "synthetic (seeded mixture)", "n_gpus": 1}
     st = torch.cuda.Stream()
-    if args.workload == "deep":
-        c = synth.CONFIGS[4]
-        t0 = time.time()
-        X = synth.base(4)
-        gen_s = time.time() - t0
-        Xd = torch.from_numpy(X).to(dev)
-        del X
-        t0 = time.time()
-        ix = ksc.build_index(Xd, c["L"], c["M"], spherical=True, perm=synth.build_perm(4, c["n"]))
-        torch.cuda.synchronize()
-        out["build_s"] = round(time.time() - t0, 1)
-        out["gen_s"] = round(gen_s, 1)
-        k, R = c["k"], c["R"]
-        nq_max = 16384
-        Qh = synth.queries(4, nq_max)
-        Qd = torch.from_numpy(Qh).to(dev)
-        npb = torch.from_numpy(synth.per_query_nprobe(4, nq_max)).to(dev)
-        rr = torch.full((nq_max,), R, dtype=torch.int32, device=dev)
-        # recall on a sample (FP32 brute force on the GPU: measurement only)
-        ns = 1000
-        ids, _ = ix.search_varprobe(Qd[:ns], k, npb[:ns], rr[:ns], nprobe_max=256, rerank_max=R)
-        kth = kth_fp32(torch, Xd, Qd[:ns], k, chunk=64)
-        d = ((Xd[ids.clamp_min(0)] - Qd[:ns, None, :]) ** 2).sum(-1)
-        out["recall@100_sample1000"] = round(float(((d <= kth[:, None] + 1e-5) & (ids >= 0)).sum(1)
-                                                 .clamp_max(k).double().mean() / k), 4)
+    if args.workload in ("deep", "stream"):
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-        batches = {}
-        with torch.cuda.stream(st):
-            for B in (1, 16, 256, 1024, 4096, 16384):
-                q, nb = Qd[:B], npb[:B]
-                # tuned at the mean of the nprobe distribution
-                o = ix.autotune(q, k, 130, R)[0] if B >= 256 else ksc.search_opts()
-                fn = lambda: ix.search_varprobe(q, k, nb, rr[:B], nprobe_max=256, rerank_max=R, opts=o)
-                for _ in range(3):
-                    fn()
-                times = []
-                for _ in range(5):
-                    flush.zero_()
-                    e0 = torch.cuda.Event(enable_timing=True)
-                    e1 = torch.cuda.Event(enable_timing=True)
-                    e0.record(st)
-                    fn()
-                    e1.record(st)
-                    e1.synchronize()
-                    times.append(e0.elapsed_time(e1))
-                ms = statistics.median(times)
-                ix.profile(True)
-                fn()
-                prof, _ = ix.profile_read()
-                ix.profile(False)
-                sts = ix.search_stats()
-                batches[B] = {"ms": round(ms, 4), "qps": round(B / (ms * 1e-3), 1),
-                              "candidates_per_query": round(sts["candidates"] / B, 1),
-                              "overflow_queries": sts["overflow_queries"],
-                              "lanes_per_query": o.lanes_per_query, "tile_blocks": o.tile_blocks,
-                              "stage_ms": {s_: round(v, 4) for s_, v in prof.items()}}
-        out["batches"] = batches
-        out["metric"] = "QPS per batch size (per-query nprobe U{4..256}, k 100, R 1000)"
+        out.update(deep_workload(torch, ksc, synth, dev, flush, args,
+                                 batches=(1, 16, 256, 1024, 4096, 16384) if args.workload == "deep" else (),
+                                 stream_batches=(16, 64, 256) if args.stream_batch == 0 else (args.stream_batch,),
+                                 stream_reps=5 if args.workload == "deep" else args.steps))
+        out["metric"] = "QPS per batch size (per-query nprobe U{4..256}, k 100, R 1000); streaming scan GB/s"
     elif args.workload == "glove":
-        c = synth.CONFIGS[3]
-        X = synth.base(3)
-        Xd = torch.from_numpy(X).to(dev)
-        ix = ksc.build_index(Xd, c["L"], c["M"], metric="ip", spherical=True, perm=synth.build_perm(3, c["n"]))
-        Qh = synth.queries(3)
-        Qd = torch.from_numpy(Qh).to(dev)
-        k = c["k"]
-        # inner-product ground truth: top-k similarity (FP32 on the GPU)
-        sims = []
-        for b in range(0, len(Qh), 2048):
-            sims.append(torch.topk(Qd[b:b + 2048] @ Xd.T, k, dim=1).values[:, k - 1])
-        kth = torch.cat(sims)
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-        res = {}
-        for name, opts, Rw in (("fp32_R200", None, 200), ("bf16_Rw400_Rf100", ksc.search_opts(precision=1, rerank_final=100), 400),
-                               ("fp8_Rw800_Rf100", ksc.search_opts(precision=2, rerank_final=100), 800)):
-            for P in (8, 12, 16, 24, 32, 48, 64):
-                ids, dd = ix.search(Qd, k, P, Rw, opts=opts)
-                sim = (Xd[ids.clamp_min(0)] * Qd[:, None, :]).sum(-1)
-                rec = float(((sim >= kth[:, None] - 1e-5) & (ids >= 0)).sum(1).clamp_max(k).double().mean() / k)
-                if rec >= TARGET_RECALL:
-                    break
-            fn = lambda: ix.search(Qd, k, P, Rw, opts=opts)
-            for _ in range(3):
-                fn()
-            times = []
-            for _ in range(5):
-                flush.zero_()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record()
-                fn()
-                e1.record()
-                e1.synchronize()
-                times.append(e0.elapsed_time(e1))
-            ms = statistics.median(times)
-            res[name] = {"nprobe": P, "recall@10": round(rec, 4), "ms": round(ms, 4), "qps": round(len(Qh) / (ms * 1e-3), 1)}
-        out["variants"] = res
+        out.update(glove_workload(torch, ksc, synth, dev, flush))
         out["metric"] = "QPS at recall@10>=0.90 per re-rank precision (1.2M x 100, inner product)"
     elif args.workload == "fashion":
         # component filtration (Sec. 4.3): the same 60k x 784 image-like data
@@ -948,8 +1013,12 @@ def main():
     ap.add_argument("--lanes", type=int, default=0, help="scan lanes per query (0 auto; 4, 8, 16, 32)")
     ap.add_argument("--tile-blocks", type=int, default=0, help="scan tile length in blocks (0 auto)")
     ap.add_argument("--scan-tc", type=int, default=0, help="1: the scan on the tensor cores")
-    ap.add_argument("--workload", default="sift", choices=["sift", "deep", "glove", "fashion", "latency"],
-                    help="sift: the headline line; deep / glove: secondary workloads")
+    ap.add_argument("--workload", default="sift", choices=["sift", "deep", "glove", "fashion", "latency", "stream"],
+                    help="sift: the headline line; deep / glove / fashion / latency: secondary workloads; "
+                         "stream: the streaming scan of the 10M x 96 index alone")
+    ap.add_argument("--stream-batch", type=int, default=0, help="stream workload: one batch size (0: 16, 64, 256)")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="headline line without the 10M x 96 and 1.2M x 100 summaries")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.workload != "sift":

@@ -1289,9 +1289,18 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32, (SMAX <= 2 ? 3 : (SMAX <= 8 ?
     int b = 0;
     bool failed = false;
     while (true) {
-        // item set-up: LUTs, bias and threshold of this lane group's query
-        const int64_t pi = slot;
-        const bool active = pi < x.npairs;
+        // item set-up: LUTs, bias and threshold of this lane group's query.
+        // An item with fewer pairs than query slots (few queries probe the
+        // list) gives every pair rep = QG / npw slots (npw: the pair count
+        // rounded up to a power of two), which take interleaved blocks of each
+        // chunk: slot = ph * npw + pi scans blocks ph, ph + rep, ...
+        const int np_eff = (int)(x.npairs < QG ? x.npairs : QG);
+        int npw = 1;
+        while (npw < np_eff) npw <<= 1;
+        const int rep = QG / npw;
+        const int64_t pi = slot % npw;
+        const int ph = slot / npw;
+        const bool active = pi < np_eff;
         int64_t q = 0;
         uint4 t[SMAX];
         int32_t bias = 0, lim = -1;
@@ -1362,11 +1371,16 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32, (SMAX <= 2 ? 3 : (SMAX <= 8 ?
                 const uint8_t* chunk = mybuf + b * SCAN_CHUNK_BYTES;
                 const int c0 = x.b0 + c * cb, nblk = min(x.b1, c0 + cb) - c0;
                 const int64_t gb0 = A.boff[x.p] + c0;
-                for (int blk = 0; blk < nblk; ++blk) {
-                    const uint4* cp = reinterpret_cast<const uint4*>(chunk + blk * blk_bytes);
+                // the same number of steps on every lane (the reduction is a
+                // warp-wide shuffle); a slot past the chunk's last block reads
+                // the last block again and keeps nothing
+                for (int blk0 = 0; blk0 < nblk; blk0 += rep) {
+                    const int blk = blk0 + ph;
+                    const bool vb = active && blk < nblk;
+                    const uint4* cp = reinterpret_cast<const uint4*>(chunk + min(blk, nblk - 1) * blk_bytes);
                     const uint32_t vslot = (uint32_t)((gb0 + blk) * 32 + V * g);
                     uint32_t idv[V];
-                    if (direct && active) {
+                    if (direct && vb) {
 #pragma unroll
                         for (int v = 0; v < V; ++v) idv[v] = (uint32_t)A.ids[vslot + v];
                     }
@@ -1390,7 +1404,7 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32, (SMAX <= 2 ? 3 : (SMAX <= 8 ?
                     uint32_t sums[V];
                     reduce_scatter<G>(acc, lane, sums);
                     if (direct) {
-                        if (active) {
+                        if (vb) {
                             const int nv = listn - (c0 + blk) * 32;
                             const int64_t pos = noff + (int64_t)(c0 + blk) * 32 + V * g;
                             uint64_t* out = O.cand + q * O.cap;
@@ -1406,7 +1420,7 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32, (SMAX <= 2 ? 3 : (SMAX <= 8 ?
                     // tail, excluded by the list length); an id is read only
                     // on a tie with the threshold's distance
                     uint32_t kmask = 0;
-                    if (active) {
+                    if (vb) {
                         const int nv = listn - (c0 + blk) * 32 - V * g;  // valid vectors of this lane
                         const uint32_t vm = nv >= V ? (1u << V) - 1u : (nv > 0 ? (1u << nv) - 1u : 0u);
                         uint32_t eq = 0;
@@ -2324,10 +2338,14 @@ static int choose_G(const ksc_index* ix, int64_t nq, int Pmax, int want) {
         int S = (ix->M + want - 1) / want;
         if (S <= 16) return want;
     }
-    // few (query, probe) pairs per list: one query per warp keeps every lane busy
-    double pairs_per_list = (double)nq * Pmax / ix->L;
-    if (ix->M <= 128 && pairs_per_list >= 8) return 8;
-    if (ix->M <= 256 && pairs_per_list >= 4) return 16;
+    // 8 lanes per query (4 query slots per warp) up to 128 subspaces: when
+    // fewer queries than slots probe a list, the item's slots split its
+    // blocks instead, so every lane stays busy at any batch size, and the
+    // per-block reduction runs over 8 lanes only
+    (void)nq;
+    (void)Pmax;
+    if (ix->M <= 128) return 8;
+    if (ix->M <= 256) return 16;
     return 32;
 }
 
@@ -2367,6 +2385,8 @@ static int dispatch_scan(int S, const ScanArgs& A, const ScanOut& O, const int64
                          cudaStream_t st) {
     if (S <= 2) return launch_scan<G, 2>(A, O, pair_off, item_off, pairs, L, TB, status, st);
     if (S <= 4) return launch_scan<G, 4>(A, O, pair_off, item_off, pairs, L, TB, status, st);
+    if constexpr (G == 8)
+        if (S == 6) return launch_scan<G, 6>(A, O, pair_off, item_off, pairs, L, TB, status, st);  // M 48
     if (S <= 8) return launch_scan<G, 8>(A, O, pair_off, item_off, pairs, L, TB, status, st);
     if (S <= 16) return launch_scan<G, 16>(A, O, pair_off, item_off, pairs, L, TB, status, st);
     set_error("M too large for %d lanes per query", G);

@@ -211,12 +211,14 @@ class Index:
         _check(lib().ksc_index_dims(self._h, _hptr(dims), C.byref(dfull)))
         return dfull.value, dims
 
-    def export(self, with_graph=False):
+    def export(self, with_graph=False, fields=None):
+        """Copy the index's interchange arrays to the host; `fields` (a subset
+        of X, c_rank, c_mean, codebook, codes, assign) limits the copy."""
         inf = self.info()
         n, d, L, M = inf["n"], inf["d"], inf["nlist"], inf["M"]
-        out = dict(X=np.zeros((n, d), np.float32), c_rank=np.zeros((L, d), np.float32),
-                   c_mean=np.zeros((L, d), np.float32), codebook=np.zeros((M, 16, d // M), np.float32),
-                   codes=np.zeros((n, M), np.uint8), assign=np.zeros(n, np.int32))
+        shapes = dict(X=((n, d), np.float32), c_rank=((L, d), np.float32), c_mean=((L, d), np.float32),
+                      codebook=((M, 16, d // M), np.float32), codes=((n, M), np.uint8), assign=((n,), np.int32))
+        out = {k: np.zeros(*v) for k, v in shapes.items() if fields is None or k in fields}
         if with_graph:
             out["graph"] = np.zeros((n, 32), np.int32)
             out["entry"] = np.zeros(L, np.int32)

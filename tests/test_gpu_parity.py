@@ -61,6 +61,9 @@ def small_index(kind):
         elif kind == "ds3ip":  # d' = 3, inner product
             X, Q, perm = mixture(3000, 36, 10, 15, ip=True)
             ix = oracle.build_index(X, 10, 12, True, perm, iters=5, ip=True)
+        elif kind == "m48":  # d = 96, M = 48: six subspaces per lane at 8 lanes per query
+            X, Q, perm = mixture(5000, 96, 20, 16, ip=True)
+            ix = oracle.build_index(X, 20, 48, True, perm, iters=5)
         elif kind == "small":  # the 10k x 128 configuration
             X = synth.base(1)
             Q = synth.queries(1)
@@ -153,6 +156,33 @@ def test_scan_candidates_bit_exact(torch, ksc, kind, lanes):
         assert np.array_equal(cand[qi, :len(ref)], ref), qi
         ref_ids[qi], ref_d[qi] = oracle.rerank(Q[qi], ix, oracle.key_id(ref).astype(np.int32), k)
     check_results(ix, Q, ids, dists, ref_ids, ref_d, k)
+    assert g.last_status() == 0
+
+
+@pytest.mark.parametrize("kind,lanes", [("l2", 0), ("l2", 16), ("m48", 0), ("m50", 8), ("ip", 8)])
+@pytest.mark.parametrize("nq", [1, 2, 3, 5])
+def test_scan_sparse_lists_bit_exact(torch, ksc, kind, lanes, nq):
+    """Few queries, so most lists are probed by fewer queries than a warp has
+    query slots: the slots of such an item split its blocks.  Candidates equal
+    the oracle's bit for bit (both scan parts: the nearest lists without a
+    filter, the rest against the threshold)."""
+    ix, Q = small_index(kind)
+    g = gpu_index(ksc, ix)
+    Qs = Q[:nq]
+    P, R, k = 9, 150, 10
+    probes = oracle_probes(ix, Qs, P)
+    opts = ksc.search_opts(lanes_per_query=lanes)
+    for tb in (0, 3):
+        opts.tile_blocks = tb
+        _, _, cand, ncand = g.search_with_probes(torch.from_numpy(Qs).cuda(), torch.from_numpy(probes).cuda(),
+                                                 k, R, opts=opts)
+        cand = cand.cpu().numpy().view(np.uint64)
+        ncand = ncand.cpu().numpy()
+        for qi in range(nq):
+            Ql, b, _ = oracle.lut_q8(Qs[qi], ix, probes[qi])
+            ref = oracle.scan_topr(ix, probes[qi], Ql, b, R)
+            assert ncand[qi] == len(ref)
+            assert np.array_equal(cand[qi, :len(ref)], ref), (qi, tb)
     assert g.last_status() == 0
 
 
