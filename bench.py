@@ -528,6 +528,41 @@ def run_ours(args, rank, ws):
             except Exception as ex:  # reported, never fatal to the benchmark line
                 ix.profile(False)
                 tcs = {"error": str(ex)[:200]}
+        # a1 on the tensor cores: the list-score call (query conversion + the
+        # tcgen05 GEMM, 2 nq L d flops) with 16-bit and with FP8 operands, and
+        # the plain step with FP8 ranking (same probes: the band is re-scored)
+        gemm = {}
+        try:
+            for mode, name in ((1, "16bit"), (2, "fp8_e4m3")):
+                for _ in range(3):
+                    ix.list_scores(Qd, tensor_cores=mode)
+                ts = []
+                for _ in range(10):
+                    flush.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    ix.list_scores(Qd, tensor_cores=mode)
+                    e1.record()
+                    e1.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                gms = statistics.median(ts)
+                fl = 2.0 * CFG["nq"] * CFG["nlist"] * CFG["d"]
+                tf = fl / (gms * 1e-3) / 1e12
+                pk = peaks["bf16_tflops_sustained"] * (2.0 if mode == 2 else 1.0)
+                gemm[name] = {"ms": round(gms, 4), "flops": fl, "TFLOPs": round(tf, 1), "peak_TFLOPs": round(pk, 1),
+                              "frac": round(tf / pk, 4),
+                              "peak_source": "bf16 sustained of MEASURED_PEAKS.json" +
+                                             (" x 2 (nominal fp8 / bf16 ratio)" if mode == 2 else "")}
+            f8o = ksc.search_opts(rank_fp8=True)
+            r8 = ix.search(Qd, k, nprobe, R, opts=f8o)
+            r16 = ix.search(Qd, k, nprobe, R)
+            stg8, ms8 = stage_median(ix, lambda: ix.search(Qd, k, nprobe, R, opts=f8o), flush, 3, 5)
+            gemm["plain_step_fp8_ranking"] = {"ms": round(ms8, 4), "rank_ms": round(stg8["rank"], 4),
+                                              "results_equal_16bit_ranking": bool(torch.equal(r8[0], r16[0]) and
+                                                                                   torch.equal(r8[1], r16[1]))}
+            gemm["note"] = "call time of ksc_list_scores (query conversion + GEMM); tensor-pipe share from ncu in profiles/"
+        except Exception as ex:  # reported, never fatal
+            gemm["error"] = str(ex)[:200]
         # re-rank of the plain step: algorithmic bytes (R gathered rows of d
         # floats per query) over the measured stage time; rows re-read by
         # several queries may come from L2, so this is an effective rate
@@ -597,6 +632,7 @@ def run_ours(args, rank, ws):
                            "effective_frac_of_hbm": None if rr_rate is None else
                            round(rr_rate / peaks.get("hbm_gbs", 6800.0), 4)},
             "scan_stream": stream,
+            "rank_gemm": gemm,
             "scan_tc": tcs,
             "clocks": clocks,
             "build_s": round(build_s, 2),

@@ -153,6 +153,11 @@ typedef struct {
     int32_t scan_tc;           /* 1: the scan on the tensor cores (one-hot codes x FP16 tables,
                                   FP32 sums of integers: the same keys as the byte-permute scan;
                                   M <= 128, not with hybrid); 0: byte permutes on the CUDA cores */
+    int32_t rank_fp8;          /* 1: list scores from FP8-e4m3 operands (queries and centroids
+                                  scaled per row by a power of two) on the tensor cores, FP32
+                                  accumulate; the lists their error bound cannot exclude are
+                                  re-scored exactly, so the ranking is the same (rank_fp32 wins
+                                  when both are set) */
 } ksc_search_opts;
 
 /* k nearest neighbours of Q_dev [nq x d] with a fixed nprobe (1..nlist) and
@@ -221,8 +226,10 @@ int ksc_rank_lists(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t P, int
 
 /* Raw list scores of step a1: scores_dev [nq x L] fp32 = ||c||^2 - 2<q, c>
  * (L2; ||q||^2 omitted) or -<q, c> (spherical), c the ranking centroids.
- * tensor_cores = 1: BF16 operands on the tensor cores (tcgen05, d <= 256);
- * tensor_cores = 0 (or d > 256): FP32 CUDA cores.  err_dev [nq] (may be
+ * tensor_cores = 1: 16-bit operands on the tensor cores (tcgen05, d <= 256);
+ * tensor_cores = 2: FP8-e4m3 operands with per-row power-of-two scales on
+ * the tensor cores (kind::f8f6f4, d <= 256); tensor_cores = 0 (or d > 256):
+ * FP32 CUDA cores.  err_dev [nq] (may be
  * NULL) receives a bound on |score - exact score| for every list of the
  * query; ranking re-scores exactly every list within twice that bound. */
 int ksc_list_scores(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t tensor_cores, float* scores_dev,

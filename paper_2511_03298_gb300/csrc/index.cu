@@ -337,6 +337,8 @@ int free_index_memory(ksc_index* ix) {
         // allocated lazily itself (not the same pointer as its source's)
         const ksc_index* s = ix->parent;
         void* own[] = {ix->status, ix->stats, ix->c_rank_bf16 != s->c_rank_bf16 ? ix->c_rank_bf16 : nullptr,
+                       ix->c_rank_f8 != s->c_rank_f8 ? ix->c_rank_f8 : nullptr,
+                       ix->c_rank_f8_scale != s->c_rank_f8_scale ? ix->c_rank_f8_scale : nullptr,
                        ix->X_bf16 != s->X_bf16 ? ix->X_bf16 : nullptr, ix->X_fp8 != s->X_fp8 ? ix->X_fp8 : nullptr,
                        ix->X_scale != s->X_scale ? ix->X_scale : nullptr};
         for (void* p : own)
@@ -350,7 +352,7 @@ int free_index_memory(ksc_index* ix) {
                     ix->blk_ids, ix->blk_codes, ix->assign, ix->graph, ix->entry, ix->status, ix->stats,
                     ix->c_rank_bf16, ix->mlp_w, ix->blk_list, ix->nbr_pos, ix->nbr_codes, ix->entry_pos,
                     ix->X_bf16, ix->X_fp8, ix->X_scale, ix->pr_stats, ix->pr_vecs, ix->pr_model, ix->dims,
-                    ix->X_rr};
+                    ix->X_rr, ix->c_rank_f8, ix->c_rank_f8_scale};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < nb; ++i) release(*bufs[i]);

@@ -49,6 +49,11 @@ struct ksc_index {
     alignas(64) unsigned char map_c[128] = {};
     float c_rank_max_norm = 0.f;
     bool tc_fp16 = false;  // 16-bit operand type of the tensor-core ranking
+    // FP8 ranking option: e4m3 copy of c_rank [L x Kp8] with power-of-two row
+    // scales [L] and its TMA map (made on first use)
+    void* c_rank_f8 = nullptr;
+    float* c_rank_f8_scale = nullptr;
+    alignas(64) unsigned char map_c8[128] = {};
     // learned nprobe / rerank predictor (Sec. 4.2.1-4.2.2)
     float* mlp_w = nullptr;  // [KSC_MLP_NPARAMS] FP32
     ksc_adaptive_params mlp_prm = {};
@@ -92,6 +97,8 @@ int free_index_memory(ksc_index* ix);
 // per-query bound err [nq] on their error.
 bool tc_rank_supported(const ksc_index* ix);
 int rank_scores_tc(ksc_index* ix, const float* Q, int64_t nq, float* scores, float* err, cudaStream_t st);
+// The same from e4m3 operands with per-row power-of-two scales (FP8 option).
+int rank_scores_tc8(ksc_index* ix, const float* Q, int64_t nq, float* scores, float* err, cudaStream_t st);
 // Per-query error bound of the list scores (tensor-core or FP32 path).
 int score_err(ksc_index* ix, const float* Q, int64_t nq, bool tensor_cores, float* err, cudaStream_t st);
 // Gather of rows src[idx[r]] (width d floats) into dst (index.cu).

@@ -10,10 +10,20 @@
 // tcgen05.ld and write score = ||c||^2 - 2 <q, c> (L2) or -<q, c>.  These
 // scores are approximate (16-bit operands); the ranking kernel re-scores in
 // FP32 every list that their error bound cannot exclude.
+//
+// FP8 option (kind::f8f6f4, e4m3 x e4m3, FP32 accumulate): every query and
+// centroid row is scaled by a power of two s = 2^(e - 8), e the exponent of
+// the row's largest magnitude (so the scaled row peaks in [128, 256), inside
+// e4m3's range, and the scaling itself is exact), rounded to e4m3, and the
+// accumulated dot product is multiplied back by s_q s_c (exact: a power of
+// two).  A 128-element e4m3 box is 128 bytes per row, the same swizzle atom
+// as a 64-element 16-bit box, and one MMA takes K = 32, so the tile loop and
+// the descriptors are those of the 16-bit path.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include <algorithm>
 #include <cstdio>
@@ -81,6 +91,17 @@ __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, 
         : "memory");
 }
 
+// The same with 8-bit operands: kind::f8f6f4, whose instruction descriptor
+// gives e4m3 for A and B with format code 0 (so the bits equal those of the
+// FP16 descriptor); K = 32 per instruction.
+__device__ __forceinline__ void tc_mma_f8(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(
+            d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
@@ -97,12 +118,17 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// scores[q][c] for one 128 x 256 tile.  KB = number of 64-wide K boxes (Kp / 64).
+// scores[q][c] for one 128 x 256 tile.  KB = number of K boxes of 128 bytes
+// per row (64 16-bit or 128 8-bit elements).  F8: e4m3 operands whose rows
+// carry the power-of-two scales qs [nq] and cs [L].
+template <bool F8>
 __global__ void __launch_bounds__(128, 1) k_rank_gemm_tc(const __grid_constant__ CUtensorMap mapA,
                                                          const __grid_constant__ CUtensorMap mapB, int KB, int64_t nq,
                                                          int L, const float* __restrict__ cn, int spherical,
-                                                         int fmt, float* __restrict__ scores,
+                                                         int fmt, const float* __restrict__ qs,
+                                                         const float* __restrict__ cs, float* __restrict__ scores,
                                                          int32_t* __restrict__ status) {
+    constexpr int BOX_K = F8 ? 128 : TC_KB;  // elements per 128-byte box row
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t bars[2];
     __shared__ uint32_t tmem_base;
@@ -129,19 +155,21 @@ __global__ void __launch_bounds__(128, 1) k_rank_gemm_tc(const __grid_constant__
     if (threadIdx.x == 0) {
         mbar_expect_tx(bar_tma, (uint32_t)KB * (TC_M + TC_N) * 128);
         for (int kb = 0; kb < KB; ++kb) {
-            tma_load_2d(sA + kb * (TC_M * 128), &mapA, bar_tma, kb * TC_KB, m0);
-            tma_load_2d(sB + kb * (TC_N * 128), &mapB, bar_tma, kb * TC_KB, n0);
+            tma_load_2d(sA + kb * (TC_M * 128), &mapA, bar_tma, kb * BOX_K, m0);
+            tma_load_2d(sB + kb * (TC_N * 128), &mapB, bar_tma, kb * BOX_K, n0);
         }
         ok = mbar_wait(bar_tma, 0, TC_WAIT_LIMIT);
         if (ok) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t idesc = idesc_f16kind(fmt, TC_M, TC_N);
+            // four MMAs per 128-byte box: K = 16 16-bit or 32 8-bit elements = 32 bytes each
             for (int kb = 0; kb < KB; ++kb)
 #pragma unroll
-                for (int k = 0; k < TC_KB / 16; ++k) {
+                for (int k = 0; k < 4; ++k) {
                     const uint64_t a = smem_desc(sA + kb * (TC_M * 128) + k * 32);
                     const uint64_t b = smem_desc(sB + kb * (TC_N * 128) + k * 32);
-                    tc_mma(tmem, a, b, idesc, (kb | k) != 0);
+                    if (F8) tc_mma_f8(tmem, a, b, idesc, (kb | k) != 0);
+                    else tc_mma(tmem, a, b, idesc, (kb | k) != 0);
                 }
             tc_commit(bar_mma);
         } else {
@@ -169,8 +197,10 @@ __global__ void __launch_bounds__(128, 1) k_rank_gemm_tc(const __grid_constant__
             const int c = n0 + c0 + lane;
             if (c < L) {
                 const float cc = spherical ? 0.f : cn[c];
+                const float sc = F8 ? cs[c] : 1.f;
                 for (int rr = 0; rr < 32 && qb + rr < nq; ++rr) {
-                    const float dot = stage[rr * 33 + lane];
+                    // F8: the product of two powers of two, an exact rescaling
+                    const float dot = F8 ? stage[rr * 33 + lane] * (qs[qb + rr] * sc) : stage[rr * 33 + lane];
                     scores[(qb + rr) * L + c] = spherical ? -dot : fmaf(-2.f, dot, cc);
                 }
             }
@@ -258,6 +288,66 @@ __global__ void k_q16_err(const float* __restrict__ Q, int64_t nq, int d, int Kp
     err[q] = (spherical ? e : 2.f * e) + r;
 }
 
+// Power-of-two scale of a row whose largest magnitude is mx: 2^(e - 8) with
+// mx = m 2^e, m in [0.5, 1), so mx / s = 256 m lies in [128, 256); 1 for a
+// zero row.
+__device__ __forceinline__ float f8_row_scale(float mx) {
+    if (!(mx > 0.f)) return 1.f;
+    int e;
+    frexpf(mx, &e);
+    return ldexpf(1.f, e - 8);
+}
+
+__device__ __forceinline__ uint8_t to_e4m3(float v) {
+    return (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+}
+
+// Rows of X [n x d] to e4m3 [n x Kp] (zero-padded K) with their power-of-two
+// scales [n].  One warp per row.
+__global__ void k_rows_f8(const float* __restrict__ X, int64_t n, int d, int Kp, uint8_t* __restrict__ out,
+                          float* __restrict__ scale) {
+    const int lane = threadIdx.x & 31;
+    const int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= n) return;
+    float mx = 0.f;
+    for (int t = lane; t < d; t += 32) mx = fmaxf(mx, fabsf(X[r * d + t]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const float s = f8_row_scale(mx);
+    const float inv = 1.f / s;  // a power of two: exact
+    for (int t = lane; t < Kp; t += 32) out[r * Kp + t] = t < d ? to_e4m3(X[r * d + t] * inv) : (uint8_t)0;
+    if (lane == 0) scale[r] = s;
+}
+
+// Queries to e4m3 rows [nq x Kp] with their scales and, in the same pass, the
+// per-query bound of the FP8 scores (rel from fp8_rel below).
+__global__ void k_q8_err(const float* __restrict__ Q, int64_t nq, int d, int Kp, float cmax, int spherical,
+                         float rel, uint8_t* __restrict__ out, float* __restrict__ qs, float* __restrict__ err) {
+    const int lane = threadIdx.x & 31;
+    const int64_t q = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (q >= nq) return;
+    float s = 0.f, mx = 0.f;
+    for (int t = lane; t < d; t += 32) {
+        const float v = Q[q * d + t];
+        s = fmaf(v, v, s);
+        mx = fmaxf(mx, fabsf(v));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    const float sq = f8_row_scale(mx);
+    const float inv = 1.f / sq;
+    for (int t = lane; t < Kp; t += 32) out[q * Kp + t] = t < d ? to_e4m3(Q[q * d + t] * inv) : (uint8_t)0;
+    if (lane != 0) return;
+    qs[q] = sq;
+    const float qn = sqrtf(s);
+    const float e = rel * qn * cmax * 1.0001f;
+    const float r = (float)(d + 8) * 1.2e-7f * (qn + cmax) * (qn + cmax);
+    err[q] = (spherical ? e : 2.f * e) + r;
+}
+
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
@@ -271,17 +361,21 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-static int make_map(CUtensorMap* map, const void* base, int64_t rows, int Kp, int box_rows, bool fp16) {
+// elem: 2 (fp16 selects FP16 or BF16) or 1 (e4m3 bytes); boxes of 128 bytes per row
+static int make_map(CUtensorMap* map, const void* base, int64_t rows, int Kp, int box_rows, bool fp16,
+                    int elem = 2) {
     auto fn = encode_fn();
     if (!fn) {
         set_error("cuTensorMapEncodeTiled is not available");
         return KSC_ECUDA;
     }
     cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
-    cuuint32_t box[2] = {(cuuint32_t)TC_KB, (cuuint32_t)box_rows};
+    cuuint64_t strides[1] = {(cuuint64_t)Kp * elem};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / elem), (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(map, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+    const CUtensorMapDataType dt = elem == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                             : (fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+    CUresult r = fn(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
@@ -323,10 +417,63 @@ int rank_scores_tc(ksc_index* ix, const float* Q, int64_t nq, float* scores, flo
     CUtensorMap mapA;
     KSC_TRY(make_map(&mapA, qb, nq, Kp, TC_M, ix->tc_fp16));
     const size_t smem = (size_t)KB * (TC_M + TC_N) * 128 + 1024;
-    KSC_CUDA(cudaFuncSetAttribute(k_rank_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    KSC_CUDA(cudaFuncSetAttribute(k_rank_gemm_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((ix->L + TC_N - 1) / TC_N, (unsigned)((nq + TC_M - 1) / TC_M));
-    k_rank_gemm_tc<<<grid, 128, smem, st>>>(mapA, *reinterpret_cast<const CUtensorMap*>(ix->map_c), KB, nq, ix->L,
-                                            ix->c_rank_sq, ix->spherical, ix->tc_fp16 ? 0 : 1, scores, ix->status);
+    k_rank_gemm_tc<false><<<grid, 128, smem, st>>>(mapA, *reinterpret_cast<const CUtensorMap*>(ix->map_c), KB, nq,
+                                                   ix->L, ix->c_rank_sq, ix->spherical, ix->tc_fp16 ? 0 : 1, nullptr,
+                                                   nullptr, scores, ix->status);
+    KSC_LAUNCH_CHECK();
+    ix->launches += 2;
+    return KSC_OK;
+}
+
+// Relative bound of the FP8 scores' dot products, per ||q|| max||c||.
+//  Rounding of a scaled element y to e4m3: |fl(y) - y| <= 2^-4 |y| + 2^-10
+//  (relative 2^-4 in the normal range, half the subnormal spacing 2^-9
+//  below it).  With the row scale s <= max|x_t| / 128 <= ||x|| / 128 and
+//  sum |x_t| <= sqrt(d) ||x||, the error of <q~, c~> is at most
+//  (2 u + u^2) ||q|| ||c|| + 2 (1 + u) 2^-10 sqrt(d) / 128 ||q|| ||c|| plus
+//  a d 2^-34 term (u = 2^-4).  Products of two e4m3 values are exact in
+//  FP32; the accumulation inside the MMA is taken as no worse than 13 bits
+//  of precision per addition (d 2^-13 (1 + u)^2 of sum |q~_t c~_t|; a
+//  reading: the accumulator's internal precision is not documented here);
+//  the rescaling by s_q s_c is exact.
+static float fp8_rel(int d) {
+    const float u = 0.0625f;
+    return (2.f * u + u * u) + 2.f * (1.f + u) * 9.765625e-4f * sqrtf((float)d) / 128.f +
+           (float)d * 1.2207e-4f * (1.f + u) * (1.f + u) + 1e-6f;
+}
+
+// The same scores from e4m3 operands with per-row power-of-two scales.
+int rank_scores_tc8(ksc_index* ix, const float* Q, int64_t nq, float* scores, float* err, cudaStream_t st) {
+    const int Kp = (ix->d + 127) / 128 * 128;
+    const int KB = Kp / 128;
+    if (!ix->c_rank_f8) {
+        KSC_CUDA(cudaMalloc(&ix->c_rank_f8, (size_t)ix->L * Kp));
+        KSC_CUDA(cudaMalloc(&ix->c_rank_f8_scale, sizeof(float) * ix->L));
+        k_rows_f8<<<(unsigned)((ix->L + 7) / 8), 256, 0, st>>>(ix->c_rank, ix->L, ix->d, Kp,
+                                                               (uint8_t*)ix->c_rank_f8, ix->c_rank_f8_scale);
+        KSC_LAUNCH_CHECK();
+        KSC_TRY(make_map(reinterpret_cast<CUtensorMap*>(ix->map_c8), ix->c_rank_f8, ix->L, Kp, TC_N, false, 1));
+    }
+    float rel, qmax;
+    KSC_TRY(err_params(ix, true, &rel, &qmax, st));  // max ||c||
+    // e4m3 rows (a multiple of 128 bytes each), then the row scales
+    const size_t rows_bytes = (size_t)nq * Kp;
+    KSC_TRY(ensure(ix->ws_qbf16, rows_bytes + sizeof(float) * (size_t)nq, st));
+    uint8_t* q8 = (uint8_t*)ix->ws_qbf16.p;
+    float* qsc = reinterpret_cast<float*>(q8 + rows_bytes);
+    k_q8_err<<<(unsigned)((nq + 7) / 8), 256, 0, st>>>(Q, nq, ix->d, Kp, ix->c_rank_max_norm, ix->spherical,
+                                                        fp8_rel(ix->d), q8, qsc, err);
+    KSC_LAUNCH_CHECK();
+    CUtensorMap mapA;
+    KSC_TRY(make_map(&mapA, q8, nq, Kp, TC_M, false, 1));
+    const size_t smem = (size_t)KB * (TC_M + TC_N) * 128 + 1024;
+    KSC_CUDA(cudaFuncSetAttribute(k_rank_gemm_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((ix->L + TC_N - 1) / TC_N, (unsigned)((nq + TC_M - 1) / TC_M));
+    k_rank_gemm_tc<true><<<grid, 128, smem, st>>>(mapA, *reinterpret_cast<const CUtensorMap*>(ix->map_c8), KB, nq,
+                                                  ix->L, ix->c_rank_sq, ix->spherical, 0, qsc, ix->c_rank_f8_scale,
+                                                  scores, ix->status);
     KSC_LAUNCH_CHECK();
     ix->launches += 2;
     return KSC_OK;

@@ -2323,7 +2323,7 @@ struct Plan {
     const int32_t* nprobe_q;
     const int32_t* rerank_q;
     int G, TB, TBa, cap;  // TB: tile blocks of the filtered scan, TBa: of the unfiltered first part
-    bool rank_exact;
+    int rank_mode;  // RankMode of the list scores
     bool hybrid;
     int n_near, efs, tau;
     int prec, Rf;  // precision variant: first re-rank of R (= Rmax) in prec, then FP32 of the best Rf
@@ -2393,13 +2393,20 @@ static int dispatch_scan(int S, const ScanArgs& A, const ScanOut& O, const int64
     return KSC_EINVAL;
 }
 
-// List scores [nq x L] on the BF16 tensor cores or the FP32 CUDA cores, with
-// the per-query bound err [nq] on their distance from the exact scores.
-static int list_scores(ksc_index* ix, const float* Q, int64_t nq, bool exact, float* scores, float** err,
+// Operand type of the list scores (a1): 16-bit tensor cores, FP32 CUDA
+// cores, or FP8 tensor cores.
+enum RankMode { RANK_TC16 = 0, RANK_FP32 = 1, RANK_FP8 = 2 };
+
+// List scores [nq x L] on the 16-bit or FP8 tensor cores or the FP32 CUDA
+// cores, with the per-query bound err [nq] on their distance from the exact
+// scores.
+static int list_scores(ksc_index* ix, const float* Q, int64_t nq, int mode, float* scores, float** err,
                        cudaStream_t st) {
     KSC_TRY(ensure(ix->ws_err, sizeof(float) * nq, st));
     *err = (float*)ix->ws_err.p;
-    if (!exact && tc_rank_supported(ix)) return rank_scores_tc(ix, Q, nq, scores, *err, st);
+    if (mode != RANK_FP32 && tc_rank_supported(ix))
+        return mode == RANK_FP8 ? rank_scores_tc8(ix, Q, nq, scores, *err, st)
+                                : rank_scores_tc(ix, Q, nq, scores, *err, st);
     dim3 grid(blocks_for(ix->L, SC_T), blocks_for(nq, SC_T));
     k_list_scores<<<grid, 256, 0, st>>>(Q, nq, ix->d, ix->c_rank, ix->c_rank_sq, ix->L, ix->spherical, scores);
     ix->launches++;
@@ -2410,11 +2417,11 @@ static int list_scores(ksc_index* ix, const float* Q, int64_t nq, bool exact, fl
 // The Pmax best lists of every query (exact ranking); feat (optional, L >=
 // FEAT_K) receives each query's FEAT_K smallest given list distances.
 static int rank_lists(ksc_index* ix, const float* Q, int64_t nq, const int32_t* nprobe_q, int Pfix, int Pmax,
-                      int32_t* probes, float* score_out, bool exact, cudaStream_t st, float* feat = nullptr) {
+                      int32_t* probes, float* score_out, int mode, cudaStream_t st, float* feat = nullptr) {
     KSC_TRY(ensure(ix->ws_scores, sizeof(float) * nq * ix->L, st));
     float* scores = (float*)ix->ws_scores.p;
     float* err = nullptr;
-    KSC_TRY(list_scores(ix, Q, nq, exact, scores, &err, st));
+    KSC_TRY(list_scores(ix, Q, nq, mode, scores, &err, st));
     // re-score buffer of the CTA kernel: 4 Pmax lists (a power of two, at least 1024, at most RS_CAP)
     const int rs_cap = std::min(RS_CAP, std::max(1024, pow2_ceil(4 * Pmax)));
     const size_t smem = rs_cap * sizeof(uint64_t) + (ix->L <= RS_SMEM_L ? sizeof(float) * ix->L : 0);
@@ -2809,7 +2816,7 @@ static int make_plan(ksc_index* ix, int64_t nq, int k, int Pmax, int Rmax, const
     set_tiles(ix, pl, nq, Pmax, opts);
     int cap = (opts && opts->cand_cap > 0) ? opts->cand_cap : std::max(32 * Rmax, 8192);
     pl.cap = std::max(cap, Rmax);
-    pl.rank_exact = opts && opts->rank_fp32;
+    pl.rank_mode = (opts && opts->rank_fp32) ? RANK_FP32 : ((opts && opts->rank_fp8) ? RANK_FP8 : RANK_TC16);
     pl.Pq_max = Pmax;
     pl.prec = opts ? opts->precision : 0;
     KSC_CHECK_ARG(pl.prec >= 0 && pl.prec <= 2, "precision must be 0 (FP32), 1 (BF16) or 2 (FP8)");
@@ -2847,7 +2854,7 @@ int ksc_rank_lists(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t P, int
     cudaStream_t st = as_stream(stream);
     const float* Qw;
     KSC_TRY(work_queries(ix, Q_dev, nq, st, &Qw));
-    return rank_lists(ix, Qw, nq, nullptr, P, P, probes_dev, scores_dev, false, st);
+    return rank_lists(ix, Qw, nq, nullptr, P, P, probes_dev, scores_dev, RANK_TC16, st);
 }
 
 int ksc_list_scores(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t tensor_cores, float* scores_dev,
@@ -2856,11 +2863,12 @@ int ksc_list_scores(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t tenso
     if (nq == 0) return KSC_OK;
     KSC_CHECK_ARG(Q_dev && scores_dev, "null argument");
     cudaStream_t st = as_stream(stream);
-    const bool exact = !tensor_cores || !tc_rank_supported(ix);
+    KSC_CHECK_ARG(tensor_cores >= 0 && tensor_cores <= 2, "tensor_cores must be 0 (FP32), 1 (16-bit) or 2 (FP8)");
+    const int mode = tensor_cores == 0 ? RANK_FP32 : (tensor_cores == 2 ? RANK_FP8 : RANK_TC16);
     float* err = nullptr;
     const float* Qw;
     KSC_TRY(work_queries(ix, Q_dev, nq, st, &Qw));
-    KSC_TRY(list_scores(ix, Qw, nq, exact, scores_dev, &err, st));
+    KSC_TRY(list_scores(ix, Qw, nq, mode, scores_dev, &err, st));
     if (err_dev) KSC_CUDA(cudaMemcpyAsync(err_dev, err, sizeof(float) * nq, cudaMemcpyDeviceToDevice, st));
     return KSC_OK;
 }
@@ -2911,7 +2919,7 @@ int ksc_search(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t k, int32_t
     mark(ix, 0, st);
     const float* Qw;
     KSC_TRY(work_queries(ix, Q_dev, nq, st, &Qw));
-    KSC_TRY(rank_lists(ix, Qw, nq, nullptr, pl.Pmax, pl.Pmax, probes, nullptr, pl.rank_exact, st));
+    KSC_TRY(rank_lists(ix, Qw, nq, nullptr, pl.Pmax, pl.Pmax, probes, nullptr, pl.rank_mode, st));
     return search_from_probes(ix, Qw, pl, probes, ids_dev, dists_dev, nullptr, nullptr, st, Q_dev);
 }
 
@@ -2935,7 +2943,7 @@ int ksc_search_varprobe(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t k
     mark(ix, 0, st);
     const float* Qw;
     KSC_TRY(work_queries(ix, Q_dev, nq, st, &Qw));
-    KSC_TRY(rank_lists(ix, Qw, nq, nprobe_dev, pl.Pmax, pl.Pmax, probes, nullptr, pl.rank_exact, st));
+    KSC_TRY(rank_lists(ix, Qw, nq, nprobe_dev, pl.Pmax, pl.Pmax, probes, nullptr, pl.rank_mode, st));
     return search_from_probes(ix, Qw, pl, probes, ids_dev, dists_dev, nullptr, nullptr, st, Q_dev);
 }
 
@@ -3088,7 +3096,7 @@ static int rank_and_features(ksc_index* ix, const float* Q, int64_t nq, int P, i
                              cudaStream_t st) {
     KSC_TRY(ensure(ix->ws_rscore, sizeof(float) * nq * FEAT_K, st));
     float* rs = (float*)ix->ws_rscore.p;
-    KSC_TRY(rank_lists(ix, Q, nq, nullptr, P, P, probes, nullptr, false, st, rs));
+    KSC_TRY(rank_lists(ix, Q, nq, nullptr, P, P, probes, nullptr, RANK_TC16, st, rs));
     KSC_TRY(mlp_features(rs, nq, FEAT_K, ix->spherical, feats, st));
     ix->launches++;
     return KSC_OK;
@@ -3690,7 +3698,7 @@ int ksc_search_pruned(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t k, 
     mark(ix, 0, st);
     const float* Qw;
     KSC_TRY(work_queries(ix, Q_dev, nq, st, &Qw));
-    KSC_TRY(rank_lists(ix, Qw, nq, nullptr, pl.Pmax, pl.Pmax, probes, nullptr, pl.rank_exact, st));
+    KSC_TRY(rank_lists(ix, Qw, nq, nullptr, pl.Pmax, pl.Pmax, probes, nullptr, pl.rank_mode, st));
     // Alg. 2: keep rank 0 and the ranks with f_prune > theta, in rank order
     KSC_TRY(prune_rows(ix, Qw, nq, probes, pl.Pmax, nullptr, pl.Pmax, theta, nullptr, nullptr, kept, pn, st));
     ix->launches++;
@@ -3737,7 +3745,7 @@ int ksc_train_pruner(ksc_index* ix, const float* Qtrain_dev, int64_t nt, const f
             const float* Qc = Qtrain_dev + c0 * rr_d(ix);
             const float* Qcw;
             if ((rc = work_queries(ix, Qc, nc, st, &Qcw))) break;
-            if ((rc = rank_lists(ix, Qcw, nc, nullptr, P, P, probes, nullptr, false, st))) break;
+            if ((rc = rank_lists(ix, Qcw, nc, nullptr, P, P, probes, nullptr, RANK_TC16, st))) break;
             Plan pl;
             if ((rc = make_plan(ix, nc, k, P, R, nullptr, pl))) break;
             if ((rc = search_from_probes(ix, Qcw, pl, probes, ids, dists, nullptr, nullptr, st, Qc))) break;

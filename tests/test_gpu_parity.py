@@ -366,6 +366,58 @@ def test_tensor_core_ranking_equals_fp32_ranking(torch, ksc, kind):
     assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
 
 
+def e4m3_rows(torch, A):
+    """Rows of A scaled by 2^(e - 8) (e: the exponent of the row's largest
+    magnitude, frexp convention) and rounded to FP8 e4m3 by torch; returns
+    the rounded rows (in FP64, times their scale) -- the arithmetic the FP8
+    ranking option is specified to do, written with library routines."""
+    A = A.astype(np.float64)
+    mx = np.abs(A).max(1)
+    e = np.frexp(mx)[1]
+    s = np.where(mx > 0, np.ldexp(1.0, e - 8), 1.0)
+    q = torch.from_numpy(A / s[:, None]).to(torch.float32).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    return q * s[:, None]
+
+
+@pytest.mark.parametrize("kind", ["l2", "ip", "small", "m50"])
+def test_fp8_list_scores_within_their_bound(torch, ksc, kind):
+    """tcgen05 kind::f8f6f4 scores (e4m3 operands, per-row power-of-two
+    scales) equal the FP64 product of the same e4m3-rounded rows up to FP32
+    accumulation, and stay within the per-query bound the ranking uses."""
+    ix, Q = small_index(kind)
+    g = gpu_index(ksc, ix)
+    s8, err = g.list_scores(torch.from_numpy(Q).cuda(), tensor_cores=2)
+    s8, err = s8.cpu().numpy().astype(np.float64), err.cpu().numpy().astype(np.float64)
+    C = ix["c_rank"].astype(np.float64)
+    Qd = Q.astype(np.float64)
+    cn = (C * C).sum(1)
+    exact = -(Qd @ C.T) if ix["spherical"] else cn[None] - 2.0 * (Qd @ C.T)
+    assert np.all(np.abs(s8 - exact) <= err[:, None])
+    dot8 = e4m3_rows(torch, Q) @ e4m3_rows(torch, ix["c_rank"]).T
+    emu = -dot8 if ix["spherical"] else cn[None].astype(np.float32).astype(np.float64) - 2.0 * dot8
+    scale = np.abs(Qd).sum(1)[:, None] * np.abs(C).max() * 4.0 + 1e-6
+    assert np.all(np.abs(s8 - emu) <= 1e-5 * scale + 1e-6 * np.abs(emu))
+
+
+@pytest.mark.parametrize("kind", ["l2", "small", "ip", "m50"])
+def test_fp8_ranking_equals_fp32_ranking(torch, ksc, kind):
+    """The FP8 scores' band is re-scored in exact FP32 like the 16-bit one:
+    the probes and the results equal those of the FP32 ranking, also through
+    the per-query-nprobe path."""
+    ix, Q = small_index(kind)
+    g = gpu_index(ksc, ix)
+    Qd = torch.from_numpy(Q).cuda()
+    a = g.search(Qd, 10, 9, 100, opts=ksc.search_opts(rank_fp8=True))
+    b = g.search(Qd, 10, 9, 100, opts=ksc.search_opts(rank_fp32=True))
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    npb = torch.from_numpy(np.random.default_rng(3).integers(1, 12, len(Q)).astype(np.int32)).cuda()
+    rr = torch.full((len(Q),), 100, dtype=torch.int32, device="cuda")
+    c = g.search_varprobe(Qd, 10, npb, rr, nprobe_max=12, rerank_max=100, opts=ksc.search_opts(rank_fp8=True))
+    d = g.search_varprobe(Qd, 10, npb, rr, nprobe_max=12, rerank_max=100, opts=ksc.search_opts(rank_fp32=True))
+    assert torch.equal(c[0], d[0]) and torch.equal(c[1], d[1])
+    assert g.last_status() == 0
+
+
 def test_warp_shaped_kernels_bit_exact(torch, ksc):
     """Batches of at least 8 queries per SM take the warp-per-query threshold,
     select, ranking and re-rank kernels; smaller ones the CTA-per-query ones.
