@@ -176,6 +176,48 @@ int ksc_search_varprobe(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t k
                         int64_t* ids_dev, float* dists_dev,
                         const ksc_search_opts* opts, void* stream);
 
+/* ------------------------------------------------------------------ */
+/* List-sharded search (the multi-process protocol of Sec. 5.1 with the  */
+/* lists themselves partitioned, for an index larger than one device)   */
+/* ------------------------------------------------------------------ */
+/* Create shard `shard` of a list-partitioned index from the whole index's
+ * host arrays (copied; graph / entry ignored): the lists p with
+ * list_owner[p] == shard keep their members, in ascending row id, every
+ * other list is empty; centroids and codebooks are replicated.  The shard
+ * keeps the global row id of each of its vectors.  Checked on the host before
+ * device work: arrays as ksc_index_import, owners >= 0, at least one vector
+ * in the shard (KSC_EINVAL).  Blocking.  Free with ksc_index_free. */
+int ksc_index_import_shard(const ksc_index_arrays* full, const int32_t* list_owner, int32_t shard,
+                           void* stream, ksc_index** out);
+
+/* Shard step 1 (Alg. 2 / Alg. 3 up to the candidate pool): rank all lists,
+ * build the tables of every probed list (so the per-query scale is the whole
+ * index's), scan the shard's own lists and keep its R = max(rerank, k)
+ * smallest keys per query: keys_dev [nq x R] uint64, ((D + 2^31) << 32) |
+ * global id, ascending, padded with all-ones.  Fixed nprobe; opts as
+ * ksc_search except hybrid and the low-precision re-rank (KSC_EINVAL). */
+int ksc_shard_candidates(ksc_index* shard, const float* Q_dev, int64_t nq, int32_t nprobe, int32_t rerank,
+                         int32_t k, uint64_t* keys_dev, const ksc_search_opts* opts, void* stream);
+
+/* Shard step 2 (Alg. 2 re-rank), after an exchange of every shard's keys:
+ * all_keys_dev [parts x nq x R] (shard-major, as an all-gather lays them
+ * out), own_keys_dev [nq x R] this shard's from step 1.  theta = the R-th
+ * smallest of all keys of the query (the whole index's R-th key); the
+ * shard's own keys at or below it are re-ranked exactly -> ids_dev
+ * [nq x k] int64 (global ids) and dists_dev [nq x k] as ksc_search (short
+ * lists padded with -1 / +-inf).  parts x R <= 8192. */
+int ksc_shard_rerank(ksc_index* shard, const float* Q_dev, int64_t nq, int32_t k, int32_t rerank,
+                     const uint64_t* own_keys_dev, const uint64_t* all_keys_dev, int32_t parts,
+                     int64_t* ids_dev, float* dists_dev, void* stream);
+
+/* Final merge of the shards' results: ids_dev / dists_dev [parts x nq x k]
+ * -> the k best per query by distance (ip = 0: ascending L2 distance;
+ * ip = 1: descending similarity), then id; pads (id -1) last.  The merged
+ * result of steps 1-2 on every shard equals ksc_search on the whole index.
+ * parts x k <= 8192. */
+int ksc_merge_topk(const int64_t* ids_dev, const float* dists_dev, int64_t nq, int32_t parts, int32_t k,
+                   int32_t ip, int64_t* ids_out_dev, float* dists_out_dev, void* stream);
+
 /* Test entry: search with caller-given probe lists probes_dev [nq x P]
  * (list ids, in rank order).  Optional outputs (NULL to skip):
  * cand_dev [nq x R] uint64 candidate keys ((D + 2^31) << 32 | id), sorted

@@ -7,6 +7,7 @@
 // ordering (a counting sort of the assignment) runs on the host.
 #include <atomic>
 #include <cstdarg>
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -352,7 +353,7 @@ int free_index_memory(ksc_index* ix) {
                     ix->blk_ids, ix->blk_codes, ix->assign, ix->graph, ix->entry, ix->status, ix->stats,
                     ix->c_rank_bf16, ix->mlp_w, ix->blk_list, ix->nbr_pos, ix->nbr_codes, ix->entry_pos,
                     ix->X_bf16, ix->X_fp8, ix->X_scale, ix->pr_stats, ix->pr_vecs, ix->pr_model, ix->dims,
-                    ix->X_rr, ix->c_rank_f8, ix->c_rank_f8_scale};
+                    ix->X_rr, ix->c_rank_f8, ix->c_rank_f8_scale, ix->gids};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < nb; ++i) release(*bufs[i]);
@@ -495,18 +496,20 @@ static int finish_common(ksc_index* ix, cudaStream_t st) {
     return KSC_OK;
 }
 
-static int check_shape(int64_t n, int32_t d, int32_t L, int32_t M) {
+static int check_shape(int64_t n, int32_t d, int32_t L, int32_t M, bool shard = false) {
     KSC_CHECK_ARG(n > 0 && n < (1ll << 31), "n must be in [1, 2^31)");
     KSC_CHECK_ARG(d > 0 && d <= KSC_MAX_DIM, "d must be in [1, %d]", KSC_MAX_DIM);
-    KSC_CHECK_ARG(L > 0 && L <= KSC_MAX_NLIST && L <= n, "nlist must be in [1, min(n, %d)]", KSC_MAX_NLIST);
+    // a shard holds every list (most of them empty): nlist may exceed its rows
+    KSC_CHECK_ARG(L > 0 && L <= KSC_MAX_NLIST && (shard || L <= n), "nlist must be in [1, min(n, %d)]",
+                  KSC_MAX_NLIST);
     KSC_CHECK_ARG(M > 0 && M <= KSC_MAX_M && d % M == 0, "M must divide d and be <= %d", KSC_MAX_M);
     return KSC_OK;
 }
 
-int ksc_index_import(const ksc_index_arrays* a, void* stream, ksc_index** out) {
+static int import_arrays(const ksc_index_arrays* a, void* stream, ksc_index** out, bool shard) {
     KSC_CHECK_ARG(a && out && a->X && a->c_rank && a->c_mean && a->codebook && a->codes && a->assign,
                   "null argument");
-    KSC_TRY(check_shape(a->n, a->d, a->nlist, a->M));
+    KSC_TRY(check_shape(a->n, a->d, a->nlist, a->M, shard));
     KSC_CHECK_ARG(a->metric == KSC_L2 || a->metric == KSC_IP, "bad metric");
     // Every index the device code follows is checked here, on the host,
     // before any device work: codes address 16-entry tables, lists address
@@ -564,6 +567,59 @@ int ksc_index_import(const ksc_index_arrays* a, void* stream, ksc_index** out) {
     if (rc != KSC_OK) {
         ksc_index_free(ix);
         return rc;
+    }
+    *out = ix;
+    return KSC_OK;
+}
+
+int ksc_index_import(const ksc_index_arrays* a, void* stream, ksc_index** out) {
+    return import_arrays(a, stream, out, false);
+}
+
+// One shard of a list-partitioned index: the lists p with list_owner[p] ==
+// shard keep their members (rows in ascending global id), every other list
+// is empty; centroids and codebooks are replicated, so every shard ranks the
+// lists and scales the tables (a_q over the whole probe set) as the whole
+// index does.  gids maps local rows back to the global ids.
+int ksc_index_import_shard(const ksc_index_arrays* full, const int32_t* list_owner, int32_t shard, void* stream,
+                           ksc_index** out) {
+    KSC_CHECK_ARG(full && list_owner && out && full->X && full->codes && full->assign, "null argument");
+    KSC_CHECK_ARG(shard >= 0, "shard must be >= 0");
+    KSC_TRY(check_shape(full->n, full->d, full->nlist, full->M));
+    for (int32_t p = 0; p < full->nlist; ++p) KSC_CHECK_ARG(list_owner[p] >= 0, "owner of list %d is negative", p);
+    std::vector<int32_t> rows;
+    for (int64_t i = 0; i < full->n; ++i) {
+        const int32_t p = full->assign[i];
+        KSC_CHECK_ARG(p >= 0 && p < full->nlist, "assignment of row %lld out of range", (long long)i);
+        if (list_owner[p] == shard) rows.push_back((int32_t)i);
+    }
+    KSC_CHECK_ARG(!rows.empty(), "shard %d holds no vector", shard);
+    const int64_t ns = (int64_t)rows.size();
+    const int d = full->d, M = full->M;
+    std::vector<float> X((size_t)ns * d);
+    std::vector<uint8_t> codes((size_t)ns * M);
+    std::vector<int32_t> assign(ns);
+    for (int64_t r = 0; r < ns; ++r) {
+        const int64_t i = rows[r];
+        std::copy(full->X + i * d, full->X + (i + 1) * d, X.begin() + r * d);
+        std::copy(full->codes + i * M, full->codes + (i + 1) * M, codes.begin() + r * M);
+        assign[r] = full->assign[i];
+    }
+    ksc_index_arrays a = *full;
+    a.n = ns;
+    a.X = X.data();
+    a.codes = codes.data();
+    a.assign = assign.data();
+    a.graph = nullptr;
+    a.entry = nullptr;
+    ksc_index* ix = nullptr;
+    KSC_TRY(import_arrays(&a, stream, &ix, true));
+    if (alloc_copy((void**)&ix->gids, rows.data(), sizeof(int32_t) * ns, as_stream(stream),
+                   cudaMemcpyHostToDevice) != KSC_OK ||
+        cudaStreamSynchronize(as_stream(stream)) != cudaSuccess) {
+        ksc_index_free(ix);
+        set_error("shard id map: device copy failed");
+        return KSC_ECUDA;
     }
     *out = ix;
     return KSC_OK;

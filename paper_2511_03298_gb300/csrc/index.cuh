@@ -69,6 +69,9 @@ struct ksc_index {
     std::vector<int32_t> h_dims;
     float* X_rr = nullptr;       // [n x d_rr] full vectors (null: no filtration)
     int32_t d_rr = 0;
+    // list sharding (ksc_index_import_shard): global id of each local row,
+    // ascending, so (distance, local id) orders keys as (distance, global id)
+    int32_t* gids = nullptr;  // [n]
     // a view (ksc_index_view): the handle it came from, whose arrays it shares
     const ksc_index* parent = nullptr;
     // stage timing (ksc_profile_enable)
@@ -128,6 +131,12 @@ int prune_targets(const float* lab, int64_t rows, float* y, cudaStream_t st);
 // Component filtration (filter.cu): column statistics, dimension gather.
 int component_stats(const float* X, int64_t n, int d, double* mu, double* sd, double* frac, cudaStream_t st);
 int gather_dims(const float* A, int64_t rows, int d, const int32_t* dims, int dw, float* out, cudaStream_t st);
+// List sharding (search.cu): steps a1 .. a5 of a fixed-nprobe search into
+// sorted keys [nq x R] (local ids), and the exact re-rank of given keys.
+int search_keys(ksc_index* ix, const float* Q, int64_t nq, int nprobe, int rerank, const ksc_search_opts* opts,
+                uint64_t* keys, cudaStream_t st);
+int rerank_keys(ksc_index* ix, const float* Q, int64_t nq, int k, const uint64_t* keys, int R, int64_t* ids,
+                float* dists, cudaStream_t st);
 // Per-list 32-NN graphs and entry points for the hybrid search (Sec. 4.4).
 int build_graph(ksc_index* ix, cudaStream_t st);
 // Search form (nbr_pos, nbr_codes, entry_pos) of graph / entry (hybrid.cu).

@@ -2723,6 +2723,10 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
         ix->launches++;
         KSC_LAUNCH_CHECK();
     }
+    if (!ids && !dists) {  // candidates only (a shard's first step): no re-rank
+        mark(ix, KSC_NUM_STAGES, st);
+        return KSC_OK;
+    }
     // 6. exact rerank (precision variant: a BF16 / FP8 re-rank of the widened
     //    shortlist first, then FP32 of its best Rf), with the full queries and
     //    vectors (Alg. 2: q_init)
@@ -2902,6 +2906,55 @@ int ksc_search_with_probes(ksc_index* ix, const float* Q_dev, int64_t nq, const 
     KSC_TRY(work_queries(ix, Q_dev, nq, st, &Qw));
     return search_from_probes(ix, Qw, pl, probes_dev, ids_dev, dists_dev, cand_dev, ncand_dev, st, Q_dev);
 }
+
+}  // extern "C"
+
+namespace ksc {
+// A shard's first step (list sharding): steps a1 .. a5 with a fixed nprobe,
+// the R = max(rerank, k) selected keys of every query, ascending, into
+// keys [nq x R] (local ids; KEY_NONE pads a short list).
+int search_keys(ksc_index* ix, const float* Q, int64_t nq, int nprobe, int rerank, const ksc_search_opts* opts,
+                uint64_t* keys, cudaStream_t st) {
+    Plan pl;
+    KSC_TRY(make_plan(ix, nq, 1, nprobe, rerank, opts, pl));
+    KSC_CHECK_ARG(!pl.hybrid && pl.prec == 0, "sharded search: plain scan and FP32 re-rank only");
+    if (nq == 0) return KSC_OK;
+    KSC_CUDA(cudaMemsetAsync(ix->status, 0, sizeof(int32_t), st));
+    KSC_TRY(ensure(ix->ws_probes, sizeof(int32_t) * nq * pl.Pmax, st));
+    int32_t* probes = (int32_t*)ix->ws_probes.p;
+    KSC_CUDA(cudaMemsetAsync(ix->stats, 0, sizeof(unsigned long long) * 4, st));
+    ix->launches = 0;
+    mark(ix, 0, st);
+    const float* Qw;
+    KSC_TRY(work_queries(ix, Q, nq, st, &Qw));
+    KSC_TRY(rank_lists(ix, Qw, nq, nullptr, pl.Pmax, pl.Pmax, probes, nullptr, pl.rank_mode, st));
+    return search_from_probes(ix, Qw, pl, probes, nullptr, nullptr, keys, nullptr, st, Q);
+}
+
+// Exact re-rank (a6) of given candidate keys [nq x R] (local ids, KEY_NONE
+// skipped): the k best by (distance, id) per query.
+int rerank_keys(ksc_index* ix, const float* Q, int64_t nq, int k, const uint64_t* keys, int R, int64_t* ids,
+                float* dists, cudaStream_t st) {
+    const float* Xr = rr_X(ix);
+    const int dr = rr_d(ix);
+    const int ip = ix->metric == KSC_IP;
+    if (k <= 32 && R <= RW_MAXR && dr <= 128 && (dr & 3) == 0 && warp_per_query(nq)) {
+        const size_t smem = sizeof(uint64_t) * RW_WARPS * R;
+        KSC_CUDA(cudaFuncSetAttribute(k_rerank_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_rerank_w<<<(unsigned)((nq + RW_WARPS - 1) / RW_WARPS), RW_WARPS * 32, smem, st>>>(
+            Q, Xr, dr, ip, keys, R, nullptr, R, k, nq, ids, dists);
+    } else {
+        const size_t smem = sizeof(uint64_t) * pow2_ceil(R < 2 ? 2 : R);
+        KSC_CUDA(cudaFuncSetAttribute(k_rerank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_rerank<<<(unsigned)nq, 256, smem, st>>>(Q, Xr, dr, ip, keys, R, nullptr, R, k, ids, dists);
+    }
+    KSC_LAUNCH_CHECK();
+    ix->launches++;
+    return KSC_OK;
+}
+}  // namespace ksc
+
+extern "C" {
 
 int ksc_search(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t k, int32_t nprobe, int32_t rerank,
                int64_t* ids_dev, float* dists_dev, const ksc_search_opts* opts, void* stream) {

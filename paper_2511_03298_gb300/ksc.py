@@ -103,6 +103,10 @@ _SIGS = {
     "ksc_index_dims": [_vp, _vp, _vp],
     "ksc_index_view": [_vp, _vp],
     "ksc_component_stats": [_vp, _i64, _i32, _vp, _vp, _vp, _vp],
+    "ksc_index_import_shard": [_vp, _vp, _i32, _vp, _vp],
+    "ksc_shard_candidates": [_vp, _vp, _i64, _i32, _i32, _i32, _vp, _vp, _vp],
+    "ksc_shard_rerank": [_vp, _vp, _i64, _i32, _i32, _vp, _vp, _i32, _vp, _vp, _vp],
+    "ksc_merge_topk": [_vp, _vp, _i64, _i32, _i32, _i32, _vp, _vp, _vp],
     "ksc_last_error": [],
     "ksc_version": [],
 }
@@ -271,6 +275,29 @@ class Index:
                                             _dptr(ids), _dptr(dists), _dptr(cand), _dptr(ncand),
                                             C.byref(opts) if opts else None, _stream(stream)))
         return ids, dists, cand, ncand
+
+    def shard_candidates(self, Q, k, nprobe, rerank, opts=None, stream=None):
+        """Shard step 1: the shard's R = max(rerank, k) smallest keys per
+        query (global ids), [nq x R] int64 holding the uint64 keys."""
+        torch = _torch()
+        nq = Q.shape[0]
+        keys = torch.empty((nq, max(rerank, k)), dtype=torch.int64, device=Q.device)
+        _check(lib().ksc_shard_candidates(self._h, _dptr(Q, torch.float32, "Q"), nq, nprobe, rerank, k, _dptr(keys),
+                                          C.byref(opts) if opts else None, _stream(stream)))
+        return keys
+
+    def shard_rerank(self, Q, k, rerank, own_keys, all_keys, stream=None):
+        """Shard step 2: all_keys [parts x nq x R] from every shard; the
+        shard's k best (global ids, distances) among the whole index's R
+        best keys."""
+        torch = _torch()
+        nq = Q.shape[0]
+        ids = torch.empty((nq, k), dtype=torch.int64, device=Q.device)
+        dists = torch.empty((nq, k), dtype=torch.float32, device=Q.device)
+        _check(lib().ksc_shard_rerank(self._h, _dptr(Q, torch.float32, "Q"), nq, k, rerank,
+                                      _dptr(own_keys, torch.int64, "own_keys"), _dptr(all_keys, torch.int64, "all_keys"),
+                                      all_keys.shape[0], _dptr(ids), _dptr(dists), _stream(stream)))
+        return ids, dists
 
     def rank_lists(self, Q, P, want_scores=True, stream=None):
         torch = _torch()
@@ -559,6 +586,38 @@ def index_import(arrs, metric="l2", spherical=False, stream=None):
     h = C.c_void_p()
     _check(lib().ksc_index_import(C.byref(a), _stream(stream), C.byref(h)))
     return Index(h.value)
+
+
+def _index_arrays(arrs, metric, spherical):
+    keep = {k: np.ascontiguousarray(arrs[k]) for k in ("X", "c_rank", "c_mean", "codebook", "codes", "assign")}
+    keep["X"] = keep["X"].astype(np.float32, copy=False)
+    n, d = keep["X"].shape
+    a = IndexArrays(n, d, keep["c_rank"].shape[0], keep["codebook"].shape[0], KSC_IP if metric == "ip" else KSC_L2,
+                    int(spherical), *[_hptr(keep.get(k)) for k in ("X", "c_rank", "c_mean", "codebook", "codes",
+                                                                   "assign")], None, None)
+    return a, keep
+
+
+def index_import_shard(arrs, list_owner, shard, metric="l2", spherical=False, stream=None):
+    """Shard `shard` of a list-partitioned index: the lists p with
+    list_owner[p] == shard (their vectors in ascending row id), centroids and
+    codebooks replicated (ksc_index_import_shard)."""
+    a, keep = _index_arrays(arrs, metric, spherical)
+    owner = np.ascontiguousarray(list_owner, dtype=np.int32)
+    h = C.c_void_p()
+    _check(lib().ksc_index_import_shard(C.byref(a), _hptr(owner), int(shard), _stream(stream), C.byref(h)))
+    return Index(h.value)
+
+
+def merge_topk(ids, dists, ip=False, stream=None):
+    """ids / dists [parts x nq x k] -> the k best per query (ksc_merge_topk)."""
+    torch = _torch()
+    parts, nq, k = ids.shape
+    out_i = torch.empty((nq, k), dtype=torch.int64, device=ids.device)
+    out_d = torch.empty((nq, k), dtype=torch.float32, device=ids.device)
+    _check(lib().ksc_merge_topk(_dptr(ids, torch.int64, "ids"), _dptr(dists, torch.float32, "dists"), nq, parts, k,
+                                int(ip), _dptr(out_i), _dptr(out_d), _stream(stream)))
+    return out_i, out_d
 
 
 def prune_mlp_grad(w, x, y, stream=None):
