@@ -36,6 +36,7 @@ constexpr int TCS_TMEM_COLS = 512;
 constexpr int TCS_D_COL = 0;      // two accumulators, tiles alternating: accumulator b at column b * TCS_NT
 constexpr int TCS_A_COL = 2 * TCS_NT;  // chunk slots: (g * TCS_SLOTS + s) * 64 after the accumulators
 constexpr uint32_t TCS_WAIT = 1u << 22;
+constexpr int TCS_KCAP = 64;      // passing keys buffered in shared memory per query column and item
 static_assert(TCS_A_COL + 2 * TCS_SLOTS * 64 <= TCS_TMEM_COLS, "tensor memory columns");
 
 struct TcsQuery {
@@ -109,10 +110,11 @@ __device__ __forceinline__ void tcs_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 
 // Shared memory of k_scan_tc: B (Mc boxes of nt rows x 128 bytes), then per
 // generating warp the transposed codes of its block (4 words x 4 Mc
-// subspaces: word w of subspace j holds the codes of vectors 8 w .. 8 w + 7).
+// subspaces: word w of subspace j holds the codes of vectors 8 w .. 8 w + 7),
+// then the filtered scan's key buffers (TCS_KCAP keys per query column).
 __host__ __device__ inline size_t tcs_smem_bytes(int M, int nt) {
     const int Mc = (M + 3) / 4, Mw = (M + 7) / 8 * 8;
-    return 1024 + (size_t)Mc * nt * 128 + (size_t)8 * 4 * Mw * 4;
+    return 1024 + (size_t)Mc * nt * 128 + (size_t)8 * 4 * Mw * 4 + (size_t)nt * TCS_KCAP * 8;
 }
 
 // Items = (list p, group of at most nt queries probing p, tile [b0, b1) of
@@ -137,6 +139,7 @@ __global__ void __launch_bounds__(TCS_THREADS, 1)
     __shared__ long long s_it;
     __shared__ int s_fail;
     __shared__ TcsQuery s_q[TCS_NT];
+    __shared__ int s_kc[TCS_NT];  // keys reserved in each query column's shared buffer (this item)
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tcs_raw) + 1023) & ~uintptr_t(1023));
     // Mc boxes of 4 subspaces (B), Mc8 chunks of 8 subspaces (A), transposed
     // code rows of Mw words
@@ -144,6 +147,7 @@ __global__ void __launch_bounds__(TCS_THREADS, 1)
     const uint32_t box = (uint32_t)nt * 128;
     const uint32_t sB = smem_addr(smem);
     uint32_t* trans = reinterpret_cast<uint32_t*>(smem + (size_t)Mc * box);
+    uint64_t* kbuf = reinterpret_cast<uint64_t*>(trans + (size_t)8 * 4 * Mw);  // [nt][TCS_KCAP]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
         for (int g = 0; g < 2; ++g) {
@@ -158,6 +162,7 @@ __global__ void __launch_bounds__(TCS_THREADS, 1)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_fail = 0;
     }
+    if (tid < TCS_NT) s_kc[tid] = 0;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
                      "r"(TCS_TMEM_COLS));
@@ -330,33 +335,55 @@ __global__ void __launch_bounds__(TCS_THREADS, 1)
                                 if (valid && pos < O.cap) O.cand[qi.q * O.cap + pos] = key;
                             }
                         } else {
-                            // passing keys of the 16 columns, then one reservation
-                            // per column with any, all 16 in flight together
-                            uint32_t msk[16];
-                            int mine_cnt = 0;
+                            // this lane's vector against the 16 columns, without
+                            // branches (independent tests, so their latencies
+                            // overlap): pass bits, then per column a ballot,
+                            // one shared reservation per column by lane i for
+                            // column n0 + i (all 16 at once), and the stores
+                            // into the column's shared buffer -- or, for what
+                            // does not fit there, into the global store
+                            uint32_t pm = 0;
+                            int32_t sums[16];
 #pragma unroll
                             for (int i = 0; i < 16; ++i) {
-                                const int n = n0 + i;
-                                bool pass = false;
-                                if (n < nqi) {
-                                    const int32_t sum = __float2int_rz(__uint_as_float(f[i])) - bias1024;
-                                    pass = valid && (sum < s_q[n].lim || (sum == s_q[n].lim && id <= s_q[n].thI));
-                                }
-                                msk[i] = __ballot_sync(0xffffffffu, pass);
-                                if (lane == i) mine_cnt = __popc(msk[i]);
+                                const int n = n0 + i;  // < TCS_NT: n0 <= TCS_NT - 16
+                                sums[i] = __float2int_rz(__uint_as_float(f[i])) - bias1024;
+                                const int32_t lim = s_q[n].lim;
+                                const uint32_t th = s_q[n].thI;
+                                const bool pass = n < nqi && valid && (sums[i] < lim || (sums[i] == lim && id <= th));
+                                pm |= (uint32_t)pass << i;
                             }
-                            int base = 0;
-                            if (mine_cnt > 0) base = atomicAdd(&O.cnt[s_q[n0 + lane].q], mine_cnt);
+                            uint32_t bal[16];
+                            int cnt = 0;
 #pragma unroll
                             for (int i = 0; i < 16; ++i) {
-                                const int bi = __shfl_sync(0xffffffffu, base, i);
-                                if ((msk[i] >> lane) & 1u) {
-                                    const TcsQuery& qi = s_q[n0 + i];
-                                    const int32_t sum = __float2int_rz(__uint_as_float(f[i])) - bias1024;
+                                bal[i] = __ballot_sync(0xffffffffu, (pm >> i) & 1u);
+                                cnt = lane == i ? __popc(bal[i]) : cnt;
+                            }
+                            int sb = 0, gb = 0;
+                            if (cnt > 0) {
+                                sb = atomicAdd(&s_kc[n0 + lane], cnt);
+                                const int fit = max(0, min(cnt, TCS_KCAP - sb));
+                                if (cnt > fit) gb = atomicAdd(&O.cnt[s_q[n0 + lane].q], cnt - fit);
+                            }
+                            const uint32_t below = (1u << lane) - 1u;
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) {
+                                if (bal[i] == 0u) continue;  // the same on every lane
+                                const int sbi = __shfl_sync(0xffffffffu, sb, i);
+                                const int gbi = __shfl_sync(0xffffffffu, gb, i);
+                                if ((pm >> i) & 1u) {
+                                    const int n = n0 + i;
                                     const uint64_t key =
-                                        ((uint64_t)((uint32_t)(qi.bias + sum) ^ 0x80000000u) << 32) | (uint64_t)id;
-                                    const int at = bi + __popc(msk[i] & ((1u << lane) - 1u));
-                                    if (at < O.cap) O.cand[qi.q * O.cap + at] = key;
+                                        ((uint64_t)((uint32_t)(s_q[n].bias + sums[i]) ^ 0x80000000u) << 32) |
+                                        (uint64_t)id;
+                                    const int p = sbi + __popc(bal[i] & below);
+                                    if (p < TCS_KCAP) {
+                                        kbuf[n * TCS_KCAP + p] = key;
+                                    } else {
+                                        const int at = gbi + (p - max(sbi, TCS_KCAP));
+                                        if (at < O.cap) O.cand[s_q[n].q * O.cap + at] = key;
+                                    }
                                 }
                             }
                         }
@@ -416,6 +443,20 @@ __global__ void __launch_bounds__(TCS_THREADS, 1)
             }
         }
         __syncthreads();  // the item is done: B, the query table and the counters are free
+        if (!DIRECT) {
+            // the shared key buffers to the store: one reservation per query
+            // column, the copy coalesced by a warp per column
+            for (int n = warp; n < nqi; n += TCS_THREADS / 32) {
+                const int c = min(s_kc[n], TCS_KCAP);
+                int base = 0;
+                if (lane == 0 && c > 0) base = atomicAdd(&O.cnt[s_q[n].q], c);
+                base = __shfl_sync(0xffffffffu, base, 0);
+                for (int i = lane; i < c; i += 32)
+                    if (base + i < O.cap) O.cand[s_q[n].q * O.cap + base + i] = kbuf[n * TCS_KCAP + i];
+            }
+            __syncthreads();
+            if (tid < TCS_NT) s_kc[tid] = 0;
+        }
     }
     // every MMA issued by this CTA has completed before the tensor memory is freed
     if (tid == 8 * 32) {

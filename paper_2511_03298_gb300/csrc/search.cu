@@ -1014,12 +1014,14 @@ __global__ void k_count_parts(ScanArgs A, int Rmax, int cap, int rs, int32_t* __
 
 // exclusive scans: pair_off = scan(cnt); item_off = scan(ceil(cnt/QG) * ntiles)
 // Several work lists at once: CTA i scans cnt + i L into pair_off / item_off +
-// i (L + 1) and clears fill + i L; the first list's tiles are TB0 blocks long,
-// the others' TB1.
+// i (L + 1) and clears fill + i L; the first list's items hold QG0 queries and
+// tiles of TB0 blocks, the others' QG1 and TB1.
 __global__ void __launch_bounds__(1024) k_scan_lists(const int32_t* __restrict__ cnt0, const int32_t* __restrict__ list_n,
-                                                     int L, int QG, int TB0, int TB1, int64_t* __restrict__ pair_off0,
-                                                     int64_t* __restrict__ item_off0, int32_t* __restrict__ fill0) {
+                                                     int L, int QG0, int QG1, int TB0, int TB1,
+                                                     int64_t* __restrict__ pair_off0, int64_t* __restrict__ item_off0,
+                                                     int32_t* __restrict__ fill0) {
     const int TB = blockIdx.x == 0 ? TB0 : TB1;  // tile length of this CTA's work list
+    const int QG = blockIdx.x == 0 ? QG0 : QG1;  // queries per item
     const int32_t* cnt = cnt0 + (size_t)blockIdx.x * L;
     int64_t* pair_off = pair_off0 + (size_t)blockIdx.x * (L + 1);
     int64_t* item_off = item_off0 + (size_t)blockIdx.x * (L + 1);
@@ -2520,8 +2522,8 @@ struct WorkList {
 };
 
 static int run_scan(const Plan& pl, int M, const ScanArgs& A, const ScanOut& O, const WorkList& w, int L,
-                    int32_t* status, cudaStream_t st, unsigned long long* next_item) {
-    if (pl.tc) return launch_scan_tc(A, O, w.pair_off, w.item_off, w.pairs, L, w.TB, pl.nt, next_item, status, st);
+                    int32_t* status, cudaStream_t st, unsigned long long* next_item, bool tc) {
+    if (tc) return launch_scan_tc(A, O, w.pair_off, w.item_off, w.pairs, L, w.TB, pl.nt, next_item, status, st);
     const int S = (M + pl.G - 1) / pl.G;
     if (pl.G == 4) {
         if (M <= 64) return launch_scan4<64>(A, O, w.pair_off, w.item_off, w.pairs, L, w.TB, status, st);
@@ -2558,7 +2560,11 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
                               const float* Qr = nullptr) {
     const int64_t nq = pl.nq;
     const int M = ix->M, L = ix->L;
-    const int QG = pl.tc ? pl.nt : 32 / pl.G;  // queries per work item
+    // queries per work item: the unfiltered first part always runs the
+    // byte-permute scan (few queries share a list there: too few columns for
+    // the tensor cores); the rest the chosen scan
+    const int QGa = 32 / pl.G;
+    const int QG = pl.tc ? pl.nt : QGa;
     // hybrid: the n_near nearest lists are the fully scanned ones (Sec. 4.4);
     // plain: a per-query split (k_count_parts)
     const int rA = std::min(pl.hybrid ? pl.n_near : 1, pl.Pmax);
@@ -2610,7 +2616,8 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
     k_count_parts<<<(unsigned)((nq + 7) / 8), 256, 0, st>>>(A, pl.Rmax, pl.cap, rA, split, wa.cnt, wb.cnt, cnt);
     wa.TB = pl.TBa;
     wb.TB = pl.TB;
-    k_scan_lists<<<2, 1024, 0, st>>>(wa.cnt, ix->list_n, L, QG, wa.TB, wb.TB, wa.pair_off, wa.item_off, wa.fill);
+    k_scan_lists<<<2, 1024, 0, st>>>(wa.cnt, ix->list_n, L, QGa, QG, wa.TB, wb.TB, wa.pair_off, wa.item_off,
+                                     wa.fill);
     k_fill_parts<<<blocks_for(nq * pl.Pmax, 256), 256, 0, st>>>(A, rA, split, wa.pair_off, wa.fill, wa.pairs,
                                                                 wb.pair_off, wb.fill, wb.pairs);
     KSC_LAUNCH_CHECK();
@@ -2645,7 +2652,7 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
     }
     // 3. scan of the nearest lists with no filter, then the threshold
     mark(ix, 3, st);
-    KSC_TRY(run_scan(pl, M, A, ScanOut{nullptr, cnt, cand, pl.cap}, wa, L, ix->status, st, tc_next));
+    KSC_TRY(run_scan(pl, M, A, ScanOut{nullptr, cnt, cand, pl.cap}, wa, L, ix->status, st, tc_next, false));
     // expected keys per query of the unfiltered scan: max(4 R, N / 16), N from
     // the mean list length; a warp per query up to SW_MAX_KEYS, else a CTA
     if (std::max(4.0 * pl.Rmax, (double)pl.Pmax * ix->n / L / 16.0) <= SW_MAX_KEYS && warp_per_query(nq))
@@ -2686,12 +2693,13 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
         KSC_CUDA(cudaMemsetAsync(wb.cnt, 0, sizeof(int32_t) * L, st));
         const int64_t nmax = nq * pl.Pmax;
         k_count_from<<<blocks_for(nmax, 256), 256, 0, st>>>(full, nfull, probes, wb.cnt);
-        k_scan_lists<<<1, 1024, 0, st>>>(wb.cnt, ix->list_n, L, QG, wb.TB, wb.TB, wb.pair_off, wb.item_off, wb.fill);
+        k_scan_lists<<<1, 1024, 0, st>>>(wb.cnt, ix->list_n, L, QG, QG, wb.TB, wb.TB, wb.pair_off, wb.item_off,
+                                         wb.fill);
         k_fill_from<<<blocks_for(nmax, 256), 256, 0, st>>>(full, nfull, probes, wb.pair_off, wb.fill, wb.pairs);
         KSC_LAUNCH_CHECK();
         ix->launches += 4;
     }
-    KSC_TRY(run_scan(pl, M, A, ScanOut{thr, cnt, cand, pl.cap}, wb, L, ix->status, st, tc_next + 1));
+    KSC_TRY(run_scan(pl, M, A, ScanOut{thr, cnt, cand, pl.cap}, wb, L, ix->status, st, tc_next + 1, pl.tc));
     ix->launches++;
     // 5. the R best keys per query
     mark(ix, 5, st);
@@ -2795,8 +2803,9 @@ static void set_tiles(const ksc_index* ix, Plan& pl, int64_t nq, double P, const
     pl.TB = tile(blocks * (1.0 - near), 220.0);
     pl.TBa = tile(blocks * near, 120.0);
     if (opts && opts->tile_blocks > 0) pl.TB = pl.TBa = std::min(opts->tile_blocks, 1 << 20);
-    // tensor-core scan: tiles of whole 128-vector products, 32 blocks unless given
-    if (pl.tc) pl.TB = pl.TBa = (opts && opts->tile_blocks > 0) ? (std::min(opts->tile_blocks, 1 << 20) + 3) / 4 * 4 : 32;
+    // tensor-core scan (the filtered part only): tiles of whole 128-vector
+    // products, 32 blocks unless given
+    if (pl.tc) pl.TB = (opts && opts->tile_blocks > 0) ? (std::min(opts->tile_blocks, 1 << 20) + 3) / 4 * 4 : 32;
 }
 
 static int make_plan(ksc_index* ix, int64_t nq, int k, int Pmax, int Rmax, const ksc_search_opts* opts, Plan& pl) {
