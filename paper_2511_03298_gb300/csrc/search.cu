@@ -1160,6 +1160,58 @@ __device__ __forceinline__ void accum_pair32(const uint4& c0, const uint4& t0, c
     accum_chunk32(c1, t1, acc);
 }
 
+// Selectors of one code word w (eight 4-bit codes, vector n in bits 4n..4n+3)
+// for lut16x8, computed once per word and shared by every query slot of a
+// warp: (s0, s1, k0, k1).
+__device__ __forceinline__ uint4 lut16_selectors(uint32_t w) {
+    const uint32_t s0 = w & 0x77777777u;
+    const uint32_t k0 = ((w >> 1) & 0x44444444u) | 0x32103210u;
+    return make_uint4(s0, s0 >> 16, k0, k0 >> 16);
+}
+
+// The lookups of one word from its selectors: lo = T[c0..c3], hi = T[c4..c7].
+__device__ __forceinline__ void lut16x8_sel(const uint4& s, const uint4& t, uint32_t& lo, uint32_t& hi) {
+    lo = prmt(prmt(t.x, t.y, s.x), prmt(t.z, t.w, s.x), s.z);
+    hi = prmt(prmt(t.x, t.y, s.y), prmt(t.z, t.w, s.y), s.w);
+}
+
+// Two subspaces j0, j1 from shared selectors (sel[k M + j]: word k of
+// subspace j): the looked-up bytes of the same vector from both subspaces
+// are interleaved by one byte permute, so one byte dot product adds two
+// lookups to the vector's 32-bit sum (acc[v], v the vector of the block).
+__device__ __forceinline__ void accum_pair_sel(const uint4* __restrict__ sel, int M, int j0, int j1, const uint4& t0,
+                                               const uint4& t1, uint32_t (&acc)[32]) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        uint32_t lo0, hi0, lo1, hi1;
+        lut16x8_sel(sel[k * M + j0], t0, lo0, hi0);
+        lut16x8_sel(sel[k * M + j1], t1, lo1, hi1);
+        uint32_t* a = acc + 8 * k;
+        uint32_t x = prmt(lo0, lo1, 0x5140u), y = prmt(lo0, lo1, 0x7362u);
+        a[0] = __dp4a(x, 0x00000101u, a[0]);
+        a[1] = __dp4a(x, 0x01010000u, a[1]);
+        a[2] = __dp4a(y, 0x00000101u, a[2]);
+        a[3] = __dp4a(y, 0x01010000u, a[3]);
+        x = prmt(hi0, hi1, 0x5140u);
+        y = prmt(hi0, hi1, 0x7362u);
+        a[4] = __dp4a(x, 0x00000101u, a[4]);
+        a[5] = __dp4a(x, 0x01010000u, a[5]);
+        a[6] = __dp4a(y, 0x00000101u, a[6]);
+        a[7] = __dp4a(y, 0x01010000u, a[7]);
+    }
+}
+
+__device__ __forceinline__ void accum_chunk_sel(const uint4* __restrict__ sel, int M, int j, const uint4& t,
+                                                uint32_t (&acc)[32]) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        uint32_t lo, hi;
+        lut16x8_sel(sel[k * M + j], t, lo, hi);
+        widen_add4(lo, acc + 8 * k);
+        widen_add4(hi, acc + 8 * k + 4);
+    }
+}
+
 template <int G>
 __device__ __forceinline__ void reduce_scatter(uint32_t (&acc)[16], int lane, uint32_t (&out)[32 / G]) {
     constexpr int V = 32 / G;
@@ -1212,7 +1264,16 @@ __device__ __forceinline__ void reduce_scatter(uint32_t (&acc)[16], int lane, ui
 // No CTA-wide barrier: warps run independently.
 constexpr int SCAN_WARPS = 8;
 constexpr int SCAN_CHUNK_BYTES = 4096;           // per buffer, per warp
-constexpr int SCAN_BUF_KEYS = 128;               // kept keys buffered per (warp, query slot)
+constexpr int SCAN_CHUNK_BYTES_SEL = 3072;       // the same with shared selectors (room for their buffer)
+constexpr int SCAN_BUF_KEYS = 64;                // kept keys buffered per (warp, query slot)
+
+// With 8 lanes per query the four query slots of a warp read the same code
+// words: their selectors are computed once per block into a shared buffer of
+// M x 64 bytes per warp.
+template <int G>
+__host__ __device__ constexpr bool scan_shared_sel() { return G == 8; }
+template <int G>
+__host__ __device__ constexpr int scan_chunk_bytes() { return scan_shared_sel<G>() ? SCAN_CHUNK_BYTES_SEL : SCAN_CHUNK_BYTES; }
 constexpr uint32_t SCAN_WAIT_LIMIT = 1u << 22;
 
 
@@ -1245,7 +1306,10 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32, (SMAX <= 2 ? 3 : (SMAX <= 8 ?
                                                           int32_t* __restrict__ status) {
     constexpr int QG = 32 / G;
     constexpr int V = 32 / G;
-    extern __shared__ __align__(128) uint8_t bufs[];  // SCAN_WARPS x 2 x SCAN_CHUNK_BYTES
+    constexpr bool SEL = scan_shared_sel<G>();
+    constexpr int CHUNK = scan_chunk_bytes<G>();
+    // SCAN_WARPS x 2 x CHUNK code buffers, then (SEL) SCAN_WARPS x M x 64 selector bytes
+    extern __shared__ __align__(128) uint8_t bufs[];
     __shared__ __align__(8) uint64_t full[SCAN_WARPS][2];
     // kept keys of the warp's current item, per query slot, flushed to the
     // candidate store with one atomic per slot when a slot fills and when the
@@ -1259,10 +1323,11 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32, (SMAX <= 2 ? 3 : (SMAX <= 8 ?
     const int M = A.M;
     const int S = (M + G - 1) / G;
     const int blk_bytes = M * 16;
-    const int cb = SCAN_CHUNK_BYTES / blk_bytes;  // blocks per chunk (>= 1)
+    const int cb = CHUNK / blk_bytes;  // blocks per chunk (>= 1)
     const int64_t total = item_off[L];
     const int64_t stride = (int64_t)gridDim.x * SCAN_WARPS;
-    uint8_t* mybuf = bufs + (size_t)warp * 2 * SCAN_CHUNK_BYTES;
+    uint8_t* mybuf = bufs + (size_t)warp * 2 * CHUNK;
+    uint4* sel = reinterpret_cast<uint4*>(bufs + (size_t)SCAN_WARPS * 2 * CHUNK) + (size_t)warp * 4 * M;
     const uint32_t bar0 = smem_addr(&full[warp][0]), bar1 = smem_addr(&full[warp][1]);
     if (lane == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
@@ -1279,7 +1344,7 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32, (SMAX <= 2 ? 3 : (SMAX <= 8 ?
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
         asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                         smem_addr(mybuf + b * SCAN_CHUNK_BYTES)),
+                         smem_addr(mybuf + b * CHUNK)),
                      "l"(src), "r"(bytes), "r"(bar)
                      : "memory");
     };
@@ -1370,7 +1435,7 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32, (SMAX <= 2 ? 3 : (SMAX <= 8 ?
                 if (lane == 0 && !failed) atomicOr(status, 4);  // a chunk never arrived: the warp stops
                 failed = true;
             } else {
-                const uint8_t* chunk = mybuf + b * SCAN_CHUNK_BYTES;
+                const uint8_t* chunk = mybuf + b * CHUNK;
                 const int c0 = x.b0 + c * cb, nblk = min(x.b1, c0 + cb) - c0;
                 const int64_t gb0 = A.boff[x.p] + c0;
                 // the same number of steps on every lane (the reduction is a
@@ -1389,15 +1454,40 @@ __global__ void __launch_bounds__(SCAN_WARPS * 32, (SMAX <= 2 ? 3 : (SMAX <= 8 ?
                     uint32_t a32[32];
 #pragma unroll
                     for (int m = 0; m < 32; ++m) a32[m] = 0;
+                    if (SEL && rep == 1) {
+                        // every slot scans this block: its selectors once, into
+                        // the warp's buffer (word k of subspace j at k M + j),
+                        // then the lookups from there
+                        for (int jj = lane; jj < M; jj += 32) {
+                            const uint4 cw = cp[jj];
+                            sel[0 * M + jj] = lut16_selectors(cw.x);
+                            sel[1 * M + jj] = lut16_selectors(cw.y);
+                            sel[2 * M + jj] = lut16_selectors(cw.z);
+                            sel[3 * M + jj] = lut16_selectors(cw.w);
+                        }
+                        __syncwarp();
 #pragma unroll
-                    for (int u = 0; u + 1 < SMAX; u += 2) {
-                        const int j = g + G * u;
-                        if (FULL || (u + 1 < S && j + G < M)) accum_pair32(cp[j], t[u], cp[j + G], t[u + 1], a32);
-                        else if (u < S && j < M) accum_chunk32(cp[j], t[u], a32);
-                    }
-                    if (SMAX & 1) {
-                        const int u = SMAX - 1, j = g + G * u;
-                        if (FULL || (u < S && j < M)) accum_chunk32(cp[j], t[u], a32);
+                        for (int u = 0; u + 1 < SMAX; u += 2) {
+                            const int j = g + G * u;
+                            if (FULL || (u + 1 < S && j + G < M)) accum_pair_sel(sel, M, j, j + G, t[u], t[u + 1], a32);
+                            else if (u < S && j < M) accum_chunk_sel(sel, M, j, t[u], a32);
+                        }
+                        if (SMAX & 1) {
+                            const int u = SMAX - 1, j = g + G * u;
+                            if (FULL || (u < S && j < M)) accum_chunk_sel(sel, M, j, t[u], a32);
+                        }
+                        __syncwarp();  // all reads done before the next block's selectors
+                    } else {
+#pragma unroll
+                        for (int u = 0; u + 1 < SMAX; u += 2) {
+                            const int j = g + G * u;
+                            if (FULL || (u + 1 < S && j + G < M)) accum_pair32(cp[j], t[u], cp[j + G], t[u + 1], a32);
+                            else if (u < S && j < M) accum_chunk32(cp[j], t[u], a32);
+                        }
+                        if (SMAX & 1) {
+                            const int u = SMAX - 1, j = g + G * u;
+                            if (FULL || (u < S && j < M)) accum_chunk32(cp[j], t[u], a32);
+                        }
                     }
                     // partial sums < 2^16: pack vector pairs for the reduction
                     uint32_t acc[16];
@@ -2354,7 +2444,8 @@ static int choose_G(const ksc_index* ix, int64_t nq, int Pmax, int want) {
 template <int G, int SMAX>
 static int launch_scan(const ScanArgs& A, const ScanOut& O, const int64_t* pair_off, const int64_t* item_off,
                        const uint32_t* pairs, int L, int TB, int32_t* status, cudaStream_t st) {
-    const size_t smem = (size_t)SCAN_WARPS * 2 * SCAN_CHUNK_BYTES;
+    const size_t smem = (size_t)SCAN_WARPS * 2 * scan_chunk_bytes<G>() +
+                        (scan_shared_sel<G>() ? (size_t)SCAN_WARPS * A.M * 64 : 0);
     // M = G SMAX: every lane has SMAX subspaces, no per-subspace guards
     const bool full = A.M == G * SMAX;
     auto kern = O.thr ? (full ? k_scan<G, SMAX, false, true> : k_scan<G, SMAX, false, false>)
