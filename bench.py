@@ -457,7 +457,7 @@ def run_ours(args, rank, ws):
         # the scan runs in two launches (nearest lists, then the rest); the
         # first stage also holds the threshold kernel between them
         scan_ms = plain_stage["scan"] + plain_stage["near_scan"]
-        peak_gl = ksc.lut16_peak()
+        peak_gl, peak_slot_gl = ksc.lut16_peak()
         achieved_gl = lookups / (scan_ms * 1e-3) / 1e9
         peaks = measured_peaks()
         # streaming form of the scan (few queries, each list read once from
@@ -611,7 +611,15 @@ def run_ours(args, rank, ws):
             "stage_ms": {s_: round(statistics.mean(v), 4) for s_, v in stage_ms.items()},
             "roofline": {"bound": "alu", "kernel": "k_scan (LUT16 ADC scan)", "achieved": round(achieved_gl, 1),
                          "peak": round(peak_gl, 1), "unit": "Glookup/s", "frac": round(achieved_gl / peak_gl, 4),
-                         "peak_source": "measured: ksc_lut16_peak (same instruction sequence, registers only)",
+                         "peak_source": "measured: ksc_lut16_peak, the scan's shared-selector lookup sequence "
+                                        "with no global memory traffic",
+                         "peak_per_slot_sequence": round(peak_slot_gl, 1),
+                         # the chip's integer-issue bound of that sequence: 64 integer-ALU
+                         # lane-operations per clock per SM, 1.156 ALU operations per lookup
+                         # (16 byte permutes per 16 lookups + 2.5 selector operations shared by
+                         # a warp's four query slots), at the maximum SM clock
+                         "integer_issue_bound": round(64 * 152 * 2.07e9 / (18.5 / 16) / 1e9, 1),
+                         "frac_of_integer_issue_bound": round(achieved_gl / (64 * 152 * 2.07e9 / (18.5 / 16) / 1e9), 4),
                          "lookups_per_launch": lookups,
                          # DRAM read + write of the scan's two launches per search, from the
                          # ncu capture of the plain step (profiles/k_scan_*.md)

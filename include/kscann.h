@@ -525,9 +525,13 @@ int ksc_last_status(ksc_index* ix, int32_t* status_host);
 int ksc_profile_enable(ksc_index* ix, int32_t on);
 int ksc_profile_read(ksc_index* ix, float* ms_host, int32_t n, int32_t* launches_host);
 
-/* Diagnostic: runs the scan's lookup/accumulate instruction sequence from
- * registers (no memory traffic) on every SM and returns the rate reached in
- * 10^9 lookups per second (the integer-ALU ceiling of the a3 scan).  Blocking. */
+/* Diagnostic: runs the scan's lookup/accumulate instruction sequences with
+ * no global memory traffic on every SM and returns the rates reached, in
+ * 10^9 lookups per second, into glookups_host[2]: [0] the sequence of items
+ * whose query slots share a block (selectors computed once per warp, read
+ * from shared memory; two lookups per byte dot product), [1] the per-slot
+ * sequence (selectors in registers; sparse items).  The integer-ALU
+ * ceilings of the a3 scan.  Blocking. */
 int ksc_lut16_peak(double* glookups_host, void* stream);
 
 /* Diagnostic: distances of the pairs (query q, ids_dev[q][i]) [nq x c] in

@@ -1913,8 +1913,42 @@ __global__ void __launch_bounds__(GS_WARPS * 32) k_graph_search(ScanArgs A, Scan
     }
 }
 
-// Register-only copy of the scan's lookup/accumulate instruction sequence
-// (no memory traffic): the lookup rate this formulation can reach on the GPU.
+// The scan's lookup sequence with shared selectors (8 lanes per query): the
+// selectors of a subspace pair from the warp's shared buffer (at indices that
+// depend on a per-iteration random number, so that nothing can be hoisted
+// out of the loop), the lookups and the interleaved widening of two
+// subspaces -- the lookup rate of the scan's inner loop with no code or
+// table traffic beyond shared memory.
+__global__ void __launch_bounds__(256) k_lut16_peak_sel(int iters, uint32_t seed, uint32_t* __restrict__ sink) {
+    __shared__ uint4 sel[4 * 64];
+    for (int i = threadIdx.x; i < 4 * 64; i += blockDim.x) {
+        uint32_t h = (uint32_t)i * 2654435761u + seed;
+        h ^= h >> 15;
+        h *= 0x2c1b3c6du;
+        sel[i] = lut16_selectors(h ^ (h >> 12));
+    }
+    __syncthreads();
+    const int g = threadIdx.x & 7;
+    const uint4 t0 = make_uint4(seed, seed * 3u + 1u, seed * 5u + 7u, seed * 9u + 3u);
+    const uint4 t1 = make_uint4(t0.y, t0.z, t0.w, t0.x);
+    uint32_t acc[32];
+#pragma unroll
+    for (int m = 0; m < 32; ++m) acc[m] = 0;
+    uint32_t w = seed ^ (blockIdx.x * blockDim.x + threadIdx.x);
+    for (int i = 0; i < iters; i += 2) {  // 64 lookups per pair of iterations
+        const int j = (g + 8 * (int)(w >> 29)) & 63;
+        accum_pair_sel(sel, 64, j, (j + 32) & 63, t0, t1, acc);
+        w = w * 1664525u + 1013904223u;
+    }
+    uint32_t s_ = 0;
+#pragma unroll
+    for (int m = 0; m < 32; ++m) s_ ^= acc[m];
+    if (s_ == 0x12345678u) sink[0] = s_;  // keeps the loop alive
+}
+
+// Register-only copy of the scan's earlier lookup/accumulate sequence (each
+// query slot computing its own selectors, one byte dot product per lookup;
+// no memory traffic): still the sequence of the scan's sparse items.
 __global__ void __launch_bounds__(128) k_lut16_peak(int iters, uint32_t seed, uint32_t* __restrict__ sink) {
     uint4 t = make_uint4(seed, seed * 3u + 1u, seed * 5u + 7u, seed * 9u + 3u);
     uint32_t acc[32];
@@ -3135,22 +3169,33 @@ int ksc_lut16_peak(double* glookups_host, void* stream) {
     cudaStream_t st = as_stream(stream);
     uint32_t* sink = nullptr;
     KSC_CUDA(cudaMalloc(&sink, 16));
-    const int grid = num_sms() * 16, iters = 4096;
+    const int iters = 4096;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    k_lut16_peak<<<grid, 128, 0, st>>>(iters, 12345u, sink);  // warm-up
-    cudaEventRecord(e0, st);
-    k_lut16_peak<<<grid, 128, 0, st>>>(iters, 54321u, sink);
-    cudaEventRecord(e1, st);
-    cudaError_t err = cudaEventSynchronize(e1);
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
+    // [0] the shared-selector sequence, 8 CTAs of 256 threads per SM;
+    // [1] the per-slot sequence, 16 CTAs of 128 threads per SM
+    double rate[2] = {0.0, 0.0};
+    cudaError_t err = cudaSuccess;
+    for (int v = 0; v < 2 && err == cudaSuccess; ++v) {
+        const int threads = v == 0 ? 256 : 128, grid = num_sms() * (v == 0 ? 8 : 16);
+        for (int rep = 0; rep < 2; ++rep) {  // the first launch warms up
+            if (rep == 1) cudaEventRecord(e0, st);
+            if (v == 0) k_lut16_peak_sel<<<grid, threads, 0, st>>>(iters, 12345u + rep, sink);
+            else k_lut16_peak<<<grid, threads, 0, st>>>(iters, 12345u + rep, sink);
+        }
+        cudaEventRecord(e1, st);
+        err = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        rate[v] = (double)grid * threads * iters * 32 / (ms * 1e-3) / 1e9;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(sink);
     KSC_CUDA(err);
-    *glookups_host = (double)grid * 128 * iters * 32 / (ms * 1e-3) / 1e9;
+    glookups_host[0] = rate[0];
+    glookups_host[1] = rate[1];
     return KSC_OK;
 }
 

@@ -642,10 +642,11 @@ def component_stats(X, stream=None):
 
 
 def lut16_peak(stream=None):
-    """Measured lookup rate (Glookup/s) of the scan's instruction sequence."""
-    v = C.c_double(0)
-    _check(lib().ksc_lut16_peak(C.byref(v), _stream(stream)))
-    return v.value
+    """Measured lookup rates (Glookup/s) of the scan's instruction sequences:
+    (shared selectors, per-slot selectors)."""
+    v = (C.c_double * 2)()
+    _check(lib().ksc_lut16_peak(v, _stream(stream)))
+    return v[0], v[1]
 
 
 def version():
