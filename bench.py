@@ -32,8 +32,11 @@ METRIC = "QPS at recall@10\u22650.90 (1M\u00d7128, 1 GB300) vs plain path; ADC-s
 TARGET_RECALL = 0.90
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of k_scan's two launches in one plain search at the
-# given nprobe, from ncu --set full (profiles/k_scan_ivfpq_sift1m_nq10k_nprobe<P>.md)
-SCAN_TRAFFIC_BYTES = {7: 190_171_648}
+# given nprobe, from ncu (profiles/k_scan_ivfpq_sift1m_nq10k_nprobe<P>.md)
+SCAN_TRAFFIC_BYTES = {7: 190_182_144}
+# the same for the streaming leg of the 10M x 96 index at batch 256, nprobe 256
+# (profiles/k_scan_deep10m_b256_nprobe256.md)
+DEEP_STREAM_TRAFFIC_BYTES = {(256, 256): 429_400_832}
 HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e, nominal
 
 
@@ -766,7 +769,9 @@ def deep_workload(torch, ksc, synth, dev, flush, args, batches=(16, 1024, 16384)
         stg, tot = stage_median(ix, lambda: ix.search(q, k, stream_nprobe, R), flush, 3, stream_reps)
         sms = stg["near_scan"] + stg["scan"]
         gbs = cb / (sms * 1e-3) / 1e9
+        tr = DEEP_STREAM_TRAFFIC_BYTES.get((B, stream_nprobe))
         stream[str(B)] = {"nprobe": stream_nprobe, "code_bytes": cb, "unique_code_bytes": ub,
+                          "dram_bytes_ncu": tr, "dram_over_unique": None if tr is None else round(tr / ub, 3),
                           "scan_ms": round(sms, 4), "search_ms": round(tot, 4), "GBps": round(gbs, 1),
                           "frac_of_hbm": round(gbs / peaks["hbm_gbs"], 4),
                           "frac_of_nominal": round(gbs / HBM_NOMINAL_GBS, 4),
