@@ -45,6 +45,9 @@ struct TcsQuery {
     int32_t bias, lim;
 };
 
+// Bounded wait on an mbarrier phase: a few quick polls, then polls spaced by
+// a short sleep, so that a waiting warp does not take issue slots from the
+// warps of its scheduler that have work (at most TCS_WAIT polls).
 __device__ __forceinline__ bool tcs_wait(uint32_t bar, uint32_t parity) {
     for (uint32_t i = 0; i < TCS_WAIT; ++i) {
         uint32_t ok;
@@ -54,6 +57,7 @@ __device__ __forceinline__ bool tcs_wait(uint32_t bar, uint32_t parity) {
             : "r"(bar), "r"(parity)
             : "memory");
         if (ok) return true;
+        if (i >= 4) __nanosleep(64);
     }
     return false;
 }
