@@ -905,8 +905,10 @@ __global__ void __launch_bounds__(SW_WARPS * 32) k_threshold(ScanArgs A, int Rma
     if (lane == 0) thr[q] = t;
 }
 
-// The same with one CTA per query, for queries with many keys.
-__global__ void __launch_bounds__(256) k_threshold_cta(ScanArgs A, int Rmax, int32_t* __restrict__ cnt,
+// The same with one CTA per query, for queries with many keys (NT threads:
+// 1024 when the batch is too small to fill the GPU with 256-thread CTAs).
+template <int NT>
+__global__ void __launch_bounds__(NT) k_threshold_cta(ScanArgs A, int Rmax, int32_t* __restrict__ cnt,
                                                        uint64_t* __restrict__ cand, int cap,
                                                        uint64_t* __restrict__ scratch,
                                                        uint64_t* __restrict__ thr) {
@@ -2012,7 +2014,8 @@ __global__ void __launch_bounds__(SW_WARPS * 32) k_select(ScanArgs A, int Rmax, 
 }
 
 // The same with one CTA per query, for queries with many candidates.
-__global__ void __launch_bounds__(256) k_select_cta(ScanArgs A, int Rmax, const int32_t* __restrict__ cnt,
+template <int NT>
+__global__ void __launch_bounds__(NT) k_select_cta(ScanArgs A, int Rmax, const int32_t* __restrict__ cnt,
                                                     const uint64_t* __restrict__ cand, int cap,
                                                     uint64_t* __restrict__ topr, int32_t* __restrict__ ncand,
                                                     int32_t* __restrict__ status,
@@ -2100,7 +2103,8 @@ __global__ void __launch_bounds__(256) k_select_redo(ScanArgs A, int Rmax, int s
 // Exact distance of each candidate (warp per candidate, 16-byte loads when d
 // is a multiple of 4): L2 = sum (q_t - x_t)^2, IP = -<q, x>; the k best by
 // (distance, id).  Output: L2 distance ascending / IP similarity descending.
-__global__ void __launch_bounds__(256) k_rerank(const float* __restrict__ Q, const float* __restrict__ X, int d,
+template <int NT>
+__global__ void __launch_bounds__(NT) k_rerank(const float* __restrict__ Q, const float* __restrict__ X, int d,
                                                 int ip, const uint64_t* __restrict__ topr, int Rmax,
                                                 const int32_t* __restrict__ rerank_q, int Rfix, int k,
                                                 int64_t* __restrict__ out_ids, float* __restrict__ out_d) {
@@ -2783,8 +2787,10 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
     if (std::max(4.0 * pl.Rmax, (double)pl.Pmax * ix->n / L / 16.0) <= SW_MAX_KEYS && warp_per_query(nq))
         k_threshold<<<(unsigned)((nq + SW_WARPS - 1) / SW_WARPS), SW_WARPS * 32, 0, st>>>(A, pl.Rmax, cnt, cand,
                                                                                            pl.cap, topr, thr);
+    else if (nq < 2 * (int64_t)num_sms())  // few queries: more threads per query
+        k_threshold_cta<1024><<<(unsigned)nq, 1024, 0, st>>>(A, pl.Rmax, cnt, cand, pl.cap, topr, thr);
     else
-        k_threshold_cta<<<(unsigned)nq, 256, 0, st>>>(A, pl.Rmax, cnt, cand, pl.cap, topr, thr);
+        k_threshold_cta<256><<<(unsigned)nq, 256, 0, st>>>(A, pl.Rmax, cnt, cand, pl.cap, topr, thr);
     KSC_LAUNCH_CHECK();
     ix->launches += 2;
     // 4. scan of the other lists, keeping keys at or below the threshold;
@@ -2836,9 +2842,12 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
         if (4 * pl.Rmax <= SW_MAX_KEYS && warp_per_query(nq))
             k_select<<<(unsigned)((nq + SW_WARPS - 1) / SW_WARPS), SW_WARPS * 32, 0, st>>>(
                 A, pl.Rmax, cnt, cand, pl.cap, topr, ncand_out, ix->status, ix->stats, redo);
+        else if (nq < 2 * (int64_t)num_sms())  // few queries: more threads per query
+            k_select_cta<1024><<<(unsigned)nq, 1024, 0, st>>>(A, pl.Rmax, cnt, cand, pl.cap, topr, ncand_out,
+                                                               ix->status, ix->stats, redo);
         else
-            k_select_cta<<<(unsigned)nq, 256, 0, st>>>(A, pl.Rmax, cnt, cand, pl.cap, topr, ncand_out, ix->status,
-                                                       ix->stats, redo);
+            k_select_cta<256><<<(unsigned)nq, 256, 0, st>>>(A, pl.Rmax, cnt, cand, pl.cap, topr, ncand_out,
+                                                             ix->status, ix->stats, redo);
         KSC_LAUNCH_CHECK();
         // overflowed queries (usually none): radix select over recomputed keys,
         // the R best plus their sort in a buffer of sel_cap keys
@@ -2895,9 +2904,17 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
         KSC_LAUNCH_CHECK();
     } else {
         const size_t smem = sizeof(uint64_t) * pow2_ceil(rr_R < 2 ? 2 : rr_R);
-        cudaFuncSetAttribute(k_rerank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_rerank<<<(unsigned)nq, 256, smem, st>>>(Qr, Xr, dr, ix->metric == KSC_IP, rr_keys, rr_R, rr_q, rr_R,
-                                                  pl.k, ids, dists);
+        // a CTA per query; 1024 threads (more rows in flight) when the batch is
+        // too small to fill the GPU with 256-thread CTAs
+        if (nq < 2 * (int64_t)num_sms()) {
+            cudaFuncSetAttribute(k_rerank<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_rerank<1024><<<(unsigned)nq, 1024, smem, st>>>(Qr, Xr, dr, ix->metric == KSC_IP, rr_keys, rr_R, rr_q,
+                                                             rr_R, pl.k, ids, dists);
+        } else {
+            cudaFuncSetAttribute(k_rerank<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_rerank<256><<<(unsigned)nq, 256, smem, st>>>(Qr, Xr, dr, ix->metric == KSC_IP, rr_keys, rr_R, rr_q,
+                                                           rr_R, pl.k, ids, dists);
+        }
         ix->launches++;
         KSC_LAUNCH_CHECK();
     }
@@ -3079,8 +3096,13 @@ int rerank_keys(ksc_index* ix, const float* Q, int64_t nq, int k, const uint64_t
             Q, Xr, dr, ip, keys, R, nullptr, R, k, nq, ids, dists);
     } else {
         const size_t smem = sizeof(uint64_t) * pow2_ceil(R < 2 ? 2 : R);
-        KSC_CUDA(cudaFuncSetAttribute(k_rerank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_rerank<<<(unsigned)nq, 256, smem, st>>>(Q, Xr, dr, ip, keys, R, nullptr, R, k, ids, dists);
+        if (nq < 2 * (int64_t)num_sms()) {
+            KSC_CUDA(cudaFuncSetAttribute(k_rerank<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_rerank<1024><<<(unsigned)nq, 1024, smem, st>>>(Q, Xr, dr, ip, keys, R, nullptr, R, k, ids, dists);
+        } else {
+            KSC_CUDA(cudaFuncSetAttribute(k_rerank<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_rerank<256><<<(unsigned)nq, 256, smem, st>>>(Q, Xr, dr, ip, keys, R, nullptr, R, k, ids, dists);
+        }
     }
     KSC_LAUNCH_CHECK();
     ix->launches++;
