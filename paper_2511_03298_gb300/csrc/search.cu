@@ -128,7 +128,8 @@ __device__ __forceinline__ float exact_list_score(const float* __restrict__ qs, 
     return spherical ? -acc : acc;
 }
 
-__global__ void __launch_bounds__(256) k_rank_select(const float* __restrict__ scores, const float* __restrict__ err,
+template <int NT>
+__global__ void __launch_bounds__(NT) k_rank_select(const float* __restrict__ scores, const float* __restrict__ err,
                                                      const float* __restrict__ Q, const float* __restrict__ Cc,
                                                      int64_t nq, int d, int L, int spherical,
                                                      const int32_t* __restrict__ nprobe_q, int Pfix, int Pmax,
@@ -2556,7 +2557,8 @@ static int rank_lists(ksc_index* ix, const float* Q, int64_t nq, const int32_t* 
     // re-score buffer of the CTA kernel: 4 Pmax lists (a power of two, at least 1024, at most RS_CAP)
     const int rs_cap = std::min(RS_CAP, std::max(1024, pow2_ceil(4 * Pmax)));
     const size_t smem = rs_cap * sizeof(uint64_t) + (ix->L <= RS_SMEM_L ? sizeof(float) * ix->L : 0);
-    KSC_CUDA(cudaFuncSetAttribute(k_rank_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    KSC_CUDA(cudaFuncSetAttribute(k_rank_select<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    KSC_CUDA(cudaFuncSetAttribute(k_rank_select<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (ix->L <= RSW_MAX_L && Pmax <= 4 * RSW_CAND / 8 && warp_per_query(nq)) {
         // a warp per query; queries with too many lists inside the bound go to the CTA kernel
         KSC_TRY(ensure(ix->ws_redo, sizeof(int32_t) * (nq + 1), st));
@@ -2569,12 +2571,19 @@ static int rank_lists(ksc_index* ix, const float* Q, int64_t nq, const int32_t* 
             redo, feat);
         feat = nullptr;  // written
         KSC_LAUNCH_CHECK();
-        k_rank_select<<<num_sms() * 2, 256, smem, st>>>(scores, err, Q, ix->c_rank, nq, ix->d, ix->L, ix->spherical,
+        k_rank_select<256><<<num_sms() * 2, 256, smem, st>>>(scores, err, Q, ix->c_rank, nq, ix->d, ix->L, ix->spherical,
                                                         nprobe_q, Pfix, Pmax, rs_cap, probes, score_out, redo);
         ix->launches += 2;
     } else {
-        k_rank_select<<<(unsigned)nq, 256, smem, st>>>(scores, err, Q, ix->c_rank, nq, ix->d, ix->L, ix->spherical,
-                                                       nprobe_q, Pfix, Pmax, rs_cap, probes, score_out, nullptr);
+        // a CTA per query; 1024 threads when the batch is too small to fill the GPU
+        if (nq < 2 * (int64_t)num_sms())
+            k_rank_select<1024><<<(unsigned)nq, 1024, smem, st>>>(scores, err, Q, ix->c_rank, nq, ix->d, ix->L,
+                                                                  ix->spherical, nprobe_q, Pfix, Pmax, rs_cap, probes,
+                                                                  score_out, nullptr);
+        else
+            k_rank_select<256><<<(unsigned)nq, 256, smem, st>>>(scores, err, Q, ix->c_rank, nq, ix->d, ix->L,
+                                                                ix->spherical, nprobe_q, Pfix, Pmax, rs_cap, probes,
+                                                                score_out, nullptr);
         ix->launches++;
     }
     KSC_LAUNCH_CHECK();
