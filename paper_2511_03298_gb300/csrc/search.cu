@@ -605,96 +605,82 @@ __device__ __forceinline__ int32_t lut_bias(const LutArgs& A, const float* __res
     return (int32_t)bf;
 }
 
-// Two-pass tables, one thread per (item, subspace row): a CTA takes tiles of
-// floor(256 / M) consecutive items.  Pass 1: the largest row range of each
-// query, R_q (max over its items: shared then global atomic max; R >= 0, so
-// the bit order is the value order).
+// Two-pass tables when a query's tables do not fit one CTA's shared memory
+// (many probes): a warp per item (query, probe rank), lane l computing the
+// rows j = l, l + 32, ... (M <= KSC_MAX_M), no block barrier.  Pass 1: the
+// largest row range of each query, R_q (a warp maximum per item, then one
+// global atomic maximum; R >= 0, so the bit order is the value order).
+constexpr int LUT_WARPS = 8;
+
 template <int DS>
-__global__ void __launch_bounds__(256) k_lut_range(LutArgs A, uint32_t* __restrict__ range_bits) {
+__global__ void __launch_bounds__(LUT_WARPS * 32) k_lut_range(LutArgs A, uint32_t* __restrict__ range_bits) {
     extern __shared__ float cbs[];
-    __shared__ uint32_t s_R[256];
     stage_codebook(A, cbs);
     const int ld = cb_ld(A.dsub);
-    const int per = blockDim.x / A.M;
-    const int il = threadIdx.x / A.M, j = threadIdx.x - il * A.M;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int64_t n0;
     const int64_t items = lut_items(A, &n0);
-    for (int64_t base = (int64_t)blockIdx.x * per; base < items; base += (int64_t)gridDim.x * per) {
-        if (threadIdx.x < per) s_R[threadIdx.x] = 0u;
-        __syncthreads();
-        const int64_t i = base + il;
-        if (il < per && i < items) {
-            const int64_t item = lut_item(A, i, n0);
-            const int64_t q = item / A.Pmax;
-            const int r = (int)(item - q * A.Pmax);
-            const int p = A.probes[item];
-            if (r < probes_of(A, q) && p >= 0 && p < A.L) {  // invalid probe ids are skipped
-                float T[PQ_K];
-                row_table<DS>(A.dsub, A.ip, A.Q + q * A.d + j * A.dsub, A.c_mean + (int64_t)p * A.d + j * A.dsub,
-                              cbs + j * ld, T);
-                float mn = T[0], mx = T[0];
+    for (int64_t i = (int64_t)blockIdx.x * LUT_WARPS + warp; i < items; i += (int64_t)gridDim.x * LUT_WARPS) {
+        const int64_t item = lut_item(A, i, n0);
+        const int64_t q = item / A.Pmax;
+        const int r = (int)(item - q * A.Pmax);
+        const int p = A.probes[item];
+        if (r >= probes_of(A, q) || p < 0 || p >= A.L) continue;  // invalid probe ids are skipped (warp-uniform)
+        float R = 0.f;
+        for (int j = lane; j < A.M; j += 32) {
+            float T[PQ_K];
+            row_table<DS>(A.dsub, A.ip, A.Q + q * A.d + j * A.dsub, A.c_mean + (int64_t)p * A.d + j * A.dsub,
+                          cbs + j * ld, T);
+            float mn = T[0], mx = T[0];
 #pragma unroll
-                for (int e = 1; e < PQ_K; ++e) { mn = fminf(mn, T[e]); mx = fmaxf(mx, T[e]); }
-                atomicMax(&s_R[il], __float_as_uint(__fsub_rn(mx, mn)));
-            }
+            for (int e = 1; e < PQ_K; ++e) { mn = fminf(mn, T[e]); mx = fmaxf(mx, T[e]); }
+            R = fmaxf(R, __fsub_rn(mx, mn));
         }
-        __syncthreads();
-        if (threadIdx.x < per && base + threadIdx.x < items && s_R[threadIdx.x] != 0u) {
-            const int64_t item = lut_item(A, base + threadIdx.x, n0);
-            atomicMax(&range_bits[item / A.Pmax], s_R[threadIdx.x]);
-        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) R = fmaxf(R, __shfl_xor_sync(0xffffffffu, R, o));
+        if (lane == 0 && R > 0.f) atomicMax(&range_bits[q], __float_as_uint(R));
     }
 }
 
 // Pass 2: u8 tables Q = min(255, floor((T - m_j) a + 1/2)), a = 255 / R_q,
-// then the bias of each item from its row minima.
+// then the item's bias from its row minima (summed in ascending j by lane 0,
+// the FP32 rule's order).
 template <int DS>
-__global__ void __launch_bounds__(256) k_lut_quant(LutArgs A, const uint32_t* __restrict__ range_bits,
-                                                   uint8_t* __restrict__ lut, int32_t* __restrict__ bias,
-                                                   float* __restrict__ scale) {
+__global__ void __launch_bounds__(LUT_WARPS * 32) k_lut_quant(LutArgs A, const uint32_t* __restrict__ range_bits,
+                                                              uint8_t* __restrict__ lut, int32_t* __restrict__ bias,
+                                                              float* __restrict__ scale) {
     extern __shared__ float cbs[];
-    __shared__ float s_min[256];
+    __shared__ float s_min[LUT_WARPS][KSC_MAX_M];
     stage_codebook(A, cbs);
     const int ld = cb_ld(A.dsub);
-    const int per = blockDim.x / A.M;
-    const int il = threadIdx.x / A.M, j = threadIdx.x - il * A.M;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int64_t n0;
     const int64_t items = lut_items(A, &n0);
-    for (int64_t base = (int64_t)blockIdx.x * per; base < items; base += (int64_t)gridDim.x * per) {
-        const int64_t i = base + il;
-        if (il < per && i < items) {
-            const int64_t item = lut_item(A, i, n0);
-            const int64_t q = item / A.Pmax;
-            const int r = (int)(item - q * A.Pmax);
-            const int p = A.probes[item];
-            if (r < probes_of(A, q) && p >= 0 && p < A.L) {
-                const float Rq = __uint_as_float(range_bits[q]);
-                const float a = (Rq == 0.f) ? 1.f : __fdiv_rn(255.f, Rq);
-                float T[PQ_K];
-                row_table<DS>(A.dsub, A.ip, A.Q + q * A.d + j * A.dsub, A.c_mean + (int64_t)p * A.d + j * A.dsub,
-                              cbs + j * ld, T);
-                float mn = T[0];
+    for (int64_t i = (int64_t)blockIdx.x * LUT_WARPS + warp; i < items; i += (int64_t)gridDim.x * LUT_WARPS) {
+        const int64_t item = lut_item(A, i, n0);
+        const int64_t q = item / A.Pmax;
+        const int r = (int)(item - q * A.Pmax);
+        const int p = A.probes[item];
+        if (r >= probes_of(A, q) || p < 0 || p >= A.L) continue;  // warp-uniform
+        const float Rq = __uint_as_float(range_bits[q]);
+        const float a = (Rq == 0.f) ? 1.f : __fdiv_rn(255.f, Rq);
+        for (int j = lane; j < A.M; j += 32) {
+            float T[PQ_K];
+            row_table<DS>(A.dsub, A.ip, A.Q + q * A.d + j * A.dsub, A.c_mean + (int64_t)p * A.d + j * A.dsub,
+                          cbs + j * ld, T);
+            float mn = T[0];
 #pragma unroll
-                for (int e = 1; e < PQ_K; ++e) mn = fminf(mn, T[e]);
-                reinterpret_cast<uint4*>(lut + item * (int64_t)A.M * PQ_K)[j] =
-                    make_uint4(quant4(T, mn, a), quant4(T + 4, mn, a), quant4(T + 8, mn, a), quant4(T + 12, mn, a));
-                s_min[threadIdx.x] = mn;
-            }
+            for (int e = 1; e < PQ_K; ++e) mn = fminf(mn, T[e]);
+            reinterpret_cast<uint4*>(lut + item * (int64_t)A.M * PQ_K)[j] =
+                make_uint4(quant4(T, mn, a), quant4(T + 4, mn, a), quant4(T + 8, mn, a), quant4(T + 12, mn, a));
+            s_min[warp][j] = mn;
         }
-        __syncthreads();
-        if (threadIdx.x < per && base + threadIdx.x < items) {
-            const int64_t item = lut_item(A, base + threadIdx.x, n0);
-            const int64_t q = item / A.Pmax;
-            const int r = (int)(item - q * A.Pmax);
-            const int p = A.probes[item];
-            if (r < probes_of(A, q) && p >= 0 && p < A.L) {
-                const float Rq = __uint_as_float(range_bits[q]);
-                const float a = (Rq == 0.f) ? 1.f : __fdiv_rn(255.f, Rq);
-                bias[item] = lut_bias(A, A.Q + q * A.d, A.c_mean + (int64_t)p * A.d, s_min + threadIdx.x * A.M, a);
-                if (r == 0) scale[q] = a;
-            }
+        __syncwarp();
+        if (lane == 0) {
+            bias[item] = lut_bias(A, A.Q + q * A.d, A.c_mean + (int64_t)p * A.d, s_min[warp], a);
+            if (r == 0) scale[q] = a;
         }
-        __syncthreads();
+        __syncwarp();  // s_min is read before the warp's next item overwrites it
     }
 }
 
@@ -2597,21 +2583,20 @@ static int rank_lists(ksc_index* ix, const float* Q, int64_t nq, const int32_t* 
 
 static int launch_luts(const LutArgs& A, uint32_t* rb, uint8_t* lut, int32_t* bias, float* scale, cudaStream_t st) {
     const size_t smem = sizeof(float) * (size_t)A.M * cb_ld(A.dsub);
-    const int per = 256 / A.M;
-    const int64_t tiles = (A.nq * A.Pmax + per - 1) / per;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)num_sms() * 8));
+    const int64_t warps = (A.nq * A.Pmax + LUT_WARPS - 1) / LUT_WARPS;  // a warp per item
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(warps, (int64_t)num_sms() * 8));
     if (lut_ds2(A)) {
         KSC_CUDA(cudaFuncSetAttribute(k_lut_range<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         KSC_CUDA(cudaFuncSetAttribute(k_lut_quant<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_lut_range<2><<<grid, 256, smem, st>>>(A, rb);
+        k_lut_range<2><<<grid, LUT_WARPS * 32, smem, st>>>(A, rb);
         KSC_LAUNCH_CHECK();
-        k_lut_quant<2><<<grid, 256, smem, st>>>(A, rb, lut, bias, scale);
+        k_lut_quant<2><<<grid, LUT_WARPS * 32, smem, st>>>(A, rb, lut, bias, scale);
     } else {
         KSC_CUDA(cudaFuncSetAttribute(k_lut_range<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         KSC_CUDA(cudaFuncSetAttribute(k_lut_quant<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_lut_range<0><<<grid, 256, smem, st>>>(A, rb);
+        k_lut_range<0><<<grid, LUT_WARPS * 32, smem, st>>>(A, rb);
         KSC_LAUNCH_CHECK();
-        k_lut_quant<0><<<grid, 256, smem, st>>>(A, rb, lut, bias, scale);
+        k_lut_quant<0><<<grid, LUT_WARPS * 32, smem, st>>>(A, rb, lut, bias, scale);
     }
     KSC_LAUNCH_CHECK();
     return KSC_OK;
