@@ -112,6 +112,9 @@ int mlp_grad(const float* w, const float* x, const float* y, int64_t B, float* g
 int mlp_infer(const float* w, const float* x, int64_t B, const ksc_adaptive_params& prm, float* prob,
               int32_t* nprobe, int32_t* rerank, cudaStream_t st);
 int mlp_features(const float* scores, int64_t nq, int ld, int spherical, float* feats, cudaStream_t st);
+// Features and inference in one kernel (the adaptive search): settings per query.
+int mlp_infer_scores(const float* w, const float* scores, int ld, int spherical, int64_t B,
+                     const ksc_adaptive_params& prm, int32_t* nprobe, int32_t* rerank, cudaStream_t st);
 int mlp_hits(const float* dists, int64_t nq, int k, const float* kth, int ip, int32_t* hits, cudaStream_t st);
 int mlp_adam(float* w, const float* g, float* m, float* v, int t, float lr, cudaStream_t st);
 int mlp_adam_n(float* w, const float* g, float* m, float* v, int n, int t, float lr, cudaStream_t st);

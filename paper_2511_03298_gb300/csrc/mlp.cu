@@ -276,6 +276,122 @@ __global__ void __launch_bounds__(256) k_mlp_infer(const float* __restrict__ w, 
     }
 }
 
+// The adaptive search's head in one kernel: per tile of MLP_STILE queries the
+// features of each query from its sorted ranking distances (as k_features),
+// then the network and the settings (as k_mlp_infer).  Each output unit is
+// accumulated in the same order from the same BF16-rounded operands as
+// there, so the settings are bit for bit those of the two kernels; what
+// differs is the blocking: the weights are staged transposed ([f][a]) and
+// the activations feature-major ([f][r]), and every thread keeps a block of
+// 4 units x 4 rows in registers, so that one float4 of activations and one of
+// weights feed 16 FMAs (the one-output-per-thread form needs two shared
+// loads per FMA).
+constexpr int MLP_STILE = 64;      // queries per tile
+constexpr int MLP_SLD = 68;        // row stride of the transposed arrays (16-byte aligned, staggered banks)
+constexpr int MLP_SW = MLP_F * MLP_SLD;
+static_assert(MLP_F == 64 && MLP_H == 64 && MLP_O == 2 && MLP_FEAT_K * 2 == MLP_F, "head layout");
+constexpr size_t mlp_scores_smem() { return sizeof(float) * (4 * MLP_SW + 2 * MLP_H + MLP_O * MLP_H + 4); }
+
+// HT[a][r] = bf(relu(b[a] + sum_f XT[f][r] WT[f][a])) for the thread's 4 x 4 block.
+__device__ __forceinline__ void dense_block(const float* XT, const float* WT, const float* bsm, float* HT, int rg,
+                                           int ug) {
+    float acc[4][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float bj = bsm[4 * ug + j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[j][i] = bj;
+    }
+#pragma unroll 4
+    for (int f = 0; f < MLP_F; ++f) {
+        const float4 x = *reinterpret_cast<const float4*>(XT + f * MLP_SLD + 4 * rg);
+        const float4 wv = *reinterpret_cast<const float4*>(WT + f * MLP_SLD + 4 * ug);
+        const float xs[4] = {x.x, x.y, x.z, x.w}, ws[4] = {wv.x, wv.y, wv.z, wv.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[j][i] = fmaf(xs[i], ws[j], acc[j][i]);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        float4 o;
+        o.x = bf(acc[j][0] > 0.f ? acc[j][0] : 0.f);
+        o.y = bf(acc[j][1] > 0.f ? acc[j][1] : 0.f);
+        o.z = bf(acc[j][2] > 0.f ? acc[j][2] : 0.f);
+        o.w = bf(acc[j][3] > 0.f ? acc[j][3] : 0.f);
+        *reinterpret_cast<float4*>(HT + (4 * ug + j) * MLP_SLD + 4 * rg) = o;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_mlp_infer_scores(const float* __restrict__ scores, int ld, int spherical,
+                                                          const float* __restrict__ w, int64_t B,
+                                                          ksc_adaptive_params prm, int32_t* __restrict__ nprobe,
+                                                          int32_t* __restrict__ rerank) {
+    extern __shared__ float4 msm4[];
+    float* WT1 = reinterpret_cast<float*>(msm4);
+    float* WT2 = WT1 + MLP_SW;
+    float* XT = WT2 + MLP_SW;  // features, then the second hidden layer
+    float* HT = XT + MLP_SW;   // first hidden layer
+    float* b1 = HT + MLP_SW;
+    float* b2 = b1 + MLP_H;
+    float* W3 = b2 + MLP_H;
+    float* b3 = W3 + MLP_O * MLP_H;
+    const MlpW G = mlp_views(w);
+    for (int e = threadIdx.x; e < MLP_H * MLP_F; e += blockDim.x) {
+        const int a = e / MLP_F, f = e - a * MLP_F;
+        WT1[f * MLP_SLD + a] = bf(G.W1[e]);
+        WT2[f * MLP_SLD + a] = bf(G.W2[e]);  // (MLP_F == MLP_H)
+    }
+    for (int e = threadIdx.x; e < MLP_H; e += blockDim.x) {
+        b1[e] = bf(G.b1[e]);
+        b2[e] = bf(G.b2[e]);
+    }
+    for (int e = threadIdx.x; e < MLP_O * MLP_H; e += blockDim.x) W3[e] = bf(G.W3[e]);
+    if (threadIdx.x < MLP_O) b3[threadIdx.x] = bf(G.b3[threadIdx.x]);
+    const int lane = threadIdx.x & 31;
+    const int rg = lane & 15, ug = (threadIdx.x >> 5) * 2 + (lane >> 4);  // rows 4 rg.., units 4 ug..
+    for (int64_t r0 = (int64_t)blockIdx.x * MLP_STILE; r0 < B; r0 += (int64_t)gridDim.x * MLP_STILE) {
+        const int rows = (int)(B - r0 < MLP_STILE ? B - r0 : MLP_STILE);
+        __syncthreads();  // staging done / the previous tile's readers done
+        if (threadIdx.x < MLP_STILE) {
+            const int r = threadIdx.x;
+            if (r < rows) {
+                const float* sq = scores + (r0 + r) * ld;
+                float mean = 0.f;
+                for (int i = 0; i < MLP_FEAT_K; ++i) mean += fmaxf(feat_dist(sq[i], spherical), 0.f);
+                mean = mean / MLP_FEAT_K + 1e-12f;
+                const float d1 = fmaxf(feat_dist(sq[0], spherical), 0.f) + 1e-12f;
+                for (int i = 0; i < MLP_FEAT_K; ++i) {
+                    const float di = fmaxf(feat_dist(sq[i], spherical), 0.f) + 1e-12f;
+                    XT[i * MLP_SLD + r] = bf(di / mean);
+                    XT[(MLP_FEAT_K + i) * MLP_SLD + r] = bf(d1 / di);
+                }
+            } else {
+                for (int f = 0; f < MLP_F; ++f) XT[f * MLP_SLD + r] = 0.f;  // rows past the batch
+            }
+        }
+        __syncthreads();
+        dense_block(XT, WT1, b1, HT, rg, ug);
+        __syncthreads();
+        dense_block(HT, WT2, b2, XT, rg, ug);
+        __syncthreads();
+        if (threadIdx.x < MLP_O * MLP_STILE) {
+            const int r = threadIdx.x & (MLP_STILE - 1), o = threadIdx.x / MLP_STILE;
+            if (r < rows) {
+                float z = b3[o];
+                for (int f = 0; f < MLP_H; ++f) z = fmaf(XT[f * MLP_SLD + r], W3[o * MLP_H + f], z);
+                const float p = 1.f / (1.f + expf(-z));
+                if (o == 0)
+                    nprobe[r0 + r] = prm.regression ? regmap(p, prm.pmin, prm.pmax, prm.p0, prm.p1)
+                                                    : eq2(p, prm.pmin, prm.pmax, prm.p0, prm.p1);
+                else
+                    rerank[r0 + r] = prm.regression ? regmap(p, prm.rmin, prm.rmax, prm.r0, prm.r1)
+                                                    : eq2(p, prm.rmin, prm.rmax, prm.r0, prm.r1);
+            }
+        }
+    }
+}
+
 // Hits of a search result: how many of the k returned distances are at most
 // the query's true k-th distance (ties count), for the label rule.
 __global__ void k_hits(const float* __restrict__ dists, int64_t nq, int k, const float* __restrict__ kth, int ip,
@@ -331,6 +447,19 @@ int mlp_infer(const float* w, const float* x, int64_t B, const ksc_adaptive_para
     const int64_t tiles = (B + MLP_ITILE - 1) / MLP_ITILE;
     const int64_t grid = std::min<int64_t>(tiles, (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1));
     k_mlp_infer<<<(unsigned)(grid > 0 ? grid : 1), 256, infer_smem(), st>>>(w, x, B, prm, prob, nprobe, rerank);
+    KSC_LAUNCH_CHECK();
+    return KSC_OK;
+}
+
+int mlp_infer_scores(const float* w, const float* scores, int ld, int spherical, int64_t B,
+                     const ksc_adaptive_params& prm, int32_t* nprobe, int32_t* rerank, cudaStream_t st) {
+    if (B == 0) return KSC_OK;
+    KSC_CUDA(cudaFuncSetAttribute(k_mlp_infer_scores, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)mlp_scores_smem()));
+    const int64_t tiles = (B + MLP_STILE - 1) / MLP_STILE;
+    const int64_t grid = std::min<int64_t>(tiles, (int64_t)num_sms() * 2);
+    k_mlp_infer_scores<<<(unsigned)grid, 256, mlp_scores_smem(), st>>>(scores, ld, spherical, w, B, prm, nprobe,
+                                                                      rerank);
     KSC_LAUNCH_CHECK();
     return KSC_OK;
 }

@@ -3596,19 +3596,21 @@ int ksc_search_adaptive(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t k
     KSC_CUDA(cudaMemsetAsync(ix->status, 0, sizeof(int32_t), st));
     KSC_CUDA(cudaMemsetAsync(ix->stats, 0, sizeof(unsigned long long) * 4, st));
     KSC_TRY(ensure(ix->ws_probes, sizeof(int32_t) * nq * Pr, st));
-    KSC_TRY(ensure(ix->ws_feat, sizeof(float) * nq * KSC_MLP_FEATURES, st));
     KSC_TRY(ensure(ix->ws_nprobe, sizeof(int32_t) * nq, st));
     KSC_TRY(ensure(ix->ws_rerank, sizeof(int32_t) * nq, st));
     int32_t* probes = (int32_t*)ix->ws_probes.p;
-    float* feats = (float*)ix->ws_feat.p;
     int32_t* np_q = (int32_t*)ix->ws_nprobe.p;
     int32_t* r_q = (int32_t*)ix->ws_rerank.p;
     ix->launches = 0;
     mark(ix, 0, st);
     const float* Qw;
     KSC_TRY(work_queries(ix, Q_dev, nq, st, &Qw));
-    KSC_TRY(rank_and_features(ix, Qw, nq, Pr, probes, feats, st));
-    KSC_TRY(mlp_infer(ix->mlp_w, feats, nq, prm, nullptr, np_q, r_q, st));
+    // ranking of the lists a query may probe, its FEAT_K smallest distances,
+    // then features + network + Eq. 2 in one kernel
+    KSC_TRY(ensure(ix->ws_rscore, sizeof(float) * nq * FEAT_K, st));
+    float* rs = (float*)ix->ws_rscore.p;
+    KSC_TRY(rank_lists(ix, Qw, nq, nullptr, Pr, Pr, probes, nullptr, RANK_TC16, st, rs));
+    KSC_TRY(mlp_infer_scores(ix->mlp_w, rs, FEAT_K, ix->spherical, nq, prm, np_q, r_q, st));
     ix->launches++;
     pl.nprobe_q = np_q;
     pl.rerank_q = r_q;

@@ -116,6 +116,17 @@ def test_eq2_and_features_on_device_follow_the_oracle(env, trained):
     # FP32 on the device, FP64 in the oracle: equal except at a ceil boundary
     assert np.abs(npb - ref_n).max() <= 1 and (npb == ref_n).mean() >= 0.99
     assert np.abs(rr - ref_r).max() <= 1 and (rr == ref_r).mean() >= 0.99
+    # the search's fused head (features + network in one kernel) gives the
+    # settings of the separate feature and forward kernels exactly: Eq. 2
+    # evaluated in FP32 on their probabilities
+    def eq2_f32(v, lo, hi, a, b):
+        v = np.float32(v)
+        relu = max(v - np.float32(a), np.float32(0))
+        r = np.float32(lo) + np.ceil(np.float32(hi - lo) * relu * (v + np.float32(b)))
+        return int(min(max(r, np.float32(lo)), np.float32(hi)))
+    p32 = p.astype(np.float32)
+    assert np.array_equal(npb, [eq2_f32(v, 4, 64, 0.25, 0.4) for v in p32[:, 0]])
+    assert np.array_equal(rr, [eq2_f32(v, 20, 400, 0.3, 0.6) for v in p32[:, 1]])
     # features: distances of the 32 nearest lists, normalised
     f = feats.cpu().numpy()
     assert np.allclose(f[:, :32].mean(1), 1.0, atol=1e-4) and np.all(f[:, 32] > 0.999)
