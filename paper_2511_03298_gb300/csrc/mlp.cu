@@ -276,110 +276,147 @@ __global__ void __launch_bounds__(256) k_mlp_infer(const float* __restrict__ w, 
     }
 }
 
-// The adaptive search's head in one kernel: per tile of MLP_STILE queries the
+// The adaptive search's head in one kernel: per tile of 32 RPT queries the
 // features of each query from its sorted ranking distances (as k_features),
 // then the network and the settings (as k_mlp_infer).  Each output unit is
 // accumulated in the same order from the same BF16-rounded operands as
 // there, so the settings are bit for bit those of the two kernels; what
 // differs is the blocking: the weights are staged transposed ([f][a]) and
-// the activations feature-major ([f][r]), and every thread keeps a block of
-// 4 units x 4 rows in registers, so that one float4 of activations and one of
-// weights feed 16 FMAs (the one-output-per-thread form needs two shared
-// loads per FMA).
-constexpr int MLP_STILE = 64;      // queries per tile
-constexpr int MLP_SLD = 68;        // row stride of the transposed arrays (16-byte aligned, staggered banks)
+// the activations feature-major ([f][r]), and each of the 512 threads keeps a
+// block of 4 units x RPT rows in registers (a warp: one group of 4 units for
+// all rows of the tile), so that RPT activations and a float4 of weights (a
+// broadcast) feed 4 RPT FMAs.  The weight loads are issued first and stored
+// after the features, so that their latency overlaps the feature loads.
+constexpr int MLP_STHREADS = 512;  // threads per CTA: 32 row groups x MLP_H / 4 unit groups
+constexpr int MLP_SLD = 68;        // row stride of the transposed weights (16-byte aligned, staggered banks)
 constexpr int MLP_SW = MLP_F * MLP_SLD;
 static_assert(MLP_F == 64 && MLP_H == 64 && MLP_O == 2 && MLP_FEAT_K * 2 == MLP_F, "head layout");
-constexpr size_t mlp_scores_smem() { return sizeof(float) * (4 * MLP_SW + 2 * MLP_H + MLP_O * MLP_H + 4); }
+static_assert(MLP_STHREADS == 32 * (MLP_H / 4), "one block of 4 units per thread");
+template <int RPT>
+constexpr int mlp_xld() { return 32 * RPT + 4; }  // row stride of the activations
+template <int RPT>
+constexpr size_t mlp_scores_smem() {
+    return sizeof(float) * (2 * MLP_SW + 2 * MLP_F * mlp_xld<RPT>() + 2 * MLP_H + MLP_O * MLP_H + 4);
+}
 
-// HT[a][r] = bf(relu(b[a] + sum_f XT[f][r] WT[f][a])) for the thread's 4 x 4 block.
+// HT[a][r] = bf(relu(b[a] + sum_f XT[f][r] WT[f][a])) for the thread's block
+// (units 4 ug.., rows rg + 32 t for t < RPT: a warp's loads of one row index
+// are consecutive words, conflict-free).
+template <int RPT>
 __device__ __forceinline__ void dense_block(const float* XT, const float* WT, const float* bsm, float* HT, int rg,
                                            int ug) {
-    float acc[4][4];
+    constexpr int XLD = mlp_xld<RPT>();
+    float acc[4][RPT];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const float bj = bsm[4 * ug + j];
+    for (int j = 0; j < 4; ++j)
 #pragma unroll
-        for (int i = 0; i < 4; ++i) acc[j][i] = bj;
-    }
-#pragma unroll 4
+        for (int t = 0; t < RPT; ++t) acc[j][t] = bsm[4 * ug + j];
+#pragma unroll 8
     for (int f = 0; f < MLP_F; ++f) {
-        const float4 x = *reinterpret_cast<const float4*>(XT + f * MLP_SLD + 4 * rg);
+        float x[RPT];
+#pragma unroll
+        for (int t = 0; t < RPT; ++t) x[t] = XT[f * XLD + rg + 32 * t];
         const float4 wv = *reinterpret_cast<const float4*>(WT + f * MLP_SLD + 4 * ug);
-        const float xs[4] = {x.x, x.y, x.z, x.w}, ws[4] = {wv.x, wv.y, wv.z, wv.w};
+        const float ws[4] = {wv.x, wv.y, wv.z, wv.w};
 #pragma unroll
         for (int j = 0; j < 4; ++j)
 #pragma unroll
-            for (int i = 0; i < 4; ++i) acc[j][i] = fmaf(xs[i], ws[j], acc[j][i]);
+            for (int t = 0; t < RPT; ++t) acc[j][t] = fmaf(x[t], ws[j], acc[j][t]);
     }
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        float4 o;
-        o.x = bf(acc[j][0] > 0.f ? acc[j][0] : 0.f);
-        o.y = bf(acc[j][1] > 0.f ? acc[j][1] : 0.f);
-        o.z = bf(acc[j][2] > 0.f ? acc[j][2] : 0.f);
-        o.w = bf(acc[j][3] > 0.f ? acc[j][3] : 0.f);
-        *reinterpret_cast<float4*>(HT + (4 * ug + j) * MLP_SLD + 4 * rg) = o;
-    }
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int t = 0; t < RPT; ++t) HT[(4 * ug + j) * XLD + rg + 32 * t] = bf(acc[j][t] > 0.f ? acc[j][t] : 0.f);
 }
 
-__global__ void __launch_bounds__(256) k_mlp_infer_scores(const float* __restrict__ scores, int ld, int spherical,
-                                                          const float* __restrict__ w, int64_t B,
-                                                          ksc_adaptive_params prm, int32_t* __restrict__ nprobe,
-                                                          int32_t* __restrict__ rerank) {
+template <int RPT>
+__global__ void __launch_bounds__(MLP_STHREADS) k_mlp_infer_scores(const float* __restrict__ scores, int ld,
+                                                                   int spherical, const float* __restrict__ w,
+                                                                   int64_t B, ksc_adaptive_params prm,
+                                                                   int32_t* __restrict__ nprobe,
+                                                                   int32_t* __restrict__ rerank) {
+    constexpr int TILE = 32 * RPT, XLD = mlp_xld<RPT>();
     extern __shared__ float4 msm4[];
+    __shared__ float s_mean[TILE], s_d1[TILE];
     float* WT1 = reinterpret_cast<float*>(msm4);
     float* WT2 = WT1 + MLP_SW;
-    float* XT = WT2 + MLP_SW;  // features, then the second hidden layer
-    float* HT = XT + MLP_SW;   // first hidden layer
-    float* b1 = HT + MLP_SW;
+    float* XT = WT2 + MLP_SW;       // features (first the clamped distances), then the second hidden layer
+    float* HT = XT + MLP_F * XLD;   // first hidden layer
+    float* b1 = HT + MLP_F * XLD;
     float* b2 = b1 + MLP_H;
     float* W3 = b2 + MLP_H;
     float* b3 = W3 + MLP_O * MLP_H;
     const MlpW G = mlp_views(w);
-    for (int e = threadIdx.x; e < MLP_H * MLP_F; e += blockDim.x) {
-        const int a = e / MLP_F, f = e - a * MLP_F;
-        WT1[f * MLP_SLD + a] = bf(G.W1[e]);
-        WT2[f * MLP_SLD + a] = bf(G.W2[e]);  // (MLP_F == MLP_H)
+    // both hidden matrices in one round of 16-byte loads; thread t takes row
+    // a = t % 64 of each (so that the transposed stores of a warp fall in
+    // distinct banks)
+    constexpr int V = MLP_H * MLP_F / 4 / MLP_STHREADS;
+    float4 v1[V], v2[V];
+#pragma unroll
+    for (int u = 0; u < V; ++u) {
+        const int a = threadIdx.x & (MLP_H - 1), fq = (threadIdx.x >> 6) + (MLP_STHREADS / MLP_H) * u;
+        v1[u] = __ldg(reinterpret_cast<const float4*>(G.W1 + a * MLP_F) + fq);
+        v2[u] = __ldg(reinterpret_cast<const float4*>(G.W2 + a * MLP_H) + fq);  // (MLP_F == MLP_H)
     }
-    for (int e = threadIdx.x; e < MLP_H; e += blockDim.x) {
-        b1[e] = bf(G.b1[e]);
-        b2[e] = bf(G.b2[e]);
-    }
-    for (int e = threadIdx.x; e < MLP_O * MLP_H; e += blockDim.x) W3[e] = bf(G.W3[e]);
-    if (threadIdx.x < MLP_O) b3[threadIdx.x] = bf(G.b3[threadIdx.x]);
-    const int lane = threadIdx.x & 31;
-    const int rg = lane & 15, ug = (threadIdx.x >> 5) * 2 + (lane >> 4);  // rows 4 rg.., units 4 ug..
-    for (int64_t r0 = (int64_t)blockIdx.x * MLP_STILE; r0 < B; r0 += (int64_t)gridDim.x * MLP_STILE) {
-        const int rows = (int)(B - r0 < MLP_STILE ? B - r0 : MLP_STILE);
-        __syncthreads();  // staging done / the previous tile's readers done
-        if (threadIdx.x < MLP_STILE) {
-            const int r = threadIdx.x;
-            if (r < rows) {
-                const float* sq = scores + (r0 + r) * ld;
-                float mean = 0.f;
-                for (int i = 0; i < MLP_FEAT_K; ++i) mean += fmaxf(feat_dist(sq[i], spherical), 0.f);
-                mean = mean / MLP_FEAT_K + 1e-12f;
-                const float d1 = fmaxf(feat_dist(sq[0], spherical), 0.f) + 1e-12f;
-                for (int i = 0; i < MLP_FEAT_K; ++i) {
-                    const float di = fmaxf(feat_dist(sq[i], spherical), 0.f) + 1e-12f;
-                    XT[i * MLP_SLD + r] = bf(di / mean);
-                    XT[(MLP_FEAT_K + i) * MLP_SLD + r] = bf(d1 / di);
-                }
-            } else {
-                for (int f = 0; f < MLP_F; ++f) XT[f * MLP_SLD + r] = 0.f;  // rows past the batch
+    const int rg = threadIdx.x & 31, ug = threadIdx.x >> 5;
+    bool staged = false;
+    for (int64_t r0 = (int64_t)blockIdx.x * TILE; r0 < B; r0 += (int64_t)gridDim.x * TILE) {
+        const int rows = (int)(B - r0 < TILE ? B - r0 : TILE);
+        // the clamped distances u_i = max(dist_i, 0) of every row (XT's first
+        // FEAT_K rows), then per row the mean in ascending order by one thread
+        for (int e = threadIdx.x; e < TILE * MLP_FEAT_K; e += blockDim.x) {
+            const int r = e % TILE, i = e / TILE;
+            XT[i * XLD + r] = r < rows ? fmaxf(feat_dist(__ldg(scores + (r0 + r) * ld + i), spherical), 0.f) : 0.f;
+        }
+        if (!staged) {
+#pragma unroll
+            for (int u = 0; u < V; ++u) {
+                const int a = threadIdx.x & (MLP_H - 1), f = 4 * ((threadIdx.x >> 6) + (MLP_STHREADS / MLP_H) * u);
+                WT1[f * MLP_SLD + a] = bf(v1[u].x);
+                WT1[(f + 1) * MLP_SLD + a] = bf(v1[u].y);
+                WT1[(f + 2) * MLP_SLD + a] = bf(v1[u].z);
+                WT1[(f + 3) * MLP_SLD + a] = bf(v1[u].w);
+                WT2[f * MLP_SLD + a] = bf(v2[u].x);
+                WT2[(f + 1) * MLP_SLD + a] = bf(v2[u].y);
+                WT2[(f + 2) * MLP_SLD + a] = bf(v2[u].z);
+                WT2[(f + 3) * MLP_SLD + a] = bf(v2[u].w);
             }
+            if (threadIdx.x < MLP_H) {
+                b1[threadIdx.x] = bf(G.b1[threadIdx.x]);
+                b2[threadIdx.x] = bf(G.b2[threadIdx.x]);
+            }
+            if (threadIdx.x < MLP_O * MLP_H) W3[threadIdx.x] = bf(G.W3[threadIdx.x]);
+            if (threadIdx.x < MLP_O) b3[threadIdx.x] = bf(G.b3[threadIdx.x]);
+            staged = true;
         }
         __syncthreads();
-        dense_block(XT, WT1, b1, HT, rg, ug);
+        if (threadIdx.x < TILE) {
+            float mean = 0.f;
+#pragma unroll
+            for (int i = 0; i < MLP_FEAT_K; ++i) mean += XT[i * XLD + threadIdx.x];
+            s_mean[threadIdx.x] = mean / MLP_FEAT_K + 1e-12f;
+            s_d1[threadIdx.x] = XT[threadIdx.x] + 1e-12f;
+        }
         __syncthreads();
-        dense_block(HT, WT2, b2, XT, rg, ug);
+        // features: u_i / mean and d_1 / u_i (+ 1e-12 each), rounded to BF16;
+        // the second half first, since the first overwrites the u_i
+        for (int e = threadIdx.x; e < TILE * MLP_FEAT_K; e += blockDim.x) {
+            const int r = e % TILE, i = e / TILE;
+            const float di = XT[i * XLD + r] + 1e-12f;
+            const bool in = r < rows;
+            XT[(MLP_FEAT_K + i) * XLD + r] = in ? bf(s_d1[r] / di) : 0.f;
+            XT[i * XLD + r] = in ? bf(di / s_mean[r]) : 0.f;
+        }
         __syncthreads();
-        if (threadIdx.x < MLP_O * MLP_STILE) {
-            const int r = threadIdx.x & (MLP_STILE - 1), o = threadIdx.x / MLP_STILE;
+        dense_block<RPT>(XT, WT1, b1, HT, rg, ug);
+        __syncthreads();
+        dense_block<RPT>(HT, WT2, b2, XT, rg, ug);
+        __syncthreads();
+        if (threadIdx.x < MLP_O * TILE) {
+            const int r = threadIdx.x % TILE, o = threadIdx.x / TILE;
             if (r < rows) {
                 float z = b3[o];
-                for (int f = 0; f < MLP_H; ++f) z = fmaf(XT[f * MLP_SLD + r], W3[o * MLP_H + f], z);
+                for (int f = 0; f < MLP_H; ++f) z = fmaf(XT[f * XLD + r], W3[o * MLP_H + f], z);
                 const float p = 1.f / (1.f + expf(-z));
                 if (o == 0)
                     nprobe[r0 + r] = prm.regression ? regmap(p, prm.pmin, prm.pmax, prm.p0, prm.p1)
@@ -389,6 +426,7 @@ __global__ void __launch_bounds__(256) k_mlp_infer_scores(const float* __restric
                                                     : eq2(p, prm.rmin, prm.rmax, prm.r0, prm.r1);
             }
         }
+        __syncthreads();  // XT, s_mean and s_d1 are reused by the next tile
     }
 }
 
@@ -454,12 +492,20 @@ int mlp_infer(const float* w, const float* x, int64_t B, const ksc_adaptive_para
 int mlp_infer_scores(const float* w, const float* scores, int ld, int spherical, int64_t B,
                      const ksc_adaptive_params& prm, int32_t* nprobe, int32_t* rerank, cudaStream_t st) {
     if (B == 0) return KSC_OK;
-    KSC_CUDA(cudaFuncSetAttribute(k_mlp_infer_scores, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)mlp_scores_smem()));
-    const int64_t tiles = (B + MLP_STILE - 1) / MLP_STILE;
-    const int64_t grid = std::min<int64_t>(tiles, (int64_t)num_sms() * 2);
-    k_mlp_infer_scores<<<(unsigned)grid, 256, mlp_scores_smem(), st>>>(scores, ld, spherical, w, B, prm, nprobe,
-                                                                      rerank);
+    // tiles of 64 queries, or of 96 when that keeps to one CTA per SM
+    const int64_t sms = num_sms();
+    if ((B + 63) / 64 <= sms || (B + 95) / 96 > sms) {
+        KSC_CUDA(cudaFuncSetAttribute(k_mlp_infer_scores<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)mlp_scores_smem<2>()));
+        const int64_t grid = std::min<int64_t>((B + 63) / 64, sms * 2);
+        k_mlp_infer_scores<2><<<(unsigned)grid, MLP_STHREADS, mlp_scores_smem<2>(), st>>>(scores, ld, spherical, w,
+                                                                                          B, prm, nprobe, rerank);
+    } else {
+        KSC_CUDA(cudaFuncSetAttribute(k_mlp_infer_scores<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)mlp_scores_smem<3>()));
+        k_mlp_infer_scores<3><<<(unsigned)((B + 95) / 96), MLP_STHREADS, mlp_scores_smem<3>(), st>>>(
+            scores, ld, spherical, w, B, prm, nprobe, rerank);
+    }
     KSC_LAUNCH_CHECK();
     return KSC_OK;
 }

@@ -272,6 +272,92 @@ __device__ __forceinline__ void warp_bitonic_smem(uint64_t* s, int S, int lane) 
     }
 }
 
+__device__ __forceinline__ uint32_t warp_sort_u32(uint32_t v, int lane) {  // ascending, one value per lane
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const uint32_t o = __shfl_xor_sync(0xffffffffu, v, j);
+            v = (((lane & k) == 0) == ((lane & j) == 0)) ? min(o, v) : max(o, v);
+        }
+    }
+    return v;
+}
+
+// Ascending sort of a bitonic sequence of one value per lane.
+__device__ __forceinline__ uint32_t warp_merge_u32(uint32_t v, int lane) {
+#pragma unroll
+    for (int j = 16; j > 0; j >>= 1) {
+        const uint32_t o = __shfl_xor_sync(0xffffffffu, v, j);
+        v = (lane & j) == 0 ? min(o, v) : max(o, v);
+    }
+    return v;
+}
+
+// The K smallest of N values load(i) (order-preserving u32 images of the
+// scores, counted with multiplicity; 0 < K <= 48, K < N), ascending into
+// vals[0..K), by one warp.  Each lane keeps the two smallest values it reads
+// (i = lane, lane + 32, ...).  The K-th smallest t of those (at most) 64 is
+// at least the K-th smallest of all values (they are K of them; with N < 64
+// they are all of them), so the values at or below t hold the K smallest:
+// they are gathered and sorted.  Two passes over the values and a few warp
+// sorts, against the radix refinement's histogram passes.  Returns the number
+// gathered (>= K), or -1 if more than 64 (the caller then selects by radix
+// refinement; at K 48 of 1024 random scores about 65 values fall at or below
+// t).  vals: 64 words of the warp's own shared memory.  All 32 lanes call.
+template <class Load>
+__device__ int warp_small_kvals(Load load, int N, int K, uint32_t* vals) {
+    const int lane = threadIdx.x & 31;
+    uint32_t a = 0xffffffffu, b = 0xffffffffu;  // a <= b: the two smallest values of this lane
+    for (int i0 = 0; i0 < N; i0 += 32 * TOPK_U) {
+        uint32_t x[TOPK_U];
+#pragma unroll
+        for (int u = 0; u < TOPK_U; ++u) {
+            const int i = i0 + 32 * u + lane;
+            x[u] = i < N ? load(i) : 0xffffffffu;
+        }
+#pragma unroll
+        for (int u = 0; u < TOPK_U; ++u) {
+            b = min(b, max(a, x[u]));
+            a = min(a, x[u]);
+        }
+    }
+    // both sets sorted across the warp; against the reversed second, the
+    // element-wise minima are the 32 smallest of the 64 and the maxima the
+    // 32 largest, each a bitonic sequence
+    const uint32_t A = warp_sort_u32(a, lane), B = warp_sort_u32(b, lane);
+    const uint32_t Br = __shfl_sync(0xffffffffu, B, 31 - lane);
+    const uint32_t v = warp_merge_u32(K <= 32 ? min(A, Br) : max(A, Br), lane);
+    const uint32_t t = __shfl_sync(0xffffffffu, v, (K - 1) & 31);
+    const uint32_t below = (1u << lane) - 1u;
+    int n = 0;
+    for (int i0 = 0; i0 < N; i0 += 32) {
+        const int i = i0 + lane;
+        const uint32_t x = i < N ? load(i) : 0xffffffffu;
+        const bool in = i < N && x <= t;
+        const uint32_t m = __ballot_sync(0xffffffffu, in);
+        const int at = n + __popc(m & below);
+        if (in && at < 64) vals[at] = x;
+        n += __popc(m);
+    }
+    if (n > 64) return -1;
+    __syncwarp();
+    const uint32_t c0 = lane < n ? vals[lane] : 0xffffffffu, c1 = lane + 32 < n ? vals[lane + 32] : 0xffffffffu;
+    const uint32_t S0 = warp_sort_u32(c0, lane);
+    if (n <= 32) {
+        __syncwarp();
+        vals[lane] = S0;
+    } else {
+        const uint32_t S1r = __shfl_sync(0xffffffffu, warp_sort_u32(c1, lane), 31 - lane);
+        const uint32_t lo = warp_merge_u32(min(S0, S1r), lane), hi = warp_merge_u32(max(S0, S1r), lane);
+        __syncwarp();
+        vals[lane] = lo;
+        vals[lane + 32] = hi;
+    }
+    __syncwarp();
+    return n;
+}
+
 // One warp per query (RSW_WARPS per CTA) for L <= RSW_MAX_L: the row of given
 // scores is staged in the warp's shared memory and the P-th smallest given
 // score s_P found by radix refinement over (score, list) keys.  Every list of
@@ -293,7 +379,8 @@ __global__ void __launch_bounds__(RSW_WARPS * 32) k_rank_select_w(const float* _
                                                                   int Pmax, int32_t* __restrict__ probes,
                                                                   float* __restrict__ score_out,
                                                                   int32_t* __restrict__ redo,
-                                                                  float* __restrict__ feat) {
+                                                                  float* __restrict__ feat,
+                                                                  const uint32_t* __restrict__ given) {
     extern __shared__ uint64_t rsm[];  // RSW_WARPS x RSW_CAND keys, then RSW_WARPS x L scores
     __shared__ uint32_t hist[RSW_WARPS][256];
     __shared__ uint64_t bb[RSW_WARPS][32];
@@ -309,30 +396,48 @@ __global__ void __launch_bounds__(RSW_WARPS * 32) k_rank_select_w(const float* _
     __syncwarp();
     float tau = INFINITY;
     auto load = [&](int c) -> uint64_t { return ((uint64_t)ordered_f32(ss[c]) << 32) | (uint32_t)c; };
+    auto load32 = [&](int c) -> uint32_t { return ordered_f32(ss[c]); };
+    uint32_t* kv = reinterpret_cast<uint32_t*>(ck);  // the small selection's values (ck's first 64 words)
     if (feat) {
         // the K = max(P, FEAT_K) smallest given scores, sorted: the predictor's
         // distances (+ ||q||^2 for L2, which the score leaves out) and s_P
         const int K = min(max(P, FEAT_K), L);
-        auto emit = [&](int i, uint64_t k) { ck[i] = k; };
-        if (K < L) warp_topk(load, L, K, emit, hist[w], bb[w]);
-        else for (int c = lane; c < L; c += 32) ck[c] = load(c);
-        const int S = pow2_ceil(K);
-        for (int i = K + lane; i < S; i += 32) ck[i] = KEY_NONE;
-        __syncwarp();
-        warp_bitonic_smem(ck, S, lane);
+        uint32_t fv, sP = 0u;  // this lane's distance, the P-th smallest (ordered images)
+        if (K < L && K <= 48 && warp_small_kvals(load32, L, K, kv) >= 0) {
+            fv = kv[lane];
+            if (P < L) sP = kv[P - 1];
+        } else {
+            auto emit = [&](int i, uint64_t k) { ck[i] = k; };
+            if (K < L) warp_topk(load, L, K, emit, hist[w], bb[w]);
+            else for (int c = lane; c < L; c += 32) ck[c] = load(c);
+            const int S = pow2_ceil(K);
+            for (int i = K + lane; i < S; i += 32) ck[i] = KEY_NONE;
+            __syncwarp();
+            warp_bitonic_smem(ck, S, lane);
+            fv = (uint32_t)(ck[lane] >> 32);
+            if (P < L) sP = (uint32_t)(ck[P - 1] >> 32);
+        }
         float qq = 0.f;
         if (!spherical) {
             for (int t = lane; t < d; t += 32) qq = fmaf(Q[q * d + t], Q[q * d + t], qq);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) qq += __shfl_xor_sync(0xffffffffu, qq, o);
         }
-        feat[q * FEAT_K + lane] = unordered_f32((uint32_t)(ck[lane] >> 32)) + qq;
-        if (P < L) tau = unordered_f32((uint32_t)(ck[P - 1] >> 32)) + (err ? 2.f * err[q] : 0.f);
+        feat[q * FEAT_K + lane] = unordered_f32(fv) + qq;
+        if (P < L) tau = unordered_f32(sP) + (err ? 2.f * err[q] : 0.f);
         __syncwarp();
     } else if (P < L) {
-        auto none = [](int, uint64_t) {};
-        const uint64_t kP = warp_topk(load, L, P, none, hist[w], bb[w]);
-        tau = unordered_f32((uint32_t)(kP >> 32)) + (err ? 2.f * err[q] : 0.f);
+        uint32_t sP;
+        if (given && P <= FEAT_K) {
+            sP = given[q * FEAT_K + P - 1];  // the P-th smallest score, from the feature pass
+        } else if (P <= 48 && warp_small_kvals(load32, L, P, kv) >= 0) {
+            sP = kv[P - 1];
+            __syncwarp();  // ck is reused for the lists below
+        } else {
+            auto none = [](int, uint64_t) {};
+            sP = (uint32_t)(warp_topk(load, L, P, none, hist[w], bb[w]) >> 32);
+        }
+        tau = unordered_f32(sP) + (err ? 2.f * err[q] : 0.f);
     }
     // the lists that can still be among the P best
     const uint32_t below = (1u << lane) - 1u;
@@ -441,29 +546,39 @@ __global__ void __launch_bounds__(RSW_WARPS * 32) k_rank_select_w(const float* _
 // scores, ascending, from the given score matrix (the tensor-core scores,
 // within their bound of the exact ones); for L2 the query's squared norm,
 // which the ranking score leaves out, is added back.  One warp per query.
+// vals_out (optional) receives the FEAT_K sorted scores' order-preserving
+// u32 images.
 __global__ void __launch_bounds__(256) k_feat_scores(const float* __restrict__ scores, const float* __restrict__ Q,
                                                      int d, int spherical, int64_t nq, int L,
-                                                     float* __restrict__ out) {
+                                                     float* __restrict__ out, uint32_t* __restrict__ vals_out) {
     __shared__ uint32_t hist[8][256];
     __shared__ uint64_t bb[8][32];
     __shared__ uint64_t kk[8][FEAT_K];
+    __shared__ uint32_t kv[8][64];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t q = (int64_t)blockIdx.x * 8 + w;
     if (q >= nq) return;
     const float* row = scores + q * L;
     auto load = [&](int c) -> uint64_t { return ((uint64_t)ordered_f32(row[c]) << 32) | (uint32_t)c; };
+    auto load32 = [&](int c) -> uint32_t { return ordered_f32(row[c]); };
     auto emit = [&](int i, uint64_t k) { kk[w][i] = k; };
-    if (L > FEAT_K) warp_topk(load, L, FEAT_K, emit, hist[w], bb[w]);
-    else kk[w][lane] = load(lane);  // L == FEAT_K (the predictor needs 32 lists)
+    uint32_t v;  // this lane's distance (ordered image) in ascending order
+    if (L > FEAT_K && warp_small_kvals(load32, L, FEAT_K, kv[w]) >= 0) {
+        v = kv[w][lane];
+    } else {
+        if (L > FEAT_K) warp_topk(load, L, FEAT_K, emit, hist[w], bb[w]);
+        else kk[w][lane] = load(lane);  // L == FEAT_K (the predictor needs 32 lists)
+        __syncwarp();
+        v = (uint32_t)(warp_sort_key(kk[w][lane], lane) >> 32);
+    }
     float qq = 0.f;
     if (!spherical) {
         for (int t = lane; t < d; t += 32) qq = fmaf(Q[q * d + t], Q[q * d + t], qq);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) qq += __shfl_xor_sync(0xffffffffu, qq, o);
     }
-    __syncwarp();
-    const uint64_t v = warp_sort_key(kk[w][lane], lane);
-    out[q * FEAT_K + lane] = unordered_f32((uint32_t)(v >> 32)) + qq;
+    out[q * FEAT_K + lane] = unordered_f32(v) + qq;
+    if (vals_out) vals_out[q * FEAT_K + lane] = v;
 }
 
 // ------------------------------------------------------------------ a2: quantised LUTs
@@ -716,9 +831,10 @@ __global__ void __launch_bounds__(256) k_lut_fused(LutArgs A, int Pb, int Pm, ui
     stage_codebook(A, cbs);  // ends with __syncthreads
     for (int buf = 0; q < A.nq; q += gridDim.x, buf ^= 1) {
         const float* qs = qsb + buf * dpad;
-        // a query with more than Pb probes recomputes its tables instead of storing them
+        // the tables of the first Pb probes are kept for the quantisation
+        // pass; those of later probes (a query with more) are computed again
         const int P = min(probes_of(A, q), Pm);
-        const bool stored = P <= Pb;
+        const int nstored = Pb * M;
         const int32_t* pr = A.probes + q * A.Pmax;
         float R = 0.f;
         {
@@ -726,6 +842,7 @@ __global__ void __launch_bounds__(256) k_lut_fused(LutArgs A, int Pb, int Pm, ui
             for (int row = threadIdx.x; row < P * M; row += blockDim.x) {
                 const int p = pr[r];
                 float* Tr = T + (size_t)row * LUT_TROW;
+                const bool stored = row < nstored;
                 if (p < 0 || p >= A.L) {
                     if (stored)
 #pragma unroll
@@ -775,7 +892,7 @@ __global__ void __launch_bounds__(256) k_lut_fused(LutArgs A, int Pb, int Pm, ui
                 const float mn = mins[row];
                 float Tv[PQ_K];
                 bool ok = true;
-                if (stored) {
+                if (row < nstored) {
                     const float* Tr = T + (size_t)row * LUT_TROW;
 #pragma unroll
                     for (int i = 0; i < PQ_K; i += 4) {
@@ -2534,18 +2651,38 @@ static int list_scores(ksc_index* ix, const float* Q, int64_t nq, int mode, floa
 
 // The Pmax best lists of every query (exact ranking); feat (optional, L >=
 // FEAT_K) receives each query's FEAT_K smallest given list distances.
+// The warp kernel ranks a batch when its lists fit a warp's share of shared
+// memory and the batch fills the GPU.
+static bool rank_by_warp(const ksc_index* ix, int64_t nq, int Pmax) {
+    return ix->L <= RSW_MAX_L && Pmax <= 4 * RSW_CAND / 8 && warp_per_query(nq);
+}
+
+// The P best lists of every query from the given approximate scores (an
+// error bound per query in err), exactly re-scored; feat: the predictor's
+// distances as well; given: the FEAT_K sorted score images of k_feat_scores, from
+// which the warp kernel reads the P-th smallest instead of selecting it.
+static int select_lists(ksc_index* ix, const float* scores, const float* err, const float* Q, int64_t nq,
+                        const int32_t* nprobe_q, int Pfix, int Pmax, int32_t* probes, float* score_out,
+                        cudaStream_t st, float* feat, const uint32_t* given);
+
 static int rank_lists(ksc_index* ix, const float* Q, int64_t nq, const int32_t* nprobe_q, int Pfix, int Pmax,
                       int32_t* probes, float* score_out, int mode, cudaStream_t st, float* feat = nullptr) {
     KSC_TRY(ensure(ix->ws_scores, sizeof(float) * nq * ix->L, st));
     float* scores = (float*)ix->ws_scores.p;
     float* err = nullptr;
     KSC_TRY(list_scores(ix, Q, nq, mode, scores, &err, st));
+    return select_lists(ix, scores, err, Q, nq, nprobe_q, Pfix, Pmax, probes, score_out, st, feat, nullptr);
+}
+
+static int select_lists(ksc_index* ix, const float* scores, const float* err, const float* Q, int64_t nq,
+                        const int32_t* nprobe_q, int Pfix, int Pmax, int32_t* probes, float* score_out,
+                        cudaStream_t st, float* feat, const uint32_t* given) {
     // re-score buffer of the CTA kernel: 4 Pmax lists (a power of two, at least 1024, at most RS_CAP)
     const int rs_cap = std::min(RS_CAP, std::max(1024, pow2_ceil(4 * Pmax)));
     const size_t smem = rs_cap * sizeof(uint64_t) + (ix->L <= RS_SMEM_L ? sizeof(float) * ix->L : 0);
     KSC_CUDA(cudaFuncSetAttribute(k_rank_select<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     KSC_CUDA(cudaFuncSetAttribute(k_rank_select<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    if (ix->L <= RSW_MAX_L && Pmax <= 4 * RSW_CAND / 8 && warp_per_query(nq)) {
+    if (rank_by_warp(ix, nq, Pmax)) {
         // a warp per query; queries with too many lists inside the bound go to the CTA kernel
         KSC_TRY(ensure(ix->ws_redo, sizeof(int32_t) * (nq + 1), st));
         int32_t* redo = (int32_t*)ix->ws_redo.p;
@@ -2554,7 +2691,7 @@ static int rank_lists(ksc_index* ix, const float* Q, int64_t nq, const int32_t* 
         KSC_CUDA(cudaFuncSetAttribute(k_rank_select_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm));
         k_rank_select_w<<<(unsigned)((nq + RSW_WARPS - 1) / RSW_WARPS), RSW_WARPS * 32, wsm, st>>>(
             scores, err, Q, ix->c_rank, nq, ix->d, ix->L, ix->spherical, nprobe_q, Pfix, Pmax, probes, score_out,
-            redo, feat);
+            redo, feat, given);
         feat = nullptr;  // written
         KSC_LAUNCH_CHECK();
         k_rank_select<256><<<num_sms() * 2, 256, smem, st>>>(scores, err, Q, ix->c_rank, nq, ix->d, ix->L, ix->spherical,
@@ -2574,7 +2711,8 @@ static int rank_lists(ksc_index* ix, const float* Q, int64_t nq, const int32_t* 
     }
     KSC_LAUNCH_CHECK();
     if (feat) {
-        k_feat_scores<<<(unsigned)((nq + 7) / 8), 256, 0, st>>>(scores, Q, ix->d, ix->spherical, nq, ix->L, feat);
+        k_feat_scores<<<(unsigned)((nq + 7) / 8), 256, 0, st>>>(scores, Q, ix->d, ix->spherical, nq, ix->L, feat,
+                                                                nullptr);
         KSC_LAUNCH_CHECK();
         ix->launches++;
     }
@@ -3316,6 +3454,36 @@ static int rank_and_features(ksc_index* ix, const float* Q, int64_t nq, int P, i
     return KSC_OK;
 }
 
+// The adaptive search's ranking (Sec. 4.2.1).  The predictor's distances
+// are the FEAT_K smallest approximate list scores; the network sets each
+// query's nprobe and R from them (features, network and Eq. 2 in one
+// kernel); only then are the nprobe best lists of each query ranked exactly,
+// the threshold of the exact pass taken from the same sorted scores.  The
+// probes equal the first nprobe of an exact ranking of Pr lists (an exact
+// top-P is a prefix of the exact top-Pr); rows past nprobe hold -1.
+static int rank_adaptive(ksc_index* ix, const float* Q, int64_t nq, int Pr, int32_t* probes,
+                         const ksc_adaptive_params& prm, int32_t* np_q, int32_t* r_q, cudaStream_t st) {
+    KSC_TRY(ensure(ix->ws_rscore, sizeof(float) * nq * FEAT_K, st));
+    float* rs = (float*)ix->ws_rscore.p;
+    if (!rank_by_warp(ix, nq, Pr) || ix->L < FEAT_K) {
+        KSC_TRY(rank_lists(ix, Q, nq, nullptr, Pr, Pr, probes, nullptr, RANK_TC16, st, rs));
+        KSC_TRY(mlp_infer_scores(ix->mlp_w, rs, FEAT_K, ix->spherical, nq, prm, np_q, r_q, st));
+        ix->launches++;
+        return KSC_OK;
+    }
+    KSC_TRY(ensure(ix->ws_scores, sizeof(float) * nq * ix->L, st));
+    KSC_TRY(ensure(ix->ws_fkeys, sizeof(uint32_t) * nq * FEAT_K, st));
+    float* scores = (float*)ix->ws_scores.p;
+    uint32_t* fkeys = (uint32_t*)ix->ws_fkeys.p;
+    float* err = nullptr;
+    KSC_TRY(list_scores(ix, Q, nq, RANK_TC16, scores, &err, st));
+    k_feat_scores<<<(unsigned)((nq + 7) / 8), 256, 0, st>>>(scores, Q, ix->d, ix->spherical, nq, ix->L, rs, fkeys);
+    KSC_LAUNCH_CHECK();
+    KSC_TRY(mlp_infer_scores(ix->mlp_w, rs, FEAT_K, ix->spherical, nq, prm, np_q, r_q, st));
+    ix->launches += 2;
+    return select_lists(ix, scores, err, Q, nq, np_q, Pr, Pr, probes, nullptr, st, nullptr, fkeys);
+}
+
 static uint64_t mix64(uint64_t& s) {  // splitmix64 (Steele, Lea, Flood 2014)
     uint64_t z = (s += 0x9E3779B97F4A7C15ull);
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -3605,13 +3773,7 @@ int ksc_search_adaptive(ksc_index* ix, const float* Q_dev, int64_t nq, int32_t k
     mark(ix, 0, st);
     const float* Qw;
     KSC_TRY(work_queries(ix, Q_dev, nq, st, &Qw));
-    // ranking of the lists a query may probe, its FEAT_K smallest distances,
-    // then features + network + Eq. 2 in one kernel
-    KSC_TRY(ensure(ix->ws_rscore, sizeof(float) * nq * FEAT_K, st));
-    float* rs = (float*)ix->ws_rscore.p;
-    KSC_TRY(rank_lists(ix, Qw, nq, nullptr, Pr, Pr, probes, nullptr, RANK_TC16, st, rs));
-    KSC_TRY(mlp_infer_scores(ix->mlp_w, rs, FEAT_K, ix->spherical, nq, prm, np_q, r_q, st));
-    ix->launches++;
+    KSC_TRY(rank_adaptive(ix, Qw, nq, Pr, probes, prm, np_q, r_q, st));
     pl.nprobe_q = np_q;
     pl.rerank_q = r_q;
     pl.Pq_max = std::min(prm.pmax, Pr);
