@@ -324,8 +324,7 @@ static int workspace_buffers(ksc_index* ix, Buffer** out) {
     Buffer* bufs[] = {&ix->ws_scores, &ix->ws_probes, &ix->ws_lut, &ix->ws_bias, &ix->ws_scale, &ix->ws_range,
                       &ix->ws_thr, &ix->ws_cnt, &ix->ws_cand, &ix->ws_topr, &ix->ws_nprobe, &ix->ws_rerank,
                       &ix->ws_items, &ix->ws_misc, &ix->ws_qbf16, &ix->ws_err, &ix->ws_feat, &ix->ws_rscore,
-                      &ix->ws_full, &ix->ws_topr2, &ix->ws_redo, &ix->ws_pprobes, &ix->ws_pn, &ix->ws_pprob, &ix->ws_qf,
-                      &ix->ws_fkeys};
+                      &ix->ws_full, &ix->ws_topr2, &ix->ws_redo, &ix->ws_pprobes, &ix->ws_pn, &ix->ws_pprob, &ix->ws_qf};
     const int n = (int)(sizeof(bufs) / sizeof(bufs[0]));
     for (int i = 0; i < n; ++i) out[i] = bufs[i];
     return n;

@@ -82,7 +82,7 @@ struct ksc_index {
     // search workspace
     ksc::Buffer ws_scores, ws_probes, ws_lut, ws_bias, ws_scale, ws_range, ws_thr, ws_cnt,
         ws_cand, ws_topr, ws_nprobe, ws_rerank, ws_items, ws_misc, ws_qbf16, ws_err, ws_feat, ws_rscore, ws_full, ws_topr2,
-        ws_redo, ws_pprobes, ws_pn, ws_pprob, ws_qf, ws_fkeys;
+        ws_redo, ws_pprobes, ws_pn, ws_pprob, ws_qf;
 };
 
 // The vectors the exact re-rank reads and their width: the full vectors when

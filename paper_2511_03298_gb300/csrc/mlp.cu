@@ -15,38 +15,14 @@
 #include <vector>
 
 #include "index.cuh"
+#include "mlp.cuh"
 
 namespace ksc {
 
-constexpr int MLP_F = 64, MLP_H = 64, MLP_O = 2, MLP_FEAT_K = 32;
-constexpr int MLP_NPARAM = MLP_H * MLP_F + MLP_H + MLP_H * MLP_H + MLP_H + MLP_O * MLP_H + MLP_O;
 constexpr int MLP_TILE = 128;  // samples per CTA (training)
 constexpr int MLP_ITILE = 32;  // queries per tile of the inference kernel (one warp's rows)
 
-struct MlpW {  // views into a packed parameter vector (same packing as the oracle)
-    const float *W1, *b1, *W2, *b2, *W3, *b3;
-};
-// Network F -> H -> H -> 2: parameter count and views.
-template <int F, int H>
-constexpr int mlp_nparam() {
-    return H * F + H + H * H + H + MLP_O * H + MLP_O;
-}
-template <int F, int H>
-__host__ __device__ inline MlpW mlp_views_t(const float* w) {
-    MlpW v;
-    v.W1 = w;
-    v.b1 = v.W1 + H * F;
-    v.W2 = v.b1 + H;
-    v.b2 = v.W2 + H * H;
-    v.W3 = v.b2 + H;
-    v.b3 = v.W3 + MLP_O * H;
-    return v;
-}
-__host__ __device__ inline MlpW mlp_views(const float* w) { return mlp_views_t<MLP_F, MLP_H>(w); }
-
 // Features of one query from its sorted ranking scores s[0..32).
-__device__ __forceinline__ float feat_dist(float s, int spherical) { return spherical ? 1.f + s : s; }
-
 __global__ void k_features(const float* __restrict__ scores, int64_t nq, int ld, int spherical,
                            float* __restrict__ feats) {
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -195,27 +171,6 @@ __global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float
     m[i] = mi;
     v[i] = vi;
     w[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
-}
-
-__device__ __forceinline__ float bf(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
-
-// Eq. 2 with the line-broken product read literally:
-// P = min(Pmax, Pmin + ceil((Pmax - Pmin) * max(0, p - p0) * (p + p1))).
-__host__ __device__ inline int eq2(float p, int pmin, int pmax, float p0, float p1) {
-    const float relu = p - p0 > 0.f ? p - p0 : 0.f;
-    const float v = ceilf((float)(pmax - pmin) * relu * (p + p1));
-    const float r = (float)pmin + v;
-    return r > (float)pmax ? pmax : (r < (float)pmin ? pmin : (int)r);
-}
-
-// Regression heads: p is the normalised log of the setting,
-// u = clamp(p (1 + b) + a, 0, 1), P = clamp(ceil(lo (hi / lo)^u - 1e-3), lo, hi)
-// (a value within 1e-3 above an integer counts as that integer).
-__device__ inline int regmap(float p, int lo, int hi, float a, float b) {
-    const float u = fminf(fmaxf(p * (1.f + b) + a, 0.f), 1.f);
-    const float v = (float)lo * powf((float)hi / (float)lo, u);
-    const float r = ceilf(v - 1e-3f);
-    return r > (float)hi ? hi : (r < (float)lo ? lo : (int)r);
 }
 
 // One layer for a tile of rows: thread e computes unit a = e / rows of row

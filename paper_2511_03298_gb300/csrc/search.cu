@@ -19,6 +19,7 @@
 #include <cuda_fp8.h>
 
 #include "index.cuh"
+#include "mlp.cuh"
 #include "scan.cuh"
 
 namespace ksc {
@@ -370,76 +371,35 @@ constexpr int RSW_WARPS = 4;
 constexpr int RSW_MAX_L = 2048;
 constexpr int RSW_CAND = 128;
 
-__global__ void __launch_bounds__(RSW_WARPS * 32) k_rank_select_w(const float* __restrict__ scores,
-                                                                  const float* __restrict__ err,
-                                                                  const float* __restrict__ Q,
-                                                                  const float* __restrict__ Cc, int64_t nq, int d,
-                                                                  int L, int spherical,
-                                                                  const int32_t* __restrict__ nprobe_q, int Pfix,
-                                                                  int Pmax, int32_t* __restrict__ probes,
-                                                                  float* __restrict__ score_out,
-                                                                  int32_t* __restrict__ redo,
-                                                                  float* __restrict__ feat,
-                                                                  const uint32_t* __restrict__ given) {
-    extern __shared__ uint64_t rsm[];  // RSW_WARPS x RSW_CAND keys, then RSW_WARPS x L scores
-    __shared__ uint32_t hist[RSW_WARPS][256];
-    __shared__ uint64_t bb[RSW_WARPS][32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t q = (int64_t)blockIdx.x * RSW_WARPS + w;
-    if (q >= nq) return;
-    uint64_t* ck = rsm + w * RSW_CAND;
-    float* ss = reinterpret_cast<float*>(rsm + RSW_WARPS * RSW_CAND) + (size_t)w * L;
-    int P = nprobe_q ? nprobe_q[q] : Pfix;
-    P = P < 1 ? 1 : (P > Pmax ? Pmax : P);
-    const float* row = scores + q * L;
-    for (int c = lane; c < L; c += 32) ss[c] = row[c];
-    __syncwarp();
-    float tau = INFINITY;
-    auto load = [&](int c) -> uint64_t { return ((uint64_t)ordered_f32(ss[c]) << 32) | (uint32_t)c; };
-    auto load32 = [&](int c) -> uint32_t { return ordered_f32(ss[c]); };
-    uint32_t* kv = reinterpret_cast<uint32_t*>(ck);  // the small selection's values (ck's first 64 words)
-    if (feat) {
-        // the K = max(P, FEAT_K) smallest given scores, sorted: the predictor's
-        // distances (+ ||q||^2 for L2, which the score leaves out) and s_P
-        const int K = min(max(P, FEAT_K), L);
-        uint32_t fv, sP = 0u;  // this lane's distance, the P-th smallest (ordered images)
-        if (K < L && K <= 48 && warp_small_kvals(load32, L, K, kv) >= 0) {
-            fv = kv[lane];
-            if (P < L) sP = kv[P - 1];
-        } else {
-            auto emit = [&](int i, uint64_t k) { ck[i] = k; };
-            if (K < L) warp_topk(load, L, K, emit, hist[w], bb[w]);
-            else for (int c = lane; c < L; c += 32) ck[c] = load(c);
-            const int S = pow2_ceil(K);
-            for (int i = K + lane; i < S; i += 32) ck[i] = KEY_NONE;
-            __syncwarp();
-            warp_bitonic_smem(ck, S, lane);
-            fv = (uint32_t)(ck[lane] >> 32);
-            if (P < L) sP = (uint32_t)(ck[P - 1] >> 32);
-        }
-        float qq = 0.f;
-        if (!spherical) {
-            for (int t = lane; t < d; t += 32) qq = fmaf(Q[q * d + t], Q[q * d + t], qq);
+// A row of L scores into the warp's shared memory ss, with up to 8 16-byte
+// loads per lane in flight (ss 16-byte aligned).
+__device__ __forceinline__ void stage_row(const float* __restrict__ row, float* ss, int L, int lane) {
+    if ((L & 3) == 0 && (reinterpret_cast<uintptr_t>(row) & 15) == 0) {
+        const float4* r4 = reinterpret_cast<const float4*>(row);
+        float4* s4 = reinterpret_cast<float4*>(ss);
+        const int L4 = L >> 2;
+        for (int c0 = 0; c0 < L4; c0 += 32 * 8) {
+            float4 v[8];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) qq += __shfl_xor_sync(0xffffffffu, qq, o);
+            for (int u = 0; u < 8; ++u) {
+                const int c = c0 + 32 * u + lane;
+                v[u] = c < L4 ? __ldg(r4 + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int c = c0 + 32 * u + lane;
+                if (c < L4) s4[c] = v[u];
+            }
         }
-        feat[q * FEAT_K + lane] = unordered_f32(fv) + qq;
-        if (P < L) tau = unordered_f32(sP) + (err ? 2.f * err[q] : 0.f);
-        __syncwarp();
-    } else if (P < L) {
-        uint32_t sP;
-        if (given && P <= FEAT_K) {
-            sP = given[q * FEAT_K + P - 1];  // the P-th smallest score, from the feature pass
-        } else if (P <= 48 && warp_small_kvals(load32, L, P, kv) >= 0) {
-            sP = kv[P - 1];
-            __syncwarp();  // ck is reused for the lists below
-        } else {
-            auto none = [](int, uint64_t) {};
-            sP = (uint32_t)(warp_topk(load, L, P, none, hist[w], bb[w]) >> 32);
-        }
-        tau = unordered_f32(sP) + (err ? 2.f * err[q] : 0.f);
+    } else {
+        for (int c = lane; c < L; c += 32) ss[c] = row[c];
     }
-    // the lists that can still be among the P best
+    __syncwarp();
+}
+
+// The lists of given score <= tau (staged in ss) into ck, ascending; returns
+// their number (only the first RSW_CAND are stored).  One warp.
+__device__ __forceinline__ int collect_lists(const float* ss, int L, float tau, uint64_t* ck, int lane) {
     const uint32_t below = (1u << lane) - 1u;
     int n = 0;
     for (int c0 = 0; c0 < L; c0 += 32) {
@@ -450,10 +410,15 @@ __global__ void __launch_bounds__(RSW_WARPS * 32) k_rank_select_w(const float* _
         if (in && at < RSW_CAND) ck[at] = (uint64_t)(uint32_t)c;
         n += __popc(m);
     }
-    if (n > RSW_CAND) {
-        if (lane == 0) redo[1 + atomicAdd(&redo[0], 1)] = (int32_t)q;
-        return;
-    }
+    return n;
+}
+
+// The n (<= RSW_CAND) lists in ck re-scored exactly in FP32 (8 at a time, as
+// in the re-rank), sorted by (score, id); the P best into row q of probes
+// (and score_out), -1 (+inf) past them up to Pmax.  One warp.
+__device__ void exact_top_p(int64_t q, int n, int P, int Pmax, uint64_t* ck, const float* __restrict__ Q,
+                            const float* __restrict__ Cc, int d, int spherical, int32_t* __restrict__ probes,
+                            float* __restrict__ score_out, int lane) {
     __syncwarp();
     // exact FP32 scores, 8 lists at a time
     const float* qv = Q + q * d;
@@ -542,15 +507,256 @@ __global__ void __launch_bounds__(RSW_WARPS * 32) k_rank_select_w(const float* _
     }
 }
 
+
+__global__ void __launch_bounds__(RSW_WARPS * 32) k_rank_select_w(const float* __restrict__ scores,
+                                                                  const float* __restrict__ err,
+                                                                  const float* __restrict__ Q,
+                                                                  const float* __restrict__ Cc, int64_t nq, int d,
+                                                                  int L, int spherical,
+                                                                  const int32_t* __restrict__ nprobe_q, int Pfix,
+                                                                  int Pmax, int32_t* __restrict__ probes,
+                                                                  float* __restrict__ score_out,
+                                                                  int32_t* __restrict__ redo,
+                                                                  float* __restrict__ feat) {
+    extern __shared__ uint64_t rsm[];  // RSW_WARPS x RSW_CAND keys, then RSW_WARPS x L scores
+    __shared__ uint32_t hist[RSW_WARPS][256];
+    __shared__ uint64_t bb[RSW_WARPS][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t q = (int64_t)blockIdx.x * RSW_WARPS + w;
+    if (q >= nq) return;
+    uint64_t* ck = rsm + w * RSW_CAND;
+    float* ss = reinterpret_cast<float*>(rsm + RSW_WARPS * RSW_CAND) + (size_t)w * L;
+    int P = nprobe_q ? nprobe_q[q] : Pfix;
+    P = P < 1 ? 1 : (P > Pmax ? Pmax : P);
+    stage_row(scores + q * L, ss, L, lane);
+    float tau = INFINITY;
+    auto load = [&](int c) -> uint64_t { return ((uint64_t)ordered_f32(ss[c]) << 32) | (uint32_t)c; };
+    auto load32 = [&](int c) -> uint32_t { return ordered_f32(ss[c]); };
+    uint32_t* kv = reinterpret_cast<uint32_t*>(ck);  // the small selection's values (ck's first 64 words)
+    if (feat) {
+        // the K = max(P, FEAT_K) smallest given scores, sorted: the predictor's
+        // distances (+ ||q||^2 for L2, which the score leaves out) and s_P
+        const int K = min(max(P, FEAT_K), L);
+        uint32_t fv, sP = 0u;  // this lane's distance, the P-th smallest (ordered images)
+        if (K < L && K <= 48 && warp_small_kvals(load32, L, K, kv) >= 0) {
+            fv = kv[lane];
+            if (P < L) sP = kv[P - 1];
+        } else {
+            auto emit = [&](int i, uint64_t k) { ck[i] = k; };
+            if (K < L) warp_topk(load, L, K, emit, hist[w], bb[w]);
+            else for (int c = lane; c < L; c += 32) ck[c] = load(c);
+            const int S = pow2_ceil(K);
+            for (int i = K + lane; i < S; i += 32) ck[i] = KEY_NONE;
+            __syncwarp();
+            warp_bitonic_smem(ck, S, lane);
+            fv = (uint32_t)(ck[lane] >> 32);
+            if (P < L) sP = (uint32_t)(ck[P - 1] >> 32);
+        }
+        float qq = 0.f;
+        if (!spherical) {
+            for (int t = lane; t < d; t += 32) qq = fmaf(Q[q * d + t], Q[q * d + t], qq);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) qq += __shfl_xor_sync(0xffffffffu, qq, o);
+        }
+        feat[q * FEAT_K + lane] = unordered_f32(fv) + qq;
+        if (P < L) tau = unordered_f32(sP) + (err ? 2.f * err[q] : 0.f);
+        __syncwarp();
+    } else if (P < L) {
+        uint32_t sP;
+        if (P <= 48 && warp_small_kvals(load32, L, P, kv) >= 0) {
+            sP = kv[P - 1];
+            __syncwarp();  // ck is reused for the lists below
+        } else {
+            auto none = [](int, uint64_t) {};
+            sP = (uint32_t)(warp_topk(load, L, P, none, hist[w], bb[w]) >> 32);
+        }
+        tau = unordered_f32(sP) + (err ? 2.f * err[q] : 0.f);
+    }
+    // the lists that can still be among the P best
+    const int n = collect_lists(ss, L, tau, ck, lane);
+    if (n > RSW_CAND) {
+        if (lane == 0) redo[1 + atomicAdd(&redo[0], 1)] = (int32_t)q;
+        return;
+    }
+    exact_top_p(q, n, P, Pmax, ck, Q, Cc, d, spherical, probes, score_out, lane);
+}
+
+// The adaptive search's ranking in one kernel (Sec. 4.2.1-4.2.2, Eq. 2), a
+// warp per query, persistent CTAs of RH_WARPS warps: the FEAT_K smallest
+// given scores (the predictor's distances, as k_feat_scores), the features,
+// network and settings (as k_features and k_mlp_infer, the same operations
+// in the same order: bit for bit their settings), then the exact ranking of
+// the predicted nprobe lists (as k_rank_select_w).  The BF16-rounded hidden
+// weights are staged once per CTA as BF16 pairs [input f][units 2l, 2l + 1]
+// (rows of 33 words: the transposing stores fall in distinct banks), so that
+// lane l accumulates units 2l and 2l + 1 from one 4-byte load per input; the
+// inputs are broadcast by shuffles.  Writes nprobe_out / rerank_out; a query
+// with more than RSW_CAND lists inside its bound goes on `redo`.
+constexpr int RH_WARPS = 8;
+constexpr int RH_WLD = 33;  // words per input row of the staged weight pairs
+constexpr size_t rh_head_bytes() { return sizeof(uint32_t) * 2 * MLP_F * RH_WLD + sizeof(float) * (4 * MLP_H + 4); }
+constexpr size_t rh_warp_bytes(int L) {
+    return sizeof(uint64_t) * (RSW_CAND + 32) + sizeof(uint32_t) * 256 + sizeof(float) * (size_t)((L + 3) & ~3);
+}
+
+__device__ __forceinline__ float bf16_lo(uint32_t pk) { return __uint_as_float(pk << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t pk) { return __uint_as_float(pk & 0xffff0000u); }
+
+__global__ void __launch_bounds__(RH_WARPS * 32) k_rank_head_w(const float* __restrict__ scores,
+                                                               const float* __restrict__ err,
+                                                               const float* __restrict__ Q,
+                                                               const float* __restrict__ Cc, int64_t nq, int d, int L,
+                                                               int spherical, const float* __restrict__ wm,
+                                                               ksc_adaptive_params prm, int Pmax,
+                                                               int32_t* __restrict__ probes,
+                                                               int32_t* __restrict__ redo,
+                                                               int32_t* __restrict__ nprobe_out,
+                                                               int32_t* __restrict__ rerank_out) {
+    extern __shared__ uint64_t hsm[];
+    uint32_t* WB1 = reinterpret_cast<uint32_t*>(hsm);
+    uint32_t* WB2 = WB1 + MLP_F * RH_WLD;
+    float* hb1 = reinterpret_cast<float*>(WB2 + MLP_H * RH_WLD);
+    float* hb2 = hb1 + MLP_H;
+    float* hW3 = hb2 + MLP_H;  // [o][f]
+    float* hb3 = hW3 + MLP_O * MLP_H;
+    unsigned char* wbase = reinterpret_cast<unsigned char*>(hsm) + rh_head_bytes();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned char* mine = wbase + (size_t)w * rh_warp_bytes(L);
+    uint64_t* ck = reinterpret_cast<uint64_t*>(mine);
+    uint64_t* bb = ck + RSW_CAND;
+    uint32_t* hist = reinterpret_cast<uint32_t*>(bb + 32);
+    float* ss = reinterpret_cast<float*>(hist + 256);
+    uint32_t* kv = reinterpret_cast<uint32_t*>(ck);
+    {
+        // hidden weights: coalesced 16-byte loads of rows a, stored transposed
+        // as BF16 (units 2l, 2l + 1 of input f in word f * RH_WLD + l)
+        const MlpW G = mlp_views(wm);
+        constexpr int V = MLP_H * MLP_F / 4 / (RH_WARPS * 32);
+        float4 v1[V], v2[V];
+#pragma unroll
+        for (int u = 0; u < V; ++u) {
+            v1[u] = __ldg(reinterpret_cast<const float4*>(G.W1) + threadIdx.x + RH_WARPS * 32 * u);
+            v2[u] = __ldg(reinterpret_cast<const float4*>(G.W2) + threadIdx.x + RH_WARPS * 32 * u);  // (MLP_F == MLP_H)
+        }
+        __nv_bfloat16* B1 = reinterpret_cast<__nv_bfloat16*>(WB1);
+        __nv_bfloat16* B2 = reinterpret_cast<__nv_bfloat16*>(WB2);
+#pragma unroll
+        for (int u = 0; u < V; ++u) {
+            const int e4 = threadIdx.x + RH_WARPS * 32 * u, a = e4 >> 4, f = 4 * (e4 & 15);
+            const float x1[4] = {v1[u].x, v1[u].y, v1[u].z, v1[u].w}, x2[4] = {v2[u].x, v2[u].y, v2[u].z, v2[u].w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                B1[2 * (f + k) * RH_WLD + a] = __float2bfloat16_rn(x1[k]);
+                B2[2 * (f + k) * RH_WLD + a] = __float2bfloat16_rn(x2[k]);
+            }
+        }
+        for (int e = threadIdx.x; e < MLP_H; e += blockDim.x) {
+            hb1[e] = bf(G.b1[e]);
+            hb2[e] = bf(G.b2[e]);
+        }
+        for (int e = threadIdx.x; e < MLP_O * MLP_H; e += blockDim.x) hW3[e] = bf(G.W3[e]);
+        if (threadIdx.x < MLP_O) hb3[threadIdx.x] = bf(G.b3[threadIdx.x]);
+    }
+    __syncthreads();
+    auto load = [&](int c) -> uint64_t { return ((uint64_t)ordered_f32(ss[c]) << 32) | (uint32_t)c; };
+    auto load32 = [&](int c) -> uint32_t { return ordered_f32(ss[c]); };
+    for (int64_t q = (int64_t)blockIdx.x * RH_WARPS + w; q < nq; q += (int64_t)gridDim.x * RH_WARPS) {
+        stage_row(scores + q * L, ss, L, lane);
+        // the FEAT_K smallest scores, ascending (order-preserving images)
+        uint32_t fv;
+        if (L > FEAT_K && warp_small_kvals(load32, L, FEAT_K, kv) >= 0) {
+            fv = kv[lane];
+        } else {
+            auto emit = [&](int i, uint64_t k) { ck[i] = k; };
+            if (L > FEAT_K) warp_topk(load, L, FEAT_K, emit, hist, bb);
+            else ck[lane] = load(lane);
+            __syncwarp();
+            fv = (uint32_t)(warp_sort_key(ck[lane], lane) >> 32);
+        }
+        __syncwarp();
+        float qq = 0.f;
+        if (!spherical) {
+            for (int t = lane; t < d; t += 32) qq = fmaf(Q[q * d + t], Q[q * d + t], qq);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) qq += __shfl_xor_sync(0xffffffffu, qq, o);
+        }
+        // features: lane i holds d_i / mean and d_1 / d_i (BF16)
+        const float u = fmaxf(feat_dist(unordered_f32(fv) + qq, spherical), 0.f);
+        float mean = 0.f;
+#pragma unroll
+        for (int i = 0; i < MLP_FEAT_K; ++i) mean += __shfl_sync(0xffffffffu, u, i);
+        mean = mean / MLP_FEAT_K + 1e-12f;
+        const float d1 = __shfl_sync(0xffffffffu, u, 0) + 1e-12f, di = u + 1e-12f;
+        const float xa = bf(di / mean), xb = bf(d1 / di);
+        // hidden layers: lane l computes units 2l and 2l + 1
+        float a0 = hb1[2 * lane], a1 = hb1[2 * lane + 1];
+#pragma unroll 8
+        for (int f = 0; f < MLP_F; ++f) {
+            const float x = __shfl_sync(0xffffffffu, f < MLP_FEAT_K ? xa : xb, f & 31);
+            const uint32_t pk = WB1[f * RH_WLD + lane];
+            a0 = fmaf(x, bf16_lo(pk), a0);
+            a1 = fmaf(x, bf16_hi(pk), a1);
+        }
+        const float h0 = bf(a0 > 0.f ? a0 : 0.f), h1 = bf(a1 > 0.f ? a1 : 0.f);
+        a0 = hb2[2 * lane];
+        a1 = hb2[2 * lane + 1];
+#pragma unroll 8
+        for (int f = 0; f < MLP_H; ++f) {
+            const float x = __shfl_sync(0xffffffffu, (f & 1) ? h1 : h0, f >> 1);
+            const uint32_t pk = WB2[f * RH_WLD + lane];
+            a0 = fmaf(x, bf16_lo(pk), a0);
+            a1 = fmaf(x, bf16_hi(pk), a1);
+        }
+        const float g0 = bf(a0 > 0.f ? a0 : 0.f), g1 = bf(a1 > 0.f ? a1 : 0.f);
+        float z0 = hb3[0], z1 = hb3[1];
+#pragma unroll 8
+        for (int f = 0; f < MLP_H; ++f) {
+            const float x = __shfl_sync(0xffffffffu, (f & 1) ? g1 : g0, f >> 1);
+            z0 = fmaf(x, hW3[f], z0);
+            z1 = fmaf(x, hW3[MLP_H + f], z1);
+        }
+        const float p0 = 1.f / (1.f + expf(-z0)), p1 = 1.f / (1.f + expf(-z1));
+        const int np = prm.regression ? regmap(p0, prm.pmin, prm.pmax, prm.p0, prm.p1)
+                                      : eq2(p0, prm.pmin, prm.pmax, prm.p0, prm.p1);
+        const int rr = prm.regression ? regmap(p1, prm.rmin, prm.rmax, prm.r0, prm.r1)
+                                      : eq2(p1, prm.rmin, prm.rmax, prm.r0, prm.r1);
+        if (lane == 0) {
+            nprobe_out[q] = np;
+            rerank_out[q] = rr;
+        }
+        // the exact ranking of the predicted lists
+        const int P = np < 1 ? 1 : (np > Pmax ? Pmax : np);
+        float tau = INFINITY;
+        if (P < L) {
+            uint32_t sP;
+            if (P <= FEAT_K) {
+                sP = __shfl_sync(0xffffffffu, fv, P - 1);
+            } else if (P <= 48 && warp_small_kvals(load32, L, P, kv) >= 0) {
+                sP = kv[P - 1];
+                __syncwarp();
+            } else {
+                auto none = [](int, uint64_t) {};
+                sP = (uint32_t)(warp_topk(load, L, P, none, hist, bb) >> 32);
+            }
+            tau = unordered_f32(sP) + (err ? 2.f * err[q] : 0.f);
+        }
+        const int n = collect_lists(ss, L, tau, ck, lane);
+        if (n > RSW_CAND) {
+            if (lane == 0) redo[1 + atomicAdd(&redo[0], 1)] = (int32_t)q;
+        } else {
+            exact_top_p(q, n, P, Pmax, ck, Q, Cc, d, spherical, probes, nullptr, lane);
+        }
+        __syncwarp();  // ss and ck are reused by the warp's next query
+    }
+}
+
 // The predictor's distances (Sec. 4.2.1): per query the FEAT_K smallest list
 // scores, ascending, from the given score matrix (the tensor-core scores,
 // within their bound of the exact ones); for L2 the query's squared norm,
 // which the ranking score leaves out, is added back.  One warp per query.
-// vals_out (optional) receives the FEAT_K sorted scores' order-preserving
-// u32 images.
 __global__ void __launch_bounds__(256) k_feat_scores(const float* __restrict__ scores, const float* __restrict__ Q,
                                                      int d, int spherical, int64_t nq, int L,
-                                                     float* __restrict__ out, uint32_t* __restrict__ vals_out) {
+                                                     float* __restrict__ out) {
     __shared__ uint32_t hist[8][256];
     __shared__ uint64_t bb[8][32];
     __shared__ uint64_t kk[8][FEAT_K];
@@ -578,7 +784,6 @@ __global__ void __launch_bounds__(256) k_feat_scores(const float* __restrict__ s
         for (int o = 16; o > 0; o >>= 1) qq += __shfl_xor_sync(0xffffffffu, qq, o);
     }
     out[q * FEAT_K + lane] = unordered_f32(v) + qq;
-    if (vals_out) vals_out[q * FEAT_K + lane] = v;
 }
 
 // ------------------------------------------------------------------ a2: quantised LUTs
@@ -2659,11 +2864,10 @@ static bool rank_by_warp(const ksc_index* ix, int64_t nq, int Pmax) {
 
 // The P best lists of every query from the given approximate scores (an
 // error bound per query in err), exactly re-scored; feat: the predictor's
-// distances as well; given: the FEAT_K sorted score images of k_feat_scores, from
-// which the warp kernel reads the P-th smallest instead of selecting it.
+// distances as well.
 static int select_lists(ksc_index* ix, const float* scores, const float* err, const float* Q, int64_t nq,
                         const int32_t* nprobe_q, int Pfix, int Pmax, int32_t* probes, float* score_out,
-                        cudaStream_t st, float* feat, const uint32_t* given);
+                        cudaStream_t st, float* feat);
 
 static int rank_lists(ksc_index* ix, const float* Q, int64_t nq, const int32_t* nprobe_q, int Pfix, int Pmax,
                       int32_t* probes, float* score_out, int mode, cudaStream_t st, float* feat = nullptr) {
@@ -2671,12 +2875,12 @@ static int rank_lists(ksc_index* ix, const float* Q, int64_t nq, const int32_t* 
     float* scores = (float*)ix->ws_scores.p;
     float* err = nullptr;
     KSC_TRY(list_scores(ix, Q, nq, mode, scores, &err, st));
-    return select_lists(ix, scores, err, Q, nq, nprobe_q, Pfix, Pmax, probes, score_out, st, feat, nullptr);
+    return select_lists(ix, scores, err, Q, nq, nprobe_q, Pfix, Pmax, probes, score_out, st, feat);
 }
 
 static int select_lists(ksc_index* ix, const float* scores, const float* err, const float* Q, int64_t nq,
                         const int32_t* nprobe_q, int Pfix, int Pmax, int32_t* probes, float* score_out,
-                        cudaStream_t st, float* feat, const uint32_t* given) {
+                        cudaStream_t st, float* feat) {
     // re-score buffer of the CTA kernel: 4 Pmax lists (a power of two, at least 1024, at most RS_CAP)
     const int rs_cap = std::min(RS_CAP, std::max(1024, pow2_ceil(4 * Pmax)));
     const size_t smem = rs_cap * sizeof(uint64_t) + (ix->L <= RS_SMEM_L ? sizeof(float) * ix->L : 0);
@@ -2691,7 +2895,7 @@ static int select_lists(ksc_index* ix, const float* scores, const float* err, co
         KSC_CUDA(cudaFuncSetAttribute(k_rank_select_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm));
         k_rank_select_w<<<(unsigned)((nq + RSW_WARPS - 1) / RSW_WARPS), RSW_WARPS * 32, wsm, st>>>(
             scores, err, Q, ix->c_rank, nq, ix->d, ix->L, ix->spherical, nprobe_q, Pfix, Pmax, probes, score_out,
-            redo, feat, given);
+            redo, feat);
         feat = nullptr;  // written
         KSC_LAUNCH_CHECK();
         k_rank_select<256><<<num_sms() * 2, 256, smem, st>>>(scores, err, Q, ix->c_rank, nq, ix->d, ix->L, ix->spherical,
@@ -2711,8 +2915,7 @@ static int select_lists(ksc_index* ix, const float* scores, const float* err, co
     }
     KSC_LAUNCH_CHECK();
     if (feat) {
-        k_feat_scores<<<(unsigned)((nq + 7) / 8), 256, 0, st>>>(scores, Q, ix->d, ix->spherical, nq, ix->L, feat,
-                                                                nullptr);
+        k_feat_scores<<<(unsigned)((nq + 7) / 8), 256, 0, st>>>(scores, Q, ix->d, ix->spherical, nq, ix->L, feat);
         KSC_LAUNCH_CHECK();
         ix->launches++;
     }
@@ -3456,32 +3659,49 @@ static int rank_and_features(ksc_index* ix, const float* Q, int64_t nq, int P, i
 
 // The adaptive search's ranking (Sec. 4.2.1).  The predictor's distances
 // are the FEAT_K smallest approximate list scores; the network sets each
-// query's nprobe and R from them (features, network and Eq. 2 in one
-// kernel); only then are the nprobe best lists of each query ranked exactly,
-// the threshold of the exact pass taken from the same sorted scores.  The
-// probes equal the first nprobe of an exact ranking of Pr lists (an exact
-// top-P is a prefix of the exact top-Pr); rows past nprobe hold -1.
+// query's nprobe and R from them; only then are the nprobe best lists of each
+// query ranked exactly, the threshold of the exact pass taken from the same
+// sorted scores -- all in k_rank_head_w, with the CTA kernel for the queries
+// it leaves on `redo`.  The probes equal the first nprobe of an exact ranking
+// of Pr lists (an exact top-P is a prefix of the exact top-Pr); rows past
+// nprobe hold -1.  Batches the warp kernels do not serve: the ranking of Pr
+// lists with the features, then the head kernel.
 static int rank_adaptive(ksc_index* ix, const float* Q, int64_t nq, int Pr, int32_t* probes,
                          const ksc_adaptive_params& prm, int32_t* np_q, int32_t* r_q, cudaStream_t st) {
-    KSC_TRY(ensure(ix->ws_rscore, sizeof(float) * nq * FEAT_K, st));
-    float* rs = (float*)ix->ws_rscore.p;
     if (!rank_by_warp(ix, nq, Pr) || ix->L < FEAT_K) {
+        KSC_TRY(ensure(ix->ws_rscore, sizeof(float) * nq * FEAT_K, st));
+        float* rs = (float*)ix->ws_rscore.p;
         KSC_TRY(rank_lists(ix, Q, nq, nullptr, Pr, Pr, probes, nullptr, RANK_TC16, st, rs));
         KSC_TRY(mlp_infer_scores(ix->mlp_w, rs, FEAT_K, ix->spherical, nq, prm, np_q, r_q, st));
         ix->launches++;
         return KSC_OK;
     }
     KSC_TRY(ensure(ix->ws_scores, sizeof(float) * nq * ix->L, st));
-    KSC_TRY(ensure(ix->ws_fkeys, sizeof(uint32_t) * nq * FEAT_K, st));
+    KSC_TRY(ensure(ix->ws_redo, sizeof(int32_t) * (nq + 1), st));
     float* scores = (float*)ix->ws_scores.p;
-    uint32_t* fkeys = (uint32_t*)ix->ws_fkeys.p;
+    int32_t* redo = (int32_t*)ix->ws_redo.p;
     float* err = nullptr;
     KSC_TRY(list_scores(ix, Q, nq, RANK_TC16, scores, &err, st));
-    k_feat_scores<<<(unsigned)((nq + 7) / 8), 256, 0, st>>>(scores, Q, ix->d, ix->spherical, nq, ix->L, rs, fkeys);
+    KSC_CUDA(cudaMemsetAsync(redo, 0, sizeof(int32_t), st));
+    const size_t hsm = rh_head_bytes() + RH_WARPS * rh_warp_bytes(ix->L);
+    KSC_CUDA(cudaFuncSetAttribute(k_rank_head_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm));
+    int per_sm = 0;
+    KSC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rank_head_w, RH_WARPS * 32, hsm));
+    const int64_t grid = std::min<int64_t>((nq + RH_WARPS - 1) / RH_WARPS,
+                                           (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1));
+    k_rank_head_w<<<(unsigned)grid, RH_WARPS * 32, hsm, st>>>(scores, err, Q, ix->c_rank, nq, ix->d, ix->L,
+                                                             ix->spherical, ix->mlp_w, prm, Pr, probes, redo, np_q,
+                                                             r_q);
     KSC_LAUNCH_CHECK();
-    KSC_TRY(mlp_infer_scores(ix->mlp_w, rs, FEAT_K, ix->spherical, nq, prm, np_q, r_q, st));
+    // queries with too many lists inside the bound: the CTA kernel
+    const int rs_cap = std::min(RS_CAP, std::max(1024, pow2_ceil(4 * Pr)));
+    const size_t smem = rs_cap * sizeof(uint64_t) + (ix->L <= RS_SMEM_L ? sizeof(float) * ix->L : 0);
+    KSC_CUDA(cudaFuncSetAttribute(k_rank_select<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_rank_select<256><<<num_sms() * 2, 256, smem, st>>>(scores, err, Q, ix->c_rank, nq, ix->d, ix->L, ix->spherical,
+                                                        np_q, Pr, Pr, rs_cap, probes, nullptr, redo);
+    KSC_LAUNCH_CHECK();
     ix->launches += 2;
-    return select_lists(ix, scores, err, Q, nq, np_q, Pr, Pr, probes, nullptr, st, nullptr, fkeys);
+    return KSC_OK;
 }
 
 static uint64_t mix64(uint64_t& s) {  // splitmix64 (Steele, Lea, Flood 2014)
