@@ -850,6 +850,34 @@ __device__ __forceinline__ void stage_codebook(const LutArgs& A, float* cbs) {
 // centroid's values of the subspace, cw = its codebook row in shared memory.
 // DS = dsub when fixed at compile time (2: 8-byte loads; qj and cj 8-byte
 // aligned), 0 = read from dsub.
+// Packed FP32 pairs (sm_100 family): each half is the IEEE single-precision
+// operation rounded to nearest, the same result as the scalar instruction,
+// in one instruction for both.
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) {
+    float2 d;
+    asm("{.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 f2_mul(float2 a, float2 b) {
+    float2 d;
+    asm("{.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 f2_add(float2 a, float2 b) {
+    float2 d;
+    asm("{.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
 template <int DS>
 __device__ __forceinline__ void row_table(int dsub, int ip, const float* __restrict__ qj,
                                           const float* __restrict__ cj, const float* cw, float (&T)[PQ_K]) {
@@ -871,9 +899,11 @@ __device__ __forceinline__ void row_table(int dsub, int ip, const float* __restr
                 T[i] = -acc;
             } else {
                 // 0 + e0^2 is e0^2 exactly (a square is +0 or more), so the sum
-                // from 0 needs one addition
-                const float e0 = __fsub_rn(u0, c.x), e1 = __fsub_rn(u1, c.y);
-                T[i] = __fadd_rn(__fmul_rn(e0, e0), __fmul_rn(e1, e1));
+                // from 0 needs one addition; both differences and both squares
+                // as packed pairs
+                const float2 e = f2_sub(make_float2(u0, u1), c);
+                const float2 e2 = f2_mul(e, e);
+                T[i] = __fadd_rn(e2.x, e2.y);
             }
         }
     } else {
@@ -905,7 +935,12 @@ __device__ __forceinline__ void row_table(int dsub, int ip, const float* __restr
 __device__ __forceinline__ uint32_t quant4(const float* T, float mn, float a) {
     uint32_t v[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) v[i] = min(__float2uint_rd(__fadd_rn(__fmul_rn(__fsub_rn(T[i], mn), a), 0.5f)), 255u);
+    for (int i = 0; i < 4; i += 2) {  // (T - m) a + 1/2 of two entries as packed pairs
+        const float2 x = f2_add(f2_mul(f2_sub(make_float2(T[i], T[i + 1]), make_float2(mn, mn)), make_float2(a, a)),
+                                make_float2(0.5f, 0.5f));
+        v[i] = min(__float2uint_rd(x.x), 255u);
+        v[i + 1] = min(__float2uint_rd(x.y), 255u);
+    }
     return __byte_perm(__byte_perm(v[0], v[1], 0x0040), __byte_perm(v[2], v[3], 0x0040), 0x5410);
 }
 
