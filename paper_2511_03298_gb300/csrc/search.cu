@@ -588,19 +588,23 @@ __global__ void __launch_bounds__(RSW_WARPS * 32) k_rank_select_w(const float* _
 // in the same order: bit for bit their settings), then the exact ranking of
 // the predicted nprobe lists (as k_rank_select_w).  The BF16-rounded hidden
 // weights are staged once per CTA as BF16 pairs [input f][units 2l, 2l + 1]
-// (rows of 33 words: the transposing stores fall in distinct banks), so that
-// lane l accumulates units 2l and 2l + 1 from one 4-byte load per input; the
-// inputs are broadcast by shuffles.  Writes nprobe_out / rerank_out; a query
-// with more than RSW_CAND lists inside its bound goes on `redo`.
+// (rows of 33 words: the transposing stores fall in distinct banks; BF16
+// keeps the CTA small enough for three per SM), so that lane l accumulates
+// units 2l and 2l + 1 from one 4-byte load and one packed FMA per input
+// (each half the scalar FMA's result); the inputs are broadcast by shuffles.
+// Writes nprobe_out / rerank_out; a query with more than RSW_CAND lists
+// inside its bound goes on `redo`.
 constexpr int RH_WARPS = 8;
 constexpr int RH_WLD = 33;  // words per input row of the staged weight pairs
 constexpr size_t rh_head_bytes() { return sizeof(uint32_t) * 2 * MLP_F * RH_WLD + sizeof(float) * (4 * MLP_H + 4); }
+
+// The two BF16 values of a staged pair as FP32 (exact).
+__device__ __forceinline__ float2 bf16_pair(uint32_t pk) {
+    return make_float2(__uint_as_float(pk << 16), __uint_as_float(pk & 0xffff0000u));
+}
 constexpr size_t rh_warp_bytes(int L) {
     return sizeof(uint64_t) * (RSW_CAND + 32) + sizeof(uint32_t) * 256 + sizeof(float) * (size_t)((L + 3) & ~3);
 }
-
-__device__ __forceinline__ float bf16_lo(uint32_t pk) { return __uint_as_float(pk << 16); }
-__device__ __forceinline__ float bf16_hi(uint32_t pk) { return __uint_as_float(pk & 0xffff0000u); }
 
 __global__ void __launch_bounds__(RH_WARPS * 32) k_rank_head_w(const float* __restrict__ scores,
                                                                const float* __restrict__ err,
@@ -617,7 +621,7 @@ __global__ void __launch_bounds__(RH_WARPS * 32) k_rank_head_w(const float* __re
     uint32_t* WB2 = WB1 + MLP_F * RH_WLD;
     float* hb1 = reinterpret_cast<float*>(WB2 + MLP_H * RH_WLD);
     float* hb2 = hb1 + MLP_H;
-    float* hW3 = hb2 + MLP_H;  // [o][f]
+    float* hW3 = hb2 + MLP_H;  // [f][o]
     float* hb3 = hW3 + MLP_O * MLP_H;
     unsigned char* wbase = reinterpret_cast<unsigned char*>(hsm) + rh_head_bytes();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -638,12 +642,12 @@ __global__ void __launch_bounds__(RH_WARPS * 32) k_rank_head_w(const float* __re
             v1[u] = __ldg(reinterpret_cast<const float4*>(G.W1) + threadIdx.x + RH_WARPS * 32 * u);
             v2[u] = __ldg(reinterpret_cast<const float4*>(G.W2) + threadIdx.x + RH_WARPS * 32 * u);  // (MLP_F == MLP_H)
         }
-        __nv_bfloat16* B1 = reinterpret_cast<__nv_bfloat16*>(WB1);
-        __nv_bfloat16* B2 = reinterpret_cast<__nv_bfloat16*>(WB2);
 #pragma unroll
         for (int u = 0; u < V; ++u) {
             const int e4 = threadIdx.x + RH_WARPS * 32 * u, a = e4 >> 4, f = 4 * (e4 & 15);
             const float x1[4] = {v1[u].x, v1[u].y, v1[u].z, v1[u].w}, x2[4] = {v2[u].x, v2[u].y, v2[u].z, v2[u].w};
+            __nv_bfloat16* B1 = reinterpret_cast<__nv_bfloat16*>(WB1);
+            __nv_bfloat16* B2 = reinterpret_cast<__nv_bfloat16*>(WB2);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 B1[2 * (f + k) * RH_WLD + a] = __float2bfloat16_rn(x1[k]);
@@ -654,7 +658,10 @@ __global__ void __launch_bounds__(RH_WARPS * 32) k_rank_head_w(const float* __re
             hb1[e] = bf(G.b1[e]);
             hb2[e] = bf(G.b2[e]);
         }
-        for (int e = threadIdx.x; e < MLP_O * MLP_H; e += blockDim.x) hW3[e] = bf(G.W3[e]);
+        for (int e = threadIdx.x; e < MLP_O * MLP_H; e += blockDim.x) {  // interleaved: [f][o]
+            const int o = e / MLP_H, f = e - o * MLP_H;
+            hW3[2 * f + o] = bf(G.W3[e]);
+        }
         if (threadIdx.x < MLP_O) hb3[threadIdx.x] = bf(G.b3[threadIdx.x]);
     }
     __syncthreads();
@@ -689,33 +696,27 @@ __global__ void __launch_bounds__(RH_WARPS * 32) k_rank_head_w(const float* __re
         const float d1 = __shfl_sync(0xffffffffu, u, 0) + 1e-12f, di = u + 1e-12f;
         const float xa = bf(di / mean), xb = bf(d1 / di);
         // hidden layers: lane l computes units 2l and 2l + 1
-        float a0 = hb1[2 * lane], a1 = hb1[2 * lane + 1];
+        float2 acc = *reinterpret_cast<const float2*>(hb1 + 2 * lane);
 #pragma unroll 8
         for (int f = 0; f < MLP_F; ++f) {
             const float x = __shfl_sync(0xffffffffu, f < MLP_FEAT_K ? xa : xb, f & 31);
-            const uint32_t pk = WB1[f * RH_WLD + lane];
-            a0 = fmaf(x, bf16_lo(pk), a0);
-            a1 = fmaf(x, bf16_hi(pk), a1);
+            acc = f2_fma(make_float2(x, x), bf16_pair(WB1[f * RH_WLD + lane]), acc);
         }
-        const float h0 = bf(a0 > 0.f ? a0 : 0.f), h1 = bf(a1 > 0.f ? a1 : 0.f);
-        a0 = hb2[2 * lane];
-        a1 = hb2[2 * lane + 1];
+        const float h0 = bf(acc.x > 0.f ? acc.x : 0.f), h1 = bf(acc.y > 0.f ? acc.y : 0.f);
+        acc = *reinterpret_cast<const float2*>(hb2 + 2 * lane);
 #pragma unroll 8
         for (int f = 0; f < MLP_H; ++f) {
             const float x = __shfl_sync(0xffffffffu, (f & 1) ? h1 : h0, f >> 1);
-            const uint32_t pk = WB2[f * RH_WLD + lane];
-            a0 = fmaf(x, bf16_lo(pk), a0);
-            a1 = fmaf(x, bf16_hi(pk), a1);
+            acc = f2_fma(make_float2(x, x), bf16_pair(WB2[f * RH_WLD + lane]), acc);
         }
-        const float g0 = bf(a0 > 0.f ? a0 : 0.f), g1 = bf(a1 > 0.f ? a1 : 0.f);
-        float z0 = hb3[0], z1 = hb3[1];
+        const float g0 = bf(acc.x > 0.f ? acc.x : 0.f), g1 = bf(acc.y > 0.f ? acc.y : 0.f);
+        float2 z = make_float2(hb3[0], hb3[1]);
 #pragma unroll 8
         for (int f = 0; f < MLP_H; ++f) {
             const float x = __shfl_sync(0xffffffffu, (f & 1) ? g1 : g0, f >> 1);
-            z0 = fmaf(x, hW3[f], z0);
-            z1 = fmaf(x, hW3[MLP_H + f], z1);
+            z = f2_fma(make_float2(x, x), *reinterpret_cast<const float2*>(hW3 + 2 * f), z);
         }
-        const float p0 = 1.f / (1.f + expf(-z0)), p1 = 1.f / (1.f + expf(-z1));
+        const float p0 = 1.f / (1.f + expf(-z.x)), p1 = 1.f / (1.f + expf(-z.y));
         const int np = prm.regression ? regmap(p0, prm.pmin, prm.pmax, prm.p0, prm.p1)
                                       : eq2(p0, prm.pmin, prm.pmax, prm.p0, prm.p1);
         const int rr = prm.regression ? regmap(p1, prm.rmin, prm.rmax, prm.r0, prm.r1)
@@ -850,34 +851,6 @@ __device__ __forceinline__ void stage_codebook(const LutArgs& A, float* cbs) {
 // centroid's values of the subspace, cw = its codebook row in shared memory.
 // DS = dsub when fixed at compile time (2: 8-byte loads; qj and cj 8-byte
 // aligned), 0 = read from dsub.
-// Packed FP32 pairs (sm_100 family): each half is the IEEE single-precision
-// operation rounded to nearest, the same result as the scalar instruction,
-// in one instruction for both.
-__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) {
-    float2 d;
-    asm("{.reg .b64 ra, rb, rd;\n\t"
-        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
-        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;}"
-        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-    return d;
-}
-__device__ __forceinline__ float2 f2_mul(float2 a, float2 b) {
-    float2 d;
-    asm("{.reg .b64 ra, rb, rd;\n\t"
-        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
-        "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;}"
-        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-    return d;
-}
-__device__ __forceinline__ float2 f2_add(float2 a, float2 b) {
-    float2 d;
-    asm("{.reg .b64 ra, rb, rd;\n\t"
-        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
-        "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;}"
-        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-    return d;
-}
-
 template <int DS>
 __device__ __forceinline__ void row_table(int dsub, int ip, const float* __restrict__ qj,
                                           const float* __restrict__ cj, const float* cw, float (&T)[PQ_K]) {
