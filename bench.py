@@ -257,11 +257,26 @@ def run_ours(args, rank, ws):
         lambda: ix.search(Qd, k, nprobe, R, opts=sopts, out=(ids, dists)))
     stats = ix.search_stats()
     if args.quick:
+        line = {"quick": True, "nprobe": nprobe, "ms_per_step": round(plain_ms, 4),
+                "value": round(CFG["nq"] / (plain_ms * 1e-3), 1),
+                "stage_ms": {s_: round(v, 4) for s_, v in plain_stage.items()}, "search_stats": stats}
+        if args.quick_learned:
+            # the adaptive search after a short training, at fixed Eq. 2
+            # settings (no tuning): for profiling its kernels
+            T = synth.train_queries(5, args.ntrain)
+            Td = torch.from_numpy(T).to(dev)
+            ix.train_predictor(Td, kth_fp32(torch, Xd, Td, k), epochs=4)
+            ix.set_predictor_params(2, 16, 100, R, 0.0, 0.0, 0.0, 2.0)
+            if args.profile_range:
+                torch.cuda.synchronize()
+                torch.cuda.profiler.start()  # a profiler started with --profile-from-start off records from here
+            l_ms, l_stage, _, _ = timed(lambda: ix.search_adaptive(Qd, k, opts=sopts))
+            if args.profile_range:
+                torch.cuda.profiler.stop()
+            line["learned"] = {"ms_per_step": round(l_ms, 4), "eq2": [2, 16, 100, R, 0.0, 0.0, 0.0, 2.0],
+                               "stage_ms": {s_: round(v, 4) for s_, v in l_stage.items()}}
         if rank == 0:
-            print(json.dumps({"quick": True, "nprobe": nprobe, "ms_per_step": round(plain_ms, 4),
-                              "value": round(CFG["nq"] / (plain_ms * 1e-3), 1),
-                              "stage_ms": {s_: round(v, 4) for s_, v in plain_stage.items()},
-                              "search_stats": stats}))
+            print(json.dumps(line))
         return None
     # learned nprobe (the paper's adaptive search module, an MLP here):
     # train on seeded training queries, tune Eq. 2 on a held-out split
@@ -1055,6 +1070,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--quick", action="store_true", help="profiling mode: timed steps only, at --nprobe")
+    ap.add_argument("--quick-learned", action="store_true",
+                    help="with --quick: also train the predictor briefly and time the adaptive search")
+    ap.add_argument("--profile-range", action="store_true",
+                    help="with --quick-learned: mark the adaptive search's steps as the profiled range")
     ap.add_argument("--nprobe", type=int, default=0)
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-nprobe path")
     ap.add_argument("--no-prune", action="store_true", help="skip predictive cluster pruning")
