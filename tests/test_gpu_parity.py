@@ -444,3 +444,40 @@ def test_warp_shaped_kernels_bit_exact(torch, ksc):
     pr_b, sc_b = g.rank_lists(torch.from_numpy(Qb).cuda(), 9)
     pr_s, sc_s = g.rank_lists(torch.from_numpy(Q).cuda(), 9)
     assert torch.equal(pr_b[:len(Q)], pr_s)
+
+
+def test_tied_list_scores_take_the_general_selection(torch, ksc):
+    """All but ten lists get the same ranking centroid, so their scores tie
+    exactly: more than 64 scores then fall at or below the warp kernels' small
+    selection bound and they fall back to radix refinement (and queries with
+    more than 128 lists inside the re-score bound to the CTA kernel).  The
+    warp-shaped ranking (a batch of 1600) equals the CTA-shaped one (the same
+    40 queries alone) and the oracle's lists (ties by list id), and the
+    adaptive search, whose one-kernel ranking takes the same fallbacks,
+    equals the variable-nprobe search at its own settings."""
+    X, Q, perm = mixture(8000, 32, 128, 31)
+    ix = dict(oracle.build_index(X, 128, 16, False, perm, iters=3))
+    cr = ix["c_rank"].copy()
+    cr[10:] = cr[10]
+    ix["c_rank"] = cr
+    g = gpu_index(ksc, ix)
+    reps = 1600 // len(Q) + 1
+    Qd = torch.from_numpy(np.tile(Q, (reps, 1))).cuda()
+    for P in (7, 32, 40):
+        pr_b, _ = g.rank_lists(Qd, P)
+        pr_s, _ = g.rank_lists(torch.from_numpy(Q).cuda(), P)
+        assert torch.equal(pr_b[:len(Q)], pr_s)
+        assert torch.equal(pr_b[-len(Q):], pr_s)
+        ref = oracle_probes(ix, Q, P)
+        # the tied lists' exact scores are identical in FP32 and FP64; the ten
+        # others may reorder against them only within FP32 rounding
+        same = (pr_s.cpu().numpy() == ref).mean()
+        assert same >= 0.95, same
+    rng = np.random.default_rng(5)
+    g.predictor_weights(set_to=rng.normal(scale=0.3, size=8450))
+    g.set_predictor_params(1, 40, 50, 100, 0.0, 0.0, 0.0, 0.0)
+    ids, dists, npb, rr = g.search_adaptive(Qd, 10)
+    assert len(np.unique(npb.cpu().numpy())) > 3
+    ids2, d2 = g.search_varprobe(Qd, 10, npb, rr, nprobe_max=40, rerank_max=100)
+    assert torch.equal(ids, ids2) and torch.equal(dists, d2)
+    assert g.last_status() == 0
