@@ -1170,6 +1170,145 @@ __device__ __forceinline__ int32_t scalar_dist(const uint8_t* __restrict__ lutp,
     return D;
 }
 
+// ------------------------------------------------------------------ candidate-key selection
+// The need smallest keys of distance word h among keys[0..N) (the others
+// mapped above every key, uniquely by index), into out[0..need) unless out
+// is null; returns the need-th.  The tie case of warp_topk_hi.
+__device__ __forceinline__ uint64_t warp_topk_tied(const uint64_t* __restrict__ keys, int N, int need, uint32_t h,
+                                                uint64_t* out, uint32_t* hist, uint64_t* bb) {
+    auto load_t = [&](int i) -> uint64_t {
+        const uint64_t k = keys[i];
+        return (uint32_t)(k >> 32) == h ? k : ((0xffffffffull << 32) | (uint32_t)i);
+    };
+    auto emit_t = [&](int i, uint64_t k) {
+        if (out) out[i] = k;
+    };
+    return warp_topk(load_t, N, need, emit_t, hist, bb);
+}
+
+// The K smallest (0 < K < N) of N unique candidate keys keys[0..N) (high word:
+// the integer distance + 2^31, below 2^32 - 1; low word: the vector id), by
+// one warp, as warp_topk but with the range, histogram and emission decided
+// on the keys' high words alone (32-bit loads and compares: the distance
+// range always spans more than the id bits matter for) until the K-th key's
+// bin holds at most 32 keys, which are sorted on their full 64 bits.  A bin
+// narrowed to a single distance with more than 32 keys in it (ties) hands the
+// rest to warp_topk over those keys.  Writes the K smallest to dst[0..K) in
+// no particular order (nothing if dst is null) and returns the K-th.
+__device__ uint64_t warp_topk_hi(const uint64_t* __restrict__ keys, int N, int K, uint64_t* dst, uint32_t* hist,
+                                 uint64_t* bb) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t below = (1u << lane) - 1u;
+    const uint32_t* hw = reinterpret_cast<const uint32_t*>(keys) + 1;  // key i's high word at hw[2 i]
+    uint32_t lo = 0xffffffffu, hi = 0u;
+    for (int i0 = 0; i0 < N; i0 += 32 * TOPK_U) {
+        uint32_t h[TOPK_U];
+#pragma unroll
+        for (int u = 0; u < TOPK_U; ++u) {
+            const int i = i0 + 32 * u + lane;
+            h[u] = i < N ? hw[2 * i] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < TOPK_U; ++u)
+            if (i0 + 32 * u + lane < N) {
+                lo = min(lo, h[u]);
+                hi = max(hi, h[u]);
+            }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    int out = 0, need = K;
+    while (lo < hi) {
+        int shift = 0;
+        while (((hi - lo) >> shift) >= 256u) ++shift;
+        for (int b = lane; b < 256; b += 32) hist[b] = 0u;
+        __syncwarp();
+        for (int i0 = 0; i0 < N; i0 += 32 * TOPK_U) {
+            uint32_t h[TOPK_U];
+#pragma unroll
+            for (int u = 0; u < TOPK_U; ++u) {
+                const int i = i0 + 32 * u + lane;
+                h[u] = i < N ? hw[2 * i] : 0xffffffffu;
+            }
+#pragma unroll
+            for (int u = 0; u < TOPK_U; ++u)
+                if (i0 + 32 * u + lane < N && h[u] >= lo && h[u] <= hi) atomicAdd(&hist[(h[u] - lo) >> shift], 1u);
+        }
+        __syncwarp();
+        uint32_t c[8], local = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            c[j] = hist[8 * lane + j];
+            local += c[j];
+        }
+        uint32_t incl = local;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const uint32_t excl = incl - local;
+        int B = -1, lt = 0, inB = 0;
+        if (excl < (uint32_t)need && (uint32_t)need <= incl) {
+            uint32_t acc = excl;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                if (B < 0 && acc + c[j] >= (uint32_t)need) {
+                    B = 8 * lane + j;
+                    lt = (int)acc;
+                    inB = (int)c[j];
+                }
+                acc += c[j];
+            }
+        }
+        const int owner = __ffs(__ballot_sync(0xffffffffu, B >= 0)) - 1;
+        B = __shfl_sync(0xffffffffu, B, owner);
+        lt = __shfl_sync(0xffffffffu, lt, owner);  // keys of the range below bin B
+        inB = __shfl_sync(0xffffffffu, inB, owner);
+        const uint32_t blo = lo + ((uint32_t)B << shift);
+        const uint32_t bhi = (hi - blo < (1u << shift)) ? hi : blo + ((1u << shift) - 1u);
+        const bool last = inB <= 32;
+        int nb = 0;
+        for (int i0 = 0; i0 < N; i0 += 32 * TOPK_U) {
+            uint32_t h[TOPK_U];
+#pragma unroll
+            for (int u = 0; u < TOPK_U; ++u) {
+                const int i = i0 + 32 * u + lane;
+                h[u] = i < N ? hw[2 * i] : 0xffffffffu;
+            }
+#pragma unroll
+            for (int u = 0; u < TOPK_U; ++u) {
+                const int i = i0 + 32 * u + lane;
+                const bool e = i < N && h[u] >= lo && h[u] < blo;
+                const bool g = last && i < N && h[u] >= blo && h[u] <= bhi;
+                const uint32_t me = __ballot_sync(0xffffffffu, e), mg = __ballot_sync(0xffffffffu, g);
+                if (e && dst) dst[out + __popc(me & below)] = keys[i];
+                if (g) bb[nb + __popc(mg & below)] = keys[i];
+                out += __popc(me);
+                nb += __popc(mg);
+            }
+        }
+        need -= lt;
+        if (last) {
+            __syncwarp();
+            const uint64_t v = warp_sort_key(lane < inB ? bb[lane] : KEY_NONE, lane);
+            if (lane < need && dst) dst[out + lane] = v;
+            const uint64_t kth = __shfl_sync(0xffffffffu, v, need - 1);
+            __syncwarp();
+            return kth;
+        }
+        lo = blo;
+        hi = bhi;
+        __syncwarp();
+    }
+    // one distance left with more keys than the sort takes: the need smallest
+    // of its keys by their ids
+    return warp_topk_tied(keys, N, need, lo, dst ? dst + out : nullptr, hist, bb);
+}
+
 // ------------------------------------------------------------------ threshold
 // Per query, after the scan of its nearest list(s) with no filter: the R-th
 // smallest of the keys found so far bounds the R-th smallest key of the whole
@@ -1208,11 +1347,7 @@ __global__ void __launch_bounds__(SW_WARPS * 32) k_threshold(ScanArgs A, int Rma
         t = m;
     } else if (n > R) {
         uint64_t* sq = scratch + q * Rmax;
-        auto load = [&](int i) -> uint64_t { return cq[i]; };
-        auto emit = [&](int i, uint64_t k) {
-            if (!ovf) sq[i] = k;
-        };
-        t = warp_topk(load, n, R, emit, hist[w], bb[w]);
+        t = warp_topk_hi(cq, n, R, ovf ? nullptr : sq, hist[w], bb[w]);
         if (!ovf) {
             __syncwarp();
             for (int i = lane; i < R; i += 32) cq[i] = sq[i];
@@ -2322,9 +2457,7 @@ __global__ void __launch_bounds__(SW_WARPS * 32) k_select(ScanArgs A, int Rmax, 
     if (n <= K) {
         for (int i = lane; i < n; i += 32) out[i] = cq[i];
     } else {
-        auto load = [&](int i) -> uint64_t { return cq[i]; };
-        auto emit = [&](int i, uint64_t k) { out[i] = k; };
-        warp_topk(load, n, K, emit, hist[w], bb[w]);
+        warp_topk_hi(cq, n, K, out, hist[w], bb[w]);
     }
     for (int i = K + lane; i < Rmax; i += 32) out[i] = KEY_NONE;
     if (lane == 0 && ncand) ncand[q] = K;
