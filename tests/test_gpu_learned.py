@@ -227,3 +227,54 @@ def test_regression_heads_follow_the_oracle_mapping_and_gain(env, trained):
     rec, mean_np = _recall(torch, X, Q, ids, kq), float(npb.double().mean().item())
     print("regression heads: fixed nprobe %d vs mean nprobe %.2f at recall %.4f" % (fixed, mean_np, rec))
     assert rec >= 0.90 and mean_np < fixed
+
+
+def _eq2_f32(v, lo, hi, a, b):
+    """Eq. 2 in FP32, operation by operation as the device evaluates it."""
+    v = np.float32(v)
+    relu = max(v - np.float32(a), np.float32(0))
+    r = np.float32(lo) + np.ceil(np.float32(hi - lo) * relu * (v + np.float32(b)))
+    return int(min(max(r, np.float32(lo)), np.float32(hi)))
+
+
+@pytest.mark.parametrize("metric", ["l2", "spherical"])
+def test_adaptive_ranking_equals_the_separate_head(env, metric):
+    """Batches of at least 8 queries per SM rank in one kernel (32 smallest
+    scores, features, network, Eq. 2, exact ranking of the predicted lists);
+    smaller ones take the ranking with features, then the head kernel.  In
+    both shapes, for L2 and spherical scores, the settings equal Eq. 2 in FP32
+    on the probabilities of the separate feature and forward kernels, and the
+    results equal the variable-nprobe search at those settings."""
+    torch, ksc = env
+    rng = np.random.default_rng(17 if metric == "l2" else 18)
+    centres = rng.uniform(-4, 4, size=(24, 48))
+    X = (centres[rng.integers(0, 24, 6000)] + rng.normal(size=(6000, 48))).astype(np.float32)
+    Q = (centres[rng.integers(0, 24, 40)] + rng.normal(size=(40, 48))).astype(np.float32)
+    sph = metric == "spherical"
+    if sph:
+        X /= np.linalg.norm(X, axis=1, keepdims=True)
+        Q /= np.linalg.norm(Q, axis=1, keepdims=True)
+    ix_o = oracle.build_index(X, 48, 24, sph, rng.permutation(6000).astype(np.int64), iters=4, ip=sph)
+    g = ksc.index_import(ix_o, metric="ip" if sph else "l2", spherical=sph)
+    # weights and Eq. 2 chosen so that nprobe spreads over 1..48 (all 48 lists):
+    # the kernel's paths for nprobe <= 32, 33..48 and every list
+    w = np.random.default_rng(99).normal(scale=0.3, size=8450).astype(np.float32)
+    g.predictor_weights(set_to=w)
+    g.set_predictor_params(1, 48, 50, 150, 0.05, 3.0, 0.0, 0.5)
+    wd = torch.from_numpy(w).cuda()
+    st = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for reps in (1, 41):  # 40 queries (CTA shapes) and 1640 (the one-kernel ranking)
+        Qd = torch.from_numpy(np.tile(Q, (reps, 1))).cuda()
+        ids, dists, npb, rr = g.search_adaptive(Qd, 10)
+        feats = g.query_features(Qd)
+        p = torch.empty((len(Qd), 2), dtype=torch.float32, device="cuda")
+        assert ksc.lib().ksc_mlp_forward(_ptr(wd), _ptr(feats), len(Qd), _ptr(p), st) == 0
+        torch.cuda.synchronize()
+        p = p.cpu().numpy()
+        npb_h, rr_h = npb.cpu().numpy(), rr.cpu().numpy()
+        assert np.array_equal(npb_h, [_eq2_f32(v, 1, 48, 0.05, 3.0) for v in p[:, 0]])
+        assert np.array_equal(rr_h, [_eq2_f32(v, 50, 150, 0.0, 0.5) for v in p[:, 1]])
+        assert len(np.unique(npb_h)) > 10 and npb_h.min() <= 32 and npb_h.max() > 32
+        ids2, d2 = g.search_varprobe(Qd, 10, npb, rr, nprobe_max=48, rerank_max=150)
+        assert torch.equal(ids, ids2) and torch.equal(dists, d2)
+        assert g.last_status() == 0
