@@ -158,6 +158,14 @@ typedef struct {
                                   accumulate; the lists their error bound cannot exclude are
                                   re-scored exactly, so the ranking is the same (rank_fp32 wins
                                   when both are set) */
+    int32_t rerank_band;       /* exact FP32 re-rank (precision 0, k <= 32, d <= 128): 1 first reads
+                                  BF16 copies of the candidate rows and bounds each FP32 distance
+                                  (BF16 rounding plus FP32 evaluation error); only candidates whose
+                                  lower bound is at most the k-th smallest upper bound are read in
+                                  FP32, so the results are those of the plain pass; -1 every
+                                  candidate in FP32; 0 auto: the band for L2 indexes.  The BF16
+                                  rows (n d 2 bytes) and norm bounds (n 4 bytes) are made on
+                                  first use */
 } ksc_search_opts;
 
 /* k nearest neighbours of Q_dev [nq x d] with a fixed nprobe (1..nlist) and

@@ -341,7 +341,8 @@ int free_index_memory(ksc_index* ix) {
                        ix->c_rank_f8 != s->c_rank_f8 ? ix->c_rank_f8 : nullptr,
                        ix->c_rank_f8_scale != s->c_rank_f8_scale ? ix->c_rank_f8_scale : nullptr,
                        ix->X_bf16 != s->X_bf16 ? ix->X_bf16 : nullptr, ix->X_fp8 != s->X_fp8 ? ix->X_fp8 : nullptr,
-                       ix->X_scale != s->X_scale ? ix->X_scale : nullptr};
+                       ix->X_scale != s->X_scale ? ix->X_scale : nullptr,
+                       ix->X_norm != s->X_norm ? ix->X_norm : nullptr};
         for (void* p : own)
             if (p) cudaFree(p);
         for (int i = 0; i < nb; ++i) release(*bufs[i]);
@@ -353,7 +354,7 @@ int free_index_memory(ksc_index* ix) {
                     ix->blk_ids, ix->blk_codes, ix->assign, ix->graph, ix->entry, ix->status, ix->stats,
                     ix->c_rank_bf16, ix->mlp_w, ix->blk_list, ix->nbr_pos, ix->nbr_codes, ix->entry_pos,
                     ix->X_bf16, ix->X_fp8, ix->X_scale, ix->pr_stats, ix->pr_vecs, ix->pr_model, ix->dims,
-                    ix->X_rr, ix->c_rank_f8, ix->c_rank_f8_scale, ix->gids};
+                    ix->X_rr, ix->c_rank_f8, ix->c_rank_f8_scale, ix->gids, ix->X_norm};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < nb; ++i) release(*bufs[i]);

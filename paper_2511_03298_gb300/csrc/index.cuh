@@ -39,6 +39,7 @@ struct ksc_index {
     void* X_bf16 = nullptr;        // [n x d] BF16 rows (precision variant, made on first use)
     void* X_fp8 = nullptr;         // [n x d] FP8 e4m3 rows
     float* X_scale = nullptr;      // [n] their per-row scales
+    float* X_norm = nullptr;       // [n] upper bounds of the re-rank rows' norms (BF16 band, made on first use)
     int32_t* status = nullptr;     // device status word
     unsigned long long* stats = nullptr;  // [4] counters of the last search
     // host mirrors

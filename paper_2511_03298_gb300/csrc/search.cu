@@ -2680,15 +2680,133 @@ __global__ void __launch_bounds__(NT) k_rerank(const float* __restrict__ Q, cons
 // dot products across the warp in a halving exchange (9 shuffles for 8 rows);
 // the k best keys are then taken by k rounds of a warp minimum.  Same
 // distance rule as k_rerank (L2 direct difference squares, IP -<q, x>), FP32.
+//
+// With xb (BF16 copies of the rows) and xn (upper bounds of the rows' norms),
+// a first pass reads the BF16 rows (half the bytes) and bounds each
+// candidate's FP32 distance: |d~ - d| <= e, from the BF16 rounding (|x~_t -
+// x_t| <= 2^-9 |x_t|) and the FP32 evaluation of both sums (relative 2^-20,
+// far above their ~11 rounding steps of 2^-24):
+//   L2: e = 2 eps n s + (eps n)^2 + g (s^2 + (s + eps n)^2), s >= sqrt of the
+//       exact BF16-row distance; IP: e = |q| n (eps + 2.01 g);
+// eps = 2^-9, g = 2^-20, n the row's norm bound, all evaluated with a factor
+// (1 + 2^-10) and directed rounding of d~ -/+ e.  U is the k-th smallest
+// d~ + e; a candidate with d~ - e > U has an FP32 distance above k FP32
+// distances, so it cannot be among the k best.  The others get the FP32
+// distance by the very code of the plain pass (a row's sum does not depend on
+// the rows beside it in the exchange), so the result is bit for bit the
+// plain pass's.
 constexpr int RW_WARPS = 8;
 constexpr int RW_MAXR = 512;
+
+// Halving exchange of 8 rows' partial sums over the warp (9 shuffles):
+// afterwards every lane of quad `myrow` (lane bits 4, 3, 2) holds that row's
+// total, summed in the same tree for every row.
+__device__ __forceinline__ float exchange_rows8(float (&a)[8], int lane) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const bool up = lane & 16;
+        const float send = up ? a[i] : a[i + 4], keep = up ? a[i + 4] : a[i];
+        a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const bool up = lane & 8;
+        const float send = up ? a[i] : a[i + 2], keep = up ? a[i + 2] : a[i];
+        a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    {
+        const bool up = lane & 4;
+        const float send = up ? a[0] : a[1], keep = up ? a[1] : a[0];
+        a[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    a[0] += __shfl_xor_sync(0xffffffffu, a[0], 2);
+    a[0] += __shfl_xor_sync(0xffffffffu, a[0], 1);
+    return a[0];
+}
+
+// FP32 partial sums of the 8 rows idv[] (-1: none) for this lane's 4
+// coordinates, summed across the warp: every lane of quad `myrow` ends with
+// that row's distance term (L2: the squared distance, IP: the dot product).
+__device__ __forceinline__ float rerank_rows8(const float4& qv, const float* __restrict__ X, int d, int ip, bool inl,
+                                              const int32_t (&idv)[8], int lane) {
+    float4 xv[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+        xv[u] = (idv[u] >= 0 && inl) ? __ldg(reinterpret_cast<const float4*>(X + (int64_t)idv[u] * d) + lane)
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+    float a[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        if (ip) {
+            a[u] = qv.x * xv[u].x + qv.y * xv[u].y + qv.z * xv[u].z + qv.w * xv[u].w;
+        } else {
+            const float e0 = qv.x - xv[u].x, e1 = qv.y - xv[u].y, e2 = qv.z - xv[u].z, e3 = qv.w - xv[u].w;
+            a[u] = fmaf(e0, e0, fmaf(e1, e1, fmaf(e2, e2, e3 * e3)));
+        }
+    }
+    return exchange_rows8(a, lane);
+}
+
+// The distance terms of 16 BF16 rows idv[] (-1: none) at once (the rows are
+// half as wide, so twice as many are in flight as in the FP32 pass): lane l
+// reads coordinates 4l..4l+3 of each row in one 8-byte load; a halving
+// exchange over lane bits 4..1 leaves row (lane >> 1) & 15 in both lanes of a
+// pair.  Only bounded, not compared bit for bit, so the summation order is
+// free.
+__device__ __forceinline__ float rerank_rows16_bf16(const float4& qv, const uint16_t* __restrict__ xb, int d, int ip,
+                                                    bool inl, const int32_t (&idv)[16], int lane) {
+    uint2 r[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u)
+        r[u] = (idv[u] >= 0 && inl) ? __ldg(reinterpret_cast<const uint2*>(xb + (int64_t)idv[u] * d) + lane)
+                                    : make_uint2(0u, 0u);
+    float a[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        const float x0 = __uint_as_float(r[u].x << 16), x1 = __uint_as_float(r[u].x & 0xffff0000u);
+        const float x2 = __uint_as_float(r[u].y << 16), x3 = __uint_as_float(r[u].y & 0xffff0000u);
+        if (ip) {
+            a[u] = qv.x * x0 + qv.y * x1 + qv.z * x2 + qv.w * x3;
+        } else {
+            const float e0 = qv.x - x0, e1 = qv.y - x1, e2 = qv.z - x2, e3 = qv.w - x3;
+            a[u] = fmaf(e0, e0, fmaf(e1, e1, fmaf(e2, e2, e3 * e3)));
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const bool up = lane & 16;
+        const float send = up ? a[i] : a[i + 8], keep = up ? a[i + 8] : a[i];
+        a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const bool up = lane & 8;
+        const float send = up ? a[i] : a[i + 4], keep = up ? a[i + 4] : a[i];
+        a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const bool up = lane & 4;
+        const float send = up ? a[i] : a[i + 2], keep = up ? a[i + 2] : a[i];
+        a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    {
+        const bool up = lane & 2;
+        const float send = up ? a[0] : a[1], keep = up ? a[1] : a[0];
+        a[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
+    a[0] += __shfl_xor_sync(0xffffffffu, a[0], 1);
+    return a[0];
+}
 
 __global__ void __launch_bounds__(RW_WARPS * 32) k_rerank_w(const float* __restrict__ Q, const float* __restrict__ X,
                                                             int d, int ip, const uint64_t* __restrict__ topr,
                                                             int Rmax, const int32_t* __restrict__ rerank_q, int Rfix,
                                                             int k, int64_t nq, int64_t* __restrict__ out_ids,
-                                                            float* __restrict__ out_d) {
-    extern __shared__ uint64_t wkeys[];  // RW_WARPS x Rmax
+                                                            float* __restrict__ out_d,
+                                                            const uint16_t* __restrict__ xb,
+                                                            const float* __restrict__ xn) {
+    extern __shared__ uint64_t wkeys[];  // RW_WARPS x Rmax keys; with xb also RW_WARPS x (Rmax + 64) words
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t q = (int64_t)blockIdx.x * RW_WARPS + w;
     if (q >= nq) return;
@@ -2703,51 +2821,88 @@ __global__ void __launch_bounds__(RW_WARPS * 32) k_rerank_w(const float* __restr
     const uint64_t* cq = topr + q * Rmax;
     // row of the sum this lane holds after the exchange
     const int myrow = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-    for (int c0 = 0; c0 < R; c0 += 8) {
-        float4 xv[8];
-        int32_t idv[8];
+    auto id_of = [&](int c) -> int32_t {
+        const uint64_t kk = c < R ? cq[c] : KEY_NONE;
+        return kk != KEY_NONE ? (int32_t)(kk & 0xffffffffu) : -1;
+    };
+    auto fp32_key = [&](int c, float a0) -> uint64_t {
+        const uint64_t kk = cq[c];
+        return kk != KEY_NONE ? (((uint64_t)ordered_f32(ip ? -a0 : a0) << 32) | (kk & 0xffffffffull)) : KEY_NONE;
+    };
+    if (xb && R > k) {
+        uint32_t* sv = reinterpret_cast<uint32_t*>(wkeys + (size_t)RW_WARPS * Rmax) + (size_t)w * (Rmax + 64);
+        uint32_t* kv = sv + Rmax;  // the small selection's values
+        float2* band = reinterpret_cast<float2*>(keys);  // (lower, upper) bound per candidate
+        const float eps = 0x1p-9f, g = 0x1p-20f, safe = 1.f + 0x1p-10f;
+        float qn = 0.f;  // IP: an upper bound of |q|
+        if (ip) {
+            float t = fmaf(qv.x, qv.x, fmaf(qv.y, qv.y, fmaf(qv.z, qv.z, qv.w * qv.w)));
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const uint64_t kk = c0 + u < R ? cq[c0 + u] : KEY_NONE;
-            idv[u] = kk != KEY_NONE ? (int32_t)(kk & 0xffffffffu) : -1;
-            xv[u] = (idv[u] >= 0 && inl) ? __ldg(reinterpret_cast<const float4*>(X + (int64_t)idv[u] * d) + lane)
-                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            qn = sqrtf(t) * (1.f + 0x1p-18f);
         }
-        float a[8];
+        const int myrow16 = (lane >> 1) & 15;
+        for (int c0 = 0; c0 < R; c0 += 16) {
+            int32_t idv[16];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            if (ip) {
-                a[u] = qv.x * xv[u].x + qv.y * xv[u].y + qv.z * xv[u].z + qv.w * xv[u].w;
-            } else {
-                const float e0 = qv.x - xv[u].x, e1 = qv.y - xv[u].y, e2 = qv.z - xv[u].z, e3 = qv.w - xv[u].w;
-                a[u] = fmaf(e0, e0, fmaf(e1, e1, fmaf(e2, e2, e3 * e3)));
+            for (int u = 0; u < 16; ++u) idv[u] = id_of(c0 + u);
+            const float a0 = rerank_rows16_bf16(qv, xb, d, ip, inl, idv, lane);
+            const int c = c0 + myrow16;
+            if ((lane & 1) == 0 && c < R) {
+                float lo = INFINITY, hi = INFINITY;
+                const int32_t id = id_of(c);
+                if (id >= 0) {
+                    const float n = xn[id] + 0x1p-100f;  // (+ BF16's subnormal spacing, summed over d)
+                    float e, dt;
+                    if (ip) {
+                        dt = -a0;
+                        e = qn * n * (eps + 2.01f * g) * safe;
+                    } else {
+                        dt = a0;
+                        const float sq = sqrtf(fmaxf(dt, 0.f) * (1.f + 2.f * g)) * (1.f + 0x1p-20f), en = eps * n;
+                        e = (2.f * en * sq + en * en + g * (sq * sq + (sq + en) * (sq + en))) * safe;
+                    }
+                    lo = __fsub_rd(dt, e);
+                    hi = __fadd_ru(dt, e);
+                }
+                band[c] = make_float2(lo, hi);
             }
         }
-        // halving exchange: 8 rows over 32 lanes
+        __syncwarp();
+        // U: the k-th smallest upper bound (+inf when the small selection
+        // cannot tell: then every candidate is re-scored)
+        float U = INFINITY;
+        auto load_hi = [&](int c) -> uint32_t { return ordered_f32(band[c].y); };
+        if (k <= 48 && warp_small_kvals(load_hi, R, k, kv) >= 0) U = unordered_f32(kv[k - 1]);
+        // survivors: lower bound <= U
+        const uint32_t below = (1u << lane) - 1u;
+        int ns = 0;
+        for (int c0 = 0; c0 < R; c0 += 32) {
+            const int c = c0 + lane;
+            const bool in = c < R && band[c].x <= U;
+            const uint32_t m = __ballot_sync(0xffffffffu, in);
+            if (in) sv[ns + __popc(m & below)] = (uint32_t)c;
+            ns += __popc(m);
+        }
+        __syncwarp();
+        for (int c = lane; c < R; c += 32) keys[c] = KEY_NONE;
+        __syncwarp();
+        for (int s0 = 0; s0 < ns; s0 += 8) {
+            int32_t idv[8];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const bool up = lane & 16;
-            const float send = up ? a[i] : a[i + 4], keep = up ? a[i + 4] : a[i];
-            a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+            for (int u = 0; u < 8; ++u) idv[u] = s0 + u < ns ? id_of((int)sv[s0 + u]) : -1;
+            const float a0 = rerank_rows8(qv, X, d, ip, inl, idv, lane);
+            const int si = s0 + myrow;
+            if ((lane & 3) == 0 && si < ns) keys[sv[si]] = fp32_key((int)sv[si], a0);
         }
+    } else {
+        for (int c0 = 0; c0 < R; c0 += 8) {
+            int32_t idv[8];
 #pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const bool up = lane & 8;
-            const float send = up ? a[i] : a[i + 2], keep = up ? a[i + 2] : a[i];
-            a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-        }
-        {
-            const bool up = lane & 4;
-            const float send = up ? a[0] : a[1], keep = up ? a[1] : a[0];
-            a[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-        }
-        a[0] += __shfl_xor_sync(0xffffffffu, a[0], 2);
-        a[0] += __shfl_xor_sync(0xffffffffu, a[0], 1);
-        const int c = c0 + myrow;
-        if ((lane & 3) == 0 && c < R) {
-            const uint64_t kk = cq[c];
-            keys[c] = kk != KEY_NONE ? (((uint64_t)ordered_f32(ip ? -a[0] : a[0]) << 32) | (kk & 0xffffffffull))
-                                     : KEY_NONE;
+            for (int u = 0; u < 8; ++u) idv[u] = id_of(c0 + u);
+            const float a0 = rerank_rows8(qv, X, d, ip, inl, idv, lane);
+            const int c = c0 + myrow;
+            if ((lane & 3) == 0 && c < R) keys[c] = fp32_key(c, a0);
         }
     }
     __syncwarp();
@@ -2758,15 +2913,15 @@ __global__ void __launch_bounds__(RW_WARPS * 32) k_rerank_w(const float* __restr
         for (int i = lane; i < R; i += 32) {
             if (keys[i] < m) { m = keys[i]; at = i; }
         }
-        uint64_t g = m;
+        uint64_t gk = m;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const uint64_t y = __shfl_xor_sync(0xffffffffu, g, o);
-            g = y < g ? y : g;
+            const uint64_t y = __shfl_xor_sync(0xffffffffu, gk, o);
+            gk = y < gk ? y : gk;
         }
-        if (g != KEY_NONE && m == g) keys[at] = KEY_NONE;  // keys are unique: one lane matches
+        if (gk != KEY_NONE && m == gk) keys[at] = KEY_NONE;  // keys are unique: one lane matches
         __syncwarp();
-        if (lane == r) mine = g;
+        if (lane == r) mine = gk;
     }
     if (lane < k) {
         if (mine == KEY_NONE) {
@@ -2778,6 +2933,22 @@ __global__ void __launch_bounds__(RW_WARPS * 32) k_rerank_w(const float* __restr
             out_d[q * k + lane] = ip ? -dist : dist;
         }
     }
+}
+
+// Upper bounds of the rows' norms: sqrt of the FP64 sum of squares, rounded
+// up to FP32.  A warp per row.
+__global__ void k_row_norms(const float* __restrict__ X, int64_t n, int d, float* __restrict__ out) {
+    const int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= n) return;
+    double s = 0.0;
+    for (int t = lane; t < d; t += 32) {
+        const double v = X[r * d + t];
+        s += v * v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[r] = __double2float_ru(sqrt(s) * (1.0 + 0x1p-40));
 }
 
 // ------------------------------------------------------------------ precision variant
@@ -2907,6 +3078,7 @@ struct Plan {
     bool hybrid;
     int n_near, efs, tau;
     int prec, Rf;  // precision variant: first re-rank of R (= Rmax) in prec, then FP32 of the best Rf
+    bool band;     // exact re-rank with the BF16 band (k_rerank_w)
     int Pq_max;    // bound on the per-query nprobe (<= Pmax)
     bool tc;       // scan on the tensor cores (k_scan_tc)
     int nt;        // its queries per item
@@ -3110,6 +3282,18 @@ static int ensure_lowp(ksc_index* ix, int prec, cudaStream_t st) {
         KSC_CUDA(cudaMalloc(&ix->X_scale, sizeof(float) * ix->n));
         k_x_lowp<<<(unsigned)((ix->n + 7) / 8), 256, 0, st>>>(rr_X(ix), ix->n, dr, 2, nullptr, (uint8_t*)ix->X_fp8,
                                                               ix->X_scale);
+        KSC_LAUNCH_CHECK();
+    }
+    return KSC_OK;
+}
+
+// The BF16 band of the exact re-rank: BF16 rows and the rows' norm bounds,
+// made on first use.
+static int ensure_band(ksc_index* ix, cudaStream_t st) {
+    KSC_TRY(ensure_lowp(ix, 1, st));
+    if (!ix->X_norm) {
+        KSC_CUDA(cudaMalloc(&ix->X_norm, sizeof(float) * ix->n));
+        k_row_norms<<<(unsigned)((ix->n + 7) / 8), 256, 0, st>>>(rr_X(ix), ix->n, rr_d(ix), ix->X_norm);
         KSC_LAUNCH_CHECK();
     }
     return KSC_OK;
@@ -3372,10 +3556,13 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
         rr_q = nullptr;
     }
     if (pl.k <= 32 && rr_R <= RW_MAXR && dr <= 128 && (dr & 3) == 0 && warp_per_query(nq)) {
-        const size_t smem = sizeof(uint64_t) * RW_WARPS * rr_R;
+        const bool band = pl.band && pl.prec == 0 && rr_R > pl.k;
+        if (band) KSC_TRY(ensure_band(ix, st));
+        const size_t smem = sizeof(uint64_t) * RW_WARPS * rr_R + (band ? sizeof(uint32_t) * RW_WARPS * (rr_R + 64) : 0);
         cudaFuncSetAttribute(k_rerank_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_rerank_w<<<(unsigned)((nq + RW_WARPS - 1) / RW_WARPS), RW_WARPS * 32, smem, st>>>(
-            Qr, Xr, dr, ix->metric == KSC_IP, rr_keys, rr_R, rr_q, rr_R, pl.k, nq, ids, dists);
+            Qr, Xr, dr, ix->metric == KSC_IP, rr_keys, rr_R, rr_q, rr_R, pl.k, nq, ids, dists,
+            band ? (const uint16_t*)ix->X_bf16 : nullptr, band ? ix->X_norm : nullptr);
         ix->launches++;
         KSC_LAUNCH_CHECK();
     } else {
@@ -3450,6 +3637,9 @@ static int make_plan(ksc_index* ix, int64_t nq, int k, int Pmax, int Rmax, const
     pl.rank_mode = (opts && opts->rank_fp32) ? RANK_FP32 : ((opts && opts->rank_fp8) ? RANK_FP8 : RANK_TC16);
     pl.Pq_max = Pmax;
     pl.prec = opts ? opts->precision : 0;
+    // the BF16 band: on by default for L2 (for inner products the band is
+    // wide against the gaps between the best scores)
+    pl.band = opts && opts->rerank_band != 0 ? opts->rerank_band > 0 : ix->metric != KSC_IP;
     KSC_CHECK_ARG(pl.prec >= 0 && pl.prec <= 2, "precision must be 0 (FP32), 1 (BF16) or 2 (FP8)");
     pl.Rf = pl.Rmax;
     if (pl.prec > 0) {
@@ -3569,7 +3759,7 @@ int rerank_keys(ksc_index* ix, const float* Q, int64_t nq, int k, const uint64_t
         const size_t smem = sizeof(uint64_t) * RW_WARPS * R;
         KSC_CUDA(cudaFuncSetAttribute(k_rerank_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_rerank_w<<<(unsigned)((nq + RW_WARPS - 1) / RW_WARPS), RW_WARPS * 32, smem, st>>>(
-            Q, Xr, dr, ip, keys, R, nullptr, R, k, nq, ids, dists);
+            Q, Xr, dr, ip, keys, R, nullptr, R, k, nq, ids, dists, nullptr, nullptr);
     } else {
         const size_t smem = sizeof(uint64_t) * pow2_ceil(R < 2 ? 2 : R);
         if (nq < 2 * (int64_t)num_sms()) {

@@ -54,7 +54,7 @@ class SearchOpts(C.Structure):
     _fields_ = [("lanes_per_query", C.c_int32), ("hybrid", C.c_int32), ("n_near", C.c_int32),
                 ("efs", C.c_int32), ("tau", C.c_int32), ("cand_cap", C.c_int32), ("rank_fp32", C.c_int32),
                 ("precision", C.c_int32), ("rerank_final", C.c_int32), ("tile_blocks", C.c_int32),
-                ("scan_tc", C.c_int32), ("rank_fp8", C.c_int32)]
+                ("scan_tc", C.c_int32), ("rank_fp8", C.c_int32), ("rerank_band", C.c_int32)]
 
 
 _vp, _i32, _i64 = C.c_void_p, C.c_int32, C.c_int64
@@ -166,13 +166,15 @@ def _hptr(a):
 
 
 def search_opts(lanes_per_query=0, hybrid=False, n_near=2, efs=64, tau=8, cand_cap=0, rank_fp32=False,
-                precision=0, rerank_final=0, tile_blocks=0, scan_tc=False, rank_fp8=False):
+                precision=0, rerank_final=0, tile_blocks=0, scan_tc=False, rank_fp8=False, rerank_band=0):
     """precision: 0 FP32 re-rank; 1 BF16 / 2 FP8 first re-rank of the widened
     shortlist, then FP32 over the best rerank_final.  scan_tc: the scan on
     the tensor cores (same keys).  rank_fp8: list scores from FP8 operands
-    (same ranking)."""
+    (same ranking).  rerank_band: 1 the exact re-rank reads BF16 rows first
+    and FP32 rows only where its bound cannot exclude a candidate (same
+    results), -1 FP32 rows of every candidate, 0 auto (the band for L2)."""
     return SearchOpts(lanes_per_query, int(hybrid), n_near, efs, tau, cand_cap, int(rank_fp32), precision,
-                      rerank_final, tile_blocks, int(scan_tc), int(rank_fp8))
+                      rerank_final, tile_blocks, int(scan_tc), int(rank_fp8), int(rerank_band))
 
 
 class Index:

@@ -481,3 +481,28 @@ def test_tied_list_scores_take_the_general_selection(torch, ksc):
     ids2, d2 = g.search_varprobe(Qd, 10, npb, rr, nprobe_max=40, rerank_max=100)
     assert torch.equal(ids, ids2) and torch.equal(dists, d2)
     assert g.last_status() == 0
+
+
+@pytest.mark.parametrize("kind", ["l2", "ip", "m50"])
+def test_bf16_band_rerank_equals_fp32_rerank(torch, ksc, kind):
+    """The exact re-rank's BF16 band (BF16 rows bound every candidate's FP32
+    distance; only candidates whose lower bound reaches the k-th upper bound
+    are read in FP32) returns what reading every candidate in FP32 returns,
+    for L2 and inner products, several k and R, a fixed and a per-query R,
+    in the warp-per-query shape (1600 queries)."""
+    ix, Q = small_index(kind)
+    g = gpu_index(ksc, ix)
+    reps = 1600 // len(Q) + 1
+    Qd = torch.from_numpy(np.tile(Q, (reps, 1))).cuda()
+    on, off = ksc.search_opts(rerank_band=1), ksc.search_opts(rerank_band=-1)
+    for k, R in ((10, 100), (32, 200), (1, 40)):
+        a = g.search(Qd, k, 9, R, opts=on)
+        b = g.search(Qd, k, 9, R, opts=off)
+        assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]), (k, R)
+    rng = np.random.default_rng(4)
+    npb = torch.from_numpy(rng.integers(1, 12, len(Qd)).astype(np.int32)).cuda()
+    rr = torch.from_numpy(rng.integers(10, 150, len(Qd)).astype(np.int32)).cuda()
+    c = g.search_varprobe(Qd, 10, npb, rr, nprobe_max=12, rerank_max=150, opts=on)
+    d = g.search_varprobe(Qd, 10, npb, rr, nprobe_max=12, rerank_max=150, opts=off)
+    assert torch.equal(c[0], d[0]) and torch.equal(c[1], d[1])
+    assert g.last_status() == 0
