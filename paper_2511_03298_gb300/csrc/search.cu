@@ -2761,16 +2761,20 @@ __device__ __forceinline__ float rerank_rows16_bf16(const float4& qv, const uint
         r[u] = (idv[u] >= 0 && inl) ? __ldg(reinterpret_cast<const uint2*>(xb + (int64_t)idv[u] * d) + lane)
                                     : make_uint2(0u, 0u);
     float a[16];
+    const float2 q01 = make_float2(qv.x, qv.y), q23 = make_float2(qv.z, qv.w);
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
-        const float x0 = __uint_as_float(r[u].x << 16), x1 = __uint_as_float(r[u].x & 0xffff0000u);
-        const float x2 = __uint_as_float(r[u].y << 16), x3 = __uint_as_float(r[u].y & 0xffff0000u);
+        const float2 x01 = make_float2(__uint_as_float(r[u].x << 16), __uint_as_float(r[u].x & 0xffff0000u));
+        const float2 x23 = make_float2(__uint_as_float(r[u].y << 16), __uint_as_float(r[u].y & 0xffff0000u));
+        // packed pairs: two coordinates per instruction (each half an FP32 operation)
+        float2 t;
         if (ip) {
-            a[u] = qv.x * x0 + qv.y * x1 + qv.z * x2 + qv.w * x3;
+            t = f2_fma(q23, x23, f2_mul(q01, x01));
         } else {
-            const float e0 = qv.x - x0, e1 = qv.y - x1, e2 = qv.z - x2, e3 = qv.w - x3;
-            a[u] = fmaf(e0, e0, fmaf(e1, e1, fmaf(e2, e2, e3 * e3)));
+            const float2 e01 = f2_sub(q01, x01), e23 = f2_sub(q23, x23);
+            t = f2_fma(e23, e23, f2_mul(e01, e01));
         }
+        a[u] = t.x + t.y;
     }
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -2846,13 +2850,15 @@ __global__ void __launch_bounds__(RW_WARPS * 32) k_rerank_w(const float* __restr
             int32_t idv[16];
 #pragma unroll
             for (int u = 0; u < 16; ++u) idv[u] = id_of(c0 + u);
-            const float a0 = rerank_rows16_bf16(qv, xb, d, ip, inl, idv, lane);
+            // this lane's row norm bound, loaded beside the rows
             const int c = c0 + myrow16;
+            const int32_t id = c < R ? id_of(c) : -1;
+            const float nb = id >= 0 ? __ldg(xn + id) : 0.f;
+            const float a0 = rerank_rows16_bf16(qv, xb, d, ip, inl, idv, lane);
             if ((lane & 1) == 0 && c < R) {
                 float lo = INFINITY, hi = INFINITY;
-                const int32_t id = id_of(c);
                 if (id >= 0) {
-                    const float n = xn[id] + 0x1p-100f;  // (+ BF16's subnormal spacing, summed over d)
+                    const float n = nb + 0x1p-100f;  // (+ BF16's subnormal spacing, summed over d)
                     float e, dt;
                     if (ip) {
                         dt = -a0;
@@ -2894,6 +2900,22 @@ __global__ void __launch_bounds__(RW_WARPS * 32) k_rerank_w(const float* __restr
             const float a0 = rerank_rows8(qv, X, d, ip, inl, idv, lane);
             const int si = s0 + myrow;
             if ((lane & 3) == 0 && si < ns) keys[sv[si]] = fp32_key((int)sv[si], a0);
+        }
+        if (ns <= 32) {
+            // few survivors: their keys sorted across the warp give the k best
+            __syncwarp();
+            const uint64_t v = warp_sort_key(lane < ns ? keys[sv[lane]] : KEY_NONE, lane);
+            if (lane < k) {
+                if (v == KEY_NONE) {
+                    out_ids[q * k + lane] = -1;
+                    out_d[q * k + lane] = ip ? -INFINITY : INFINITY;
+                } else {
+                    out_ids[q * k + lane] = (int64_t)(v & 0xffffffffu);
+                    const float dist = unordered_f32((uint32_t)(v >> 32));
+                    out_d[q * k + lane] = ip ? -dist : dist;
+                }
+            }
+            return;
         }
     } else {
         for (int c0 = 0; c0 < R; c0 += 8) {
