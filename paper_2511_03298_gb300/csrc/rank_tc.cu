@@ -199,19 +199,19 @@ __global__ void __launch_bounds__(128, 1) k_rank_gemm_tc(const __grid_constant__
                 const float cc = spherical ? 0.f : cn[c];
                 const float sc = F8 ? cs[c] : 1.f;
                 const int nr = nq - qb < 32 ? (int)(nq - qb) : 32;  // rows of this warp inside the batch
-                // eight rows at a time: their shared loads, then their stores
+                // sixteen rows at a time: their shared loads, then their stores
 #pragma unroll 1
-                for (int r0 = 0; r0 < nr; r0 += 8) {
-                    float v[8];
+                for (int r0 = 0; r0 < nr; r0 += 16) {
+                    float v[16];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
+                    for (int u = 0; u < 16; ++u) {
                         const int rr = r0 + u < nr ? r0 + u : nr - 1;
                         // F8: the product of two powers of two, an exact rescaling
                         const float dot = F8 ? stage[rr * 33 + lane] * (qs[qb + rr] * sc) : stage[rr * 33 + lane];
                         v[u] = spherical ? -dot : fmaf(-2.f, dot, cc);
                     }
 #pragma unroll
-                    for (int u = 0; u < 8; ++u)
+                    for (int u = 0; u < 16; ++u)
                         if (r0 + u < nr) scores[(qb + r0 + u) * L + c] = v[u];
                 }
             }
