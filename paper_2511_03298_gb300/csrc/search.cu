@@ -2810,11 +2810,12 @@ __global__ void __launch_bounds__(RW_WARPS * 32) k_rerank_w(const float* __restr
                                                             float* __restrict__ out_d,
                                                             const uint16_t* __restrict__ xb,
                                                             const float* __restrict__ xn) {
-    extern __shared__ uint64_t wkeys[];  // RW_WARPS x Rmax keys; with xb also RW_WARPS x (Rmax + 64) words
+    // RW_WARPS x Rmax keys; with xb also RW_WARPS x Rmax bound pairs and RW_WARPS x (Rmax + 64) words
+    extern __shared__ uint64_t wkeys[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t q = (int64_t)blockIdx.x * RW_WARPS + w;
     if (q >= nq) return;
-    uint64_t* keys = wkeys + (size_t)w * Rmax;
+    uint64_t* keys = wkeys + (size_t)w * Rmax;  // the candidates' keys, staged; then their FP32 keys
     const int R = rerank_of(rerank_q, Rfix, k, Rmax, q);
     const bool inl = lane * 4 < d;
     float4 qv = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -2822,21 +2823,61 @@ __global__ void __launch_bounds__(RW_WARPS * 32) k_rerank_w(const float* __restr
         const float* qp = Q + q * d + lane * 4;
         qv = make_float4(qp[0], qp[1], qp[2], qp[3]);
     }
-    const uint64_t* cq = topr + q * Rmax;
+    // the candidate keys in shared memory (one coalesced pass), so that a
+    // step's row loads wait for a shared load, not for a global one
+    {
+        const uint64_t* cq = topr + q * Rmax;
+        for (int c = lane; c < R; c += 32) keys[c] = cq[c];
+        __syncwarp();
+    }
     // row of the sum this lane holds after the exchange
     const int myrow = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
     auto id_of = [&](int c) -> int32_t {
-        const uint64_t kk = c < R ? cq[c] : KEY_NONE;
+        const uint64_t kk = c < R ? keys[c] : KEY_NONE;
         return kk != KEY_NONE ? (int32_t)(kk & 0xffffffffu) : -1;
     };
-    auto fp32_key = [&](int c, float a0) -> uint64_t {
-        const uint64_t kk = cq[c];
+    auto fp32_key = [&](uint64_t kk, float a0) -> uint64_t {
         return kk != KEY_NONE ? (((uint64_t)ordered_f32(ip ? -a0 : a0) << 32) | (kk & 0xffffffffull)) : KEY_NONE;
     };
+    // the k smallest of arr[0..cnt) to the outputs: one warp sort when they
+    // fit a warp, else k rounds of a warp minimum
+    auto emit_best = [&](uint64_t* arr, int cnt) {
+        uint64_t mine = KEY_NONE;  // lane r keeps the r-th smallest
+        if (cnt <= 32) {
+            mine = warp_sort_key(lane < cnt ? arr[lane] : KEY_NONE, lane);
+        } else {
+            for (int r = 0; r < k; ++r) {
+                uint64_t m = KEY_NONE;
+                int at = -1;
+                for (int i = lane; i < cnt; i += 32) {
+                    if (arr[i] < m) { m = arr[i]; at = i; }
+                }
+                uint64_t gk = m;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const uint64_t y = __shfl_xor_sync(0xffffffffu, gk, o);
+                    gk = y < gk ? y : gk;
+                }
+                if (gk != KEY_NONE && m == gk) arr[at] = KEY_NONE;  // keys are unique: one lane matches
+                __syncwarp();
+                if (lane == r) mine = gk;
+            }
+        }
+        if (lane < k) {
+            if (mine == KEY_NONE) {
+                out_ids[q * k + lane] = -1;
+                out_d[q * k + lane] = ip ? -INFINITY : INFINITY;
+            } else {
+                out_ids[q * k + lane] = (int64_t)(mine & 0xffffffffu);
+                const float dist = unordered_f32((uint32_t)(mine >> 32));
+                out_d[q * k + lane] = ip ? -dist : dist;
+            }
+        }
+    };
     if (xb && R > k) {
-        uint32_t* sv = reinterpret_cast<uint32_t*>(wkeys + (size_t)RW_WARPS * Rmax) + (size_t)w * (Rmax + 64);
+        float2* band = reinterpret_cast<float2*>(wkeys + (size_t)RW_WARPS * Rmax) + (size_t)w * Rmax;
+        uint32_t* sv = reinterpret_cast<uint32_t*>(wkeys + (size_t)2 * RW_WARPS * Rmax) + (size_t)w * (Rmax + 64);
         uint32_t* kv = sv + Rmax;  // the small selection's values
-        float2* band = reinterpret_cast<float2*>(keys);  // (lower, upper) bound per candidate
         const float eps = 0x1p-9f, g = 0x1p-20f, safe = 1.f + 0x1p-10f;
         float qn = 0.f;  // IP: an upper bound of |q|
         if (ip) {
@@ -2891,32 +2932,18 @@ __global__ void __launch_bounds__(RW_WARPS * 32) k_rerank_w(const float* __restr
             ns += __popc(m);
         }
         __syncwarp();
-        for (int c = lane; c < R; c += 32) keys[c] = KEY_NONE;
-        __syncwarp();
+        // their FP32 keys, by survivor index, where the bounds were
+        uint64_t* fk = reinterpret_cast<uint64_t*>(band);
         for (int s0 = 0; s0 < ns; s0 += 8) {
             int32_t idv[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) idv[u] = s0 + u < ns ? id_of((int)sv[s0 + u]) : -1;
             const float a0 = rerank_rows8(qv, X, d, ip, inl, idv, lane);
             const int si = s0 + myrow;
-            if ((lane & 3) == 0 && si < ns) keys[sv[si]] = fp32_key((int)sv[si], a0);
+            if ((lane & 3) == 0 && si < ns) fk[si] = fp32_key(keys[sv[si]], a0);
         }
-        if (ns <= 32) {
-            // few survivors: their keys sorted across the warp give the k best
-            __syncwarp();
-            const uint64_t v = warp_sort_key(lane < ns ? keys[sv[lane]] : KEY_NONE, lane);
-            if (lane < k) {
-                if (v == KEY_NONE) {
-                    out_ids[q * k + lane] = -1;
-                    out_d[q * k + lane] = ip ? -INFINITY : INFINITY;
-                } else {
-                    out_ids[q * k + lane] = (int64_t)(v & 0xffffffffu);
-                    const float dist = unordered_f32((uint32_t)(v >> 32));
-                    out_d[q * k + lane] = ip ? -dist : dist;
-                }
-            }
-            return;
-        }
+        __syncwarp();
+        emit_best(fk, ns);
     } else {
         for (int c0 = 0; c0 < R; c0 += 8) {
             int32_t idv[8];
@@ -2924,36 +2951,12 @@ __global__ void __launch_bounds__(RW_WARPS * 32) k_rerank_w(const float* __restr
             for (int u = 0; u < 8; ++u) idv[u] = id_of(c0 + u);
             const float a0 = rerank_rows8(qv, X, d, ip, inl, idv, lane);
             const int c = c0 + myrow;
-            if ((lane & 3) == 0 && c < R) keys[c] = fp32_key(c, a0);
+            const uint64_t kk = c < R ? keys[c] : KEY_NONE;
+            __syncwarp();  // this step's keys are read before they are replaced
+            if ((lane & 3) == 0 && c < R) keys[c] = fp32_key(kk, a0);
         }
-    }
-    __syncwarp();
-    uint64_t mine = KEY_NONE;  // lane r keeps the r-th smallest
-    for (int r = 0; r < k; ++r) {
-        uint64_t m = KEY_NONE;
-        int at = -1;
-        for (int i = lane; i < R; i += 32) {
-            if (keys[i] < m) { m = keys[i]; at = i; }
-        }
-        uint64_t gk = m;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const uint64_t y = __shfl_xor_sync(0xffffffffu, gk, o);
-            gk = y < gk ? y : gk;
-        }
-        if (gk != KEY_NONE && m == gk) keys[at] = KEY_NONE;  // keys are unique: one lane matches
         __syncwarp();
-        if (lane == r) mine = gk;
-    }
-    if (lane < k) {
-        if (mine == KEY_NONE) {
-            out_ids[q * k + lane] = -1;
-            out_d[q * k + lane] = ip ? -INFINITY : INFINITY;
-        } else {
-            out_ids[q * k + lane] = (int64_t)(mine & 0xffffffffu);
-            const float dist = unordered_f32((uint32_t)(mine >> 32));
-            out_d[q * k + lane] = ip ? -dist : dist;
-        }
+        emit_best(keys, R);
     }
 }
 
@@ -3580,7 +3583,8 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
     if (pl.k <= 32 && rr_R <= RW_MAXR && dr <= 128 && (dr & 3) == 0 && warp_per_query(nq)) {
         const bool band = pl.band && pl.prec == 0 && rr_R > pl.k;
         if (band) KSC_TRY(ensure_band(ix, st));
-        const size_t smem = sizeof(uint64_t) * RW_WARPS * rr_R + (band ? sizeof(uint32_t) * RW_WARPS * (rr_R + 64) : 0);
+        const size_t smem = sizeof(uint64_t) * RW_WARPS * rr_R * (band ? 2 : 1) +
+                            (band ? sizeof(uint32_t) * RW_WARPS * (rr_R + 64) : 0);
         cudaFuncSetAttribute(k_rerank_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_rerank_w<<<(unsigned)((nq + RW_WARPS - 1) / RW_WARPS), RW_WARPS * 32, smem, st>>>(
             Qr, Xr, dr, ix->metric == KSC_IP, rr_keys, rr_R, rr_q, rr_R, pl.k, nq, ids, dists,
