@@ -2564,8 +2564,12 @@ __global__ void __launch_bounds__(NT) k_rerank(const float* __restrict__ Q, cons
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int R = rerank_of(rerank_q, Rfix, k, Rmax, q);
     for (int t = threadIdx.x; t < d; t += blockDim.x) qs[t] = Q[q * d + t];
+    // the candidate keys staged in shared memory (each row load then waits
+    // for a shared load); each slot is later replaced by its FP32 key by
+    // the one warp that read it
+    for (int c = threadIdx.x; c < R; c += blockDim.x) keys[c] = topr[q * Rmax + c];
     __syncthreads();
-    const uint64_t* cq = topr + q * Rmax;
+    const uint64_t* cq = keys;
     const bool vec4 = (d & 3) == 0;
     if (vec4 && d <= 128) {
         // one float4 per lane per row; four rows in flight per warp
@@ -2592,6 +2596,7 @@ __global__ void __launch_bounds__(NT) k_rerank(const float* __restrict__ Q, cons
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                __syncwarp();  // (every lane read the step's keys before they are replaced)
                 if (lane == 0 && c0 + u < R)
                     keys[c0 + u] = idv[u] >= 0 ? (((uint64_t)ordered_f32(ip ? -s : s) << 32) | (uint32_t)idv[u])
                                                : KEY_NONE;
@@ -2629,6 +2634,7 @@ __global__ void __launch_bounds__(NT) k_rerank(const float* __restrict__ Q, cons
             const float dist = ip ? -s : s;
             outk = ((uint64_t)ordered_f32(dist) << 32) | (uint32_t)id;
         }
+        __syncwarp();  // (every lane read the key before it is replaced)
         if (lane == 0) keys[c] = outk;
     }
     __syncthreads();
