@@ -1034,12 +1034,15 @@ __global__ void __launch_bounds__(256) k_lut_fused(LutArgs A, int Pb, int Pm, ui
     float* T = cbs + (((size_t)M * ld + 3) & ~(size_t)3);              // Pb x M rows, LUT_TROW apart
     float* mins = T + (size_t)Pb * M * LUT_TROW;                       // Pm x M
     float* qsb = mins + (((size_t)Pm * M + 3) & ~(size_t)3);           // 2 x dpad
+    int32_t* prb = reinterpret_cast<int32_t*>(qsb + 2 * dpad);         // 2 x Pm probe ids
     __shared__ uint32_t s_rbits[2];
     const int r0 = threadIdx.x / M, j0 = threadIdx.x - r0 * M;         // first row of this thread
     const int dr = blockDim.x / M, dj = blockDim.x - dr * M;           // step of blockDim.x rows
     int64_t q = blockIdx.x;
-    if (q < A.nq)
+    if (q < A.nq) {
         for (int t = threadIdx.x; t < A.d; t += blockDim.x) qsb[t] = A.Q[q * A.d + t];
+        for (int r = threadIdx.x; r < Pm; r += blockDim.x) prb[r] = A.probes[q * A.Pmax + r];
+    }
     if (threadIdx.x == 0) s_rbits[0] = 0u;
     stage_codebook(A, cbs);  // ends with __syncthreads
     for (int buf = 0; q < A.nq; q += gridDim.x, buf ^= 1) {
@@ -1048,7 +1051,7 @@ __global__ void __launch_bounds__(256) k_lut_fused(LutArgs A, int Pb, int Pm, ui
         // pass; those of later probes (a query with more) are computed again
         const int P = min(probes_of(A, q), Pm);
         const int nstored = Pb * M;
-        const int32_t* pr = A.probes + q * A.Pmax;
+        const int32_t* pr = prb + buf * Pm;  // the query's probes, staged in shared memory
         float R = 0.f;
         {
             int r = r0, j = j0;
@@ -1141,15 +1144,18 @@ __global__ void __launch_bounds__(256) k_lut_fused(LutArgs A, int Pb, int Pm, ui
         }
         if (threadIdx.x == 0) scale[q] = a;
         if (pre) qs_next[threadIdx.x] = nx;
-        if (qn < A.nq)
+        if (qn < A.nq) {
             for (int t = threadIdx.x + blockDim.x; t < A.d; t += blockDim.x) qs_next[t] = A.Q[qn * A.d + t];
+            for (int r = threadIdx.x; r < Pm; r += blockDim.x) prb[(buf ^ 1) * Pm + r] = A.probes[qn * A.Pmax + r];
+        }
         __syncthreads();  // the next query reuses the shared tables
     }
 }
 
 static size_t lut_fused_smem(int M, int dsub, int d, int Pb, int Pm) {
     return sizeof(float) * ((((size_t)M * cb_ld(dsub) + 3) & ~(size_t)3) + (size_t)Pb * M * LUT_TROW +
-                            (((size_t)Pm * M + 3) & ~(size_t)3) + 2 * (((size_t)d + 3) & ~(size_t)3));
+                            (((size_t)Pm * M + 3) & ~(size_t)3) + 2 * (((size_t)d + 3) & ~(size_t)3)) +
+           sizeof(int32_t) * 2 * (size_t)Pm;
 }
 
 // 8-byte row loads need dsub = 2 and an 8-byte aligned query matrix.
