@@ -3644,7 +3644,7 @@ static void set_tiles(const ksc_index* ix, Plan& pl, int64_t nq, double P, const
         return t;
     };
     pl.TB = tile(blocks * (1.0 - near), 220.0);
-    pl.TBa = tile(blocks * near, 120.0);
+    pl.TBa = tile(blocks * near, 60.0);
     if (opts && opts->tile_blocks > 0) pl.TB = pl.TBa = std::min(opts->tile_blocks, 1 << 20);
     // tensor-core scan (the filtered part only): tiles of whole 128-vector
     // products, 32 blocks unless given
