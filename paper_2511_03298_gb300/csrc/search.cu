@@ -2695,12 +2695,13 @@ __global__ void __launch_bounds__(NT) k_rerank(const float* __restrict__ Q, cons
 //
 // With xb (BF16 copies of the rows) and xn (upper bounds of the rows' norms),
 // a first pass reads the BF16 rows (half the bytes) and bounds each
-// candidate's FP32 distance: |d~ - d| <= e, from the BF16 rounding (|x~_t -
-// x_t| <= 2^-9 |x_t|) and the FP32 evaluation of both sums (relative 2^-20,
-// far above their ~11 rounding steps of 2^-24):
+// candidate's FP32 distance: |d~ - d| <= e, from the BF16 rounding
+// (|x~_t - x_t| <= 2^-8 |x_t|: BF16 carries 8 significant bits) and the FP32
+// evaluation of both sums (relative 2^-20, far above their ~11 rounding steps
+// of 2^-24):
 //   L2: e = 2 eps n s + (eps n)^2 + g (s^2 + (s + eps n)^2), s >= sqrt of the
 //       exact BF16-row distance; IP: e = |q| n (eps + 2.01 g);
-// eps = 2^-9, g = 2^-20, n the row's norm bound, all evaluated with a factor
+// eps = 2^-8, g = 2^-20, n the row's norm bound, all evaluated with a factor
 // (1 + 2^-10) and directed rounding of d~ -/+ e.  U is the k-th smallest
 // d~ + e; a candidate with d~ - e > U has an FP32 distance above k FP32
 // distances, so it cannot be among the k best.  The others get the FP32
@@ -2890,7 +2891,7 @@ __global__ void __launch_bounds__(RW_WARPS * 32) k_rerank_w(const float* __restr
         float2* band = reinterpret_cast<float2*>(wkeys + (size_t)RW_WARPS * Rmax) + (size_t)w * Rmax;
         uint32_t* sv = reinterpret_cast<uint32_t*>(wkeys + (size_t)2 * RW_WARPS * Rmax) + (size_t)w * (Rmax + 64);
         uint32_t* kv = sv + Rmax;  // the small selection's values
-        const float eps = 0x1p-9f, g = 0x1p-20f, safe = 1.f + 0x1p-10f;
+        const float eps = 0x1p-8f, g = 0x1p-20f, safe = 1.f + 0x1p-10f;
         float qn = 0.f;  // IP: an upper bound of |q|
         if (ip) {
             float t = fmaf(qv.x, qv.x, fmaf(qv.y, qv.y, fmaf(qv.z, qv.z, qv.w * qv.w)));
