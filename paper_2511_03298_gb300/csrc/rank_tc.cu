@@ -243,7 +243,8 @@ __global__ void k_to_16(const float* __restrict__ X, int64_t n, int d, int Kp, i
 // the exact FP32 re-score.
 //  16-bit tensor-core operands: |<q~, c~> - <q, c>| <= (2u + u^2) sum |q_t c_t|
 //    + FP32 accumulation, u = 2^-11 (FP16) or 2^-8 (BF16), and
-//    sum |q_t c_t| <= ||q|| ||c|| (Cauchy-Schwarz).  FP16 is used when every
+//    sum |q_t c_t| <= ||q|| ||c|| (Cauchy-Schwarz); for FP16 also the
+//    subnormal range's absolute error, 2^-25 per element.  FP16 is used when every
 //    centroid element is below 2^14 and a query element above 6e4 voids the
 //    bound (err = inf: every list is re-scored).
 //  FP32 CUDA cores: a dot product of d terms errs by at most about d 2^-24
@@ -294,7 +295,12 @@ __global__ void k_q16_err(const float* __restrict__ Q, int64_t nq, int d, int Kp
         return;
     }
     const float qn = sqrtf(s);
-    const float e = rel * qn * cmax * 1.0001f;
+    // FP16 elements below 2^-14 are subnormal: their rounding error is up to
+    // half the spacing 2^-24 rather than relative, for the query's and the
+    // centroids' elements alike: eta sum(|c_t| + |q_t|) <= eta sqrt(d) (|q| +
+    // max|c|) (BF16 keeps the FP32 exponent range: its 2^-134 is far below r)
+    const float sub = fp16 ? 0x1p-25f * sqrtf((float)d) * (qn + cmax) * 1.01f : 0.f;
+    const float e = (rel * qn * cmax + sub) * 1.0001f;
     const float r = (float)(d + 8) * 1.2e-7f * (qn + cmax) * (qn + cmax);
     err[q] = (spherical ? e : 2.f * e) + r;
 }

@@ -1,0 +1,87 @@
+"""The list ranking's bound on its 16-bit scores, pinned on the CPU.
+
+The ranking re-scores in FP32 every list whose given (tensor-core) score is
+within 2 err of the P-th, so err must bound |given - exact| for every list.
+This restates the bound -- for 16-bit operands (FP16 when every centroid
+element is below 2^14, else BF16):
+  e = (rel |q| max|c| + sub) 1.0001,  rel = (2u + u^2) + d 4.8e-7,
+  sub = 2^-25 sqrt(d) (|q| + max|c|) 1.01 for FP16 (subnormal elements), 0 for BF16,
+  err = (2 e for L2, e for spherical) + (d + 8) 1.2e-7 (|q| + max|c|)^2
+-- and checks it against scores evaluated as the kernel does (operands
+rounded to 16 bits, the dot product summed in FP32 in two orders, L2 as
+FP32 ||c||^2 - 2 dot by one FMA) on random and adversarial data: tiny
+magnitudes (FP16 subnormals), wide dynamic range, and rows near the FP16
+limit.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+
+def r16(x, fp16):
+    t = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32))
+    return (t.to(torch.float16) if fp16 else t.to(torch.bfloat16)).to(torch.float32).numpy()
+
+
+def dot_f32(a, b, pairwise):
+    t = (a * b).astype(np.float32)
+    if not pairwise:
+        acc = np.float32(0)
+        for v in t:
+            acc = np.float32(acc + v)
+        return acc
+    while len(t) > 1:
+        if len(t) % 2:
+            t = np.append(t, np.float32(0))
+        t = (t[0::2] + t[1::2]).astype(np.float32)
+    return t[0]
+
+
+def bound(qn, cmax, d, fp16, spherical):
+    u2 = 9.77e-4 + 1e-6 if fp16 else 0.0078125 + 6.2e-5
+    rel = u2 + d * 4.8e-7
+    sub = 2.0 ** -25 * np.sqrt(d) * (qn + cmax) * 1.01 if fp16 else 0.0
+    e = (rel * qn * cmax + sub) * 1.0001
+    r = (d + 8) * 1.2e-7 * (qn + cmax) ** 2
+    return (e if spherical else 2 * e) + r
+
+
+def data(rng, kind, d, L):
+    if kind == "normal":
+        return rng.normal(size=(L, d)), rng.normal(size=d)
+    if kind == "tiny":  # FP16 subnormals throughout
+        return rng.normal(size=(L, d)) * 1e-6, rng.normal(size=d) * 1e-6
+    if kind == "range":  # magnitudes over ten decades
+        return rng.normal(size=(L, d)) * 10.0 ** rng.uniform(-8, 2, size=(L, d)), \
+            rng.normal(size=d) * 10.0 ** rng.uniform(-8, 2, size=d)
+    if kind == "big":  # centroids near the FP16 limit (BF16 then)
+        return rng.uniform(-2e4, 2e4, size=(L, d)), rng.uniform(-1e3, 1e3, size=d)
+    raise ValueError(kind)
+
+
+@pytest.mark.parametrize("kind", ["normal", "tiny", "range", "big"])
+@pytest.mark.parametrize("spherical", [False, True])
+def test_16bit_score_bound_holds(kind, spherical):
+    rng = np.random.default_rng(hash((kind, spherical)) % 2 ** 32)
+    d, L = 96, 64
+    for _ in range(20):
+        C, q = data(rng, kind, d, L)
+        C = C.astype(np.float32)
+        q = q.astype(np.float32)
+        fp16 = np.abs(C).max() < 16384.0
+        if fp16 and np.abs(q).max() > 6.0e4:
+            continue  # the kernel gives no bound then (every list re-scored)
+        cn = (C.astype(np.float64) ** 2).sum(1)
+        cmax = np.float32(np.sqrt(np.float32(cn.max())))
+        qn = float(np.sqrt(np.float32((q.astype(np.float64) ** 2).sum())))
+        err = bound(qn, float(cmax), d, fp16, spherical)
+        qt, Ct = r16(q, fp16), r16(C, fp16)
+        exact = -(C.astype(np.float64) @ q) if spherical else cn - 2.0 * (C.astype(np.float64) @ q)
+        for pw in (False, True):
+            dot = np.array([dot_f32(Ct[i], qt, pw) for i in range(L)], dtype=np.float32)
+            if spherical:
+                given = -dot
+            else:
+                given = np.array([np.float32(np.float32(-2.0) * dot[i] + np.float32(cn[i])) for i in range(L)])
+            assert np.all(np.abs(given.astype(np.float64) - exact) <= err), (kind, fp16)
