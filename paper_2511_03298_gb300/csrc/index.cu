@@ -324,7 +324,7 @@ static int workspace_buffers(ksc_index* ix, Buffer** out) {
     Buffer* bufs[] = {&ix->ws_scores, &ix->ws_probes, &ix->ws_lut, &ix->ws_bias, &ix->ws_scale, &ix->ws_range,
                       &ix->ws_thr, &ix->ws_cnt, &ix->ws_cand, &ix->ws_topr, &ix->ws_nprobe, &ix->ws_rerank,
                       &ix->ws_items, &ix->ws_misc, &ix->ws_qbf16, &ix->ws_err, &ix->ws_feat, &ix->ws_rscore,
-                      &ix->ws_full, &ix->ws_topr2, &ix->ws_redo, &ix->ws_pprobes, &ix->ws_pn, &ix->ws_pprob, &ix->ws_qf};
+                      &ix->ws_full, &ix->ws_topr2, &ix->ws_flag, &ix->ws_redo, &ix->ws_pprobes, &ix->ws_pn, &ix->ws_pprob, &ix->ws_qf};
     const int n = (int)(sizeof(bufs) / sizeof(bufs[0]));
     for (int i = 0; i < n; ++i) out[i] = bufs[i];
     return n;
@@ -342,7 +342,8 @@ int free_index_memory(ksc_index* ix) {
                        ix->c_rank_f8_scale != s->c_rank_f8_scale ? ix->c_rank_f8_scale : nullptr,
                        ix->X_bf16 != s->X_bf16 ? ix->X_bf16 : nullptr, ix->X_fp8 != s->X_fp8 ? ix->X_fp8 : nullptr,
                        ix->X_scale != s->X_scale ? ix->X_scale : nullptr,
-                       ix->X_norm != s->X_norm ? ix->X_norm : nullptr};
+                       ix->X_band != s->X_band ? ix->X_band : nullptr,
+                       ix->X_u8 != s->X_u8 ? ix->X_u8 : nullptr};
         for (void* p : own)
             if (p) cudaFree(p);
         for (int i = 0; i < nb; ++i) release(*bufs[i]);
@@ -354,7 +355,7 @@ int free_index_memory(ksc_index* ix) {
                     ix->blk_ids, ix->blk_codes, ix->assign, ix->graph, ix->entry, ix->status, ix->stats,
                     ix->c_rank_bf16, ix->mlp_w, ix->blk_list, ix->nbr_pos, ix->nbr_codes, ix->entry_pos,
                     ix->X_bf16, ix->X_fp8, ix->X_scale, ix->pr_stats, ix->pr_vecs, ix->pr_model, ix->dims,
-                    ix->X_rr, ix->c_rank_f8, ix->c_rank_f8_scale, ix->gids, ix->X_norm};
+                    ix->X_rr, ix->c_rank_f8, ix->c_rank_f8_scale, ix->gids, ix->X_band, ix->X_u8};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < nb; ++i) release(*bufs[i]);

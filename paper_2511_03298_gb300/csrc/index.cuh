@@ -39,7 +39,9 @@ struct ksc_index {
     void* X_bf16 = nullptr;        // [n x d] BF16 rows (precision variant, made on first use)
     void* X_fp8 = nullptr;         // [n x d] FP8 e4m3 rows
     float* X_scale = nullptr;      // [n] their per-row scales
-    float* X_norm = nullptr;       // [n] upper bounds of the re-rank rows' norms (BF16 band, made on first use)
+    void* X_u8 = nullptr;          // [n x d] U8 rows when every coordinate is an integer in [0, 255] (exact)
+    int x_u8_state = 0;            // 0 not checked, 1 X_u8 holds the rows exactly, -1 they do not fit bytes
+    float2* X_band = nullptr;      // [n] per re-rank row: bounds of its norm and of its BF16 rounding error's norm (made on first use)
     int32_t* status = nullptr;     // device status word
     unsigned long long* stats = nullptr;  // [4] counters of the last search
     // host mirrors
@@ -82,7 +84,7 @@ struct ksc_index {
     int32_t launches = 0;
     // search workspace
     ksc::Buffer ws_scores, ws_probes, ws_lut, ws_bias, ws_scale, ws_range, ws_thr, ws_cnt,
-        ws_cand, ws_topr, ws_nprobe, ws_rerank, ws_items, ws_misc, ws_qbf16, ws_err, ws_feat, ws_rscore, ws_full, ws_topr2,
+        ws_cand, ws_topr, ws_nprobe, ws_rerank, ws_items, ws_misc, ws_qbf16, ws_err, ws_feat, ws_rscore, ws_full, ws_topr2, ws_flag,
         ws_redo, ws_pprobes, ws_pn, ws_pprob, ws_qf;
 };
 

@@ -2693,18 +2693,24 @@ __global__ void __launch_bounds__(NT) k_rerank(const float* __restrict__ Q, cons
 // the k best keys are then taken by k rounds of a warp minimum.  Same
 // distance rule as k_rerank (L2 direct difference squares, IP -<q, x>), FP32.
 //
-// With xb (BF16 copies of the rows) and xn (upper bounds of the rows' norms),
-// a first pass reads the BF16 rows (half the bytes) and bounds each
-// candidate's FP32 distance: |d~ - d| <= e, from the BF16 rounding
-// (|x~_t - x_t| <= 2^-8 |x_t|: BF16 carries 8 significant bits) and the FP32
-// evaluation of both sums (relative 2^-20, far above their ~11 rounding steps
-// of 2^-24):
-//   L2: e = 2 eps n s + (eps n)^2 + g (s^2 + (s + eps n)^2), s >= sqrt of the
-//       exact BF16-row distance; IP: e = |q| n (eps + 2.01 g);
-// eps = 2^-8, g = 2^-20, n the row's norm bound, all evaluated with a factor
-// (1 + 2^-10) and directed rounding of d~ -/+ e.  U is the k-th smallest
-// d~ + e; a candidate with d~ - e > U has an FP32 distance above k FP32
-// distances, so it cannot be among the k best.  The others get the FP32
+// With xb (BF16 copies of the rows; or xu, U8 copies, when every coordinate
+// is an integer in [0, 255] and a byte holds it exactly) and xe (per row:
+// n >= |x| and r >= |x~ - x|, the norm of its rounding error, both from FP64
+// sums rounded up), a first pass reads the low-precision rows (half or a
+// quarter of the bytes) and bounds
+// each candidate's FP32 distance: |d~ - d| <= e, from the rounding of the row
+// (|<v, x~ - x>| <= |v| r) and the FP32 evaluation of both sums (relative
+// g = 2^-20, above the at most 14 rounding steps of 2^-24 on a term's path in
+// either pass):
+//   L2: e = 2 r s + r^2 + g (s^2 + (s + r)^2), s >= sqrt of the exact
+//       BF16-row distance (so s + r >= |q - x|);
+//   IP: e = |q| (r + 2.01 g (n + r)),
+// all evaluated with a factor (1 + 2^-10) and directed rounding of d~ -/+ e.
+// r is the row's own rounding error, not the format's worst case
+// (2^-8 |x|): a row that BF16 holds exactly (integer coordinates up to 256,
+// say) has r = 0 and a band of the evaluation term alone.  U is the k-th
+// smallest d~ + e; a candidate with d~ - e > U has an FP32 distance above k
+// FP32 distances, so it cannot be among the k best.  The others get the FP32
 // distance by the very code of the plain pass (a row's sum does not depend on
 // the rows beside it in the exchange), so the result is bit for bit the
 // plain pass's.
@@ -2760,46 +2766,66 @@ __device__ __forceinline__ float rerank_rows8(const float4& qv, const float* __r
     return exchange_rows8(a, lane);
 }
 
-// The distance terms of 16 BF16 rows idv[] (-1: none) at once (the rows are
-// half as wide, so twice as many are in flight as in the FP32 pass): lane l
-// reads coordinates 4l..4l+3 of each row in one 8-byte load; a halving
-// exchange over lane bits 4..1 leaves row (lane >> 1) & 15 in both lanes of a
-// pair.  Only bounded, not compared bit for bit, so the summation order is
-// free.
-__device__ __forceinline__ float rerank_rows16_bf16(const float4& qv, const uint16_t* __restrict__ xb, int d, int ip,
-                                                    bool inl, const int32_t (&idv)[16], int lane) {
-    uint2 r[16];
+// The distance terms of 16 low-precision rows at once, 8 lanes per row:
+// lane l = 8 h + j takes rows 4 h .. 4 h + 3 of the step (idv[], -1: none)
+// and, of each, the 4-coordinate chunks j, j + 8, j + 16, j + 24 below d (one
+// load each: 8 bytes of BF16, or 4 bytes of U8 rows; qv[] holds the query's
+// coordinates of those chunks), summed in FP32 pairs; a halving exchange over
+// lane bits 2, 1 and a sum over bit 0 leave row (lane >> 1) & 15 in both
+// lanes of a pair.  The row's id, address and exchange cost one lane in
+// eight, not every lane.  Only bounded, not compared bit for bit, so the
+// summation order is free (its depth, at most 8 + 1 + 3 additions after the
+// square, stays inside the bound's g).  A U8 byte b becomes the float
+// (2^23 + b) - 2^23, exact.
+template <bool U8>
+__device__ __forceinline__ float rerank_rows16_band(const float4 (&qv)[4], const void* __restrict__ rows, int d,
+                                                    int ip, int nch, const int32_t (&idv)[4], int lane) {
+    const int j = lane & 7;
+    uint2 r[4][4];
 #pragma unroll
-    for (int u = 0; u < 16; ++u)
-        r[u] = (idv[u] >= 0 && inl) ? __ldg(reinterpret_cast<const uint2*>(xb + (int64_t)idv[u] * d) + lane)
-                                    : make_uint2(0u, 0u);
-    float a[16];
-    const float2 q01 = make_float2(qv.x, qv.y), q23 = make_float2(qv.z, qv.w);
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int u = 0; u < 16; ++u) {
-        const float2 x01 = make_float2(__uint_as_float(r[u].x << 16), __uint_as_float(r[u].x & 0xffff0000u));
-        const float2 x23 = make_float2(__uint_as_float(r[u].y << 16), __uint_as_float(r[u].y & 0xffff0000u));
-        // packed pairs: two coordinates per instruction (each half an FP32 operation)
-        float2 t;
-        if (ip) {
-            t = f2_fma(q23, x23, f2_mul(q01, x01));
-        } else {
-            const float2 e01 = f2_sub(q01, x01), e23 = f2_sub(q23, x23);
-            t = f2_fma(e23, e23, f2_mul(e01, e01));
+        for (int k = 0; k < 4; ++k) {
+            const bool ok = k < nch && idv[i] >= 0 && 4 * (j + 8 * k) < d;
+            if (U8)
+                r[i][k] = make_uint2(ok ? __ldg(reinterpret_cast<const uint32_t*>(
+                                              static_cast<const uint8_t*>(rows) + (int64_t)idv[i] * d) + j + 8 * k)
+                                        : 0u, 0u);
+            else
+                r[i][k] = ok ? __ldg(reinterpret_cast<const uint2*>(static_cast<const uint16_t*>(rows) +
+                                                                    (int64_t)idv[i] * d) + j + 8 * k)
+                             : make_uint2(0u, 0u);
         }
-        a[u] = t.x + t.y;
-    }
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const bool up = lane & 16;
-        const float send = up ? a[i] : a[i + 8], keep = up ? a[i + 8] : a[i];
-        a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-    }
+    float a[4];
+    const float2 m23 = make_float2(8388608.f, 8388608.f);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        const bool up = lane & 8;
-        const float send = up ? a[i] : a[i + 4], keep = up ? a[i + 4] : a[i];
-        a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (k >= nch) break;  // warp-uniform
+            float2 x01, x23;
+            if (U8) {
+                const uint32_t w = r[i][k].x;
+                x01 = f2_sub(make_float2(__uint_as_float(prmt(w, 0x4B000000u, 0x7540u)),
+                                         __uint_as_float(prmt(w, 0x4B000000u, 0x7541u))), m23);
+                x23 = f2_sub(make_float2(__uint_as_float(prmt(w, 0x4B000000u, 0x7542u)),
+                                         __uint_as_float(prmt(w, 0x4B000000u, 0x7543u))), m23);
+            } else {
+                x01 = make_float2(__uint_as_float(r[i][k].x << 16), __uint_as_float(r[i][k].x & 0xffff0000u));
+                x23 = make_float2(__uint_as_float(r[i][k].y << 16), __uint_as_float(r[i][k].y & 0xffff0000u));
+            }
+            const float2 q01 = make_float2(qv[k].x, qv[k].y), q23 = make_float2(qv[k].z, qv[k].w);
+            if (ip) {
+                acc = f2_fma(q01, x01, acc);
+                acc = f2_fma(q23, x23, acc);
+            } else {
+                const float2 e01 = f2_sub(q01, x01), e23 = f2_sub(q23, x23);
+                acc = f2_fma(e01, e01, acc);
+                acc = f2_fma(e23, e23, acc);
+            }
+        }
+        a[i] = acc.x + acc.y;
     }
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
@@ -2816,13 +2842,16 @@ __device__ __forceinline__ float rerank_rows16_bf16(const float4& qv, const uint
     return a[0];
 }
 
+// U8: the band's rows are U8 (xu), else BF16 (xb).
+template <bool U8>
 __global__ void __launch_bounds__(RW_WARPS * 32) k_rerank_w(const float* __restrict__ Q, const float* __restrict__ X,
                                                             int d, int ip, const uint64_t* __restrict__ topr,
                                                             int Rmax, const int32_t* __restrict__ rerank_q, int Rfix,
                                                             int k, int64_t nq, int64_t* __restrict__ out_ids,
                                                             float* __restrict__ out_d,
                                                             const uint16_t* __restrict__ xb,
-                                                            const float* __restrict__ xn) {
+                                                            const uint8_t* __restrict__ xu,
+                                                            const float2* __restrict__ xe) {
     // RW_WARPS x Rmax keys; with xb also RW_WARPS x Rmax bound pairs and RW_WARPS x (Rmax + 64) words
     extern __shared__ uint64_t wkeys[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -2887,11 +2916,11 @@ __global__ void __launch_bounds__(RW_WARPS * 32) k_rerank_w(const float* __restr
             }
         }
     };
-    if (xb && R > k) {
+    if ((xb || xu) && R > k) {
         float2* band = reinterpret_cast<float2*>(wkeys + (size_t)RW_WARPS * Rmax) + (size_t)w * Rmax;
         uint32_t* sv = reinterpret_cast<uint32_t*>(wkeys + (size_t)2 * RW_WARPS * Rmax) + (size_t)w * (Rmax + 64);
         uint32_t* kv = sv + Rmax;  // the small selection's values
-        const float eps = 0x1p-8f, g = 0x1p-20f, safe = 1.f + 0x1p-10f;
+        const float g = 0x1p-20f, safe = 1.f + 0x1p-10f;
         float qn = 0.f;  // IP: an upper bound of |q|
         if (ip) {
             float t = fmaf(qv.x, qv.x, fmaf(qv.y, qv.y, fmaf(qv.z, qv.z, qv.w * qv.w)));
@@ -2899,31 +2928,50 @@ __global__ void __launch_bounds__(RW_WARPS * 32) k_rerank_w(const float* __restr
             for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
             qn = sqrtf(t) * (1.f + 0x1p-18f);
         }
-        const int myrow16 = (lane >> 1) & 15;
-        for (int c0 = 0; c0 < R; c0 += 16) {
-            int32_t idv[16];
+        // this lane's query chunks for the 8-lanes-per-row BF16 pass
+        const int nch = (d + 31) >> 5;
+        float4 qc[4];
 #pragma unroll
-            for (int u = 0; u < 16; ++u) idv[u] = id_of(c0 + u);
-            // this lane's row norm bound, loaded beside the rows
+        for (int h = 0; h < 4; ++h) {
+            const int t0 = 4 * ((lane & 7) + 8 * h);
+            qc[h] = t0 < d ? make_float4(Q[q * d + t0], Q[q * d + t0 + 1], Q[q * d + t0 + 2], Q[q * d + t0 + 3])
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        const int myrow16 = (lane >> 1) & 15;
+        // the candidates' ids (-1: none) to 16 past R, in sv until the
+        // survivors replace them: one shared load per row and step
+        const int R16 = (R + 15) & ~15;
+        for (int c = lane; c < R16; c += 32) sv[c] = (uint32_t)id_of(c);
+        __syncwarp();
+        for (int c0 = 0; c0 < R; c0 += 16) {
+            int32_t idv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) idv[i] = (int32_t)sv[c0 + 4 * (lane >> 3) + i];
+            // this lane's row bounds, loaded beside the rows
             const int c = c0 + myrow16;
-            const int32_t id = c < R ? id_of(c) : -1;
-            const float nb = id >= 0 ? __ldg(xn + id) : 0.f;
-            const float a0 = rerank_rows16_bf16(qv, xb, d, ip, inl, idv, lane);
+            const int32_t id = (int32_t)sv[c];
+            const float2 nr = id >= 0 ? __ldg(xe + id) : make_float2(0.f, 0.f);
+            const float a0 = U8 ? rerank_rows16_band<true>(qc, xu, d, ip, nch, idv, lane)
+                                : rerank_rows16_band<false>(qc, xb, d, ip, nch, idv, lane);
             if ((lane & 1) == 0 && c < R) {
                 float lo = INFINITY, hi = INFINITY;
                 if (id >= 0) {
-                    const float n = nb + 0x1p-100f;  // (+ BF16's subnormal spacing, summed over d)
+                    const float n = nr.x, r = nr.y;
                     float e, dt;
                     if (ip) {
                         dt = -a0;
-                        e = qn * n * (eps + 2.01f * g) * safe;
+                        e = qn * (r + 2.01f * g * (n + r)) * safe;
                     } else {
                         dt = a0;
-                        const float sq = sqrtf(fmaxf(dt, 0.f) * (1.f + 2.f * g)) * (1.f + 0x1p-20f), en = eps * n;
-                        e = (2.f * en * sq + en * en + g * (sq * sq + (sq + en) * (sq + en))) * safe;
+                        const float sq = sqrtf(fmaxf(dt, 0.f) * (1.f + 2.f * g)) * (1.f + 0x1p-20f);
+                        e = (2.f * r * sq + r * r + g * (sq * sq + (sq + r) * (sq + r))) * safe;
                     }
                     lo = __fsub_rd(dt, e);
                     hi = __fadd_ru(dt, e);
+                    if (!(lo <= hi)) {  // a NaN: no bound, the candidate is read in FP32
+                        lo = -INFINITY;
+                        hi = INFINITY;
+                    }
                 }
                 band[c] = make_float2(lo, hi);
             }
@@ -2973,20 +3021,50 @@ __global__ void __launch_bounds__(RW_WARPS * 32) k_rerank_w(const float* __restr
     }
 }
 
-// Upper bounds of the rows' norms: sqrt of the FP64 sum of squares, rounded
-// up to FP32.  A warp per row.
-__global__ void k_row_norms(const float* __restrict__ X, int64_t n, int d, float* __restrict__ out) {
+// Per row of X and of its low-precision copy (BF16 xb, or U8 xu): (an upper
+// bound of |x|, an upper bound of |x~ - x|), each the sqrt of an FP64 sum of
+// squares rounded up to FP32 (x~ - x is exact in FP64).  A row the copy holds
+// exactly gets r = 0; a row with a non-finite coordinate gets r = +inf (every
+// bound infinite).  A warp per row.
+__global__ void k_band_rows(const float* __restrict__ X, const uint16_t* __restrict__ xb,
+                            const uint8_t* __restrict__ xu, int64_t n, int d, float2* __restrict__ out) {
     const int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (r >= n) return;
-    double s = 0.0;
+    double s = 0.0, e = 0.0;
     for (int t = lane; t < d; t += 32) {
         const double v = X[r * d + t];
+        const double w = xu ? (double)xu[r * d + t] : (double)__uint_as_float((uint32_t)xb[r * d + t] << 16);
         s += v * v;
+        e += (v - w) * (v - w);
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) out[r] = __double2float_ru(sqrt(s) * (1.0 + 0x1p-40));
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        e += __shfl_xor_sync(0xffffffffu, e, o);
+    }
+    if (lane == 0) {
+        float nb = __double2float_ru(sqrt(s) * (1.0 + 0x1p-40));
+        float rb = e == 0.0 ? 0.f : __double2float_ru(sqrt(e) * (1.0 + 0x1p-40));
+        if (!(nb < INFINITY) || !(rb < INFINITY)) nb = rb = INFINITY;
+        out[r] = make_float2(nb, rb);
+    }
+}
+
+// Clears *ok unless every element of X [m] is an integer in [0, 255] (a
+// byte holds it exactly; -0 counts as 0).
+__global__ void k_bytes_exact(const float* __restrict__ X, int64_t m, int32_t* __restrict__ ok) {
+    bool all = true;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const float v = X[i];
+        all &= v >= 0.f && v <= 255.f && v == rintf(v);
+    }
+    if (!__all_sync(0xffffffffu, all) && (threadIdx.x & 31) == 0) atomicAnd(ok, 0);
+}
+
+__global__ void k_x_u8(const float* __restrict__ X, int64_t m, uint8_t* __restrict__ xu) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        xu[i] = (uint8_t)X[i];
 }
 
 // ------------------------------------------------------------------ precision variant
@@ -3325,13 +3403,38 @@ static int ensure_lowp(ksc_index* ix, int prec, cudaStream_t st) {
     return KSC_OK;
 }
 
-// The BF16 band of the exact re-rank: BF16 rows and the rows' norm bounds,
-// made on first use.
+// The band of the exact re-rank, made on first use: U8 copies of the rows
+// when every coordinate is an integer in [0, 255] (checked once; exact, a
+// quarter of the FP32 bytes), else BF16 copies; and the rows' bounds (norm,
+// rounding error).
 static int ensure_band(ksc_index* ix, cudaStream_t st) {
-    KSC_TRY(ensure_lowp(ix, 1, st));
-    if (!ix->X_norm) {
-        KSC_CUDA(cudaMalloc(&ix->X_norm, sizeof(float) * ix->n));
-        k_row_norms<<<(unsigned)((ix->n + 7) / 8), 256, 0, st>>>(rr_X(ix), ix->n, rr_d(ix), ix->X_norm);
+    const int64_t m = ix->n * (int64_t)rr_d(ix);
+    if (ix->x_u8_state == 0) {
+        KSC_TRY(ensure(ix->ws_flag, sizeof(int32_t), st));
+        int32_t* ok = (int32_t*)ix->ws_flag.p;
+        const int32_t one = 1;
+        KSC_CUDA(cudaMemcpyAsync(ok, &one, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        k_bytes_exact<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, 8 * (int64_t)num_sms())),
+                        256, 0, st>>>(rr_X(ix), m, ok);
+        KSC_LAUNCH_CHECK();
+        int32_t h = 0;
+        KSC_CUDA(cudaMemcpyAsync(&h, ok, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        KSC_CUDA(cudaStreamSynchronize(st));
+        ix->x_u8_state = (h && m > 0) ? 1 : -1;
+        if (ix->x_u8_state == 1 && !ix->X_u8) {
+            KSC_CUDA(cudaMalloc(&ix->X_u8, (size_t)m));
+            k_x_u8<<<(unsigned)std::min<int64_t>((m + 255) / 256, 8 * (int64_t)num_sms()), 256, 0, st>>>(
+                rr_X(ix), m, (uint8_t*)ix->X_u8);
+            KSC_LAUNCH_CHECK();
+        }
+    }
+    const bool u8 = ix->x_u8_state == 1;
+    if (!u8) KSC_TRY(ensure_lowp(ix, 1, st));
+    if (!ix->X_band) {
+        KSC_CUDA(cudaMalloc(&ix->X_band, sizeof(float2) * ix->n));
+        k_band_rows<<<(unsigned)((ix->n + 7) / 8), 256, 0, st>>>(
+            rr_X(ix), u8 ? nullptr : (const uint16_t*)ix->X_bf16, u8 ? (const uint8_t*)ix->X_u8 : nullptr, ix->n,
+            rr_d(ix), ix->X_band);
         KSC_LAUNCH_CHECK();
     }
     return KSC_OK;
@@ -3598,10 +3701,12 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
         if (band) KSC_TRY(ensure_band(ix, st));
         const size_t smem = sizeof(uint64_t) * RW_WARPS * rr_R * (band ? 2 : 1) +
                             (band ? sizeof(uint32_t) * RW_WARPS * (rr_R + 64) : 0);
-        cudaFuncSetAttribute(k_rerank_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_rerank_w<<<(unsigned)((nq + RW_WARPS - 1) / RW_WARPS), RW_WARPS * 32, smem, st>>>(
+        auto kr = band && ix->x_u8_state == 1 ? k_rerank_w<true> : k_rerank_w<false>;
+        cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kr<<<(unsigned)((nq + RW_WARPS - 1) / RW_WARPS), RW_WARPS * 32, smem, st>>>(
             Qr, Xr, dr, ix->metric == KSC_IP, rr_keys, rr_R, rr_q, rr_R, pl.k, nq, ids, dists,
-            band ? (const uint16_t*)ix->X_bf16 : nullptr, band ? ix->X_norm : nullptr);
+            band && ix->x_u8_state != 1 ? (const uint16_t*)ix->X_bf16 : nullptr,
+            band && ix->x_u8_state == 1 ? (const uint8_t*)ix->X_u8 : nullptr, band ? ix->X_band : nullptr);
         ix->launches++;
         KSC_LAUNCH_CHECK();
     } else {
@@ -3796,9 +3901,9 @@ int rerank_keys(ksc_index* ix, const float* Q, int64_t nq, int k, const uint64_t
     const int ip = ix->metric == KSC_IP;
     if (k <= 32 && R <= RW_MAXR && dr <= 128 && (dr & 3) == 0 && warp_per_query(nq)) {
         const size_t smem = sizeof(uint64_t) * RW_WARPS * R;
-        KSC_CUDA(cudaFuncSetAttribute(k_rerank_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_rerank_w<<<(unsigned)((nq + RW_WARPS - 1) / RW_WARPS), RW_WARPS * 32, smem, st>>>(
-            Q, Xr, dr, ip, keys, R, nullptr, R, k, nq, ids, dists, nullptr, nullptr);
+        KSC_CUDA(cudaFuncSetAttribute(k_rerank_w<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_rerank_w<false><<<(unsigned)((nq + RW_WARPS - 1) / RW_WARPS), RW_WARPS * 32, smem, st>>>(
+            Q, Xr, dr, ip, keys, R, nullptr, R, k, nq, ids, dists, nullptr, nullptr, nullptr);
     } else {
         const size_t smem = sizeof(uint64_t) * pow2_ceil(R < 2 ? 2 : R);
         if (nq < 2 * (int64_t)num_sms()) {

@@ -483,13 +483,15 @@ def test_tied_list_scores_take_the_general_selection(torch, ksc):
     assert g.last_status() == 0
 
 
-@pytest.mark.parametrize("kind", ["l2", "ip", "m50"])
+@pytest.mark.parametrize("kind", ["l2", "ip", "m50", "small"])
 def test_bf16_band_rerank_equals_fp32_rerank(torch, ksc, kind):
     """The exact re-rank's BF16 band (BF16 rows bound every candidate's FP32
     distance; only candidates whose lower bound reaches the k-th upper bound
     are read in FP32) returns what reading every candidate in FP32 returns,
     for L2 and inner products, several k and R, a fixed and a per-query R,
-    in the warp-per-query shape (1600 queries)."""
+    in the warp-per-query shape (1600 queries); rows of real values (d = 64,
+    48, 100: BF16 rows) and integer rows in [0, 255] (the 10k x 128 set: U8
+    rows, exact, whose band is the FP32 evaluation term alone)."""
     ix, Q = small_index(kind)
     g = gpu_index(ksc, ix)
     reps = 1600 // len(Q) + 1
