@@ -653,16 +653,17 @@ def run_ours(args, rank, ws):
                          else round(SCAN_TRAFFIC_BYTES[nprobe] / (CFG["n"] * CFG["M"] / 2), 2)},
             # re-rank of the plain step: R gathered rows of d floats per query
             # (algorithmic bytes; an effective rate, some rows hit L2).  With
-            # the BF16 band (the default for L2) most candidates are read as
-            # BF16 rows, half the bytes, so the effective rate exceeds the
-            # copy peak: the band's gain, not a bandwidth
+            # the band (the default for L2) every candidate is first read as
+            # a low-precision row (U8 here: the rows are integers in
+            # [0, 255], held exactly; else BF16), so the effective rate
+            # exceeds the copy peak: the band's gain, not a bandwidth
             "rerank_hbm": {"algorithmic_bytes": rr_bytes, "ms": round(rr_ms, 4) if rr_ms > 0 else None,
                            "effective_GBps": None if rr_rate is None else round(rr_rate, 1),
                            "effective_frac_of_hbm": None if rr_rate is None else
                            round(rr_rate / peaks.get("hbm_gbs", 6800.0), 4),
-                           "bf16_band": True,
-                           "bytes_note": "algorithmic = every candidate's FP32 row; the band reads BF16 rows "
-                                         "(d 2 bytes) of all and FP32 rows of those its bound keeps"},
+                           "band": "u8 rows (exact) or bf16 rows, then fp32 rows of the candidates kept",
+                           "bytes_note": "algorithmic = every candidate's FP32 row; the band reads U8 rows "
+                                         "(d bytes) of all and FP32 rows of those its bound keeps"},
             "scan_stream": stream,
             "rank_gemm": gemm,
             "scan_tc": tcs,
