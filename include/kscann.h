@@ -159,13 +159,17 @@ typedef struct {
                                   re-scored exactly, so the ranking is the same (rank_fp32 wins
                                   when both are set) */
     int32_t rerank_band;       /* exact FP32 re-rank (precision 0, k <= 32, d <= 128): 1 first reads
-                                  BF16 copies of the candidate rows and bounds each FP32 distance
-                                  (BF16 rounding plus FP32 evaluation error); only candidates whose
-                                  lower bound is at most the k-th smallest upper bound are read in
-                                  FP32, so the results are those of the plain pass; -1 every
-                                  candidate in FP32; 0 auto: the band for L2 indexes.  The BF16
-                                  rows (n d 2 bytes) and norm bounds (n 4 bytes) are made on
-                                  first use */
+                                  low-precision copies of the candidate rows and bounds each FP32
+                                  distance (the row's own rounding error plus FP32 evaluation
+                                  error); only candidates whose lower bound is at most the k-th
+                                  smallest upper bound are read in FP32, so the results are those
+                                  of the plain pass; -1 every candidate in FP32; 0 auto: the band
+                                  for L2 indexes.  The copies are made on first use: U8 rows
+                                  (n d bytes, exact) when every re-rank coordinate is an integer
+                                  in [0, 255], else BF16 rows (n d 2 bytes), and two bounds per
+                                  row (n 8 bytes).  That first use synchronises the stream once
+                                  (the check's result is read on the host), so run one banded
+                                  search before capturing the stream in a graph */
 } ksc_search_opts;
 
 /* k nearest neighbours of Q_dev [nq x d] with a fixed nprobe (1..nlist) and

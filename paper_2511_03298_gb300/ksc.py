@@ -170,9 +170,10 @@ def search_opts(lanes_per_query=0, hybrid=False, n_near=2, efs=64, tau=8, cand_c
     """precision: 0 FP32 re-rank; 1 BF16 / 2 FP8 first re-rank of the widened
     shortlist, then FP32 over the best rerank_final.  scan_tc: the scan on
     the tensor cores (same keys).  rank_fp8: list scores from FP8 operands
-    (same ranking).  rerank_band: 1 the exact re-rank reads BF16 rows first
-    and FP32 rows only where its bound cannot exclude a candidate (same
-    results), -1 FP32 rows of every candidate, 0 auto (the band for L2)."""
+    (same ranking).  rerank_band: 1 the exact re-rank reads U8 rows (exact,
+    when every coordinate is an integer in [0, 255]) or BF16 rows first and
+    FP32 rows only where its bound cannot exclude a candidate (same results),
+    -1 FP32 rows of every candidate, 0 auto (the band for L2)."""
     return SearchOpts(lanes_per_query, int(hybrid), n_near, efs, tau, cand_cap, int(rank_fp32), precision,
                       rerank_final, tile_blocks, int(scan_tc), int(rank_fp8), int(rerank_band))
 
