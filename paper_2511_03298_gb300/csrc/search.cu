@@ -3194,7 +3194,7 @@ struct Plan {
     bool hybrid;
     int n_near, efs, tau;
     int prec, Rf;  // precision variant: first re-rank of R (= Rmax) in prec, then FP32 of the best Rf
-    bool band;     // exact re-rank with the BF16 band (k_rerank_w)
+    bool band;     // exact re-rank with the band of U8 / BF16 rows (k_rerank_w)
     int Pq_max;    // bound on the per-query nprobe (<= Pmax)
     bool tc;       // scan on the tensor cores (k_scan_tc)
     int nt;        // its queries per item
@@ -3781,8 +3781,9 @@ static int make_plan(ksc_index* ix, int64_t nq, int k, int Pmax, int Rmax, const
     pl.rank_mode = (opts && opts->rank_fp32) ? RANK_FP32 : ((opts && opts->rank_fp8) ? RANK_FP8 : RANK_TC16);
     pl.Pq_max = Pmax;
     pl.prec = opts ? opts->precision : 0;
-    // the BF16 band: on by default for L2 (for inner products the band is
-    // wide against the gaps between the best scores)
+    // the re-rank band: on by default for L2 (for inner products of
+    // real-valued rows the BF16 band is wide against the gaps between the
+    // best scores)
     pl.band = opts && opts->rerank_band != 0 ? opts->rerank_band > 0 : ix->metric != KSC_IP;
     KSC_CHECK_ARG(pl.prec >= 0 && pl.prec <= 2, "precision must be 0 (FP32), 1 (BF16) or 2 (FP8)");
     pl.Rf = pl.Rmax;

@@ -1,4 +1,4 @@
-"""The exact re-rank's BF16 band: the bound on |d~ - d| it relies on.
+"""The exact re-rank's band: the bound on |d~ - d| it relies on.
 
 The re-rank may skip a candidate's FP32 distance d when a distance d~
 computed in FP32 from the BF16-rounded row, widened by a bound e, already
