@@ -10,8 +10,9 @@ element is below 2^14, else BF16):
 -- and checks it against scores evaluated as the kernel does (operands
 rounded to 16 bits, the dot product summed in FP32 in two orders, L2 as
 FP32 ||c||^2 - 2 dot by one FMA) on random and adversarial data: tiny
-magnitudes (FP16 subnormals), wide dynamic range, and rows near the FP16
-limit.
+magnitudes (FP16 subnormals), wide dynamic range, rows near the FP16 limit,
+and rows whose every element rounds up by nearly u with the query aligned
+(FP16 and BF16), which come within a few percent of the bound.
 """
 import numpy as np
 import pytest
@@ -57,14 +58,24 @@ def data(rng, kind, d, L):
             rng.normal(size=d) * 10.0 ** rng.uniform(-8, 2, size=d)
     if kind == "big":  # centroids near the FP16 limit (BF16 then)
         return rng.uniform(-2e4, 2e4, size=(L, d)), rng.uniform(-1e3, 1e3, size=d)
+    if kind in ("aligned", "aligned_bf16"):
+        # every element just above a halfway point, so it rounds up by nearly
+        # u (FP16: 1 + 2^-11 + 2^-20 -> 1 + 2^-10; BF16: 1 + 2^-8 + 2^-16 ->
+        # 1 + 2^-7), and the query aligned with row 0, the largest row: the
+        # operand term 2u + u^2 is nearly attained
+        m, scale = (1 + 2.0 ** -11 + 2.0 ** -20, 1.0) if kind == "aligned" else (1 + 2.0 ** -8 + 2.0 ** -16, 2.0 ** 15)
+        C = rng.choice([-1.0, 1.0], size=(L, d)) * m * scale * 2.0 ** rng.integers(-4, 1, size=(L, 1))
+        C[0] = np.sign(C[0]) * m * scale
+        return C, np.sign(C[0]) * m * scale  # |q| = |c_0|: the norm term stays small beside it
     raise ValueError(kind)
 
 
-@pytest.mark.parametrize("kind", ["normal", "tiny", "range", "big"])
+@pytest.mark.parametrize("kind", ["normal", "tiny", "range", "big", "aligned", "aligned_bf16"])
 @pytest.mark.parametrize("spherical", [False, True])
 def test_16bit_score_bound_holds(kind, spherical):
     rng = np.random.default_rng(hash((kind, spherical)) % 2 ** 32)
     d, L = 96, 64
+    worst = 0.0
     for _ in range(20):
         C, q = data(rng, kind, d, L)
         C = C.astype(np.float32)
@@ -84,4 +95,9 @@ def test_16bit_score_bound_holds(kind, spherical):
                 given = -dot
             else:
                 given = np.array([np.float32(np.float32(-2.0) * dot[i] + np.float32(cn[i])) for i in range(L)])
-            assert np.all(np.abs(given.astype(np.float64) - exact) <= err), (kind, fp16)
+            dev = np.abs(given.astype(np.float64) - exact)
+            assert np.all(dev <= err), (kind, fp16)
+            worst = max(worst, float(dev.max() / err))
+    if kind.startswith("aligned"):  # the operand term nearly attained: u halved fails
+        assert fp16 == (kind == "aligned")
+        assert worst > 0.75, worst
