@@ -3420,13 +3420,13 @@ static int ensure_band(ksc_index* ix, cudaStream_t st) {
         int32_t h = 0;
         KSC_CUDA(cudaMemcpyAsync(&h, ok, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         KSC_CUDA(cudaStreamSynchronize(st));
-        ix->x_u8_state = (h && m > 0) ? 1 : -1;
-        if (ix->x_u8_state == 1 && !ix->X_u8) {
+        if (h && m > 0 && !ix->X_u8) {
             KSC_CUDA(cudaMalloc(&ix->X_u8, (size_t)m));
             k_x_u8<<<(unsigned)std::min<int64_t>((m + 255) / 256, 8 * (int64_t)num_sms()), 256, 0, st>>>(
                 rr_X(ix), m, (uint8_t*)ix->X_u8);
             KSC_LAUNCH_CHECK();
         }
+        ix->x_u8_state = (h && m > 0) ? 1 : -1;  // only once the copy exists
     }
     const bool u8 = ix->x_u8_state == 1;
     if (!u8) KSC_TRY(ensure_lowp(ix, 1, st));
