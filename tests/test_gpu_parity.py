@@ -508,3 +508,25 @@ def test_bf16_band_rerank_equals_fp32_rerank(torch, ksc, kind):
     d = g.search_varprobe(Qd, 10, npb, rr, nprobe_max=12, rerank_max=150, opts=off)
     assert torch.equal(c[0], d[0]) and torch.equal(c[1], d[1])
     assert g.last_status() == 0
+
+
+@pytest.mark.parametrize("bump", ["frac", "256", "neg"])
+def test_band_on_rows_that_do_not_fit_bytes(torch, ksc, bump):
+    """Integer rows with a few coordinates moved out of what a byte holds (a
+    fraction 0.3 that BF16 cannot hold either, the value 256, the value -1)
+    take the BF16 band, with a rounding-error bound of 0 for the rows BF16
+    still holds exactly; the results are still those of the FP32 re-rank."""
+    ix, Q = small_index("small")
+    rng = np.random.default_rng({"frac": 21, "256": 22, "neg": 23}[bump])
+    X = np.array(ix["X"], dtype=np.float32, copy=True)
+    rows = rng.choice(len(X), 300, replace=False)
+    cols = rng.integers(0, X.shape[1], len(rows))
+    X[rows, cols] = {"frac": X[rows, cols] + 0.3, "256": 256.0, "neg": -1.0}[bump]
+    g = gpu_index(ksc, dict(ix, X=X))
+    Qd = torch.from_numpy(np.tile(Q, (1600 // len(Q) + 1, 1))).cuda()
+    on, off = ksc.search_opts(rerank_band=1), ksc.search_opts(rerank_band=-1)
+    for k, R in ((10, 100), (32, 200)):
+        a = g.search(Qd, k, 9, R, opts=on)
+        b = g.search(Qd, k, 9, R, opts=off)
+        assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]), (bump, k, R)
+    assert g.last_status() == 0
