@@ -118,7 +118,7 @@ def cases(rng, d):
 
 
 @pytest.mark.parametrize("d", [16, 100, 128])
-def test_bf16_band_bound_holds(d):
+def test_band_bound_holds(d):
     rng = np.random.default_rng(d)
     worst = 0.0
     for _ in range(60):

@@ -484,7 +484,7 @@ def test_tied_list_scores_take_the_general_selection(torch, ksc):
 
 
 @pytest.mark.parametrize("kind", ["l2", "ip", "m50", "small"])
-def test_bf16_band_rerank_equals_fp32_rerank(torch, ksc, kind):
+def test_band_rerank_equals_fp32_rerank(torch, ksc, kind):
     """The exact re-rank's band (U8 or BF16 rows bound every candidate's FP32
     distance; only candidates whose lower bound reaches the k-th upper bound
     are read in FP32) returns what reading every candidate in FP32 returns,
