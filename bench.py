@@ -866,7 +866,8 @@ def glove_workload(torch, ksc, synth, dev, flush):
 
 
 def measured_peaks():
-    """The measured peaks of the GB300s, else the fallback."""
+    """Measured GB300 peaks (copy bandwidth, BF16 GEMM) from MEASURED_PEAKS.json,
+    else fixed fallback figures."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         pk = json.load(open(path))
