@@ -202,7 +202,10 @@ def test_rank_lists_within_fp32_tolerance(torch, ksc, kind):
         # every returned list is within rounding of the oracle's P-th score
         assert np.all(exact[probes[qi]] <= ref_s[-1] + tol)
         np.testing.assert_allclose(scores[qi], exact[probes[qi]], rtol=1e-4, atol=tol)
-        assert (probes[qi] == ref).mean() >= 0.75
+        # the same list at every rank, except where two lists' exact scores
+        # are within rounding of each other (an FP32 near-tie may swap them)
+        same = probes[qi] == ref
+        assert np.all(same | (np.abs(exact[probes[qi]] - exact[ref]) <= 2 * tol)), (qi, probes[qi], ref)
 
 
 @pytest.mark.parametrize("kind", ["l2", "ip", "small"])
