@@ -3685,7 +3685,7 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
         KSC_TRY(ensure(ix->ws_topr2, sizeof(uint64_t) * nq * pl.Rf, st));
         uint64_t* topr2 = (uint64_t*)ix->ws_topr2.p;
         const size_t smem = sizeof(uint64_t) * pow2_ceil(pl.Rmax < 2 ? 2 : pl.Rmax);
-        cudaFuncSetAttribute(k_rerank_lowp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        KSC_CUDA(cudaFuncSetAttribute(k_rerank_lowp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_rerank_lowp<<<(unsigned)nq, 256, smem, st>>>(Qr, dr, ix->metric == KSC_IP, pl.prec,
                                                        (const uint16_t*)ix->X_bf16, (const uint8_t*)ix->X_fp8,
                                                        ix->X_scale, topr, pl.Rmax, pl.rerank_q, pl.Rfix, pl.k, pl.Rf,
@@ -3702,7 +3702,7 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
         const size_t smem = sizeof(uint64_t) * RW_WARPS * rr_R * (band ? 2 : 1) +
                             (band ? sizeof(uint32_t) * RW_WARPS * (rr_R + 64) : 0);
         auto kr = band && ix->x_u8_state == 1 ? k_rerank_w<true> : k_rerank_w<false>;
-        cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        KSC_CUDA(cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         kr<<<(unsigned)((nq + RW_WARPS - 1) / RW_WARPS), RW_WARPS * 32, smem, st>>>(
             Qr, Xr, dr, ix->metric == KSC_IP, rr_keys, rr_R, rr_q, rr_R, pl.k, nq, ids, dists,
             band && ix->x_u8_state != 1 ? (const uint16_t*)ix->X_bf16 : nullptr,
@@ -3714,11 +3714,11 @@ static int search_from_probes(ksc_index* ix, const float* Q, const Plan& pl, con
         // a CTA per query; 1024 threads (more rows in flight) when the batch is
         // too small to fill the GPU with 256-thread CTAs
         if (nq < 2 * (int64_t)num_sms()) {
-            cudaFuncSetAttribute(k_rerank<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            KSC_CUDA(cudaFuncSetAttribute(k_rerank<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             k_rerank<1024><<<(unsigned)nq, 1024, smem, st>>>(Qr, Xr, dr, ix->metric == KSC_IP, rr_keys, rr_R, rr_q,
                                                              rr_R, pl.k, ids, dists);
         } else {
-            cudaFuncSetAttribute(k_rerank<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            KSC_CUDA(cudaFuncSetAttribute(k_rerank<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             k_rerank<256><<<(unsigned)nq, 256, smem, st>>>(Qr, Xr, dr, ix->metric == KSC_IP, rr_keys, rr_R, rr_q,
                                                            rr_R, pl.k, ids, dists);
         }
