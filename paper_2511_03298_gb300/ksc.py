@@ -113,10 +113,12 @@ _SIGS = {
 
 
 def lib_path():
+    """Path of the in-tree shared library."""
     return LIB
 
 
 def lib():
+    """The loaded library (loaded once; raises if it is not built)."""
     global _lib
     if _lib is None:
         if not os.path.exists(LIB):
@@ -188,15 +190,18 @@ class Index:
         self.free()
 
     def free(self):
+        """Release the index's device memory (ksc_index_free); idempotent."""
         if getattr(self, "_h", None) and self._h.value and _lib is not None:
             _lib.ksc_index_free(self._h)
         self._h = C.c_void_p(None)
 
     @property
     def handle(self):
+        """The opaque ksc_index* as a ctypes pointer."""
         return self._h
 
     def info(self):
+        """n, d, nlist, M, metric and spherical of the index (ksc_index_info)."""
         a = IndexArrays()
         _check(lib().ksc_index_info(self._h, C.byref(a)))
         return dict(n=a.n, d=a.d, nlist=a.nlist, M=a.M, metric=a.metric, spherical=a.spherical)
@@ -242,6 +247,8 @@ class Index:
         _check(lib().ksc_index_save(self._h, os.fsencode(path)))
 
     def search(self, Q, k, nprobe, rerank, opts=None, out=None, stream=None):
+        """Alg. 2 with a fixed nprobe (ksc_search): Q [nq x d] fp32 on the device;
+        returns ids [nq x k] int64 and dists [nq x k] fp32 (into `out` if given)."""
         torch = _torch()
         nq = Q.shape[0]
         ids, dists = out if out is not None else (
@@ -252,6 +259,8 @@ class Index:
         return ids, dists
 
     def search_varprobe(self, Q, k, nprobe, rerank, nprobe_max=None, rerank_max=None, opts=None, stream=None):
+        """Alg. 2 with per-query nprobe / rerank (int32 device tensors [nq]),
+        bounded by nprobe_max / rerank_max (ksc_search_varprobe)."""
         torch = _torch()
         nq = Q.shape[0]
         ids = torch.empty((nq, k), dtype=torch.int64, device=Q.device)
@@ -266,6 +275,8 @@ class Index:
         return ids, dists
 
     def search_with_probes(self, Q, probes, k, rerank, want_cands=True, opts=None, stream=None):
+        """Steps a2-a6 on given probe lists (int32 [nq x P], ranked); also the
+        candidate keys [nq x R] and their counts (ksc_search_with_probes)."""
         torch = _torch()
         nq, P = probes.shape
         R = max(rerank, k)
@@ -303,6 +314,8 @@ class Index:
         return ids, dists
 
     def rank_lists(self, Q, P, want_scores=True, stream=None):
+        """Alg. 2 TopNClusters: the P nearest lists per query, ranked, and their
+        exact FP32 scores (ksc_rank_lists)."""
         torch = _torch()
         nq = Q.shape[0]
         probes = torch.empty((nq, P), dtype=torch.int32, device=Q.device)
@@ -324,6 +337,8 @@ class Index:
         return scores, err
 
     def compute_luts(self, Q, probes, stream=None):
+        """Step a2: the 8-bit residual tables [nq x P x M x 16], biases and
+        per-query scales of the given probes (Sec. 2.5, Sec. 4.6.1; ksc_compute_luts)."""
         torch = _torch()
         nq, P = probes.shape
         M = self.info()["M"]
@@ -359,6 +374,8 @@ class Index:
                                                                            int(regression)))))
 
     def predictor_weights(self, set_to=None):
+        """The learned predictor's FP32 parameters (8450 values): read them, or
+        set them from `set_to` (ksc_predictor_weights)."""
         if set_to is not None:
             w = np.ascontiguousarray(set_to, dtype=np.float32)
             _check(lib().ksc_predictor_weights(self._h, None, _hptr(w)))
@@ -368,6 +385,8 @@ class Index:
         return w
 
     def search_adaptive(self, Q, k, opts=None, stream=None):
+        """Alg. 2 with nprobe and rerank per query from the learned predictor and
+        Eq. 2; returns ids, dists and the settings used (ksc_search_adaptive)."""
         torch = _torch()
         nq = Q.shape[0]
         ids = torch.empty((nq, k), dtype=torch.int64, device=Q.device)
@@ -379,6 +398,7 @@ class Index:
         return ids, dists, npb, rr
 
     def query_features(self, Q, stream=None):
+        """The predictor's 64 input features per query [nq x 64] (ksc_query_features)."""
         torch = _torch()
         f = torch.empty((Q.shape[0], 64), dtype=torch.float32, device=Q.device)
         _check(lib().ksc_query_features(self._h, _dptr(Q, torch.float32, "Q"), Q.shape[0], _dptr(f),
@@ -435,6 +455,9 @@ class Index:
         return out
 
     def prune_labels(self, ids, dists, kth, probes, P, stream=None):
+        """Training labels of the pruning classifier per (query, probe rank): 1
+        where the list holds a returned id whose distance is within the true
+        k-th distance kth, else 0 (ksc_prune_labels)."""
         torch = _torch()
         nq, Pmax = probes.shape
         lab = torch.empty((nq, Pmax), dtype=torch.float32, device=ids.device)
@@ -496,6 +519,7 @@ class Index:
     STAGES = ("rank", "worklist", "lut", "near_scan", "scan", "select", "rerank")
 
     def profile(self, on=True):
+        """Turn the per-stage CUDA-event timing of searches on or off."""
         _check(lib().ksc_profile_enable(self._h, int(on)))
 
     def profile_read(self):
@@ -506,6 +530,8 @@ class Index:
         return {k: ms[i] for i, k in enumerate(self.STAGES)}, n.value
 
     def pair_distances(self, Q, ids, precision, stream=None):
+        """Distances of given (query, id) pairs [nq x m] from FP32, BF16 (1) or
+        FP8 (2) rows (ksc_pair_distances)."""
         torch = _torch()
         out = torch.empty(ids.shape, dtype=torch.float32, device=Q.device)
         _check(lib().ksc_pair_distances(self._h, _dptr(Q, torch.float32, "Q"), Q.shape[0],
@@ -520,6 +546,9 @@ class Index:
         return dict(overflow_queries=v[0], candidates=v[1], max_candidates=v[2])
 
     def last_status(self):
+        """The device status word of the last search: 0 clean, else a bitwise OR
+        of KSC_STATUS_* flags (1: a candidate store overflowed and was redone
+        exactly); a blocking read (ksc_last_status)."""
         s = C.c_int32(0)
         _check(lib().ksc_last_status(self._h, C.byref(s)))
         return s.value
@@ -540,6 +569,8 @@ class Plan:
         self._h = C.c_void_p(None)
 
     def execute(self, Q, ids=None, dists=None, stream=None):
+        """Copy Q into the plan's input, replay the captured search and return its
+        results (views of the plan's buffers unless ids / dists are given)."""
         torch = _torch()
         st = stream if stream is not None else torch.cuda.current_stream()
         if ids is None:
@@ -653,4 +684,5 @@ def lut16_peak(stream=None):
 
 
 def version():
+    """Library version and target architecture."""
     return lib().ksc_version().decode()
