@@ -21,17 +21,22 @@ ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EUNSUPPORTED", -5: "ETIM
 
 
 class KscError(RuntimeError):
+    """A non-zero ksc_status with the library's message (ksc_last_error)."""
+
     def __init__(self, code, msg):
         super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
         self.code = code
 
 
 class BuildOpts(C.Structure):
+    """ksc_build_opts: k-means iterations, spherical ranking, build permutation,
+    seed, intra-list graphs, component-filtration threshold (Alg. 1, Sec. 4.3)."""
     _fields_ = [("kmeans_iters", C.c_int32), ("spherical", C.c_int32), ("perm_host", C.c_void_p),
                 ("seed", C.c_uint64), ("build_graph", C.c_int32), ("filter_threshold", C.c_float)]
 
 
 class IndexArrays(C.Structure):
+    """ksc_index_arrays: sizes and host pointers of an index's interchange arrays."""
     _fields_ = [("n", C.c_int64), ("d", C.c_int32), ("nlist", C.c_int32), ("M", C.c_int32),
                 ("metric", C.c_int32), ("spherical", C.c_int32),
                 ("X", C.c_void_p), ("c_rank", C.c_void_p), ("c_mean", C.c_void_p), ("codebook", C.c_void_p),
@@ -39,18 +44,21 @@ class IndexArrays(C.Structure):
 
 
 class AdaptiveParams(C.Structure):
+    """ksc_adaptive_params: Eq. 2's bounds and offsets for nprobe and rerank."""
     _fields_ = [("pmin", C.c_int32), ("pmax", C.c_int32), ("rmin", C.c_int32), ("rmax", C.c_int32),
                 ("p0", C.c_float), ("p1", C.c_float), ("r0", C.c_float), ("r1", C.c_float),
                 ("regression", C.c_int32)]
 
 
 class TrainOpts(C.Structure):
+    """ksc_train_opts: labels (k, target hits, label grids) and training schedule."""
     _fields_ = [("k", C.c_int32), ("target_hits", C.c_int32), ("rerank_label", C.c_int32), ("epochs", C.c_int32),
                 ("batch", C.c_int32), ("lr", C.c_float), ("seed", C.c_uint64), ("grid_host", C.c_void_p),
                 ("ngrid", C.c_int32), ("rgrid_host", C.c_void_p), ("nrgrid", C.c_int32), ("regression", C.c_int32)]
 
 
 class SearchOpts(C.Structure):
+    """ksc_search_opts (see search_opts() for the fields' meaning)."""
     _fields_ = [("lanes_per_query", C.c_int32), ("hybrid", C.c_int32), ("n_near", C.c_int32),
                 ("efs", C.c_int32), ("tau", C.c_int32), ("cand_cap", C.c_int32), ("rank_fp32", C.c_int32),
                 ("precision", C.c_int32), ("rerank_final", C.c_int32), ("tile_blocks", C.c_int32),
