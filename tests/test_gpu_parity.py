@@ -486,16 +486,29 @@ def test_tied_list_scores_take_the_general_selection(torch, ksc):
     assert g.last_status() == 0
 
 
-@pytest.mark.parametrize("kind", ["l2", "ip", "m50", "small"])
+def byte_index():
+    """The 10k x 128 set mapped onto integer coordinates in [0, 255]: rows
+    12 x + 128 rounded and clipped, centroids and codebooks mapped with them
+    (so the codes still encode the rows), queries 12 q + 128."""
+    ix, Q = small_index("small")
+    X = np.clip(np.rint(12.0 * np.asarray(ix["X"], np.float64) + 128.0), 0, 255).astype(np.float32)
+    assert X.min() >= 0 and X.max() <= 255 and np.all(X == np.rint(X))
+    out = dict(ix, X=X, c_rank=(12.0 * np.asarray(ix["c_rank"], np.float64) + 128.0).astype(np.float32),
+               c_mean=(12.0 * np.asarray(ix["c_mean"], np.float64) + 128.0).astype(np.float32),
+               codebook=(12.0 * np.asarray(ix["codebook"], np.float64)).astype(np.float32))
+    return out, (12.0 * np.asarray(Q, np.float64) + 128.0).astype(np.float32)
+
+
+@pytest.mark.parametrize("kind", ["l2", "ip", "m50", "small", "bytes"])
 def test_band_rerank_equals_fp32_rerank(torch, ksc, kind):
     """The exact re-rank's band (U8 or BF16 rows bound every candidate's FP32
     distance; only candidates whose lower bound reaches the k-th upper bound
     are read in FP32) returns what reading every candidate in FP32 returns,
     for L2 and inner products, several k and R, a fixed and a per-query R,
     in the warp-per-query shape (1600 queries); rows of real values (d = 64,
-    48, 100: BF16 rows) and integer rows in [0, 255] (the 10k x 128 set: U8
-    rows, exact, whose band is the FP32 evaluation term alone)."""
-    ix, Q = small_index(kind)
+    48, 100, 128: BF16 rows) and rows of integers in [0, 255] (U8 rows, exact,
+    whose band is the FP32 evaluation term alone)."""
+    ix, Q = byte_index() if kind == "bytes" else small_index(kind)
     g = gpu_index(ksc, ix)
     reps = 1600 // len(Q) + 1
     Qd = torch.from_numpy(np.tile(Q, (reps, 1))).cuda()
@@ -519,7 +532,7 @@ def test_band_on_rows_that_do_not_fit_bytes(torch, ksc, bump):
     fraction 0.3 that BF16 cannot hold either, the value 256, the value -1)
     take the BF16 band, with a rounding-error bound of 0 for the rows BF16
     still holds exactly; the results are still those of the FP32 re-rank."""
-    ix, Q = small_index("small")
+    ix, Q = byte_index()
     rng = np.random.default_rng({"frac": 21, "256": 22, "neg": 23}[bump])
     X = np.array(ix["X"], dtype=np.float32, copy=True)
     rows = rng.choice(len(X), 300, replace=False)
