@@ -95,13 +95,15 @@ def row_bounds(x, xb):
         float(np.nextafter(np.float32(r), np.float32(np.inf))) if r > 0 else 0.0
 
 
-def bound_l2(dt, r):
+def bound_l2(dt, r, mistake=None):
     sq = np.sqrt(max(float(dt), 0.0) * (1 + 2 * G)) * (1 + 2.0 ** -20)
-    return (2 * r * sq + r * r + G * (sq * sq + (sq + r) ** 2)) * SAFE
+    two = 1.0 if mistake == "r s in place of 2 r s" else 2.0
+    return (two * r * sq + r * r + G * (sq * sq + (sq + r) ** 2)) * SAFE
 
 
-def bound_ip(qn, n, r):
-    return qn * (1 + 2.0 ** -18) * (r + 2.01 * G * (n + r)) * SAFE
+def bound_ip(qn, n, r, mistake=None):
+    rr = r / 2 if mistake == "r / 2 for inner products" else r
+    return qn * (1 + 2.0 ** -18) * (rr + 2.01 * G * (n + r)) * SAFE
 
 
 def cases(rng, d):
@@ -115,13 +117,21 @@ def cases(rng, d):
     yield rng.uniform(0, 255, size=d), np.rint(rng.uniform(0, 255, size=d))  # integer row: r = 0
     x = np.rint(rng.uniform(0, 255, size=d))
     yield x + rng.normal(size=d) * 0.01, x                             # integer row, query close by
+    # queries along the row's own rounding error, where Cauchy-Schwarz is tight:
+    # <q, x~ - x> = |q| r (inner products), q - x~ parallel to x~ - x (L2)
+    x = rng.normal(size=d).astype(np.float32)
+    dx = bf16(x).astype(np.float64) - x
+    u = dx / np.linalg.norm(dx)
+    yield 3.0 * u, x
+    yield bf16(x) + 5.0 * u, x
 
 
-@pytest.mark.parametrize("d", [16, 100, 128])
-def test_band_bound_holds(d):
+def worst_ratios(d, mistake=None, draws=60):
+    """Largest |d~ - d| / e for L2 and for inner products over the cases,
+    nine pairs of summation orders each."""
     rng = np.random.default_rng(d)
-    worst = 0.0
-    for _ in range(60):
+    wl = wi = 0.0
+    for _ in range(draws):
         for q, x in cases(rng, d):
             q = q.astype(np.float32)
             x = x.astype(np.float32)
@@ -136,13 +146,29 @@ def test_band_bound_holds(d):
                 i32 = float(ip_f32(q, x, o_exact))
                 for o_bf in ORDERS:
                     db = float(l2_f32(q, xb, o_bf))
-                    e = bound_l2(db, r)
-                    assert abs(db - d32) <= e, (d, o_exact, o_bf, db, d32, e)
-                    worst = max(worst, abs(db - d32) / e if e > 0 else 0.0)
+                    e = bound_l2(db, r, mistake)
+                    dev = abs(db - d32)
+                    wl = max(wl, dev / e if e > 0 else (0.0 if dev == 0 else np.inf))
                     ib = float(ip_f32(q, xb, o_bf))
-                    ei = bound_ip(qn, n, r)
-                    assert abs(ib - i32) <= ei, (d, o_exact, o_bf, ib, i32, ei)
-    assert worst < 1.0
+                    ei = bound_ip(qn, n, r, mistake)
+                    dev = abs(ib - i32)
+                    wi = max(wi, dev / ei if ei > 0 else (0.0 if dev == 0 else np.inf))
+    return wl, wi
+
+
+@pytest.mark.parametrize("d", [16, 100, 128])
+def test_band_bound_holds(d):
+    wl, wi = worst_ratios(d)
+    assert wl < 1.0 and wi <= 1.0, (d, wl, wi)
+
+
+@pytest.mark.parametrize("mistake", ["r s in place of 2 r s", "r / 2 for inner products"])
+def test_band_pin_catches_a_smaller_bound(mistake):
+    """The same check with a plausible mistake planted in the restated bound
+    (the cross term's factor 2 dropped, half the row's error for inner
+    products) fails on the rows above."""
+    wl, wi = worst_ratios(128, mistake)
+    assert (wl if mistake.startswith("r s") else wi) > 1.0, (mistake, wl, wi)
 
 
 def test_integer_rows_band_is_the_evaluation_term():

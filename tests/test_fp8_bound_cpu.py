@@ -64,12 +64,12 @@ def dots(Cq, qq, mode):
     return acc.astype(np.float32)
 
 
-def fp8_rel(d):
-    return (2 * U + U * U) + 2 * (1 + U) * 2.0 ** -10 * np.sqrt(d) / 128 + d * 2.0 ** -13 * (1 + U) ** 2 + 1e-6
+def fp8_rel(d, u=U, two=2.0):
+    return (two * u + u * u) + 2 * (1 + u) * 2.0 ** -10 * np.sqrt(d) / 128 + d * 2.0 ** -13 * (1 + u) ** 2 + 1e-6
 
 
-def bound(qn, cmax, d, spherical):
-    e = fp8_rel(d) * qn * cmax * 1.0001
+def bound(qn, cmax, d, spherical, rel=fp8_rel):
+    e = rel(d) * qn * cmax * 1.0001
     r = (d + 8) * 1.2e-7 * (qn + cmax) ** 2
     return (e if spherical else 2 * e) + r
 
@@ -119,9 +119,8 @@ def test_row_scale_peaks_in_128_256():
     assert np.all((peak >= 128) & (peak < 256))
 
 
-@pytest.mark.parametrize("kind", ["normal", "range", "spike", "aligned"])
-@pytest.mark.parametrize("spherical", [False, True])
-def test_fp8_score_bound_holds(kind, spherical):
+def worst_ratio(kind, spherical, rel=fp8_rel):
+    """Largest |given - exact| / err over 20 draws and three accumulations."""
     rng = np.random.default_rng(hash(("fp8", kind, spherical)) % 2 ** 32)
     d, L = 128, 64
     worst = 0.0
@@ -132,7 +131,7 @@ def test_fp8_score_bound_holds(kind, spherical):
         cn = (C.astype(np.float64) ** 2).sum(1)
         cmax = float(np.sqrt(np.float32(cn.max())))
         qn = float(np.sqrt(np.float32((q.astype(np.float64) ** 2).sum())))
-        err = bound(qn, cmax, d, spherical)
+        err = bound(qn, cmax, d, spherical, rel)
         sc, sq = row_scale(C), row_scale(q[None, :])[0]
         Cq, qq = e4m3(C / sc[:, None]), e4m3(q / sq)
         exact = -(C.astype(np.float64) @ q) if spherical else cn - 2.0 * (C.astype(np.float64) @ q)
@@ -143,8 +142,23 @@ def test_fp8_score_bound_holds(kind, spherical):
             else:
                 given = np.array([np.float32(np.float32(-2.0) * dot[i] + np.float32(cn[i])) for i in range(L)],
                                  dtype=np.float64)
-            dev = np.abs(given - exact)
-            assert np.all(dev <= err), (kind, mode, float(dev.max()), err)
-            worst = max(worst, float(dev.max() / err))
-    if kind == "aligned":  # the operand rounding's term is nearly attained: a factor 2 or a bit short fails
+            worst = max(worst, float(np.abs(given - exact).max() / err))
+    return worst
+
+
+@pytest.mark.parametrize("kind", ["normal", "range", "spike", "aligned"])
+@pytest.mark.parametrize("spherical", [False, True])
+def test_fp8_score_bound_holds(kind, spherical):
+    worst = worst_ratio(kind, spherical)
+    assert worst <= 1.0, (kind, worst)
+    if kind == "aligned":  # the operand rounding's term is nearly attained
         assert worst > 0.75, worst
+
+
+@pytest.mark.parametrize("mistake", ["u = 2^-5", "u in place of 2u"])
+def test_fp8_pin_catches_a_smaller_bound(mistake):
+    """The same check with a plausible mistake planted in the restated bound
+    (one bit too many for e4m3, the factor 2 of the two operands' rounding
+    dropped) fails on the aligned rows."""
+    rel = (lambda d: fp8_rel(d, u=2.0 ** -5)) if mistake == "u = 2^-5" else (lambda d: fp8_rel(d, two=1.0))
+    assert worst_ratio("aligned", True, rel) > 1.0

@@ -39,10 +39,12 @@ def dot_f32(a, b, pairwise):
     return t[0]
 
 
-def bound(qn, cmax, d, fp16, spherical):
+def bound(qn, cmax, d, fp16, spherical, mistake=None):
     u2 = 9.77e-4 + 1e-6 if fp16 else 0.0078125 + 6.2e-5
+    if mistake == "u halved":
+        u2 /= 2
     rel = u2 + d * 4.8e-7
-    sub = 2.0 ** -25 * np.sqrt(d) * (qn + cmax) * 1.01 if fp16 else 0.0
+    sub = 2.0 ** -25 * np.sqrt(d) * (qn + cmax) * 1.01 if fp16 and mistake != "no subnormal term" else 0.0
     e = (rel * qn * cmax + sub) * 1.0001
     r = (d + 8) * 1.2e-7 * (qn + cmax) ** 2
     return (e if spherical else 2 * e) + r
@@ -70,12 +72,12 @@ def data(rng, kind, d, L):
     raise ValueError(kind)
 
 
-@pytest.mark.parametrize("kind", ["normal", "tiny", "range", "big", "aligned", "aligned_bf16"])
-@pytest.mark.parametrize("spherical", [False, True])
-def test_16bit_score_bound_holds(kind, spherical):
+def worst_ratio(kind, spherical, mistake=None):
+    """Largest |given - exact| / err over 20 draws and two summation orders;
+    also whether FP16 operands were used."""
     rng = np.random.default_rng(hash((kind, spherical)) % 2 ** 32)
     d, L = 96, 64
-    worst = 0.0
+    worst, fp16 = 0.0, None
     for _ in range(20):
         C, q = data(rng, kind, d, L)
         C = C.astype(np.float32)
@@ -86,7 +88,7 @@ def test_16bit_score_bound_holds(kind, spherical):
         cn = (C.astype(np.float64) ** 2).sum(1)
         cmax = np.float32(np.sqrt(np.float32(cn.max())))
         qn = float(np.sqrt(np.float32((q.astype(np.float64) ** 2).sum())))
-        err = bound(qn, float(cmax), d, fp16, spherical)
+        err = bound(qn, float(cmax), d, fp16, spherical, mistake)
         qt, Ct = r16(q, fp16), r16(C, fp16)
         exact = -(C.astype(np.float64) @ q) if spherical else cn - 2.0 * (C.astype(np.float64) @ q)
         for pw in (False, True):
@@ -95,9 +97,24 @@ def test_16bit_score_bound_holds(kind, spherical):
                 given = -dot
             else:
                 given = np.array([np.float32(np.float32(-2.0) * dot[i] + np.float32(cn[i])) for i in range(L)])
-            dev = np.abs(given.astype(np.float64) - exact)
-            assert np.all(dev <= err), (kind, fp16)
-            worst = max(worst, float(dev.max() / err))
-    if kind.startswith("aligned"):  # the operand term nearly attained: u halved fails
+            worst = max(worst, float(np.abs(given.astype(np.float64) - exact).max() / err))
+    return worst, fp16
+
+
+@pytest.mark.parametrize("kind", ["normal", "tiny", "range", "big", "aligned", "aligned_bf16"])
+@pytest.mark.parametrize("spherical", [False, True])
+def test_16bit_score_bound_holds(kind, spherical):
+    worst, fp16 = worst_ratio(kind, spherical)
+    assert worst <= 1.0, (kind, fp16, worst)
+    if kind.startswith("aligned"):  # the operand term nearly attained
         assert fp16 == (kind == "aligned")
         assert worst > 0.75, worst
+
+
+@pytest.mark.parametrize("mistake,kind", [("u halved", "aligned"), ("u halved", "aligned_bf16"),
+                                          ("no subnormal term", "tiny")])
+def test_16bit_pin_catches_a_smaller_bound(mistake, kind):
+    """The same check with a plausible mistake planted in the restated bound
+    (the unit roundoff of FP16 or BF16 halved, FP16's subnormal term left
+    out) fails on the rows built for it."""
+    assert worst_ratio(kind, True, mistake)[0] > 1.0
